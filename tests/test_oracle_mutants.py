@@ -1,0 +1,94 @@
+"""The pins must catch plausible mistakes in the oracle.
+
+Each case plants one mistake (a wrong comparison, a dropped term, a wrong
+index) in a temporary copy of ``oracle/peel_oracle.c``, compiles it on the CPU,
+swaps it in, and runs the pin tests against it: at least one pin has to fail.
+"""
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+import pytest
+
+import oracle
+import test_oracle_pins as pins
+
+MUTANTS = [
+    ("round removes degree <= k",
+     "if (vround[v] == 0 && deg[v] < (int64_t)k) ++nr;",
+     "if (vround[v] == 0 && deg[v] <= (int64_t)k) ++nr;"),
+    ("removed edge decrements only its first endpoint",
+     "for (uint32_t j = 0; j < r; ++j) deg[edges[e * r + j]] -= 1;",
+     "for (uint32_t j = 0; j < 1; ++j) deg[edges[e * r + j]] -= 1;"),
+    ("queue peeler pushes at the wrong crossing",
+     "if (deg[u] == (int64_t)k - 1 && v_core[u]) stack[top++] = u;",
+     "if (deg[u] == (int64_t)k && v_core[u]) stack[top++] = u;"),
+    ("edge removal tested against the previous round",
+     "if (vround[edges[e * r + j]] == (int32_t)round) hit = 1;",
+     "if (vround[edges[e * r + j]] == (int32_t)round - 1) hit = 1;"),
+    ("hash uses sub-table 0's seed for every sub-table",
+     "uint64_t h = mix64(x ^ seeds[j]);",
+     "uint64_t h = mix64(x ^ seeds[0]);"),
+    ("checksum not removed on recovery",
+     "        keyx[c] ^= x;\n        chkx[c] ^= cs;\n      }\n      out_keys[total + i] = x;",
+     "        keyx[c] ^= x;\n      }\n      out_keys[total + i] = x;"),
+    ("pure test drops the checksum comparison",
+     "return count[c] == 1 && chkx[c] == checksum_of(keyx[c], seeds, r);",
+     "return count[c] == 1 || chkx[c] == checksum_of(keyx[c], seeds, r);"),
+    ("a key pure in two cells is recovered twice",
+     "if (i == 0 || pure_keys[i] != pure_keys[i - 1]) pure_keys[nk++] = pure_keys[i];",
+     "pure_keys[nk++] = pure_keys[i];"),
+    ("surviving cells counted from degree 1",
+     "if (count[c] >= 2) ++alive;",
+     "if (count[c] >= 1) ++alive;"),
+    ("sub-table split puts the remainder last",
+     "off[j + 1] = off[j] + q + (j < rem ? 1 : 0);",
+     "off[j + 1] = off[j] + q + (j >= r - rem ? 1 : 0);"),
+    ("mix64 shift constant off by one",
+     "z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;",
+     "z = (z ^ (z >> 28)) * 0x94D049BB133111EBULL;"),
+]
+
+PINS = [
+    lambda: pins.test_mix64_published_splitmix_vector(),
+    lambda: pins.test_hash_known_answers(),
+    lambda: pins.test_part_offsets_headline(),
+    lambda: [pins.test_handmade_cores(*h) for h in pins.HANDMADE],
+    lambda: pins.test_handmade_expected_values(),
+    lambda: pins.test_random_tiny_hypergraphs_vs_brute_force(),
+    lambda: pins.test_iblt_build_definition(),
+    lambda: pins.test_iblt_rounds_equal_kcore_rounds(4000, 3, 0.7, 1),
+    lambda: pins.test_iblt_rounds_equal_kcore_rounds(3000, 4, 0.85, 3),
+    lambda: pins.test_iblt_below_threshold_recovered_inserted_set_wrapper(),
+    lambda: pins.test_iblt_residue_invariants_above_threshold(),
+    lambda: pins.test_iblt_checksum_rejects_impure_count_one(),
+]
+
+
+def _compile_mutant(tmp_path, old, new):
+    src = open(os.path.join(os.path.dirname(oracle.__file__), "peel_oracle.c")).read()
+    assert src.count(old) == 1, old
+    path = tmp_path / "mutant.c"
+    path.write_text(src.replace(old, new))
+    so = tmp_path / "mutant.so"
+    subprocess.check_call(["gcc", "-O1", "-std=c11", "-shared", "-fPIC", "-o", str(so), str(path)])
+    return oracle.configure(ctypes.CDLL(str(so)))
+
+
+@pytest.mark.parametrize("name,old,new", MUTANTS, ids=[m[0] for m in MUTANTS])
+def test_pins_catch_mutant(tmp_path, monkeypatch, name, old, new):
+    mutant = _compile_mutant(tmp_path, old, new)
+    monkeypatch.setattr(oracle, "_lib", mutant)
+    caught = []
+    for i, pin in enumerate(PINS):
+        try:
+            pin()
+        except Exception as exc:   # an assertion or a crash-free error both count
+            caught.append((i, type(exc).__name__))
+    assert caught, f"no pin failed for planted mistake: {name}"
+
+
+def test_unmutated_oracle_passes_every_pin():
+    for pin in PINS:
+        pin()
