@@ -1,0 +1,202 @@
+/* ppeel -- round-synchronous parallel peeling on one B300 (sm_103a).
+ *
+ * C ABI of libppeel.so.  The operations follow Jiang, Mitzenmacher & Thaler,
+ * "Parallel Peeling Algorithms":
+ *   - peeling (Sec. 1): repeatedly remove vertices of degree < k with their
+ *     edges; what remains is the k-core, unique and independent of the order;
+ *   - the parallel round (Sec. 1, Sec. 3.1): one round removes every vertex
+ *     whose degree is < k at the start of the round, all at once, together
+ *     with every edge that touches one of them;
+ *   - Invertible Bloom Lookup Tables (Sec. 6): each key is XORed, with its
+ *     checksum, into one cell of each of r sub-tables (App. B); a pure cell
+ *     holds exactly one key; recovery is the k = 2 peel of the hypergraph whose
+ *     vertices are cells and whose edges are keys, and succeeds iff that
+ *     hypergraph's 2-core is empty.
+ *
+ * General rules for every entry point:
+ *   - Pointers named d_* are device pointers owned by the caller; pointers
+ *     named h_* and result structs are host memory owned by the caller.
+ *   - Handles (pp_iblt, pp_batch, pp_server) own their device memory.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  Work is ordered on that stream.  Calls that return results in a
+ *     host struct (decode, peel) synchronize that stream before returning;
+ *     insert and clear only enqueue work.
+ *   - Every call returns a pp_status; no exception or longjmp crosses the ABI.
+ *     pp_last_error() gives a one-line message for the calling thread's last
+ *     failure.  A status other than PP_OK leaves output buffers unspecified
+ *     unless stated otherwise.
+ *   - Vertex ids, cell ids and edge ids are 32-bit: n, n_cells and m*r must be
+ *     below 2^32 - 64.  1 <= k, 2 <= r <= PP_MAX_R.
+ */
+#ifndef PPEEL_H
+#define PPEEL_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define PP_MAX_R 8
+
+typedef enum pp_status {
+  PP_OK = 0,
+  PP_ERR_INVALID_ARG = 1,   /* bad size, null pointer, out-of-range id, ... */
+  PP_ERR_OUT_OF_MEMORY = 2, /* a device or host allocation failed */
+  PP_ERR_CAPACITY = 3,      /* an output buffer is too small */
+  PP_ERR_ROUND_LIMIT = 4,   /* max_rounds reached with vertices still peelable */
+  PP_ERR_TIMEOUT = 5,       /* a bounded wait ran out (server, batch engine) */
+  PP_ERR_CUDA = 6,          /* a CUDA runtime call failed; see pp_last_error */
+  PP_ERR_BUSY = 7,          /* server: result not ready / queue full */
+  PP_ERR_NOT_FOUND = 8      /* server: unknown ticket */
+} pp_status;
+
+/* Tuning knobs.  Zero in any field selects the default. */
+typedef struct pp_options {
+  uint32_t block;        /* threads per CTA of the round kernels (default 256) */
+  uint32_t ctas_per_sm;  /* persistent grid = ctas_per_sm * #SMs, capped by occupancy (default 8) */
+  uint32_t max_rounds;   /* stop after this many rounds (default 65535) */
+  uint32_t host_loop;    /* 1 = drive rounds from the host (one sync per round);
+                            0 (default) = one CUDA graph whose while-node keeps
+                            looping on the device until the frontier is empty */
+  uint32_t stats_rounds; /* batch: per-table per-round counters kept (default 128) */
+  uint32_t reserved[3];
+} pp_options;
+
+/* Fills *opt with the defaults above. */
+void pp_options_default(pp_options *opt);
+
+/* Human-readable name of a status code (static storage). */
+const char *pp_status_string(pp_status s);
+
+/* Message describing the calling thread's most recent failure ("" if none). */
+const char *pp_last_error(void);
+
+/* ------------------------------------------------------------------------
+ * IBLT (Sec. 6 "Motivation" and "Implementation Details"; App. B layout)
+ *
+ * Cell layout in device memory (32 bytes, 32-byte aligned, cell i at
+ * byte 32*i of the table):
+ *     uint64 key_xor;   XOR of the keys in the cell
+ *     uint64 chk_xor;   XOR of checkSum(key) of those keys
+ *     int32  count;     number of keys in the cell (inserts - deletes)
+ *     uint32 reserved[3];
+ * Cells are split into r sub-tables, in order; sub-table j holds
+ * floor(n/r) + [j < n mod r] cells.  Key x lives in cell
+ *     off_j + floor(mix64(x ^ s_j) * size_j / 2^64)   of each sub-table j,
+ * and checkSum(x) = mix64(x ^ s_r), where mix64 is the SplitMix64 finaliser
+ * and s_0..s_r are outputs 1..r+1 of SplitMix64 started at the table seed.
+ * A cell is pure iff count == 1 and chk_xor == checkSum(key_xor).
+ * ------------------------------------------------------------------------ */
+typedef struct pp_iblt pp_iblt;
+
+typedef struct pp_cell {
+  uint64_t key_xor;
+  uint64_t chk_xor;
+  int32_t count;
+  uint32_t reserved[3];
+} pp_cell;
+
+/* Result of a decode.  The caller sets round_cap and the three array pointers
+ * (host arrays of round_cap entries each, or NULL); the decode fills the rest.
+ * Entry t-1 describes round t, for t = 1..min(rounds, round_cap):
+ *   recovered_per_round[t-1]   keys recovered in round t;
+ *   remaining_per_round[t-1]   keys still in the table after round t;
+ *   alive_cells_per_round[t-1] cells holding >= 2 keys at the start of round
+ *                              t, i.e. the hypergraph's vertices that survive
+ *                              round t (Sec. 3.1's survivors at k = 2). */
+typedef struct pp_decode_result {
+  uint32_t rounds;          /* rounds that recovered >= 1 key */
+  uint32_t status_flags;    /* device-side flags (0 = clean) */
+  uint64_t recovered;       /* keys written to d_out_keys */
+  uint64_t items_before;    /* keys in the table before the decode */
+  uint64_t residual_cells;  /* non-empty cells after the decode (2-core residue) */
+  uint32_t round_cap;
+  uint32_t pad;
+  uint64_t *recovered_per_round;
+  uint64_t *remaining_per_round;
+  uint64_t *alive_cells_per_round;
+} pp_decode_result;
+
+/* Creates an empty (all-zero) table of n_cells cells for r hash functions.
+ * Allocates the table (32 B/cell) and the decode workspace (~17 B/cell).
+ * Errors: INVALID_ARG (r outside 2..PP_MAX_R, n_cells < r or too large),
+ * OUT_OF_MEMORY, CUDA. */
+pp_status pp_iblt_create(pp_iblt **out, uint64_t n_cells, uint32_t r, uint64_t seed,
+                         const pp_options *opt);
+
+/* Frees the table and its workspace (synchronizes the device first).  NULL is a no-op. */
+pp_status pp_iblt_destroy(pp_iblt *t);
+
+/* Zeroes every cell (enqueued on `stream`). */
+pp_status pp_iblt_clear(pp_iblt *t, void *stream);
+
+/* Inserts m keys (Sec. 6 "Motivation": XOR the key and its checksum into its r
+ * cells and add 1 to their counts).  d_keys: m uint64 on the device.  Keys are
+ * a set: inserting a key twice makes both copies unrecoverable.  Enqueued on
+ * `stream`; the caller keeps d_keys alive until the stream reaches this work. */
+pp_status pp_iblt_insert(pp_iblt *t, const uint64_t *d_keys, uint64_t m, void *stream);
+
+/* Deletes m keys: the same XORs with count -1 (Sec. 6: insertion and deletion
+ * are identical XOR operations). */
+pp_status pp_iblt_delete(pp_iblt *t, const uint64_t *d_keys, uint64_t m, void *stream);
+
+/* Round-synchronous recovery (Sec. 6 recovery; Sec. 1 rounds at k = 2).
+ * Round t recovers every key that is alone in some cell at the start of round
+ * t (each such key once, however many of its cells are pure), then deletes
+ * those keys from all their cells.  Stops at the first round that recovers
+ * nothing.  The table is decoded in place: afterwards it holds the 2-core
+ * residue (all zero iff every key was recovered).
+ * d_out_keys: out_cap uint64 on the device; receives the recovered keys grouped
+ * by round (round 1 first), in no particular order within a round.
+ * out_cap must be >= the number of keys in the table, else CAPACITY (nothing
+ * is decoded).  ROUND_LIMIT if opt.max_rounds rounds did not finish; the table
+ * is then left after the last completed round and *res describes those rounds.
+ * Synchronizes `stream`. */
+pp_status pp_iblt_decode(pp_iblt *t, uint64_t *d_out_keys, uint64_t out_cap,
+                         pp_decode_result *res, void *stream);
+
+/* Copies `count` cells starting at `first` into dst (device memory if
+ * to_host == 0, else host memory), on `stream`, and synchronizes it. */
+pp_status pp_iblt_copy_cells(pp_iblt *t, void *dst, uint64_t first, uint64_t count,
+                             int to_host, void *stream);
+
+/* Number of cells, r, and the r+1 derived seeds (hash seeds, then checksum seed). */
+pp_status pp_iblt_info(const pp_iblt *t, uint64_t *n_cells, uint32_t *r, uint64_t *h_seeds);
+
+/* ------------------------------------------------------------------------
+ * k-core peeling of an explicit hypergraph (Sec. 1; Sec. 3.1 round rule)
+ * ------------------------------------------------------------------------ */
+typedef struct pp_peel_result {
+  uint32_t rounds;        /* T: rounds that removed >= 1 vertex */
+  uint32_t status_flags;
+  uint64_t core_vertices; /* |V_T| */
+  uint64_t core_edges;    /* |E_T| */
+  uint32_t round_cap;     /* in: entries in the two host arrays below */
+  uint32_t pad;
+  uint64_t *vertices_left; /* out: s_t = vertices left after round t (may be NULL) */
+  uint64_t *edges_left;    /* out: m_t = edges left after round t (may be NULL) */
+} pp_peel_result;
+
+/* Peels the r-uniform hypergraph with n vertices and m edges to its k-core.
+ * d_edges: m*r uint32 vertex ids, row-major (edge e = d_edges[e*r .. e*r+r-1]).
+ * A vertex's degree counts incidences: an edge naming a vertex twice adds 2.
+ * Round t removes every vertex whose degree is < k at the start of round t and
+ * every edge touching one of them.
+ * d_vertex_round (n int32, or NULL): round each vertex was removed in, 0 = in
+ * the k-core.  d_edge_round (m int32, or NULL): the same for edges.
+ * Workspace (~16 B per vertex + 4 B per incidence) is taken from the stream's
+ * memory pool and returned before the call ends.
+ * Errors: INVALID_ARG (k < 1, r outside 2..PP_MAX_R, a vertex id >= n -- the
+ * id check runs on the device), ROUND_LIMIT, OUT_OF_MEMORY, CUDA.
+ * Synchronizes `stream`. */
+pp_status pp_peel_kcore(uint32_t n, uint32_t r, uint32_t k, const uint32_t *d_edges,
+                        uint64_t m, int32_t *d_vertex_round, int32_t *d_edge_round,
+                        pp_peel_result *res, const pp_options *opt, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PPEEL_H */

@@ -1,0 +1,200 @@
+"""Round-synchronous parallel peeling on one B300 (Python binding of libppeel.so).
+
+Every operation runs in the CUDA kernels of ``libppeel.so``; this module only
+marshals arguments (torch CUDA tensors for device memory, the current torch
+stream) and turns status codes into exceptions.  Names follow the C ABI in
+``include/ppeel.h``:
+
+* ``IBLT`` / ``iblt_create``, ``iblt_insert``, ``iblt_delete``, ``iblt_decode``
+  -- Invertible Bloom Lookup Tables (Sec. 6 of Jiang, Mitzenmacher & Thaler,
+  "Parallel Peeling Algorithms"), decoded by round-synchronous peeling at k=2.
+* ``peel_kcore`` -- round-synchronous k-core peeling of an explicit r-uniform
+  hypergraph (Sec. 1, Sec. 3.1).
+"""
+from __future__ import annotations
+
+import ctypes
+from dataclasses import dataclass, field
+
+from . import _lib
+from ._lib import PP_MAX_R, Cell, DecodeResult, Options, PeelResult
+
+__all__ = ["PPError", "IBLT", "iblt_create", "iblt_insert", "iblt_delete", "iblt_decode",
+           "peel_kcore", "options", "PP_MAX_R"]
+
+
+class PPError(RuntimeError):
+    def __init__(self, status: int, fn: str, msg: str):
+        self.status = status
+        self.name = _lib.STATUS.get(status, f"status {status}")
+        super().__init__(f"{fn}: {self.name}: {msg}")
+
+
+def _check(status: int, fn: str):
+    if status != 0:
+        msg = _lib.load().pp_last_error()
+        raise PPError(status, fn, msg.decode() if msg else "")
+
+
+def options(**kw) -> Options:
+    """A pp_options struct with defaults, overridden by keyword arguments."""
+    o = Options()
+    _lib.load().pp_options_default(ctypes.byref(o))
+    for k, v in kw.items():
+        setattr(o, k, int(v))
+    return o
+
+
+def _stream_ptr(stream=None):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(int(s.cuda_stream))
+
+
+def _dev_ptr(t, elem_size: int, what: str):
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError(f"{what} must be a CUDA tensor")
+    if t.element_size() != elem_size:
+        raise ValueError(f"{what} must have {elem_size}-byte elements")
+    if not t.is_contiguous():
+        raise ValueError(f"{what} must be contiguous")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+@dataclass
+class DecodeOutcome:
+    rounds: int
+    recovered: int
+    items_before: int
+    residual_cells: int
+    status_flags: int
+    recovered_per_round: list = field(default_factory=list)
+    remaining_per_round: list = field(default_factory=list)
+    alive_cells_per_round: list = field(default_factory=list)
+
+
+@dataclass
+class PeelOutcome:
+    rounds: int
+    core_vertices: int
+    core_edges: int
+    status_flags: int
+    vertices_left: list = field(default_factory=list)
+    edges_left: list = field(default_factory=list)
+
+
+class IBLT:
+    """An IBLT of ``n_cells`` cells and ``r`` hash functions on the current CUDA device."""
+
+    def __init__(self, n_cells: int, r: int, seed: int, opts: Options | None = None):
+        lib = _lib.load()
+        h = ctypes.c_void_p()
+        _check(lib.pp_iblt_create(ctypes.byref(h), int(n_cells), int(r), int(seed) & (2**64 - 1),
+                                  ctypes.byref(opts) if opts is not None else None),
+               "pp_iblt_create")
+        self._h = h
+        self.n_cells, self.r, self.seed = int(n_cells), int(r), int(seed)
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            _lib.load().pp_iblt_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def handle(self):
+        return self._h
+
+    def clear(self, stream=None):
+        _check(_lib.load().pp_iblt_clear(self._h, _stream_ptr(stream)), "pp_iblt_clear")
+
+    def insert(self, keys, stream=None):
+        _check(_lib.load().pp_iblt_insert(self._h, _dev_ptr(keys, 8, "keys"), keys.numel(),
+                                          _stream_ptr(stream)), "pp_iblt_insert")
+
+    def delete(self, keys, stream=None):
+        _check(_lib.load().pp_iblt_delete(self._h, _dev_ptr(keys, 8, "keys"), keys.numel(),
+                                          _stream_ptr(stream)), "pp_iblt_delete")
+
+    def decode(self, out, round_cap: int = 4096, stream=None) -> DecodeOutcome:
+        """Decode in place; ``out`` (CUDA, 8-byte elements) receives the keys."""
+        rec = (ctypes.c_uint64 * round_cap)()
+        rem = (ctypes.c_uint64 * round_cap)()
+        alive = (ctypes.c_uint64 * round_cap)()
+        res = DecodeResult()
+        res.round_cap = round_cap
+        res.recovered_per_round = ctypes.cast(rec, ctypes.POINTER(ctypes.c_uint64))
+        res.remaining_per_round = ctypes.cast(rem, ctypes.POINTER(ctypes.c_uint64))
+        res.alive_cells_per_round = ctypes.cast(alive, ctypes.POINTER(ctypes.c_uint64))
+        st = _lib.load().pp_iblt_decode(self._h, _dev_ptr(out, 8, "out"),
+                                        out.numel() if out is not None else 0, ctypes.byref(res),
+                                        _stream_ptr(stream))
+        _check(st, "pp_iblt_decode")
+        n = min(res.rounds, round_cap)
+        return DecodeOutcome(res.rounds, res.recovered, res.items_before, res.residual_cells,
+                             res.status_flags, list(rec[:n]), list(rem[:n]), list(alive[:n]))
+
+    def cells(self, stream=None):
+        """Host copy of the table as a numpy structured array (key_xor, chk_xor, count)."""
+        import numpy as np
+        dt = np.dtype([("key_xor", "<u8"), ("chk_xor", "<u8"), ("count", "<i4"), ("reserved", "<u4", 3)])
+        out = np.zeros(self.n_cells, dtype=dt)
+        _check(_lib.load().pp_iblt_copy_cells(self._h, ctypes.c_void_p(out.ctypes.data), 0,
+                                              self.n_cells, 1, _stream_ptr(stream)),
+               "pp_iblt_copy_cells")
+        return out
+
+    def seeds(self) -> list[int]:
+        n = ctypes.c_uint64()
+        r = ctypes.c_uint32()
+        s = (ctypes.c_uint64 * (PP_MAX_R + 1))()
+        _check(_lib.load().pp_iblt_info(self._h, ctypes.byref(n), ctypes.byref(r), s), "pp_iblt_info")
+        return list(s[: r.value + 1])
+
+
+# Function-style names matching the C ABI.
+def iblt_create(n_cells: int, r: int, seed: int, opts: Options | None = None) -> IBLT:
+    return IBLT(n_cells, r, seed, opts)
+
+
+def iblt_insert(table: IBLT, keys, stream=None) -> None:
+    table.insert(keys, stream)
+
+
+def iblt_delete(table: IBLT, keys, stream=None) -> None:
+    table.delete(keys, stream)
+
+
+def iblt_decode(table: IBLT, out, round_cap: int = 4096, stream=None) -> DecodeOutcome:
+    return table.decode(out, round_cap, stream)
+
+
+def peel_kcore(n: int, r: int, k: int, edges, vertex_round=None, edge_round=None,
+               opts: Options | None = None, round_cap: int = 4096, stream=None) -> PeelOutcome:
+    """Peel the hypergraph ``edges`` ((m, r) CUDA tensor of 4-byte ids) to its k-core."""
+    m = edges.shape[0] if edges is not None and edges.numel() else 0
+    if edges is not None and edges.numel() and (edges.dim() != 2 or edges.shape[1] != r):
+        raise ValueError("edges must have shape (m, r)")
+    s_left = (ctypes.c_uint64 * round_cap)()
+    m_left = (ctypes.c_uint64 * round_cap)()
+    res = PeelResult()
+    res.round_cap = round_cap
+    res.vertices_left = ctypes.cast(s_left, ctypes.POINTER(ctypes.c_uint64))
+    res.edges_left = ctypes.cast(m_left, ctypes.POINTER(ctypes.c_uint64))
+    st = _lib.load().pp_peel_kcore(int(n), int(r), int(k),
+                                   _dev_ptr(edges, 4, "edges") if m else None, int(m),
+                                   _dev_ptr(vertex_round, 4, "vertex_round"),
+                                   _dev_ptr(edge_round, 4, "edge_round"), ctypes.byref(res),
+                                   ctypes.byref(opts) if opts is not None else None,
+                                   _stream_ptr(stream))
+    _check(st, "pp_peel_kcore")
+    nr = min(res.rounds, round_cap)
+    return PeelOutcome(res.rounds, res.core_vertices, res.core_edges, res.status_flags,
+                       list(s_left[:nr]), list(m_left[:nr]))

@@ -1,0 +1,103 @@
+// Device-side building blocks shared by the peeling kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "ppeel.h"
+
+namespace pp {
+
+typedef unsigned long long u64;
+typedef unsigned int u32;
+
+constexpr u32 kFull = 0xffffffffu;
+constexpr u64 kGamma = 0x9E3779B97F4A7C15ULL;
+
+// Device-side status flags (DecodeCtl::flags, PeelCtl::flags).
+enum : u32 {
+  FLAG_CAPACITY = 1u,     // an output index ran past its capacity
+  FLAG_ROUND_LIMIT = 2u,  // max_rounds reached with a non-empty frontier
+  FLAG_BAD_ID = 4u,       // a vertex id >= n was seen
+  FLAG_INTERNAL = 8u      // an invariant failed (frontier cell not among its key's cells)
+};
+
+// One IBLT cell: 32 bytes, so a random touch costs one DRAM sector.
+struct __align__(32) Cell {
+  u64 key;    // XOR of the keys in the cell
+  u64 chk;    // XOR of checkSum(key)
+  int count;  // keys in the cell
+  u32 pad[3];
+};
+static_assert(sizeof(Cell) == 32, "cell must be one 32-byte sector");
+static_assert(sizeof(Cell) == sizeof(pp_cell), "public and device cell layouts differ");
+
+// SplitMix64 output finaliser (Steele, Lea & Flood 2014): the hash family of
+// the IBLT (cell positions and checksums).
+__host__ __device__ __forceinline__ u64 mix64(u64 z) {
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+  return z ^ (z >> 31);
+}
+
+// Per-table constants.  Sub-table j is cells base+off[j] .. base+off[j+1]-1.
+struct __align__(16) TableArgs {
+  u64 seed[PP_MAX_R + 1];  // hash seeds s_0..s_{r-1}, checksum seed at [r]
+  u32 off[PP_MAX_R + 1];
+  u32 base;                // global id of cell 0 (a multiple of 32)
+  u32 n_cells;
+  u32 r;
+  u64 out_base;            // batch: first slot of this table's output region
+  u64 out_cap;             // batch: slots in that region
+};
+
+// The r cells of key x (one per sub-table).
+template <int R>
+__device__ __forceinline__ void cells_of(u64 x, const TableArgs &t, u32 (&c)[R]) {
+#pragma unroll
+  for (int j = 0; j < R; ++j) {
+    const u64 h = mix64(x ^ t.seed[j]);
+    const u64 size = (u64)(t.off[j + 1] - t.off[j]);
+    c[j] = t.base + t.off[j] + (u32)__umul64hi(h, size);
+  }
+}
+
+__device__ __forceinline__ u32 lane_id() { return threadIdx.x & 31u; }
+
+__device__ __forceinline__ u32 lanemask_lt() {
+  u32 m;
+  asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+  return m;
+}
+
+// Warp-aggregated reservation of slots in a counter: every lane with pred gets
+// a distinct index.  All 32 lanes must call it.
+template <typename T>
+__device__ __forceinline__ T warp_reserve(bool pred, T *counter) {
+  const u32 mask = __ballot_sync(kFull, pred);
+  T base = 0;
+  if (mask) {
+    const int leader = __ffs(mask) - 1;
+    if ((int)lane_id() == leader) base = atomicAdd(counter, (T)__popc(mask));
+    base = __shfl_sync(kFull, base, leader);
+  }
+  return base + (T)__popc(mask & lanemask_lt());
+}
+
+// Sum over a block (all threads call it); result valid in thread 0.
+template <typename T, int BLOCK>
+__device__ __forceinline__ T block_sum(T v, T *scratch /* BLOCK/32 entries */) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(kFull, v, o);
+  if (lane_id() == 0) scratch[threadIdx.x >> 5] = v;
+  __syncthreads();
+  T s = 0;
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int w = 0; w < BLOCK / 32; ++w) s += scratch[w];
+  }
+  __syncthreads();
+  return s;
+}
+
+}  // namespace pp

@@ -1,0 +1,428 @@
+// C-ABI: one IBLT on the device (create, insert/delete, decode).
+//
+// Decode = initial full scan, then rounds of (peel, filter, round_end) until
+// the frontier is empty (Sec. 1 rounds at k = 2 on the IBLT hypergraph of
+// Sec. 6).  By default the round loop is a single CUDA graph: a while-node
+// whose body is the three round kernels; the last one decides on the device
+// whether another round runs, so the host neither syncs nor launches per round.
+#include <stdlib.h>
+#include <string.h>
+
+#include "host.cuh"
+#include "iblt_kernels.cuh"
+
+using namespace pp;
+
+namespace pp {
+
+struct IbltKernels {
+  const void *insert, *scan, *peel, *filter;
+  int nr;  // compile-time rank (PP_MAX_R for the generic instance)
+};
+
+template <int R, bool B>
+static IbltKernels iblt_kernels_t() {
+  return {(const void *)k_insert<R, B>, (const void *)k_scan<R, B>, (const void *)k_peel<R, B>,
+          (const void *)k_filter<R, B>, R ? R : PP_MAX_R};
+}
+
+IbltKernels iblt_kernels(uint32_t r, bool batch) {
+  if (batch) {
+    if (r == 3) return iblt_kernels_t<3, true>();
+    if (r == 4) return iblt_kernels_t<4, true>();
+    return iblt_kernels_t<0, true>();
+  }
+  if (r == 3) return iblt_kernels_t<3, false>();
+  if (r == 4) return iblt_kernels_t<4, false>();
+  return iblt_kernels_t<0, false>();
+}
+
+size_t peel_smem_bytes(int nr, bool batch) {
+  const size_t ch = (size_t)kBlock * kPeelItems;
+  return (batch ? 0 : ch * sizeof(u64)) + ch * nr * sizeof(u32) * (batch ? 2 : 1);
+}
+
+}  // namespace pp
+
+struct pp_iblt {
+  uint64_t n = 0;
+  uint32_t r = 0;
+  uint64_t seed = 0;
+  pp_options opt{};
+  TableArgs args{};
+  Cell *cells = nullptr;
+  u64 *fkey = nullptr;
+  u32 *fcell = nullptr, *cand = nullptr, *bitmap = nullptr;
+  DecodeCtl *ctl = nullptr, *h_ctl = nullptr;
+  u64 *st_rec = nullptr, *st_alive = nullptr;
+  u32 *st_front = nullptr;
+  u64 *h_rec = nullptr, *h_alive = nullptr;
+  int64_t items = 0;
+  IbltKernels k{};
+  int grid_scan = 0, grid_peel = 0, grid_filter = 0, grid_insert = 0;
+  size_t smem_peel = 0;
+  cudaGraphExec_t exec = nullptr;
+};
+
+namespace {
+
+void free_all(pp_iblt *t) {
+  if (!t) return;
+  if (t->exec) cudaGraphExecDestroy(t->exec);
+  cudaFree(t->cells);
+  cudaFree(t->fkey);
+  cudaFree(t->fcell);
+  cudaFree(t->cand);
+  cudaFree(t->bitmap);
+  cudaFree(t->ctl);
+  cudaFree(t->st_rec);
+  cudaFree(t->st_alive);
+  cudaFree(t->st_front);
+  cudaFreeHost(t->h_ctl);
+  cudaFreeHost(t->h_rec);
+  cudaFreeHost(t->h_alive);
+  delete t;
+}
+
+struct ScanArgs {
+  Cell *cells;
+  TableArgs tab0;
+  const TableArgs *tabs;
+  const Chunk *chunks;
+  u32 n_chunks;
+  u64 *fkey;
+  u32 *fcell;
+  u32 *ftab;
+  u32 *bitmap;
+  DecodeCtl *ctl;
+  BatchCounters bc;
+  void *p[11];
+  void bind() {
+    void *q[11] = {&cells, &tab0, &tabs, &chunks, &n_chunks, &fkey, &fcell, &ftab, &bitmap, &ctl, &bc};
+    memcpy(p, q, sizeof q);
+  }
+};
+
+struct PeelArgs {
+  Cell *cells;
+  TableArgs tab0;
+  const TableArgs *tabs;
+  const u64 *fkey;
+  const u32 *fcell;
+  const u32 *ftab;
+  const u32 *bitmap;
+  u32 *cand;
+  u32 *ctab;
+  u64 *bout;
+  DecodeCtl *ctl;
+  BatchCounters bc;
+  void *p[12];
+  void bind() {
+    void *q[12] = {&cells, &tab0, &tabs, &fkey, &fcell, &ftab, &bitmap, &cand, &ctab, &bout, &ctl, &bc};
+    memcpy(p, q, sizeof q);
+  }
+};
+
+struct FilterArgs {
+  const Cell *cells;
+  TableArgs tab0;
+  const TableArgs *tabs;
+  const u32 *cand;
+  const u32 *ctab;
+  u64 *fkey;
+  u32 *fcell;
+  u32 *ftab;
+  u32 *bitmap;
+  DecodeCtl *ctl;
+  void *p[10];
+  void bind() {
+    void *q[10] = {&cells, &tab0, &tabs, &cand, &ctab, &fkey, &fcell, &ftab, &bitmap, &ctl};
+    memcpy(p, q, sizeof q);
+  }
+};
+
+struct EndArgs {
+  DecodeCtl *ctl;
+  RoundStats st;
+  int set_cond;
+  cudaGraphConditionalHandle cond;
+  void *p[4];
+  void bind() {
+    void *q[4] = {&ctl, &st, &set_cond, &cond};
+    memcpy(p, q, sizeof q);
+  }
+};
+
+void fill_args(pp_iblt *t, ScanArgs &sa, PeelArgs &pa, FilterArgs &fa, EndArgs &ea) {
+  BatchCounters bc{};
+  sa = ScanArgs{t->cells, t->args, nullptr, nullptr,
+                (u32)((t->n + kBlock * kScanItems - 1) / (kBlock * kScanItems)),
+                t->fkey, t->fcell, nullptr, t->bitmap, t->ctl, bc, {}};
+  pa = PeelArgs{t->cells, t->args, nullptr, t->fkey, t->fcell, nullptr, t->bitmap, t->cand,
+                nullptr, nullptr, t->ctl, bc, {}};
+  fa = FilterArgs{t->cells, t->args, nullptr, t->cand, nullptr, t->fkey, t->fcell, nullptr,
+                  t->bitmap, t->ctl, {}};
+  ea = EndArgs{t->ctl, RoundStats{t->st_rec, t->st_alive, t->st_front}, 0, 0, {}};
+  sa.bind();
+  pa.bind();
+  fa.bind();
+  ea.bind();
+}
+
+pp_status add_kernel(cudaGraphNode_t *node, cudaGraph_t g, const cudaGraphNode_t *dep, size_t ndep,
+                     const void *fn, int grid, int block, size_t smem, void **args) {
+  cudaKernelNodeParams kp{};
+  kp.func = const_cast<void *>(fn);
+  kp.gridDim = dim3((unsigned)grid);
+  kp.blockDim = dim3((unsigned)block);
+  kp.sharedMemBytes = (unsigned)smem;
+  kp.kernelParams = args;
+  PP_CUDA(cudaGraphAddKernelNode(node, g, dep, ndep, &kp));
+  return PP_OK;
+}
+
+// scan -> while (more) { peel -> filter -> round_end }
+pp_status build_graph(pp_iblt *t) {
+  ScanArgs sa;
+  PeelArgs pa;
+  FilterArgs fa;
+  EndArgs ea;
+  fill_args(t, sa, pa, fa, ea);
+  cudaGraph_t g = nullptr;
+  PP_CUDA(cudaGraphCreate(&g, 0));
+  pp_status st = PP_OK;
+  cudaGraphNode_t n_scan, n_cond, n_peel, n_filter, n_end;
+  cudaGraphConditionalHandle h;
+  cudaGraphNodeParams cp{};
+  cudaGraph_t body;
+  st = add_kernel(&n_scan, g, nullptr, 0, t->k.scan, t->grid_scan, kBlock, 0, sa.p);
+  if (st != PP_OK) goto done;
+  if (cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault) != cudaSuccess) {
+    st = fail(PP_ERR_CUDA, "cudaGraphConditionalHandleCreate failed");
+    goto done;
+  }
+  cp.type = cudaGraphNodeTypeConditional;
+  cp.conditional.handle = h;
+  cp.conditional.type = cudaGraphCondTypeWhile;
+  cp.conditional.size = 1;
+  if (cudaGraphAddNode(&n_cond, g, &n_scan, nullptr, 1, &cp) != cudaSuccess) {
+    st = fail(PP_ERR_CUDA, "cudaGraphAddNode(conditional while) failed");
+    goto done;
+  }
+  body = cp.conditional.phGraph_out[0];
+  ea.set_cond = 1;
+  ea.cond = h;
+  st = add_kernel(&n_peel, body, nullptr, 0, t->k.peel, t->grid_peel, kBlock, t->smem_peel, pa.p);
+  if (st != PP_OK) goto done;
+  st = add_kernel(&n_filter, body, &n_peel, 1, t->k.filter, t->grid_filter, kBlock, 0, fa.p);
+  if (st != PP_OK) goto done;
+  st = add_kernel(&n_end, body, &n_filter, 1, (const void *)k_round_end, 1, 32, 0, ea.p);
+  if (st != PP_OK) goto done;
+  if (cudaGraphInstantiate(&t->exec, g, 0) != cudaSuccess) {
+    st = fail(PP_ERR_CUDA, "cudaGraphInstantiate failed: %s", cudaGetErrorString(cudaGetLastError()));
+    t->exec = nullptr;
+  }
+done:
+  cudaGraphDestroy(g);
+  return st;
+}
+
+pp_status run_host_loop(pp_iblt *t, cudaStream_t s) {
+  ScanArgs sa;
+  PeelArgs pa;
+  FilterArgs fa;
+  EndArgs ea;
+  fill_args(t, sa, pa, fa, ea);
+  PP_CUDA(cudaLaunchKernel(t->k.scan, dim3(t->grid_scan), dim3(kBlock), sa.p, 0, s));
+  for (;;) {
+    PP_CUDA(cudaLaunchKernel(t->k.peel, dim3(t->grid_peel), dim3(kBlock), pa.p, t->smem_peel, s));
+    PP_CUDA(cudaLaunchKernel(t->k.filter, dim3(t->grid_filter), dim3(kBlock), fa.p, 0, s));
+    PP_CUDA(cudaLaunchKernel((const void *)k_round_end, dim3(1), dim3(32), ea.p, 0, s));
+    PP_CUDA(cudaMemcpyAsync(&t->h_ctl->more, &t->ctl->more, sizeof(u32), cudaMemcpyDeviceToHost, s));
+    PP_CUDA(cudaStreamSynchronize(s));
+    if (!t->h_ctl->more) break;
+  }
+  return PP_OK;
+}
+
+pp_status launch_insert(pp_iblt *t, const uint64_t *d_keys, uint64_t m, int sign, cudaStream_t s) {
+  if (m == 0) return PP_OK;
+  TableArgs a = t->args;
+  const TableArgs *tabs = nullptr;
+  const Chunk *chunks = nullptr;
+  u32 nch = 0;
+  Cell *cells = t->cells;
+  const u64 *keys = reinterpret_cast<const u64 *>(d_keys);
+  u64 mm = m;
+  void *args[] = {&cells, &a, &tabs, &chunks, &nch, &keys, &mm, &sign};
+  const u64 want = (m + kBlock - 1) / kBlock;
+  const int grid = (int)(want < (u64)t->grid_insert ? want : (u64)t->grid_insert);
+  PP_CUDA(cudaLaunchKernel(t->k.insert, dim3(grid), dim3(kBlock), args, 0, s));
+  return PP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+pp_status pp_iblt_create(pp_iblt **out, uint64_t n_cells, uint32_t r, uint64_t seed,
+                         const pp_options *opt) {
+  if (!out) return fail(PP_ERR_INVALID_ARG, "pp_iblt_create: out is NULL");
+  *out = nullptr;
+  if (r < 2 || r > PP_MAX_R)
+    return fail(PP_ERR_INVALID_ARG, "pp_iblt_create: r=%u outside 2..%d", r, PP_MAX_R);
+  if (n_cells < r || n_cells > 0xFFFFFFFFull - 64)
+    return fail(PP_ERR_INVALID_ARG, "pp_iblt_create: n_cells=%llu outside r..2^32-65",
+                (unsigned long long)n_cells);
+  pp_iblt *t = new pp_iblt();
+  t->n = n_cells;
+  t->r = r;
+  t->seed = seed;
+  t->opt = resolve_options(opt);
+  make_table_args(t->args, n_cells, r, seed, 0);
+  t->k = iblt_kernels(r, false);
+  t->smem_peel = peel_smem_bytes(t->k.nr, false);
+  const uint64_t words = (n_cells + 31) / 32 + 1;
+  const uint32_t mr = t->opt.max_rounds;
+  cudaError_t e = cudaSuccess;
+  auto al = [&](void **p, size_t bytes) {
+    if (e == cudaSuccess) e = cudaMalloc(p, bytes ? bytes : 16);
+  };
+  al((void **)&t->cells, n_cells * sizeof(Cell));
+  al((void **)&t->fkey, n_cells * sizeof(u64));
+  al((void **)&t->fcell, n_cells * sizeof(u32));
+  al((void **)&t->cand, n_cells * sizeof(u32));
+  al((void **)&t->bitmap, words * sizeof(u32));
+  al((void **)&t->ctl, sizeof(DecodeCtl));
+  al((void **)&t->st_rec, (size_t)mr * sizeof(u64));
+  al((void **)&t->st_alive, (size_t)mr * sizeof(u64));
+  al((void **)&t->st_front, (size_t)mr * sizeof(u32));
+  if (e == cudaSuccess) e = cudaMallocHost((void **)&t->h_ctl, sizeof(DecodeCtl));
+  if (e == cudaSuccess) e = cudaMallocHost((void **)&t->h_rec, (size_t)mr * sizeof(u64));
+  if (e == cudaSuccess) e = cudaMallocHost((void **)&t->h_alive, (size_t)mr * sizeof(u64));
+  if (e == cudaSuccess) e = cudaMemset(t->cells, 0, n_cells * sizeof(Cell));
+  if (e == cudaSuccess) e = cudaMemset(t->bitmap, 0, words * sizeof(u32));
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) {
+    pp_status st = cuda_fail(e, "pp_iblt_create allocation", __FILE__, __LINE__);
+    free_all(t);
+    return st;
+  }
+  t->grid_scan = persistent_grid(t->k.scan, kBlock, 0, t->opt.ctas_per_sm);
+  t->grid_peel = persistent_grid(t->k.peel, kBlock, t->smem_peel, t->opt.ctas_per_sm);
+  t->grid_filter = persistent_grid(t->k.filter, kBlock, 0, t->opt.ctas_per_sm);
+  t->grid_insert = persistent_grid(t->k.insert, kBlock, 0, 8) * 4;
+  *out = t;
+  return PP_OK;
+}
+
+pp_status pp_iblt_destroy(pp_iblt *t) {
+  if (!t) return PP_OK;
+  cudaDeviceSynchronize();
+  free_all(t);
+  return PP_OK;
+}
+
+pp_status pp_iblt_clear(pp_iblt *t, void *stream) {
+  if (!t) return fail(PP_ERR_INVALID_ARG, "pp_iblt_clear: NULL table");
+  PP_CUDA(cudaMemsetAsync(t->cells, 0, t->n * sizeof(Cell), as_stream(stream)));
+  t->items = 0;
+  return PP_OK;
+}
+
+pp_status pp_iblt_insert(pp_iblt *t, const uint64_t *d_keys, uint64_t m, void *stream) {
+  if (!t) return fail(PP_ERR_INVALID_ARG, "pp_iblt_insert: NULL table");
+  if (m && !d_keys) return fail(PP_ERR_INVALID_ARG, "pp_iblt_insert: NULL keys");
+  pp_status st = launch_insert(t, d_keys, m, +1, as_stream(stream));
+  if (st == PP_OK) t->items += (int64_t)m;
+  return st;
+}
+
+pp_status pp_iblt_delete(pp_iblt *t, const uint64_t *d_keys, uint64_t m, void *stream) {
+  if (!t) return fail(PP_ERR_INVALID_ARG, "pp_iblt_delete: NULL table");
+  if (m && !d_keys) return fail(PP_ERR_INVALID_ARG, "pp_iblt_delete: NULL keys");
+  pp_status st = launch_insert(t, d_keys, m, -1, as_stream(stream));
+  if (st == PP_OK) t->items -= (int64_t)m;
+  return st;
+}
+
+pp_status pp_iblt_decode(pp_iblt *t, uint64_t *d_out_keys, uint64_t out_cap, pp_decode_result *res,
+                         void *stream) {
+  if (!t || !res) return fail(PP_ERR_INVALID_ARG, "pp_iblt_decode: NULL table or result");
+  const uint64_t items = t->items > 0 ? (uint64_t)t->items : 0;
+  if (out_cap < items)
+    return fail(PP_ERR_CAPACITY, "pp_iblt_decode: out_cap=%llu < %llu keys in the table",
+                (unsigned long long)out_cap, (unsigned long long)items);
+  if (out_cap && !d_out_keys) return fail(PP_ERR_INVALID_ARG, "pp_iblt_decode: NULL output");
+  cudaStream_t s = as_stream(stream);
+  memset(t->h_ctl, 0, sizeof(DecodeCtl));
+  t->h_ctl->out = reinterpret_cast<u64 *>(d_out_keys);
+  t->h_ctl->out_cap = out_cap;
+  t->h_ctl->max_rounds = t->opt.max_rounds;
+  PP_CUDA(cudaMemcpyAsync(t->ctl, t->h_ctl, sizeof(DecodeCtl), cudaMemcpyHostToDevice, s));
+  if (t->opt.host_loop) {
+    pp_status st = run_host_loop(t, s);
+    if (st != PP_OK) return st;
+  } else {
+    if (!t->exec) {
+      pp_status st = build_graph(t);
+      if (st != PP_OK) return st;
+    }
+    PP_CUDA(cudaGraphLaunch(t->exec, s));
+  }
+  PP_CUDA(cudaMemcpyAsync(t->h_ctl, t->ctl, sizeof(DecodeCtl), cudaMemcpyDeviceToHost, s));
+  PP_CUDA(cudaStreamSynchronize(s));
+  const DecodeCtl c = *t->h_ctl;
+  const uint32_t T = c.round;
+  const uint32_t ncopy = T < res->round_cap ? T : res->round_cap;
+  if (ncopy && (res->recovered_per_round || res->remaining_per_round || res->alive_cells_per_round)) {
+    PP_CUDA(cudaMemcpyAsync(t->h_rec, t->st_rec, ncopy * sizeof(u64), cudaMemcpyDeviceToHost, s));
+    PP_CUDA(cudaMemcpyAsync(t->h_alive, t->st_alive, ncopy * sizeof(u64), cudaMemcpyDeviceToHost, s));
+    PP_CUDA(cudaStreamSynchronize(s));
+    uint64_t left = items;
+    for (uint32_t i = 0; i < ncopy; ++i) {
+      left -= t->h_rec[i] <= left ? t->h_rec[i] : left;
+      if (res->recovered_per_round) res->recovered_per_round[i] = t->h_rec[i];
+      if (res->remaining_per_round) res->remaining_per_round[i] = left;
+      if (res->alive_cells_per_round) res->alive_cells_per_round[i] = t->h_alive[i];
+    }
+  }
+  res->rounds = T;
+  res->status_flags = c.flags;
+  res->recovered = c.n_out < out_cap ? c.n_out : out_cap;
+  res->items_before = items;
+  res->residual_cells = c.nonempty - c.emptied;
+  t->items -= (int64_t)res->recovered;
+  if (c.flags & FLAG_CAPACITY)
+    return fail(PP_ERR_CAPACITY, "pp_iblt_decode: more keys recovered than out_cap=%llu",
+                (unsigned long long)out_cap);
+  if (c.flags & FLAG_INTERNAL)
+    return fail(PP_ERR_INVALID_ARG, "pp_iblt_decode: a pure cell's key does not hash to it");
+  if (c.flags & FLAG_ROUND_LIMIT)
+    return fail(PP_ERR_ROUND_LIMIT, "pp_iblt_decode: stopped after max_rounds=%u rounds",
+                t->opt.max_rounds);
+  return PP_OK;
+}
+
+pp_status pp_iblt_copy_cells(pp_iblt *t, void *dst, uint64_t first, uint64_t count, int to_host,
+                             void *stream) {
+  if (!t || (!dst && count)) return fail(PP_ERR_INVALID_ARG, "pp_iblt_copy_cells: NULL argument");
+  if (first > t->n || count > t->n - first)
+    return fail(PP_ERR_INVALID_ARG, "pp_iblt_copy_cells: range outside the table");
+  cudaStream_t s = as_stream(stream);
+  PP_CUDA(cudaMemcpyAsync(dst, t->cells + first, count * sizeof(Cell),
+                          to_host ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, s));
+  PP_CUDA(cudaStreamSynchronize(s));
+  return PP_OK;
+}
+
+pp_status pp_iblt_info(const pp_iblt *t, uint64_t *n_cells, uint32_t *r, uint64_t *h_seeds) {
+  if (!t) return fail(PP_ERR_INVALID_ARG, "pp_iblt_info: NULL table");
+  if (n_cells) *n_cells = t->n;
+  if (r) *r = t->r;
+  if (h_seeds)
+    for (uint32_t j = 0; j <= t->r; ++j) h_seeds[j] = t->args.seed[j];
+  return PP_OK;
+}
+
+}  // extern "C"

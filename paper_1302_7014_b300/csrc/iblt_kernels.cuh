@@ -1,0 +1,457 @@
+// IBLT kernels: build, initial full scan, per-round peel and frontier filter.
+//
+// The recovery is the round-synchronous k = 2 peel of Sec. 1 applied to the
+// IBLT hypergraph of Sec. 6 (cells = vertices, keys = edges):
+//   round t recovers every key that is alone in some cell at the start of the
+//   round, exactly once, and deletes it from its r cells.
+// Each round is two kernels:
+//   peel   (phase B)  for every frontier entry (cell c, key x snapshot taken
+//                     at the start of the round) decide whether c is the
+//                     lowest-index cell of x that was pure at the round's
+//                     start; if so recover x and XOR it out of its r cells.
+//                     A cell whose count drops from 2 to 1 becomes a candidate.
+//   filter (phase A)  keep the candidates that are pure once the round is
+//                     over, snapshot their keys and mark them in the
+//                     "pure at round start" bitmap: the next frontier.
+// The kernel boundary between the two phases is what makes the snapshot and
+// the bitmap describe the round's start.  A cell is pure at the start of at
+// most one round in the whole decode (its count then drops to 0 and never
+// rises), so the bitmap needs no clearing between rounds.
+#pragma once
+
+#include "device.cuh"
+
+namespace pp {
+
+constexpr int kBlock = 256;       // threads per CTA of the staged kernels
+constexpr int kScanItems = 4;     // cells per thread per scan chunk
+constexpr int kPeelItems = 2;     // frontier entries per thread per peel chunk
+constexpr int kFilterItems = 2;   // candidates per thread per filter chunk
+
+// Decode state on the device.  One instance per decode (plain or batched).
+struct DecodeCtl {
+  u64 *out;             // plain decode: recovered keys (caller's buffer)
+  u64 out_cap;          // plain decode: capacity of out
+  u64 n_out;            // keys recovered so far (plain decode)
+  u64 out_round_start;  // n_out when the current round started
+  u64 alive;            // cells with count >= 2 at the start of the current round
+  u64 nonempty;         // cells with count != 0 when the decode started
+  u64 emptied;          // cells whose count went from 1 to 0 during the decode
+  u32 round;            // rounds started so far
+  u32 n_front;          // |F_t|: entries of the current frontier
+  u32 n_next;           // entries of F_{t+1} written so far
+  u32 n_cand;           // candidates pushed during the current round
+  u32 flags;            // FLAG_*
+  u32 max_rounds;
+  u32 more;             // 1 while another round must run
+  u32 stats_rounds;     // batch: per-table per-round counter slots
+};
+
+// Per-round device statistics (index t-1 for round t).
+struct RoundStats {
+  u64 *recovered;  // keys recovered in round t
+  u64 *alive;      // cells with count >= 2 at the start of round t
+  u32 *front;      // |F_t|
+};
+
+// Per-table device counters of a batched decode.
+struct BatchCounters {
+  u64 *recovered;      // per table: keys recovered (also the output cursor)
+  u64 *nonempty;       // per table: non-empty cells at the start
+  u64 *emptied;        // per table: cells emptied during the decode
+  u32 *rounds;         // per table: last round that recovered a key
+  u32 *round_rec;      // per table x stats_rounds: keys recovered per round
+};
+
+// A contiguous range of one table's cells or keys.
+struct Chunk {
+  u32 table;
+  u32 begin;  // global cell id (scan) or key index (insert)
+  u32 end;
+};
+
+template <int R>
+__device__ __forceinline__ int rank_of(const TableArgs &T) { return R ? R : (int)T.r; }
+
+// --------------------------------------------------------------------------
+// Build (Sec. 6 "Motivation"; one thread per key as in Sec. 6 "Implementation
+// Details", with fire-and-forget atomics: nothing reads their results).
+// --------------------------------------------------------------------------
+template <int R, bool BATCH>
+__global__ void __launch_bounds__(kBlock) k_insert(Cell *__restrict__ cells, const TableArgs tab0,
+                                                   const TableArgs *__restrict__ tabs,
+                                                   const Chunk *__restrict__ chunks, u32 n_chunks,
+                                                   const u64 *__restrict__ keys, u64 m, int sign) {
+  constexpr int NR = R ? R : PP_MAX_R;
+  if (!BATCH) {
+    const int r = rank_of<R>(tab0);
+    const u64 stride = (u64)gridDim.x * blockDim.x;
+    for (u64 i = (u64)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += stride) {
+      const u64 x = __ldcs(keys + i);
+      u32 c[NR];
+      cells_of<NR>(x, tab0, c);
+      const u64 cx = mix64(x ^ tab0.seed[r]);
+#pragma unroll
+      for (int j = 0; j < NR; ++j) {
+        if (j < r) {
+          Cell *p = cells + c[j];
+          atomicAdd(&p->count, sign);
+          atomicXor(&p->key, x);
+          atomicXor(&p->chk, cx);
+        }
+      }
+    }
+  } else {
+    for (u32 ch = blockIdx.x; ch < n_chunks; ch += gridDim.x) {
+      const Chunk k = chunks[ch];
+      const TableArgs &T = tabs[k.table];
+      const int r = rank_of<R>(T);
+      for (u32 i = k.begin + threadIdx.x; i < k.end; i += blockDim.x) {
+        const u64 x = __ldcs(keys + i);
+        u32 c[NR];
+        cells_of<NR>(x, T, c);
+        const u64 cx = mix64(x ^ T.seed[r]);
+#pragma unroll
+        for (int j = 0; j < NR; ++j) {
+          if (j < r) {
+            Cell *p = cells + c[j];
+            atomicAdd(&p->count, sign);
+            atomicXor(&p->key, x);
+            atomicXor(&p->chk, cx);
+          }
+        }
+      }
+    }
+  }
+}
+
+// --------------------------------------------------------------------------
+// Initial full scan: F_1 = cells pure before any round; sets their bits.
+// Every 32-cell bitmap word of the table is written here (whole word per warp),
+// so a previous decode's bits never leak into this one.
+// --------------------------------------------------------------------------
+template <int R, bool BATCH>
+__global__ void __launch_bounds__(kBlock) k_scan(const Cell *__restrict__ cells, const TableArgs tab0,
+                                                 const TableArgs *__restrict__ tabs,
+                                                 const Chunk *__restrict__ chunks, u32 n_chunks,
+                                                 u64 *__restrict__ fkey, u32 *__restrict__ fcell,
+                                                 u32 *__restrict__ ftab, u32 *__restrict__ bitmap,
+                                                 DecodeCtl *__restrict__ ctl, BatchCounters bc) {
+  constexpr int CH = kBlock * kScanItems;
+  __shared__ u64 s_key[CH];
+  __shared__ u32 s_cell[CH];
+  __shared__ u32 s_n, s_base;
+  __shared__ u64 s_red[kBlock / 32];
+  const u32 tid = threadIdx.x;
+  u64 alive = 0, nonempty = 0;
+  if (tid == 0) s_n = 0;
+  __syncthreads();
+  for (u32 ch = blockIdx.x; ch < n_chunks; ch += gridDim.x) {
+    u32 begin, end, table = 0;
+    if (BATCH) {
+      const Chunk k = chunks[ch];
+      begin = k.begin, end = k.end, table = k.table;
+    } else {
+      begin = ch * (u32)CH;
+      end = min(begin + (u32)CH, tab0.n_cells);
+    }
+    const TableArgs &T = BATCH ? tabs[table] : tab0;
+    const int r = rank_of<R>(T);
+    const u64 seed_chk = T.seed[r];
+    u64 c_alive = 0, c_nonempty = 0;
+#pragma unroll
+    for (int it = 0; it < kScanItems; ++it) {
+      const u32 c = begin + (u32)it * kBlock + tid;
+      const bool valid = c < end;
+      bool pure = false;
+      u64 key = 0;
+      if (valid) {
+        const uint4 a = __ldcs(reinterpret_cast<const uint4 *>(cells + c));
+        const uint4 b = __ldcs(reinterpret_cast<const uint4 *>(cells + c) + 1);
+        key = ((u64)a.y << 32) | a.x;
+        const u64 chk = ((u64)a.w << 32) | a.z;
+        const int cnt = (int)b.x;
+        pure = cnt == 1 && chk == mix64(key ^ seed_chk);
+        c_alive += cnt >= 2;
+        c_nonempty += cnt != 0;
+      }
+      const u32 ball = __ballot_sync(kFull, pure);
+      const u32 first = begin + (u32)it * kBlock + (tid & ~31u);
+      if (lane_id() == 0 && first < end) bitmap[first >> 5] = ball;
+      const u32 p = warp_reserve<u32>(pure, &s_n);
+      if (pure) {
+        s_key[p] = key;
+        s_cell[p] = c;
+      }
+    }
+    alive += c_alive;
+    nonempty += c_nonempty;
+    __syncthreads();
+    const u32 n = s_n;
+    if (tid == 0) s_base = atomicAdd(&ctl->n_next, n);
+    if (BATCH) {
+      const u64 ne = block_sum<u64, kBlock>(c_nonempty, s_red);
+      if (tid == 0 && ne) atomicAdd(bc.nonempty + table, ne);
+    }
+    __syncthreads();
+    const u32 base = s_base;
+    for (u32 q = tid; q < n; q += kBlock) {
+      fkey[base + q] = s_key[q];
+      fcell[base + q] = s_cell[q];
+      if (BATCH) ftab[base + q] = table;
+    }
+    __syncthreads();
+    if (tid == 0) s_n = 0;
+    __syncthreads();
+  }
+  const u64 a = block_sum<u64, kBlock>(alive, s_red);
+  const u64 ne = block_sum<u64, kBlock>(nonempty, s_red);
+  if (tid == 0) {
+    if (a) atomicAdd(&ctl->alive, a);
+    if (ne) atomicAdd(&ctl->nonempty, ne);
+  }
+}
+
+// --------------------------------------------------------------------------
+// Phase B of round t: claim and recover.
+// --------------------------------------------------------------------------
+template <int R, bool BATCH>
+__global__ void __launch_bounds__(kBlock) k_peel(Cell *__restrict__ cells, const TableArgs tab0,
+                                                 const TableArgs *__restrict__ tabs,
+                                                 const u64 *__restrict__ fkey, const u32 *__restrict__ fcell,
+                                                 const u32 *__restrict__ ftab, const u32 *__restrict__ bitmap,
+                                                 u32 *__restrict__ cand, u32 *__restrict__ ctab,
+                                                 u64 *__restrict__ bout, DecodeCtl *__restrict__ ctl,
+                                                 BatchCounters bc) {
+  constexpr int NR = R ? R : PP_MAX_R;
+  constexpr int CH = kBlock * kPeelItems;
+  extern __shared__ __align__(16) unsigned char smem[];
+  u64 *s_out = reinterpret_cast<u64 *>(smem);                    // CH      (plain)
+  u32 *s_cand = reinterpret_cast<u32 *>(s_out + (BATCH ? 0 : CH)); // CH * NR
+  u32 *s_ctab = s_cand + CH * NR;                                 // CH * NR (batch)
+  __shared__ u32 s_nout, s_ncand, s_cbase;
+  __shared__ u64 s_obase;
+  __shared__ u64 s_red[kBlock / 32];
+  const u32 tid = threadIdx.x;
+  const u32 n = *(volatile u32 *)&ctl->n_front;
+  const u32 round = *(volatile u32 *)&ctl->round;
+  u64 *out = BATCH ? bout : ctl->out;
+  const u64 out_cap = BATCH ? 0 : ctl->out_cap;
+  const u32 stats_rounds = BATCH ? ctl->stats_rounds : 0;
+  u64 emptied = 0;
+  u32 flags = 0;
+  if (tid == 0) s_nout = 0, s_ncand = 0;
+  __syncthreads();
+  for (u64 c0 = (u64)blockIdx.x * CH; c0 < n; c0 += (u64)gridDim.x * CH) {
+#pragma unroll
+    for (int it = 0; it < kPeelItems; ++it) {
+      const u64 i = c0 + (u64)it * kBlock + tid;
+      const bool valid = i < n;
+      u64 x = 0;
+      u32 c = 0, tb = 0;
+      if (valid) {
+        x = __ldcs(fkey + i);
+        c = __ldcs(fcell + i);
+        if (BATCH) tb = __ldcs(ftab + i);
+      }
+      const TableArgs &T = BATCH ? tabs[tb] : tab0;
+      const int r = rank_of<R>(T);
+      u32 cj[NR];
+      cells_of<NR>(x, T, cj);
+      int jstar = -1;
+#pragma unroll
+      for (int j = NR - 1; j >= 0; --j)
+        if (j < r && cj[j] == c) jstar = j;
+      bool win = valid;
+      if (valid && jstar < 0) {
+        flags |= FLAG_INTERNAL;
+        win = false;
+      }
+      // The lowest-index cell of x that was pure at the round's start wins.
+      // Sub-tables are laid out in order, so only sub-tables j < jstar matter.
+#pragma unroll
+      for (int j = 0; j < NR - 1; ++j) {
+        if (win && j < jstar) {
+          const u32 w = __ldcg(bitmap + (cj[j] >> 5));
+          if ((w >> (cj[j] & 31u)) & 1u) win = false;
+        }
+      }
+      int old[NR];
+      u32 n_empty = 0;
+      if (win) {
+        const u64 cx = mix64(x ^ T.seed[r]);
+#pragma unroll
+        for (int j = 0; j < NR; ++j) {
+          old[j] = 0;
+          if (j < r) {
+            Cell *p = cells + cj[j];
+            old[j] = atomicSub(&p->count, 1);
+            atomicXor(&p->key, x);
+            atomicXor(&p->chk, cx);
+            n_empty += old[j] == 1;
+          }
+        }
+      } else {
+#pragma unroll
+        for (int j = 0; j < NR; ++j) old[j] = 0;
+      }
+      emptied += n_empty;
+      if constexpr (!BATCH) {
+        const u32 p = warp_reserve<u32>(win, &s_nout);
+        if (win) s_out[p] = x;
+      } else {
+        // Per-table output slots: lanes of one table share one atomic.
+        const u32 label = win ? tb : 0xffffffffu;
+        const u32 grp = __match_any_sync(kFull, label);
+        const int leader = __ffs(grp) - 1;
+        const u32 gsize = __popc(grp);
+        const u32 gempty = __reduce_add_sync(grp, n_empty);
+        u64 base = 0;
+        if (win && (int)lane_id() == leader) {
+          base = atomicAdd(bc.recovered + tb, (u64)gsize);
+          if (gempty) atomicAdd(bc.emptied + tb, (u64)gempty);
+          atomicMax(bc.rounds + tb, round);
+          if (round <= stats_rounds) atomicAdd(bc.round_rec + (u64)tb * stats_rounds + (round - 1), gsize);
+        }
+        base = __shfl_sync(kFull, base, leader);
+        if (win) {
+          const u64 slot = base + __popc(grp & lanemask_lt());
+          if (slot < T.out_cap) out[T.out_base + slot] = x;
+          else flags |= FLAG_CAPACITY;
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < NR; ++j) {
+        const bool push = win && j < r && old[j] == 2;
+        const u32 q = warp_reserve<u32>(push, &s_ncand);
+        if (push) {
+          s_cand[q] = cj[j];
+          if (BATCH) s_ctab[q] = tb;
+        }
+      }
+    }
+    __syncthreads();
+    const u32 nout = BATCH ? 0 : s_nout;
+    const u32 ncand = s_ncand;
+    if (tid == 0) {
+      if (!BATCH && nout) s_obase = atomicAdd(&ctl->n_out, (u64)nout);
+      if (ncand) s_cbase = atomicAdd(&ctl->n_cand, ncand);
+    }
+    __syncthreads();
+    if constexpr (!BATCH) {
+      const u64 ob = s_obase;
+      for (u32 q = tid; q < nout; q += kBlock) {
+        if (ob + q < out_cap) out[ob + q] = s_out[q];
+        else flags |= FLAG_CAPACITY;
+      }
+    }
+    const u32 cb = s_cbase;
+    for (u32 q = tid; q < ncand; q += kBlock) {
+      cand[cb + q] = s_cand[q];
+      if (BATCH) ctab[cb + q] = s_ctab[q];
+    }
+    __syncthreads();
+    if (tid == 0) s_nout = 0, s_ncand = 0;
+    __syncthreads();
+  }
+  if (!BATCH) {
+    const u64 e = block_sum<u64, kBlock>(emptied, s_red);
+    if (tid == 0 && e) atomicAdd(&ctl->emptied, e);
+  }
+  if (flags) atomicOr(&ctl->flags, flags);
+}
+
+// --------------------------------------------------------------------------
+// Phase A of round t+1: candidates that are pure now form F_{t+1}.
+// --------------------------------------------------------------------------
+template <int R, bool BATCH>
+__global__ void __launch_bounds__(kBlock) k_filter(const Cell *__restrict__ cells, const TableArgs tab0,
+                                                   const TableArgs *__restrict__ tabs,
+                                                   const u32 *__restrict__ cand, const u32 *__restrict__ ctab,
+                                                   u64 *__restrict__ fkey, u32 *__restrict__ fcell,
+                                                   u32 *__restrict__ ftab, u32 *__restrict__ bitmap,
+                                                   DecodeCtl *__restrict__ ctl) {
+  constexpr int CH = kBlock * kFilterItems;
+  __shared__ u64 s_key[CH];
+  __shared__ u32 s_cell[CH];
+  __shared__ u32 s_tab[BATCH ? CH : 1];
+  __shared__ u32 s_n, s_base;
+  const u32 tid = threadIdx.x;
+  const u32 n = *(volatile u32 *)&ctl->n_cand;
+  if (tid == 0) s_n = 0;
+  __syncthreads();
+  for (u64 c0 = (u64)blockIdx.x * CH; c0 < n; c0 += (u64)gridDim.x * CH) {
+#pragma unroll
+    for (int it = 0; it < kFilterItems; ++it) {
+      const u64 i = c0 + (u64)it * kBlock + tid;
+      const bool valid = i < n;
+      u32 c = 0, tb = 0;
+      bool pure = false;
+      u64 key = 0;
+      if (valid) {
+        c = __ldcs(cand + i);
+        if (BATCH) tb = __ldcs(ctab + i);
+        const TableArgs &T = BATCH ? tabs[tb] : tab0;
+        const uint4 a = __ldcg(reinterpret_cast<const uint4 *>(cells + c));
+        const uint4 b = __ldcg(reinterpret_cast<const uint4 *>(cells + c) + 1);
+        key = ((u64)a.y << 32) | a.x;
+        const u64 chk = ((u64)a.w << 32) | a.z;
+        pure = (int)b.x == 1 && chk == mix64(key ^ T.seed[rank_of<R>(T)]);
+        if (pure) atomicOr(bitmap + (c >> 5), 1u << (c & 31u));
+      }
+      const u32 p = warp_reserve<u32>(pure, &s_n);
+      if (pure) {
+        s_key[p] = key;
+        s_cell[p] = c;
+        if (BATCH) s_tab[p] = tb;
+      }
+    }
+    __syncthreads();
+    const u32 nn = s_n;
+    if (tid == 0 && nn) s_base = atomicAdd(&ctl->n_next, nn);
+    __syncthreads();
+    const u32 base = s_base;
+    for (u32 q = tid; q < nn; q += kBlock) {
+      fkey[base + q] = s_key[q];
+      fcell[base + q] = s_cell[q];
+      if (BATCH) ftab[base + q] = s_tab[q];
+    }
+    __syncthreads();
+    if (tid == 0) s_n = 0;
+    __syncthreads();
+  }
+}
+
+// --------------------------------------------------------------------------
+// End of a loop iteration: record the finished round, promote F_{t+1} to the
+// current frontier, decide whether another round runs.  One thread.
+// The first iteration after the scan has an empty frontier and only promotes
+// F_1; it is not a round.
+// --------------------------------------------------------------------------
+__global__ void k_round_end(DecodeCtl *__restrict__ ctl, RoundStats st, int set_cond,
+                            cudaGraphConditionalHandle cond) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  DecodeCtl &c = *ctl;
+  const u32 t = c.round;
+  if (c.n_front > 0 && t > 0) {
+    // round t just finished
+    st.recovered[t - 1] = c.n_out - c.out_round_start;
+    st.alive[t - 1] = c.alive;
+    st.front[t - 1] = c.n_front;
+    c.alive -= c.n_cand;  // every cell leaving "count >= 2" crossed 2 -> 1 once
+  }
+  c.out_round_start = c.n_out;
+  c.n_front = c.n_next;
+  c.n_next = 0;
+  c.n_cand = 0;
+  u32 more = c.n_front > 0 && (c.flags & (FLAG_CAPACITY | FLAG_INTERNAL)) == 0;
+  if (more && t >= c.max_rounds) {
+    c.flags |= FLAG_ROUND_LIMIT;
+    more = 0;
+  }
+  if (more) c.round = t + 1;
+  c.more = more;
+  if (set_cond) cudaGraphSetConditional(cond, more);
+}
+
+}  // namespace pp

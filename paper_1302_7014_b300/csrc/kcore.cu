@@ -1,0 +1,408 @@
+// C-ABI: round-synchronous k-core peeling of an explicit r-uniform hypergraph.
+//
+// Round t (Sec. 1, Sec. 3.1): every vertex whose degree is < k at the start of
+// the round is removed, with every edge touching it.  On the device:
+//   build   degree histogram -> exclusive scan -> scatter of edge ids gives
+//           each vertex its incidence list (CSR);
+//   scan    F_1 = {v : deg(v) < k};
+//   peel    for v in F_t and each edge e of v: the first thread to clear e's
+//           alive bit removes e and takes one degree from each endpoint; the
+//           decrement that takes a degree from k to k-1 pushes that endpoint
+//           into F_{t+1} (its degree was >= k at the start of round t, and is
+//           < k at its end: exactly the vertices round t+1 removes).
+#include <string.h>
+
+#include "host.cuh"
+#include "scan.cuh"
+
+using namespace pp;
+
+namespace pp {
+
+constexpr int kKBlock = 256;
+constexpr int kKStage = 2048;  // staged pushes per CTA before spilling to global atomics
+
+struct PeelCtl {
+  u64 claimed;  // edges removed in the current round
+  u64 s;        // vertices left
+  u64 m;        // edges left
+  u32 round;    // rounds started
+  u32 n_front;
+  u32 n_next;
+  u32 flags;
+  u32 max_rounds;
+  u32 more;
+  u32 k;
+  u32 pad;
+};
+
+struct PeelStats {
+  u64 *s;  // vertices left after round t
+  u64 *m;  // edges left after round t
+};
+
+__global__ void k_kinit(PeelCtl *ctl, u64 n, u64 m, u32 k, u32 max_rounds) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    PeelCtl c;
+    memset(&c, 0, sizeof c);
+    c.s = n;
+    c.m = m;
+    c.k = k;
+    c.max_rounds = max_rounds;
+    *ctl = c;
+  }
+}
+
+// Degree of every vertex (with multiplicity); zeroes the edge-round output.
+__global__ void __launch_bounds__(kKBlock) k_hist(const u32 *__restrict__ edges, u64 m, u32 r, u32 n,
+                                                  u32 *__restrict__ deg, int *__restrict__ eround,
+                                                  PeelCtl *__restrict__ ctl) {
+  u32 bad = 0;
+  const u64 stride = (u64)gridDim.x * blockDim.x;
+  for (u64 e = (u64)blockIdx.x * blockDim.x + threadIdx.x; e < m; e += stride) {
+    for (u32 j = 0; j < r; ++j) {
+      const u32 v = edges[e * r + j];
+      if (v < n) atomicAdd(deg + v, 1u);
+      else bad = 1;
+    }
+    if (eround) eround[e] = 0;
+  }
+  if (bad) atomicOr(&ctl->flags, (u32)FLAG_BAD_ID);
+}
+
+__global__ void __launch_bounds__(kKBlock) k_scatter(const u32 *__restrict__ edges, u64 m, u32 r, u32 n,
+                                                     u32 *__restrict__ cursor, u32 *__restrict__ inc) {
+  const u64 stride = (u64)gridDim.x * blockDim.x;
+  for (u64 e = (u64)blockIdx.x * blockDim.x + threadIdx.x; e < m; e += stride) {
+    for (u32 j = 0; j < r; ++j) {
+      const u32 v = edges[e * r + j];
+      if (v < n) inc[atomicAdd(cursor + v, 1u)] = (u32)e;
+    }
+  }
+}
+
+// F_1 = {v : deg(v) < k}; writes every vertex's round (1 or 0).
+__global__ void __launch_bounds__(kKBlock) k_kscan(const u32 *__restrict__ deg, u32 n,
+                                                   u32 *__restrict__ f0, int *__restrict__ vround,
+                                                   PeelCtl *__restrict__ ctl) {
+  __shared__ u32 s_buf[kKBlock * 4];
+  __shared__ u32 s_n, s_base;
+  const u32 k = ctl->k;
+  const u32 CH = kKBlock * 4;
+  if (threadIdx.x == 0) s_n = 0;
+  __syncthreads();
+  for (u64 c0 = (u64)blockIdx.x * CH; c0 < n; c0 += (u64)gridDim.x * CH) {
+#pragma unroll
+    for (int it = 0; it < 4; ++it) {
+      const u64 v = c0 + (u64)it * kKBlock + threadIdx.x;
+      const bool valid = v < n;
+      const bool low = valid && deg[v] < k;
+      if (valid && vround) vround[v] = low ? 1 : 0;
+      const u32 p = warp_reserve<u32>(low, &s_n);
+      if (low) s_buf[p] = (u32)v;
+    }
+    __syncthreads();
+    const u32 nn = s_n;
+    if (threadIdx.x == 0 && nn) s_base = atomicAdd(&ctl->n_next, nn);
+    __syncthreads();
+    for (u32 q = threadIdx.x; q < nn; q += kKBlock) f0[s_base + q] = s_buf[q];
+    __syncthreads();
+    if (threadIdx.x == 0) s_n = 0;
+    __syncthreads();
+  }
+}
+
+// One round: remove F_t and its edges.
+__global__ void __launch_bounds__(kKBlock) k_kpeel(const u32 *__restrict__ edges, u32 r, u32 n,
+                                                   const u32 *__restrict__ off, const u32 *__restrict__ inc,
+                                                   u32 *__restrict__ alive, u32 *__restrict__ deg,
+                                                   u32 *__restrict__ f0, u32 *__restrict__ f1,
+                                                   int *__restrict__ vround, int *__restrict__ eround,
+                                                   PeelCtl *__restrict__ ctl) {
+  __shared__ u32 s_buf[kKStage];
+  __shared__ u32 s_n, s_base;
+  __shared__ u64 s_red[kKBlock / 32];
+  const u32 t = *(volatile u32 *)&ctl->round;
+  const u32 nf = *(volatile u32 *)&ctl->n_front;
+  const u32 k = ctl->k;
+  const u32 *fin = (t & 1u) ? f0 : f1;  // round t reads F[(t-1) & 1]
+  u32 *fout = (t & 1u) ? f1 : f0;       // and writes F[t & 1]
+  u64 claimed = 0;
+  if (threadIdx.x == 0) s_n = 0;
+  __syncthreads();
+  for (u64 c0 = (u64)blockIdx.x * kKBlock; c0 < nf; c0 += (u64)gridDim.x * kKBlock) {
+    const u64 i = c0 + threadIdx.x;
+    if (i < nf) {
+      const u32 v = fin[i];
+      const u32 b = off[v], e_end = off[v + 1];
+      for (u32 p = b; p < e_end; ++p) {
+        const u32 e = inc[p];
+        const u32 bit = 1u << (e & 31u);
+        const u32 old = atomicAnd(alive + (e >> 5), ~bit);
+        if (!(old & bit)) continue;  // another vertex of this round took it
+        ++claimed;
+        if (eround) eround[e] = (int)t;
+        for (u32 j = 0; j < r; ++j) {
+          const u32 u = edges[(u64)e * r + j];
+          if (u >= n) continue;
+          const u32 od = atomicSub(deg + u, 1u);
+          if (od == k) {
+            if (vround) vround[u] = (int)t + 1;
+            const u32 q = atomicAdd(&s_n, 1u);
+            if (q < (u32)kKStage) s_buf[q] = u;
+            else fout[atomicAdd(&ctl->n_next, 1u)] = u;
+          }
+        }
+      }
+    }
+    __syncthreads();
+    const u32 nn = min(s_n, (u32)kKStage);
+    if (threadIdx.x == 0 && nn) s_base = atomicAdd(&ctl->n_next, nn);
+    __syncthreads();
+    for (u32 q = threadIdx.x; q < nn; q += kKBlock) fout[s_base + q] = s_buf[q];
+    __syncthreads();
+    if (threadIdx.x == 0) s_n = 0;
+    __syncthreads();
+  }
+  const u64 c = block_sum<u64, kKBlock>(claimed, s_red);
+  if (threadIdx.x == 0 && c) atomicAdd(&ctl->claimed, c);
+}
+
+__global__ void k_kround_end(PeelCtl *__restrict__ ctl, PeelStats st, int set_cond,
+                             cudaGraphConditionalHandle cond) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  PeelCtl &c = *ctl;
+  const u32 t = c.round;
+  if (c.n_front > 0 && t > 0) {
+    c.s -= c.n_front;
+    c.m -= c.claimed;
+    st.s[t - 1] = c.s;
+    st.m[t - 1] = c.m;
+  }
+  c.claimed = 0;
+  c.n_front = c.n_next;
+  c.n_next = 0;
+  u32 more = c.n_front > 0;
+  if (more && t >= c.max_rounds) {
+    c.flags |= FLAG_ROUND_LIMIT;
+    more = 0;
+  }
+  if (more) c.round = t + 1;
+  c.more = more;
+  if (set_cond) cudaGraphSetConditional(cond, more);
+}
+
+}  // namespace pp
+
+namespace {
+
+struct KWork {
+  u32 *deg = nullptr, *off = nullptr, *cursor = nullptr, *inc = nullptr, *alive = nullptr;
+  u32 *f0 = nullptr, *f1 = nullptr;
+  PeelCtl *ctl = nullptr;
+  u64 *st_s = nullptr, *st_m = nullptr;
+  void *scan_tmp = nullptr;
+};
+
+struct KPeelArgs {
+  const u32 *edges;
+  u32 r, n;
+  const u32 *off, *inc;
+  u32 *alive, *deg, *f0, *f1;
+  int *vround, *eround;
+  PeelCtl *ctl;
+  void *p[12];
+  void bind() {
+    void *q[12] = {&edges, &r, &n, &off, &inc, &alive, &deg, &f0, &f1, &vround, &eround, &ctl};
+    memcpy(p, q, sizeof q);
+  }
+};
+
+struct KEndArgs {
+  PeelCtl *ctl;
+  PeelStats st;
+  int set_cond;
+  cudaGraphConditionalHandle cond;
+  void *p[4];
+  void bind() {
+    void *q[4] = {&ctl, &st, &set_cond, &cond};
+    memcpy(p, q, sizeof q);
+  }
+};
+
+pp_status run_rounds(KPeelArgs &pa, KEndArgs &ea, int grid, bool host_loop, cudaStream_t s,
+                     PeelCtl *ctl) {
+  if (host_loop) {
+    u32 more = 0;
+    for (;;) {
+      PP_CUDA(cudaLaunchKernel((const void *)k_kpeel, dim3(grid), dim3(kKBlock), pa.p, 0, s));
+      PP_CUDA(cudaLaunchKernel((const void *)k_kround_end, dim3(1), dim3(32), ea.p, 0, s));
+      PP_CUDA(cudaMemcpyAsync(&more, &ctl->more, sizeof more, cudaMemcpyDeviceToHost, s));
+      PP_CUDA(cudaStreamSynchronize(s));
+      if (!more) break;
+    }
+    return PP_OK;
+  }
+  cudaGraph_t g = nullptr, body;
+  cudaGraphExec_t exec = nullptr;
+  cudaGraphConditionalHandle h;
+  cudaGraphNodeParams cp{};
+  cudaGraphNode_t n_cond, n_peel, n_end;
+  cudaKernelNodeParams kp{};
+  pp_status st = PP_OK;
+  PP_CUDA(cudaGraphCreate(&g, 0));
+  if (cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault) != cudaSuccess) {
+    st = fail(PP_ERR_CUDA, "cudaGraphConditionalHandleCreate failed");
+    goto done;
+  }
+  cp.type = cudaGraphNodeTypeConditional;
+  cp.conditional.handle = h;
+  cp.conditional.type = cudaGraphCondTypeWhile;
+  cp.conditional.size = 1;
+  if (cudaGraphAddNode(&n_cond, g, nullptr, nullptr, 0, &cp) != cudaSuccess) {
+    st = fail(PP_ERR_CUDA, "cudaGraphAddNode(conditional while) failed");
+    goto done;
+  }
+  body = cp.conditional.phGraph_out[0];
+  ea.set_cond = 1;
+  ea.cond = h;
+  ea.bind();
+  kp.func = (void *)k_kpeel;
+  kp.gridDim = dim3(grid);
+  kp.blockDim = dim3(kKBlock);
+  kp.kernelParams = pa.p;
+  if (cudaGraphAddKernelNode(&n_peel, body, nullptr, 0, &kp) != cudaSuccess) {
+    st = fail(PP_ERR_CUDA, "cudaGraphAddKernelNode(peel) failed");
+    goto done;
+  }
+  kp.func = (void *)k_kround_end;
+  kp.gridDim = dim3(1);
+  kp.blockDim = dim3(32);
+  kp.kernelParams = ea.p;
+  if (cudaGraphAddKernelNode(&n_end, body, &n_peel, 1, &kp) != cudaSuccess) {
+    st = fail(PP_ERR_CUDA, "cudaGraphAddKernelNode(round_end) failed");
+    goto done;
+  }
+  if (cudaGraphInstantiate(&exec, g, 0) != cudaSuccess) {
+    st = fail(PP_ERR_CUDA, "cudaGraphInstantiate failed");
+    exec = nullptr;
+    goto done;
+  }
+  if (cudaGraphLaunch(exec, s) != cudaSuccess) st = fail(PP_ERR_CUDA, "cudaGraphLaunch failed");
+done:
+  if (exec) {
+    cudaStreamSynchronize(s);
+    cudaGraphExecDestroy(exec);
+  }
+  cudaGraphDestroy(g);
+  return st;
+}
+
+}  // namespace
+
+extern "C" pp_status pp_peel_kcore(uint32_t n, uint32_t r, uint32_t k, const uint32_t *d_edges,
+                                   uint64_t m, int32_t *d_vertex_round, int32_t *d_edge_round,
+                                   pp_peel_result *res, const pp_options *opt, void *stream) {
+  if (!res) return fail(PP_ERR_INVALID_ARG, "pp_peel_kcore: NULL result");
+  if (k < 1) return fail(PP_ERR_INVALID_ARG, "pp_peel_kcore: k=%u < 1", k);
+  if (r < 2 || r > PP_MAX_R) return fail(PP_ERR_INVALID_ARG, "pp_peel_kcore: r=%u outside 2..%d", r, PP_MAX_R);
+  if ((uint64_t)n > 0xFFFFFFFFull - 64) return fail(PP_ERR_INVALID_ARG, "pp_peel_kcore: n too large");
+  if (m > (0xFFFFFFFFull - 64) / r) return fail(PP_ERR_INVALID_ARG, "pp_peel_kcore: m*r >= 2^32-64");
+  if (m && !d_edges) return fail(PP_ERR_INVALID_ARG, "pp_peel_kcore: NULL edges");
+  const pp_options o = resolve_options(opt);
+  cudaStream_t s = as_stream(stream);
+  KWork w;
+  const u64 nn = n ? n : 1, mm = m ? m : 1;
+  cudaError_t e = cudaSuccess;
+  auto al = [&](void **p, size_t b) {
+    if (e == cudaSuccess) e = cudaMallocAsync(p, b, s);
+  };
+  al((void **)&w.deg, nn * 4);
+  al((void **)&w.off, (nn + 1) * 4);
+  al((void **)&w.cursor, nn * 4);
+  al((void **)&w.inc, mm * r * 4);
+  al((void **)&w.alive, ((mm + 31) / 32) * 4);
+  al((void **)&w.f0, nn * 4);
+  al((void **)&w.f1, nn * 4);
+  al((void **)&w.ctl, sizeof(PeelCtl));
+  al((void **)&w.st_s, (size_t)o.max_rounds * 8);
+  al((void **)&w.st_m, (size_t)o.max_rounds * 8);
+  al(&w.scan_tmp, exclusive_scan_temp_bytes(nn));
+  pp_status status = PP_OK;
+  PeelCtl hc{};
+  uint32_t T = 0, ncopy = 0;
+  if (e != cudaSuccess) {
+    status = cuda_fail(e, "pp_peel_kcore workspace", __FILE__, __LINE__);
+    goto cleanup;
+  }
+  {
+    const int sms = sm_count();
+    const u64 eb = (m + kKBlock - 1) / kKBlock;
+    const int egrid = (int)(eb < (u64)sms * 16 ? (eb ? eb : 1) : (u64)sms * 16);
+    const u64 vb = (nn + kKBlock * 4 - 1) / (kKBlock * 4);
+    const int vgrid = (int)(vb < (u64)sms * 8 ? vb : (u64)sms * 8);
+    if ((e = cudaMemsetAsync(w.deg, 0, nn * 4, s)) != cudaSuccess ||
+        (e = cudaMemsetAsync(w.alive, 0xff, ((mm + 31) / 32) * 4, s)) != cudaSuccess) {
+      status = cuda_fail(e, "pp_peel_kcore memset", __FILE__, __LINE__);
+      goto cleanup;
+    }
+    k_kinit<<<1, 32, 0, s>>>(w.ctl, n, m, k, o.max_rounds);
+    if (m) k_hist<<<egrid, kKBlock, 0, s>>>(d_edges, m, r, n, w.deg, d_edge_round, w.ctl);
+    status = exclusive_scan(w.deg, w.off, n, w.scan_tmp, s);
+    if (status != PP_OK) goto cleanup;
+    if (n && (e = cudaMemcpyAsync(w.cursor, w.off, (size_t)n * 4, cudaMemcpyDeviceToDevice, s)) != cudaSuccess) {
+      status = cuda_fail(e, "pp_peel_kcore cursor copy", __FILE__, __LINE__);
+      goto cleanup;
+    }
+    if (m) k_scatter<<<egrid, kKBlock, 0, s>>>(d_edges, m, r, n, w.cursor, w.inc);
+    if (n) k_kscan<<<vgrid, kKBlock, 0, s>>>(w.deg, n, w.f0, d_vertex_round, w.ctl);
+    if ((e = cudaGetLastError()) != cudaSuccess) {
+      status = cuda_fail(e, "pp_peel_kcore build kernels", __FILE__, __LINE__);
+      goto cleanup;
+    }
+    KPeelArgs pa{d_edges, r, n, w.off, w.inc, w.alive, w.deg, w.f0, w.f1, d_vertex_round, d_edge_round, w.ctl, {}};
+    pa.bind();
+    KEndArgs ea{w.ctl, PeelStats{w.st_s, w.st_m}, 0, 0, {}};
+    ea.bind();
+    const int pgrid = persistent_grid((const void *)k_kpeel, kKBlock, 0, o.ctas_per_sm);
+    status = run_rounds(pa, ea, pgrid, o.host_loop != 0, s, w.ctl);
+    if (status != PP_OK) goto cleanup;
+    if ((e = cudaMemcpyAsync(&hc, w.ctl, sizeof hc, cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
+        (e = cudaStreamSynchronize(s)) != cudaSuccess) {
+      status = cuda_fail(e, "pp_peel_kcore readback", __FILE__, __LINE__);
+      goto cleanup;
+    }
+    T = hc.round;
+    ncopy = T < res->round_cap ? T : res->round_cap;
+    if (ncopy && res->vertices_left)
+      e = cudaMemcpyAsync(res->vertices_left, w.st_s, ncopy * 8, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess && ncopy && res->edges_left)
+      e = cudaMemcpyAsync(res->edges_left, w.st_m, ncopy * 8, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) {
+      status = cuda_fail(e, "pp_peel_kcore stats readback", __FILE__, __LINE__);
+      goto cleanup;
+    }
+    res->rounds = T;
+    res->status_flags = hc.flags;
+    res->core_vertices = hc.s;
+    res->core_edges = hc.m;
+    if (hc.flags & FLAG_BAD_ID) status = fail(PP_ERR_INVALID_ARG, "pp_peel_kcore: a vertex id is >= n=%u", n);
+    else if (hc.flags & FLAG_ROUND_LIMIT)
+      status = fail(PP_ERR_ROUND_LIMIT, "pp_peel_kcore: stopped after max_rounds=%u rounds", o.max_rounds);
+  }
+cleanup:
+  cudaFreeAsync(w.deg, s);
+  cudaFreeAsync(w.off, s);
+  cudaFreeAsync(w.cursor, s);
+  cudaFreeAsync(w.inc, s);
+  cudaFreeAsync(w.alive, s);
+  cudaFreeAsync(w.f0, s);
+  cudaFreeAsync(w.f1, s);
+  cudaFreeAsync(w.ctl, s);
+  cudaFreeAsync(w.st_s, s);
+  cudaFreeAsync(w.st_m, s);
+  cudaFreeAsync(w.scan_tmp, s);
+  cudaStreamSynchronize(s);
+  return status;
+}

@@ -29,3 +29,20 @@ def read_golden(name):
 @pytest.fixture(scope="session")
 def golden():
     return read_golden
+
+
+@pytest.fixture(scope="session")
+def ppeel_lib():
+    """libppeel.so, built in place if missing or stale (nvcc cross-compiles)."""
+    from paper_1302_7014_b300 import _lib
+    from paper_1302_7014_b300.build import build
+    build()
+    return _lib.load()
+
+
+def cuda_ok():
+    try:
+        import torch
+        return torch.cuda.is_available()
+    except Exception:
+        return False

@@ -1,0 +1,226 @@
+"""GPU parity: IBLT build and round-synchronous decode against the CPU oracle.
+
+Every comparison is exact (integer/XOR work): the built table bit for bit,
+each round's recovered key set, the number of rounds, the per-round survivor
+counts and the residue left in the table.  Sizes span several scan chunks
+(1024 cells) and peel chunks (512 entries) with ragged tails.
+"""
+import hashlib
+import json
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import ppgen
+from conftest import GOLDEN
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def pp(ppeel_lib):
+    import paper_1302_7014_b300 as pp
+    return pp
+
+
+def _dev(keys):
+    return torch.from_numpy(np.ascontiguousarray(keys).view(np.int64)).cuda()
+
+
+def _split_rounds(out_keys, rec_per_round):
+    ends = np.cumsum([0] + list(rec_per_round))
+    return [np.sort(out_keys[ends[i]:ends[i + 1]]) for i in range(len(rec_per_round))]
+
+
+def _assert_cells_equal(cells, ot):
+    assert (cells["count"].astype(np.int64) == ot.count).all()
+    assert (cells["key_xor"] == ot.keyx).all()
+    assert (cells["chk_xor"] == ot.chkx).all()
+
+
+def run_case(pp, n, r, keys, seed, opts=None, deletes=None, max_rounds=None):
+    """Build and decode on the GPU and in the oracle; compare everything."""
+    gt = pp.IBLT(n, r, seed, opts)
+    ot = oracle.IBLT(n, r, seed)
+    if len(keys):
+        gt.insert(_dev(keys))
+    ot.insert(keys)
+    if deletes is not None and len(deletes):
+        gt.delete(_dev(deletes))
+        ot.insert(deletes, sign=-1)
+    torch.cuda.synchronize()
+    _assert_cells_equal(gt.cells(), ot)                     # build parity
+    items = len(keys) - (0 if deletes is None else len(deletes))
+    out = torch.zeros(max(1, items), dtype=torch.int64, device="cuda")
+    res = gt.decode(out)
+    ores = ot.decode_rounds() if max_rounds is None else ot.decode_rounds(max_rounds=max_rounds)
+    assert res.rounds == ores["rounds"]
+    got = out[: res.recovered].cpu().numpy().view(np.uint64)
+    rounds = _split_rounds(got, res.recovered_per_round)
+    assert len(rounds) == len(ores["keys"])
+    for t, (a, b) in enumerate(zip(rounds, ores["keys"])):
+        assert a.size == b.size, f"round {t + 1}"
+        assert (a == np.sort(b)).all(), f"round {t + 1}"
+    assert res.alive_cells_per_round == ores["cells_alive"]
+    left = items - np.cumsum([k.size for k in ores["keys"]])
+    assert res.remaining_per_round == [int(x) for x in left]
+    _assert_cells_equal(gt.cells(), ot)                     # residue parity
+    assert res.residual_cells == ot.residual_cells()
+    gt.close()
+    return res, ores
+
+
+CASES = [
+    # n_cells, r, load c, seed
+    (1000, 3, 0.70, 1),
+    (3 * 1024 + 17, 3, 0.75, 2),
+    (65541, 3, 0.75, 3),
+    (65536, 4, 0.70, 4),
+    (50000, 4, 0.85, 5),        # above c*_{2,4}: non-empty core
+    (20000, 3, 0.90, 6),        # above c*_{2,3}
+    (7777, 2, 0.40, 7),         # r = 2 (generic kernels)
+    (4099, 5, 0.60, 8),
+    (3001, 8, 0.50, 9),
+    (256, 3, 0.70, 10),
+    (200003, 3, 1.20, 12),      # far above threshold
+    ((1 << 20) + 13, 3, 0.80, 13),
+    ((1 << 18) + 1, 4, 0.76, 14),
+]
+
+
+@pytest.mark.parametrize("n,r,c,seed", CASES, ids=[f"n{n}-r{r}-c{c}" for n, r, c, _ in CASES])
+def test_iblt_parity(pp, n, r, c, seed):
+    keys = ppgen.distinct_keys(ppgen.edges_from_c(c, n), 1000 + seed)
+    run_case(pp, n, r, keys, seed)
+
+
+@pytest.mark.parametrize("n,r,c,seed", CASES[:6], ids=[f"hostloop-n{n}-r{r}" for n, r, c, _ in CASES[:6]])
+def test_iblt_parity_host_loop(pp, n, r, c, seed):
+    keys = ppgen.distinct_keys(ppgen.edges_from_c(c, n), 2000 + seed)
+    run_case(pp, n, r, keys, seed, opts=pp.options(host_loop=1))
+
+
+def test_small_grid_many_chunks_per_cta(pp):
+    # one CTA per SM forces every kernel through several grid-stride chunks
+    keys = ppgen.distinct_keys(ppgen.edges_from_c(0.78, 300007), 77)
+    run_case(pp, 300007, 3, keys, 21, opts=pp.options(ctas_per_sm=1))
+
+
+def test_empty_table(pp):
+    res, _ = run_case(pp, 100, 3, np.zeros(0, np.uint64), 5)
+    assert res.rounds == 0 and res.recovered == 0 and res.residual_cells == 0
+
+
+def test_minimum_table_and_single_key(pp):
+    run_case(pp, 3, 3, ppgen.distinct_keys(1, 9), 9)
+    run_case(pp, 30, 3, ppgen.distinct_keys(1, 10), 10)
+    run_case(pp, 3, 3, ppgen.distinct_keys(2, 11), 11)
+
+
+def test_duplicate_cells_leave_a_core(pp):
+    n, r, seed = 9, 3, 77
+    cand = ppgen.distinct_keys(200000, 5)
+    cells = oracle.key_cells(n, r, seed, cand)
+    seen, pair = {}, None
+    for x, row in zip(cand.tolist(), map(tuple, cells.tolist())):
+        if row in seen:
+            pair = (seen[row], x)
+            break
+        seen[row] = x
+    res, _ = run_case(pp, n, r, np.array(pair, np.uint64), seed)
+    assert res.rounds == 0 and res.residual_cells == 3
+
+
+def test_deletions(pp):
+    keys = ppgen.distinct_keys(30000, 31)
+    dele = keys[::3].copy()
+    run_case(pp, 50000, 3, keys, 31, deletes=dele)
+
+
+def test_round_limit(pp):
+    keys = ppgen.distinct_keys(ppgen.edges_from_c(0.80, 100000), 41)
+    with pytest.raises(pp.PPError) as ei:
+        run_case(pp, 100000, 3, keys, 41, opts=pp.options(max_rounds=3), max_rounds=3)
+    assert ei.value.name == "PP_ERR_ROUND_LIMIT"
+    # the table is left after round 3, like the oracle's
+    gt = pp.IBLT(100000, 3, 41, pp.options(max_rounds=3))
+    ot = oracle.IBLT(100000, 3, 41)
+    gt.insert(_dev(keys))
+    ot.insert(keys)
+    out = torch.zeros(keys.size, dtype=torch.int64, device="cuda")
+    with pytest.raises(pp.PPError):
+        gt.decode(out)
+    ores = ot.decode_rounds(max_rounds=3)
+    assert ores["status"] == oracle.ROUND_LIMIT and ores["rounds"] == 3
+    _assert_cells_equal(gt.cells(), ot)
+
+
+def test_capacity_checked_before_decoding(pp):
+    keys = ppgen.distinct_keys(1000, 51)
+    gt = pp.IBLT(2000, 3, 51)
+    gt.insert(_dev(keys))
+    before = gt.cells().copy()
+    out = torch.zeros(999, dtype=torch.int64, device="cuda")
+    with pytest.raises(pp.PPError) as ei:
+        gt.decode(out)
+    assert ei.value.name == "PP_ERR_CAPACITY"
+    assert (gt.cells() == before).all()
+
+
+def test_decode_twice_and_reuse(pp):
+    n, r, seed = 40000, 3, 61
+    gt = pp.IBLT(n, r, seed)
+    for rep in range(3):
+        keys = ppgen.distinct_keys(ppgen.edges_from_c(0.7, n), 6100 + rep)
+        gt.clear()
+        gt.insert(_dev(keys))
+        out = torch.zeros(keys.size, dtype=torch.int64, device="cuda")
+        res = gt.decode(out)
+        got = np.sort(out[: res.recovered].cpu().numpy().view(np.uint64))
+        ot = oracle.IBLT(n, r, seed)
+        ot.insert(keys)
+        ores = ot.decode_rounds()
+        assert res.rounds == ores["rounds"]
+        assert (got == np.sort(np.concatenate(ores["keys"]))).all()
+        res2 = gt.decode(out)     # nothing left to recover
+        assert res2.rounds == 0 and res2.recovered == 0
+
+
+def test_invalid_arguments(pp):
+    with pytest.raises(pp.PPError) as ei:
+        pp.IBLT(100, 1, 0)
+    assert ei.value.name == "PP_ERR_INVALID_ARG"
+    with pytest.raises(pp.PPError):
+        pp.IBLT(100, 9, 0)
+    with pytest.raises(pp.PPError):
+        pp.IBLT(2, 3, 0)
+
+
+def test_seeds_match_convention(pp):
+    gt = pp.IBLT(1000, 4, 0x1234)
+    assert gt.seeds() == [int(s) for s in oracle.hash_seeds(0x1234, 4)]
+
+
+def test_headline_full_size(pp):
+    """2^26 cells, r = 3, load 0.75 against the oracle's stored trajectory."""
+    gold = json.load(open(os.path.join(GOLDEN, "full_size.json")))["iblt_headline"]
+    n, r, m = gold["n_cells"], gold["r"], gold["m"]
+    keys = ppgen.distinct_keys(m, gold["key_seed"])
+    gt = pp.IBLT(n, r, gold["table_seed"])
+    dkeys = _dev(keys)
+    gt.insert(dkeys)
+    out = torch.zeros(m, dtype=torch.int64, device="cuda")
+    res = gt.decode(out)
+    assert res.rounds == gold["rounds"]
+    assert res.recovered_per_round == gold["recovered_per_round"]
+    assert res.alive_cells_per_round == gold["alive_cells_per_round"]
+    assert res.residual_cells == gold["residual_cells"] == 0
+    got = out.cpu().numpy().view(np.uint64)
+    rounds = _split_rounds(got, res.recovered_per_round)
+    for t, (a, h) in enumerate(zip(rounds, gold["round_sha256"])):
+        assert hashlib.sha256(a.tobytes()).hexdigest() == h, f"round {t + 1}"
+    assert (np.sort(got) == np.sort(keys)).all()   # recovered set == inserted set

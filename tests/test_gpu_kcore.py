@@ -1,0 +1,139 @@
+"""GPU parity: round-synchronous k-core peeling against the CPU oracle.
+
+Exact comparison of each vertex's and edge's removal round, the number of
+rounds and the per-round survivor counts s_t and m_t.
+"""
+import hashlib
+import json
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import ppgen
+from conftest import GOLDEN
+import test_oracle_pins as pins
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def pp(ppeel_lib):
+    import paper_1302_7014_b300 as pp
+    return pp
+
+
+def gpu_peel(pp, n, r, k, edges, opts=None):
+    m = edges.shape[0]
+    d_edges = torch.from_numpy(np.ascontiguousarray(edges, dtype=np.uint32).view(np.int32)).cuda()
+    if m == 0:
+        d_edges = torch.zeros((0, r), dtype=torch.int32, device="cuda")
+    vr = torch.full((max(n, 1),), -7, dtype=torch.int32, device="cuda")
+    er = torch.full((max(m, 1),), -7, dtype=torch.int32, device="cuda")
+    res = pp.peel_kcore(n, r, k, d_edges, vr[:n] if n else None, er[:m] if m else None, opts)
+    return res, vr[:n].cpu().numpy(), er[:m].cpu().numpy()
+
+
+def check(pp, n, k, edges, opts=None):
+    edges = np.ascontiguousarray(edges, dtype=np.uint32)
+    r = edges.shape[1]
+    res, vr, er = gpu_peel(pp, n, r, k, edges, opts)
+    o = oracle.kcore_rounds(n, k, edges)
+    assert res.rounds == o["rounds"]
+    assert (vr == o["vround"]).all()
+    assert (er == o["eround"]).all()
+    assert res.vertices_left == o["s"] and res.edges_left == o["m"]
+    assert res.core_vertices == int((o["vround"] == 0).sum())
+    assert res.core_edges == int((o["eround"] == 0).sum())
+    return res
+
+
+@pytest.mark.parametrize("name,n,k,edges", pins.HANDMADE, ids=[h[0] for h in pins.HANDMADE])
+def test_handmade(pp, name, n, k, edges):
+    if edges.shape[1] < 2:
+        pytest.skip("r >= 2")
+    check(pp, n, k, edges)
+
+
+def test_random_small(pp):
+    rng = np.random.default_rng(2024)
+    for trial in range(60):
+        n = int(rng.integers(1, 3000))
+        r = int(rng.choice([2, 3, 4, 6]))
+        k = int(rng.choice([1, 2, 3, 4]))
+        c = float(rng.uniform(0.2, 1.6))
+        m = int(c * n)
+        edges = ppgen.uniform_edges(n, r, m, 900 + trial)   # repeats inside an edge allowed
+        check(pp, n, k, edges)
+
+
+@pytest.mark.parametrize("n,r,k,c", [(5000, 3, 2, 0.8), (65537, 4, 2, 0.76), (40000, 2, 3, 1.6),
+                                     (30011, 3, 3, 1.5), (100000, 4, 2, 0.9), (2 ** 17 + 3, 5, 2, 0.6)])
+def test_partitioned(pp, n, r, k, c):
+    edges = ppgen.partitioned_edges(n, r, ppgen.edges_from_c(c, n), n + r)
+    check(pp, n, k, edges)
+
+
+def test_host_loop_matches(pp):
+    edges = ppgen.partitioned_edges(70000, 4, ppgen.edges_from_c(0.8, 70000), 5)
+    check(pp, 70000, 2, edges, opts=pp.options(host_loop=1))
+    check(pp, 70000, 2, edges, opts=pp.options(ctas_per_sm=1))
+
+
+def test_plain_peel_config(pp):
+    cfg = ppgen.PLAIN_PEEL
+    n, r, k = cfg["n"], cfg["r"], cfg["k"]
+    edges = ppgen.partitioned_edges(n, r, ppgen.edges_from_c(cfg["c"], n), cfg["seed"])
+    res = check(pp, n, k, edges)
+    assert res.core_vertices == 0 and 8 <= res.rounds <= 20
+
+
+def test_no_edges(pp):
+    res = check(pp, 5, 2, np.zeros((0, 3), np.uint32))
+    assert res.rounds == 1 and res.vertices_left == [0]
+
+
+def test_invalid_vertex_id(pp):
+    edges = np.array([[0, 1, 2], [0, 5, 1]], np.uint32)
+    with pytest.raises(pp.PPError) as ei:
+        gpu_peel(pp, 5, 3, 2, edges)
+    assert ei.value.name == "PP_ERR_INVALID_ARG"
+
+
+def test_round_limit(pp):
+    edges = ppgen.partitioned_edges(20000, 3, 14000, 3)
+    with pytest.raises(pp.PPError) as ei:
+        gpu_peel(pp, 20000, 3, 2, edges, pp.options(max_rounds=2))
+    assert ei.value.name == "PP_ERR_ROUND_LIMIT"
+
+
+def test_iblt_decode_is_the_k2_peel(pp):
+    # Sec. 6: recovery is peeling at k = 2 on the key hypergraph; both GPU paths agree
+    n, r, seed = 120000, 3, 88
+    keys = ppgen.distinct_keys(ppgen.edges_from_c(0.8, n), 89)
+    edges = oracle.key_cells(n, r, seed, keys).astype(np.uint32)
+    kres, vr, er = gpu_peel(pp, n, r, 2, edges)
+    t = pp.IBLT(n, r, seed)
+    t.insert(torch.from_numpy(keys.view(np.int64)).cuda())
+    out = torch.zeros(keys.size, dtype=torch.int64, device="cuda")
+    ires = t.decode(out)
+    removed = np.bincount(er[er > 0], minlength=kres.rounds + 1)[1:]
+    assert ires.rounds == max([t_ for t_ in range(1, kres.rounds + 1) if removed[t_ - 1]], default=0)
+    assert ires.recovered_per_round == [int(x) for x in removed[: ires.rounds]]
+    assert ires.alive_cells_per_round == kres.vertices_left[: ires.rounds]
+
+
+@pytest.mark.parametrize("idx", range(5))
+def test_density_sweep_full_size(pp, idx):
+    gold = json.load(open(os.path.join(GOLDEN, "full_size.json")))["density_sweep"][idx]
+    n, r, k = gold["n"], gold["r"], gold["k"]
+    edges = ppgen.partitioned_edges(n, r, gold["m"], gold["seed"])
+    res, vr, er = gpu_peel(pp, n, r, k, edges)
+    assert res.rounds == gold["rounds"]
+    assert res.vertices_left == gold["s"] and res.edges_left == gold["m_t"]
+    assert res.core_vertices == gold["core_vertices"] and res.core_edges == gold["core_edges"]
+    assert hashlib.sha256(vr.astype("<i4").tobytes()).hexdigest() == gold["vround_sha256"]
+    assert hashlib.sha256(er.astype("<i4").tobytes()).hexdigest() == gold["eround_sha256"]
