@@ -195,6 +195,38 @@ pp_status pp_peel_kcore(uint32_t n, uint32_t r, uint32_t k, const uint32_t *d_ed
                         uint64_t m, int32_t *d_vertex_round, int32_t *d_edge_round,
                         pp_peel_result *res, const pp_options *opt, void *stream);
 
+/* ------------------------------------------------------------------------
+ * IBLT decode that allocates nothing.  The paper has no counterpart: this is
+ * a convenience for callers that may not allocate device memory while they
+ * run -- for instance under a host framework that has already reserved nearly
+ * all GPU memory for its own pool, under a "no allocation after start-up"
+ * rule, or in latency-bound code that cannot afford cudaFree's implicit
+ * device-wide synchronisation.
+ *
+ * Decodes the caller's table in place, exactly as pp_iblt_decode does (same
+ * kernels, same rounds, same results); rounds are driven from the host.
+ * d_cells: n_cells pp_cell records on the device (layout above), built with
+ * the same r and seed.  d_out_keys/out_cap and *res as for pp_iblt_decode;
+ * items_before is computed from the cells (sum of counts / r), and out_cap
+ * below it returns CAPACITY before anything is decoded.
+ *
+ * Working memory is one fixed array of about 17 MB in the library's device
+ * code, which each GPU that loads the library keeps until the process exits.
+ * It holds tables of at most PP_NOALLOC_MAX_CELLS cells and decodes of at
+ * most PP_NOALLOC_MAX_ROUNDS rounds; larger tables give INVALID_ARG, longer
+ * decodes ROUND_LIMIT.  The first call on each device looks up that array's
+ * device address: make it before any stream capture.  All calls on a device
+ * share the array: calls whose GPU work overlaps race and must be serialised.
+ * No cudaMalloc/cudaFree or other allocating routine is called.
+ * Synchronizes `stream`.
+ * ------------------------------------------------------------------------ */
+#define PP_NOALLOC_MAX_CELLS (1u << 20)
+#define PP_NOALLOC_MAX_ROUNDS 4096u
+
+pp_status pp_iblt_decode_noalloc(pp_cell *d_cells, uint64_t n_cells, uint32_t r, uint64_t seed,
+                                 uint64_t *d_out_keys, uint64_t out_cap, pp_decode_result *res,
+                                 void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -57,7 +57,12 @@ _SIGNATURES = {
     "pp_iblt_info": (ctypes.c_int, [vp, ctypes.POINTER(u64), ctypes.POINTER(u32), ctypes.POINTER(u64)]),
     "pp_peel_kcore": (ctypes.c_int, [u32, u32, u32, vp, u64, vp, vp, ctypes.POINTER(PeelResult),
                                      ctypes.POINTER(Options), vp]),
+    "pp_iblt_decode_noalloc": (ctypes.c_int, [vp, u64, u32, u64, vp, u64,
+                                              ctypes.POINTER(DecodeResult), vp]),
 }
+
+PP_NOALLOC_MAX_CELLS = 1 << 20
+PP_NOALLOC_MAX_ROUNDS = 4096
 
 _lib = None
 

@@ -15,11 +15,6 @@ using namespace pp;
 
 namespace pp {
 
-struct IbltKernels {
-  const void *insert, *scan, *peel, *filter;
-  int nr;  // compile-time rank (PP_MAX_R for the generic instance)
-};
-
 template <int R, bool B>
 static IbltKernels iblt_kernels_t() {
   return {(const void *)k_insert<R, B>, (const void *)k_scan<R, B>, (const void *)k_peel<R, B>,
@@ -36,6 +31,8 @@ IbltKernels iblt_kernels(uint32_t r, bool batch) {
   if (r == 4) return iblt_kernels_t<4, false>();
   return iblt_kernels_t<0, false>();
 }
+
+const void *round_end_kernel() { return (const void *)k_round_end; }
 
 size_t peel_smem_bytes(int nr, bool batch) {
   const size_t ch = (size_t)kBlock * kPeelItems;
