@@ -191,8 +191,15 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--host-loop", action="store_true",
+                    help="drive rounds from the host (kernels launched one by one, as profilers need)")
+    ap.add_argument("--cells-log2", type=int, default=26,
+                    help="table size for profiling runs (the benchmark itself is 2^26)")
     args = ap.parse_args()
     cfg = dict(ppgen.IBLT_HEADLINE)
+    if args.cells_log2 != 26:
+        cfg["n_cells"] = 1 << args.cells_log2
+        cfg["name"] = f"iblt n=2^{args.cells_log2} r=3 c=0.75 (profiling size)"
     if args.impl == "reference":
         run_reference(args, cfg)
         return
@@ -222,7 +229,7 @@ def main():
     m = ppgen.edges_from_c(c, n)
     keys_h = ppgen.distinct_keys(m, cfg["key_seed"] + 7919 * rank)
     stream = torch.cuda.Stream()
-    table = pp.IBLT(n, r, cfg["table_seed"] + rank)
+    table = pp.IBLT(n, r, cfg["table_seed"] + rank, pp.options(host_loop=1) if args.host_loop else None)
     with torch.cuda.stream(stream):
         dkeys = torch.from_numpy(keys_h.view(np.int64)).cuda()
         out = torch.empty(m, dtype=torch.int64, device="cuda")
@@ -331,7 +338,8 @@ def main():
                 "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
                 "config": {"workload": cfg["name"], "n_cells": n, "r": r, "load": c, "keys": m,
                            "rounds": rounds, "l2": "inputs > L2 (2.1 GB table, 0.4 GB keys)",
-                           "parallelism": f"replicas x{world}" if world > 1 else "single"},
+                           "parallelism": f"replicas x{world}" if world > 1 else "single",
+                           "round_loop": "host" if args.host_loop else "graph"},
                 "build_ms": b_ms, "decode_ms": d_ms, "peel_ms": d_ms,
                 "decode_keys_per_s": m / (d_ms * 1e-3),
                 "kernels": kernels, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,

@@ -196,6 +196,67 @@ pp_status pp_peel_kcore(uint32_t n, uint32_t r, uint32_t k, const uint32_t *d_ed
                         pp_peel_result *res, const pp_options *opt, void *stream);
 
 /* ------------------------------------------------------------------------
+ * Batched decode: many IBLTs of uneven size, decoded together.
+ *
+ * The tables share one device arena and one frontier: a decode is one CUDA
+ * graph launch in which each device-side round peels the current frontier of
+ * every table at once (Sec. 1 rounds at k = 2, per table).  Tables never share
+ * cells, so every table's rounds, recovered keys and residue equal those of a
+ * plain pp_iblt_decode of that table alone.
+ * ------------------------------------------------------------------------ */
+typedef struct pp_batch pp_batch;
+
+/* Per-table outcome of pp_batch_decode.  round_cap / recovered_per_round are
+ * set by the caller (host array or NULL). */
+typedef struct pp_table_result {
+  uint32_t rounds;           /* rounds that recovered >= 1 key of this table */
+  uint32_t stats_complete;   /* 1 if every round fit in opt.stats_rounds */
+  uint64_t recovered;        /* keys written to this table's output slots */
+  uint64_t items_before;     /* keys in this table before the decode */
+  uint64_t residual_cells;   /* non-empty cells left (the table's 2-core) */
+  uint32_t round_cap;
+  uint32_t pad;
+  uint64_t *recovered_per_round; /* keys recovered in round t at [t-1] */
+} pp_table_result;
+
+/* Creates n_tables empty tables; table i has n_cells[i] cells, r[i] hash
+ * functions (2..PP_MAX_R, mixed values allowed) and seed seeds[i] (same
+ * convention as pp_iblt_create).  All tables together must hold fewer than
+ * 2^32 - 64 cells.  Allocates ~49 B per cell. */
+pp_status pp_batch_create(pp_batch **out, uint32_t n_tables, const uint64_t *n_cells,
+                          const uint32_t *r, const uint64_t *seeds, const pp_options *opt);
+
+pp_status pp_batch_destroy(pp_batch *b);
+
+/* Zeroes every table (enqueued on `stream`). */
+pp_status pp_batch_clear(pp_batch *b, void *stream);
+
+/* Inserts keys: table i receives d_keys[h_key_offsets[i] .. h_key_offsets[i+1]-1].
+ * h_key_offsets: host array of n_tables+1 nondecreasing entries (< 2^32).
+ * Enqueued on `stream` (the host arrays are copied before return). */
+pp_status pp_batch_insert(pp_batch *b, const uint64_t *d_keys, const uint64_t *h_key_offsets,
+                          void *stream);
+
+/* Deletes keys, same layout as pp_batch_insert. */
+pp_status pp_batch_delete(pp_batch *b, const uint64_t *d_keys, const uint64_t *h_key_offsets,
+                          void *stream);
+
+/* Decodes every table in place.  Table i's recovered keys go to
+ * d_out_keys[h_out_offsets[i] ..], grouped by round, in no order within a
+ * round; each table needs at least as many slots as it holds keys, else
+ * CAPACITY before anything runs.  results: host array of n_tables entries.
+ * Synchronizes `stream`. */
+pp_status pp_batch_decode(pp_batch *b, uint64_t *d_out_keys, const uint64_t *h_out_offsets,
+                          pp_table_result *results, void *stream);
+
+/* Copies table `table`'s cells to dst (host if to_host, else device). */
+pp_status pp_batch_copy_cells(pp_batch *b, uint32_t table, void *dst, int to_host, void *stream);
+
+/* Number of tables, arena cells (with alignment padding), rounds of the last decode. */
+pp_status pp_batch_info(const pp_batch *b, uint32_t *n_tables, uint64_t *total_cells,
+                        uint32_t *last_rounds);
+
+/* ------------------------------------------------------------------------
  * IBLT decode that allocates nothing.  The paper has no counterpart: this is
  * a convenience for callers that may not allocate device memory while they
  * run -- for instance under a host framework that has already reserved nearly

@@ -1,0 +1,131 @@
+"""Batched IBLT decode (pp_batch_* in include/ppeel.h): many tables, one graph launch."""
+from __future__ import annotations
+
+import ctypes
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import _lib
+from . import _check, _dev_ptr, _stream_ptr
+from ._lib import Options
+
+u32, u64, vp = ctypes.c_uint32, ctypes.c_uint64, ctypes.c_void_p
+
+
+class TableResult(ctypes.Structure):
+    _fields_ = [("rounds", u32), ("stats_complete", u32), ("recovered", u64), ("items_before", u64),
+                ("residual_cells", u64), ("round_cap", u32), ("pad", u32),
+                ("recovered_per_round", ctypes.POINTER(u64))]
+
+
+_lib.declare("pp_batch_create", ctypes.c_int, [ctypes.POINTER(vp), u32, ctypes.POINTER(u64),
+                                               ctypes.POINTER(u32), ctypes.POINTER(u64),
+                                               ctypes.POINTER(Options)])
+_lib.declare("pp_batch_destroy", ctypes.c_int, [vp])
+_lib.declare("pp_batch_clear", ctypes.c_int, [vp, vp])
+_lib.declare("pp_batch_insert", ctypes.c_int, [vp, vp, ctypes.POINTER(u64), vp])
+_lib.declare("pp_batch_delete", ctypes.c_int, [vp, vp, ctypes.POINTER(u64), vp])
+_lib.declare("pp_batch_decode", ctypes.c_int, [vp, vp, ctypes.POINTER(u64), ctypes.POINTER(TableResult), vp])
+_lib.declare("pp_batch_copy_cells", ctypes.c_int, [vp, u32, vp, ctypes.c_int, vp])
+_lib.declare("pp_batch_info", ctypes.c_int, [vp, ctypes.POINTER(u32), ctypes.POINTER(u64), ctypes.POINTER(u32)])
+
+
+@dataclass
+class BatchOutcome:
+    rounds: np.ndarray          # per table
+    recovered: np.ndarray
+    items_before: np.ndarray
+    residual_cells: np.ndarray
+    recovered_per_round: list   # per table: list of per-round counts
+    stats_complete: np.ndarray
+
+
+def _u64_array(values):
+    a = np.ascontiguousarray(np.asarray(values, dtype=np.uint64))
+    return a, a.ctypes.data_as(ctypes.POINTER(u64))
+
+
+class Batch:
+    """n tables (sizes n_cells[i], ranks r[i], seeds seeds[i]) in one device arena."""
+
+    def __init__(self, n_cells, r, seeds, opts: Options | None = None):
+        lib = _lib.load()
+        self.n_cells = [int(x) for x in n_cells]
+        self.r = [int(x) for x in r]
+        self.seeds = [int(x) & (2**64 - 1) for x in seeds]
+        n = len(self.n_cells)
+        nc, nc_p = _u64_array(self.n_cells)
+        rr = np.ascontiguousarray(np.asarray(self.r, dtype=np.uint32))
+        sd, sd_p = _u64_array(self.seeds)
+        h = ctypes.c_void_p()
+        _check(lib.pp_batch_create(ctypes.byref(h), n, nc_p, rr.ctypes.data_as(ctypes.POINTER(u32)), sd_p,
+                                   ctypes.byref(opts) if opts is not None else None), "pp_batch_create")
+        self._h = h
+        self.n_tables = n
+        self.stats_rounds = opts.stats_rounds if opts is not None and opts.stats_rounds else 128
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            _lib.load().pp_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def clear(self, stream=None):
+        _check(_lib.load().pp_batch_clear(self._h, _stream_ptr(stream)), "pp_batch_clear")
+
+    def insert(self, keys, key_offsets, stream=None, sign: int = 1):
+        """keys: CUDA tensor (8-byte elements); table i gets keys[key_offsets[i]:key_offsets[i+1]]."""
+        off, off_p = _u64_array(key_offsets)
+        assert off.size == self.n_tables + 1
+        fn = _lib.load().pp_batch_insert if sign > 0 else _lib.load().pp_batch_delete
+        ptr = _dev_ptr(keys, 8, "keys") if keys is not None and keys.numel() else None
+        _check(fn(self._h, ptr, off_p, _stream_ptr(stream)), "pp_batch_insert")
+
+    def delete(self, keys, key_offsets, stream=None):
+        self.insert(keys, key_offsets, stream, sign=-1)
+
+    def decode(self, out, out_offsets, round_cap: int = 256, stream=None) -> BatchOutcome:
+        off, off_p = _u64_array(out_offsets)
+        n = self.n_tables
+        results = (TableResult * n)()
+        per_round = np.zeros((n, round_cap), dtype=np.uint64)
+        for i in range(n):
+            results[i].round_cap = round_cap
+            results[i].recovered_per_round = per_round[i].ctypes.data_as(ctypes.POINTER(u64))
+        ptr = _dev_ptr(out, 8, "out") if out is not None and out.numel() else None
+        _check(_lib.load().pp_batch_decode(self._h, ptr, off_p, results, _stream_ptr(stream)),
+               "pp_batch_decode")
+        rounds = np.array([results[i].rounds for i in range(n)], dtype=np.int64)
+        return BatchOutcome(
+            rounds=rounds,
+            recovered=np.array([results[i].recovered for i in range(n)], dtype=np.int64),
+            items_before=np.array([results[i].items_before for i in range(n)], dtype=np.int64),
+            residual_cells=np.array([results[i].residual_cells for i in range(n)], dtype=np.int64),
+            recovered_per_round=[per_round[i, : min(rounds[i], round_cap)].tolist() for i in range(n)],
+            stats_complete=np.array([results[i].stats_complete for i in range(n)], dtype=bool))
+
+    def cells(self, table: int):
+        dt = np.dtype([("key_xor", "<u8"), ("chk_xor", "<u8"), ("count", "<i4"), ("reserved", "<u4", 3)])
+        out = np.zeros(self.n_cells[table], dtype=dt)
+        _check(_lib.load().pp_batch_copy_cells(self._h, table, ctypes.c_void_p(out.ctypes.data), 1,
+                                               _stream_ptr(None)), "pp_batch_copy_cells")
+        return out
+
+
+# Function-style names matching the C ABI.
+def batch_create(n_cells, r, seeds, opts: Options | None = None) -> Batch:
+    return Batch(n_cells, r, seeds, opts)
+
+
+def batch_insert(batch: Batch, keys, key_offsets, stream=None) -> None:
+    batch.insert(keys, key_offsets, stream)
+
+
+def batch_decode(batch: Batch, out, out_offsets, round_cap: int = 256, stream=None) -> BatchOutcome:
+    return batch.decode(out, out_offsets, round_cap, stream)

@@ -1,0 +1,480 @@
+// C-ABI: many IBLTs decoded together (batched form of the round-synchronous
+// decode).
+//
+// All tables live in one device arena (table i starts at a 32-cell-aligned
+// global cell id) and share one frontier.  A decode is one CUDA graph launch:
+// the full scan covers every table, then each device-side round peels the
+// current frontier entries of all tables at once.  Tables never share cells,
+// so each table's rounds, recovered keys and residue are exactly those of a
+// plain decode of that table alone; a table whose frontier empties simply
+// stops contributing entries.  Per-table counters record keys recovered per
+// round (the first stats_rounds rounds), the last productive round, and the
+// residue size.
+#include <string.h>
+
+#include <vector>
+
+#include "host.cuh"
+#include "iblt_types.cuh"
+
+using namespace pp;
+
+namespace {
+
+constexpr u32 kInsertChunk = 4096;        // keys per insert work item
+constexpr u32 kScanChunk = kBlock * kScanItems;
+
+}  // namespace
+
+struct pp_batch {
+  uint32_t n_tables = 0;
+  uint32_t rank = 0;          // 0 = mixed r (generic kernels), else the common r
+  uint64_t total_cells = 0;   // arena size (cells), including alignment padding
+  pp_options opt{};
+  std::vector<TableArgs> h_tabs;
+  std::vector<uint64_t> items;  // keys per table (inserted - deleted)
+  TableArgs *tabs = nullptr;
+  Cell *cells = nullptr;
+  u64 *fkey = nullptr;
+  u32 *fcell = nullptr, *ftab = nullptr, *cand = nullptr, *ctab = nullptr, *bitmap = nullptr;
+  Chunk *scan_chunks = nullptr;
+  u32 n_scan_chunks = 0;
+  Chunk *ins_chunks = nullptr;
+  u32 ins_chunk_cap = 0;
+  Chunk *h_ins_chunks = nullptr;  // pinned staging
+  DecodeCtl *ctl = nullptr, *h_ctl = nullptr;
+  u64 *st_rec = nullptr, *st_alive = nullptr;
+  u32 *st_front = nullptr;
+  BatchCounters bc{};
+  // pinned copies of the per-table counters
+  u64 *h_recovered = nullptr, *h_nonempty = nullptr, *h_emptied = nullptr;
+  u32 *h_rounds = nullptr, *h_round_rec = nullptr;
+  IbltKernels k{};
+  int grid_scan = 0, grid_peel = 0, grid_filter = 0, grid_insert = 0;
+  size_t smem_peel = 0;
+  cudaGraphExec_t exec = nullptr;
+  u64 *graph_out = nullptr;  // output buffer the instantiated graph writes to
+};
+
+namespace {
+
+void free_batch(pp_batch *b) {
+  if (!b) return;
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  cudaFree(b->tabs);
+  cudaFree(b->cells);
+  cudaFree(b->fkey);
+  cudaFree(b->fcell);
+  cudaFree(b->ftab);
+  cudaFree(b->cand);
+  cudaFree(b->ctab);
+  cudaFree(b->bitmap);
+  cudaFree(b->scan_chunks);
+  cudaFree(b->ins_chunks);
+  cudaFreeHost(b->h_ins_chunks);
+  cudaFree(b->ctl);
+  cudaFreeHost(b->h_ctl);
+  cudaFree(b->st_rec);
+  cudaFree(b->st_alive);
+  cudaFree(b->st_front);
+  cudaFree(b->bc.recovered);
+  cudaFree(b->bc.nonempty);
+  cudaFree(b->bc.emptied);
+  cudaFree(b->bc.rounds);
+  cudaFree(b->bc.round_rec);
+  cudaFreeHost(b->h_recovered);
+  cudaFreeHost(b->h_nonempty);
+  cudaFreeHost(b->h_emptied);
+  cudaFreeHost(b->h_rounds);
+  cudaFreeHost(b->h_round_rec);
+  delete b;
+}
+
+struct BatchArgs {
+  // scan
+  Cell *cells;
+  TableArgs tab0;
+  const TableArgs *tabs;
+  const Chunk *chunks;
+  u32 n_chunks;
+  u64 *fkey;
+  u32 *fcell, *ftab, *bitmap;
+  DecodeCtl *ctl;
+  BatchCounters bc;
+  // peel
+  const u64 *fkey_c;
+  const u32 *fcell_c, *ftab_c, *bitmap_c;
+  u32 *cand, *ctab;
+  u64 *bout;
+  // filter
+  const Cell *cells_c;
+  const u32 *cand_c, *ctab_c;
+  // round end
+  RoundStats st;
+  int set_cond;
+  cudaGraphConditionalHandle cond;
+  void *scan_p[11], *peel_p[12], *filter_p[10], *end_p[4];
+  void bind() {
+    void *s[11] = {&cells, &tab0, &tabs, &chunks, &n_chunks, &fkey, &fcell, &ftab, &bitmap, &ctl, &bc};
+    void *p[12] = {&cells, &tab0, &tabs, &fkey_c, &fcell_c, &ftab_c, &bitmap_c, &cand, &ctab, &bout, &ctl, &bc};
+    void *f[10] = {&cells_c, &tab0, &tabs, &cand_c, &ctab_c, &fkey, &fcell, &ftab, &bitmap, &ctl};
+    void *e[4] = {&ctl, &st, &set_cond, &cond};
+    memcpy(scan_p, s, sizeof s);
+    memcpy(peel_p, p, sizeof p);
+    memcpy(filter_p, f, sizeof f);
+    memcpy(end_p, e, sizeof e);
+  }
+};
+
+void fill(pp_batch *b, BatchArgs &a, u64 *out) {
+  memset(&a, 0, sizeof a);
+  a.cells = b->cells;
+  a.tabs = b->tabs;
+  a.chunks = b->scan_chunks;
+  a.n_chunks = b->n_scan_chunks;
+  a.fkey = b->fkey;
+  a.fcell = b->fcell;
+  a.ftab = b->ftab;
+  a.bitmap = b->bitmap;
+  a.ctl = b->ctl;
+  a.bc = b->bc;
+  a.fkey_c = b->fkey;
+  a.fcell_c = b->fcell;
+  a.ftab_c = b->ftab;
+  a.bitmap_c = b->bitmap;
+  a.cand = b->cand;
+  a.ctab = b->ctab;
+  a.bout = out;
+  a.cells_c = b->cells;
+  a.cand_c = b->cand;
+  a.ctab_c = b->ctab;
+  a.st = RoundStats{b->st_rec, b->st_alive, b->st_front};
+  a.bind();
+}
+
+pp_status add_kernel(cudaGraphNode_t *node, cudaGraph_t g, const cudaGraphNode_t *dep, size_t ndep,
+                     const void *fn, int grid, int block, size_t smem, void **args) {
+  cudaKernelNodeParams kp{};
+  kp.func = const_cast<void *>(fn);
+  kp.gridDim = dim3((unsigned)grid);
+  kp.blockDim = dim3((unsigned)block);
+  kp.sharedMemBytes = (unsigned)smem;
+  kp.kernelParams = args;
+  PP_CUDA(cudaGraphAddKernelNode(node, g, dep, ndep, &kp));
+  return PP_OK;
+}
+
+// The output pointer is a kernel argument, so the graph is rebuilt when it
+// changes (the caller usually decodes into the same buffer every time).
+pp_status build_graph(pp_batch *b, u64 *out) {
+  if (b->exec) {
+    cudaGraphExecDestroy(b->exec);
+    b->exec = nullptr;
+  }
+  BatchArgs a;
+  fill(b, a, out);
+  cudaGraph_t g = nullptr;
+  PP_CUDA(cudaGraphCreate(&g, 0));
+  pp_status st = PP_OK;
+  cudaGraphNode_t n_scan, n_cond, n_peel, n_filter, n_end;
+  cudaGraphConditionalHandle h;
+  cudaGraphNodeParams cp{};
+  cudaGraph_t body;
+  st = add_kernel(&n_scan, g, nullptr, 0, b->k.scan, b->grid_scan, kBlock, 0, a.scan_p);
+  if (st != PP_OK) goto done;
+  if (cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault) != cudaSuccess) {
+    st = fail(PP_ERR_CUDA, "cudaGraphConditionalHandleCreate failed");
+    goto done;
+  }
+  cp.type = cudaGraphNodeTypeConditional;
+  cp.conditional.handle = h;
+  cp.conditional.type = cudaGraphCondTypeWhile;
+  cp.conditional.size = 1;
+  if (cudaGraphAddNode(&n_cond, g, &n_scan, nullptr, 1, &cp) != cudaSuccess) {
+    st = fail(PP_ERR_CUDA, "cudaGraphAddNode(conditional while) failed");
+    goto done;
+  }
+  body = cp.conditional.phGraph_out[0];
+  a.set_cond = 1;
+  a.cond = h;
+  st = add_kernel(&n_peel, body, nullptr, 0, b->k.peel, b->grid_peel, kBlock, b->smem_peel, a.peel_p);
+  if (st != PP_OK) goto done;
+  st = add_kernel(&n_filter, body, &n_peel, 1, b->k.filter, b->grid_filter, kBlock, 0, a.filter_p);
+  if (st != PP_OK) goto done;
+  st = add_kernel(&n_end, body, &n_filter, 1, round_end_kernel(), 1, 32, 0, a.end_p);
+  if (st != PP_OK) goto done;
+  if (cudaGraphInstantiate(&b->exec, g, 0) != cudaSuccess) {
+    st = fail(PP_ERR_CUDA, "cudaGraphInstantiate failed");
+    b->exec = nullptr;
+  }
+done:
+  cudaGraphDestroy(g);
+  return st;
+}
+
+}  // namespace
+
+extern "C" {
+
+pp_status pp_batch_create(pp_batch **out, uint32_t n_tables, const uint64_t *n_cells,
+                          const uint32_t *r, const uint64_t *seeds, const pp_options *opt) {
+  if (!out) return fail(PP_ERR_INVALID_ARG, "pp_batch_create: out is NULL");
+  *out = nullptr;
+  if (n_tables == 0 || !n_cells || !r || !seeds)
+    return fail(PP_ERR_INVALID_ARG, "pp_batch_create: empty batch or NULL arrays");
+  pp_batch *b = new pp_batch();
+  b->n_tables = n_tables;
+  b->opt = resolve_options(opt);
+  b->h_tabs.resize(n_tables);
+  b->items.assign(n_tables, 0);
+  uint64_t base = 0;
+  uint32_t common_r = r[0];
+  std::vector<Chunk> chunks;
+  for (uint32_t i = 0; i < n_tables; ++i) {
+    if (r[i] < 2 || r[i] > PP_MAX_R || n_cells[i] < r[i] || n_cells[i] > 0xFFFFFFFFull) {
+      free_batch(b);
+      return fail(PP_ERR_INVALID_ARG, "pp_batch_create: table %u has r=%u, n_cells=%llu", i, r[i],
+                  (unsigned long long)n_cells[i]);
+    }
+    if (r[i] != common_r) common_r = 0;
+    if (base + n_cells[i] > 0xFFFFFFFFull - 64) {
+      free_batch(b);
+      return fail(PP_ERR_INVALID_ARG, "pp_batch_create: more than 2^32-64 cells in total");
+    }
+    make_table_args(b->h_tabs[i], n_cells[i], r[i], seeds[i], (uint32_t)base);
+    for (uint64_t c = 0; c < n_cells[i]; c += kScanChunk) {
+      const uint64_t e = c + kScanChunk < n_cells[i] ? c + kScanChunk : n_cells[i];
+      chunks.push_back(Chunk{i, (u32)(base + c), (u32)(base + e)});
+    }
+    base += (n_cells[i] + 31) & ~31ull;
+  }
+  b->rank = common_r;
+  b->total_cells = base;
+  b->n_scan_chunks = (u32)chunks.size();
+  b->k = iblt_kernels(common_r ? common_r : 0, true);
+  b->smem_peel = peel_smem_bytes(b->k.nr, true);
+  const uint64_t N = base;
+  const uint32_t mr = b->opt.max_rounds;
+  const uint32_t sr = b->opt.stats_rounds;
+  b->ins_chunk_cap = 1024;
+  cudaError_t e = cudaSuccess;
+  auto al = [&](void **p, size_t bytes) {
+    if (e == cudaSuccess) e = cudaMalloc(p, bytes ? bytes : 16);
+  };
+  al((void **)&b->tabs, n_tables * sizeof(TableArgs));
+  al((void **)&b->cells, N * sizeof(Cell));
+  al((void **)&b->fkey, N * sizeof(u64));
+  al((void **)&b->fcell, N * sizeof(u32));
+  al((void **)&b->ftab, N * sizeof(u32));
+  al((void **)&b->cand, N * sizeof(u32));
+  al((void **)&b->ctab, N * sizeof(u32));
+  al((void **)&b->bitmap, (N / 32 + 1) * sizeof(u32));
+  al((void **)&b->scan_chunks, chunks.size() * sizeof(Chunk));
+  al((void **)&b->ins_chunks, b->ins_chunk_cap * sizeof(Chunk));
+  al((void **)&b->ctl, sizeof(DecodeCtl));
+  al((void **)&b->st_rec, (size_t)mr * sizeof(u64));
+  al((void **)&b->st_alive, (size_t)mr * sizeof(u64));
+  al((void **)&b->st_front, (size_t)mr * sizeof(u32));
+  al((void **)&b->bc.recovered, n_tables * sizeof(u64));
+  al((void **)&b->bc.nonempty, n_tables * sizeof(u64));
+  al((void **)&b->bc.emptied, n_tables * sizeof(u64));
+  al((void **)&b->bc.rounds, n_tables * sizeof(u32));
+  al((void **)&b->bc.round_rec, (size_t)n_tables * sr * sizeof(u32));
+  if (e == cudaSuccess) e = cudaMallocHost((void **)&b->h_ctl, sizeof(DecodeCtl));
+  if (e == cudaSuccess) e = cudaMallocHost((void **)&b->h_ins_chunks, b->ins_chunk_cap * sizeof(Chunk));
+  if (e == cudaSuccess) e = cudaMallocHost((void **)&b->h_recovered, n_tables * sizeof(u64));
+  if (e == cudaSuccess) e = cudaMallocHost((void **)&b->h_nonempty, n_tables * sizeof(u64));
+  if (e == cudaSuccess) e = cudaMallocHost((void **)&b->h_emptied, n_tables * sizeof(u64));
+  if (e == cudaSuccess) e = cudaMallocHost((void **)&b->h_rounds, n_tables * sizeof(u32));
+  if (e == cudaSuccess) e = cudaMallocHost((void **)&b->h_round_rec, (size_t)n_tables * sr * sizeof(u32));
+  if (e == cudaSuccess) e = cudaMemcpy(b->tabs, b->h_tabs.data(), n_tables * sizeof(TableArgs), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(b->scan_chunks, chunks.data(), chunks.size() * sizeof(Chunk), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemset(b->cells, 0, N * sizeof(Cell));
+  if (e == cudaSuccess) e = cudaMemset(b->bitmap, 0, (N / 32 + 1) * sizeof(u32));
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) {
+    pp_status st = cuda_fail(e, "pp_batch_create allocation", __FILE__, __LINE__);
+    free_batch(b);
+    return st;
+  }
+  b->grid_scan = persistent_grid(b->k.scan, kBlock, 0, b->opt.ctas_per_sm);
+  b->grid_peel = persistent_grid(b->k.peel, kBlock, b->smem_peel, b->opt.ctas_per_sm);
+  b->grid_filter = persistent_grid(b->k.filter, kBlock, 0, b->opt.ctas_per_sm);
+  b->grid_insert = persistent_grid(b->k.insert, kBlock, 0, 8) * 2;
+  *out = b;
+  return PP_OK;
+}
+
+pp_status pp_batch_destroy(pp_batch *b) {
+  if (!b) return PP_OK;
+  cudaDeviceSynchronize();
+  free_batch(b);
+  return PP_OK;
+}
+
+pp_status pp_batch_clear(pp_batch *b, void *stream) {
+  if (!b) return fail(PP_ERR_INVALID_ARG, "pp_batch_clear: NULL batch");
+  PP_CUDA(cudaMemsetAsync(b->cells, 0, b->total_cells * sizeof(Cell), as_stream(stream)));
+  for (auto &x : b->items) x = 0;
+  return PP_OK;
+}
+
+static pp_status batch_update(pp_batch *b, const uint64_t *d_keys, const uint64_t *h_key_offsets,
+                              int sign, void *stream) {
+  if (!b || !h_key_offsets) return fail(PP_ERR_INVALID_ARG, "pp_batch_insert: NULL argument");
+  cudaStream_t s = as_stream(stream);
+  std::vector<Chunk> chunks;
+  for (uint32_t i = 0; i < b->n_tables; ++i) {
+    const uint64_t k0 = h_key_offsets[i], k1 = h_key_offsets[i + 1];
+    if (k1 < k0) return fail(PP_ERR_INVALID_ARG, "pp_batch_insert: key offsets decrease at table %u", i);
+    if (k1 > 0xFFFFFFFFull) return fail(PP_ERR_INVALID_ARG, "pp_batch_insert: more than 2^32 keys");
+    for (uint64_t k = k0; k < k1; k += kInsertChunk)
+      chunks.push_back(Chunk{i, (u32)k, (u32)(k + kInsertChunk < k1 ? k + kInsertChunk : k1)});
+  }
+  if (chunks.empty()) return PP_OK;
+  if (!d_keys) return fail(PP_ERR_INVALID_ARG, "pp_batch_insert: NULL keys");
+  if (chunks.size() > b->ins_chunk_cap) {
+    PP_CUDA(cudaStreamSynchronize(s));
+    cudaFree(b->ins_chunks);
+    cudaFreeHost(b->h_ins_chunks);
+    b->ins_chunks = nullptr;
+    b->h_ins_chunks = nullptr;
+    b->ins_chunk_cap = (u32)chunks.size();
+    PP_CUDA(cudaMalloc((void **)&b->ins_chunks, b->ins_chunk_cap * sizeof(Chunk)));
+    PP_CUDA(cudaMallocHost((void **)&b->h_ins_chunks, b->ins_chunk_cap * sizeof(Chunk)));
+  } else {
+    // the pinned staging buffer may still feed a previous copy
+    PP_CUDA(cudaStreamSynchronize(s));
+  }
+  memcpy(b->h_ins_chunks, chunks.data(), chunks.size() * sizeof(Chunk));
+  PP_CUDA(cudaMemcpyAsync(b->ins_chunks, b->h_ins_chunks, chunks.size() * sizeof(Chunk),
+                          cudaMemcpyHostToDevice, s));
+  Cell *cells = b->cells;
+  TableArgs t0{};
+  const TableArgs *tabs = b->tabs;
+  const Chunk *ch = b->ins_chunks;
+  u32 nch = (u32)chunks.size();
+  const u64 *keys = reinterpret_cast<const u64 *>(d_keys);
+  u64 m = 0;
+  void *args[] = {&cells, &t0, &tabs, &ch, &nch, &keys, &m, &sign};
+  const int grid = nch < (u32)b->grid_insert ? (int)nch : b->grid_insert;
+  PP_CUDA(cudaLaunchKernel(b->k.insert, dim3(grid), dim3(kBlock), args, 0, s));
+  for (uint32_t i = 0; i < b->n_tables; ++i) {
+    const uint64_t d = h_key_offsets[i + 1] - h_key_offsets[i];
+    b->items[i] = sign > 0 ? b->items[i] + d : (b->items[i] >= d ? b->items[i] - d : 0);
+  }
+  return PP_OK;
+}
+
+pp_status pp_batch_insert(pp_batch *b, const uint64_t *d_keys, const uint64_t *h_key_offsets,
+                          void *stream) {
+  return batch_update(b, d_keys, h_key_offsets, +1, stream);
+}
+
+pp_status pp_batch_delete(pp_batch *b, const uint64_t *d_keys, const uint64_t *h_key_offsets,
+                          void *stream) {
+  return batch_update(b, d_keys, h_key_offsets, -1, stream);
+}
+
+pp_status pp_batch_decode(pp_batch *b, uint64_t *d_out_keys, const uint64_t *h_out_offsets,
+                          pp_table_result *results, void *stream) {
+  if (!b || !h_out_offsets || !results) return fail(PP_ERR_INVALID_ARG, "pp_batch_decode: NULL argument");
+  cudaStream_t s = as_stream(stream);
+  bool moved = false;
+  for (uint32_t i = 0; i < b->n_tables; ++i) {
+    const uint64_t o0 = h_out_offsets[i], o1 = h_out_offsets[i + 1];
+    if (o1 < o0) return fail(PP_ERR_INVALID_ARG, "pp_batch_decode: output offsets decrease at table %u", i);
+    if (o1 - o0 < b->items[i])
+      return fail(PP_ERR_CAPACITY, "pp_batch_decode: table %u has %llu keys but %llu output slots", i,
+                  (unsigned long long)b->items[i], (unsigned long long)(o1 - o0));
+    if (b->h_tabs[i].out_base != o0 || b->h_tabs[i].out_cap != o1 - o0) {
+      b->h_tabs[i].out_base = o0;
+      b->h_tabs[i].out_cap = o1 - o0;
+      moved = true;
+    }
+  }
+  if (h_out_offsets[b->n_tables] && !d_out_keys) return fail(PP_ERR_INVALID_ARG, "pp_batch_decode: NULL output");
+  if (moved)
+    PP_CUDA(cudaMemcpyAsync(b->tabs, b->h_tabs.data(), b->n_tables * sizeof(TableArgs),
+                            cudaMemcpyHostToDevice, s));
+  // fresh counters
+  const uint32_t n = b->n_tables, sr = b->opt.stats_rounds;
+  PP_CUDA(cudaMemsetAsync(b->bc.recovered, 0, n * sizeof(u64), s));
+  PP_CUDA(cudaMemsetAsync(b->bc.nonempty, 0, n * sizeof(u64), s));
+  PP_CUDA(cudaMemsetAsync(b->bc.emptied, 0, n * sizeof(u64), s));
+  PP_CUDA(cudaMemsetAsync(b->bc.rounds, 0, n * sizeof(u32), s));
+  PP_CUDA(cudaMemsetAsync(b->bc.round_rec, 0, (size_t)n * sr * sizeof(u32), s));
+  memset(b->h_ctl, 0, sizeof(DecodeCtl));
+  b->h_ctl->max_rounds = b->opt.max_rounds;
+  b->h_ctl->stats_rounds = sr;
+  PP_CUDA(cudaMemcpyAsync(b->ctl, b->h_ctl, sizeof(DecodeCtl), cudaMemcpyHostToDevice, s));
+  u64 *out = reinterpret_cast<u64 *>(d_out_keys);
+  if (b->opt.host_loop) {
+    BatchArgs a;
+    fill(b, a, out);
+    PP_CUDA(cudaLaunchKernel(b->k.scan, dim3(b->grid_scan), dim3(kBlock), a.scan_p, 0, s));
+    for (;;) {
+      PP_CUDA(cudaLaunchKernel(b->k.peel, dim3(b->grid_peel), dim3(kBlock), a.peel_p, b->smem_peel, s));
+      PP_CUDA(cudaLaunchKernel(b->k.filter, dim3(b->grid_filter), dim3(kBlock), a.filter_p, 0, s));
+      PP_CUDA(cudaLaunchKernel(round_end_kernel(), dim3(1), dim3(32), a.end_p, 0, s));
+      PP_CUDA(cudaMemcpyAsync(&b->h_ctl->more, &b->ctl->more, sizeof(u32), cudaMemcpyDeviceToHost, s));
+      PP_CUDA(cudaStreamSynchronize(s));
+      if (!b->h_ctl->more) break;
+    }
+  } else {
+    if (!b->exec || b->graph_out != out) {
+      pp_status st = build_graph(b, out);
+      if (st != PP_OK) return st;
+      b->graph_out = out;
+    }
+    PP_CUDA(cudaGraphLaunch(b->exec, s));
+  }
+  PP_CUDA(cudaMemcpyAsync(b->h_ctl, b->ctl, sizeof(DecodeCtl), cudaMemcpyDeviceToHost, s));
+  PP_CUDA(cudaMemcpyAsync(b->h_recovered, b->bc.recovered, n * sizeof(u64), cudaMemcpyDeviceToHost, s));
+  PP_CUDA(cudaMemcpyAsync(b->h_nonempty, b->bc.nonempty, n * sizeof(u64), cudaMemcpyDeviceToHost, s));
+  PP_CUDA(cudaMemcpyAsync(b->h_emptied, b->bc.emptied, n * sizeof(u64), cudaMemcpyDeviceToHost, s));
+  PP_CUDA(cudaMemcpyAsync(b->h_rounds, b->bc.rounds, n * sizeof(u32), cudaMemcpyDeviceToHost, s));
+  PP_CUDA(cudaMemcpyAsync(b->h_round_rec, b->bc.round_rec, (size_t)n * sr * sizeof(u32),
+                          cudaMemcpyDeviceToHost, s));
+  PP_CUDA(cudaStreamSynchronize(s));
+  for (uint32_t i = 0; i < n; ++i) {
+    pp_table_result &r = results[i];
+    r.rounds = b->h_rounds[i];
+    r.recovered = b->h_recovered[i];
+    r.items_before = b->items[i];
+    r.residual_cells = b->h_nonempty[i] - b->h_emptied[i];
+    const uint32_t nc = r.rounds < r.round_cap ? r.rounds : r.round_cap;
+    if (r.recovered_per_round) {
+      for (uint32_t t = 0; t < nc; ++t)
+        r.recovered_per_round[t] = t < sr ? b->h_round_rec[(size_t)i * sr + t] : 0;
+    }
+    r.stats_complete = r.rounds <= sr;
+    b->items[i] -= r.recovered <= b->items[i] ? r.recovered : b->items[i];
+  }
+  if (b->h_ctl->flags & FLAG_CAPACITY) return fail(PP_ERR_CAPACITY, "pp_batch_decode: output overflow");
+  if (b->h_ctl->flags & FLAG_INTERNAL)
+    return fail(PP_ERR_INVALID_ARG, "pp_batch_decode: a pure cell's key does not hash to it");
+  if (b->h_ctl->flags & FLAG_ROUND_LIMIT)
+    return fail(PP_ERR_ROUND_LIMIT, "pp_batch_decode: stopped after max_rounds=%u rounds", b->opt.max_rounds);
+  return PP_OK;
+}
+
+pp_status pp_batch_copy_cells(pp_batch *b, uint32_t table, void *dst, int to_host, void *stream) {
+  if (!b || !dst || table >= b->n_tables) return fail(PP_ERR_INVALID_ARG, "pp_batch_copy_cells: bad argument");
+  cudaStream_t s = as_stream(stream);
+  const TableArgs &t = b->h_tabs[table];
+  PP_CUDA(cudaMemcpyAsync(dst, b->cells + t.base, (size_t)t.n_cells * sizeof(Cell),
+                          to_host ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, s));
+  PP_CUDA(cudaStreamSynchronize(s));
+  return PP_OK;
+}
+
+pp_status pp_batch_info(const pp_batch *b, uint32_t *n_tables, uint64_t *total_cells, uint32_t *last_rounds) {
+  if (!b) return fail(PP_ERR_INVALID_ARG, "pp_batch_info: NULL batch");
+  if (n_tables) *n_tables = b->n_tables;
+  if (total_cells) *total_cells = b->total_cells;
+  if (last_rounds) *last_rounds = b->h_ctl ? b->h_ctl->round : 0;
+  return PP_OK;
+}
+
+}  // extern "C"

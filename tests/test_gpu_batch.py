@@ -1,0 +1,146 @@
+"""GPU parity of the batched decode: every table against the CPU oracle, and
+against a plain per-table decode on the GPU (identical output)."""
+import numpy as np
+import pytest
+
+import oracle
+import ppgen
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def ppb(ppeel_lib):
+    import paper_1302_7014_b300 as pp
+    import paper_1302_7014_b300.batch as batch
+    return pp, batch
+
+
+def _specs(count, seed, rs=(2, 3, 4, 5, 6), lo=5, hi=16, c_lo=0.3, c_hi=1.1):
+    rng = np.random.default_rng(seed)
+    specs = []
+    for i in range(count):
+        n = int(2 ** rng.uniform(lo, hi))
+        r = int(rng.choice(rs))
+        n = max(n, r)
+        c = float(rng.uniform(c_lo, c_hi))
+        specs.append((n, r, c, int(rng.integers(1, 2**62)), int(rng.integers(1, 2**62))))
+    return specs
+
+
+def run_batch(pp, batch_mod, specs, opts=None, out_slack=0):
+    n_cells = [s[0] for s in specs]
+    rs = [s[1] for s in specs]
+    seeds = [s[3] for s in specs]
+    keys = [ppgen.distinct_keys(ppgen.edges_from_c(s[2], s[0]), s[4]) for s in specs]
+    koff = np.concatenate([[0], np.cumsum([k.size for k in keys])]).astype(np.uint64)
+    allk = np.concatenate(keys) if koff[-1] else np.zeros(1, np.uint64)
+    b = batch_mod.Batch(n_cells, rs, seeds, opts)
+    dk = torch.from_numpy(allk.view(np.int64)).cuda()
+    b.insert(dk, koff)
+    ooff = np.concatenate([[0], np.cumsum([k.size + out_slack for k in keys])]).astype(np.uint64)
+    out = torch.full((max(1, int(ooff[-1])),), -1, dtype=torch.int64, device="cuda")
+    res = b.decode(out, ooff)
+    got = out.cpu().numpy().view(np.uint64)
+    return b, keys, ooff, res, got
+
+
+def check_against_oracle(specs, keys, ooff, res, got, b=None, cells_every=1):
+    for i, (n, r, c, seed, _) in enumerate(specs):
+        ot = oracle.IBLT(n, r, seed)
+        ot.insert(keys[i])
+        ores = ot.decode_rounds()
+        assert res.rounds[i] == ores["rounds"], i
+        assert res.recovered[i] == sum(k.size for k in ores["keys"]), i
+        assert res.residual_cells[i] == ot.residual_cells(), i
+        assert res.stats_complete[i]
+        assert res.recovered_per_round[i] == [k.size for k in ores["keys"]], i
+        region = got[int(ooff[i]): int(ooff[i]) + int(res.recovered[i])]
+        ends = np.cumsum([0] + [k.size for k in ores["keys"]])
+        for t, k in enumerate(ores["keys"]):
+            assert (np.sort(region[ends[t]:ends[t + 1]]) == np.sort(k)).all(), (i, t)
+        if b is not None and i % cells_every == 0:
+            cells = b.cells(i)
+            assert (cells["count"].astype(np.int64) == ot.count).all(), i
+            assert (cells["key_xor"] == ot.keyx).all() and (cells["chk_xor"] == ot.chkx).all(), i
+
+
+def test_mixed_ranks(ppb):
+    pp, bm = ppb
+    specs = _specs(60, 1)
+    b, keys, ooff, res, got = run_batch(pp, bm, specs)
+    check_against_oracle(specs, keys, ooff, res, got, b)
+
+
+@pytest.mark.parametrize("r", [3, 4])
+def test_uniform_rank(ppb, r):
+    pp, bm = ppb
+    specs = _specs(40, 10 + r, rs=(r,), lo=8, hi=17, c_lo=0.5, c_hi=0.95)
+    b, keys, ooff, res, got = run_batch(pp, bm, specs, out_slack=3)
+    check_against_oracle(specs, keys, ooff, res, got, b, cells_every=4)
+
+
+def test_host_loop_and_small_grid(ppb):
+    pp, bm = ppb
+    specs = _specs(30, 3)
+    for opts in (pp.options(host_loop=1), pp.options(ctas_per_sm=1)):
+        b, keys, ooff, res, got = run_batch(pp, bm, specs, opts)
+        check_against_oracle(specs, keys, ooff, res, got)
+
+
+def test_batched_workload_prefix_matches_plain(ppb):
+    # the first 300 tables of the 4096-table recipe: batch == plain per-table decode
+    pp, bm = ppb
+    tabs = ppgen.batch_tables(4096)[:300]
+    specs = [(t.n_cells, t.r, t.c, t.table_seed, t.key_seed) for t in tabs]
+    b, keys, ooff, res, got = run_batch(pp, bm, specs)
+    for i, (n, r, c, seed, _) in enumerate(specs):
+        t = pp.IBLT(n, r, seed)
+        t.insert(torch.from_numpy(keys[i].view(np.int64)).cuda())
+        out = torch.zeros(max(1, keys[i].size), dtype=torch.int64, device="cuda")
+        pr = t.decode(out)
+        assert pr.rounds == res.rounds[i] and pr.recovered == res.recovered[i]
+        assert pr.recovered_per_round == res.recovered_per_round[i]
+        assert pr.residual_cells == res.residual_cells[i]
+        mine = got[int(ooff[i]): int(ooff[i]) + pr.recovered]
+        theirs = out[: pr.recovered].cpu().numpy().view(np.uint64)
+        ends = np.cumsum([0] + pr.recovered_per_round)
+        for a0, a1 in zip(ends[:-1], ends[1:]):
+            assert (np.sort(mine[a0:a1]) == np.sort(theirs[a0:a1])).all()
+        t.close()
+    # and a sample against the oracle
+    for i in range(0, 300, 7):
+        n, r, c, seed, _ = specs[i]
+        ot = oracle.IBLT(n, r, seed)
+        ot.insert(keys[i])
+        ores = ot.decode_rounds()
+        assert res.recovered_per_round[i] == [k.size for k in ores["keys"]]
+
+
+def test_capacity_and_reuse(ppb):
+    pp, bm = ppb
+    specs = _specs(8, 5, lo=8, hi=12)
+    b, keys, ooff, res, got = run_batch(pp, bm, specs)
+    # re-insert, decode into a different buffer with one table short of room
+    koff = np.concatenate([[0], np.cumsum([k.size for k in keys])]).astype(np.uint64)
+    b.clear()
+    b.insert(torch.from_numpy(np.concatenate(keys).view(np.int64)).cuda(), koff)
+    short = ooff.copy()
+    short[3:] -= 1
+    out2 = torch.zeros(int(ooff[-1]), dtype=torch.int64, device="cuda")
+    with pytest.raises(pp.PPError) as ei:
+        b.decode(out2, short)
+    assert ei.value.name == "PP_ERR_CAPACITY"
+    res2 = b.decode(out2, ooff)   # a new output buffer: the graph is rebuilt
+    got2 = out2.cpu().numpy().view(np.uint64)
+    check_against_oracle(specs, keys, ooff, res2, got2)
+
+
+def test_empty_tables_in_batch(ppb):
+    pp, bm = ppb
+    specs = [(100, 3, 0.0, 1, 2), (257, 4, 0.5, 3, 4), (64, 3, 0.0, 5, 6)]
+    b, keys, ooff, res, got = run_batch(pp, bm, specs)
+    check_against_oracle(specs, keys, ooff, res, got, b)
+    assert res.rounds[0] == 0 and res.rounds[2] == 0
