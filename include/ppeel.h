@@ -257,6 +257,88 @@ pp_status pp_batch_info(const pp_batch *b, uint32_t *n_tables, uint64_t *total_c
                         uint32_t *last_rounds);
 
 /* ------------------------------------------------------------------------
+ * Decode service with continuous batching.
+ *
+ * A host thread owns device arenas of cells and keys.  Submitted requests
+ * wait in FIFO order until their table (n_cells cells) and keys (m slots) fit
+ * in the free arena space and a table slot is free (admission by free HBM).
+ * The thread then runs device iterations, each one round of the
+ * round-synchronous decode (Sec. 1 at k = 2 on the IBLT of Sec. 6) for every
+ * admitted table at once; tables admitted since the previous iteration are
+ * built and scanned in it and join the others at the next round boundary.
+ * A request completes when its table has no pure cell left; each result equals
+ * that of decoding the request alone with pp_iblt_decode.
+ * ------------------------------------------------------------------------ */
+typedef struct pp_server pp_server;
+
+typedef struct pp_server_config {
+  uint64_t arena_cells; /* cells shared by all admitted tables (default 2^26) */
+  uint64_t arena_keys;  /* key/output slots shared by admitted requests (default 2^26) */
+  uint32_t max_slots;   /* tables on the device at once (default 4096) */
+  uint32_t max_queue;   /* waiting requests before submit returns BUSY (default 2^20) */
+  uint32_t r;           /* 0 = any r; 3 or 4 = only that r (specialised kernels) */
+  int32_t device;       /* CUDA device of the server thread (default 0) */
+} pp_server_config;
+
+/* One decode request.  The table is built from m keys: either h_keys (host
+ * memory, kept alive by the caller until the request completes) or, when
+ * h_keys is NULL, the synthetic keys SplitMix64(key_seed) outputs 1..m.  The
+ * table uses r and table_seed as in pp_iblt_create.  If h_out is not NULL the
+ * recovered keys are copied there (out_cap >= m entries) before completion. */
+typedef struct pp_request {
+  uint64_t n_cells;
+  uint32_t r;
+  uint32_t pad;
+  uint64_t table_seed;
+  uint64_t m;
+  uint64_t key_seed;
+  const uint64_t *h_keys;
+  uint64_t *h_out;
+  uint64_t out_cap;
+  double arrival_s;     /* arrival on pp_server_now()'s clock; 0 = time of submit */
+} pp_request;
+
+typedef struct pp_request_result {
+  uint64_t ticket;
+  int32_t status;       /* PP_OK, or PP_ERR_TIMEOUT if cancelled by a non-draining stop */
+  uint32_t rounds;      /* rounds that recovered >= 1 key */
+  uint64_t recovered;
+  uint64_t items_before;
+  uint64_t residual_cells;
+  double arrival_s, admit_s, done_s;  /* latency = done_s - arrival_s */
+} pp_request_result;
+
+typedef struct pp_server_stats {
+  uint64_t submitted, admitted, completed, rejected, pending, active, iterations, keys_recovered;
+} pp_server_stats;
+
+/* Monotonic clock (seconds) used for arrival and completion times. */
+double pp_server_now(void);
+
+void pp_server_config_default(pp_server_config *cfg);
+
+/* Allocates the arenas and starts the server thread. */
+pp_status pp_server_start(pp_server **out, const pp_server_config *cfg, const pp_options *opt);
+
+/* Queues a request (thread-safe).  INVALID_ARG for an r or size the server
+ * cannot serve, CAPACITY if it can never fit in the arenas, BUSY if the queue
+ * is full or the server is stopping. */
+pp_status pp_server_submit(pp_server *s, const pp_request *req, uint64_t *ticket);
+
+/* Non-blocking: PP_OK and *res if the request finished (the ticket is then
+ * released), PP_ERR_BUSY if not yet, PP_ERR_NOT_FOUND for an unknown ticket. */
+pp_status pp_server_poll(pp_server *s, uint64_t ticket, pp_request_result *res);
+
+/* Waits up to timeout_s seconds; PP_ERR_TIMEOUT if the request is not done by then. */
+pp_status pp_server_wait(pp_server *s, uint64_t ticket, double timeout_s, pp_request_result *res);
+
+pp_status pp_server_get_stats(pp_server *s, pp_server_stats *out);
+
+/* Stops the thread (drain != 0: finish every queued and admitted request
+ * first) and frees the server. */
+pp_status pp_server_stop(pp_server *s, int drain);
+
+/* ------------------------------------------------------------------------
  * IBLT decode that allocates nothing.  The paper has no counterpart: this is
  * a convenience for callers that may not allocate device memory while they
  * run -- for instance under a host framework that has already reserved nearly

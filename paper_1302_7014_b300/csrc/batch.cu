@@ -113,11 +113,11 @@ struct BatchArgs {
   RoundStats st;
   int set_cond;
   cudaGraphConditionalHandle cond;
-  void *scan_p[11], *peel_p[12], *filter_p[10], *end_p[4];
+  void *scan_p[11], *peel_p[12], *filter_p[11], *end_p[4];
   void bind() {
     void *s[11] = {&cells, &tab0, &tabs, &chunks, &n_chunks, &fkey, &fcell, &ftab, &bitmap, &ctl, &bc};
     void *p[12] = {&cells, &tab0, &tabs, &fkey_c, &fcell_c, &ftab_c, &bitmap_c, &cand, &ctab, &bout, &ctl, &bc};
-    void *f[10] = {&cells_c, &tab0, &tabs, &cand_c, &ctab_c, &fkey, &fcell, &ftab, &bitmap, &ctl};
+    void *f[11] = {&cells_c, &tab0, &tabs, &cand_c, &ctab_c, &fkey, &fcell, &ftab, &bitmap, &ctl, &bc};
     void *e[4] = {&ctl, &st, &set_cond, &cond};
     memcpy(scan_p, s, sizeof s);
     memcpy(peel_p, p, sizeof p);

@@ -60,6 +60,7 @@ void make_table_args(TableArgs &a, uint64_t n_cells, uint32_t r, uint64_t seed, 
   a.base = base;
   a.n_cells = (uint32_t)n_cells;
   a.r = r;
+  a.start_round = 1;
 }
 
 int persistent_grid(const void *fn, int block, size_t smem, uint32_t ctas_per_sm) {

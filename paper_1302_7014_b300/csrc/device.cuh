@@ -47,6 +47,7 @@ struct __align__(16) TableArgs {
   u32 base;                // global id of cell 0 (a multiple of 32)
   u32 n_cells;
   u32 r;
+  u32 start_round;         // global round that is this table's round 1 (batch/server)
   u64 out_base;            // batch: first slot of this table's output region
   u64 out_cap;             // batch: slots in that region
 };

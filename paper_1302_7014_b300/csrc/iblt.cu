@@ -131,9 +131,10 @@ struct FilterArgs {
   u32 *ftab;
   u32 *bitmap;
   DecodeCtl *ctl;
-  void *p[10];
+  BatchCounters bc;
+  void *p[11];
   void bind() {
-    void *q[10] = {&cells, &tab0, &tabs, &cand, &ctab, &fkey, &fcell, &ftab, &bitmap, &ctl};
+    void *q[11] = {&cells, &tab0, &tabs, &cand, &ctab, &fkey, &fcell, &ftab, &bitmap, &ctl, &bc};
     memcpy(p, q, sizeof q);
   }
 };
@@ -158,7 +159,7 @@ void fill_args(pp_iblt *t, ScanArgs &sa, PeelArgs &pa, FilterArgs &fa, EndArgs &
   pa = PeelArgs{t->cells, t->args, nullptr, t->fkey, t->fcell, nullptr, t->bitmap, t->cand,
                 nullptr, nullptr, t->ctl, bc, {}};
   fa = FilterArgs{t->cells, t->args, nullptr, t->cand, nullptr, t->fkey, t->fcell, nullptr,
-                  t->bitmap, t->ctl, {}};
+                  t->bitmap, t->ctl, bc, {}};
   ea = EndArgs{t->ctl, RoundStats{t->st_rec, t->st_alive, t->st_front}, 0, 0, {}};
   sa.bind();
   pa.bind();

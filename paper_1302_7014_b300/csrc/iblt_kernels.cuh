@@ -145,6 +145,7 @@ __global__ void __launch_bounds__(kBlock) k_scan(const Cell *__restrict__ cells,
     if (BATCH) {
       const u64 ne = block_sum<u64, kBlock>(c_nonempty, s_red);
       if (tid == 0 && ne) atomicAdd(bc.nonempty + table, ne);
+      if (tid == 0 && n && bc.live) atomicAdd(bc.live + table, n);
     }
     __syncthreads();
     const u32 base = s_base;
@@ -261,10 +262,11 @@ __global__ void __launch_bounds__(kBlock) k_peel(Cell *__restrict__ cells, const
         const u32 gempty = __reduce_add_sync(grp, n_empty);
         u64 base = 0;
         if (win && (int)lane_id() == leader) {
+          const u32 local = round + 1 - T.start_round;  // this table's own round number
           base = atomicAdd(bc.recovered + tb, (u64)gsize);
           if (gempty) atomicAdd(bc.emptied + tb, (u64)gempty);
-          atomicMax(bc.rounds + tb, round);
-          if (round <= stats_rounds) atomicAdd(bc.round_rec + (u64)tb * stats_rounds + (round - 1), gsize);
+          atomicMax(bc.rounds + tb, local);
+          if (local <= stats_rounds) atomicAdd(bc.round_rec + (u64)tb * stats_rounds + (local - 1), gsize);
         }
         base = __shfl_sync(kFull, base, leader);
         if (win) {
@@ -323,7 +325,7 @@ __global__ void __launch_bounds__(kBlock) k_filter(const Cell *__restrict__ cell
                                                    const u32 *__restrict__ cand, const u32 *__restrict__ ctab,
                                                    u64 *__restrict__ fkey, u32 *__restrict__ fcell,
                                                    u32 *__restrict__ ftab, u32 *__restrict__ bitmap,
-                                                   DecodeCtl *__restrict__ ctl) {
+                                                   DecodeCtl *__restrict__ ctl, BatchCounters bc) {
   constexpr int CH = kBlock * kFilterItems;
   __shared__ u64 s_key[CH];
   __shared__ u32 s_cell[CH];
@@ -358,6 +360,10 @@ __global__ void __launch_bounds__(kBlock) k_filter(const Cell *__restrict__ cell
         s_cell[p] = c;
         if (BATCH) s_tab[p] = tb;
       }
+      if (BATCH && bc.live) {
+        const u32 grp = __match_any_sync(kFull, pure ? tb : 0xffffffffu);
+        if (pure && (int)lane_id() == __ffs(grp) - 1) atomicAdd(bc.live + tb, (u32)__popc(grp));
+      }
     }
     __syncthreads();
     const u32 nn = s_n;
@@ -386,7 +392,7 @@ __global__ void k_round_end(DecodeCtl *__restrict__ ctl, RoundStats st, int set_
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   DecodeCtl &c = *ctl;
   const u32 t = c.round;
-  if (c.n_front > 0 && t > 0) {
+  if (c.n_front > 0 && t > 0 && st.recovered) {
     // round t just finished
     st.recovered[t - 1] = c.n_out - c.out_round_start;
     st.alive[t - 1] = c.alive;

@@ -155,7 +155,7 @@ extern "C" pp_status pp_iblt_decode_noalloc(pp_cell *d_cells, uint64_t n_cells, 
                        &bitmap, &ctl, &bc};
   void *peel_args[] = {&cells, &tab0, &no_tabs, &fkey, &fcell, &no_u32, &bitmap, &cand, &no_u32,
                        &no_u64, &ctl, &bc};
-  void *filter_args[] = {&cells, &tab0, &no_tabs, &cand, &no_u32, &fkey, &fcell, &no_u32, &bitmap, &ctl};
+  void *filter_args[] = {&cells, &tab0, &no_tabs, &cand, &no_u32, &fkey, &fcell, &no_u32, &bitmap, &ctl, &bc};
   RoundStats rs{st_rec, st_alive, st_front};
   int set_cond = 0;
   cudaGraphConditionalHandle no_cond = 0;

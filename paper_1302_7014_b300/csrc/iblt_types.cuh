@@ -43,6 +43,7 @@ struct BatchCounters {
   u64 *emptied;        // per table: cells emptied during the decode
   u32 *rounds;         // per table: last round that recovered a key
   u32 *round_rec;      // per table x stats_rounds: keys recovered per round
+  u32 *live;           // per table: entries it has in the frontier being built (or NULL)
 };
 
 // A contiguous range of one table's cells or keys.
