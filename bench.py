@@ -183,6 +183,123 @@ def run_reference(args, cfg):
     print(json.dumps(line), flush=True)
 
 
+def bench_batched(pp, torch, args):
+    """4096 IBLTs (cells log-uniform in [2^8, 2^20), r in {3, 4}, load uniform in
+    [0.5, 0.9 c*]): one batched graph launch vs a loop of plain per-table decodes,
+    same tables, same keys, identical output."""
+    import paper_1302_7014_b300.batch as pb
+    tabs = ppgen.batch_tables(4096)
+    keys = [t.keys() for t in tabs]
+    koff = np.concatenate([[0], np.cumsum([k.size for k in keys])]).astype(np.uint64)
+    total_keys = int(koff[-1])
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        dkeys = torch.from_numpy(np.concatenate(keys).view(np.int64)).cuda()
+        out = torch.empty(total_keys, dtype=torch.int64, device="cuda")
+    stream.synchronize()
+    b = pb.Batch([t.n_cells for t in tabs], [t.r for t in tabs], [t.table_seed for t in tabs])
+
+    def bstep():
+        b.clear(stream)
+        b.insert(dkeys, koff, stream)
+        return b.decode(out, koff, stream=stream)
+
+    for _ in range(max(2, args.warmup)):
+        res = bstep()
+    steps = max(3, min(args.steps, 10))
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    rec = 0
+    for _ in range(steps):
+        res = bstep()
+        rec += int(res.recovered.sum())
+    e1.record(stream)
+    stream.synchronize()
+    b_ms = e0.elapsed_time(e1) / steps
+    b_rounds = int(res.rounds.max())
+    b_rec = res.recovered.copy()
+    b.close()
+    del out
+    torch.cuda.empty_cache()
+    # plain loop: one handle per table, created before timing
+    handles = [pp.IBLT(t.n_cells, t.r, t.table_seed) for t in tabs]
+    with torch.cuda.stream(stream):
+        out = torch.empty(total_keys, dtype=torch.int64, device="cuda")
+    stream.synchronize()
+    views = [(dkeys[int(koff[i]):int(koff[i + 1])], out[int(koff[i]):int(koff[i + 1])] if koff[i + 1] > koff[i]
+              else out[:1]) for i in range(len(tabs))]
+
+    def pstep():
+        got = []
+        for h, (kv, ov) in zip(handles, views):
+            h.clear(stream)
+            h.insert(kv, stream)
+            got.append(h.decode(ov, stream=stream).recovered)
+        return got
+
+    pstep()
+    torch.cuda.synchronize()
+    psteps = 2
+    e0.record(stream)
+    for _ in range(psteps):
+        got = pstep()
+    e1.record(stream)
+    stream.synchronize()
+    p_ms = e0.elapsed_time(e1) / psteps
+    identical = bool((np.array(got) == b_rec).all())
+    for h in handles:
+        h.close()
+    del out, dkeys
+    torch.cuda.empty_cache()
+    n = len(tabs)
+    return {"workload": "4096 IBLTs, cells log-uniform [2^8,2^20), r in {3,4}, load U[0.5, 0.9 c*]",
+            "tables": n, "cells": int(sum(t.n_cells for t in tabs)), "keys": total_keys,
+            "batched_ms": b_ms, "plain_loop_ms": p_ms,
+            "batched_tables_per_s": n / (b_ms * 1e-3), "plain_tables_per_s": n / (p_ms * 1e-3),
+            "batched_keys_per_s": rec / steps / (b_ms * 1e-3), "speedup": p_ms / b_ms,
+            "rounds_max": b_rounds, "identical_output": identical,
+            "step": "clear + insert + decode of every table"}
+
+
+def bench_served(pp, torch, args):
+    """Open-loop Poisson arrivals (mean 20k req/s) of decode requests, cells
+    log-uniform in [2^10, 2^22), r = 3, load U[0.6, 0.8]; keys generated on the
+    device from each request's seed.  Latency = completion - scheduled arrival."""
+    import paper_1302_7014_b300.server as ps
+    rate = 20000.0
+    n_req = max(1, int(rate * args.serve_seconds))
+    reqs = ppgen.serving_requests(n_req, rate_per_s=rate)
+    srv = ps.Server(arena_cells=1 << 29, arena_keys=1 << 29, max_slots=8192, r=3)
+    # warm up the kernels
+    for at, spec in reqs[:4]:
+        srv.wait(srv.submit(spec.n_cells, 3, spec.table_seed, spec.m, key_seed=spec.key_seed), 120.0)
+    t0 = ps.server_now() + 0.01
+    tickets = []
+    for at, spec in reqs:
+        while ps.server_now() < t0 + at:
+            pass
+        tickets.append(srv.submit(spec.n_cells, 3, spec.table_seed, spec.m, key_seed=spec.key_seed,
+                                  arrival_s=t0 + at))
+    lat, keys, last = [], 0, t0
+    for t in tickets:
+        r = srv.wait(t, 600.0)
+        lat.append(r["done_s"] - r["arrival_s"])
+        keys += r["recovered"]
+        last = max(last, r["done_s"])
+    st = srv.stats()
+    srv.stop()
+    span = last - t0
+    lat = np.array(lat)
+    served_rate = n_req / span
+    return {"workload": "Poisson 20k req/s, cells log-uniform [2^10,2^22), r=3, load U[0.6,0.8]",
+            "requests": n_req, "arrival_window_s": args.serve_seconds, "span_s": span,
+            "p50_ms": float(np.percentile(lat, 50) * 1e3), "p99_ms": float(np.percentile(lat, 99) * 1e3),
+            "keys_per_s": keys / span, "requests_per_s": served_rate,
+            "offered_req_per_s": rate, "saturated": bool(served_rate < 0.95 * rate),
+            "iterations": st["iterations"], "keys_source": "generated on the device from request seeds"}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -191,6 +308,10 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="skip the batched (4096 tables) and served (Poisson arrivals) sections")
+    ap.add_argument("--serve-seconds", type=float, default=0.5,
+                    help="arrival window of the served section")
     ap.add_argument("--host-loop", action="store_true",
                     help="drive rounds from the host (kernels launched one by one, as profilers need)")
     ap.add_argument("--cells-log2", type=int, default=26,
@@ -325,6 +446,15 @@ def main():
                 "kernel": dk["kernel"], "peak_source": f"{peak_kind} hbm_gbs",
                 "model": "sector floor: 32 B/cell scan + (64r+8) B/key decode; (8+64r) B/key build"}
 
+    batched = served = None
+    if world == 1 and not args.no_extra:
+        table.close()
+        torch.cuda.empty_cache()
+        del dkeys, out
+        batched = bench_batched(pp, torch, args)
+        torch.cuda.empty_cache()
+        served = bench_served(pp, torch, args)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         try:
@@ -343,9 +473,11 @@ def main():
                 "build_ms": b_ms, "decode_ms": d_ms, "peel_ms": d_ms,
                 "decode_keys_per_s": m / (d_ms * 1e-3),
                 "kernels": kernels, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+                "batched": batched, "served": served,
                 "gpu_launches": args.steps * (2 + 3 * (rounds + 1)), "clocks": clk}
         print(json.dumps(line), flush=True)
-    table.close()
+    if batched is None:
+        table.close()
     if dist is not None:
         dist.destroy_process_group()
 
