@@ -14,11 +14,12 @@ seeded input generators in ``ppgen``.
 * ``brute.py``: brute-force k-core and a set-by-set round simulator for tiny
   hypergraphs (pins for the C code).
 
-Parity notes: the hash/checksum convention and the split of n cells into r
+Parity unpinned: the IBLT cell map and the split of n cells into r
 sub-tables are conventions the paper leaves open (it asks only for r hash
-functions and 'some simple pseudorandom function'); they are fixed in
-``peel_oracle.c`` and pinned by the known-answer file
-``tests/golden/hash_kat.txt``, which the CUDA side must reproduce.
+functions and 'some simple pseudorandom function').  They are fixed in
+``peel_oracle.c`` and frozen by the known-answer file
+``tests/golden/hash_kat.txt``, which the CUDA side must reproduce; only the
+mix64 finaliser inside them is pinned to a published vector.
 """
 from __future__ import annotations
 

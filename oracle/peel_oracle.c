@@ -19,7 +19,9 @@
  *   - sequential queue k-core peeler (Sec. 1: the core is unique and does not
  *     depend on the removal order).
  *
- * Conventions the paper leaves open (stated, not derived):
+ * Conventions the paper leaves open (stated, not derived; parity unpinned for
+ * the cell map and the sub-table split, which only the known-answer file
+ * freezes):
  *   - mix64 is the SplitMix64 output finaliser (Steele, Lea & Flood 2014);
  *     hash seed j (j = 0..r-1) and the checksum seed (index r) are outputs
  *     1..r+1 of SplitMix64 started at the table seed;
