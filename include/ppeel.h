@@ -61,7 +61,9 @@ typedef struct pp_options {
                             0 (default) = one CUDA graph whose while-node keeps
                             looping on the device until the frontier is empty */
   uint32_t stats_rounds; /* batch: per-table per-round counters kept (default 128) */
-  uint32_t reserved[3];
+  uint32_t binned;       /* IBLT build/insert: 0 = slab-binned when the table is at least
+                            2^23 cells (default), 1 = always binned, 2 = never */
+  uint32_t reserved[2];
 } pp_options;
 
 /* Fills *opt with the defaults above. */
@@ -141,6 +143,12 @@ pp_status pp_iblt_insert(pp_iblt *t, const uint64_t *d_keys, uint64_t m, void *s
 /* Deletes m keys: the same XORs with count -1 (Sec. 6: insertion and deletion
  * are identical XOR operations). */
 pp_status pp_iblt_delete(pp_iblt *t, const uint64_t *d_keys, uint64_t m, void *stream);
+
+/* Builds the table from scratch: the result equals pp_iblt_clear followed by
+ * pp_iblt_insert.  Large tables are built slab by slab (2^21 cells at a time),
+ * each slab zero-filled and updated while it sits in L2.  Synchronizes
+ * `stream` once (after sorting the keys' updates into slabs). */
+pp_status pp_iblt_build(pp_iblt *t, const uint64_t *d_keys, uint64_t m, void *stream);
 
 /* Round-synchronous recovery (Sec. 6 recovery; Sec. 1 rounds at k = 2).
  * Round t recovers every key that is alone in some cell at the start of round

@@ -19,7 +19,7 @@ from dataclasses import dataclass, field
 from . import _lib
 from ._lib import PP_MAX_R, Cell, DecodeResult, Options, PeelResult
 
-__all__ = ["PPError", "IBLT", "iblt_create", "iblt_insert", "iblt_delete", "iblt_decode",
+__all__ = ["PPError", "IBLT", "iblt_create", "iblt_insert", "iblt_delete", "iblt_build", "iblt_decode",
            "peel_kcore", "options", "PP_MAX_R"]
 
 
@@ -123,6 +123,11 @@ class IBLT:
         _check(_lib.load().pp_iblt_delete(self._h, _dev_ptr(keys, 8, "keys"), keys.numel(),
                                           _stream_ptr(stream)), "pp_iblt_delete")
 
+    def build(self, keys, stream=None):
+        """Clear the table and insert ``keys`` (one call, built slab by slab when large)."""
+        _check(_lib.load().pp_iblt_build(self._h, _dev_ptr(keys, 8, "keys"), keys.numel(),
+                                         _stream_ptr(stream)), "pp_iblt_build")
+
     def decode(self, out, round_cap: int = 4096, stream=None) -> DecodeOutcome:
         """Decode in place; ``out`` (CUDA, 8-byte elements) receives the keys."""
         rec = (ctypes.c_uint64 * round_cap)()
@@ -170,6 +175,10 @@ def iblt_insert(table: IBLT, keys, stream=None) -> None:
 
 def iblt_delete(table: IBLT, keys, stream=None) -> None:
     table.delete(keys, stream)
+
+
+def iblt_build(table: IBLT, keys, stream=None) -> None:
+    table.build(keys, stream)
 
 
 def iblt_decode(table: IBLT, out, round_cap: int = 4096, stream=None) -> DecodeOutcome:

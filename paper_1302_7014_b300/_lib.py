@@ -22,7 +22,7 @@ u32, u64, i32, vp = ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int32, ctypes.c_v
 
 class Options(ctypes.Structure):
     _fields_ = [("block", u32), ("ctas_per_sm", u32), ("max_rounds", u32), ("host_loop", u32),
-                ("stats_rounds", u32), ("reserved", u32 * 3)]
+                ("stats_rounds", u32), ("binned", u32), ("reserved", u32 * 2)]
 
 
 class DecodeResult(ctypes.Structure):
@@ -52,6 +52,7 @@ _SIGNATURES = {
     "pp_iblt_clear": (ctypes.c_int, [vp, vp]),
     "pp_iblt_insert": (ctypes.c_int, [vp, vp, u64, vp]),
     "pp_iblt_delete": (ctypes.c_int, [vp, vp, u64, vp]),
+    "pp_iblt_build": (ctypes.c_int, [vp, vp, u64, vp]),
     "pp_iblt_decode": (ctypes.c_int, [vp, vp, u64, ctypes.POINTER(DecodeResult), vp]),
     "pp_iblt_copy_cells": (ctypes.c_int, [vp, vp, u64, u64, ctypes.c_int, vp]),
     "pp_iblt_info": (ctypes.c_int, [vp, ctypes.POINTER(u64), ctypes.POINTER(u32), ctypes.POINTER(u64)]),

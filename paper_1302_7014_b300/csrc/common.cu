@@ -47,6 +47,7 @@ pp_options resolve_options(const pp_options *opt) {
     if (opt->max_rounds) o.max_rounds = opt->max_rounds;
     o.host_loop = opt->host_loop;
     if (opt->stats_rounds) o.stats_rounds = opt->stats_rounds;
+    o.binned = opt->binned;
   }
   return o;
 }

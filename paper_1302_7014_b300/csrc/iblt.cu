@@ -9,6 +9,7 @@
 #include <string.h>
 
 #include "host.cuh"
+#include "iblt_binned.cuh"
 #include "iblt_kernels.cuh"
 
 using namespace pp;
@@ -17,8 +18,16 @@ namespace pp {
 
 template <int R, bool B>
 static IbltKernels iblt_kernels_t() {
+  static bool attr_set = false;
+  if (!attr_set) {
+    // the binning kernel's staging grows with r and the number of slabs
+    cudaFuncSetAttribute((const void *)k_bin<R, B>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         200 * 1024);
+    attr_set = true;
+  }
   return {(const void *)k_insert<R, B>, (const void *)k_scan<R, B>, (const void *)k_peel<R, B>,
-          (const void *)k_filter<R, B>, R ? R : PP_MAX_R};
+          (const void *)k_filter<R, B>, (const void *)k_bin<R, B>, (const void *)k_apply<R, B>,
+          R ? R : PP_MAX_R};
 }
 
 IbltKernels iblt_kernels(uint32_t r, bool batch) {
@@ -33,6 +42,11 @@ IbltKernels iblt_kernels(uint32_t r, bool batch) {
 }
 
 const void *round_end_kernel() { return (const void *)k_round_end; }
+
+size_t bin_smem_bytes(int nr, bool batch, uint32_t n_slabs) {
+  const size_t cap = (size_t)kBinKeys * nr;
+  return cap * (8 + 4 + 4 + (batch ? 4 : 0)) + 3 * (size_t)n_slabs * 4;
+}
 
 size_t peel_smem_bytes(int nr, bool batch) {
   const size_t ch = (size_t)kBlock * kPeelItems;
@@ -56,9 +70,14 @@ struct pp_iblt {
   u64 *h_rec = nullptr, *h_alive = nullptr;
   int64_t items = 0;
   IbltKernels k{};
-  int grid_scan = 0, grid_peel = 0, grid_filter = 0, grid_insert = 0;
-  size_t smem_peel = 0;
+  int grid_scan = 0, grid_peel = 0, grid_filter = 0, grid_insert = 0, grid_bin = 0, grid_apply = 0;
+  size_t smem_peel = 0, smem_bin = 0;
   cudaGraphExec_t exec = nullptr;
+  // slab-binned build workspace (allocated on first use, grown as needed)
+  uint32_t n_slabs = 0;
+  u64 *rec_key = nullptr;
+  u32 *rec_cell = nullptr, *bin_count = nullptr, *bin_overflow = nullptr;
+  uint64_t rec_cap_total = 0;
 };
 
 namespace {
@@ -78,6 +97,10 @@ void free_all(pp_iblt *t) {
   cudaFreeHost(t->h_ctl);
   cudaFreeHost(t->h_rec);
   cudaFreeHost(t->h_alive);
+  cudaFree(t->rec_key);
+  cudaFree(t->rec_cell);
+  cudaFree(t->bin_count);
+  cudaFree(t->bin_overflow);
   delete t;
 }
 
@@ -259,6 +282,83 @@ pp_status launch_insert(pp_iblt *t, const uint64_t *d_keys, uint64_t m, int sign
   return PP_OK;
 }
 
+bool use_binned(const pp_iblt *t, uint64_t m) {
+  if (m == 0 || t->opt.binned == 2) return false;
+  if (t->opt.binned == 1) return true;
+  return t->n >= (1ull << 23) && m * t->r >= t->n / 4;
+}
+
+// Pass 1 of a binned build: route every (cell, key) update into its slab's list.
+pp_status bin_pass(pp_iblt *t, const uint64_t *d_keys, uint64_t m, int sign, int direct_overflow,
+                   cudaStream_t s, BinArgs &ba) {
+  const uint32_t ns = (uint32_t)((t->n + kSlabCells - 1) / kSlabCells);
+  // updates are uniform over the cells: expected count per slab plus slack
+  const double per = (double)m * t->r * ((double)kSlabCells / (double)t->n);
+  const uint64_t cap = (uint64_t)(per * 1.05) + 4096;
+  if (cap > 0xFFFFFFF0ull) return fail(PP_ERR_INVALID_ARG, "pp_iblt_insert: too many keys for one call");
+  if (cap * ns > t->rec_cap_total || ns != t->n_slabs) {
+    PP_CUDA(cudaStreamSynchronize(s));
+    cudaFree(t->rec_key);
+    cudaFree(t->rec_cell);
+    cudaFree(t->bin_count);
+    cudaFree(t->bin_overflow);
+    t->rec_key = nullptr;
+    t->rec_cell = nullptr;
+    t->bin_count = nullptr;
+    t->bin_overflow = nullptr;
+    t->rec_cap_total = 0;
+    PP_CUDA(cudaMalloc((void **)&t->rec_key, cap * ns * sizeof(u64)));
+    PP_CUDA(cudaMalloc((void **)&t->rec_cell, cap * ns * sizeof(u32)));
+    PP_CUDA(cudaMalloc((void **)&t->bin_count, ns * sizeof(u32)));
+    PP_CUDA(cudaMalloc((void **)&t->bin_overflow, sizeof(u32)));
+    t->rec_cap_total = cap * ns;
+    t->n_slabs = ns;
+    t->smem_bin = bin_smem_bytes(t->k.nr, false, ns);
+    t->grid_bin = persistent_grid(t->k.bin, kBlock, t->smem_bin, t->opt.ctas_per_sm);
+  }
+  PP_CUDA(cudaMemsetAsync(t->bin_count, 0, ns * sizeof(u32), s));
+  PP_CUDA(cudaMemsetAsync(t->bin_overflow, 0, sizeof(u32), s));
+  ba = BinArgs{t->rec_key, t->rec_cell, nullptr, t->bin_count, t->bin_overflow, (u32)cap, ns, direct_overflow};
+  TableArgs a = t->args;
+  const TableArgs *tabs = nullptr;
+  const Chunk *chunks = nullptr;
+  u32 nch = 0;
+  Cell *cells = t->cells;
+  const u64 *keys = reinterpret_cast<const u64 *>(d_keys);
+  u64 mm = m;
+  void *args[] = {&cells, &a, &tabs, &chunks, &nch, &keys, &mm, &sign, &ba};
+  const u64 items = (m + kBinKeys - 1) / kBinKeys;
+  const int grid = (int)(items < (u64)t->grid_bin ? items : (u64)t->grid_bin);
+  PP_CUDA(cudaLaunchKernel(t->k.bin, dim3(grid), dim3(kBlock), args, t->smem_bin, s));
+  return PP_OK;
+}
+
+// Pass 2: slab by slab (zero-filled first when building from scratch).
+pp_status apply_pass(pp_iblt *t, BinArgs &ba, int sign, bool zero_fill, cudaStream_t s) {
+  TableArgs a = t->args;
+  const TableArgs *tabs = nullptr;
+  Cell *cells = t->cells;
+  u32 slab = 0;
+  void *args[] = {&cells, &a, &tabs, &ba, &slab, &sign};
+  for (slab = 0; slab < ba.n_slabs; ++slab) {
+    if (zero_fill) {
+      const uint64_t c0 = (uint64_t)slab * kSlabCells;
+      const uint64_t c1 = c0 + kSlabCells < t->n ? c0 + kSlabCells : t->n;
+      PP_CUDA(cudaMemsetAsync(t->cells + c0, 0, (c1 - c0) * sizeof(Cell), s));
+    }
+    PP_CUDA(cudaLaunchKernel(t->k.apply, dim3(t->grid_apply), dim3(kBlock), args, 0, s));
+  }
+  return PP_OK;
+}
+
+pp_status update(pp_iblt *t, const uint64_t *d_keys, uint64_t m, int sign, cudaStream_t s) {
+  if (!use_binned(t, m)) return launch_insert(t, d_keys, m, sign, s);
+  BinArgs ba;
+  pp_status st = bin_pass(t, d_keys, m, sign, 1, s, ba);
+  if (st != PP_OK) return st;
+  return apply_pass(t, ba, sign, false, s);
+}
+
 }  // namespace
 
 extern "C" {
@@ -310,6 +410,7 @@ pp_status pp_iblt_create(pp_iblt **out, uint64_t n_cells, uint32_t r, uint64_t s
   t->grid_peel = persistent_grid(t->k.peel, kBlock, t->smem_peel, t->opt.ctas_per_sm);
   t->grid_filter = persistent_grid(t->k.filter, kBlock, 0, t->opt.ctas_per_sm);
   t->grid_insert = persistent_grid(t->k.insert, kBlock, 0, 8) * 4;
+  t->grid_apply = persistent_grid(t->k.apply, kBlock, 0, 8);
   *out = t;
   return PP_OK;
 }
@@ -331,7 +432,7 @@ pp_status pp_iblt_clear(pp_iblt *t, void *stream) {
 pp_status pp_iblt_insert(pp_iblt *t, const uint64_t *d_keys, uint64_t m, void *stream) {
   if (!t) return fail(PP_ERR_INVALID_ARG, "pp_iblt_insert: NULL table");
   if (m && !d_keys) return fail(PP_ERR_INVALID_ARG, "pp_iblt_insert: NULL keys");
-  pp_status st = launch_insert(t, d_keys, m, +1, as_stream(stream));
+  pp_status st = update(t, d_keys, m, +1, as_stream(stream));
   if (st == PP_OK) t->items += (int64_t)m;
   return st;
 }
@@ -339,8 +440,35 @@ pp_status pp_iblt_insert(pp_iblt *t, const uint64_t *d_keys, uint64_t m, void *s
 pp_status pp_iblt_delete(pp_iblt *t, const uint64_t *d_keys, uint64_t m, void *stream) {
   if (!t) return fail(PP_ERR_INVALID_ARG, "pp_iblt_delete: NULL table");
   if (m && !d_keys) return fail(PP_ERR_INVALID_ARG, "pp_iblt_delete: NULL keys");
-  pp_status st = launch_insert(t, d_keys, m, -1, as_stream(stream));
+  pp_status st = update(t, d_keys, m, -1, as_stream(stream));
   if (st == PP_OK) t->items -= (int64_t)m;
+  return st;
+}
+
+pp_status pp_iblt_build(pp_iblt *t, const uint64_t *d_keys, uint64_t m, void *stream) {
+  if (!t) return fail(PP_ERR_INVALID_ARG, "pp_iblt_build: NULL table");
+  if (m && !d_keys) return fail(PP_ERR_INVALID_ARG, "pp_iblt_build: NULL keys");
+  cudaStream_t s = as_stream(stream);
+  t->items = 0;
+  if (!use_binned(t, m)) {
+    PP_CUDA(cudaMemsetAsync(t->cells, 0, t->n * sizeof(Cell), s));
+    pp_status st = launch_insert(t, d_keys, m, +1, s);
+    if (st == PP_OK) t->items = (int64_t)m;
+    return st;
+  }
+  BinArgs ba;
+  pp_status st = bin_pass(t, d_keys, m, +1, 0, s, ba);
+  if (st != PP_OK) return st;
+  PP_CUDA(cudaMemcpyAsync(&t->h_ctl->more, t->bin_overflow, sizeof(u32), cudaMemcpyDeviceToHost, s));
+  PP_CUDA(cudaStreamSynchronize(s));
+  if (t->h_ctl->more) {
+    // a slab got more updates than its list holds: build the plain way
+    PP_CUDA(cudaMemsetAsync(t->cells, 0, t->n * sizeof(Cell), s));
+    st = launch_insert(t, d_keys, m, +1, s);
+  } else {
+    st = apply_pass(t, ba, +1, true, s);
+  }
+  if (st == PP_OK) t->items = (int64_t)m;
   return st;
 }
 

@@ -56,6 +56,7 @@ struct Chunk {
 // Entry points of one instantiation of the IBLT kernels (plain or batched).
 struct IbltKernels {
   const void *insert, *scan, *peel, *filter;
+  const void *bin, *apply;  // slab-binned build
   int nr;  // compile-time rank (PP_MAX_R for the generic instance)
 };
 
@@ -64,6 +65,9 @@ IbltKernels iblt_kernels(uint32_t r, bool batch);
 
 // Dynamic shared memory of the peel kernel.
 size_t peel_smem_bytes(int nr, bool batch);
+
+// Dynamic shared memory of the binning kernel for n_slabs slabs.
+size_t bin_smem_bytes(int nr, bool batch, uint32_t n_slabs);
 
 // The round_end kernel (one thread; records a round and decides on the next).
 const void *round_end_kernel();

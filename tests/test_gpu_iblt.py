@@ -224,3 +224,66 @@ def test_headline_full_size(pp):
     for t, (a, h) in enumerate(zip(rounds, gold["round_sha256"])):
         assert hashlib.sha256(a.tobytes()).hexdigest() == h, f"round {t + 1}"
     assert (np.sort(got) == np.sort(keys)).all()   # recovered set == inserted set
+
+
+@pytest.mark.parametrize("n,r,c", [(3 * (1 << 21) + 17, 3, 0.75), ((1 << 22) + 5, 4, 0.7), (5000, 3, 0.8),
+                                   (70001, 5, 0.6)])
+def test_binned_build_insert_delete(pp, n, r, c):
+    """The slab-binned update paths (forced on) against the oracle, cell for cell."""
+    seed = n + r
+    keys = ppgen.distinct_keys(ppgen.edges_from_c(c, n), seed + 1)
+    dk = _dev(keys)
+    # build from scratch (zero-filled slab by slab)
+    gt = pp.IBLT(n, r, seed, pp.options(binned=1))
+    gt.insert(_dev(ppgen.distinct_keys(1000, 5)))   # junk that build() must wipe
+    gt.build(dk)
+    ot = oracle.IBLT(n, r, seed)
+    ot.insert(keys)
+    _assert_cells_equal(gt.cells(), ot)
+    out = torch.zeros(keys.size, dtype=torch.int64, device="cuda")
+    res = gt.decode(out)
+    ores = ot.decode_rounds()
+    assert res.rounds == ores["rounds"] and res.recovered_per_round == [k.size for k in ores["keys"]]
+    _assert_cells_equal(gt.cells(), ot)
+    # incremental inserts and a delete on a non-empty table
+    gt.clear()
+    half = keys.size // 2
+    gt.insert(_dev(keys[:half]))
+    gt.insert(_dev(keys[half:]))
+    gt.delete(_dev(keys[::5]))
+    ot2 = oracle.IBLT(n, r, seed)
+    ot2.insert(keys)
+    ot2.insert(keys[::5], sign=-1)
+    _assert_cells_equal(gt.cells(), ot2)
+    gt.close()
+
+
+def test_build_without_binning_matches(pp):
+    n, r = 100000, 3
+    keys = ppgen.distinct_keys(70000, 3)
+    gt = pp.IBLT(n, r, 9, pp.options(binned=2))
+    gt.build(_dev(keys))
+    ot = oracle.IBLT(n, r, 9)
+    ot.insert(keys)
+    _assert_cells_equal(gt.cells(), ot)
+
+
+def test_headline_full_size_build(pp):
+    """The benchmark's step (build + decode) at 2^26 cells against the stored oracle trajectory."""
+    gold = json.load(open(os.path.join(GOLDEN, "full_size.json")))["iblt_headline"]
+    n, r, m = gold["n_cells"], gold["r"], gold["m"]
+    keys = ppgen.distinct_keys(m, gold["key_seed"])
+    gt = pp.IBLT(n, r, gold["table_seed"])
+    dkeys = _dev(keys)
+    out = torch.zeros(m, dtype=torch.int64, device="cuda")
+    for _ in range(2):                                    # twice: workspace reuse
+        gt.build(dkeys)
+        res = gt.decode(out)
+        assert res.rounds == gold["rounds"]
+        assert res.recovered_per_round == gold["recovered_per_round"]
+        assert res.alive_cells_per_round == gold["alive_cells_per_round"]
+        assert res.residual_cells == 0
+    got = out.cpu().numpy().view(np.uint64)
+    rounds = _split_rounds(got, res.recovered_per_round)
+    for t, (a, h) in enumerate(zip(rounds, gold["round_sha256"])):
+        assert hashlib.sha256(a.tobytes()).hexdigest() == h, f"round {t + 1}"
