@@ -11,6 +11,7 @@
 #include "host.cuh"
 #include "iblt_binned.cuh"
 #include "iblt_kernels.cuh"
+#include "iblt_rounds.cuh"
 
 using namespace pp;
 
@@ -23,11 +24,15 @@ static IbltKernels iblt_kernels_t() {
     // the binning kernel's staging grows with r and the number of slabs
     cudaFuncSetAttribute((const void *)k_bin<R, B>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          200 * 1024);
+    cudaFuncSetAttribute((const void *)k_claim<R, B>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         200 * 1024);
+    cudaFuncSetAttribute((const void *)k_apply_round<R, B>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         200 * 1024);
     attr_set = true;
   }
   return {(const void *)k_insert<R, B>, (const void *)k_scan<R, B>, (const void *)k_peel<R, B>,
           (const void *)k_filter<R, B>, (const void *)k_bin<R, B>, (const void *)k_apply<R, B>,
-          R ? R : PP_MAX_R};
+          (const void *)k_claim<R, B>, (const void *)k_apply_round<R, B>, R ? R : PP_MAX_R};
 }
 
 IbltKernels iblt_kernels(uint32_t r, bool batch) {
@@ -42,6 +47,17 @@ IbltKernels iblt_kernels(uint32_t r, bool batch) {
 }
 
 const void *round_end_kernel() { return (const void *)k_round_end; }
+
+const void *bins_reset_kernel() { return (const void *)k_bins_reset; }
+
+size_t claim_smem_bytes(int nr, uint32_t n_bins) {
+  const size_t cap = (size_t)kBlock * nr;
+  return cap * 8 + (size_t)kBlock * 8 + cap * 4 * 3 + 3 * (size_t)n_bins * 4;
+}
+
+size_t apply_round_smem_bytes(bool batch, uint32_t n_bins) {
+  return ((size_t)n_bins + 1) * 4 + (size_t)kApplyChunk * 4 * (batch ? 2 : 1);
+}
 
 size_t bin_smem_bytes(int nr, bool batch, uint32_t n_slabs) {
   const size_t cap = (size_t)kBinKeys * nr;
@@ -73,11 +89,20 @@ struct pp_iblt {
   int grid_scan = 0, grid_peel = 0, grid_filter = 0, grid_insert = 0, grid_bin = 0, grid_apply = 0;
   size_t smem_peel = 0, smem_bin = 0;
   cudaGraphExec_t exec = nullptr;
-  // slab-binned build workspace (allocated on first use, grown as needed)
+  // update records shared by the slab-binned build and the binned decode
+  // rounds (allocated on first use, grown as needed)
   uint32_t n_slabs = 0;
   u64 *rec_key = nullptr;
   u32 *rec_cell = nullptr, *bin_count = nullptr, *bin_overflow = nullptr;
   uint64_t rec_cap_total = 0;
+  uint32_t count_cap = 0;
+  uint32_t rec_gen = 0;    // bumped whenever the record or count buffers move
+  uint32_t graph_gen = 0;  // rec_gen the instantiated graph was built with
+  // binned decode rounds
+  bool binned_rounds = false;
+  uint32_t n_bins = 0, bin_cap = 0;
+  size_t smem_claim = 0, smem_apply_round = 0;
+  int grid_claim = 0, grid_apply_round = 0;
 };
 
 namespace {
@@ -174,6 +199,61 @@ struct EndArgs {
   }
 };
 
+struct ClaimArgs {
+  Cell *cells;
+  TableArgs tab0;
+  const TableArgs *tabs;
+  const u64 *fkey;
+  const u32 *fcell, *ftab, *bitmap;
+  RoundBins rb;
+  u32 *cand, *ctab;
+  u64 *bout;
+  DecodeCtl *ctl;
+  BatchCounters bc;
+  void *p[13];
+  void bind() {
+    void *q[13] = {&cells, &tab0, &tabs, &fkey, &fcell, &ftab, &bitmap, &rb, &cand, &ctab, &bout, &ctl, &bc};
+    memcpy(p, q, sizeof q);
+  }
+};
+
+struct ApplyRArgs {
+  Cell *cells;
+  TableArgs tab0;
+  const TableArgs *tabs;
+  RoundBins rb;
+  u32 *cand, *ctab;
+  DecodeCtl *ctl;
+  BatchCounters bc;
+  void *p[8];
+  void bind() {
+    void *q[8] = {&cells, &tab0, &tabs, &rb, &cand, &ctab, &ctl, &bc};
+    memcpy(p, q, sizeof q);
+  }
+};
+
+struct ResetArgs {
+  RoundBins rb;
+  DecodeCtl *ctl;
+  void *p[2];
+  void bind() {
+    void *q[2] = {&rb, &ctl};
+    memcpy(p, q, sizeof q);
+  }
+};
+
+void fill_round_args(pp_iblt *t, ClaimArgs &ca, ApplyRArgs &aa, ResetArgs &ra) {
+  BatchCounters bc{};
+  RoundBins rb{t->rec_key, t->rec_cell, nullptr, t->bin_count, t->bin_cap, t->n_bins};
+  ca = ClaimArgs{t->cells, t->args, nullptr, t->fkey, t->fcell, nullptr, t->bitmap, rb, t->cand, nullptr,
+                 nullptr, t->ctl, bc, {}};
+  aa = ApplyRArgs{t->cells, t->args, nullptr, rb, t->cand, nullptr, t->ctl, bc, {}};
+  ra = ResetArgs{rb, t->ctl, {}};
+  ca.bind();
+  aa.bind();
+  ra.bind();
+}
+
 void fill_args(pp_iblt *t, ScanArgs &sa, PeelArgs &pa, FilterArgs &fa, EndArgs &ea) {
   BatchCounters bc{};
   sa = ScanArgs{t->cells, t->args, nullptr, nullptr,
@@ -208,7 +288,11 @@ pp_status build_graph(pp_iblt *t) {
   PeelArgs pa;
   FilterArgs fa;
   EndArgs ea;
+  ClaimArgs ca;
+  ApplyRArgs aa;
+  ResetArgs ra;
   fill_args(t, sa, pa, fa, ea);
+  if (t->binned_rounds) fill_round_args(t, ca, aa, ra);
   cudaGraph_t g = nullptr;
   PP_CUDA(cudaGraphCreate(&g, 0));
   pp_status st = PP_OK;
@@ -233,16 +317,35 @@ pp_status build_graph(pp_iblt *t) {
   body = cp.conditional.phGraph_out[0];
   ea.set_cond = 1;
   ea.cond = h;
-  st = add_kernel(&n_peel, body, nullptr, 0, t->k.peel, t->grid_peel, kBlock, t->smem_peel, pa.p);
-  if (st != PP_OK) goto done;
-  st = add_kernel(&n_filter, body, &n_peel, 1, t->k.filter, t->grid_filter, kBlock, 0, fa.p);
-  if (st != PP_OK) goto done;
-  st = add_kernel(&n_end, body, &n_filter, 1, (const void *)k_round_end, 1, 32, 0, ea.p);
-  if (st != PP_OK) goto done;
+  if (t->binned_rounds) {
+    // claim -> apply (binned) -> filter -> reset bins -> round end
+    cudaGraphNode_t n_apply, n_reset;
+    st = add_kernel(&n_peel, body, nullptr, 0, t->k.claim, t->grid_claim, kBlock, t->smem_claim, ca.p);
+    if (st != PP_OK) goto done;
+    st = add_kernel(&n_apply, body, &n_peel, 1, t->k.apply_round, t->grid_apply_round, kBlock,
+                    t->smem_apply_round, aa.p);
+    if (st != PP_OK) goto done;
+    st = add_kernel(&n_filter, body, &n_apply, 1, t->k.filter, t->grid_filter, kBlock, 0, fa.p);
+    if (st != PP_OK) goto done;
+    st = add_kernel(&n_reset, body, &n_filter, 1, (const void *)k_bins_reset, 1, 256, 0, ra.p);
+    if (st != PP_OK) goto done;
+    st = add_kernel(&n_end, body, &n_reset, 1, (const void *)k_round_end, 1, 32, 0, ea.p);
+    if (st != PP_OK) goto done;
+  } else {
+    st = add_kernel(&n_peel, body, nullptr, 0, t->k.peel, t->grid_peel, kBlock, t->smem_peel, pa.p);
+    if (st != PP_OK) goto done;
+    st = add_kernel(&n_filter, body, &n_peel, 1, t->k.filter, t->grid_filter, kBlock, 0, fa.p);
+    if (st != PP_OK) goto done;
+    st = add_kernel(&n_end, body, &n_filter, 1, (const void *)k_round_end, 1, 32, 0, ea.p);
+    if (st != PP_OK) goto done;
+  }
+  // PPEEL_GRAPH_DOT=<path>: write the decode graph in DOT format (debugging aid)
+  if (const char *dot = getenv("PPEEL_GRAPH_DOT")) cudaGraphDebugDotPrint(g, dot, cudaGraphDebugDotFlagsVerbose);
   if (cudaGraphInstantiate(&t->exec, g, 0) != cudaSuccess) {
     st = fail(PP_ERR_CUDA, "cudaGraphInstantiate failed: %s", cudaGetErrorString(cudaGetLastError()));
     t->exec = nullptr;
   }
+  t->graph_gen = t->rec_gen;
 done:
   cudaGraphDestroy(g);
   return st;
@@ -254,10 +357,22 @@ pp_status run_host_loop(pp_iblt *t, cudaStream_t s) {
   FilterArgs fa;
   EndArgs ea;
   fill_args(t, sa, pa, fa, ea);
+  ClaimArgs ca;
+  ApplyRArgs aa;
+  ResetArgs ra;
+  if (t->binned_rounds) fill_round_args(t, ca, aa, ra);
   PP_CUDA(cudaLaunchKernel(t->k.scan, dim3(t->grid_scan), dim3(kBlock), sa.p, 0, s));
   for (;;) {
-    PP_CUDA(cudaLaunchKernel(t->k.peel, dim3(t->grid_peel), dim3(kBlock), pa.p, t->smem_peel, s));
-    PP_CUDA(cudaLaunchKernel(t->k.filter, dim3(t->grid_filter), dim3(kBlock), fa.p, 0, s));
+    if (t->binned_rounds) {
+      PP_CUDA(cudaLaunchKernel(t->k.claim, dim3(t->grid_claim), dim3(kBlock), ca.p, t->smem_claim, s));
+      PP_CUDA(cudaLaunchKernel(t->k.apply_round, dim3(t->grid_apply_round), dim3(kBlock), aa.p,
+                               t->smem_apply_round, s));
+      PP_CUDA(cudaLaunchKernel(t->k.filter, dim3(t->grid_filter), dim3(kBlock), fa.p, 0, s));
+      PP_CUDA(cudaLaunchKernel((const void *)k_bins_reset, dim3(1), dim3(256), ra.p, 0, s));
+    } else {
+      PP_CUDA(cudaLaunchKernel(t->k.peel, dim3(t->grid_peel), dim3(kBlock), pa.p, t->smem_peel, s));
+      PP_CUDA(cudaLaunchKernel(t->k.filter, dim3(t->grid_filter), dim3(kBlock), fa.p, 0, s));
+    }
     PP_CUDA(cudaLaunchKernel((const void *)k_round_end, dim3(1), dim3(32), ea.p, 0, s));
     PP_CUDA(cudaMemcpyAsync(&t->h_ctl->more, &t->ctl->more, sizeof(u32), cudaMemcpyDeviceToHost, s));
     PP_CUDA(cudaStreamSynchronize(s));
@@ -288,6 +403,36 @@ bool use_binned(const pp_iblt *t, uint64_t m) {
   return t->n >= (1ull << 23) && m * t->r >= t->n / 4;
 }
 
+// Grows the shared update-record buffers to `records` entries and the count
+// array to `counts` entries (synchronizes `s` when it reallocates).
+pp_status ensure_records(pp_iblt *t, uint64_t records, uint32_t counts, cudaStream_t s) {
+  if (records > t->rec_cap_total) {
+    PP_CUDA(cudaStreamSynchronize(s));
+    cudaFree(t->rec_key);
+    cudaFree(t->rec_cell);
+    t->rec_key = nullptr;
+    t->rec_cell = nullptr;
+    t->rec_cap_total = 0;
+    PP_CUDA(cudaMalloc((void **)&t->rec_key, records * sizeof(u64)));
+    PP_CUDA(cudaMalloc((void **)&t->rec_cell, records * sizeof(u32)));
+    t->rec_cap_total = records;
+    ++t->rec_gen;
+  }
+  if (counts > t->count_cap || !t->bin_overflow) {
+    PP_CUDA(cudaStreamSynchronize(s));
+    cudaFree(t->bin_count);
+    cudaFree(t->bin_overflow);
+    t->bin_count = nullptr;
+    t->bin_overflow = nullptr;
+    t->count_cap = 0;
+    PP_CUDA(cudaMalloc((void **)&t->bin_count, (counts ? counts : 1) * sizeof(u32)));
+    PP_CUDA(cudaMalloc((void **)&t->bin_overflow, sizeof(u32)));
+    t->count_cap = counts;
+    ++t->rec_gen;
+  }
+  return PP_OK;
+}
+
 // Pass 1 of a binned build: route every (cell, key) update into its slab's list.
 pp_status bin_pass(pp_iblt *t, const uint64_t *d_keys, uint64_t m, int sign, int direct_overflow,
                    cudaStream_t s, BinArgs &ba) {
@@ -296,22 +441,9 @@ pp_status bin_pass(pp_iblt *t, const uint64_t *d_keys, uint64_t m, int sign, int
   const double per = (double)m * t->r * ((double)kSlabCells / (double)t->n);
   const uint64_t cap = (uint64_t)(per * 1.05) + 4096;
   if (cap > 0xFFFFFFF0ull) return fail(PP_ERR_INVALID_ARG, "pp_iblt_insert: too many keys for one call");
-  if (cap * ns > t->rec_cap_total || ns != t->n_slabs) {
-    PP_CUDA(cudaStreamSynchronize(s));
-    cudaFree(t->rec_key);
-    cudaFree(t->rec_cell);
-    cudaFree(t->bin_count);
-    cudaFree(t->bin_overflow);
-    t->rec_key = nullptr;
-    t->rec_cell = nullptr;
-    t->bin_count = nullptr;
-    t->bin_overflow = nullptr;
-    t->rec_cap_total = 0;
-    PP_CUDA(cudaMalloc((void **)&t->rec_key, cap * ns * sizeof(u64)));
-    PP_CUDA(cudaMalloc((void **)&t->rec_cell, cap * ns * sizeof(u32)));
-    PP_CUDA(cudaMalloc((void **)&t->bin_count, ns * sizeof(u32)));
-    PP_CUDA(cudaMalloc((void **)&t->bin_overflow, sizeof(u32)));
-    t->rec_cap_total = cap * ns;
+  pp_status st = ensure_records(t, cap * ns, ns, s);
+  if (st != PP_OK) return st;
+  if (ns != t->n_slabs) {
     t->n_slabs = ns;
     t->smem_bin = bin_smem_bytes(t->k.nr, false, ns);
     t->grid_bin = persistent_grid(t->k.bin, kBlock, t->smem_bin, t->opt.ctas_per_sm);
@@ -330,6 +462,24 @@ pp_status bin_pass(pp_iblt *t, const uint64_t *d_keys, uint64_t m, int sign, int
   const u64 items = (m + kBinKeys - 1) / kBinKeys;
   const int grid = (int)(items < (u64)t->grid_bin ? items : (u64)t->grid_bin);
   PP_CUDA(cudaLaunchKernel(t->k.bin, dim3(grid), dim3(kBlock), args, t->smem_bin, s));
+  return PP_OK;
+}
+
+// Bins of the binned decode rounds: 2^19 cells each; a bin's list holds the
+// updates of half its cells' worth of recovered keys (a round recovers far
+// fewer; a fuller bin applies the excess directly).
+pp_status ensure_round_bins(pp_iblt *t, cudaStream_t s) {
+  const uint32_t nb = (uint32_t)((t->n + (1u << kRoundShift) - 1) >> kRoundShift);
+  const uint64_t span = t->n < (1ull << kRoundShift) ? t->n : (1ull << kRoundShift);
+  const uint64_t cap = (uint64_t)((double)t->r * (double)span * 0.525) + 4096;
+  pp_status st = ensure_records(t, cap * nb, nb, s);
+  if (st != PP_OK) return st;
+  t->n_bins = nb;
+  t->bin_cap = (uint32_t)cap;
+  t->smem_claim = claim_smem_bytes(t->k.nr, nb);
+  t->smem_apply_round = apply_round_smem_bytes(false, nb);
+  t->grid_claim = persistent_grid(t->k.claim, kBlock, t->smem_claim, t->opt.ctas_per_sm);
+  t->grid_apply_round = persistent_grid(t->k.apply_round, kBlock, t->smem_apply_round, 4);
   return PP_OK;
 }
 
@@ -485,6 +635,18 @@ pp_status pp_iblt_decode(pp_iblt *t, uint64_t *d_out_keys, uint64_t out_cap, pp_
   t->h_ctl->out = reinterpret_cast<u64 *>(d_out_keys);
   t->h_ctl->out_cap = out_cap;
   t->h_ctl->max_rounds = t->opt.max_rounds;
+  const bool want_bins = t->opt.binned == 1 || (t->opt.binned == 0 && t->n >= (1ull << 21));
+  if (want_bins) {
+    pp_status st = ensure_round_bins(t, s);
+    if (st != PP_OK) return st;
+    PP_CUDA(cudaMemsetAsync(t->bin_count, 0, t->n_bins * sizeof(u32), s));
+  }
+  // the graph holds buffer pointers: rebuild it when they moved or the round kind changed
+  if (t->exec && (want_bins != t->binned_rounds || (want_bins && t->graph_gen != t->rec_gen))) {
+    cudaGraphExecDestroy(t->exec);
+    t->exec = nullptr;
+  }
+  t->binned_rounds = want_bins;
   PP_CUDA(cudaMemcpyAsync(t->ctl, t->h_ctl, sizeof(DecodeCtl), cudaMemcpyHostToDevice, s));
   if (t->opt.host_loop) {
     pp_status st = run_host_loop(t, s);

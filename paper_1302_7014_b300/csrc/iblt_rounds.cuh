@@ -1,0 +1,357 @@
+// Binned decode round: the round of Sec. 1 (at k = 2, on the IBLT hypergraph
+// of Sec. 6) split so that its cell updates reach HBM in address order.
+//
+//   k_claim  (phase B1) for every frontier entry (cell c, key x snapshotted at
+//            the round's start): c recovers x iff no lower-sub-table cell of x
+//            was pure at the round's start (the same lowest-index rule as
+//            k_peel).  A winner writes x to the output and one update record
+//            (cell, key) per cell of x into the bin of that cell: bins are
+//            2^19 consecutive cells (16 MB).  Records are ordered by bin inside
+//            the block and leave it as contiguous runs.
+//   k_apply_round (phase B2) walks the records bin by bin: blocks take the next
+//            chunk of 1024 records from an atomic counter, so at any moment the
+//            whole GPU updates a narrow, moving window of the table and HBM
+//            sees near-sequential traffic.  Each update is atomicSub(count)
+//            and atomicXor(key, checksum); a count that drops from 2 to 1
+//            makes the cell a candidate for the next frontier.
+// Updates commute, so the order of application does not change the state at
+// the end of the round; the claim decisions are all taken in B1, before any
+// update of the round lands.
+#pragma once
+
+#include "iblt_types.cuh"
+
+namespace pp {
+
+constexpr int kRoundShift = 19;            // 2^19 cells per bin
+constexpr int kApplyPer = 4;               // records per thread per grab
+constexpr int kApplyChunk = kBlock * kApplyPer;
+
+// Record lists of one round: bin b owns records [b*cap, b*cap + min(count[b], cap)).
+struct RoundBins {
+  u64 *rec_key;
+  u32 *rec_cell;
+  u32 *rec_tab;   // batch only
+  u32 *count;
+  u32 cap;
+  u32 n_bins;
+};
+
+__device__ __forceinline__ int remove_key(Cell *cells, u32 c, u64 x, u64 cx) {
+  Cell *p = cells + c;
+  const int old = atomicSub(&p->count, 1);
+  atomicXor(&p->key, x);
+  atomicXor(&p->chk, cx);
+  return old;
+}
+
+// Shared memory of k_claim: staged records (4 arrays of kBlock*NR) + 3 * n_bins u32
+// + the plain decode's output staging (kBlock u64).
+template <int R, bool BATCH>
+__global__ void __launch_bounds__(kBlock) k_claim(Cell *__restrict__ cells, const TableArgs tab0,
+                                                  const TableArgs *__restrict__ tabs,
+                                                  const u64 *__restrict__ fkey, const u32 *__restrict__ fcell,
+                                                  const u32 *__restrict__ ftab, const u32 *__restrict__ bitmap,
+                                                  RoundBins rb, u32 *__restrict__ cand, u32 *__restrict__ ctab,
+                                                  u64 *__restrict__ bout, DecodeCtl *__restrict__ ctl,
+                                                  BatchCounters bc) {
+  constexpr int NR = R ? R : PP_MAX_R;
+  constexpr int CAP = kBlock * NR;
+  extern __shared__ __align__(16) unsigned char smem[];
+  u64 *s_key = reinterpret_cast<u64 *>(smem);       // CAP
+  u64 *s_out = s_key + CAP;                         // kBlock (plain)
+  u32 *s_cell = reinterpret_cast<u32 *>(s_out + kBlock);
+  u32 *s_bin = s_cell + CAP;
+  u32 *s_tab = s_bin + CAP;
+  u32 *s_hist = s_tab + CAP;                        // n_bins
+  u32 *s_scan = s_hist + rb.n_bins;
+  u32 *s_base = s_scan + rb.n_bins;
+  __shared__ u32 s_wt[33];
+  __shared__ u32 s_total, s_nout;
+  __shared__ u64 s_obase;
+  const u32 tid = threadIdx.x;
+  const u32 nb = rb.n_bins;
+  const u32 n = *(volatile u32 *)&ctl->n_front;
+  const u32 round = *(volatile u32 *)&ctl->round;
+  u64 *out = BATCH ? bout : ctl->out;
+  const u64 out_cap = BATCH ? 0 : ctl->out_cap;
+  const u32 stats_rounds = BATCH ? ctl->stats_rounds : 0;
+  u32 flags = 0;
+  u64 ovf_emptied = 0;
+  for (u64 c0 = (u64)blockIdx.x * kBlock; c0 < n; c0 += (u64)gridDim.x * kBlock) {
+    for (u32 i = tid; i < nb; i += kBlock) s_hist[i] = 0;
+    if (tid == 0) s_nout = 0;
+    __syncthreads();
+    const u64 i = c0 + tid;
+    const bool valid = i < n;
+    u64 x = 0;
+    u32 c = 0, tb = 0;
+    if (valid) {
+      x = __ldcs(fkey + i);
+      c = __ldcs(fcell + i);
+      if (BATCH) tb = __ldcs(ftab + i);
+    }
+    const TableArgs &T = BATCH ? tabs[tb] : tab0;
+    const int r = R ? R : (int)T.r;
+    u32 cj[NR];
+    cells_of<NR>(x, T, cj);
+    int jstar = -1;
+#pragma unroll
+    for (int j = NR - 1; j >= 0; --j)
+      if (j < r && cj[j] == c) jstar = j;
+    bool win = valid;
+    if (valid && jstar < 0) {
+      flags |= FLAG_INTERNAL;
+      win = false;
+    }
+#pragma unroll
+    for (int j = 0; j < NR - 1; ++j) {
+      if (win && j < jstar) {
+        const u32 w = __ldcg(bitmap + (cj[j] >> 5));
+        if ((w >> (cj[j] & 31u)) & 1u) win = false;
+      }
+    }
+    // recovered key
+    if constexpr (!BATCH) {
+      const u32 p = warp_reserve<u32>(win, &s_nout);
+      if (win) s_out[p] = x;
+    } else {
+      const u32 label = win ? tb : 0xffffffffu;
+      const u32 grp = __match_any_sync(kFull, label);
+      const int leader = __ffs(grp) - 1;
+      const u32 gsize = __popc(grp);
+      u64 base = 0;
+      if (win && (int)lane_id() == leader) {
+        const u32 local = round + 1 - T.start_round;
+        base = atomicAdd(bc.recovered + tb, (u64)gsize);
+        atomicMax(bc.rounds + tb, local);
+        if (local <= stats_rounds) atomicAdd(bc.round_rec + (u64)tb * stats_rounds + (local - 1), gsize);
+      }
+      base = __shfl_sync(kFull, base, leader);
+      if (win) {
+        const u64 slot = base + __popc(grp & lanemask_lt());
+        if (slot < T.out_cap) out[T.out_base + slot] = x;
+        else flags |= FLAG_CAPACITY;
+      }
+    }
+    // update records, counted per bin
+    u32 rank[NR];
+#pragma unroll
+    for (int j = 0; j < NR; ++j)
+      rank[j] = (win && j < r) ? atomicAdd(s_hist + (cj[j] >> kRoundShift), 1u) : 0u;
+    __syncthreads();
+    // exclusive scan of the histogram: thread t owns bins [t*per, (t+1)*per)
+    const u32 per = (nb + kBlock - 1) / kBlock;
+    const u32 lo = tid * per, hi = lo + per < nb ? lo + per : nb;
+    u32 own = 0;
+    for (u32 k = lo; k < hi; ++k) own += s_hist[k];
+    u32 inc = own;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const u32 y = __shfl_up_sync(kFull, inc, o);
+      if ((int)lane_id() >= o) inc += y;
+    }
+    if (lane_id() == 31) s_wt[tid >> 5] = inc;
+    __syncthreads();
+    if (tid < 32) {
+      const u32 w = tid < kBlock / 32 ? s_wt[tid] : 0;
+      u32 wi = w;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const u32 y = __shfl_up_sync(kFull, wi, o);
+        if ((int)tid >= o) wi += y;
+      }
+      if (tid < kBlock / 32) s_wt[tid] = wi - w;
+      if (tid == 31) s_total = wi;
+      if (!BATCH && tid == 0 && s_nout) s_obase = atomicAdd(&ctl->n_out, (u64)s_nout);
+    }
+    __syncthreads();
+    u32 run = s_wt[tid >> 5] + inc - own;
+    for (u32 k = lo; k < hi; ++k) {
+      s_scan[k] = run;
+      const u32 h = s_hist[k];
+      s_base[k] = h ? atomicAdd(rb.count + k, h) : 0u;
+      run += h;
+    }
+    __syncthreads();
+    if (win) {
+#pragma unroll
+      for (int j = 0; j < NR; ++j) {
+        if (j < r) {
+          const u32 bn = cj[j] >> kRoundShift;
+          const u32 pos = s_scan[bn] + rank[j];
+          s_key[pos] = x;
+          s_cell[pos] = cj[j];
+          s_bin[pos] = bn;
+          if (BATCH) s_tab[pos] = tb;
+        }
+      }
+    }
+    __syncthreads();
+    const u32 total = s_total;
+    for (u32 p = tid; p < total; p += kBlock) {
+      const u32 bn = s_bin[p];
+      const u32 slot = s_base[bn] + (p - s_scan[bn]);
+      if (slot < rb.cap) {
+        const u64 dst = (u64)bn * rb.cap + slot;
+        rb.rec_key[dst] = s_key[p];
+        rb.rec_cell[dst] = s_cell[p];
+        if (BATCH) rb.rec_tab[dst] = s_tab[p];
+      } else {
+        // the bin is full: apply this update right away (updates commute)
+        const u32 t2 = BATCH ? s_tab[p] : 0u;
+        const TableArgs &TT = BATCH ? tabs[t2] : tab0;
+        const u64 xx = s_key[p];
+        const u32 cc = s_cell[p];
+        const int old = remove_key(cells, cc, xx, mix64(xx ^ TT.seed[R ? R : (int)TT.r]));
+        if (old == 2) {
+          const u32 q = atomicAdd(&ctl->n_cand, 1u);
+          cand[q] = cc;
+          if (BATCH) ctab[q] = t2;
+        }
+        if (old == 1) {
+          if (BATCH) atomicAdd(bc.emptied + t2, 1ull);
+          else ++ovf_emptied;
+        }
+      }
+    }
+    if constexpr (!BATCH) {
+      const u32 no = s_nout;
+      const u64 ob = s_obase;
+      for (u32 q = tid; q < no; q += kBlock) {
+        if (ob + q < out_cap) out[ob + q] = s_out[q];
+        else flags |= FLAG_CAPACITY;
+      }
+    }
+    __syncthreads();
+  }
+  if (ovf_emptied) atomicAdd(&ctl->emptied, ovf_emptied);
+  if (flags) atomicOr(&ctl->flags, flags);
+}
+
+// Shared memory of k_apply_round: chunk prefix (n_bins + 1 u32) + pushes
+// (kApplyChunk cells [+ tables]).
+template <int R, bool BATCH>
+__global__ void __launch_bounds__(kBlock) k_apply_round(Cell *__restrict__ cells, const TableArgs tab0,
+                                                        const TableArgs *__restrict__ tabs, RoundBins rb,
+                                                        u32 *__restrict__ cand, u32 *__restrict__ ctab,
+                                                        DecodeCtl *__restrict__ ctl, BatchCounters bc) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  u32 *s_pre = reinterpret_cast<u32 *>(smem);       // n_bins + 1
+  u32 *s_cand = s_pre + rb.n_bins + 1;              // kApplyChunk
+  u32 *s_ctab = s_cand + kApplyChunk;               // kApplyChunk (batch)
+  __shared__ u32 s_wt[33];
+  __shared__ u32 s_chunk, s_ncand, s_cbase;
+  __shared__ u64 s_red[kBlock / 32];
+  const u32 tid = threadIdx.x;
+  const u32 nb = rb.n_bins;
+  // chunk prefix over the bins (every block computes it)
+  const u32 per = (nb + kBlock - 1) / kBlock;
+  const u32 lo = tid * per, hi = lo + per < nb ? lo + per : nb;
+  u32 own = 0;
+  for (u32 k = lo; k < hi; ++k) {
+    const u32 cnt = rb.count[k];
+    own += ((cnt < rb.cap ? cnt : rb.cap) + kApplyChunk - 1) / kApplyChunk;
+  }
+  u32 inc = own;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const u32 y = __shfl_up_sync(kFull, inc, o);
+    if ((int)lane_id() >= o) inc += y;
+  }
+  if (lane_id() == 31) s_wt[tid >> 5] = inc;
+  __syncthreads();
+  if (tid < 32) {
+    const u32 w = tid < kBlock / 32 ? s_wt[tid] : 0;
+    u32 wi = w;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const u32 y = __shfl_up_sync(kFull, wi, o);
+      if ((int)tid >= o) wi += y;
+    }
+    if (tid < kBlock / 32) s_wt[tid] = wi - w;
+    if (tid == 31) s_pre[nb] = wi;
+  }
+  __syncthreads();
+  {
+    u32 run = s_wt[tid >> 5] + inc - own;
+    for (u32 k = lo; k < hi; ++k) {
+      s_pre[k] = run;
+      const u32 cnt = rb.count[k];
+      run += ((cnt < rb.cap ? cnt : rb.cap) + kApplyChunk - 1) / kApplyChunk;
+    }
+  }
+  if (tid == 0) s_ncand = 0;
+  __syncthreads();
+  const u32 total = s_pre[nb];
+  u64 emptied = 0;
+  for (;;) {
+    if (tid == 0) s_chunk = atomicAdd(&ctl->apply_next, 1u);
+    __syncthreads();
+    const u32 chunk = s_chunk;
+    if (chunk >= total) break;
+    // bin of this chunk: last k with s_pre[k] <= chunk
+    u32 a = 0, b = nb;
+    while (b - a > 1) {
+      const u32 mid = (a + b) >> 1;
+      if (s_pre[mid] <= chunk) a = mid;
+      else b = mid;
+    }
+    const u32 bn = a;
+    const u32 cnt = rb.count[bn];
+    const u32 in_bin = cnt < rb.cap ? cnt : rb.cap;
+    const u32 first = (chunk - s_pre[bn]) * kApplyChunk;
+    const u64 base = (u64)bn * rb.cap;
+#pragma unroll
+    for (int k = 0; k < kApplyPer; ++k) {
+      const u32 i = first + (u32)k * kBlock + tid;
+      const bool valid = i < in_bin;
+      int old = 0;
+      u32 c = 0, tb = 0;
+      if (valid) {
+        const u64 x = __ldcs(rb.rec_key + base + i);
+        c = __ldcs(rb.rec_cell + base + i);
+        if (BATCH) tb = __ldcs(rb.rec_tab + base + i);
+        const TableArgs &T = BATCH ? tabs[tb] : tab0;
+        old = remove_key(cells, c, x, mix64(x ^ T.seed[R ? R : (int)T.r]));
+      }
+      const bool push = old == 2;
+      const u32 q = warp_reserve<u32>(push, &s_ncand);
+      if (push) {
+        s_cand[q] = c;
+        if (BATCH) s_ctab[q] = tb;
+      }
+      if constexpr (BATCH) {
+        const u32 e = old == 1 ? 1u : 0u;
+        const u32 grp = __match_any_sync(kFull, e ? tb : 0xffffffffu);
+        const u32 ge = __reduce_add_sync(grp, e);
+        if (e && (int)lane_id() == __ffs(grp) - 1) atomicAdd(bc.emptied + tb, (u64)ge);
+      } else {
+        emptied += old == 1;
+      }
+    }
+    __syncthreads();
+    const u32 nc = s_ncand;
+    if (tid == 0 && nc) s_cbase = atomicAdd(&ctl->n_cand, nc);
+    __syncthreads();
+    for (u32 q = tid; q < nc; q += kBlock) {
+      cand[s_cbase + q] = s_cand[q];
+      if (BATCH) ctab[s_cbase + q] = s_ctab[q];
+    }
+    __syncthreads();
+    if (tid == 0) s_ncand = 0;
+  }
+  if (!BATCH) {
+    const u64 e = block_sum<u64, kBlock>(emptied, s_red);
+    if (tid == 0 && e) atomicAdd(&ctl->emptied, e);
+  }
+}
+
+// End of a binned round: clears the bins and the apply work counter for the
+// next round, then does what k_round_end does.
+__global__ void k_bins_reset(RoundBins rb, DecodeCtl *__restrict__ ctl) {
+  for (u32 i = threadIdx.x; i < rb.n_bins; i += blockDim.x) rb.count[i] = 0;
+  if (threadIdx.x == 0) ctl->apply_next = 0;
+}
+
+}  // namespace pp

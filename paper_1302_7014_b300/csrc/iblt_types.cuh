@@ -27,6 +27,8 @@ struct DecodeCtl {
   u32 max_rounds;
   u32 more;             // 1 while another round must run
   u32 stats_rounds;     // batch: per-table per-round counter slots
+  u32 apply_next;       // binned rounds: next chunk of update records to apply
+  u32 pad_;
 };
 
 // Per-round device statistics (index t-1 for round t).
@@ -56,7 +58,8 @@ struct Chunk {
 // Entry points of one instantiation of the IBLT kernels (plain or batched).
 struct IbltKernels {
   const void *insert, *scan, *peel, *filter;
-  const void *bin, *apply;  // slab-binned build
+  const void *bin, *apply;           // slab-binned build
+  const void *claim, *apply_round;   // binned decode round
   int nr;  // compile-time rank (PP_MAX_R for the generic instance)
 };
 
@@ -68,6 +71,13 @@ size_t peel_smem_bytes(int nr, bool batch);
 
 // Dynamic shared memory of the binning kernel for n_slabs slabs.
 size_t bin_smem_bytes(int nr, bool batch, uint32_t n_slabs);
+
+// Dynamic shared memory of the binned round's claim and apply kernels.
+size_t claim_smem_bytes(int nr, uint32_t n_bins);
+size_t apply_round_smem_bytes(bool batch, uint32_t n_bins);
+
+// The bin-reset kernel that ends a binned round.
+const void *bins_reset_kernel();
 
 // The round_end kernel (one thread; records a round and decides on the next).
 const void *round_end_kernel();

@@ -287,3 +287,38 @@ def test_headline_full_size_build(pp):
     rounds = _split_rounds(got, res.recovered_per_round)
     for t, (a, h) in enumerate(zip(rounds, gold["round_sha256"])):
         assert hashlib.sha256(a.tobytes()).hexdigest() == h, f"round {t + 1}"
+
+
+BINNED_CASES = CASES + [(3 * (1 << 19) + 17, 3, 0.75, 31), ((1 << 21) + 1, 4, 0.85, 32),
+                        (5 * (1 << 19) - 3, 5, 0.6, 33)]
+
+
+@pytest.mark.parametrize("n,r,c,seed", BINNED_CASES, ids=[f"binned-n{n}-r{r}-c{c}" for n, r, c, _ in BINNED_CASES])
+def test_iblt_parity_binned_rounds(pp, n, r, c, seed):
+    """Rounds split into claim + address-ordered apply (forced on) against the oracle."""
+    keys = ppgen.distinct_keys(ppgen.edges_from_c(c, n), 3000 + seed)
+    run_case(pp, n, r, keys, seed, opts=pp.options(binned=1))
+
+
+@pytest.mark.parametrize("n,r,c,seed", BINNED_CASES[-3:], ids=[f"binned-hostloop-n{n}" for n, r, c, _ in BINNED_CASES[-3:]])
+def test_iblt_parity_binned_rounds_host_loop(pp, n, r, c, seed):
+    keys = ppgen.distinct_keys(ppgen.edges_from_c(c, n), 4000 + seed)
+    run_case(pp, n, r, keys, seed, opts=pp.options(binned=1, host_loop=1, ctas_per_sm=1))
+
+
+def test_binned_rounds_after_workspace_growth(pp):
+    # a small build first, then a bigger one: the record buffers move and the
+    # decode graph must follow them
+    n, r = 3 * (1 << 19) + 5, 3
+    gt = pp.IBLT(n, r, 5, pp.options(binned=1))
+    for m_frac in (0.1, 0.8, 0.75):
+        keys = ppgen.distinct_keys(ppgen.edges_from_c(m_frac, n), int(m_frac * 100))
+        gt.build(_dev(keys))
+        out = torch.zeros(keys.size, dtype=torch.int64, device="cuda")
+        res = gt.decode(out)
+        ot = oracle.IBLT(n, r, 5)
+        ot.insert(keys)
+        ores = ot.decode_rounds()
+        assert res.rounds == ores["rounds"]
+        assert res.recovered_per_round == [k.size for k in ores["keys"]]
+        _assert_cells_equal(gt.cells(), ot)
