@@ -200,8 +200,7 @@ def bench_batched(pp, torch, args):
     b = pb.Batch([t.n_cells for t in tabs], [t.r for t in tabs], [t.table_seed for t in tabs])
 
     def bstep():
-        b.clear(stream)
-        b.insert(dkeys, koff, stream)
+        b.build(dkeys, koff, stream)   # clear + insert
         return b.decode(out, koff, stream=stream)
 
     for _ in range(max(2, args.warmup)):

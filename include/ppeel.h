@@ -249,6 +249,12 @@ pp_status pp_batch_insert(pp_batch *b, const uint64_t *d_keys, const uint64_t *h
 pp_status pp_batch_delete(pp_batch *b, const uint64_t *d_keys, const uint64_t *h_key_offsets,
                           void *stream);
 
+/* Builds every table from scratch: equal to pp_batch_clear followed by
+ * pp_batch_insert.  A large arena is built slab by slab (2^21 cells at a time,
+ * each zero-filled and updated while in L2).  Synchronizes `stream` once. */
+pp_status pp_batch_build(pp_batch *b, const uint64_t *d_keys, const uint64_t *h_key_offsets,
+                         void *stream);
+
 /* Decodes every table in place.  Table i's recovered keys go to
  * d_out_keys[h_out_offsets[i] ..], grouped by round, in no order within a
  * round; each table needs at least as many slots as it holds keys, else

@@ -26,6 +26,7 @@ _lib.declare("pp_batch_destroy", ctypes.c_int, [vp])
 _lib.declare("pp_batch_clear", ctypes.c_int, [vp, vp])
 _lib.declare("pp_batch_insert", ctypes.c_int, [vp, vp, ctypes.POINTER(u64), vp])
 _lib.declare("pp_batch_delete", ctypes.c_int, [vp, vp, ctypes.POINTER(u64), vp])
+_lib.declare("pp_batch_build", ctypes.c_int, [vp, vp, ctypes.POINTER(u64), vp])
 _lib.declare("pp_batch_decode", ctypes.c_int, [vp, vp, ctypes.POINTER(u64), ctypes.POINTER(TableResult), vp])
 _lib.declare("pp_batch_copy_cells", ctypes.c_int, [vp, u32, vp, ctypes.c_int, vp])
 _lib.declare("pp_batch_info", ctypes.c_int, [vp, ctypes.POINTER(u32), ctypes.POINTER(u64), ctypes.POINTER(u32)])
@@ -90,6 +91,13 @@ class Batch:
     def delete(self, keys, key_offsets, stream=None):
         self.insert(keys, key_offsets, stream, sign=-1)
 
+    def build(self, keys, key_offsets, stream=None):
+        """Clear every table and insert ``keys`` (one call, slab by slab when large)."""
+        off, off_p = _u64_array(key_offsets)
+        assert off.size == self.n_tables + 1
+        ptr = _dev_ptr(keys, 8, "keys") if keys is not None and keys.numel() else None
+        _check(_lib.load().pp_batch_build(self._h, ptr, off_p, _stream_ptr(stream)), "pp_batch_build")
+
     def decode(self, out, out_offsets, round_cap: int = 256, stream=None) -> BatchOutcome:
         off, off_p = _u64_array(out_offsets)
         n = self.n_tables
@@ -125,6 +133,10 @@ def batch_create(n_cells, r, seeds, opts: Options | None = None) -> Batch:
 
 def batch_insert(batch: Batch, keys, key_offsets, stream=None) -> None:
     batch.insert(keys, key_offsets, stream)
+
+
+def batch_build(batch: Batch, keys, key_offsets, stream=None) -> None:
+    batch.build(keys, key_offsets, stream)
 
 
 def batch_decode(batch: Batch, out, out_offsets, round_cap: int = 256, stream=None) -> BatchOutcome:

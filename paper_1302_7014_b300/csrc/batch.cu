@@ -54,6 +54,19 @@ struct pp_batch {
   size_t smem_peel = 0;
   cudaGraphExec_t exec = nullptr;
   u64 *graph_out = nullptr;  // output buffer the instantiated graph writes to
+  // update records shared by the slab-binned build and the binned rounds
+  u64 *rec_key = nullptr;
+  u32 *rec_cell = nullptr, *rec_tab = nullptr, *bin_count = nullptr, *bin_overflow = nullptr;
+  uint64_t rec_cap_total = 0;
+  uint32_t count_cap = 0, rec_gen = 0, graph_gen = 0;
+  uint32_t max_r = 0;
+  bool binned_rounds = false;
+  bool had_deletes = false;   // since the last clear/build
+  u64 *h_items = nullptr;     // pinned copy of items[] for upload
+  u64 *h_residual = nullptr;
+  uint32_t n_bins = 0, bin_cap = 0, n_slabs = 0, bin_shift = 0;
+  size_t smem_claim = 0, smem_apply_round = 0, smem_bin = 0;
+  int grid_claim = 0, grid_apply_round = 0, grid_bin = 0, grid_apply = 0;
 };
 
 namespace {
@@ -82,12 +95,78 @@ void free_batch(pp_batch *b) {
   cudaFree(b->bc.emptied);
   cudaFree(b->bc.rounds);
   cudaFree(b->bc.round_rec);
+  cudaFree((void *)b->bc.chk_seed);
+  cudaFree(b->bc.residual);
+  cudaFree((void *)b->bc.items);
+  cudaFreeHost(b->h_items);
+  cudaFreeHost(b->h_residual);
   cudaFreeHost(b->h_recovered);
   cudaFreeHost(b->h_nonempty);
   cudaFreeHost(b->h_emptied);
   cudaFreeHost(b->h_rounds);
   cudaFreeHost(b->h_round_rec);
+  cudaFree(b->rec_key);
+  cudaFree(b->rec_cell);
+  cudaFree(b->rec_tab);
+  cudaFree(b->bin_count);
+  cudaFree(b->bin_overflow);
   delete b;
+}
+
+pp_status ensure_records(pp_batch *b, uint64_t records, uint32_t counts, cudaStream_t s) {
+  if (records > b->rec_cap_total) {
+    PP_CUDA(cudaStreamSynchronize(s));
+    cudaFree(b->rec_key);
+    cudaFree(b->rec_cell);
+    cudaFree(b->rec_tab);
+    b->rec_key = nullptr;
+    b->rec_cell = nullptr;
+    b->rec_tab = nullptr;
+    b->rec_cap_total = 0;
+    PP_CUDA(cudaMalloc((void **)&b->rec_key, records * sizeof(u64)));
+    PP_CUDA(cudaMalloc((void **)&b->rec_cell, records * sizeof(u32)));
+    PP_CUDA(cudaMalloc((void **)&b->rec_tab, records * sizeof(u32)));
+    b->rec_cap_total = records;
+    ++b->rec_gen;
+  }
+  if (counts > b->count_cap || !b->bin_overflow) {
+    PP_CUDA(cudaStreamSynchronize(s));
+    cudaFree(b->bin_count);
+    cudaFree(b->bin_overflow);
+    b->bin_count = nullptr;
+    b->bin_overflow = nullptr;
+    PP_CUDA(cudaMalloc((void **)&b->bin_count, (counts ? counts : 1) * sizeof(u32)));
+    PP_CUDA(cudaMalloc((void **)&b->bin_overflow, sizeof(u32)));
+    b->count_cap = counts;
+    ++b->rec_gen;
+  }
+  return PP_OK;
+}
+
+bool use_binned(const pp_batch *b, uint64_t records) {
+  if (records == 0 || b->opt.binned == 2) return false;
+  if (b->opt.binned == 1) return true;
+  return b->total_cells >= (1ull << 23) && records >= b->total_cells / 4;
+}
+
+// Bins of the binned rounds over the whole arena (2^19 cells each).  A bin's
+// list holds the updates of 0.35 keys per cell at the largest r in the batch;
+// fuller bins apply their excess directly.
+pp_status ensure_round_bins(pp_batch *b, cudaStream_t s) {
+  const u32 shift = round_bin_shift(b->total_cells);
+  const uint32_t nb = (uint32_t)((b->total_cells + (1ull << shift) - 1) >> shift);
+  const uint64_t span = b->total_cells < (1ull << shift) ? b->total_cells : (1ull << shift);
+  const uint64_t cap = (uint64_t)((double)b->max_r * (double)span * 0.35) + 4096;
+  pp_status st = ensure_records(b, cap * nb, nb, s);
+  if (st != PP_OK) return st;
+  b->n_bins = nb;
+  b->bin_cap = (uint32_t)cap;
+  b->bin_shift = shift;
+  b->smem_claim = claim_smem_bytes(b->k.nr, nb);
+  b->smem_apply_round = apply_round_smem_bytes(true, nb);
+  b->grid_claim = persistent_grid(b->k.claim, kBlock, b->smem_claim, b->opt.ctas_per_sm);
+  b->grid_apply_round = persistent_grid(b->k.apply_round, kBlock, b->smem_apply_round, 4);
+  return PP_OK;
 }
 
 struct BatchArgs {
@@ -113,7 +192,9 @@ struct BatchArgs {
   RoundStats st;
   int set_cond;
   cudaGraphConditionalHandle cond;
-  void *scan_p[11], *peel_p[12], *filter_p[11], *end_p[4];
+  // binned rounds
+  RoundBins rb;
+  void *scan_p[11], *peel_p[12], *filter_p[11], *end_p[4], *claim_p[13], *applyr_p[8], *reset_p[2];
   void bind() {
     void *s[11] = {&cells, &tab0, &tabs, &chunks, &n_chunks, &fkey, &fcell, &ftab, &bitmap, &ctl, &bc};
     void *p[12] = {&cells, &tab0, &tabs, &fkey_c, &fcell_c, &ftab_c, &bitmap_c, &cand, &ctab, &bout, &ctl, &bc};
@@ -123,6 +204,12 @@ struct BatchArgs {
     memcpy(peel_p, p, sizeof p);
     memcpy(filter_p, f, sizeof f);
     memcpy(end_p, e, sizeof e);
+    void *c[13] = {&cells, &tab0, &tabs, &fkey_c, &fcell_c, &ftab_c, &bitmap_c, &rb, &cand, &ctab, &bout, &ctl, &bc};
+    void *a[8] = {&cells, &tab0, &tabs, &rb, &cand, &ctab, &ctl, &bc};
+    void *z[2] = {&rb, &ctl};
+    memcpy(claim_p, c, sizeof c);
+    memcpy(applyr_p, a, sizeof a);
+    memcpy(reset_p, z, sizeof z);
   }
 };
 
@@ -149,6 +236,7 @@ void fill(pp_batch *b, BatchArgs &a, u64 *out) {
   a.cand_c = b->cand;
   a.ctab_c = b->ctab;
   a.st = RoundStats{b->st_rec, b->st_alive, b->st_front};
+  a.rb = RoundBins{b->rec_key, b->rec_cell, b->rec_tab, b->bin_count, b->bin_cap, b->n_bins, b->bin_shift, 0};
   a.bind();
 }
 
@@ -197,16 +285,32 @@ pp_status build_graph(pp_batch *b, u64 *out) {
   body = cp.conditional.phGraph_out[0];
   a.set_cond = 1;
   a.cond = h;
-  st = add_kernel(&n_peel, body, nullptr, 0, b->k.peel, b->grid_peel, kBlock, b->smem_peel, a.peel_p);
-  if (st != PP_OK) goto done;
-  st = add_kernel(&n_filter, body, &n_peel, 1, b->k.filter, b->grid_filter, kBlock, 0, a.filter_p);
-  if (st != PP_OK) goto done;
-  st = add_kernel(&n_end, body, &n_filter, 1, round_end_kernel(), 1, 32, 0, a.end_p);
-  if (st != PP_OK) goto done;
+  if (b->binned_rounds) {
+    cudaGraphNode_t n_apply, n_reset;
+    st = add_kernel(&n_peel, body, nullptr, 0, b->k.claim, b->grid_claim, kBlock, b->smem_claim, a.claim_p);
+    if (st != PP_OK) goto done;
+    st = add_kernel(&n_apply, body, &n_peel, 1, b->k.apply_round, b->grid_apply_round, kBlock,
+                    b->smem_apply_round, a.applyr_p);
+    if (st != PP_OK) goto done;
+    st = add_kernel(&n_filter, body, &n_apply, 1, b->k.filter, b->grid_filter, kBlock, 0, a.filter_p);
+    if (st != PP_OK) goto done;
+    st = add_kernel(&n_reset, body, &n_filter, 1, bins_reset_kernel(), 1, 256, 0, a.reset_p);
+    if (st != PP_OK) goto done;
+    st = add_kernel(&n_end, body, &n_reset, 1, round_end_kernel(), 1, 32, 0, a.end_p);
+    if (st != PP_OK) goto done;
+  } else {
+    st = add_kernel(&n_peel, body, nullptr, 0, b->k.peel, b->grid_peel, kBlock, b->smem_peel, a.peel_p);
+    if (st != PP_OK) goto done;
+    st = add_kernel(&n_filter, body, &n_peel, 1, b->k.filter, b->grid_filter, kBlock, 0, a.filter_p);
+    if (st != PP_OK) goto done;
+    st = add_kernel(&n_end, body, &n_filter, 1, round_end_kernel(), 1, 32, 0, a.end_p);
+    if (st != PP_OK) goto done;
+  }
   if (cudaGraphInstantiate(&b->exec, g, 0) != cudaSuccess) {
     st = fail(PP_ERR_CUDA, "cudaGraphInstantiate failed");
     b->exec = nullptr;
   }
+  b->graph_gen = b->rec_gen;
 done:
   cudaGraphDestroy(g);
   return st;
@@ -251,7 +355,9 @@ pp_status pp_batch_create(pp_batch **out, uint32_t n_tables, const uint64_t *n_c
   b->rank = common_r;
   b->total_cells = base;
   b->n_scan_chunks = (u32)chunks.size();
-  b->k = iblt_kernels(common_r ? common_r : 0, true);
+  uint32_t max_r = 0;
+  for (uint32_t i = 0; i < n_tables; ++i) max_r = r[i] > max_r ? r[i] : max_r;
+  b->k = iblt_kernels(common_r ? (int)common_r : (max_r <= 4 ? -4 : 0), true);
   b->smem_peel = peel_smem_bytes(b->k.nr, true);
   const uint64_t N = base;
   const uint32_t mr = b->opt.max_rounds;
@@ -280,6 +386,9 @@ pp_status pp_batch_create(pp_batch **out, uint32_t n_tables, const uint64_t *n_c
   al((void **)&b->bc.emptied, n_tables * sizeof(u64));
   al((void **)&b->bc.rounds, n_tables * sizeof(u32));
   al((void **)&b->bc.round_rec, (size_t)n_tables * sr * sizeof(u32));
+  al((void **)&b->bc.chk_seed, n_tables * sizeof(u64));
+  al((void **)&b->bc.residual, n_tables * sizeof(u64));
+  al((void **)&b->bc.items, n_tables * sizeof(u64));
   if (e == cudaSuccess) e = cudaMallocHost((void **)&b->h_ctl, sizeof(DecodeCtl));
   if (e == cudaSuccess) e = cudaMallocHost((void **)&b->h_ins_chunks, b->ins_chunk_cap * sizeof(Chunk));
   if (e == cudaSuccess) e = cudaMallocHost((void **)&b->h_recovered, n_tables * sizeof(u64));
@@ -287,6 +396,13 @@ pp_status pp_batch_create(pp_batch **out, uint32_t n_tables, const uint64_t *n_c
   if (e == cudaSuccess) e = cudaMallocHost((void **)&b->h_emptied, n_tables * sizeof(u64));
   if (e == cudaSuccess) e = cudaMallocHost((void **)&b->h_rounds, n_tables * sizeof(u32));
   if (e == cudaSuccess) e = cudaMallocHost((void **)&b->h_round_rec, (size_t)n_tables * sr * sizeof(u32));
+  if (e == cudaSuccess) e = cudaMallocHost((void **)&b->h_items, n_tables * sizeof(u64));
+  if (e == cudaSuccess) e = cudaMallocHost((void **)&b->h_residual, n_tables * sizeof(u64));
+  if (e == cudaSuccess) {
+    std::vector<u64> cs(n_tables);
+    for (uint32_t i = 0; i < n_tables; ++i) cs[i] = b->h_tabs[i].seed[b->h_tabs[i].r];
+    e = cudaMemcpy((void *)b->bc.chk_seed, cs.data(), n_tables * sizeof(u64), cudaMemcpyHostToDevice);
+  }
   if (e == cudaSuccess) e = cudaMemcpy(b->tabs, b->h_tabs.data(), n_tables * sizeof(TableArgs), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(b->scan_chunks, chunks.data(), chunks.size() * sizeof(Chunk), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemset(b->cells, 0, N * sizeof(Cell));
@@ -301,6 +417,8 @@ pp_status pp_batch_create(pp_batch **out, uint32_t n_tables, const uint64_t *n_c
   b->grid_peel = persistent_grid(b->k.peel, kBlock, b->smem_peel, b->opt.ctas_per_sm);
   b->grid_filter = persistent_grid(b->k.filter, kBlock, 0, b->opt.ctas_per_sm);
   b->grid_insert = persistent_grid(b->k.insert, kBlock, 0, 8) * 2;
+  b->grid_apply = persistent_grid(b->k.apply, kBlock, 0, 8);
+  b->max_r = max_r;
   *out = b;
   return PP_OK;
 }
@@ -316,23 +434,26 @@ pp_status pp_batch_clear(pp_batch *b, void *stream) {
   if (!b) return fail(PP_ERR_INVALID_ARG, "pp_batch_clear: NULL batch");
   PP_CUDA(cudaMemsetAsync(b->cells, 0, b->total_cells * sizeof(Cell), as_stream(stream)));
   for (auto &x : b->items) x = 0;
+  b->had_deletes = false;
   return PP_OK;
 }
 
-static pp_status batch_update(pp_batch *b, const uint64_t *d_keys, const uint64_t *h_key_offsets,
-                              int sign, void *stream) {
-  if (!b || !h_key_offsets) return fail(PP_ERR_INVALID_ARG, "pp_batch_insert: NULL argument");
-  cudaStream_t s = as_stream(stream);
+// Uploads the insert work list (key ranges of at most kInsertChunk keys, one table each).
+static pp_status upload_chunks(pp_batch *b, const uint64_t *h_key_offsets, cudaStream_t s, u32 *n_chunks,
+                               uint64_t *records) {
   std::vector<Chunk> chunks;
+  uint64_t rec = 0;
   for (uint32_t i = 0; i < b->n_tables; ++i) {
     const uint64_t k0 = h_key_offsets[i], k1 = h_key_offsets[i + 1];
     if (k1 < k0) return fail(PP_ERR_INVALID_ARG, "pp_batch_insert: key offsets decrease at table %u", i);
     if (k1 > 0xFFFFFFFFull) return fail(PP_ERR_INVALID_ARG, "pp_batch_insert: more than 2^32 keys");
     for (uint64_t k = k0; k < k1; k += kInsertChunk)
       chunks.push_back(Chunk{i, (u32)k, (u32)(k + kInsertChunk < k1 ? k + kInsertChunk : k1)});
+    rec += (k1 - k0) * b->h_tabs[i].r;
   }
+  *n_chunks = (u32)chunks.size();
+  *records = rec;
   if (chunks.empty()) return PP_OK;
-  if (!d_keys) return fail(PP_ERR_INVALID_ARG, "pp_batch_insert: NULL keys");
   if (chunks.size() > b->ins_chunk_cap) {
     PP_CUDA(cudaStreamSynchronize(s));
     cudaFree(b->ins_chunks);
@@ -349,21 +470,109 @@ static pp_status batch_update(pp_batch *b, const uint64_t *d_keys, const uint64_
   memcpy(b->h_ins_chunks, chunks.data(), chunks.size() * sizeof(Chunk));
   PP_CUDA(cudaMemcpyAsync(b->ins_chunks, b->h_ins_chunks, chunks.size() * sizeof(Chunk),
                           cudaMemcpyHostToDevice, s));
+  return PP_OK;
+}
+
+static pp_status direct_update(pp_batch *b, const uint64_t *d_keys, u32 nch, int sign, cudaStream_t s) {
   Cell *cells = b->cells;
   TableArgs t0{};
   const TableArgs *tabs = b->tabs;
   const Chunk *ch = b->ins_chunks;
-  u32 nch = (u32)chunks.size();
   const u64 *keys = reinterpret_cast<const u64 *>(d_keys);
   u64 m = 0;
   void *args[] = {&cells, &t0, &tabs, &ch, &nch, &keys, &m, &sign};
   const int grid = nch < (u32)b->grid_insert ? (int)nch : b->grid_insert;
   PP_CUDA(cudaLaunchKernel(b->k.insert, dim3(grid), dim3(kBlock), args, 0, s));
+  return PP_OK;
+}
+
+// Pass 1 of a binned batch update: every (cell, key) update into its slab's
+// list.  Tables differ in load and r, so each slab's expected share is summed
+// from the tables it overlaps.
+static pp_status batch_bin_pass(pp_batch *b, const uint64_t *d_keys, const uint64_t *h_key_offsets, u32 nch,
+                                int sign, int direct_overflow, cudaStream_t s, BinArgs &ba) {
+  const uint32_t ns = (uint32_t)((b->total_cells + kSlabCells - 1) / kSlabCells);
+  std::vector<double> expect(ns, 0.0);
+  for (uint32_t i = 0; i < b->n_tables; ++i) {
+    const TableArgs &t = b->h_tabs[i];
+    const double rec = (double)(h_key_offsets[i + 1] - h_key_offsets[i]) * t.r;
+    if (rec == 0) continue;
+    const uint64_t c0 = t.base, c1 = (uint64_t)t.base + t.n_cells;
+    for (uint64_t sl = c0 / kSlabCells; sl * kSlabCells < c1; ++sl) {
+      const uint64_t a0 = sl * kSlabCells > c0 ? sl * kSlabCells : c0;
+      const uint64_t a1 = (sl + 1) * kSlabCells < c1 ? (sl + 1) * kSlabCells : c1;
+      expect[sl] += rec * (double)(a1 - a0) / (double)t.n_cells;
+    }
+  }
+  double mx = 0;
+  for (double e : expect) mx = e > mx ? e : mx;
+  const uint64_t cap = (uint64_t)(mx * 1.05) + 4096;
+  if (cap > 0xFFFFFFF0ull) return fail(PP_ERR_INVALID_ARG, "pp_batch_insert: too many keys for one call");
+  pp_status st = ensure_records(b, cap * ns, ns, s);
+  if (st != PP_OK) return st;
+  if (ns != b->n_slabs) {
+    b->n_slabs = ns;
+    b->smem_bin = bin_smem_bytes(b->k.nr, true, ns);
+    b->grid_bin = persistent_grid(b->k.bin, kBlock, b->smem_bin, b->opt.ctas_per_sm);
+  }
+  PP_CUDA(cudaMemsetAsync(b->bin_count, 0, ns * sizeof(u32), s));
+  PP_CUDA(cudaMemsetAsync(b->bin_overflow, 0, sizeof(u32), s));
+  ba = BinArgs{b->rec_key, b->rec_cell, b->rec_tab, b->bin_count, b->bin_overflow, (u32)cap, ns, direct_overflow};
+  Cell *cells = b->cells;
+  TableArgs t0{};
+  const TableArgs *tabs = b->tabs;
+  const Chunk *ch = b->ins_chunks;
+  const u64 *keys = reinterpret_cast<const u64 *>(d_keys);
+  u64 m = 0;
+  void *args[] = {&cells, &t0, &tabs, &ch, &nch, &keys, &m, &sign, &ba};
+  const int grid = nch < (u32)b->grid_bin ? (int)nch : b->grid_bin;
+  PP_CUDA(cudaLaunchKernel(b->k.bin, dim3(grid), dim3(kBlock), args, b->smem_bin, s));
+  return PP_OK;
+}
+
+// Pass 2: slab by slab (zero-filled first when building from scratch).
+static pp_status batch_apply_pass(pp_batch *b, BinArgs &ba, int sign, bool zero_fill, cudaStream_t s) {
+  Cell *cells = b->cells;
+  TableArgs t0{};
+  const TableArgs *tabs = b->tabs;
+  u32 slab = 0;
+  void *args[] = {&cells, &t0, &tabs, &ba, &slab, &sign};
+  for (slab = 0; slab < ba.n_slabs; ++slab) {
+    if (zero_fill) {
+      const uint64_t c0 = (uint64_t)slab * kSlabCells;
+      const uint64_t c1 = c0 + kSlabCells < b->total_cells ? c0 + kSlabCells : b->total_cells;
+      PP_CUDA(cudaMemsetAsync(b->cells + c0, 0, (c1 - c0) * sizeof(Cell), s));
+    }
+    PP_CUDA(cudaLaunchKernel(b->k.apply, dim3(b->grid_apply), dim3(kBlock), args, 0, s));
+  }
+  return PP_OK;
+}
+
+static void add_items(pp_batch *b, const uint64_t *h_key_offsets, int sign) {
   for (uint32_t i = 0; i < b->n_tables; ++i) {
     const uint64_t d = h_key_offsets[i + 1] - h_key_offsets[i];
     b->items[i] = sign > 0 ? b->items[i] + d : (b->items[i] >= d ? b->items[i] - d : 0);
   }
-  return PP_OK;
+}
+
+static pp_status batch_update(pp_batch *b, const uint64_t *d_keys, const uint64_t *h_key_offsets,
+                              int sign, void *stream) {
+  if (!b || !h_key_offsets) return fail(PP_ERR_INVALID_ARG, "pp_batch_insert: NULL argument");
+  cudaStream_t s = as_stream(stream);
+  u32 nch = 0;
+  uint64_t records = 0;
+  pp_status st = upload_chunks(b, h_key_offsets, s, &nch, &records);
+  if (st != PP_OK || nch == 0) return st;
+  if (!d_keys) return fail(PP_ERR_INVALID_ARG, "pp_batch_insert: NULL keys");
+  if (use_binned(b, records)) {
+    BinArgs ba;
+    st = batch_bin_pass(b, d_keys, h_key_offsets, nch, sign, 1, s, ba);
+    if (st == PP_OK) st = batch_apply_pass(b, ba, sign, false, s);
+  } else {
+    st = direct_update(b, d_keys, nch, sign, s);
+  }
+  if (st == PP_OK) add_items(b, h_key_offsets, sign);
+  return st;
 }
 
 pp_status pp_batch_insert(pp_batch *b, const uint64_t *d_keys, const uint64_t *h_key_offsets,
@@ -373,7 +582,39 @@ pp_status pp_batch_insert(pp_batch *b, const uint64_t *d_keys, const uint64_t *h
 
 pp_status pp_batch_delete(pp_batch *b, const uint64_t *d_keys, const uint64_t *h_key_offsets,
                           void *stream) {
+  if (b) b->had_deletes = true;
   return batch_update(b, d_keys, h_key_offsets, -1, stream);
+}
+
+pp_status pp_batch_build(pp_batch *b, const uint64_t *d_keys, const uint64_t *h_key_offsets, void *stream) {
+  if (!b || !h_key_offsets) return fail(PP_ERR_INVALID_ARG, "pp_batch_build: NULL argument");
+  cudaStream_t s = as_stream(stream);
+  for (auto &x : b->items) x = 0;
+  b->had_deletes = false;
+  u32 nch = 0;
+  uint64_t records = 0;
+  pp_status st = upload_chunks(b, h_key_offsets, s, &nch, &records);
+  if (st != PP_OK) return st;
+  if (nch && !d_keys) return fail(PP_ERR_INVALID_ARG, "pp_batch_build: NULL keys");
+  if (nch == 0 || !use_binned(b, records)) {
+    PP_CUDA(cudaMemsetAsync(b->cells, 0, b->total_cells * sizeof(Cell), s));
+    if (nch) st = direct_update(b, d_keys, nch, +1, s);
+  } else {
+    BinArgs ba;
+    st = batch_bin_pass(b, d_keys, h_key_offsets, nch, +1, 0, s, ba);
+    if (st != PP_OK) return st;
+    PP_CUDA(cudaMemcpyAsync(&b->h_ctl->more, b->bin_overflow, sizeof(u32), cudaMemcpyDeviceToHost, s));
+    PP_CUDA(cudaStreamSynchronize(s));
+    if (b->h_ctl->more) {
+      // a slab got more updates than its list holds: build the plain way
+      PP_CUDA(cudaMemsetAsync(b->cells, 0, b->total_cells * sizeof(Cell), s));
+      st = direct_update(b, d_keys, nch, +1, s);
+    } else {
+      st = batch_apply_pass(b, ba, +1, true, s);
+    }
+  }
+  if (st == PP_OK) add_items(b, h_key_offsets, +1);
+  return st;
 }
 
 pp_status pp_batch_decode(pp_batch *b, uint64_t *d_out_keys, const uint64_t *h_out_offsets,
@@ -407,6 +648,17 @@ pp_status pp_batch_decode(pp_batch *b, uint64_t *d_out_keys, const uint64_t *h_o
   memset(b->h_ctl, 0, sizeof(DecodeCtl));
   b->h_ctl->max_rounds = b->opt.max_rounds;
   b->h_ctl->stats_rounds = sr;
+  const bool want_bins = b->opt.binned == 1 || (b->opt.binned == 0 && b->total_cells >= (1ull << 21));
+  if (want_bins) {
+    pp_status st = ensure_round_bins(b, s);
+    if (st != PP_OK) return st;
+    PP_CUDA(cudaMemsetAsync(b->bin_count, 0, b->n_bins * sizeof(u32), s));
+  }
+  if (b->exec && (want_bins != b->binned_rounds || (want_bins && b->graph_gen != b->rec_gen))) {
+    cudaGraphExecDestroy(b->exec);
+    b->exec = nullptr;
+  }
+  b->binned_rounds = want_bins;
   PP_CUDA(cudaMemcpyAsync(b->ctl, b->h_ctl, sizeof(DecodeCtl), cudaMemcpyHostToDevice, s));
   u64 *out = reinterpret_cast<u64 *>(d_out_keys);
   if (b->opt.host_loop) {
@@ -414,8 +666,16 @@ pp_status pp_batch_decode(pp_batch *b, uint64_t *d_out_keys, const uint64_t *h_o
     fill(b, a, out);
     PP_CUDA(cudaLaunchKernel(b->k.scan, dim3(b->grid_scan), dim3(kBlock), a.scan_p, 0, s));
     for (;;) {
-      PP_CUDA(cudaLaunchKernel(b->k.peel, dim3(b->grid_peel), dim3(kBlock), a.peel_p, b->smem_peel, s));
-      PP_CUDA(cudaLaunchKernel(b->k.filter, dim3(b->grid_filter), dim3(kBlock), a.filter_p, 0, s));
+      if (b->binned_rounds) {
+        PP_CUDA(cudaLaunchKernel(b->k.claim, dim3(b->grid_claim), dim3(kBlock), a.claim_p, b->smem_claim, s));
+        PP_CUDA(cudaLaunchKernel(b->k.apply_round, dim3(b->grid_apply_round), dim3(kBlock), a.applyr_p,
+                                 b->smem_apply_round, s));
+        PP_CUDA(cudaLaunchKernel(b->k.filter, dim3(b->grid_filter), dim3(kBlock), a.filter_p, 0, s));
+        PP_CUDA(cudaLaunchKernel(bins_reset_kernel(), dim3(1), dim3(256), a.reset_p, 0, s));
+      } else {
+        PP_CUDA(cudaLaunchKernel(b->k.peel, dim3(b->grid_peel), dim3(kBlock), a.peel_p, b->smem_peel, s));
+        PP_CUDA(cudaLaunchKernel(b->k.filter, dim3(b->grid_filter), dim3(kBlock), a.filter_p, 0, s));
+      }
       PP_CUDA(cudaLaunchKernel(round_end_kernel(), dim3(1), dim3(32), a.end_p, 0, s));
       PP_CUDA(cudaMemcpyAsync(&b->h_ctl->more, &b->ctl->more, sizeof(u32), cudaMemcpyDeviceToHost, s));
       PP_CUDA(cudaStreamSynchronize(s));
@@ -428,6 +688,20 @@ pp_status pp_batch_decode(pp_batch *b, uint64_t *d_out_keys, const uint64_t *h_o
       b->graph_out = out;
     }
     PP_CUDA(cudaGraphLaunch(b->exec, s));
+  }
+  if (b->binned_rounds) {
+    // the binned rounds do not track emptied cells per table: count the residue
+    for (uint32_t i = 0; i < n; ++i) b->h_items[i] = b->items[i];
+    PP_CUDA(cudaMemcpyAsync((void *)b->bc.items, b->h_items, n * sizeof(u64), cudaMemcpyHostToDevice, s));
+    PP_CUDA(cudaMemsetAsync(b->bc.residual, 0, n * sizeof(u64), s));
+    BatchCounters bc = b->bc;
+    bc.skip_full = b->had_deletes ? 0u : 1u;
+    const Cell *cells = b->cells;
+    const Chunk *ch = b->scan_chunks;
+    u32 nch = b->n_scan_chunks;
+    void *args[] = {&cells, &ch, &nch, &bc};
+    PP_CUDA(cudaLaunchKernel(residual_kernel(), dim3(b->grid_scan), dim3(kBlock), args, 0, s));
+    PP_CUDA(cudaMemcpyAsync(b->h_residual, b->bc.residual, n * sizeof(u64), cudaMemcpyDeviceToHost, s));
   }
   PP_CUDA(cudaMemcpyAsync(b->h_ctl, b->ctl, sizeof(DecodeCtl), cudaMemcpyDeviceToHost, s));
   PP_CUDA(cudaMemcpyAsync(b->h_recovered, b->bc.recovered, n * sizeof(u64), cudaMemcpyDeviceToHost, s));
@@ -442,7 +716,7 @@ pp_status pp_batch_decode(pp_batch *b, uint64_t *d_out_keys, const uint64_t *h_o
     r.rounds = b->h_rounds[i];
     r.recovered = b->h_recovered[i];
     r.items_before = b->items[i];
-    r.residual_cells = b->h_nonempty[i] - b->h_emptied[i];
+    r.residual_cells = b->binned_rounds ? b->h_residual[i] : b->h_nonempty[i] - b->h_emptied[i];
     const uint32_t nc = r.rounds < r.round_cap ? r.rounds : r.round_cap;
     if (r.recovered_per_round) {
       for (uint32_t t = 0; t < nc; ++t)

@@ -52,6 +52,15 @@ struct __align__(16) TableArgs {
   u64 out_cap;             // batch: slots in that region
 };
 
+// Kernels are instantiated per rank R: R > 0 is a fixed r; R = 0 takes r at run
+// time (up to PP_MAX_R); R = -4 takes r at run time with r <= 4 (mixed r = 3 / 4
+// batches), sizing registers and shared memory for 4.
+template <int R>
+__host__ __device__ constexpr int nr_of() { return R > 0 ? R : (R < 0 ? -R : PP_MAX_R); }
+
+template <int R>
+__device__ __forceinline__ int rank_of(const TableArgs &T) { return R > 0 ? R : (int)T.r; }
+
 // The r cells of key x (one per sub-table).
 template <int R>
 __device__ __forceinline__ void cells_of(u64 x, const TableArgs &t, u32 (&c)[R]) {

@@ -32,15 +32,17 @@ static IbltKernels iblt_kernels_t() {
   }
   return {(const void *)k_insert<R, B>, (const void *)k_scan<R, B>, (const void *)k_peel<R, B>,
           (const void *)k_filter<R, B>, (const void *)k_bin<R, B>, (const void *)k_apply<R, B>,
-          (const void *)k_claim<R, B>, (const void *)k_apply_round<R, B>, R ? R : PP_MAX_R};
+          (const void *)k_claim<R, B>, (const void *)k_apply_round<R, B>, nr_of<R>()};
 }
 
-IbltKernels iblt_kernels(uint32_t r, bool batch) {
+IbltKernels iblt_kernels(int rank, bool batch) {
   if (batch) {
-    if (r == 3) return iblt_kernels_t<3, true>();
-    if (r == 4) return iblt_kernels_t<4, true>();
+    if (rank == 3) return iblt_kernels_t<3, true>();
+    if (rank == 4) return iblt_kernels_t<4, true>();
+    if (rank == -4) return iblt_kernels_t<-4, true>();
     return iblt_kernels_t<0, true>();
   }
+  const uint32_t r = (uint32_t)rank;
   if (r == 3) return iblt_kernels_t<3, false>();
   if (r == 4) return iblt_kernels_t<4, false>();
   return iblt_kernels_t<0, false>();
@@ -50,9 +52,11 @@ const void *round_end_kernel() { return (const void *)k_round_end; }
 
 const void *bins_reset_kernel() { return (const void *)k_bins_reset; }
 
+const void *residual_kernel() { return (const void *)k_residual; }
+
 size_t claim_smem_bytes(int nr, uint32_t n_bins) {
-  const size_t cap = (size_t)kBlock * nr;
-  return cap * 8 + (size_t)kBlock * 8 + cap * 4 * 3 + 3 * (size_t)n_bins * 4;
+  const size_t cap = (size_t)kClaimChunk * nr;
+  return cap * 8 + (size_t)kClaimChunk * 8 + cap * 4 * 3 + 3 * (size_t)n_bins * 4;
 }
 
 size_t apply_round_smem_bytes(bool batch, uint32_t n_bins) {
@@ -100,7 +104,7 @@ struct pp_iblt {
   uint32_t graph_gen = 0;  // rec_gen the instantiated graph was built with
   // binned decode rounds
   bool binned_rounds = false;
-  uint32_t n_bins = 0, bin_cap = 0;
+  uint32_t n_bins = 0, bin_cap = 0, bin_shift = 0;
   size_t smem_claim = 0, smem_apply_round = 0;
   int grid_claim = 0, grid_apply_round = 0;
 };
@@ -244,7 +248,7 @@ struct ResetArgs {
 
 void fill_round_args(pp_iblt *t, ClaimArgs &ca, ApplyRArgs &aa, ResetArgs &ra) {
   BatchCounters bc{};
-  RoundBins rb{t->rec_key, t->rec_cell, nullptr, t->bin_count, t->bin_cap, t->n_bins};
+  RoundBins rb{t->rec_key, t->rec_cell, nullptr, t->bin_count, t->bin_cap, t->n_bins, t->bin_shift, 0};
   ca = ClaimArgs{t->cells, t->args, nullptr, t->fkey, t->fcell, nullptr, t->bitmap, rb, t->cand, nullptr,
                  nullptr, t->ctl, bc, {}};
   aa = ApplyRArgs{t->cells, t->args, nullptr, rb, t->cand, nullptr, t->ctl, bc, {}};
@@ -469,13 +473,15 @@ pp_status bin_pass(pp_iblt *t, const uint64_t *d_keys, uint64_t m, int sign, int
 // updates of half its cells' worth of recovered keys (a round recovers far
 // fewer; a fuller bin applies the excess directly).
 pp_status ensure_round_bins(pp_iblt *t, cudaStream_t s) {
-  const uint32_t nb = (uint32_t)((t->n + (1u << kRoundShift) - 1) >> kRoundShift);
-  const uint64_t span = t->n < (1ull << kRoundShift) ? t->n : (1ull << kRoundShift);
+  const u32 shift = round_bin_shift(t->n);
+  const uint32_t nb = (uint32_t)((t->n + (1ull << shift) - 1) >> shift);
+  const uint64_t span = t->n < (1ull << shift) ? t->n : (1ull << shift);
   const uint64_t cap = (uint64_t)((double)t->r * (double)span * 0.525) + 4096;
   pp_status st = ensure_records(t, cap * nb, nb, s);
   if (st != PP_OK) return st;
   t->n_bins = nb;
   t->bin_cap = (uint32_t)cap;
+  t->bin_shift = shift;
   t->smem_claim = claim_smem_bytes(t->k.nr, nb);
   t->smem_apply_round = apply_round_smem_bytes(false, nb);
   t->grid_claim = persistent_grid(t->k.claim, kBlock, t->smem_claim, t->opt.ctas_per_sm);
@@ -528,7 +534,7 @@ pp_status pp_iblt_create(pp_iblt **out, uint64_t n_cells, uint32_t r, uint64_t s
   t->seed = seed;
   t->opt = resolve_options(opt);
   make_table_args(t->args, n_cells, r, seed, 0);
-  t->k = iblt_kernels(r, false);
+  t->k = iblt_kernels((int)r, false);
   t->smem_peel = peel_smem_bytes(t->k.nr, false);
   const uint64_t words = (n_cells + 31) / 32 + 1;
   const uint32_t mr = t->opt.max_rounds;

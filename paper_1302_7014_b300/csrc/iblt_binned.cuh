@@ -20,22 +20,6 @@
 
 namespace pp {
 
-constexpr int kSlabShift = 21;               // 2^21 cells = 64 MB per slab
-constexpr u32 kSlabCells = 1u << kSlabShift;
-constexpr int kBinKeys = kBlock;             // keys per block per partition step
-
-// Record lists of a binned build: slab s owns records [s*cap, s*cap + min(count[s], cap)).
-struct BinArgs {
-  u64 *rec_key;
-  u32 *rec_cell;   // global cell id
-  u32 *rec_tab;    // table id (batched builds)
-  u32 *count;      // records routed to each slab (may exceed cap)
-  u32 *overflow;   // set to 1 when a record did not fit and could not be applied directly
-  u32 cap;
-  u32 n_slabs;
-  int direct_overflow;  // 1: apply records that do not fit right away (plain insert)
-};
-
 template <int R>
 __device__ __forceinline__ void apply_touch(Cell *cells, u32 c, u64 x, u64 cx, int sign) {
   Cell *p = cells + c;
@@ -51,7 +35,7 @@ __global__ void __launch_bounds__(kBlock) k_bin(Cell *__restrict__ cells, const 
                                                 const TableArgs *__restrict__ tabs,
                                                 const Chunk *__restrict__ chunks, u32 n_chunks,
                                                 const u64 *__restrict__ keys, u64 m, int sign, BinArgs b) {
-  constexpr int NR = R ? R : PP_MAX_R;
+  constexpr int NR = nr_of<R>();
   constexpr int CAP = kBinKeys * NR;
   extern __shared__ __align__(16) unsigned char smem[];
   u64 *s_key = reinterpret_cast<u64 *>(smem);                 // CAP
@@ -78,21 +62,26 @@ __global__ void __launch_bounds__(kBlock) k_bin(Cell *__restrict__ cells, const 
       k1 = k0 + kBinKeys < m ? k0 + kBinKeys : m;
     }
     const TableArgs &T = BATCH ? tabs[tb] : tab0;
-    const int r = R ? R : (int)T.r;
+    const int r = rank_of<R>(T);
     // a batch chunk may hold more than kBinKeys keys: walk it in steps
     for (u64 s0 = k0; s0 < k1; s0 += kBinKeys) {
       for (u32 i = tid; i < ns; i += kBlock) s_hist[i] = 0;
       __syncthreads();
-      const u64 ki = s0 + tid;
-      const bool valid = ki < k1;
-      u64 x = 0;
-      u32 c[NR], bin[NR], rank[NR];
-      if (valid) x = __ldcs(keys + ki);
-      cells_of<NR>(x, T, c);
+      u64 x[kBinItems];
+      u32 c[kBinItems][NR], rank[kBinItems][NR];
+      bool valid[kBinItems];
 #pragma unroll
-      for (int j = 0; j < NR; ++j) {
-        bin[j] = c[j] >> kSlabShift;
-        rank[j] = (valid && j < r) ? atomicAdd(s_hist + bin[j], 1u) : 0u;
+      for (int it = 0; it < kBinItems; ++it) {
+        const u64 ki = s0 + (u64)it * kBlock + tid;
+        valid[it] = ki < k1;
+        x[it] = valid[it] ? __ldcs(keys + ki) : 0ull;
+      }
+#pragma unroll
+      for (int it = 0; it < kBinItems; ++it) {
+        cells_of<NR>(x[it], T, c[it]);
+#pragma unroll
+        for (int j = 0; j < NR; ++j)
+          rank[it][j] = (valid[it] && j < r) ? atomicAdd(s_hist + (c[it][j] >> kSlabShift), 1u) : 0u;
       }
       __syncthreads();
       // exclusive scan of the histogram: thread t owns slabs [t*per, (t+1)*per)
@@ -100,7 +89,6 @@ __global__ void __launch_bounds__(kBlock) k_bin(Cell *__restrict__ cells, const 
       const u32 lo = tid * per, hi = lo + per < ns ? lo + per : ns;
       u32 own = 0;
       for (u32 i = lo; i < hi; ++i) own += s_hist[i];
-      // block-wide exclusive scan of per-thread totals
       u32 inc = own;
 #pragma unroll
       for (int o = 1; o < 32; o <<= 1) {
@@ -129,15 +117,19 @@ __global__ void __launch_bounds__(kBlock) k_bin(Cell *__restrict__ cells, const 
         run += h;
       }
       __syncthreads();
-      if (valid) {
 #pragma unroll
-        for (int j = 0; j < NR; ++j) {
-          if (j < r) {
-            const u32 pos = s_scan[bin[j]] + rank[j];
-            s_key[pos] = x;
-            s_cell[pos] = c[j];
-            s_bin[pos] = bin[j];
-            if (BATCH) s_tab[pos] = tb;
+      for (int it = 0; it < kBinItems; ++it) {
+        if (valid[it]) {
+#pragma unroll
+          for (int j = 0; j < NR; ++j) {
+            if (j < r) {
+              const u32 bn = c[it][j] >> kSlabShift;
+              const u32 pos = s_scan[bn] + rank[it][j];
+              s_key[pos] = x[it];
+              s_cell[pos] = c[it][j];
+              s_bin[pos] = bn;
+              if (BATCH) s_tab[pos] = tb;
+            }
           }
         }
       }
@@ -154,7 +146,7 @@ __global__ void __launch_bounds__(kBlock) k_bin(Cell *__restrict__ cells, const 
         } else if (b.direct_overflow) {
           const TableArgs &TT = BATCH ? tabs[s_tab[p]] : tab0;
           const u64 xx = s_key[p];
-          apply_touch<R>(cells, s_cell[p], xx, mix64(xx ^ TT.seed[R ? R : (int)TT.r]), sign);
+          apply_touch<R>(cells, s_cell[p], xx, mix64(xx ^ TT.seed[rank_of<R>(TT)]), sign);
         } else {
           *b.overflow = 1u;
         }
@@ -177,7 +169,7 @@ __global__ void __launch_bounds__(kBlock) k_apply(Cell *__restrict__ cells, cons
     const u64 x = __ldcs(b.rec_key + base + i);
     const u32 c = __ldcs(b.rec_cell + base + i);
     const TableArgs &T = BATCH ? tabs[__ldcs(b.rec_tab + base + i)] : tab0;
-    apply_touch<R>(cells, c, x, mix64(x ^ T.seed[R ? R : (int)T.r]), sign);
+    apply_touch<R>(cells, c, x, mix64(x ^ T.seed[rank_of<R>(T)]), sign);
   }
 }
 

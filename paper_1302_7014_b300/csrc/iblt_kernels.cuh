@@ -23,8 +23,7 @@
 
 namespace pp {
 
-template <int R>
-__device__ __forceinline__ int rank_of(const TableArgs &T) { return R ? R : (int)T.r; }
+
 
 // --------------------------------------------------------------------------
 // Build (Sec. 6 "Motivation"; one thread per key as in Sec. 6 "Implementation
@@ -35,7 +34,7 @@ __global__ void __launch_bounds__(kBlock) k_insert(Cell *__restrict__ cells, con
                                                    const TableArgs *__restrict__ tabs,
                                                    const Chunk *__restrict__ chunks, u32 n_chunks,
                                                    const u64 *__restrict__ keys, u64 m, int sign) {
-  constexpr int NR = R ? R : PP_MAX_R;
+  constexpr int NR = nr_of<R>();
   if (!BATCH) {
     const int r = rank_of<R>(tab0);
     const u64 stride = (u64)gridDim.x * blockDim.x;
@@ -177,7 +176,7 @@ __global__ void __launch_bounds__(kBlock) k_peel(Cell *__restrict__ cells, const
                                                  u32 *__restrict__ cand, u32 *__restrict__ ctab,
                                                  u64 *__restrict__ bout, DecodeCtl *__restrict__ ctl,
                                                  BatchCounters bc) {
-  constexpr int NR = R ? R : PP_MAX_R;
+  constexpr int NR = nr_of<R>();
   constexpr int CH = kBlock * kPeelItems;
   extern __shared__ __align__(16) unsigned char smem[];
   u64 *s_out = reinterpret_cast<u64 *>(smem);                    // CH      (plain)
@@ -346,12 +345,18 @@ __global__ void __launch_bounds__(kBlock) k_filter(const Cell *__restrict__ cell
       if (valid) {
         c = __ldcs(cand + i);
         if (BATCH) tb = __ldcs(ctab + i);
-        const TableArgs &T = BATCH ? tabs[tb] : tab0;
         const uint4 a = __ldcg(reinterpret_cast<const uint4 *>(cells + c));
         const uint4 b = __ldcg(reinterpret_cast<const uint4 *>(cells + c) + 1);
         key = ((u64)a.y << 32) | a.x;
         const u64 chk = ((u64)a.w << 32) | a.z;
-        pure = (int)b.x == 1 && chk == mix64(key ^ T.seed[rank_of<R>(T)]);
+        u64 seed_chk;
+        if (BATCH && bc.chk_seed) {
+          seed_chk = bc.chk_seed[tb];
+        } else {
+          const TableArgs &T = BATCH ? tabs[tb] : tab0;
+          seed_chk = T.seed[rank_of<R>(T)];
+        }
+        pure = (int)b.x == 1 && chk == mix64(key ^ seed_chk);
         if (pure) atomicOr(bitmap + (c >> 5), 1u << (c & 31u));
       }
       const u32 p = warp_reserve<u32>(pure, &s_n);

@@ -139,7 +139,7 @@ extern "C" pp_status pp_iblt_decode_noalloc(pp_cell *d_cells, uint64_t n_cells, 
 
   TableArgs tab0;
   make_table_args(tab0, n_cells, r, seed, 0);
-  const IbltKernels k = iblt_kernels(r, false);
+  const IbltKernels k = iblt_kernels((int)r, false);
   const size_t smem_peel = peel_smem_bytes(k.nr, false);
   const int grid_scan = persistent_grid(k.scan, kBlock, 0, 8);
   const int grid_peel = persistent_grid(k.peel, kBlock, smem_peel, 8);

@@ -23,20 +23,6 @@
 
 namespace pp {
 
-constexpr int kRoundShift = 19;            // 2^19 cells per bin
-constexpr int kApplyPer = 4;               // records per thread per grab
-constexpr int kApplyChunk = kBlock * kApplyPer;
-
-// Record lists of one round: bin b owns records [b*cap, b*cap + min(count[b], cap)).
-struct RoundBins {
-  u64 *rec_key;
-  u32 *rec_cell;
-  u32 *rec_tab;   // batch only
-  u32 *count;
-  u32 cap;
-  u32 n_bins;
-};
-
 __device__ __forceinline__ int remove_key(Cell *cells, u32 c, u64 x, u64 cx) {
   Cell *p = cells + c;
   const int old = atomicSub(&p->count, 1);
@@ -45,8 +31,9 @@ __device__ __forceinline__ int remove_key(Cell *cells, u32 c, u64 x, u64 cx) {
   return old;
 }
 
-// Shared memory of k_claim: staged records (4 arrays of kBlock*NR) + 3 * n_bins u32
-// + the plain decode's output staging (kBlock u64).
+// Shared memory of k_claim: staged records (4 arrays of kClaimChunk*NR) + 3 *
+// n_bins u32 + the plain decode's output staging (kClaimChunk u64).
+
 template <int R, bool BATCH>
 __global__ void __launch_bounds__(kBlock) k_claim(Cell *__restrict__ cells, const TableArgs tab0,
                                                   const TableArgs *__restrict__ tabs,
@@ -55,12 +42,12 @@ __global__ void __launch_bounds__(kBlock) k_claim(Cell *__restrict__ cells, cons
                                                   RoundBins rb, u32 *__restrict__ cand, u32 *__restrict__ ctab,
                                                   u64 *__restrict__ bout, DecodeCtl *__restrict__ ctl,
                                                   BatchCounters bc) {
-  constexpr int NR = R ? R : PP_MAX_R;
-  constexpr int CAP = kBlock * NR;
+  constexpr int NR = nr_of<R>();
+  constexpr int CAP = kClaimChunk * NR;
   extern __shared__ __align__(16) unsigned char smem[];
   u64 *s_key = reinterpret_cast<u64 *>(smem);       // CAP
-  u64 *s_out = s_key + CAP;                         // kBlock (plain)
-  u32 *s_cell = reinterpret_cast<u32 *>(s_out + kBlock);
+  u64 *s_out = s_key + CAP;                         // kClaimChunk (plain)
+  u32 *s_cell = reinterpret_cast<u32 *>(s_out + kClaimChunk);
   u32 *s_bin = s_cell + CAP;
   u32 *s_tab = s_bin + CAP;
   u32 *s_hist = s_tab + CAP;                        // n_bins
@@ -78,67 +65,80 @@ __global__ void __launch_bounds__(kBlock) k_claim(Cell *__restrict__ cells, cons
   const u32 stats_rounds = BATCH ? ctl->stats_rounds : 0;
   u32 flags = 0;
   u64 ovf_emptied = 0;
-  for (u64 c0 = (u64)blockIdx.x * kBlock; c0 < n; c0 += (u64)gridDim.x * kBlock) {
+  for (u64 c0 = (u64)blockIdx.x * kClaimChunk; c0 < n; c0 += (u64)gridDim.x * kClaimChunk) {
     for (u32 i = tid; i < nb; i += kBlock) s_hist[i] = 0;
     if (tid == 0) s_nout = 0;
     __syncthreads();
-    const u64 i = c0 + tid;
-    const bool valid = i < n;
-    u64 x = 0;
-    u32 c = 0, tb = 0;
-    if (valid) {
-      x = __ldcs(fkey + i);
-      c = __ldcs(fcell + i);
-      if (BATCH) tb = __ldcs(ftab + i);
-    }
-    const TableArgs &T = BATCH ? tabs[tb] : tab0;
-    const int r = R ? R : (int)T.r;
-    u32 cj[NR];
-    cells_of<NR>(x, T, cj);
-    int jstar = -1;
+    u64 x[kClaimItems];
+    u32 cj[kClaimItems][NR], rank[kClaimItems][NR], tb[kClaimItems];
+    bool win[kClaimItems];
+    int rr[kClaimItems];
+    // load every entry of this thread first (independent loads in flight)
+    u32 c[kClaimItems];
 #pragma unroll
-    for (int j = NR - 1; j >= 0; --j)
-      if (j < r && cj[j] == c) jstar = j;
-    bool win = valid;
-    if (valid && jstar < 0) {
-      flags |= FLAG_INTERNAL;
-      win = false;
+    for (int it = 0; it < kClaimItems; ++it) {
+      const u64 i = c0 + (u64)it * kBlock + tid;
+      const bool valid = i < n;
+      x[it] = valid ? __ldcs(fkey + i) : 0ull;
+      c[it] = valid ? __ldcs(fcell + i) : 0u;
+      tb[it] = (BATCH && valid) ? __ldcs(ftab + i) : 0u;
+      win[it] = valid;
     }
 #pragma unroll
-    for (int j = 0; j < NR - 1; ++j) {
-      if (win && j < jstar) {
-        const u32 w = __ldcg(bitmap + (cj[j] >> 5));
-        if ((w >> (cj[j] & 31u)) & 1u) win = false;
-      }
-    }
-    // recovered key
-    if constexpr (!BATCH) {
-      const u32 p = warp_reserve<u32>(win, &s_nout);
-      if (win) s_out[p] = x;
-    } else {
-      const u32 label = win ? tb : 0xffffffffu;
-      const u32 grp = __match_any_sync(kFull, label);
-      const int leader = __ffs(grp) - 1;
-      const u32 gsize = __popc(grp);
-      u64 base = 0;
-      if (win && (int)lane_id() == leader) {
-        const u32 local = round + 1 - T.start_round;
-        base = atomicAdd(bc.recovered + tb, (u64)gsize);
-        atomicMax(bc.rounds + tb, local);
-        if (local <= stats_rounds) atomicAdd(bc.round_rec + (u64)tb * stats_rounds + (local - 1), gsize);
-      }
-      base = __shfl_sync(kFull, base, leader);
-      if (win) {
-        const u64 slot = base + __popc(grp & lanemask_lt());
-        if (slot < T.out_cap) out[T.out_base + slot] = x;
-        else flags |= FLAG_CAPACITY;
-      }
-    }
-    // update records, counted per bin
-    u32 rank[NR];
+    for (int it = 0; it < kClaimItems; ++it) {
+      const TableArgs &T = BATCH ? tabs[tb[it]] : tab0;
+      const int r = rank_of<R>(T);
+      rr[it] = r;
+      cells_of<NR>(x[it], T, cj[it]);
+      int jstar = -1;
 #pragma unroll
-    for (int j = 0; j < NR; ++j)
-      rank[j] = (win && j < r) ? atomicAdd(s_hist + (cj[j] >> kRoundShift), 1u) : 0u;
+      for (int j = NR - 1; j >= 0; --j)
+        if (j < r && cj[it][j] == c[it]) jstar = j;
+      if (win[it] && jstar < 0) {
+        flags |= FLAG_INTERNAL;
+        win[it] = false;
+      }
+      // the lowest-index cell of x that was pure at the round's start wins
+#pragma unroll
+      for (int j = 0; j < NR - 1; ++j) {
+        if (win[it] && j < jstar) {
+          const u32 w = __ldcg(bitmap + (cj[it][j] >> 5));
+          if ((w >> (cj[it][j] & 31u)) & 1u) win[it] = false;
+        }
+      }
+    }
+#pragma unroll
+    for (int it = 0; it < kClaimItems; ++it) {
+      // recovered key
+      if constexpr (!BATCH) {
+        const u32 p = warp_reserve<u32>(win[it], &s_nout);
+        if (win[it]) s_out[p] = x[it];
+      } else {
+        const TableArgs &T = tabs[tb[it]];
+        const u32 label = win[it] ? tb[it] : 0xffffffffu;
+        const u32 grp = __match_any_sync(kFull, label);
+        const int leader = __ffs(grp) - 1;
+        const u32 gsize = __popc(grp);
+        u64 base = 0;
+        if (win[it] && (int)lane_id() == leader) {
+          const u32 local = round + 1 - T.start_round;
+          base = atomicAdd(bc.recovered + tb[it], (u64)gsize);
+          atomicMax(bc.rounds + tb[it], local);
+          if (local <= stats_rounds)
+            atomicAdd(bc.round_rec + (u64)tb[it] * stats_rounds + (local - 1), gsize);
+        }
+        base = __shfl_sync(kFull, base, leader);
+        if (win[it]) {
+          const u64 slot = base + __popc(grp & lanemask_lt());
+          if (slot < T.out_cap) out[T.out_base + slot] = x[it];
+          else flags |= FLAG_CAPACITY;
+        }
+      }
+      // update records, counted per bin
+#pragma unroll
+      for (int j = 0; j < NR; ++j)
+        rank[it][j] = (win[it] && j < rr[it]) ? atomicAdd(s_hist + (cj[it][j] >> rb.shift), 1u) : 0u;
+    }
     __syncthreads();
     // exclusive scan of the histogram: thread t owns bins [t*per, (t+1)*per)
     const u32 per = (nb + kBlock - 1) / kBlock;
@@ -174,16 +174,19 @@ __global__ void __launch_bounds__(kBlock) k_claim(Cell *__restrict__ cells, cons
       run += h;
     }
     __syncthreads();
-    if (win) {
 #pragma unroll
-      for (int j = 0; j < NR; ++j) {
-        if (j < r) {
-          const u32 bn = cj[j] >> kRoundShift;
-          const u32 pos = s_scan[bn] + rank[j];
-          s_key[pos] = x;
-          s_cell[pos] = cj[j];
-          s_bin[pos] = bn;
-          if (BATCH) s_tab[pos] = tb;
+    for (int it = 0; it < kClaimItems; ++it) {
+      if (win[it]) {
+#pragma unroll
+        for (int j = 0; j < NR; ++j) {
+          if (j < rr[it]) {
+            const u32 bn = cj[it][j] >> rb.shift;
+            const u32 pos = s_scan[bn] + rank[it][j];
+            s_key[pos] = x[it];
+            s_cell[pos] = cj[it][j];
+            s_bin[pos] = bn;
+            if (BATCH) s_tab[pos] = tb[it];
+          }
         }
       }
     }
@@ -200,19 +203,16 @@ __global__ void __launch_bounds__(kBlock) k_claim(Cell *__restrict__ cells, cons
       } else {
         // the bin is full: apply this update right away (updates commute)
         const u32 t2 = BATCH ? s_tab[p] : 0u;
-        const TableArgs &TT = BATCH ? tabs[t2] : tab0;
+        const u64 seed_chk = BATCH ? bc.chk_seed[t2] : tab0.seed[rank_of<R>(tab0)];
         const u64 xx = s_key[p];
         const u32 cc = s_cell[p];
-        const int old = remove_key(cells, cc, xx, mix64(xx ^ TT.seed[R ? R : (int)TT.r]));
+        const int old = remove_key(cells, cc, xx, mix64(xx ^ seed_chk));
         if (old == 2) {
           const u32 q = atomicAdd(&ctl->n_cand, 1u);
           cand[q] = cc;
           if (BATCH) ctab[q] = t2;
         }
-        if (old == 1) {
-          if (BATCH) atomicAdd(bc.emptied + t2, 1ull);
-          else ++ovf_emptied;
-        }
+        if (!BATCH && old == 1) ++ovf_emptied;
       }
     }
     if constexpr (!BATCH) {
@@ -312,8 +312,13 @@ __global__ void __launch_bounds__(kBlock) k_apply_round(Cell *__restrict__ cells
         const u64 x = __ldcs(rb.rec_key + base + i);
         c = __ldcs(rb.rec_cell + base + i);
         if (BATCH) tb = __ldcs(rb.rec_tab + base + i);
-        const TableArgs &T = BATCH ? tabs[tb] : tab0;
-        old = remove_key(cells, c, x, mix64(x ^ T.seed[R ? R : (int)T.r]));
+        u64 seed_chk;
+        if (BATCH) {
+          seed_chk = bc.chk_seed[tb];
+        } else {
+          seed_chk = tab0.seed[rank_of<R>(tab0)];
+        }
+        old = remove_key(cells, c, x, mix64(x ^ seed_chk));
       }
       const bool push = old == 2;
       const u32 q = warp_reserve<u32>(push, &s_ncand);
@@ -321,14 +326,8 @@ __global__ void __launch_bounds__(kBlock) k_apply_round(Cell *__restrict__ cells
         s_cand[q] = c;
         if (BATCH) s_ctab[q] = tb;
       }
-      if constexpr (BATCH) {
-        const u32 e = old == 1 ? 1u : 0u;
-        const u32 grp = __match_any_sync(kFull, e ? tb : 0xffffffffu);
-        const u32 ge = __reduce_add_sync(grp, e);
-        if (e && (int)lane_id() == __ffs(grp) - 1) atomicAdd(bc.emptied + tb, (u64)ge);
-      } else {
-        emptied += old == 1;
-      }
+      // batched decodes count their residue with k_residual afterwards
+      if (!BATCH) emptied += old == 1;
     }
     __syncthreads();
     const u32 nc = s_ncand;
@@ -347,8 +346,25 @@ __global__ void __launch_bounds__(kBlock) k_apply_round(Cell *__restrict__ cells
   }
 }
 
+// Residue of a batched binned decode: non-empty cells per table, one chunk of
+// one table per step (tables that recovered every key and saw no deletion are
+// empty by construction and skipped).
+__global__ void __launch_bounds__(kBlock) k_residual(const Cell *__restrict__ cells,
+                                                     const Chunk *__restrict__ chunks, u32 n_chunks,
+                                                     BatchCounters bc) {
+  __shared__ u64 s_red[kBlock / 32];
+  for (u32 ch = blockIdx.x; ch < n_chunks; ch += gridDim.x) {
+    const Chunk k = chunks[ch];
+    if (bc.skip_full && bc.recovered[k.table] >= bc.items[k.table]) continue;  // uniform per block
+    u64 nz = 0;
+    for (u32 c = k.begin + threadIdx.x; c < k.end; c += kBlock) nz += cells[c].count != 0;
+    const u64 t = block_sum<u64, kBlock>(nz, s_red);
+    if (threadIdx.x == 0 && t) atomicAdd(bc.residual + k.table, t);
+  }
+}
+
 // End of a binned round: clears the bins and the apply work counter for the
-// next round, then does what k_round_end does.
+// next round.
 __global__ void k_bins_reset(RoundBins rb, DecodeCtl *__restrict__ ctl) {
   for (u32 i = threadIdx.x; i < rb.n_bins; i += blockDim.x) rb.count[i] = 0;
   if (threadIdx.x == 0) ctl->apply_next = 0;

@@ -46,6 +46,11 @@ struct BatchCounters {
   u32 *rounds;         // per table: last round that recovered a key
   u32 *round_rec;      // per table x stats_rounds: keys recovered per round
   u32 *live;           // per table: entries it has in the frontier being built (or NULL)
+  const u64 *chk_seed; // per table: checksum seed (or NULL: read it from TableArgs)
+  u64 *residual;       // per table: non-empty cells counted after a binned decode
+  const u64 *items;    // per table: keys before the decode (residual scan skips full decodes)
+  u32 skip_full;       // 1: tables with every key recovered have no residue to count
+  u32 pad;
 };
 
 // A contiguous range of one table's cells or keys.
@@ -55,6 +60,53 @@ struct Chunk {
   u32 end;
 };
 
+// Slab-binned build (iblt_binned.cuh).
+constexpr int kSlabShift = 21;               // 2^21 cells = 64 MB per slab
+constexpr u32 kSlabCells = 1u << kSlabShift;
+constexpr int kBinItems = 4;                 // keys per thread per partition step
+constexpr int kBinKeys = kBlock * kBinItems; // keys per block per partition step
+
+// Record lists of a binned build: slab s owns records [s*cap, s*cap + min(count[s], cap)).
+struct BinArgs {
+  u64 *rec_key;
+  u32 *rec_cell;   // global cell id
+  u32 *rec_tab;    // table id (batched builds)
+  u32 *count;      // records routed to each slab (may exceed cap)
+  u32 *overflow;   // set to 1 when a record did not fit and could not be applied directly
+  u32 cap;
+  u32 n_slabs;
+  int direct_overflow;  // 1: apply records that do not fit right away (plain insert)
+};
+
+// Binned decode rounds (iblt_rounds.cuh).
+constexpr int kRoundShiftMin = 19;         // bins hold at least 2^19 cells
+constexpr u32 kMaxRoundBins = 128;         // ... and there are at most this many
+constexpr int kApplyPer = 4;               // records per thread per grab
+constexpr int kApplyChunk = kBlock * kApplyPer;
+
+// Record lists of one round: bin b owns records [b*cap, b*cap + min(count[b], cap)).
+struct RoundBins {
+  u64 *rec_key;
+  u32 *rec_cell;
+  u32 *rec_tab;   // batch only
+  u32 *count;
+  u32 cap;
+  u32 n_bins;
+  u32 shift;      // bin of cell c = c >> shift
+  u32 pad;
+};
+
+// Bin shift for a table (or arena) of n cells: bins of 2^19 cells or more, at
+// most kMaxRoundBins of them (few bins keep each block's runs long).
+inline u32 round_bin_shift(uint64_t n) {
+  u32 sh = kRoundShiftMin;
+  while ((n + (1ull << sh) - 1) >> sh > kMaxRoundBins) ++sh;
+  return sh;
+}
+
+constexpr int kClaimItems = 4;                  // frontier entries per thread per chunk
+constexpr int kClaimChunk = kBlock * kClaimItems;
+
 // Entry points of one instantiation of the IBLT kernels (plain or batched).
 struct IbltKernels {
   const void *insert, *scan, *peel, *filter;
@@ -63,8 +115,9 @@ struct IbltKernels {
   int nr;  // compile-time rank (PP_MAX_R for the generic instance)
 };
 
-// The kernel set for rank r (specialised for r = 3 and r = 4).
-IbltKernels iblt_kernels(uint32_t r, bool batch);
+// The kernel set for a rank code: 3 or 4 = that r; -4 = any r <= 4 (batched
+// kernels only); 0 = any r up to PP_MAX_R.
+IbltKernels iblt_kernels(int rank, bool batch);
 
 // Dynamic shared memory of the peel kernel.
 size_t peel_smem_bytes(int nr, bool batch);
@@ -78,6 +131,9 @@ size_t apply_round_smem_bytes(bool batch, uint32_t n_bins);
 
 // The bin-reset kernel that ends a binned round.
 const void *bins_reset_kernel();
+
+// The residue counter of batched binned decodes (k_residual).
+const void *residual_kernel();
 
 // The round_end kernel (one thread; records a round and decides on the next).
 const void *round_end_kernel();

@@ -497,7 +497,7 @@ pp_status pp_server_start(pp_server **out, const pp_server_config *cfg, const pp
     delete s;
     return cuda_fail(e, "cudaSetDevice", __FILE__, __LINE__);
   }
-  s->k = iblt_kernels(cfg->r, true);
+  s->k = iblt_kernels((int)cfg->r, true);
   s->smem_peel = peel_smem_bytes(s->k.nr, true);
   pp_status st = alloc_server(s);
   if (st != PP_OK) {

@@ -144,3 +144,67 @@ def test_empty_tables_in_batch(ppb):
     b, keys, ooff, res, got = run_batch(pp, bm, specs)
     check_against_oracle(specs, keys, ooff, res, got, b)
     assert res.rounds[0] == 0 and res.rounds[2] == 0
+
+
+@pytest.mark.parametrize("rs", [(3, 4), (2, 3, 5, 6)], ids=["r3-4", "r2-6"])
+def test_binned_batch_build_and_rounds(ppb, rs):
+    """Slab-binned build and binned rounds over the arena (forced on), mixed ranks."""
+    pp, bm = ppb
+    specs = _specs(50, 77 + len(rs), rs=rs, lo=10, hi=17, c_lo=0.5, c_hi=0.95)
+    n_cells = [s[0] for s in specs]
+    keys = [ppgen.distinct_keys(ppgen.edges_from_c(s[2], s[0]), s[4]) for s in specs]
+    koff = np.concatenate([[0], np.cumsum([k.size for k in keys])]).astype(np.uint64)
+    dk = torch.from_numpy(np.concatenate(keys).view(np.int64)).cuda()
+    b = bm.Batch(n_cells, [s[1] for s in specs], [s[3] for s in specs], pp.options(binned=1))
+    b.insert(torch.from_numpy(ppgen.distinct_keys(int(koff[-1]), 3).view(np.int64)).cuda(), koff)  # junk
+    b.build(dk, koff)                       # must wipe the junk
+    for i in range(0, len(specs), 5):
+        ot = oracle.IBLT(specs[i][0], specs[i][1], specs[i][3])
+        ot.insert(keys[i])
+        cells = b.cells(i)
+        assert (cells["count"].astype(np.int64) == ot.count).all()
+        assert (cells["key_xor"] == ot.keyx).all() and (cells["chk_xor"] == ot.chkx).all()
+    out = torch.full((int(koff[-1]),), -1, dtype=torch.int64, device="cuda")
+    res = b.decode(out, koff)
+    check_against_oracle(specs, keys, koff, res, out.cpu().numpy().view(np.uint64), b, cells_every=3)
+    # incremental insert + delete through the binned path
+    b.clear()
+    b.insert(dk, koff)
+    dele = [k[::4] for k in keys]
+    doff = np.concatenate([[0], np.cumsum([d.size for d in dele])]).astype(np.uint64)
+    b.delete(torch.from_numpy(np.concatenate(dele).view(np.int64)).cuda(), doff)
+    for i in range(0, len(specs), 7):
+        ot = oracle.IBLT(specs[i][0], specs[i][1], specs[i][3])
+        ot.insert(keys[i])
+        ot.insert(dele[i], sign=-1)
+        cells = b.cells(i)
+        assert (cells["count"].astype(np.int64) == ot.count).all()
+        assert (cells["key_xor"] == ot.keyx).all()
+
+
+def test_binned_batch_decode_after_deletions(ppb):
+    """Residue counted by the scan (no shortcut once keys were deleted)."""
+    pp, bm = ppb
+    specs = _specs(30, 91, rs=(3, 4), lo=10, hi=15, c_lo=0.6, c_hi=1.0)
+    keys = [ppgen.distinct_keys(ppgen.edges_from_c(s[2], s[0]), s[4]) for s in specs]
+    koff = np.concatenate([[0], np.cumsum([k.size for k in keys])]).astype(np.uint64)
+    b = bm.Batch([s[0] for s in specs], [s[1] for s in specs], [s[3] for s in specs], pp.options(binned=1))
+    b.insert(torch.from_numpy(np.concatenate(keys).view(np.int64)).cuda(), koff)
+    dele = [k[::3] for k in keys]
+    doff = np.concatenate([[0], np.cumsum([d.size for d in dele])]).astype(np.uint64)
+    b.delete(torch.from_numpy(np.concatenate(dele).view(np.int64)).cuda(), doff)
+    left = [np.setdiff1d(k, d) for k, d in zip(keys, dele)]
+    ooff = np.concatenate([[0], np.cumsum([x.size for x in left])]).astype(np.uint64)
+    out = torch.full((int(ooff[-1]),), -1, dtype=torch.int64, device="cuda")
+    res = b.decode(out, ooff)
+    got = out.cpu().numpy().view(np.uint64)
+    for i, s in enumerate(specs):
+        ot = oracle.IBLT(s[0], s[1], s[3])
+        ot.insert(keys[i])
+        ot.insert(dele[i], sign=-1)
+        ores = ot.decode_rounds()
+        assert res.rounds[i] == ores["rounds"]
+        assert res.residual_cells[i] == ot.residual_cells()
+        region = np.sort(got[int(ooff[i]): int(ooff[i]) + int(res.recovered[i])])
+        want = np.sort(np.concatenate(ores["keys"])) if ores["keys"] else np.zeros(0, np.uint64)
+        assert (region == want).all()
