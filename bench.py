@@ -434,7 +434,7 @@ def main():
     kernels = {
         "build": {"kernel": "k_bin + per-slab k_apply (slab-binned build)", "ms": b_ms, "bytes": build_bytes,
                   "achieved_gbs": build_bytes / (b_ms * 1e-3) / 1e9},
-        "decode": {"kernel": "decode graph (k_scan, k_peel, k_filter, k_round_end)", "ms": d_ms,
+        "decode": {"kernel": "decode graph (k_scan; per round k_claim, k_apply_round, k_filter, k_bins_reset, k_round_end)", "ms": d_ms,
                    "bytes": decode_bytes, "achieved_gbs": decode_bytes / (d_ms * 1e-3) / 1e9},
     }
     dom = "decode" if d_ms >= b_ms else "build"
