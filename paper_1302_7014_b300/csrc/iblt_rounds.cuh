@@ -302,32 +302,36 @@ __global__ void __launch_bounds__(kBlock) k_apply_round(Cell *__restrict__ cells
     const u32 in_bin = cnt < rb.cap ? cnt : rb.cap;
     const u32 first = (chunk - s_pre[bn]) * kApplyChunk;
     const u64 base = (u64)bn * rb.cap;
+    // Loads of every record of this thread first, then every update, then
+    // the pushes: kApplyPer records' atomics are in flight at once.
+    u64 x[kApplyPer], seed_chk[kApplyPer];
+    u32 c[kApplyPer], tb[kApplyPer];
+    bool v[kApplyPer];
+    int old[kApplyPer];
 #pragma unroll
     for (int k = 0; k < kApplyPer; ++k) {
       const u32 i = first + (u32)k * kBlock + tid;
-      const bool valid = i < in_bin;
-      int old = 0;
-      u32 c = 0, tb = 0;
-      if (valid) {
-        const u64 x = __ldcs(rb.rec_key + base + i);
-        c = __ldcs(rb.rec_cell + base + i);
-        if (BATCH) tb = __ldcs(rb.rec_tab + base + i);
-        u64 seed_chk;
-        if (BATCH) {
-          seed_chk = bc.chk_seed[tb];
-        } else {
-          seed_chk = tab0.seed[rank_of<R>(tab0)];
-        }
-        old = remove_key(cells, c, x, mix64(x ^ seed_chk));
-      }
-      const bool push = old == 2;
+      v[k] = i < in_bin;
+      x[k] = v[k] ? __ldcs(rb.rec_key + base + i) : 0ull;
+      c[k] = v[k] ? __ldcs(rb.rec_cell + base + i) : 0u;
+      tb[k] = (BATCH && v[k]) ? __ldcs(rb.rec_tab + base + i) : 0u;
+    }
+#pragma unroll
+    for (int k = 0; k < kApplyPer; ++k)
+      seed_chk[k] = BATCH ? (v[k] ? bc.chk_seed[tb[k]] : 0ull) : tab0.seed[rank_of<R>(tab0)];
+#pragma unroll
+    for (int k = 0; k < kApplyPer; ++k)
+      old[k] = v[k] ? remove_key(cells, c[k], x[k], mix64(x[k] ^ seed_chk[k])) : 0;
+#pragma unroll
+    for (int k = 0; k < kApplyPer; ++k) {
+      const bool push = old[k] == 2;
       const u32 q = warp_reserve<u32>(push, &s_ncand);
       if (push) {
-        s_cand[q] = c;
-        if (BATCH) s_ctab[q] = tb;
+        s_cand[q] = c[k];
+        if (BATCH) s_ctab[q] = tb[k];
       }
       // batched decodes count their residue with k_residual afterwards
-      if (!BATCH) emptied += old == 1;
+      if (!BATCH) emptied += old[k] == 1;
     }
     __syncthreads();
     const u32 nc = s_ncand;
