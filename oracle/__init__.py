@@ -7,7 +7,8 @@ seeded input generators in ``ppgen``.
 
 * ``peel_oracle.c`` (compiled with gcc on first use): IBLT insertion,
   round-synchronous and sequential IBLT recovery, round-synchronous and
-  sequential k-core peeling.
+  sequential k-core peeling, and the sub-table (sub-round) variants of the
+  round-synchronous peel and recovery (App. B).
 * ``predict.py``: the threshold c*_{k,r} (Eq. 2.1), the idealised recurrences
   for rho_i, lambda_i, beta_i (Sec. 3.1), the above-threshold fixed point
   (Sec. 4) and the sub-table recurrences (App. B).
@@ -67,8 +68,11 @@ def configure(so):
         so.orc_iblt_decode_queue.argtypes = [u64, u32, u64, vp, vp, vp, vp, u64, vp]
         so.orc_kcore_rounds.argtypes = [u32, u32, u32, vp, u64, u32, vp, vp, vp, vp, vp]
         so.orc_kcore_queue.argtypes = [u32, u32, u32, vp, u64, vp, vp]
+        so.orc_kcore_subrounds.argtypes = [u32, u32, u32, vp, u64, u32, vp, u32, vp, vp, vp, vp, vp]
+        so.orc_iblt_decode_subrounds.argtypes = [u64, u32, u64, vp, vp, vp, u32, vp, u64, vp, vp]
         for f in ("orc_iblt_insert", "orc_iblt_decode_rounds", "orc_iblt_decode_queue",
-                  "orc_kcore_rounds", "orc_kcore_queue"):
+                  "orc_kcore_rounds", "orc_kcore_queue", "orc_kcore_subrounds",
+                  "orc_iblt_decode_subrounds"):
             getattr(so, f).restype = ctypes.c_int
     return so
 
@@ -167,6 +171,24 @@ class IBLT:
                                          _ptr(got))
         return out[: int(got[0])].copy(), st
 
+    def decode_subrounds(self, max_subrounds: int = 1 << 20):
+        """Recovery with sub-tables (App. B): one sub-table per sub-round; mutates
+        the table.  Returns dict(keys=[array per sub-round, sorted], subrounds=S,
+        status=code)."""
+        cap = int(max(1, (np.abs(self.count).sum() // self.r) + 1))
+        cap = max(cap, self.n)
+        out = np.zeros(cap, dtype=np.uint64)
+        ms = int(min(max_subrounds, self.r * (self.n + 2)))
+        sub_end = np.zeros(ms + 1, dtype=np.uint64)
+        S = np.zeros(1, dtype=np.uint32)
+        st = lib().orc_iblt_decode_subrounds(self.n, self.r, self.seed, _ptr(self.count),
+                                             _ptr(self.keyx), _ptr(self.chkx), ms, _ptr(out), cap,
+                                             _ptr(sub_end), _ptr(S))
+        S = int(S[0])
+        ends = [0] + [int(x) for x in sub_end[:S]]
+        keys = [out[ends[i]:ends[i + 1]].copy() for i in range(S)]
+        return dict(keys=keys, subrounds=S, status=st)
+
     def residual_cells(self) -> int:
         return int(np.count_nonzero(self.count))
 
@@ -203,3 +225,26 @@ def kcore_queue(n: int, k: int, edges: np.ndarray):
     if st == INVALID:
         raise ValueError("invalid hypergraph (vertex id >= n)")
     return vc[:n], ec[:m]
+
+
+def kcore_subrounds(n: int, k: int, edges: np.ndarray, part_off, max_subrounds: int = 1 << 30):
+    """Peeling with sub-tables (App. B): part j = vertex ids part_off[j] ..
+    part_off[j+1]-1, one part per sub-round.  Returns dict(vround, eround, s, m,
+    subrounds, status) with s/m the vertices/edges left after each sub-round."""
+    edges = np.ascontiguousarray(edges, dtype=np.uint32)
+    m, r = (edges.shape if edges.ndim == 2 else (0, 1))
+    off = np.ascontiguousarray(np.asarray(part_off, dtype=np.uint32))
+    p = off.size - 1
+    vround = np.zeros(max(n, 1), dtype=np.int32)
+    eround = np.zeros(max(m, 1), dtype=np.int32)
+    ms = int(min(max_subrounds, p * (n + 1)))
+    s = np.zeros(ms + 1, dtype=np.uint64)
+    mt = np.zeros(ms + 1, dtype=np.uint64)
+    S = np.zeros(1, dtype=np.uint32)
+    st = lib().orc_kcore_subrounds(n, r, k, _ptr(edges), m, p, _ptr(off), ms, _ptr(vround),
+                                   _ptr(eround), _ptr(s), _ptr(mt), _ptr(S))
+    if st == INVALID:
+        raise ValueError("invalid hypergraph or parts")
+    S = int(S[0])
+    return dict(vround=vround[:n], eround=eround[:m], s=[int(x) for x in s[:S]],
+                m=[int(x) for x in mt[:S]], subrounds=S, status=st)

@@ -9,6 +9,8 @@ definitions with no bookkeeping, to pin the C oracle:
 * ``rounds_by_sets``: the round rule of Sec. 1 with sets recomputed from
   scratch every round: remove every vertex of degree < k, and every edge that
   touches one.
+* ``subrounds_by_sets``: the sub-table rule of App. B with the same
+  from-scratch sets: sub-round j of each round looks at part j only.
 """
 from __future__ import annotations
 
@@ -65,3 +67,38 @@ def rounds_by_sets(n: int, k: int, edges):
         s.append(len(V))
         m.append(len(E))
     return vround, eround, s, m, t
+
+
+def subrounds_by_sets(n: int, k: int, edges, parts):
+    """parts: list of vertex-id lists, one per part, visited in order each round.
+    Returns (vround, eround, s list, m list, S) with sub-rounds numbered from 1
+    and S the last sub-round that removed a vertex."""
+    edges = [tuple(int(u) for u in e) for e in edges]
+    V = set(range(n))
+    E = set(range(len(edges)))
+    vround = [0] * n
+    eround = [0] * len(edges)
+    s, m = [], []
+    S = 0
+    sub = 0
+    idle = 0
+    while idle < len(parts):
+        part = set(parts[sub % len(parts)])
+        sub += 1
+        deg = _degrees(V, E, edges)
+        R = {v for v in V & part if deg[v] < k}
+        if R:
+            idle = 0
+            S = sub
+        else:
+            idle += 1
+        D = {e for e in E if any(u in R for u in edges[e])}
+        for v in R:
+            vround[v] = sub
+        for e in D:
+            eround[e] = sub
+        V -= R
+        E -= D
+        s.append(len(V))
+        m.append(len(E))
+    return vround, eround, s[:S], m[:S], S

@@ -18,6 +18,8 @@
  *     Sec. 3.1), reported per round;
  *   - sequential queue k-core peeler (Sec. 1: the core is unique and does not
  *     depend on the removal order).
+ *   - peeling and IBLT recovery with sub-tables (App. B, Sec. 6
+ *     "Implementation Details"): one part / sub-table per sub-round.
  *
  * Conventions the paper leaves open (stated, not derived; parity unpinned for
  * the cell map and the sub-table split, which only the known-answer file
@@ -341,4 +343,142 @@ int orc_kcore_queue(uint32_t n, uint32_t r, uint32_t k, const uint32_t *edges, u
   }
   free(deg); free(start); free(fill); free(inc); free(stack);
   return ORC_OK;
+}
+
+/* Peeling with sub-tables (App. B; the recovery order of Sec. 6
+ * "Implementation Details").
+ *
+ * The vertices are split into p parts: part j (j = 0..p-1) holds the ids
+ * part_off[j] .. part_off[j+1]-1, with part_off[0] = 0 and part_off[p] = n.
+ * Each round runs one sub-round per part, in part order.  The sub-round of part
+ * j removes every alive vertex of part j whose degree is < k at the start of
+ * that sub-round, together with every alive edge touching one of them (each
+ * endpoint of such an edge loses one degree per incidence).  Vertices of the
+ * other parts wait for their own sub-round, so a removal can enable a removal
+ * later in the same round (App. B).
+ *
+ * Sub-rounds are numbered s = (i-1) p + j + 1 for round i and part j.  The
+ * process stops once p consecutive sub-rounds removed nothing; S (*S_out) is
+ * the number of the last sub-round that removed a vertex (0 if none).
+ * Outputs: vround[v] / eround[e] = the sub-round that removed v / e (0 = in
+ * the k-core); s_s[s-1] = |V| and m_s[s-1] = |E| after sub-round s, for
+ * s = 1..S.  With p = 1 this is orc_kcore_rounds. */
+int orc_kcore_subrounds(uint32_t n, uint32_t r, uint32_t k, const uint32_t *edges, uint64_t m,
+                        uint32_t p, const uint32_t *part_off, uint32_t max_subrounds,
+                        int32_t *vround, int32_t *eround, uint64_t *s_s, uint64_t *m_s,
+                        uint32_t *S_out) {
+  if (r < 1 || k < 1 || p < 1) return ORC_INVALID;
+  if (part_off[0] != 0 || part_off[p] != n) return ORC_INVALID;
+  for (uint32_t j = 0; j < p; ++j)
+    if (part_off[j] > part_off[j + 1]) return ORC_INVALID;
+  for (uint64_t i = 0; i < m * r; ++i)
+    if (edges[i] >= n) return ORC_INVALID;
+  int64_t *deg = (int64_t *)calloc(n ? n : 1, sizeof(int64_t));
+  if (!deg) return ORC_NOMEM;
+  for (uint64_t i = 0; i < m * r; ++i) deg[edges[i]] += 1;
+  for (uint32_t v = 0; v < n; ++v) vround[v] = 0;
+  for (uint64_t e = 0; e < m; ++e) eround[e] = 0;
+  uint64_t n_alive_v = n, n_alive_e = m;
+  uint32_t s = 0, idle = 0, S = 0;
+  int status = ORC_OK;
+  while (idle < p) {
+    const uint32_t j = s % p, sub = s + 1;
+    /* the vertices of part j with degree < k at the start of the sub-round */
+    uint64_t nrem = 0;
+    for (uint32_t v = part_off[j]; v < part_off[j + 1]; ++v)
+      if (vround[v] == 0 && deg[v] < (int64_t)k) ++nrem;
+    if (nrem == 0) {
+      if (s < max_subrounds) { s_s[s] = n_alive_v; m_s[s] = n_alive_e; }
+      ++idle;
+      ++s;
+      continue;
+    }
+    if (s >= max_subrounds) { status = ORC_ROUND_LIMIT; break; }
+    idle = 0;
+    for (uint32_t v = part_off[j]; v < part_off[j + 1]; ++v)
+      if (vround[v] == 0 && deg[v] < (int64_t)k) vround[v] = (int32_t)sub;
+    n_alive_v -= nrem;
+    /* every alive edge with an endpoint removed now goes too */
+    for (uint64_t e = 0; e < m; ++e) {
+      if (eround[e] != 0) continue;
+      int hit = 0;
+      for (uint32_t q = 0; q < r; ++q)
+        if (vround[edges[e * r + q]] == (int32_t)sub) hit = 1;
+      if (!hit) continue;
+      eround[e] = (int32_t)sub;
+      --n_alive_e;
+      for (uint32_t q = 0; q < r; ++q) deg[edges[e * r + q]] -= 1;
+    }
+    s_s[s] = n_alive_v;
+    m_s[s] = n_alive_e;
+    S = sub;
+    ++s;
+  }
+  *S_out = S;
+  free(deg);
+  return status;
+}
+
+/* IBLT recovery with sub-tables (Sec. 6 "Implementation Details"; App. B at
+ * k = 2): round i runs r sub-rounds, one per sub-table, in order.  The
+ * sub-round of sub-table j takes every cell of sub-table j that is pure at the
+ * start of the sub-round, recovers the key found in it and deletes that key
+ * from its r cells.  A key has exactly one cell in each sub-table, so no key
+ * is found twice within a sub-round; every pure cell's key is deleted as
+ * found, with no further de-duplication.
+ *
+ * Sub-rounds are numbered s = (i-1) r + j + 1; the loop stops once r
+ * consecutive sub-rounds recovered nothing, and *S_out is the number of the
+ * last sub-round that recovered a key.  out_keys receives the keys of
+ * sub-rounds 1, 2, ... in order, each sub-round sorted ascending;
+ * sub_end[s-1] = the number of keys recovered in sub-rounds 1..s, s = 1..S.
+ * Returns ORC_CAPACITY if out_cap is too small and ORC_ROUND_LIMIT if a
+ * sub-round past max_subrounds would recover a key. */
+int orc_iblt_decode_subrounds(uint64_t n, uint32_t r, uint64_t table_seed, int64_t *count,
+                              uint64_t *keyx, uint64_t *chkx, uint32_t max_subrounds,
+                              uint64_t *out_keys, uint64_t out_cap, uint64_t *sub_end,
+                              uint32_t *S_out) {
+  if (r < 2 || r > 16 || n < r) return ORC_INVALID;
+  uint64_t seeds[17], off[17];
+  orc_hash_seeds(table_seed, r, seeds);
+  orc_part_offsets(n, r, off);
+  uint64_t *found = (uint64_t *)malloc((n ? n : 1) * sizeof(uint64_t));
+  if (!found) return ORC_NOMEM;
+  uint64_t total = 0;
+  uint32_t s = 0, idle = 0, S = 0;
+  int status = ORC_OK;
+  while (idle < r) {
+    const uint32_t j = s % r;
+    /* the pure cells of sub-table j at the start of the sub-round */
+    uint64_t nf = 0;
+    for (uint64_t c = off[j]; c < off[j + 1]; ++c)
+      if (is_pure(c, count, keyx, chkx, seeds, r)) found[nf++] = keyx[c];
+    if (nf == 0) {
+      if (s < max_subrounds) sub_end[s] = total;
+      ++idle;
+      ++s;
+      continue;
+    }
+    if (s >= max_subrounds) { status = ORC_ROUND_LIMIT; break; }
+    if (total + nf > out_cap) { status = ORC_CAPACITY; break; }
+    idle = 0;
+    qsort(found, nf, sizeof(uint64_t), cmp_u64);
+    for (uint64_t i = 0; i < nf; ++i) {
+      uint64_t x = found[i], cs = checksum_of(x, seeds, r);
+      out_keys[total + i] = x;
+      for (uint32_t q = 0; q < r; ++q) {
+        uint64_t c = cell_of(x, q, seeds, off);
+        count[c] -= 1;
+        keyx[c] ^= x;
+        chkx[c] ^= cs;
+      }
+    }
+    total += nf;
+    sub_end[s] = total;
+    S = s + 1;
+    ++s;
+  }
+  *S_out = S;
+  free(found);
+  return status;
 }

@@ -13,6 +13,7 @@ import pytest
 
 import oracle
 import test_oracle_pins as pins
+import test_oracle_subrounds as sub
 
 MUTANTS = [
     ("round removes degree <= k",
@@ -45,6 +46,21 @@ MUTANTS = [
     ("sub-table split puts the remainder last",
      "off[j + 1] = off[j] + q + (j < rem ? 1 : 0);",
      "off[j + 1] = off[j] + q + (j >= r - rem ? 1 : 0);"),
+    ("sub-round looks at every part at once",
+     "    for (uint32_t v = part_off[j]; v < part_off[j + 1]; ++v)\n      if (vround[v] == 0 && deg[v] < (int64_t)k) ++nrem;\n",
+     "    for (uint32_t v = 0; v < n; ++v)\n      if (vround[v] == 0 && deg[v] < (int64_t)k) ++nrem;\n"),
+    ("sub-round process stops at the first idle sub-round",
+     "while (idle < p) {",
+     "while (idle < 1) {"),
+    ("sub-round count includes the trailing idle sub-rounds",
+     "  *S_out = S;\n  free(deg);",
+     "  *S_out = s;\n  free(deg);"),
+    ("IBLT sub-round scans every sub-table",
+     "for (uint64_t c = off[j]; c < off[j + 1]; ++c)",
+     "for (uint64_t c = 0; c < n; ++c)"),
+    ("IBLT sub-tables visited in reverse order",
+     "    const uint32_t j = s % r;",
+     "    const uint32_t j = r - 1 - s % r;"),
     ("mix64 shift constant off by one",
      "z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;",
      "z = (z ^ (z >> 28)) * 0x94D049BB133111EBULL;"),
@@ -63,6 +79,12 @@ PINS = [
     lambda: pins.test_iblt_below_threshold_recovered_inserted_set_wrapper(),
     lambda: pins.test_iblt_residue_invariants_above_threshold(),
     lambda: pins.test_iblt_checksum_rejects_impure_count_one(),
+    lambda: sub.test_hand_worked_path(),
+    lambda: sub.test_hand_worked_idle_part_in_the_middle(),
+    lambda: sub.test_one_part_is_the_round_process(),
+    lambda: sub.test_tiny_hypergraphs_vs_sets(),
+    lambda: sub.test_iblt_subrounds_equal_kcore_subrounds(2000, 3, 0.75, 1),
+    lambda: sub.test_iblt_subrounds_recover_inserted_set_below_threshold(),
 ]
 
 
