@@ -165,6 +165,29 @@ pp_status pp_iblt_build(pp_iblt *t, const uint64_t *d_keys, uint64_t m, void *st
 pp_status pp_iblt_decode(pp_iblt *t, uint64_t *d_out_keys, uint64_t out_cap,
                          pp_decode_result *res, void *stream);
 
+/* Recovery with sub-tables, the order of the paper's GPU implementation
+ * (Sec. 6 "Implementation Details"; analysed in App. B): every round visits
+ * the r sub-tables in order, and the sub-round of sub-table j recovers the key
+ * of every cell of sub-table j that is pure at the start of that sub-round,
+ * then deletes it from its r cells before the next sub-round starts.  A key
+ * has one cell per sub-table, so no key is found twice in a sub-round.
+ * Sub-rounds are numbered s = (i-1) r + j + 1 for round i and sub-table j;
+ * sub-rounds whose sub-table has no candidate cell are skipped, keeping their
+ * numbers.  The table is decoded in place to the same 2-core residue as
+ * pp_iblt_decode, and the same keys come out.
+ * d_out_keys: out_cap uint64 on the device; receives the keys grouped by
+ * sub-round (sub-round 1 first), in no particular order within a sub-round.
+ * *res as for pp_iblt_decode, read per sub-round: res->rounds = S, the last
+ * sub-round that recovered a key; recovered_per_round[s-1] and
+ * remaining_per_round[s-1] describe sub-round s (0 for a skipped one);
+ * alive_cells_per_round is not computed in this order and is zero-filled.
+ * opt.max_rounds bounds the number of sub-rounds: ROUND_LIMIT if a sub-round
+ * past it still has cells to examine.  CAPACITY as for pp_iblt_decode;
+ * INVALID_ARG if a pure cell's key does not hash to that cell.
+ * Synchronizes `stream`. */
+pp_status pp_iblt_decode_subrounds(pp_iblt *t, uint64_t *d_out_keys, uint64_t out_cap,
+                                   pp_decode_result *res, void *stream);
+
 /* Copies `count` cells starting at `first` into dst (device memory if
  * to_host == 0, else host memory), on `stream`, and synchronizes it. */
 pp_status pp_iblt_copy_cells(pp_iblt *t, void *dst, uint64_t first, uint64_t count,
@@ -202,6 +225,26 @@ typedef struct pp_peel_result {
 pp_status pp_peel_kcore(uint32_t n, uint32_t r, uint32_t k, const uint32_t *d_edges,
                         uint64_t m, int32_t *d_vertex_round, int32_t *d_edge_round,
                         pp_peel_result *res, const pp_options *opt, void *stream);
+
+/* Peeling with sub-tables (App. B): the vertices are split into n_parts parts,
+ * part j holding the ids h_part_off[j] .. h_part_off[j+1]-1 (a host array of
+ * n_parts + 1 entries running from 0 to n, non-decreasing; 1 <= n_parts <= 64).
+ * Every round runs one sub-round per part, in part order; the sub-round of part
+ * j removes every vertex of part j whose degree is < k at the start of that
+ * sub-round, with every edge touching one of them.  With one part this is
+ * pp_peel_kcore.  Sub-rounds are numbered s = (i-1) n_parts + j + 1; sub-rounds
+ * whose part has nothing to remove are skipped on the device but keep their
+ * numbers and statistics.
+ * Outputs as for pp_peel_kcore, read per sub-round: d_vertex_round /
+ * d_edge_round hold sub-round numbers, res->rounds = S (the last sub-round that
+ * removed a vertex), vertices_left[s-1] / edges_left[s-1] describe sub-round s.
+ * opt.max_rounds bounds the number of sub-rounds (ROUND_LIMIT).  Errors as for
+ * pp_peel_kcore, plus INVALID_ARG for bad part offsets.  Synchronizes
+ * `stream`. */
+pp_status pp_peel_kcore_subrounds(uint32_t n, uint32_t r, uint32_t k, const uint32_t *d_edges,
+                                  uint64_t m, uint32_t n_parts, const uint32_t *h_part_off,
+                                  int32_t *d_vertex_round, int32_t *d_edge_round,
+                                  pp_peel_result *res, const pp_options *opt, void *stream);
 
 /* ------------------------------------------------------------------------
  * Batched decode: many IBLTs of uneven size, decoded together.

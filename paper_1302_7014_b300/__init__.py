@@ -10,6 +10,9 @@ stream) and turns status codes into exceptions.  Names follow the C ABI in
   "Parallel Peeling Algorithms"), decoded by round-synchronous peeling at k=2.
 * ``peel_kcore`` -- round-synchronous k-core peeling of an explicit r-uniform
   hypergraph (Sec. 1, Sec. 3.1).
+* ``IBLT.decode_subrounds`` / ``iblt_decode_subrounds`` and
+  ``peel_kcore_subrounds`` -- the same processes with one part (sub-table) per
+  sub-round, the order of the paper's GPU implementation (App. B).
 """
 from __future__ import annotations
 
@@ -20,7 +23,7 @@ from . import _lib
 from ._lib import PP_MAX_R, Cell, DecodeResult, Options, PeelResult
 
 __all__ = ["PPError", "IBLT", "iblt_create", "iblt_insert", "iblt_delete", "iblt_build", "iblt_decode",
-           "peel_kcore", "options", "PP_MAX_R"]
+           "iblt_decode_subrounds", "peel_kcore", "peel_kcore_subrounds", "options", "PP_MAX_R"]
 
 
 class PPError(RuntimeError):
@@ -130,6 +133,15 @@ class IBLT:
 
     def decode(self, out, round_cap: int = 4096, stream=None) -> DecodeOutcome:
         """Decode in place; ``out`` (CUDA, 8-byte elements) receives the keys."""
+        return self._decode(_lib.load().pp_iblt_decode, "pp_iblt_decode", out, round_cap, stream)
+
+    def decode_subrounds(self, out, round_cap: int = 4096, stream=None) -> DecodeOutcome:
+        """Decode in place with one sub-table per sub-round (App. B); the per-round
+        lists of the outcome are per sub-round."""
+        return self._decode(_lib.load().pp_iblt_decode_subrounds, "pp_iblt_decode_subrounds", out,
+                            round_cap, stream)
+
+    def _decode(self, fn, name, out, round_cap, stream) -> DecodeOutcome:
         rec = (ctypes.c_uint64 * round_cap)()
         rem = (ctypes.c_uint64 * round_cap)()
         alive = (ctypes.c_uint64 * round_cap)()
@@ -138,10 +150,9 @@ class IBLT:
         res.recovered_per_round = ctypes.cast(rec, ctypes.POINTER(ctypes.c_uint64))
         res.remaining_per_round = ctypes.cast(rem, ctypes.POINTER(ctypes.c_uint64))
         res.alive_cells_per_round = ctypes.cast(alive, ctypes.POINTER(ctypes.c_uint64))
-        st = _lib.load().pp_iblt_decode(self._h, _dev_ptr(out, 8, "out"),
-                                        out.numel() if out is not None else 0, ctypes.byref(res),
-                                        _stream_ptr(stream))
-        _check(st, "pp_iblt_decode")
+        st = fn(self._h, _dev_ptr(out, 8, "out"), out.numel() if out is not None else 0, ctypes.byref(res),
+                _stream_ptr(stream))
+        _check(st, name)
         n = min(res.rounds, round_cap)
         return DecodeOutcome(res.rounds, res.recovered, res.items_before, res.residual_cells,
                              res.status_flags, list(rec[:n]), list(rem[:n]), list(alive[:n]))
@@ -185,9 +196,25 @@ def iblt_decode(table: IBLT, out, round_cap: int = 4096, stream=None) -> DecodeO
     return table.decode(out, round_cap, stream)
 
 
+def iblt_decode_subrounds(table: IBLT, out, round_cap: int = 4096, stream=None) -> DecodeOutcome:
+    return table.decode_subrounds(out, round_cap, stream)
+
+
 def peel_kcore(n: int, r: int, k: int, edges, vertex_round=None, edge_round=None,
                opts: Options | None = None, round_cap: int = 4096, stream=None) -> PeelOutcome:
     """Peel the hypergraph ``edges`` ((m, r) CUDA tensor of 4-byte ids) to its k-core."""
+    return _peel(n, r, k, edges, None, vertex_round, edge_round, opts, round_cap, stream)
+
+
+def peel_kcore_subrounds(n: int, r: int, k: int, edges, part_off, vertex_round=None, edge_round=None,
+                         opts: Options | None = None, round_cap: int = 4096,
+                         stream=None) -> PeelOutcome:
+    """Peel to the k-core with one part per sub-round (App. B): part j is vertex ids
+    part_off[j] .. part_off[j+1]-1.  Rounds in the outcome are sub-rounds."""
+    return _peel(n, r, k, edges, part_off, vertex_round, edge_round, opts, round_cap, stream)
+
+
+def _peel(n, r, k, edges, part_off, vertex_round, edge_round, opts, round_cap, stream) -> PeelOutcome:
     m = edges.shape[0] if edges is not None and edges.numel() else 0
     if edges is not None and edges.numel() and (edges.dim() != 2 or edges.shape[1] != r):
         raise ValueError("edges must have shape (m, r)")
@@ -197,13 +224,18 @@ def peel_kcore(n: int, r: int, k: int, edges, vertex_round=None, edge_round=None
     res.round_cap = round_cap
     res.vertices_left = ctypes.cast(s_left, ctypes.POINTER(ctypes.c_uint64))
     res.edges_left = ctypes.cast(m_left, ctypes.POINTER(ctypes.c_uint64))
-    st = _lib.load().pp_peel_kcore(int(n), int(r), int(k),
-                                   _dev_ptr(edges, 4, "edges") if m else None, int(m),
-                                   _dev_ptr(vertex_round, 4, "vertex_round"),
-                                   _dev_ptr(edge_round, 4, "edge_round"), ctypes.byref(res),
-                                   ctypes.byref(opts) if opts is not None else None,
-                                   _stream_ptr(stream))
-    _check(st, "pp_peel_kcore")
+    common = (_dev_ptr(vertex_round, 4, "vertex_round"), _dev_ptr(edge_round, 4, "edge_round"),
+              ctypes.byref(res), ctypes.byref(opts) if opts is not None else None, _stream_ptr(stream))
+    e_ptr = _dev_ptr(edges, 4, "edges") if m else None
+    if part_off is None:
+        st = _lib.load().pp_peel_kcore(int(n), int(r), int(k), e_ptr, int(m), *common)
+        _check(st, "pp_peel_kcore")
+    else:
+        off = [int(x) for x in part_off]
+        arr = (ctypes.c_uint32 * len(off))(*off)
+        st = _lib.load().pp_peel_kcore_subrounds(int(n), int(r), int(k), e_ptr, int(m), len(off) - 1,
+                                                 arr, *common)
+        _check(st, "pp_peel_kcore_subrounds")
     nr = min(res.rounds, round_cap)
     return PeelOutcome(res.rounds, res.core_vertices, res.core_edges, res.status_flags,
                        list(s_left[:nr]), list(m_left[:nr]))

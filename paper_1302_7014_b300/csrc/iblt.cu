@@ -12,6 +12,7 @@
 #include "iblt_binned.cuh"
 #include "iblt_kernels.cuh"
 #include "iblt_rounds.cuh"
+#include "iblt_subrounds.cuh"
 
 using namespace pp;
 
@@ -30,9 +31,15 @@ static IbltKernels iblt_kernels_t() {
                          200 * 1024);
     attr_set = true;
   }
-  return {(const void *)k_insert<R, B>, (const void *)k_scan<R, B>, (const void *)k_peel<R, B>,
-          (const void *)k_filter<R, B>, (const void *)k_bin<R, B>, (const void *)k_apply<R, B>,
-          (const void *)k_claim<R, B>, (const void *)k_apply_round<R, B>, nr_of<R>()};
+  IbltKernels k{(const void *)k_insert<R, B>, (const void *)k_scan<R, B>, (const void *)k_peel<R, B>,
+                (const void *)k_filter<R, B>, (const void *)k_bin<R, B>, (const void *)k_apply<R, B>,
+                (const void *)k_claim<R, B>, (const void *)k_apply_round<R, B>, nr_of<R>()};
+  if constexpr (!B && R >= 0) {
+    k.sub_scan = (const void *)k_sscan<R>;
+    k.sub_filter = (const void *)k_sfilter<R>;
+    k.sub_peel = (const void *)k_speel<R>;
+  }
+  return k;
 }
 
 IbltKernels iblt_kernels(int rank, bool batch) {
@@ -107,6 +114,10 @@ struct pp_iblt {
   uint32_t n_bins = 0, bin_cap = 0, bin_shift = 0;
   size_t smem_claim = 0, smem_apply_round = 0;
   int grid_claim = 0, grid_apply_round = 0;
+  // decode with sub-tables (allocated on first use)
+  SubDecCtl *sctl = nullptr, *h_sctl = nullptr;
+  cudaGraphExec_t sub_exec = nullptr;
+  int grid_sscan = 0, grid_sfilter = 0, grid_speel = 0;
 };
 
 namespace {
@@ -114,6 +125,9 @@ namespace {
 void free_all(pp_iblt *t) {
   if (!t) return;
   if (t->exec) cudaGraphExecDestroy(t->exec);
+  if (t->sub_exec) cudaGraphExecDestroy(t->sub_exec);
+  cudaFree(t->sctl);
+  cudaFreeHost(t->h_sctl);
   cudaFree(t->cells);
   cudaFree(t->fkey);
   cudaFree(t->fcell);
@@ -353,6 +367,127 @@ pp_status build_graph(pp_iblt *t) {
 done:
   cudaGraphDestroy(g);
   return st;
+}
+
+// ---- decode with sub-tables ----------------------------------------------
+struct SubArgs {
+  // k_sscan
+  const Cell *cells_c;
+  TableArgs tab;
+  u32 *queue;
+  SubDecCtl *ctl;
+  void *scan[4];
+  // k_sfilter
+  u64 *fkey;
+  u32 *fcell;
+  void *filter[6];
+  // k_speel
+  Cell *cells;
+  void *peel[6];
+  // k_send
+  u64 *st_rec;
+  int set_cond;
+  cudaGraphConditionalHandle cond;
+  void *end[4];
+  void bind() {
+    void *a[4] = {&cells_c, &tab, &queue, &ctl};
+    memcpy(scan, a, sizeof a);
+    void *b[6] = {&cells_c, &tab, &queue, &fkey, &fcell, &ctl};
+    memcpy(filter, b, sizeof b);
+    void *c[6] = {&cells, &tab, &fkey, &fcell, &queue, &ctl};
+    memcpy(peel, c, sizeof c);
+    void *d[4] = {&ctl, &st_rec, &set_cond, &cond};
+    memcpy(end, d, sizeof d);
+  }
+};
+
+void fill_sub_args(pp_iblt *t, SubArgs &a) {
+  a.cells_c = t->cells;
+  a.tab = t->args;
+  a.queue = t->cand;  // the candidate list doubles as the per-sub-table queues
+  a.ctl = t->sctl;
+  a.fkey = t->fkey;
+  a.fcell = t->fcell;
+  a.cells = t->cells;
+  a.st_rec = t->st_rec;
+  a.set_cond = 0;
+  a.cond = 0;
+  a.bind();
+}
+
+pp_status sub_prepare(pp_iblt *t) {
+  if (!t->k.sub_scan) return fail(PP_ERR_INVALID_ARG, "decode with sub-tables: no kernels for r=%u", t->r);
+  if (!t->sctl) {
+    PP_CUDA(cudaMalloc((void **)&t->sctl, sizeof(SubDecCtl)));
+    PP_CUDA(cudaMallocHost((void **)&t->h_sctl, sizeof(SubDecCtl)));
+    t->grid_sscan = persistent_grid(t->k.sub_scan, kBlock, 0, t->opt.ctas_per_sm);
+    t->grid_sfilter = persistent_grid(t->k.sub_filter, kBlock, 0, t->opt.ctas_per_sm);
+    t->grid_speel = persistent_grid(t->k.sub_peel, kBlock, 0, t->opt.ctas_per_sm);
+  }
+  return PP_OK;
+}
+
+pp_status sub_host_loop(pp_iblt *t, cudaStream_t s) {
+  SubArgs a;
+  fill_sub_args(t, a);
+  PP_CUDA(cudaLaunchKernel(t->k.sub_scan, dim3(t->grid_sscan), dim3(kBlock), a.scan, 0, s));
+  for (;;) {
+    PP_CUDA(cudaLaunchKernel(t->k.sub_filter, dim3(t->grid_sfilter), dim3(kBlock), a.filter, 0, s));
+    PP_CUDA(cudaLaunchKernel(t->k.sub_peel, dim3(t->grid_speel), dim3(kBlock), a.peel, 0, s));
+    PP_CUDA(cudaLaunchKernel((const void *)k_send, dim3(1), dim3(32), a.end, 0, s));
+    PP_CUDA(cudaMemcpyAsync(&t->h_sctl->more, &t->sctl->more, sizeof(u32), cudaMemcpyDeviceToHost, s));
+    PP_CUDA(cudaStreamSynchronize(s));
+    if (!t->h_sctl->more) break;
+  }
+  return PP_OK;
+}
+
+// sscan -> while (more) { sfilter -> speel -> send }; every pointer it holds
+// lives as long as the handle, so the graph is built once.
+pp_status sub_graph_launch(pp_iblt *t, cudaStream_t s) {
+  if (!t->sub_exec) {
+    SubArgs a;
+    fill_sub_args(t, a);
+    cudaGraph_t g = nullptr;
+    PP_CUDA(cudaGraphCreate(&g, 0));
+    pp_status st = PP_OK;
+    cudaGraphNode_t n_scan, n_cond, n_filter, n_peel, n_end;
+    cudaGraphConditionalHandle h;
+    cudaGraphNodeParams cp{};
+    cudaGraph_t body;
+    st = add_kernel(&n_scan, g, nullptr, 0, t->k.sub_scan, t->grid_sscan, kBlock, 0, a.scan);
+    if (st != PP_OK) goto done;
+    if (cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault) != cudaSuccess) {
+      st = fail(PP_ERR_CUDA, "cudaGraphConditionalHandleCreate failed");
+      goto done;
+    }
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = h;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    if (cudaGraphAddNode(&n_cond, g, &n_scan, nullptr, 1, &cp) != cudaSuccess) {
+      st = fail(PP_ERR_CUDA, "cudaGraphAddNode(conditional while) failed");
+      goto done;
+    }
+    body = cp.conditional.phGraph_out[0];
+    a.set_cond = 1;
+    a.cond = h;
+    st = add_kernel(&n_filter, body, nullptr, 0, t->k.sub_filter, t->grid_sfilter, kBlock, 0, a.filter);
+    if (st != PP_OK) goto done;
+    st = add_kernel(&n_peel, body, &n_filter, 1, t->k.sub_peel, t->grid_speel, kBlock, 0, a.peel);
+    if (st != PP_OK) goto done;
+    st = add_kernel(&n_end, body, &n_peel, 1, (const void *)k_send, 1, 32, 0, a.end);
+    if (st != PP_OK) goto done;
+    if (cudaGraphInstantiate(&t->sub_exec, g, 0) != cudaSuccess) {
+      st = fail(PP_ERR_CUDA, "cudaGraphInstantiate failed: %s", cudaGetErrorString(cudaGetLastError()));
+      t->sub_exec = nullptr;
+    }
+  done:
+    cudaGraphDestroy(g);
+    if (st != PP_OK) return st;
+  }
+  PP_CUDA(cudaGraphLaunch(t->sub_exec, s));
+  return PP_OK;
 }
 
 pp_status run_host_loop(pp_iblt *t, cudaStream_t s) {
@@ -694,6 +829,61 @@ pp_status pp_iblt_decode(pp_iblt *t, uint64_t *d_out_keys, uint64_t out_cap, pp_
     return fail(PP_ERR_INVALID_ARG, "pp_iblt_decode: a pure cell's key does not hash to it");
   if (c.flags & FLAG_ROUND_LIMIT)
     return fail(PP_ERR_ROUND_LIMIT, "pp_iblt_decode: stopped after max_rounds=%u rounds",
+                t->opt.max_rounds);
+  return PP_OK;
+}
+
+pp_status pp_iblt_decode_subrounds(pp_iblt *t, uint64_t *d_out_keys, uint64_t out_cap,
+                                   pp_decode_result *res, void *stream) {
+  if (!t || !res) return fail(PP_ERR_INVALID_ARG, "pp_iblt_decode_subrounds: NULL table or result");
+  const uint64_t items = t->items > 0 ? (uint64_t)t->items : 0;
+  if (out_cap < items)
+    return fail(PP_ERR_CAPACITY, "pp_iblt_decode_subrounds: out_cap=%llu < %llu keys in the table",
+                (unsigned long long)out_cap, (unsigned long long)items);
+  if (out_cap && !d_out_keys) return fail(PP_ERR_INVALID_ARG, "pp_iblt_decode_subrounds: NULL output");
+  cudaStream_t s = as_stream(stream);
+  pp_status st = sub_prepare(t);
+  if (st != PP_OK) return st;
+  SubDecCtl &h = *t->h_sctl;
+  memset(&h, 0, sizeof h);
+  h.out = reinterpret_cast<u64 *>(d_out_keys);
+  h.out_cap = out_cap;
+  h.max_sub = t->opt.max_rounds;
+  h.r = t->r;
+  h.part = t->r - 1;  // the first sub-round looks at sub-table 0
+  PP_CUDA(cudaMemcpyAsync(t->sctl, t->h_sctl, sizeof(SubDecCtl), cudaMemcpyHostToDevice, s));
+  st = t->opt.host_loop ? sub_host_loop(t, s) : sub_graph_launch(t, s);
+  if (st != PP_OK) return st;
+  PP_CUDA(cudaMemcpyAsync(t->h_sctl, t->sctl, sizeof(SubDecCtl), cudaMemcpyDeviceToHost, s));
+  PP_CUDA(cudaStreamSynchronize(s));
+  const SubDecCtl c = *t->h_sctl;
+  const uint32_t S = c.last;
+  const uint32_t ncopy = S < res->round_cap ? S : res->round_cap;
+  if (ncopy && (res->recovered_per_round || res->remaining_per_round)) {
+    PP_CUDA(cudaMemcpyAsync(t->h_rec, t->st_rec, ncopy * sizeof(u64), cudaMemcpyDeviceToHost, s));
+    PP_CUDA(cudaStreamSynchronize(s));
+    uint64_t left = items;
+    for (uint32_t i = 0; i < ncopy; ++i) {
+      left -= t->h_rec[i] <= left ? t->h_rec[i] : left;
+      if (res->recovered_per_round) res->recovered_per_round[i] = t->h_rec[i];
+      if (res->remaining_per_round) res->remaining_per_round[i] = left;
+    }
+  }
+  if (ncopy && res->alive_cells_per_round)
+    memset(res->alive_cells_per_round, 0, ncopy * sizeof(uint64_t));
+  res->rounds = S;
+  res->status_flags = c.flags;
+  res->recovered = c.n_out < out_cap ? c.n_out : out_cap;
+  res->items_before = items;
+  res->residual_cells = c.nonempty - c.emptied;
+  t->items -= (int64_t)res->recovered;
+  if (c.flags & FLAG_CAPACITY)
+    return fail(PP_ERR_CAPACITY, "pp_iblt_decode_subrounds: more keys recovered than out_cap=%llu",
+                (unsigned long long)out_cap);
+  if (c.flags & FLAG_INTERNAL)
+    return fail(PP_ERR_INVALID_ARG, "pp_iblt_decode_subrounds: a pure cell's key does not hash to it");
+  if (c.flags & FLAG_ROUND_LIMIT)
+    return fail(PP_ERR_ROUND_LIMIT, "pp_iblt_decode_subrounds: stopped after max_rounds=%u sub-rounds",
                 t->opt.max_rounds);
   return PP_OK;
 }

@@ -241,14 +241,14 @@ __global__ void __launch_bounds__(kBlock) k_peel(Cell *__restrict__ cells, const
             old[j] = atomicSub(&p->count, 1);
             atomicXor(&p->key, x);
             atomicXor(&p->chk, cx);
-            n_empty += old[j] == 1;
+            n_empty += (u32)((old[j] == 1) - (old[j] == 0));  // net change of non-zero counts
           }
         }
       } else {
 #pragma unroll
         for (int j = 0; j < NR; ++j) old[j] = 0;
       }
-      emptied += n_empty;
+      emptied += (u64)(long long)(int)n_empty;
       if constexpr (!BATCH) {
         const u32 p = warp_reserve<u32>(win, &s_nout);
         if (win) s_out[p] = x;
@@ -263,7 +263,7 @@ __global__ void __launch_bounds__(kBlock) k_peel(Cell *__restrict__ cells, const
         if (win && (int)lane_id() == leader) {
           const u32 local = round + 1 - T.start_round;  // this table's own round number
           base = atomicAdd(bc.recovered + tb, (u64)gsize);
-          if (gempty) atomicAdd(bc.emptied + tb, (u64)gempty);
+          if (gempty) atomicAdd(bc.emptied + tb, (u64)(long long)(int)gempty);
           atomicMax(bc.rounds + tb, local);
           if (local <= stats_rounds) atomicAdd(bc.round_rec + (u64)tb * stats_rounds + (local - 1), gsize);
         }

@@ -212,7 +212,7 @@ __global__ void __launch_bounds__(kBlock) k_claim(Cell *__restrict__ cells, cons
           cand[q] = cc;
           if (BATCH) ctab[q] = t2;
         }
-        if (!BATCH && old == 1) ++ovf_emptied;
+        if (!BATCH) ovf_emptied += (u64)(long long)((old == 1) - (old == 0));
       }
     }
     if constexpr (!BATCH) {
@@ -331,7 +331,7 @@ __global__ void __launch_bounds__(kBlock) k_apply_round(Cell *__restrict__ cells
         if (BATCH) s_ctab[q] = tb[k];
       }
       // batched decodes count their residue with k_residual afterwards
-      if (!BATCH) emptied += old[k] == 1;
+      if (!BATCH && v[k]) emptied += (u64)(long long)((old[k] == 1) - (old[k] == 0));
     }
     __syncthreads();
     const u32 nc = s_ncand;

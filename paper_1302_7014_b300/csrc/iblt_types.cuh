@@ -18,7 +18,7 @@ struct DecodeCtl {
   u64 out_round_start;  // n_out when the current round started
   u64 alive;            // cells with count >= 2 at the start of the current round
   u64 nonempty;         // cells with count != 0 when the decode started
-  u64 emptied;          // cells whose count went from 1 to 0 during the decode
+  u64 emptied;          // net count of cells whose count became 0 (1 -> 0 minus 0 -> -1), mod 2^64
   u32 round;            // rounds started so far
   u32 n_front;          // |F_t|: entries of the current frontier
   u32 n_next;           // entries of F_{t+1} written so far
@@ -42,7 +42,7 @@ struct RoundStats {
 struct BatchCounters {
   u64 *recovered;      // per table: keys recovered (also the output cursor)
   u64 *nonempty;       // per table: non-empty cells at the start
-  u64 *emptied;        // per table: cells emptied during the decode
+  u64 *emptied;        // per table: net cells emptied (1 -> 0 minus 0 -> -1), mod 2^64
   u32 *rounds;         // per table: last round that recovered a key
   u32 *round_rec;      // per table x stats_rounds: keys recovered per round
   u32 *live;           // per table: entries it has in the frontier being built (or NULL)
@@ -125,6 +125,7 @@ struct IbltKernels {
   const void *bin, *apply;           // slab-binned build
   const void *claim, *apply_round;   // binned decode round
   int nr;  // compile-time rank (PP_MAX_R for the generic instance)
+  const void *sub_scan = nullptr, *sub_filter = nullptr, *sub_peel = nullptr;  // sub-rounds (plain only)
 };
 
 // The kernel set for a rank code: 3 or 4 = that r; -4 = any r <= 4 (batched

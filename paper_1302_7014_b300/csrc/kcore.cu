@@ -10,6 +10,18 @@
 //           decrement that takes a degree from k to k-1 pushes that endpoint
 //           into F_{t+1} (its degree was >= k at the start of round t, and is
 //           < k at its end: exactly the vertices round t+1 removes).
+//
+// Sub-round mode (App. B, pp_peel_kcore_subrounds): the vertices are split into
+// p parts and each round runs one sub-round per part; a sub-round removes the
+// part's vertices whose degree is < k at the sub-round's start.  Each part
+// keeps a queue of its vertices that are due (degree < k, not yet removed):
+// the scan fills it, and the k -> k-1 crossing of a vertex appends the vertex
+// to its own part's queue.  A sub-round takes the entries its part's queue
+// held when the sub-round started; an entry appended during the sub-round of
+// its own part waits for the next round, as the definition requires.  Every
+// vertex enters a queue at most once (degrees only fall), so part j's queue
+// fits in the part's own n_j slots.  Sub-rounds whose part has nothing due
+// are skipped on the device (their statistics are still written).
 #include <string.h>
 
 #include "host.cuh"
@@ -192,6 +204,213 @@ __global__ void k_kround_end(PeelCtl *__restrict__ ctl, PeelStats st, int set_co
   if (set_cond) cudaGraphSetConditional(cond, more);
 }
 
+// ---------------------------------------------------------------------------
+// Sub-round mode
+// ---------------------------------------------------------------------------
+constexpr int kMaxParts = 64;
+constexpr int kSubStage = 2048;
+
+struct Parts {
+  u32 off[kMaxParts + 1];  // part j = vertex ids off[j] .. off[j+1]-1
+  u32 p;
+};
+
+struct SubCtl {
+  u64 claimed;  // edges removed in the current sub-round
+  u64 s;        // vertices left
+  u64 m;        // edges left
+  u32 sub;      // number of the current sub-round (0 before the first)
+  u32 part;     // its part
+  u32 fb, fe;   // its frontier: queue entries fb .. fe-1 of that part
+  u32 flags;
+  u32 max_sub;
+  u32 more;
+  u32 k;
+  u32 head[kMaxParts];  // entries consumed, per part
+  u32 tail[kMaxParts];  // entries appended, per part
+};
+
+__device__ __forceinline__ u32 part_of(const Parts &P, u32 v) {
+  u32 a = 0, b = P.p;  // the last j with off[j] <= v
+  while (b - a > 1) {
+    const u32 mid = (a + b) >> 1;
+    if (P.off[mid] <= v) a = mid;
+    else b = mid;
+  }
+  return a;
+}
+
+// Per-block staging of queue appends: entries are counted per part in shared
+// memory and leave the block with one global atomic per part.
+struct PartStage {
+  u32 *buf;   // kSubStage vertices
+  u32 *pt;    // their parts
+  u32 *rank;  // their rank within the part in this block
+  u32 *cnt;   // per part
+  u32 *base;  // per part
+  u32 *n;
+};
+
+__device__ __forceinline__ void stage_push(PartStage &S, const Parts &P, u32 *queue, SubCtl *ctl, u32 u) {
+  const u32 j = part_of(P, u);
+  const u32 q = atomicAdd(S.n, 1u);
+  if (q < (u32)kSubStage) {
+    S.buf[q] = u;
+    S.pt[q] = j;
+    S.rank[q] = atomicAdd(S.cnt + j, 1u);
+  } else {
+    const u32 slot = atomicAdd(&ctl->tail[j], 1u);
+    if (slot < P.off[j + 1] - P.off[j]) queue[P.off[j] + slot] = u;
+    else atomicOr(&ctl->flags, (u32)FLAG_INTERNAL);
+  }
+}
+
+// Writes the block's staged entries; call with the whole block.
+__device__ __forceinline__ void stage_flush(PartStage &S, const Parts &P, u32 *queue, SubCtl *ctl) {
+  __syncthreads();
+  for (u32 j = threadIdx.x; j < P.p; j += blockDim.x) {
+    const u32 c = S.cnt[j];
+    S.base[j] = c ? atomicAdd(&ctl->tail[j], c) : 0u;
+  }
+  __syncthreads();
+  const u32 nn = min(*S.n, (u32)kSubStage);
+  for (u32 q = threadIdx.x; q < nn; q += blockDim.x) {
+    const u32 j = S.pt[q];
+    const u32 slot = S.base[j] + S.rank[q];
+    if (slot < P.off[j + 1] - P.off[j]) queue[P.off[j] + slot] = S.buf[q];
+    else atomicOr(&ctl->flags, (u32)FLAG_INTERNAL);
+  }
+  __syncthreads();
+  for (u32 j = threadIdx.x; j < P.p; j += blockDim.x) S.cnt[j] = 0;
+  if (threadIdx.x == 0) *S.n = 0;
+  __syncthreads();
+}
+
+#define PP_PART_STAGE                                                             \
+  __shared__ u32 s_buf[kSubStage], s_pt[kSubStage], s_rank[kSubStage];            \
+  __shared__ u32 s_cnt[kMaxParts], s_base[kMaxParts], s_n;                        \
+  PartStage S{s_buf, s_pt, s_rank, s_cnt, s_base, &s_n};                          \
+  for (u32 j = threadIdx.x; j < kMaxParts; j += blockDim.x) s_cnt[j] = 0;         \
+  if (threadIdx.x == 0) s_n = 0;                                                  \
+  __syncthreads();
+
+__global__ void k_kinit_sub(SubCtl *ctl, u64 n, u64 m, u32 k, u32 max_sub, u32 p) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    SubCtl c;
+    memset(&c, 0, sizeof c);
+    c.s = n;
+    c.m = m;
+    c.k = k;
+    c.max_sub = max_sub;
+    c.part = p - 1;  // the first sub-round looks at part 0
+    *ctl = c;
+  }
+}
+
+// The queues before the first sub-round: every vertex of degree < k.
+__global__ void __launch_bounds__(kKBlock) k_kscan_sub(const u32 *__restrict__ deg, u32 n, const Parts P,
+                                                       u32 *__restrict__ queue, int *__restrict__ vround,
+                                                       SubCtl *__restrict__ ctl) {
+  PP_PART_STAGE
+  const u32 k = ctl->k;
+  const u32 CH = kKBlock * 4;
+  for (u64 c0 = (u64)blockIdx.x * CH; c0 < n; c0 += (u64)gridDim.x * CH) {
+#pragma unroll
+    for (int it = 0; it < 4; ++it) {
+      const u64 v = c0 + (u64)it * kKBlock + threadIdx.x;
+      if (v < n) {
+        if (vround) vround[v] = 0;
+        if (deg[v] < k) stage_push(S, P, queue, ctl, (u32)v);
+      }
+    }
+    stage_flush(S, P, queue, ctl);
+  }
+}
+
+// One sub-round: remove the frontier of the current part and its edges.
+__global__ void __launch_bounds__(kKBlock) k_kpeel_sub(const u32 *__restrict__ edges, u32 r, u32 n,
+                                                       const u32 *__restrict__ off, const u32 *__restrict__ inc,
+                                                       u32 *__restrict__ alive, u32 *__restrict__ deg,
+                                                       const Parts P, u32 *__restrict__ queue,
+                                                       int *__restrict__ vround, int *__restrict__ eround,
+                                                       SubCtl *__restrict__ ctl) {
+  PP_PART_STAGE
+  __shared__ u64 s_red[kKBlock / 32];
+  const u32 t = *(volatile u32 *)&ctl->sub;
+  const u32 j = *(volatile u32 *)&ctl->part;
+  const u32 fb = *(volatile u32 *)&ctl->fb, fe = *(volatile u32 *)&ctl->fe;
+  const u32 k = ctl->k;
+  const u32 *front = queue + P.off[j];
+  u64 claimed = 0;
+  for (u64 c0 = (u64)fb + (u64)blockIdx.x * kKBlock; c0 < fe; c0 += (u64)gridDim.x * kKBlock) {
+    const u64 i = c0 + threadIdx.x;
+    if (i < fe) {
+      const u32 v = front[i];
+      if (vround) vround[v] = (int)t;
+      const u32 b = off[v], e_end = off[v + 1];
+      for (u32 q = b; q < e_end; ++q) {
+        const u32 e = inc[q];
+        const u32 bit = 1u << (e & 31u);
+        const u32 old = atomicAnd(alive + (e >> 5), ~bit);
+        if (!(old & bit)) continue;  // another vertex of this sub-round took it
+        ++claimed;
+        if (eround) eround[e] = (int)t;
+        for (u32 h = 0; h < r; ++h) {
+          const u32 u = edges[(u64)e * r + h];
+          if (u >= n) continue;
+          const u32 od = atomicSub(deg + u, 1u);
+          if (od == k) stage_push(S, P, queue, ctl, u);
+        }
+      }
+    }
+    stage_flush(S, P, queue, ctl);
+  }
+  const u64 c = block_sum<u64, kKBlock>(claimed, s_red);
+  if (threadIdx.x == 0 && c) atomicAdd(&ctl->claimed, c);
+}
+
+// End of a sub-round: statistics, then the next sub-round whose part has
+// something due (the idle ones in between keep their numbers and statistics).
+__global__ void k_kround_end_sub(SubCtl *__restrict__ ctl, PeelStats st, const Parts P, int set_cond,
+                                 cudaGraphConditionalHandle cond) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  SubCtl &c = *ctl;
+  const u32 t = c.sub;
+  if (t > 0) {
+    c.s -= c.fe - c.fb;
+    c.m -= c.claimed;
+    st.s[t - 1] = c.s;
+    st.m[t - 1] = c.m;
+    c.head[c.part] = c.fe;
+  }
+  c.claimed = 0;
+  u32 more = 0, d = 1;
+  for (; d <= P.p; ++d) {
+    const u32 j = (c.part + d) % P.p;
+    if (c.tail[j] > c.head[j]) {
+      more = 1;
+      break;
+    }
+  }
+  if (more && (u64)t + d > c.max_sub) {
+    c.flags |= FLAG_ROUND_LIMIT;
+    more = 0;
+  }
+  if (more) {
+    for (u32 q = 1; q < d; ++q) {  // idle sub-rounds
+      st.s[t + q - 1] = c.s;
+      st.m[t + q - 1] = c.m;
+    }
+    const u32 j = (c.part + d) % P.p;
+    c.sub = t + d;
+    c.part = j;
+    c.fb = c.head[j];
+    c.fe = c.tail[j];
+  }
+  c.more = more;
+  if (set_cond) cudaGraphSetConditional(cond, more);
+}
+
 }  // namespace pp
 
 namespace {
@@ -200,6 +419,7 @@ struct KWork {
   u32 *deg = nullptr, *off = nullptr, *cursor = nullptr, *inc = nullptr, *alive = nullptr;
   u32 *f0 = nullptr, *f1 = nullptr;
   PeelCtl *ctl = nullptr;
+  SubCtl *sub = nullptr;
   u64 *st_s = nullptr, *st_m = nullptr;
   void *scan_tmp = nullptr;
 };
@@ -230,14 +450,46 @@ struct KEndArgs {
   }
 };
 
-pp_status run_rounds(KPeelArgs &pa, KEndArgs &ea, int grid, bool host_loop, cudaStream_t s,
-                     PeelCtl *ctl) {
+struct KSubPeelArgs {
+  const u32 *edges;
+  u32 r, n;
+  const u32 *off, *inc;
+  u32 *alive, *deg;
+  Parts P;
+  u32 *queue;
+  int *vround, *eround;
+  SubCtl *ctl;
+  void *p[12];
+  void bind() {
+    void *q[12] = {&edges, &r, &n, &off, &inc, &alive, &deg, &P, &queue, &vround, &eround, &ctl};
+    memcpy(p, q, sizeof q);
+  }
+};
+
+struct KSubEndArgs {
+  SubCtl *ctl;
+  PeelStats st;
+  Parts P;
+  int set_cond;
+  cudaGraphConditionalHandle cond;
+  void *p[5];
+  void bind() {
+    void *q[5] = {&ctl, &st, &P, &set_cond, &cond};
+    memcpy(p, q, sizeof q);
+  }
+};
+
+// The round loop: a CUDA graph whose while node runs peel -> round_end until
+// round_end clears the condition, or the same kernels driven from the host.
+template <class EndArgs>
+pp_status run_rounds(const void *peel_fn, void **peel_p, const void *end_fn, EndArgs &ea, int grid,
+                     bool host_loop, cudaStream_t s, const u32 *d_more) {
   if (host_loop) {
     u32 more = 0;
     for (;;) {
-      PP_CUDA(cudaLaunchKernel((const void *)k_kpeel, dim3(grid), dim3(kKBlock), pa.p, 0, s));
-      PP_CUDA(cudaLaunchKernel((const void *)k_kround_end, dim3(1), dim3(32), ea.p, 0, s));
-      PP_CUDA(cudaMemcpyAsync(&more, &ctl->more, sizeof more, cudaMemcpyDeviceToHost, s));
+      PP_CUDA(cudaLaunchKernel(peel_fn, dim3(grid), dim3(kKBlock), peel_p, 0, s));
+      PP_CUDA(cudaLaunchKernel(end_fn, dim3(1), dim3(32), ea.p, 0, s));
+      PP_CUDA(cudaMemcpyAsync(&more, d_more, sizeof more, cudaMemcpyDeviceToHost, s));
       PP_CUDA(cudaStreamSynchronize(s));
       if (!more) break;
     }
@@ -267,15 +519,15 @@ pp_status run_rounds(KPeelArgs &pa, KEndArgs &ea, int grid, bool host_loop, cuda
   ea.set_cond = 1;
   ea.cond = h;
   ea.bind();
-  kp.func = (void *)k_kpeel;
+  kp.func = (void *)peel_fn;
   kp.gridDim = dim3(grid);
   kp.blockDim = dim3(kKBlock);
-  kp.kernelParams = pa.p;
+  kp.kernelParams = peel_p;
   if (cudaGraphAddKernelNode(&n_peel, body, nullptr, 0, &kp) != cudaSuccess) {
     st = fail(PP_ERR_CUDA, "cudaGraphAddKernelNode(peel) failed");
     goto done;
   }
-  kp.func = (void *)k_kround_end;
+  kp.func = (void *)end_fn;
   kp.gridDim = dim3(1);
   kp.blockDim = dim3(32);
   kp.kernelParams = ea.p;
@@ -300,9 +552,9 @@ done:
 
 }  // namespace
 
-extern "C" pp_status pp_peel_kcore(uint32_t n, uint32_t r, uint32_t k, const uint32_t *d_edges,
-                                   uint64_t m, int32_t *d_vertex_round, int32_t *d_edge_round,
-                                   pp_peel_result *res, const pp_options *opt, void *stream) {
+static pp_status peel_kcore_impl(uint32_t n, uint32_t r, uint32_t k, const uint32_t *d_edges, uint64_t m,
+                          const Parts *parts, int32_t *d_vertex_round, int32_t *d_edge_round,
+                          pp_peel_result *res, const pp_options *opt, void *stream) {
   if (!res) return fail(PP_ERR_INVALID_ARG, "pp_peel_kcore: NULL result");
   if (k < 1) return fail(PP_ERR_INVALID_ARG, "pp_peel_kcore: k=%u < 1", k);
   if (r < 2 || r > PP_MAX_R) return fail(PP_ERR_INVALID_ARG, "pp_peel_kcore: r=%u outside 2..%d", r, PP_MAX_R);
@@ -325,11 +577,13 @@ extern "C" pp_status pp_peel_kcore(uint32_t n, uint32_t r, uint32_t k, const uin
   al((void **)&w.f0, nn * 4);
   al((void **)&w.f1, nn * 4);
   al((void **)&w.ctl, sizeof(PeelCtl));
+  if (parts) al((void **)&w.sub, sizeof(SubCtl));
   al((void **)&w.st_s, (size_t)o.max_rounds * 8);
   al((void **)&w.st_m, (size_t)o.max_rounds * 8);
   al(&w.scan_tmp, exclusive_scan_temp_bytes(nn));
   pp_status status = PP_OK;
   PeelCtl hc{};
+  SubCtl hsub{};
   uint32_t T = 0, ncopy = 0;
   if (e != cudaSuccess) {
     status = cuda_fail(e, "pp_peel_kcore workspace", __FILE__, __LINE__);
@@ -355,22 +609,47 @@ extern "C" pp_status pp_peel_kcore(uint32_t n, uint32_t r, uint32_t k, const uin
       goto cleanup;
     }
     if (m) k_scatter<<<egrid, kKBlock, 0, s>>>(d_edges, m, r, n, w.cursor, w.inc);
-    if (n) k_kscan<<<vgrid, kKBlock, 0, s>>>(w.deg, n, w.f0, d_vertex_round, w.ctl);
+    if (parts) {
+      k_kinit_sub<<<1, 32, 0, s>>>(w.sub, n, m, k, o.max_rounds, parts->p);
+      if (n) k_kscan_sub<<<vgrid, kKBlock, 0, s>>>(w.deg, n, *parts, w.f0, d_vertex_round, w.sub);
+    } else if (n) {
+      k_kscan<<<vgrid, kKBlock, 0, s>>>(w.deg, n, w.f0, d_vertex_round, w.ctl);
+    }
     if ((e = cudaGetLastError()) != cudaSuccess) {
       status = cuda_fail(e, "pp_peel_kcore build kernels", __FILE__, __LINE__);
       goto cleanup;
     }
-    KPeelArgs pa{d_edges, r, n, w.off, w.inc, w.alive, w.deg, w.f0, w.f1, d_vertex_round, d_edge_round, w.ctl, {}};
-    pa.bind();
-    KEndArgs ea{w.ctl, PeelStats{w.st_s, w.st_m}, 0, 0, {}};
-    ea.bind();
-    const int pgrid = persistent_grid((const void *)k_kpeel, kKBlock, 0, o.ctas_per_sm);
-    status = run_rounds(pa, ea, pgrid, o.host_loop != 0, s, w.ctl);
+    if (parts) {
+      KSubPeelArgs pa{d_edges, r, n, w.off, w.inc, w.alive, w.deg, *parts, w.f0, d_vertex_round,
+                      d_edge_round, w.sub, {}};
+      pa.bind();
+      KSubEndArgs ea{w.sub, PeelStats{w.st_s, w.st_m}, *parts, 0, 0, {}};
+      ea.bind();
+      const int pgrid = persistent_grid((const void *)k_kpeel_sub, kKBlock, 0, o.ctas_per_sm);
+      status = run_rounds((const void *)k_kpeel_sub, pa.p, (const void *)k_kround_end_sub, ea, pgrid,
+                          o.host_loop != 0, s, &w.sub->more);
+    } else {
+      KPeelArgs pa{d_edges, r, n, w.off, w.inc, w.alive, w.deg, w.f0, w.f1, d_vertex_round, d_edge_round,
+                   w.ctl, {}};
+      pa.bind();
+      KEndArgs ea{w.ctl, PeelStats{w.st_s, w.st_m}, 0, 0, {}};
+      ea.bind();
+      const int pgrid = persistent_grid((const void *)k_kpeel, kKBlock, 0, o.ctas_per_sm);
+      status = run_rounds((const void *)k_kpeel, pa.p, (const void *)k_kround_end, ea, pgrid,
+                          o.host_loop != 0, s, &w.ctl->more);
+    }
     if (status != PP_OK) goto cleanup;
     if ((e = cudaMemcpyAsync(&hc, w.ctl, sizeof hc, cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
+        (parts && (e = cudaMemcpyAsync(&hsub, w.sub, sizeof hsub, cudaMemcpyDeviceToHost, s)) != cudaSuccess) ||
         (e = cudaStreamSynchronize(s)) != cudaSuccess) {
       status = cuda_fail(e, "pp_peel_kcore readback", __FILE__, __LINE__);
       goto cleanup;
+    }
+    if (parts) {
+      hc.round = hsub.sub;
+      hc.flags |= hsub.flags;
+      hc.s = hsub.s;
+      hc.m = hsub.m;
     }
     T = hc.round;
     ncopy = T < res->round_cap ? T : res->round_cap;
@@ -388,8 +667,9 @@ extern "C" pp_status pp_peel_kcore(uint32_t n, uint32_t r, uint32_t k, const uin
     res->core_vertices = hc.s;
     res->core_edges = hc.m;
     if (hc.flags & FLAG_BAD_ID) status = fail(PP_ERR_INVALID_ARG, "pp_peel_kcore: a vertex id is >= n=%u", n);
+    else if (hc.flags & FLAG_INTERNAL) status = fail(PP_ERR_CUDA, "pp_peel_kcore: a part queue overflowed");
     else if (hc.flags & FLAG_ROUND_LIMIT)
-      status = fail(PP_ERR_ROUND_LIMIT, "pp_peel_kcore: stopped after max_rounds=%u rounds", o.max_rounds);
+      status = fail(PP_ERR_ROUND_LIMIT, "pp_peel_kcore: stopped after max_rounds=%u (sub-)rounds", o.max_rounds);
   }
 cleanup:
   cudaFreeAsync(w.deg, s);
@@ -400,9 +680,35 @@ cleanup:
   cudaFreeAsync(w.f0, s);
   cudaFreeAsync(w.f1, s);
   cudaFreeAsync(w.ctl, s);
+  cudaFreeAsync(w.sub, s);
   cudaFreeAsync(w.st_s, s);
   cudaFreeAsync(w.st_m, s);
   cudaFreeAsync(w.scan_tmp, s);
   cudaStreamSynchronize(s);
   return status;
+}
+
+extern "C" pp_status pp_peel_kcore(uint32_t n, uint32_t r, uint32_t k, const uint32_t *d_edges,
+                                   uint64_t m, int32_t *d_vertex_round, int32_t *d_edge_round,
+                                   pp_peel_result *res, const pp_options *opt, void *stream) {
+  return peel_kcore_impl(n, r, k, d_edges, m, nullptr, d_vertex_round, d_edge_round, res, opt, stream);
+}
+
+extern "C" pp_status pp_peel_kcore_subrounds(uint32_t n, uint32_t r, uint32_t k, const uint32_t *d_edges,
+                                             uint64_t m, uint32_t n_parts, const uint32_t *h_part_off,
+                                             int32_t *d_vertex_round, int32_t *d_edge_round,
+                                             pp_peel_result *res, const pp_options *opt, void *stream) {
+  if (n_parts < 1 || n_parts > (uint32_t)kMaxParts)
+    return fail(PP_ERR_INVALID_ARG, "pp_peel_kcore_subrounds: n_parts=%u outside 1..%d", n_parts, kMaxParts);
+  if (!h_part_off) return fail(PP_ERR_INVALID_ARG, "pp_peel_kcore_subrounds: NULL part offsets");
+  if (h_part_off[0] != 0 || h_part_off[n_parts] != n)
+    return fail(PP_ERR_INVALID_ARG, "pp_peel_kcore_subrounds: part offsets must run from 0 to n=%u", n);
+  Parts P{};
+  P.p = n_parts;
+  for (uint32_t j = 0; j <= n_parts; ++j) {
+    if (j && h_part_off[j] < h_part_off[j - 1])
+      return fail(PP_ERR_INVALID_ARG, "pp_peel_kcore_subrounds: part offsets decrease at %u", j);
+    P.off[j] = h_part_off[j];
+  }
+  return peel_kcore_impl(n, r, k, d_edges, m, &P, d_vertex_round, d_edge_round, res, opt, stream);
 }

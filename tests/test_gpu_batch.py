@@ -208,3 +208,29 @@ def test_binned_batch_decode_after_deletions(ppb):
         region = np.sort(got[int(ooff[i]): int(ooff[i]) + int(res.recovered[i])])
         want = np.sort(np.concatenate(ores["keys"])) if ores["keys"] else np.zeros(0, np.uint64)
         assert (region == want).all()
+
+
+@pytest.mark.parametrize("binned", [1, 2])
+def test_batch_deleting_keys_never_inserted(ppb, binned):
+    """Negative counts in every table: the per-table residue is the number of
+    cells with a non-zero count, as in the oracle, with either round kind."""
+    pp, bm = ppb
+    specs = _specs(20, 93 + binned, rs=(3, 4), lo=10, hi=15, c_lo=0.5, c_hi=0.9)
+    keys = [ppgen.distinct_keys(ppgen.edges_from_c(s[2], s[0]), s[4]) for s in specs]
+    ghost = [ppgen.distinct_keys(max(1, s[0] // 20), 1000 + i) for i, s in enumerate(specs)]
+    koff = np.concatenate([[0], np.cumsum([k.size for k in keys])]).astype(np.uint64)
+    goff = np.concatenate([[0], np.cumsum([g.size for g in ghost])]).astype(np.uint64)
+    b = bm.Batch([s[0] for s in specs], [s[1] for s in specs], [s[3] for s in specs],
+                 pp.options(binned=binned))
+    b.insert(torch.from_numpy(np.concatenate(keys).view(np.int64)).cuda(), koff)
+    b.delete(torch.from_numpy(np.concatenate(ghost).view(np.int64)).cuda(), goff)
+    out = torch.full((int(koff[-1]),), -1, dtype=torch.int64, device="cuda")
+    res = b.decode(out, koff)
+    for i, s in enumerate(specs):
+        ot = oracle.IBLT(s[0], s[1], s[3])
+        ot.insert(keys[i])
+        ot.insert(ghost[i], sign=-1)
+        ores = ot.decode_rounds()
+        assert res.rounds[i] == ores["rounds"], i
+        assert res.recovered[i] == sum(k.size for k in ores["keys"]), i
+        assert res.residual_cells[i] == ot.residual_cells(), i

@@ -141,6 +141,29 @@ def test_deletions(pp):
     run_case(pp, 50000, 3, keys, 31, deletes=dele)
 
 
+@pytest.mark.parametrize("n,binned", [(50000, 2), (1 << 22, 1)])
+def test_deleting_keys_never_inserted(pp, n, binned):
+    """Cells left with negative counts: the residue count is every cell with a
+    non-zero count, as in the oracle (a count can go from 0 to -1 while keys
+    are deleted from the table during the decode)."""
+    r, seed = 3, 61
+    keys = ppgen.distinct_keys(int(0.6 * n), 62)
+    ghost = ppgen.distinct_keys(int(0.05 * n), 63)
+    gt = pp.IBLT(n, r, seed, pp.options(binned=binned))
+    ot = oracle.IBLT(n, r, seed)
+    gt.insert(_dev(keys))
+    gt.delete(_dev(ghost))
+    ot.insert(keys)
+    ot.insert(ghost, sign=-1)
+    out = torch.zeros(keys.size, dtype=torch.int64, device="cuda")
+    res = gt.decode(out)
+    ores = ot.decode_rounds()
+    assert res.rounds == ores["rounds"]
+    assert res.recovered_per_round == [k.size for k in ores["keys"]]
+    _assert_cells_equal(gt.cells(), ot)
+    assert res.residual_cells == ot.residual_cells()
+
+
 def test_round_limit(pp):
     keys = ppgen.distinct_keys(ppgen.edges_from_c(0.80, 100000), 41)
     with pytest.raises(pp.PPError) as ei:
