@@ -299,6 +299,70 @@ def bench_served(pp, torch, args):
             "iterations": st["iterations"], "keys_source": "generated on the device from request seeds"}
 
 
+def bench_subrounds(pp, torch, table, dkeys, out, stream, m, steps):
+    """The headline table decoded in the paper's own order: one sub-table per
+    sub-round (Sec. 6 "Implementation Details", App. B), same build."""
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    table.build(dkeys, stream)
+    res = table.decode_subrounds(out, stream=stream)
+    assert res.recovered == m and res.residual_cells == 0
+    ms = []
+    for _ in range(steps):
+        table.build(dkeys, stream)
+        ev[0].record(stream)
+        res = table.decode_subrounds(out, stream=stream)
+        ev[1].record(stream)
+        stream.synchronize()
+        ms.append(ev[0].elapsed_time(ev[1]))
+    d = float(np.mean(ms))
+    return {"workload": "headline table, one sub-table per sub-round", "decode_ms": d,
+            "decode_keys_per_s": res.recovered / (d * 1e-3), "subrounds": res.rounds,
+            "recovered_per_subround_first": res.recovered_per_round[:6]}
+
+
+def bench_kcore(pp, torch, args):
+    """k-core peeling of the density sweep (n = 2^25 vertices in 4 parts, r = 4,
+    k = 2, one vertex per part per edge): the whole call (incidence build +
+    rounds) in full rounds and in sub-rounds."""
+    cfg = ppgen.DENSITY_SWEEP
+    n, r, k = cfg["n"], cfg["r"], cfg["k"]
+    off = [int(x) for x in np.asarray(ppgen.part_offsets(n, r))]
+    stream = torch.cuda.Stream()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    rows = []
+    for c in cfg["cs"]:
+        m = ppgen.edges_from_c(c, n)
+        e = ppgen.partitioned_edges(n, r, m, cfg["seed"])
+        with torch.cuda.stream(stream):
+            d = torch.from_numpy(e.view(np.int32)).cuda()
+        stream.synchronize()
+        del e
+
+        def timed(fn, reps=3):
+            fn()
+            best = []
+            for _ in range(reps):
+                ev[0].record(stream)
+                res = fn()
+                ev[1].record(stream)
+                stream.synchronize()
+                best.append(ev[0].elapsed_time(ev[1]))
+            return res, float(np.median(best))
+
+        full, full_ms = timed(lambda: pp.peel_kcore(n, r, k, d, stream=stream))
+        sub, sub_ms = timed(lambda: pp.peel_kcore_subrounds(n, r, k, d, off, stream=stream, round_cap=1 << 14))
+        rows.append({"c": c, "edges": m, "rounds": full.rounds, "core_vertices": full.core_vertices,
+                     "core_edges": full.core_edges, "ms": full_ms, "edges_per_s": m / (full_ms * 1e-3),
+                     "subrounds": sub.rounds, "subround_ms": sub_ms,
+                     "same_core": bool(sub.core_vertices == full.core_vertices
+                                       and sub.core_edges == full.core_edges)})
+        del d
+        torch.cuda.empty_cache()
+    return {"workload": cfg["name"], "k": k, "parts": r,
+            "timed": "one pp_peel_kcore call: degree histogram, scan, incidence scatter, rounds",
+            "densities": rows}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -426,6 +490,11 @@ def main():
                "h2d_bytes_per_step": int(m * 8), "d2h_bytes_per_step": int(m * 8),
                "ms_per_step": e_ms / args.steps}
 
+    # kernels of one step: the binned build (k_bin, then one k_apply per 2^21-cell
+    # slab), the scan, and five kernels per loop iteration (rounds + the first
+    # promote-only iteration)
+    launches_per_step = 1 + -(-n // (1 << 21)) + 1 + 5 * (rounds + 1)
+
     # roofline of the two halves of a step (sector-floor byte model)
     peak, peak_kind = hbm_peak()
     build_bytes = m * (8 + 64 * r)                 # key read + r cell sectors read+written
@@ -444,14 +513,17 @@ def main():
                 "kernel": dk["kernel"], "peak_source": f"{peak_kind} hbm_gbs",
                 "model": "sector floor: 32 B/cell scan + (64r+8) B/key decode; (8+64r) B/key build"}
 
-    batched = served = None
+    batched = served = subrounds = kcore = None
     if world == 1 and not args.no_extra:
+        subrounds = bench_subrounds(pp, torch, table, dkeys, out, stream, m, max(3, min(args.steps, 5)))
         table.close()
         torch.cuda.empty_cache()
         del dkeys, out
         batched = bench_batched(pp, torch, args)
         torch.cuda.empty_cache()
         served = bench_served(pp, torch, args)
+        torch.cuda.empty_cache()
+        kcore = bench_kcore(pp, torch, args)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -471,8 +543,8 @@ def main():
                 "build_ms": b_ms, "decode_ms": d_ms, "peel_ms": d_ms,
                 "decode_keys_per_s": m / (d_ms * 1e-3),
                 "kernels": kernels, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
-                "batched": batched, "served": served,
-                "gpu_launches": args.steps * (2 + 3 * (rounds + 1)), "clocks": clk}
+                "batched": batched, "served": served, "subrounds": subrounds, "kcore": kcore,
+                "gpu_launches": args.steps * launches_per_step, "clocks": clk}
         print(json.dumps(line), flush=True)
     if batched is None:
         table.close()
