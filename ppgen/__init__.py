@@ -283,11 +283,55 @@ def distinct_uniform_edges(n: int, r: int, m: int, seed: int) -> np.ndarray:
     Rows that repeat a vertex are redrawn from further xorshift64* streams
     (seed + 1, seed + 2, ...) until every row is repeat-free."""
     out = uniform_edges(n, r, m, seed)
+    bad = np.nonzero(_has_repeat(out))[0]
     bump = 1
-    while True:
-        srt = np.sort(out, axis=1)
-        bad = np.nonzero((srt[:, 1:] == srt[:, :-1]).any(axis=1))[0] if r > 1 else np.zeros(0, int)
-        if bad.size == 0:
-            return out
+    while bad.size:
         out[bad] = uniform_edges(n, r, bad.size, seed + bump)
+        bad = bad[_has_repeat(out[bad])]
         bump += 1
+    return out
+
+
+def _has_repeat(rows: np.ndarray) -> np.ndarray:
+    """Per row: does some vertex appear twice?"""
+    bad = np.zeros(rows.shape[0], dtype=bool)
+    for a in range(rows.shape[1]):
+        for b in range(a + 1, rows.shape[1]):
+            bad |= rows[:, a] == rows[:, b]
+    return bad
+
+
+def trials_union(n: int, r: int, m: int, trials: int, seed: int, kind: str = "distinct"):
+    """`trials` independent hypergraphs of n vertices and m edges as one
+    hypergraph on trials * n vertices (their disjoint union), so that one peel
+    runs every trial at once: trials never share a vertex, so each peels
+    exactly as it would alone.
+
+    kind="distinct": G^r_{n,cn} (r distinct vertices per edge); trial i owns
+    vertex ids i*n .. (i+1)*n - 1.  kind="partitioned": one vertex per part
+    (the sub-table model); the union keeps r contiguous parts, part j holding
+    part j of every trial in trial order, so that a sub-round of part j is the
+    sub-round of part j in every trial.
+
+    Returns (edges (trials*m, r) uint32, union part offsets (r+1 ints) or None,
+    to_trials) where to_trials(x) maps a per-vertex array of the union to a
+    (trials, n) array in each trial's own vertex order."""
+    T = int(trials)
+    if kind == "distinct":
+        e = distinct_uniform_edges(n, r, m * T, seed)
+        e += (np.arange(T, dtype=np.uint64).repeat(m) * n).astype(np.uint32)[:, None]
+        return e, None, lambda x: np.asarray(x).reshape(T, n)
+    if kind != "partitioned":
+        raise ValueError(kind)
+    offs, sizes = part_offsets(n, r), part_sizes(n, r)
+    e = _edges(seed, m * T, offs, sizes)
+    trial = np.arange(T, dtype=np.int64).repeat(m)
+    for j in range(r):
+        col = e[:, j].astype(np.int64)
+        e[:, j] = (T * offs[j] + trial * sizes[j] + (col - offs[j])).astype(np.uint32)
+    uoff = [T * o for o in offs[:r]] + [T * n]
+
+    def to_trials(x):
+        x = np.asarray(x)
+        return np.concatenate([x[uoff[j]:uoff[j + 1]].reshape(T, sizes[j]) for j in range(r)], axis=1)
+    return e, uoff, to_trials

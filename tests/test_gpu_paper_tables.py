@@ -1,0 +1,97 @@
+"""The paper's simulation tables reproduced on the GPU.
+
+Each table entry is a mean over many random hypergraphs.  The trials are
+peeled together: ``ppgen.trials_union`` lays them out as one hypergraph whose
+components are the trials (disjoint vertex ranges), so one ``pp_peel_kcore``
+(or ``pp_peel_kcore_subrounds``) call runs every trial in lockstep.  A trial's
+round count is the last round in which one of its vertices went; the mean
+survivor count after round t is the union's count divided by the number of
+trials.
+
+Tolerances: 4-5 standard errors of our own mean (plus the table's rounding);
+the paper used 1000 trials per entry.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import ppgen
+from conftest import read_golden
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def pp(ppeel_lib):
+    import paper_1302_7014_b300 as pp
+    return pp
+
+
+def run_trials(pp, n, r, c, trials, seed, kind, k=2):
+    m = ppgen.edges_from_c(c, n)
+    e, uoff, to_trials = ppgen.trials_union(n, r, m, trials, seed, kind)
+    N = n * trials
+    d = torch.from_numpy(e.view(np.int32)).cuda()
+    del e
+    vr = torch.empty(N, dtype=torch.int32, device="cuda")
+    if kind == "partitioned":
+        res = pp.peel_kcore_subrounds(N, r, k, d, uoff, vr, round_cap=1 << 14)
+    else:
+        res = pp.peel_kcore(N, r, k, d, vr, round_cap=1 << 14)
+    per = to_trials(vr.cpu().numpy())
+    rounds = per.max(axis=1).astype(float)
+    failed = int((per == 0).any(axis=1).sum())
+    left = np.array(res.vertices_left, float) / trials
+    return rounds, failed, left, res
+
+
+@pytest.mark.parametrize("row", [0, 2])
+@pytest.mark.parametrize("col,c", [(1, 0.70), (3, 0.75), (5, 0.80), (7, 0.85)])
+def test_table1_mean_rounds(pp, row, col, c):
+    line = read_golden("table1_rounds.txt")[row]
+    n = int(line[0])
+    want_fail, want = int(line[col]), float(line[col + 1])
+    rounds, failed, _, _ = run_trials(pp, n, 4, c, 1000, 11 + row + col, "distinct")
+    se = rounds.std(ddof=1) / math.sqrt(rounds.size)
+    assert abs(rounds.mean() - want) < 4 * se + 0.02, (rounds.mean(), want)
+    assert failed == want_fail
+
+
+@pytest.mark.parametrize("pcol,ecol,c", [(1, 2, 0.70), (3, 4, 0.85)])
+def test_table2_mean_survivors(pp, pcol, ecol, c):
+    rows = read_golden("table2_prediction.txt")
+    trials = 100
+    _, _, left, res = run_trials(pp, 10**6, 4, c, trials, 23 + pcol, "distinct")
+    left = list(left) + [left[-1]] * (len(rows) - len(left))
+    # the spread of one trial's count: sqrt(n) in round 1, a few thousand in
+    # the cascade rounds (Table 2's own rounds 7-11 at c = 0.7)
+    for row in rows:
+        t, exp = int(row[0]), float(row[ecol])
+        sd = 1000.0 if t < 6 else 6000.0
+        assert abs(left[t - 1] - exp) < 5 * sd / math.sqrt(trials) + 1.0, (t, left[t - 1], exp)
+
+
+@pytest.mark.parametrize("col,c", [(1, 0.70), (3, 0.75)])
+def test_table5_mean_subrounds(pp, col, c):
+    line = read_golden("table5_subrounds.txt")[0]
+    n = int(line[0])
+    want_fail, want = int(line[col]), float(line[col + 1])
+    rounds, failed, _, _ = run_trials(pp, n, 4, c, 1000, 31 + col, "partitioned")
+    se = rounds.std(ddof=1) / math.sqrt(rounds.size)
+    assert abs(rounds.mean() - want) < 4 * se + 0.02, (rounds.mean(), want)
+    assert failed == want_fail
+
+
+def test_table6_mean_survivors_per_subround(pp):
+    rows = read_golden("table6_prediction.txt")
+    trials = 100
+    _, _, left, _ = run_trials(pp, 10**6, 4, 0.70, trials, 41, "partitioned")
+    left = list(left) + [0.0] * (len(rows) - len(left))
+    for row in rows:
+        i, j, exp = int(row[0]), int(row[1]), float(row[3])
+        s = (i - 1) * 4 + j
+        sd = 1500.0 if s <= 8 else 6000.0
+        assert abs(left[s - 1] - exp) < 5 * sd / math.sqrt(trials) + 1.0, (i, j, left[s - 1], exp)

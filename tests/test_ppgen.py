@@ -79,3 +79,31 @@ def test_serving_recipe():
     gaps = np.diff(times)
     assert abs(gaps.mean() * 20000.0 - 1.0) < 0.05
     assert all(1024 <= s.n_cells < (1 << 22) and s.r == 3 and 0.6 <= s.c <= 0.8 for _, s in reqs)
+
+
+def test_trials_union_is_a_disjoint_union():
+    import oracle
+    n, r, m, T = 300, 4, 210, 7
+    for kind in ("distinct", "partitioned"):
+        e, uoff, to_trials = ppgen.trials_union(n, r, m, T, 5, kind)
+        assert e.shape == (m * T, r)
+        if kind == "partitioned":
+            assert uoff == [T * o for o in ppgen.part_offsets(n, r)[:r]] + [T * n]
+            whole = oracle.kcore_subrounds(n * T, 2, e, uoff)
+        else:
+            assert uoff is None
+            whole = oracle.kcore_rounds(n * T, 2, e)
+        per = to_trials(whole["vround"])
+        # each trial, peeled alone, removes the same vertices in the same
+        # (sub-)rounds as inside the union
+        for i in range(T):
+            rows = e[i * m:(i + 1) * m].astype(np.int64)
+            if kind == "partitioned":
+                offs, sizes = ppgen.part_offsets(n, r), ppgen.part_sizes(n, r)
+                local = np.stack([rows[:, j] - T * offs[j] - i * sizes[j] + offs[j] for j in range(r)], axis=1)
+                alone = oracle.kcore_subrounds(n, 2, local.astype(np.uint32), offs[:r] + [n])
+            else:
+                local = rows - i * n
+                alone = oracle.kcore_rounds(n, 2, local.astype(np.uint32))
+            assert (local >= 0).all() and (local < n).all()
+            assert (per[i] == alone["vround"]).all(), (kind, i)
