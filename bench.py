@@ -363,6 +363,42 @@ def bench_kcore(pp, torch, args):
             "densities": rows}
 
 
+def bench_tables(pp, torch, args):
+    """Table 1 (rounds of G^4_{n,cn}, k = 2) and Table 5 (sub-rounds with 4
+    sub-tables) at n = 10^4, 1000 trials per density, each density one peel of
+    the trials' disjoint union (10^7 vertices)."""
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    n, r, trials = 10000, 4, 1000
+    out = {"workload": "n=10^4, r=4, k=2, 1000 trials per density as one disjoint union",
+           "table1": [], "table5": []}
+    for name, kind, cs in (("table1", "distinct", (0.70, 0.75, 0.80, 0.85)),
+                           ("table5", "partitioned", (0.70, 0.75))):
+        for c in cs:
+            e, uoff, to_trials = ppgen.trials_union(n, r, ppgen.edges_from_c(c, n), trials, 7, kind)
+            d = torch.from_numpy(e.view(np.int32)).cuda()
+            vr = torch.empty(n * trials, dtype=torch.int32, device="cuda")
+
+            def run():
+                if uoff is None:
+                    return pp.peel_kcore(n * trials, r, 2, d, vr, round_cap=1 << 12)
+                return pp.peel_kcore_subrounds(n * trials, r, 2, d, uoff, vr, round_cap=1 << 12)
+            run()
+            torch.cuda.synchronize()
+            ev[0].record()
+            run()
+            ev[1].record()
+            torch.cuda.synchronize()
+            ms = ev[0].elapsed_time(ev[1])
+            per = to_trials(vr.cpu().numpy())
+            rounds = per.max(axis=1)
+            out[name].append({"c": c, "mean_rounds": float(rounds.mean()),
+                              "failed": int((per == 0).any(axis=1).sum()), "ms": ms,
+                              "trials_per_s": trials / (ms * 1e-3)})
+            del d, vr
+    torch.cuda.empty_cache()
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -513,7 +549,7 @@ def main():
                 "kernel": dk["kernel"], "peak_source": f"{peak_kind} hbm_gbs",
                 "model": "sector floor: 32 B/cell scan + (64r+8) B/key decode; (8+64r) B/key build"}
 
-    batched = served = subrounds = kcore = None
+    batched = served = subrounds = kcore = tables = None
     if world == 1 and not args.no_extra:
         subrounds = bench_subrounds(pp, torch, table, dkeys, out, stream, m, max(3, min(args.steps, 5)))
         table.close()
@@ -524,6 +560,7 @@ def main():
         served = bench_served(pp, torch, args)
         torch.cuda.empty_cache()
         kcore = bench_kcore(pp, torch, args)
+        tables = bench_tables(pp, torch, args)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -544,6 +581,7 @@ def main():
                 "decode_keys_per_s": m / (d_ms * 1e-3),
                 "kernels": kernels, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
                 "batched": batched, "served": served, "subrounds": subrounds, "kcore": kcore,
+                "paper_tables": tables,
                 "gpu_launches": args.steps * launches_per_step, "clocks": clk}
         print(json.dumps(line), flush=True)
     if batched is None:

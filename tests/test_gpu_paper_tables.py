@@ -95,3 +95,16 @@ def test_table6_mean_survivors_per_subround(pp):
         s = (i - 1) * 4 + j
         sd = 1500.0 if s <= 8 else 6000.0
         assert abs(left[s - 1] - exp) < 5 * sd / math.sqrt(trials) + 1.0, (i, j, left[s - 1], exp)
+
+
+def test_rounds_growth_k3_graphs(pp):
+    # k = 3 on graphs (r = 2; c*_{3,2} ~ 1.675): below the threshold the round
+    # count barely moves between n = 10^4 and 10^6 (Thm 1: log log n / log((k-1)(r-1))
+    # + O(1)); above it, the count grows with log n (Thm 3)
+    def mean_rounds(n, c, trials, seed):
+        rounds, _, _, _ = run_trials(pp, n, 2, c, trials, seed, "distinct", k=3)
+        return rounds.mean()
+    below = [mean_rounds(10**4, 1.45, 500, 51), mean_rounds(10**6, 1.45, 20, 52)]
+    above = [mean_rounds(10**4, 1.85, 500, 53), mean_rounds(10**6, 1.85, 20, 54)]
+    assert below[1] - below[0] < 1.5, below
+    assert above[1] - above[0] > 3.0, above
