@@ -66,7 +66,8 @@ struct pp_batch {
   u64 *h_residual = nullptr;
   uint32_t n_bins = 0, bin_cap = 0, n_slabs = 0, bin_shift = 0;
   size_t smem_claim = 0, smem_apply_round = 0, smem_bin = 0;
-  int grid_claim = 0, grid_apply_round = 0, grid_bin = 0, grid_apply = 0;
+  int grid_claim = 0, grid_apply_round = 0, grid_bin = 0;
+  TileBufs tiles;  // tile pass of the binned build (allocated on first use)
 };
 
 namespace {
@@ -110,6 +111,7 @@ void free_batch(pp_batch *b) {
   cudaFree(b->rec_tab);
   cudaFree(b->bin_count);
   cudaFree(b->bin_overflow);
+  free_tiles(b->tiles);
   delete b;
 }
 
@@ -417,7 +419,6 @@ pp_status pp_batch_create(pp_batch **out, uint32_t n_tables, const uint64_t *n_c
   b->grid_peel = persistent_grid(b->k.peel, kBlock, b->smem_peel, b->opt.ctas_per_sm);
   b->grid_filter = persistent_grid(b->k.filter, kBlock, 0, b->opt.ctas_per_sm);
   b->grid_insert = persistent_grid(b->k.insert, kBlock, 0, 8) * 2;
-  b->grid_apply = persistent_grid(b->k.apply, kBlock, 0, 8);
   b->max_r = max_r;
   *out = b;
   return PP_OK;
@@ -532,20 +533,11 @@ static pp_status batch_bin_pass(pp_batch *b, const uint64_t *d_keys, const uint6
 
 // Pass 2: slab by slab (zero-filled first when building from scratch).
 static pp_status batch_apply_pass(pp_batch *b, BinArgs &ba, int sign, bool zero_fill, cudaStream_t s) {
-  Cell *cells = b->cells;
+  const uint64_t tile_cap = (uint64_t)((double)ba.cap / kTilesPerSlab * 1.15) + 256;
+  pp_status st = ensure_tiles(b->tiles, tile_cap, ba.cap, ba.n_slabs, true, s);
+  if (st != PP_OK) return st;
   TableArgs t0{};
-  const TableArgs *tabs = b->tabs;
-  u32 slab = 0;
-  void *args[] = {&cells, &t0, &tabs, &ba, &slab, &sign};
-  for (slab = 0; slab < ba.n_slabs; ++slab) {
-    if (zero_fill) {
-      const uint64_t c0 = (uint64_t)slab * kSlabCells;
-      const uint64_t c1 = c0 + kSlabCells < b->total_cells ? c0 + kSlabCells : b->total_cells;
-      PP_CUDA(cudaMemsetAsync(b->cells + c0, 0, (c1 - c0) * sizeof(Cell), s));
-    }
-    PP_CUDA(cudaLaunchKernel(b->k.apply, dim3(b->grid_apply), dim3(kBlock), args, 0, s));
-  }
-  return PP_OK;
+  return tile_apply_pass(b->cells, t0, b->tabs, ba, b->tiles, b->total_cells, sign, zero_fill, s);
 }
 
 static void add_items(pp_batch *b, const uint64_t *h_key_offsets, int sign) {

@@ -110,4 +110,25 @@ __device__ __forceinline__ T block_sum(T v, T *scratch /* BLOCK/32 entries */) {
   return s;
 }
 
+// L2 eviction-priority policy "evict last" for the whole access (PTX
+// createpolicy), and stores that carry a policy: for data written by one
+// kernel and read back by the next.
+__device__ __forceinline__ u64 l2_evict_last_policy() {
+  u64 p;
+  asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+__device__ __forceinline__ void st_l2_policy(u64 *a, u64 v, u64 pol) {
+  asm volatile("st.global.L2::cache_hint.b64 [%0], %1, %2;" ::"l"(a), "l"(v), "l"(pol) : "memory");
+}
+__device__ __forceinline__ void st_l2_policy(u32 *a, u32 v, u64 pol) {
+  asm volatile("st.global.L2::cache_hint.b32 [%0], %1, %2;" ::"l"(a), "r"(v), "l"(pol) : "memory");
+}
+
+// Invalidates the 128-byte L2 line at `a` (128-byte aligned) without writing
+// it back: for scratch data that no one reads again.
+__device__ __forceinline__ void l2_discard(const void *a) {
+  asm volatile("discard.global.L2 [%0], 128;" ::"l"(a) : "memory");
+}
+
 }  // namespace pp

@@ -32,8 +32,8 @@ static IbltKernels iblt_kernels_t() {
     attr_set = true;
   }
   IbltKernels k{(const void *)k_insert<R, B>, (const void *)k_scan<R, B>, (const void *)k_peel<R, B>,
-                (const void *)k_filter<R, B>, (const void *)k_bin<R, B>, (const void *)k_apply<R, B>,
-                (const void *)k_claim<R, B>, (const void *)k_apply_round<R, B>, nr_of<R>()};
+                (const void *)k_filter<R, B>, (const void *)k_bin<R, B>, (const void *)k_claim<R, B>,
+                (const void *)k_apply_round<R, B>, nr_of<R>()};
   if constexpr (!B && R >= 0) {
     k.sub_scan = (const void *)k_sscan<R>;
     k.sub_filter = (const void *)k_sfilter<R>;
@@ -97,7 +97,7 @@ struct pp_iblt {
   u64 *h_rec = nullptr, *h_alive = nullptr;
   int64_t items = 0;
   IbltKernels k{};
-  int grid_scan = 0, grid_peel = 0, grid_filter = 0, grid_insert = 0, grid_bin = 0, grid_apply = 0;
+  int grid_scan = 0, grid_peel = 0, grid_filter = 0, grid_insert = 0, grid_bin = 0;
   size_t smem_peel = 0, smem_bin = 0;
   cudaGraphExec_t exec = nullptr;
   // update records shared by the slab-binned build and the binned decode
@@ -114,6 +114,7 @@ struct pp_iblt {
   uint32_t n_bins = 0, bin_cap = 0, bin_shift = 0;
   size_t smem_claim = 0, smem_apply_round = 0;
   int grid_claim = 0, grid_apply_round = 0;
+  TileBufs tiles;  // tile pass of the binned build (allocated on first use)
   // decode with sub-tables (allocated on first use)
   SubDecCtl *sctl = nullptr, *h_sctl = nullptr;
   cudaGraphExec_t sub_exec = nullptr;
@@ -144,6 +145,7 @@ void free_all(pp_iblt *t) {
   cudaFree(t->rec_cell);
   cudaFree(t->bin_count);
   cudaFree(t->bin_overflow);
+  free_tiles(t->tiles);
   delete t;
 }
 
@@ -626,20 +628,12 @@ pp_status ensure_round_bins(pp_iblt *t, cudaStream_t s) {
 
 // Pass 2: slab by slab (zero-filled first when building from scratch).
 pp_status apply_pass(pp_iblt *t, BinArgs &ba, int sign, bool zero_fill, cudaStream_t s) {
-  TableArgs a = t->args;
-  const TableArgs *tabs = nullptr;
-  Cell *cells = t->cells;
-  u32 slab = 0;
-  void *args[] = {&cells, &a, &tabs, &ba, &slab, &sign};
-  for (slab = 0; slab < ba.n_slabs; ++slab) {
-    if (zero_fill) {
-      const uint64_t c0 = (uint64_t)slab * kSlabCells;
-      const uint64_t c1 = c0 + kSlabCells < t->n ? c0 + kSlabCells : t->n;
-      PP_CUDA(cudaMemsetAsync(t->cells + c0, 0, (c1 - c0) * sizeof(Cell), s));
-    }
-    PP_CUDA(cudaLaunchKernel(t->k.apply, dim3(t->grid_apply), dim3(kBlock), args, 0, s));
-  }
-  return PP_OK;
+  // a tile's expected share of a slab's list, with slack (a fuller tile overflows
+  // to the slab's overflow list, which holds a whole slab)
+  const uint64_t tile_cap = (uint64_t)((double)ba.cap / kTilesPerSlab * 1.15) + 256;
+  pp_status st = ensure_tiles(t->tiles, tile_cap, ba.cap, ba.n_slabs, false, s);
+  if (st != PP_OK) return st;
+  return tile_apply_pass(t->cells, t->args, nullptr, ba, t->tiles, t->n, sign, zero_fill, s);
 }
 
 pp_status update(pp_iblt *t, const uint64_t *d_keys, uint64_t m, int sign, cudaStream_t s) {
@@ -701,7 +695,6 @@ pp_status pp_iblt_create(pp_iblt **out, uint64_t n_cells, uint32_t r, uint64_t s
   t->grid_peel = persistent_grid(t->k.peel, kBlock, t->smem_peel, t->opt.ctas_per_sm);
   t->grid_filter = persistent_grid(t->k.filter, kBlock, 0, t->opt.ctas_per_sm);
   t->grid_insert = persistent_grid(t->k.insert, kBlock, 0, 8) * 4;
-  t->grid_apply = persistent_grid(t->k.apply, kBlock, 0, 8);
   *out = t;
   return PP_OK;
 }

@@ -3,17 +3,15 @@
 // Random cell updates spread over a table much larger than L2 run at the rate
 // at which HBM can open rows for scattered 32-byte sectors.  The binned build
 // first sorts every (cell, key) update of the batch into slabs of 2^21 cells
-// (64 MB, half of L2) and then applies one slab at a time, so all updates of
-// a slab land in L2 while the slab is resident.  When the table is built from
-// scratch the slab is zero-filled just before its updates: the zero lines are
-// then already in L2 and the slab is never read from HBM at all.
+// (64 MB, half of L2) and then applies one slab at a time, so each slab's
+// updates are read back from L2 and each cell is written to HBM once.
 //
 // Pass 1, k_bin: each block takes 256 keys, computes their r cells, counts
 // them per slab in shared memory, reserves a run in each slab's record list
 // with one atomic per slab, orders its records by slab in shared memory and
 // writes every run contiguously.
-// Pass 2, k_apply: all updates of one slab (count += sign, XOR key and
-// checksum), one launch per slab.
+// Pass 2 (iblt_tiles.cuh) applies one slab at a time, tile by tile in shared
+// memory.
 #pragma once
 
 #include "iblt_types.cuh"
@@ -153,23 +151,6 @@ __global__ void __launch_bounds__(kBlock) k_bin(Cell *__restrict__ cells, const 
       }
       __syncthreads();
     }
-  }
-}
-
-// All recorded updates of slab `slab`.
-template <int R, bool BATCH>
-__global__ void __launch_bounds__(kBlock) k_apply(Cell *__restrict__ cells, const TableArgs tab0,
-                                                  const TableArgs *__restrict__ tabs, BinArgs b, u32 slab,
-                                                  int sign) {
-  const u32 cnt = b.count[slab];
-  const u32 n = cnt < b.cap ? cnt : b.cap;
-  const u64 base = (u64)slab * b.cap;
-  const u32 stride = gridDim.x * blockDim.x;
-  for (u32 i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
-    const u64 x = __ldcs(b.rec_key + base + i);
-    const u32 c = __ldcs(b.rec_cell + base + i);
-    const TableArgs &T = BATCH ? tabs[__ldcs(b.rec_tab + base + i)] : tab0;
-    apply_touch<R>(cells, c, x, mix64(x ^ T.seed[rank_of<R>(T)]), sign);
   }
 }
 

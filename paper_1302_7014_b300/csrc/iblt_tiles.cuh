@@ -1,0 +1,247 @@
+// Tile pass of the slab-binned IBLT build.
+//
+// Applying a slab's updates with L2 atomics is bound by the L2's atomic
+// throughput: every update is three atomics on one 32-byte cell.  The tile
+// pass replaces them with shared-memory atomics, in two roles:
+//   bin    sorts a slab's update records into the slab's 512 tiles of 4096
+//          cells (per-block histogram in shared memory, one atomic per tile
+//          per block, runs written contiguously with an L2 "evict last" hint:
+//          the next launch reads them back);
+//   apply  one block per tile: the tile's cells in shared memory (zero for a
+//          build, loaded for an insert), every update of the tile applied
+//          there, the 4096 cells written back coalesced.
+// Launch s of k_tile_step runs "bin slab s" and "apply slab s-1" side by side
+// (block roles interleaved), so the latency-bound sort of one slab overlaps
+// the update of the previous one.  Sorted records alternate between two
+// buffer sets (slab s in set s % 2).
+// A tile whose list is full sends its extra records to the slab's overflow
+// list (three sets, slab s in set s % 3); the apply role of launch s + 2
+// applies them with global atomics, after the slab's tiles were written.
+// Updates commute, so the cells end up exactly as with any other order.
+#pragma once
+
+#include "iblt_types.cuh"
+
+namespace pp {
+
+__device__ __forceinline__ u64 chk_seed_of(const TableArgs &T) { return T.seed[T.r]; }
+
+// Role "bin" for slab `slab`, as block `bi` of `nb` bin blocks.
+template <bool BATCH>
+__device__ __forceinline__ void tile_bin(unsigned char *smem, const BinArgs &b, const TileArgs &ta, u32 slab,
+                                         u32 bi, u32 nb) {
+  u64 *s_key = reinterpret_cast<u64 *>(smem);              // kTileBinChunk
+  u32 *s_cell = reinterpret_cast<u32 *>(s_key + kTileBinChunk);
+  u32 *s_tab = s_cell + kTileBinChunk;                     // (batch)
+  __shared__ u32 s_hist[kTilesPerSlab], s_scan[kTilesPerSlab], s_base[kTilesPerSlab];
+  __shared__ u32 s_wt[kTileThreads / 32];
+  const u32 tid = threadIdx.x;
+  const u64 keep = l2_evict_last_policy();
+  const u32 set = slab & 1u;
+  u64 *tkey = ta.key + set * ta.set_stride;
+  u32 *tcell = ta.cell + set * ta.set_stride;
+  u32 *ttab = BATCH ? ta.tab + set * ta.set_stride : nullptr;
+  u32 *tcount = ta.count + set * kTilesPerSlab;
+  const u64 oset = (u64)(slab % 3u) * ta.o_cap;
+  const u32 cnt = b.count[slab];
+  const u32 n = cnt < b.cap ? cnt : b.cap;
+  const u64 src = (u64)slab * b.cap;
+  const u32 cbase = slab << kSlabShift;
+  for (u32 c0 = bi * (u32)kTileBinChunk; c0 < n; c0 += nb * (u32)kTileBinChunk) {
+    s_hist[tid] = 0;
+    __syncthreads();
+    const u32 c1 = c0 + kTileBinChunk < n ? c0 + kTileBinChunk : n;
+    // this thread's records: every load in flight at once, then their ranks
+    // within their tiles (shared-memory histogram)
+    u64 x[kTileBinItems];
+    u32 c[kTileBinItems], tb[kTileBinItems], rk[kTileBinItems];
+#pragma unroll
+    for (int it = 0; it < kTileBinItems; ++it) {
+      const u32 i = c0 + (u32)it * kTileThreads + tid;
+      const bool v = i < c1;
+      c[it] = v ? __ldcs(b.rec_cell + src + i) : 0xffffffffu;  // no cell has this index
+      x[it] = v ? __ldcs(b.rec_key + src + i) : 0ull;
+      tb[it] = (BATCH && v) ? __ldcs(b.rec_tab + src + i) : 0u;
+    }
+#pragma unroll
+    for (int it = 0; it < kTileBinItems; ++it)
+      rk[it] = c[it] != 0xffffffffu ? atomicAdd(s_hist + ((c[it] - cbase) >> kTileShift), 1u) : 0u;
+    __syncthreads();
+    // exclusive scan of the 512-entry histogram: one entry per thread
+    const u32 own = s_hist[tid];
+    u32 inc = own;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const u32 y = __shfl_up_sync(kFull, inc, o);
+      if ((int)lane_id() >= o) inc += y;
+    }
+    if (lane_id() == 31) s_wt[tid >> 5] = inc;
+    __syncthreads();
+    if (tid < 32) {
+      const u32 w = tid < kTileThreads / 32 ? s_wt[tid] : 0;
+      u32 wi = w;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const u32 y = __shfl_up_sync(kFull, wi, o);
+        if ((int)tid >= o) wi += y;
+      }
+      if (tid < kTileThreads / 32) s_wt[tid] = wi - w;
+    }
+    __syncthreads();
+    s_scan[tid] = s_wt[tid >> 5] + inc - own;
+    s_base[tid] = own ? atomicAdd(tcount + tid, own) : 0u;
+    __syncthreads();
+    // order the chunk by tile in shared memory
+#pragma unroll
+    for (int it = 0; it < kTileBinItems; ++it) {
+      if (c[it] != 0xffffffffu) {
+        const u32 pos = s_scan[(c[it] - cbase) >> kTileShift] + rk[it];
+        s_key[pos] = x[it];
+        s_cell[pos] = c[it];
+        if (BATCH) s_tab[pos] = tb[it];
+      }
+    }
+    __syncthreads();
+    // contiguous runs per tile; a full tile spills to the overflow list
+    for (u32 p = tid; p < c1 - c0; p += kTileThreads) {
+      const u32 tile = (s_cell[p] - cbase) >> kTileShift;
+      const u32 slot = s_base[tile] + (p - s_scan[tile]);
+      if (slot < ta.cap) {
+        const u64 dst = (u64)tile * ta.cap + slot;
+        st_l2_policy(tkey + dst, s_key[p], keep);
+        st_l2_policy(tcell + dst, s_cell[p], keep);
+        if (BATCH) st_l2_policy(ttab + dst, s_tab[p], keep);
+      } else {
+        const u32 q = atomicAdd(ta.o_count + slab, 1u);
+        if (q < ta.o_cap) {
+          ta.o_key[oset + q] = s_key[p];
+          ta.o_cell[oset + q] = s_cell[p];
+          if (BATCH) ta.o_tab[oset + q] = s_tab[p];
+        }
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// Role "apply" for tile `tile` of slab `slab`.
+template <bool BATCH>
+__device__ __forceinline__ void tile_apply(unsigned char *smem, Cell *cells, const TableArgs &tab0,
+                                           const TableArgs *tabs, const TileArgs &ta, u32 slab, u32 tile,
+                                           u64 n_cells, int sign, int zero) {
+  u64 *s_key = reinterpret_cast<u64 *>(smem);   // kTileCells
+  u64 *s_chk = s_key + kTileCells;              // kTileCells
+  int *s_cnt = reinterpret_cast<int *>(s_chk + kTileCells);
+  u32 *s_key32 = reinterpret_cast<u32 *>(s_key);  // XOR works on each 32-bit half
+  u32 *s_chk32 = reinterpret_cast<u32 *>(s_chk);
+  const u64 c0 = ((u64)slab << kSlabShift) + ((u64)tile << kTileShift);
+  if (c0 >= n_cells) return;  // uniform per block
+  const u32 nc = (u32)(c0 + kTileCells <= n_cells ? kTileCells : n_cells - c0);
+  const u32 set = slab & 1u;
+  const u64 src = set * ta.set_stride + (u64)tile * ta.cap;
+  u32 *tcount = ta.count + set * kTilesPerSlab;
+  for (u32 i = threadIdx.x; i < nc; i += kTileThreads) {
+    if (zero) {
+      s_key[i] = 0;
+      s_chk[i] = 0;
+      s_cnt[i] = 0;
+    } else {
+      const uint4 a = __ldcs(reinterpret_cast<const uint4 *>(cells + c0 + i));
+      const uint4 bb = __ldcs(reinterpret_cast<const uint4 *>(cells + c0 + i) + 1);
+      s_key[i] = ((u64)a.y << 32) | a.x;
+      s_chk[i] = ((u64)a.w << 32) | a.z;
+      s_cnt[i] = (int)bb.x;
+    }
+  }
+  __syncthreads();
+  const u32 cnt = tcount[tile];
+  const u32 n = cnt < ta.cap ? cnt : ta.cap;
+  const u64 seed0 = BATCH ? 0 : chk_seed_of(tab0);
+  for (u32 i0 = 0; i0 < n; i0 += kTileThreads * kTileApplyItems) {
+    u64 x[kTileApplyItems], seed[kTileApplyItems];
+    u32 off[kTileApplyItems];
+#pragma unroll
+    for (int it = 0; it < kTileApplyItems; ++it) {
+      const u32 i = i0 + (u32)it * kTileThreads + threadIdx.x;
+      const bool v = i < n;
+      x[it] = v ? __ldcs(ta.key + src + i) : 0ull;
+      off[it] = v ? (u32)(__ldcs(ta.cell + src + i) - c0) : 0xffffffffu;
+      seed[it] = (BATCH && v) ? chk_seed_of(tabs[__ldcs(ta.tab + src + i)]) : seed0;
+    }
+#pragma unroll
+    for (int it = 0; it < kTileApplyItems; ++it) {
+      if (off[it] != 0xffffffffu) {
+        const u32 o = off[it];
+        const u64 cx = mix64(x[it] ^ seed[it]);
+        atomicAdd(s_cnt + o, sign);
+        atomicXor(s_key32 + 2 * o, (u32)x[it]);
+        atomicXor(s_key32 + 2 * o + 1, (u32)(x[it] >> 32));
+        atomicXor(s_chk32 + 2 * o, (u32)cx);
+        atomicXor(s_chk32 + 2 * o + 1, (u32)(cx >> 32));
+      }
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) tcount[tile] = 0;  // ready for slab + 2
+  // the tile's sorted records are dead now: drop their L2 lines unwritten (the
+  // tile's region starts on a 128-byte line, cap being a multiple of 32)
+  for (u32 l = threadIdx.x; l < (n * 8 + 127) / 128; l += kTileThreads) l2_discard(ta.key + src + l * 16);
+  for (u32 l = threadIdx.x; l < (n * 4 + 127) / 128; l += kTileThreads) l2_discard(ta.cell + src + l * 32);
+  if (BATCH)
+    for (u32 l = threadIdx.x; l < (n * 4 + 127) / 128; l += kTileThreads) l2_discard(ta.tab + src + l * 32);
+  for (u32 i = threadIdx.x; i < nc; i += kTileThreads) {
+    const u64 k = s_key[i], h = s_chk[i];
+    uint4 a, bb;
+    a.x = (u32)k, a.y = (u32)(k >> 32), a.z = (u32)h, a.w = (u32)(h >> 32);
+    bb.x = (u32)s_cnt[i], bb.y = 0, bb.z = 0, bb.w = 0;
+    uint4 *dst = reinterpret_cast<uint4 *>(cells + c0 + i);
+    __stcs(dst, a);
+    __stcs(dst + 1, bb);
+  }
+}
+
+// Launch s (0 <= s <= n_slabs + 1):
+//   apply role  (s >= 1 and s - 1 < n_slabs): the overflow of slab s - 2, then
+//               the tiles of slab s - 1;  for s = n_slabs + 1: the overflow of
+//               slab s - 2 only;
+//   bin role    (s < n_slabs): slab s.
+// n_apply / n_bin blocks of each role, interleaved by block index.
+template <bool BATCH>
+__global__ void __launch_bounds__(kTileThreads, 2) k_tile_step(Cell *__restrict__ cells, const TableArgs tab0,
+                                                      const TableArgs *__restrict__ tabs, BinArgs b,
+                                                      TileArgs ta, u32 s, u32 n_apply, u32 n_bin,
+                                                      u64 n_cells, int sign, int zero) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const u32 both = n_apply < n_bin ? n_apply : n_bin;
+  const u32 blk = blockIdx.x;
+  bool apply;
+  u32 idx;
+  if (blk < 2 * both) {
+    apply = (blk & 1u) == 0;
+    idx = blk >> 1;
+  } else {
+    apply = n_apply > n_bin;
+    idx = blk - both;
+  }
+  if (!apply) {
+    tile_bin<BATCH>(smem, b, ta, s, idx, n_bin);
+    return;
+  }
+  if (s >= 2) {
+    // the overflow of slab s - 2: its tiles were written by launch s - 1
+    const u32 os = s - 2;
+    const u64 oset = (u64)(os % 3u) * ta.o_cap;
+    const u32 no = min(ta.o_count[os], (u32)ta.o_cap);
+    for (u32 i = idx * kTileThreads + threadIdx.x; i < no; i += n_apply * kTileThreads) {
+      const u64 x = ta.o_key[oset + i];
+      Cell *p = cells + ta.o_cell[oset + i];
+      const TableArgs &T = BATCH ? tabs[ta.o_tab[oset + i]] : tab0;
+      atomicAdd(&p->count, sign);
+      atomicXor(&p->key, x);
+      atomicXor(&p->chk, mix64(x ^ chk_seed_of(T)));
+    }
+  }
+  if (s >= 1 && s - 1 < b.n_slabs) tile_apply<BATCH>(smem, cells, tab0, tabs, ta, s - 1, idx, n_cells, sign, zero);
+}
+
+}  // namespace pp

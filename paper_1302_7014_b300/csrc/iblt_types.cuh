@@ -67,6 +67,31 @@ constexpr int kBinItems = 4;                 // keys per thread per partition st
 constexpr int kBinKeys = kBlock * kBinItems; // keys per block per partition step
 
 // Record lists of a binned build: slab s owns records [s*cap, s*cap + min(count[s], cap)).
+// Tile pass of the binned build (iblt_tiles.cuh): a slab's updates are
+// re-sorted into tiles of 2^12 cells, and each tile is updated in shared
+// memory and written out whole.
+constexpr int kTileShift = 12;
+constexpr u32 kTileCells = 1u << kTileShift;               // 4096 cells, 80 KB of shared state
+constexpr u32 kTilesPerSlab = kSlabCells >> kTileShift;    // 512
+constexpr int kTileThreads = 512;                          // threads per CTA of both tile kernels
+constexpr int kTileBinItems = 8;                           // records per thread per chunk
+constexpr int kTileApplyItems = 8;                         // records per thread per step of the apply
+constexpr int kTileBinChunk = kTileThreads * kTileBinItems;  // 4096 records per bin step
+
+struct TileArgs {
+  u64 *key;         // sorted records: two sets, set_stride records apart
+  u32 *cell;
+  u32 *tab;         // batch: table of each record
+  u32 *count;       // per tile, two sets of kTilesPerSlab (the apply role resets them)
+  u64 set_stride;   // kTilesPerSlab * cap
+  u32 cap;          // records per tile
+  u32 o_cap;        // records per overflow set (a slab's whole record capacity)
+  u64 *o_key;       // overflow: three sets, o_cap records apart
+  u32 *o_cell;
+  u32 *o_tab;
+  u32 *o_count;     // per slab
+};
+
 struct BinArgs {
   u64 *rec_key;
   u32 *rec_cell;   // global cell id
@@ -119,10 +144,31 @@ inline u32 round_bin_shift(uint64_t n) {
 constexpr int kClaimItems = 4;                  // frontier entries per thread per chunk
 constexpr int kClaimChunk = kBlock * kClaimItems;
 
+// Tile-pass buffers of one handle (host side; csrc/tiles.cu).
+struct TileBufs {
+  u64 *key = nullptr, *o_key = nullptr;
+  u32 *cell = nullptr, *tab = nullptr, *count = nullptr;
+  u32 *o_cell = nullptr, *o_tab = nullptr, *o_count = nullptr;
+  uint64_t cap = 0, o_cap = 0;  // per tile; per overflow set
+  uint32_t o_slabs = 0;
+  bool batch = false;
+};
+
+// Grows the buffers to tile_cap records per tile, o_cap per slab's overflow,
+// n_slabs overflow counters.
+pp_status ensure_tiles(TileBufs &tb, uint64_t tile_cap, uint64_t o_cap, uint32_t n_slabs, bool batch,
+                       cudaStream_t s);
+void free_tiles(TileBufs &tb);
+
+// Pass 2 of a binned update: every slab of `ba` through k_tile_bin and
+// k_tile_apply (zero = build from empty cells), then the last overflow flush.
+pp_status tile_apply_pass(Cell *cells, const TableArgs &tab0, const TableArgs *tabs, const BinArgs &ba,
+                          TileBufs &tb, uint64_t n_cells, int sign, bool zero, cudaStream_t s);
+
 // Entry points of one instantiation of the IBLT kernels (plain or batched).
 struct IbltKernels {
   const void *insert, *scan, *peel, *filter;
-  const void *bin, *apply;           // slab-binned build
+  const void *bin;                   // slab-binned build (pass 1)
   const void *claim, *apply_round;   // binned decode round
   int nr;  // compile-time rank (PP_MAX_R for the generic instance)
   const void *sub_scan = nullptr, *sub_filter = nullptr, *sub_peel = nullptr;  // sub-rounds (plain only)

@@ -1,0 +1,103 @@
+// Host side of the build's tile pass (kernels in iblt_tiles.cuh): buffers and
+// the per-slab launch sequence, shared by the single-table and batched paths.
+#include "host.cuh"
+#include "iblt_tiles.cuh"
+
+namespace pp {
+
+static_assert(kTilesPerSlab == kTileThreads, "the bin role scans one histogram entry per thread");
+
+void free_tiles(TileBufs &tb) {
+  cudaFree(tb.key);
+  cudaFree(tb.cell);
+  cudaFree(tb.tab);
+  cudaFree(tb.count);
+  cudaFree(tb.o_key);
+  cudaFree(tb.o_cell);
+  cudaFree(tb.o_tab);
+  cudaFree(tb.o_count);
+  tb = TileBufs{};
+}
+
+// dynamic shared memory of k_tile_step: the larger of the two roles
+static size_t tile_step_smem() {
+  const size_t bin = (size_t)kTileBinChunk * (8 + 4 + 4);  // + 4 per record in a batch: still smaller
+  const size_t apply = (size_t)kTileCells * (8 + 8 + 4);
+  return bin > apply ? bin : apply;
+}
+static_assert((size_t)kTileBinChunk * (8 + 4 + 4 + 4) <= (size_t)kTileCells * (8 + 8 + 4),
+              "the apply role's shared memory also holds a batch bin step");
+
+static const void *tile_step_fn(bool batch) {
+  return batch ? (const void *)k_tile_step<true> : (const void *)k_tile_step<false>;
+}
+
+pp_status ensure_tiles(TileBufs &tb, uint64_t tile_cap, uint64_t o_cap, uint32_t n_slabs, bool batch,
+                       cudaStream_t s) {
+  if (tile_cap > 0xFFFFFFF0ull || o_cap > 0xFFFFFFF0ull)
+    return fail(PP_ERR_INVALID_ARG, "tile pass: too many updates for one call");
+  if (tb.key && tile_cap <= tb.cap && o_cap <= tb.o_cap && n_slabs <= tb.o_slabs && batch == tb.batch)
+    return PP_OK;
+  PP_CUDA(cudaStreamSynchronize(s));
+  // a multiple of 32 records: every tile's region starts on a 128-byte line
+  const uint64_t cap = ((tile_cap > tb.cap ? tile_cap : tb.cap) + 31) / 32 * 32;
+  const uint64_t ocap = o_cap > tb.o_cap ? o_cap : tb.o_cap;
+  const uint32_t ns = n_slabs > tb.o_slabs ? n_slabs : tb.o_slabs;
+  free_tiles(tb);
+  const uint64_t rec = 2 * cap * kTilesPerSlab;
+  cudaError_t e = cudaSuccess;
+  auto al = [&](void **p, size_t bytes) {
+    if (e == cudaSuccess) e = cudaMalloc(p, bytes);
+  };
+  al((void **)&tb.key, rec * 8);
+  al((void **)&tb.cell, rec * 4);
+  if (batch) al((void **)&tb.tab, rec * 4);
+  al((void **)&tb.count, 2 * kTilesPerSlab * 4);
+  al((void **)&tb.o_key, 3 * ocap * 8);
+  al((void **)&tb.o_cell, 3 * ocap * 4);
+  if (batch) al((void **)&tb.o_tab, 3 * ocap * 4);
+  al((void **)&tb.o_count, (size_t)ns * 4);
+  if (e == cudaSuccess) e = cudaMemsetAsync(tb.count, 0, 2 * kTilesPerSlab * 4, s);
+  if (e != cudaSuccess) {
+    free_tiles(tb);
+    return cuda_fail(e, "tile pass buffers", __FILE__, __LINE__);
+  }
+  tb.cap = cap;
+  tb.o_cap = ocap;
+  tb.o_slabs = ns;
+  tb.batch = batch;
+  static bool attr[2] = {false, false};
+  if (!attr[batch]) {
+    cudaFuncSetAttribute(tile_step_fn(batch), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tile_step_smem());
+    attr[batch] = true;
+  }
+  return PP_OK;
+}
+
+pp_status tile_apply_pass(Cell *cells, const TableArgs &tab0, const TableArgs *tabs, const BinArgs &ba,
+                          TileBufs &tb, uint64_t n_cells, int sign, bool zero, cudaStream_t s) {
+  PP_CUDA(cudaMemsetAsync(tb.o_count, 0, (size_t)ba.n_slabs * 4, s));
+  TileArgs ta{tb.key, tb.cell, tb.tab, tb.count, tb.cap * kTilesPerSlab, (u32)tb.cap, (u32)tb.o_cap,
+              tb.o_key, tb.o_cell, tb.o_tab, tb.o_count};
+  Cell *c = cells;
+  TableArgs t0 = tab0;
+  const TableArgs *tp = tabs;
+  BinArgs b = ba;
+  u32 step = 0, n_apply = 0, n_bin = 0;
+  u64 n = n_cells;
+  int sg = sign, z = zero ? 1 : 0;
+  void *args[] = {&c, &t0, &tp, &b, &ta, &step, &n_apply, &n_bin, &n, &sg, &z};
+  const u32 ns = ba.n_slabs;
+  const u32 sms = (u32)sm_count();
+  // launch s: sort slab s while slab s - 1 is applied tile by tile
+  for (step = 0; step <= ns + 1; ++step) {
+    n_bin = step < ns ? sms : 0u;
+    n_apply = (step >= 1 && step - 1 < ns) ? kTilesPerSlab : (step == ns + 1 ? 2 * sms : 0u);
+    if (n_apply + n_bin == 0) continue;
+    PP_CUDA(cudaLaunchKernel(tile_step_fn(tb.batch), dim3(n_apply + n_bin), dim3(kTileThreads), args,
+                             tile_step_smem(), s));
+  }
+  return PP_OK;
+}
+
+}  // namespace pp
