@@ -70,9 +70,10 @@ def configure(so):
         so.orc_kcore_queue.argtypes = [u32, u32, u32, vp, u64, vp, vp]
         so.orc_kcore_subrounds.argtypes = [u32, u32, u32, vp, u64, u32, vp, u32, vp, vp, vp, vp, vp]
         so.orc_iblt_decode_subrounds.argtypes = [u64, u32, u64, vp, vp, vp, u32, vp, u64, vp, vp]
+        so.orc_iblt_decode_signed.argtypes = [u64, u32, u64, vp, vp, vp, u32, vp, vp, u64, vp, vp]
         for f in ("orc_iblt_insert", "orc_iblt_decode_rounds", "orc_iblt_decode_queue",
                   "orc_kcore_rounds", "orc_kcore_queue", "orc_kcore_subrounds",
-                  "orc_iblt_decode_subrounds"):
+                  "orc_iblt_decode_subrounds", "orc_iblt_decode_signed"):
             getattr(so, f).restype = ctypes.c_int
     return so
 
@@ -188,6 +189,25 @@ class IBLT:
         ends = [0] + [int(x) for x in sub_end[:S]]
         keys = [out[ends[i]:ends[i + 1]].copy() for i in range(S)]
         return dict(keys=keys, subrounds=S, status=st)
+
+    def decode_signed(self, max_rounds: int = 1 << 20):
+        """Signed recovery of a set difference (count = +1 or -1 cells are pure);
+        mutates the table.  Returns dict(keys=[array per round], signs=[int8 array
+        per round], rounds=T, status=code); each round sorted by (key, sign)."""
+        cap = int(max(1, np.abs(self.count).sum() + 1))
+        cap = max(cap, self.n)
+        out = np.zeros(cap, dtype=np.uint64)
+        sg = np.zeros(cap, dtype=np.int8)
+        mr = min(max_rounds, self.n + 2)
+        round_end = np.zeros(mr + 1, dtype=np.uint64)
+        T = np.zeros(1, dtype=np.uint32)
+        st = lib().orc_iblt_decode_signed(self.n, self.r, self.seed, _ptr(self.count), _ptr(self.keyx),
+                                          _ptr(self.chkx), mr, _ptr(out), _ptr(sg), cap, _ptr(round_end),
+                                          _ptr(T))
+        T = int(T[0])
+        ends = [0] + [int(x) for x in round_end[:T]]
+        return dict(keys=[out[ends[i]:ends[i + 1]].copy() for i in range(T)],
+                    signs=[sg[ends[i]:ends[i + 1]].copy() for i in range(T)], rounds=T, status=st)
 
     def residual_cells(self) -> int:
         return int(np.count_nonzero(self.count))

@@ -20,6 +20,8 @@
  *     depend on the removal order).
  *   - peeling and IBLT recovery with sub-tables (App. B, Sec. 6
  *     "Implementation Details"): one part / sub-table per sub-round.
+ *   - signed IBLT recovery of a set difference (Sec. 6 "Motivation":
+ *     insertions and deletions are the same XORs): count = +1 or -1 is pure.
  *
  * Conventions the paper leaves open (stated, not derived; parity unpinned for
  * the cell map and the sub-table split, which only the known-answer file
@@ -479,6 +481,80 @@ int orc_iblt_decode_subrounds(uint64_t n, uint32_t r, uint64_t table_seed, int64
     ++s;
   }
   *S_out = S;
+  free(found);
+  return status;
+}
+
+/* Signed IBLT recovery: the table holds a set difference (keys inserted with
+ * sign +1 and deleted with sign -1 that were never inserted), as in the sparse
+ * recovery use of Sec. 6 "Motivation".  A cell is pure when |count| == 1 and
+ * its checksum field equals checkSum(key field); its key comes out with the
+ * sign of its count.
+ *
+ * Round t (Sec. 1's round rule at k = 2 on the hypergraph of the difference):
+ *   P_t = every cell pure at the start of round t;
+ *   K_t = the distinct (key, sign) pairs found in P_t;
+ *   each (x, s) in K_t is removed from its r cells: count -= s, XOR x and
+ *   checkSum(x).
+ * The loop ends at the first round with K_t empty; *rounds_out counts the
+ * rounds that recovered something.  out_keys / out_signs receive K_1, K_2,
+ * ... in order, each round sorted by (key, sign); round_end[t-1] = the total
+ * after round t.  Returns ORC_CAPACITY or ORC_ROUND_LIMIT like the unsigned
+ * recovery. */
+typedef struct { uint64_t x; int64_t s; } orc_signed_key;
+
+static int cmp_signed(const void *a, const void *b) {
+  const orc_signed_key *p = (const orc_signed_key *)a, *q = (const orc_signed_key *)b;
+  if (p->x != q->x) return p->x < q->x ? -1 : 1;
+  return p->s < q->s ? -1 : (p->s > q->s ? 1 : 0);
+}
+
+int orc_iblt_decode_signed(uint64_t n, uint32_t r, uint64_t table_seed, int64_t *count, uint64_t *keyx,
+                           uint64_t *chkx, uint32_t max_rounds, uint64_t *out_keys, int8_t *out_signs,
+                           uint64_t out_cap, uint64_t *round_end, uint32_t *rounds_out) {
+  if (r < 2 || r > 16 || n < r) return ORC_INVALID;
+  uint64_t seeds[17], off[17];
+  orc_hash_seeds(table_seed, r, seeds);
+  orc_part_offsets(n, r, off);
+  orc_signed_key *found = (orc_signed_key *)malloc((n ? n : 1) * sizeof(orc_signed_key));
+  if (!found) return ORC_NOMEM;
+  uint64_t total = 0;
+  uint32_t t = 0;
+  int status = ORC_OK;
+  *rounds_out = 0;
+  for (;;) {
+    uint64_t nf = 0;
+    for (uint64_t c = 0; c < n; ++c) {
+      if ((count[c] == 1 || count[c] == -1) && chkx[c] == checksum_of(keyx[c], seeds, r)) {
+        found[nf].x = keyx[c];
+        found[nf].s = count[c];
+        ++nf;
+      }
+    }
+    if (nf == 0) break;
+    if (t == max_rounds) { status = ORC_ROUND_LIMIT; break; }
+    qsort(found, nf, sizeof(orc_signed_key), cmp_signed);
+    uint64_t nk = 0;
+    for (uint64_t i = 0; i < nf; ++i)
+      if (i == 0 || found[i].x != found[i - 1].x || found[i].s != found[i - 1].s) found[nk++] = found[i];
+    if (total + nk > out_cap) { status = ORC_CAPACITY; break; }
+    for (uint64_t i = 0; i < nk; ++i) {
+      const uint64_t x = found[i].x, cs = checksum_of(x, seeds, r);
+      const int64_t sg = found[i].s;
+      out_keys[total + i] = x;
+      out_signs[total + i] = (int8_t)sg;
+      for (uint32_t q = 0; q < r; ++q) {
+        const uint64_t c = cell_of(x, q, seeds, off);
+        count[c] -= sg;
+        keyx[c] ^= x;
+        chkx[c] ^= cs;
+      }
+    }
+    total += nk;
+    round_end[t] = total;
+    ++t;
+  }
+  *rounds_out = t;
   free(found);
   return status;
 }

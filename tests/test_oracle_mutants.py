@@ -14,6 +14,7 @@ import pytest
 import oracle
 import test_oracle_pins as pins
 import test_oracle_subrounds as sub
+import test_oracle_signed as signed
 
 MUTANTS = [
     ("round removes degree <= k",
@@ -61,6 +62,15 @@ MUTANTS = [
     ("IBLT sub-tables visited in reverse order",
      "    const uint32_t j = s % r;",
      "    const uint32_t j = r - 1 - s % r;"),
+    ("signed removal ignores the sign",
+     "        count[c] -= sg;",
+     "        count[c] -= 1;"),
+    ("signed purity misses negative counts",
+     "if ((count[c] == 1 || count[c] == -1) && chkx[c] == checksum_of(keyx[c], seeds, r)) {",
+     "if (count[c] == 1 && chkx[c] == checksum_of(keyx[c], seeds, r)) {"),
+    ("signed recovery leaves the checksum in",
+     "        chkx[c] ^= cs;\n      }\n    }\n    total += nk;",
+     "      }\n    }\n    total += nk;"),
     ("mix64 shift constant off by one",
      "z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;",
      "z = (z ^ (z >> 28)) * 0x94D049BB133111EBULL;"),
@@ -85,6 +95,9 @@ PINS = [
     lambda: sub.test_tiny_hypergraphs_vs_sets(),
     lambda: sub.test_iblt_subrounds_equal_kcore_subrounds(2000, 3, 0.75, 1),
     lambda: sub.test_iblt_subrounds_recover_inserted_set_below_threshold(),
+    lambda: signed.test_insert_only_equals_unsigned(3000, 3, 0.7, 1),
+    lambda: signed.test_set_difference_recovered(4000, 3, 4),
+    lambda: signed.test_rounds_equal_the_k2_peel_of_the_difference(4000, 3, 9, 0.4, 0.35),
 ]
 
 
