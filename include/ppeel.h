@@ -188,6 +188,27 @@ pp_status pp_iblt_decode(pp_iblt *t, uint64_t *d_out_keys, uint64_t out_cap,
 pp_status pp_iblt_decode_subrounds(pp_iblt *t, uint64_t *d_out_keys, uint64_t out_cap,
                                    pp_decode_result *res, void *stream);
 
+/* Signed recovery of a set difference (the sparse recovery use of Sec. 6
+ * "Motivation": insertion and deletion are the same XORs, so a table built by
+ * inserting the keys of A and deleting those of B holds A \ B with count
+ * contribution +1 and B \ A with -1).  A cell is pure when its count is +1 or
+ * -1 and its checksum field matches its key field; its key comes out with the
+ * sign of the count and is removed from its r cells with that sign.  Rounds as
+ * in pp_iblt_decode (Sec. 1 at k = 2, the lowest-index pure cell of a key
+ * recovers it).  The table is decoded in place.
+ * d_out_keys: out_cap uint64 on the device, keys grouped by round;
+ * d_out_signs: out_cap int8 on the device (+1 / -1 per key), or NULL.
+ * res: rounds, status_flags, recovered, residual_cells (cells with a non-zero
+ * count) and recovered_per_round as for pp_iblt_decode; remaining_per_round
+ * and alive_cells_per_round are zero-filled; items_before is the
+ * inserted-minus-deleted count.
+ * The size of the difference is not known beforehand: a decode that recovers
+ * more than out_cap keys stops after that round with CAPACITY.  Decodes in
+ * single kernels per phase (no update binning).  Requires r * n_cells < 2^32
+ * (INVALID_ARG).  ROUND_LIMIT as for pp_iblt_decode.  Synchronizes `stream`. */
+pp_status pp_iblt_decode_signed(pp_iblt *t, uint64_t *d_out_keys, int8_t *d_out_signs, uint64_t out_cap,
+                                pp_decode_result *res, void *stream);
+
 /* Copies `count` cells starting at `first` into dst (device memory if
  * to_host == 0, else host memory), on `stream`, and synchronizes it. */
 pp_status pp_iblt_copy_cells(pp_iblt *t, void *dst, uint64_t first, uint64_t count,

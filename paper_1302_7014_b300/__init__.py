@@ -23,7 +23,8 @@ from . import _lib
 from ._lib import PP_MAX_R, Cell, DecodeResult, Options, PeelResult
 
 __all__ = ["PPError", "IBLT", "iblt_create", "iblt_insert", "iblt_delete", "iblt_build", "iblt_decode",
-           "iblt_decode_subrounds", "peel_kcore", "peel_kcore_subrounds", "options", "PP_MAX_R"]
+           "iblt_decode_subrounds", "iblt_decode_signed", "peel_kcore", "peel_kcore_subrounds", "options",
+           "PP_MAX_R"]
 
 
 class PPError(RuntimeError):
@@ -141,6 +142,13 @@ class IBLT:
         return self._decode(_lib.load().pp_iblt_decode_subrounds, "pp_iblt_decode_subrounds", out,
                             round_cap, stream)
 
+    def decode_signed(self, out, signs=None, round_cap: int = 4096, stream=None) -> DecodeOutcome:
+        """Signed recovery of a set difference: ``out`` receives the keys and
+        ``signs`` (CUDA int8, or None) +1 / -1 for each (Sec. 6 sparse recovery)."""
+        sp = _dev_ptr(signs, 1, "signs")
+        return self._decode(lambda h, o, cap, res, st: _lib.load().pp_iblt_decode_signed(h, o, sp, cap, res, st),
+                            "pp_iblt_decode_signed", out, round_cap, stream)
+
     def _decode(self, fn, name, out, round_cap, stream) -> DecodeOutcome:
         rec = (ctypes.c_uint64 * round_cap)()
         rem = (ctypes.c_uint64 * round_cap)()
@@ -198,6 +206,10 @@ def iblt_decode(table: IBLT, out, round_cap: int = 4096, stream=None) -> DecodeO
 
 def iblt_decode_subrounds(table: IBLT, out, round_cap: int = 4096, stream=None) -> DecodeOutcome:
     return table.decode_subrounds(out, round_cap, stream)
+
+
+def iblt_decode_signed(table: IBLT, out, signs=None, round_cap: int = 4096, stream=None) -> DecodeOutcome:
+    return table.decode_signed(out, signs, round_cap, stream)
 
 
 def peel_kcore(n: int, r: int, k: int, edges, vertex_round=None, edge_round=None,

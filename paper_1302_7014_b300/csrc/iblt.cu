@@ -13,6 +13,7 @@
 #include "iblt_kernels.cuh"
 #include "iblt_rounds.cuh"
 #include "iblt_subrounds.cuh"
+#include "iblt_signed.cuh"
 
 using namespace pp;
 
@@ -38,6 +39,9 @@ static IbltKernels iblt_kernels_t() {
     k.sub_scan = (const void *)k_sscan<R>;
     k.sub_filter = (const void *)k_sfilter<R>;
     k.sub_peel = (const void *)k_speel<R>;
+    k.sg_scan = (const void *)k_sgscan<R>;
+    k.sg_peel = (const void *)k_sgpeel<R>;
+    k.sg_filter = (const void *)k_sgfilter<R>;
   }
   return k;
 }
@@ -119,6 +123,13 @@ struct pp_iblt {
   SubDecCtl *sctl = nullptr, *h_sctl = nullptr;
   cudaGraphExec_t sub_exec = nullptr;
   int grid_sscan = 0, grid_sfilter = 0, grid_speel = 0;
+  // signed decode (allocated on first use)
+  signed char *fsign = nullptr;
+  u32 *sg_cand = nullptr;  // r pushes per recovered key at most: r * n entries
+  cudaGraphExec_t sg_exec = nullptr;
+  int grid_sgscan = 0, grid_sgpeel = 0, grid_sgfilter = 0;
+  signed char *sg_graph_out = nullptr;  // output sign pointer the graph was built with
+  bool sg_graph_built = false;
 };
 
 namespace {
@@ -127,6 +138,9 @@ void free_all(pp_iblt *t) {
   if (!t) return;
   if (t->exec) cudaGraphExecDestroy(t->exec);
   if (t->sub_exec) cudaGraphExecDestroy(t->sub_exec);
+  if (t->sg_exec) cudaGraphExecDestroy(t->sg_exec);
+  cudaFree(t->fsign);
+  cudaFree(t->sg_cand);
   cudaFree(t->sctl);
   cudaFreeHost(t->h_sctl);
   cudaFree(t->cells);
@@ -877,6 +891,130 @@ pp_status pp_iblt_decode_subrounds(pp_iblt *t, uint64_t *d_out_keys, uint64_t ou
     return fail(PP_ERR_INVALID_ARG, "pp_iblt_decode_subrounds: a pure cell's key does not hash to it");
   if (c.flags & FLAG_ROUND_LIMIT)
     return fail(PP_ERR_ROUND_LIMIT, "pp_iblt_decode_subrounds: stopped after max_rounds=%u sub-rounds",
+                t->opt.max_rounds);
+  return PP_OK;
+}
+
+pp_status pp_iblt_decode_signed(pp_iblt *t, uint64_t *d_out_keys, int8_t *d_out_signs, uint64_t out_cap,
+                                pp_decode_result *res, void *stream) {
+  if (!t || !res) return fail(PP_ERR_INVALID_ARG, "pp_iblt_decode_signed: NULL table or result");
+  if (out_cap && !d_out_keys) return fail(PP_ERR_INVALID_ARG, "pp_iblt_decode_signed: NULL output");
+  if (!t->k.sg_scan) return fail(PP_ERR_INVALID_ARG, "pp_iblt_decode_signed: no kernels for r=%u", t->r);
+  if ((uint64_t)t->r * t->n >= (1ull << 32))
+    return fail(PP_ERR_INVALID_ARG, "pp_iblt_decode_signed: r * n_cells must stay below 2^32");
+  cudaStream_t s = as_stream(stream);
+  if (!t->fsign) {
+    PP_CUDA(cudaMalloc((void **)&t->fsign, t->n));
+    PP_CUDA(cudaMalloc((void **)&t->sg_cand, (size_t)t->r * t->n * sizeof(u32)));
+    t->grid_sgscan = persistent_grid(t->k.sg_scan, kBlock, 0, t->opt.ctas_per_sm);
+    t->grid_sgpeel = persistent_grid(t->k.sg_peel, kBlock, 0, t->opt.ctas_per_sm);
+    t->grid_sgfilter = persistent_grid(t->k.sg_filter, kBlock, 0, t->opt.ctas_per_sm);
+  }
+  memset(t->h_ctl, 0, sizeof(DecodeCtl));
+  t->h_ctl->out = reinterpret_cast<u64 *>(d_out_keys);
+  t->h_ctl->out_cap = out_cap;
+  t->h_ctl->max_rounds = t->opt.max_rounds;
+  PP_CUDA(cudaMemcpyAsync(t->ctl, t->h_ctl, sizeof(DecodeCtl), cudaMemcpyHostToDevice, s));
+  // kernel arguments (the output sign pointer is one of them)
+  const Cell *cells_c = t->cells;
+  Cell *cells = t->cells;
+  TableArgs tab = t->args;
+  u64 *fkey = t->fkey;
+  u32 *fcell = t->fcell, *bitmap = t->bitmap, *cand = t->sg_cand;
+  signed char *fsign = t->fsign, *osign = reinterpret_cast<signed char *>(d_out_signs);
+  const u64 *fkey_c = t->fkey;
+  const u32 *fcell_c = t->fcell, *bitmap_c = t->bitmap, *cand_c = t->sg_cand;
+  const signed char *fsign_c = t->fsign;
+  u64 cand_cap = (u64)t->r * t->n;
+  DecodeCtl *ctl = t->ctl;
+  RoundStats rs{t->st_rec, t->st_alive, t->st_front};
+  int set_cond = 0;
+  cudaGraphConditionalHandle cond = 0;
+  void *scan_p[] = {&cells_c, &tab, &fkey, &fcell, &fsign, &bitmap, &ctl};
+  void *peel_p[] = {&cells, &tab, &fkey_c, &fcell_c, &fsign_c, &bitmap_c, &cand, &cand_cap, &osign, &ctl};
+  void *filt_p[] = {&cells_c, &tab, &cand_c, &fkey, &fcell, &fsign, &bitmap, &ctl};
+  void *end_p[] = {&ctl, &rs, &set_cond, &cond};
+  if (t->opt.host_loop) {
+    PP_CUDA(cudaLaunchKernel(t->k.sg_scan, dim3(t->grid_sgscan), dim3(kBlock), scan_p, 0, s));
+    for (;;) {
+      PP_CUDA(cudaLaunchKernel(t->k.sg_peel, dim3(t->grid_sgpeel), dim3(kBlock), peel_p, 0, s));
+      PP_CUDA(cudaLaunchKernel(t->k.sg_filter, dim3(t->grid_sgfilter), dim3(kBlock), filt_p, 0, s));
+      PP_CUDA(cudaLaunchKernel((const void *)k_round_end, dim3(1), dim3(32), end_p, 0, s));
+      PP_CUDA(cudaMemcpyAsync(&t->h_ctl->more, &t->ctl->more, sizeof(u32), cudaMemcpyDeviceToHost, s));
+      PP_CUDA(cudaStreamSynchronize(s));
+      if (!t->h_ctl->more) break;
+    }
+  } else {
+    if (t->sg_exec && t->sg_graph_out != osign) {
+      cudaGraphExecDestroy(t->sg_exec);
+      t->sg_exec = nullptr;
+    }
+    if (!t->sg_exec) {
+      // sgscan -> while (more) { sgpeel -> sgfilter -> round_end }
+      cudaGraph_t g = nullptr;
+      PP_CUDA(cudaGraphCreate(&g, 0));
+      pp_status st = PP_OK;
+      cudaGraphNode_t n_scan, n_cond, n_peel, n_filter, n_end;
+      cudaGraphNodeParams cp{};
+      cudaGraph_t body;
+      st = add_kernel(&n_scan, g, nullptr, 0, t->k.sg_scan, t->grid_sgscan, kBlock, 0, scan_p);
+      if (st != PP_OK) goto sg_done;
+      if (cudaGraphConditionalHandleCreate(&cond, g, 1, cudaGraphCondAssignDefault) != cudaSuccess) {
+        st = fail(PP_ERR_CUDA, "cudaGraphConditionalHandleCreate failed");
+        goto sg_done;
+      }
+      cp.type = cudaGraphNodeTypeConditional;
+      cp.conditional.handle = cond;
+      cp.conditional.type = cudaGraphCondTypeWhile;
+      cp.conditional.size = 1;
+      if (cudaGraphAddNode(&n_cond, g, &n_scan, nullptr, 1, &cp) != cudaSuccess) {
+        st = fail(PP_ERR_CUDA, "cudaGraphAddNode(conditional while) failed");
+        goto sg_done;
+      }
+      body = cp.conditional.phGraph_out[0];
+      set_cond = 1;
+      st = add_kernel(&n_peel, body, nullptr, 0, t->k.sg_peel, t->grid_sgpeel, kBlock, 0, peel_p);
+      if (st != PP_OK) goto sg_done;
+      st = add_kernel(&n_filter, body, &n_peel, 1, t->k.sg_filter, t->grid_sgfilter, kBlock, 0, filt_p);
+      if (st != PP_OK) goto sg_done;
+      st = add_kernel(&n_end, body, &n_filter, 1, (const void *)k_round_end, 1, 32, 0, end_p);
+      if (st != PP_OK) goto sg_done;
+      if (cudaGraphInstantiate(&t->sg_exec, g, 0) != cudaSuccess) {
+        st = fail(PP_ERR_CUDA, "cudaGraphInstantiate failed: %s", cudaGetErrorString(cudaGetLastError()));
+        t->sg_exec = nullptr;
+      }
+      t->sg_graph_out = osign;
+    sg_done:
+      cudaGraphDestroy(g);
+      if (st != PP_OK) return st;
+    }
+    PP_CUDA(cudaGraphLaunch(t->sg_exec, s));
+  }
+  PP_CUDA(cudaMemcpyAsync(t->h_ctl, t->ctl, sizeof(DecodeCtl), cudaMemcpyDeviceToHost, s));
+  PP_CUDA(cudaStreamSynchronize(s));
+  const DecodeCtl c = *t->h_ctl;
+  const uint32_t T = c.round;
+  const uint32_t ncopy = T < res->round_cap ? T : res->round_cap;
+  if (ncopy && res->recovered_per_round) {
+    PP_CUDA(cudaMemcpyAsync(t->h_rec, t->st_rec, ncopy * sizeof(u64), cudaMemcpyDeviceToHost, s));
+    PP_CUDA(cudaStreamSynchronize(s));
+    for (uint32_t i = 0; i < ncopy; ++i) res->recovered_per_round[i] = t->h_rec[i];
+  }
+  if (ncopy && res->remaining_per_round) memset(res->remaining_per_round, 0, ncopy * sizeof(uint64_t));
+  if (ncopy && res->alive_cells_per_round) memset(res->alive_cells_per_round, 0, ncopy * sizeof(uint64_t));
+  res->rounds = T;
+  res->status_flags = c.flags;
+  res->recovered = c.n_out < out_cap ? c.n_out : out_cap;
+  res->items_before = t->items > 0 ? (uint64_t)t->items : 0;
+  res->residual_cells = c.nonempty - c.emptied;
+  t->items -= (int64_t)c.n_out - 2 * (int64_t)c.n_neg;  // positives minus negatives
+  if (c.flags & FLAG_CAPACITY)
+    return fail(PP_ERR_CAPACITY, "pp_iblt_decode_signed: more keys recovered than out_cap=%llu",
+                (unsigned long long)out_cap);
+  if (c.flags & FLAG_INTERNAL)
+    return fail(PP_ERR_INVALID_ARG, "pp_iblt_decode_signed: a pure cell's key does not hash to it");
+  if (c.flags & FLAG_ROUND_LIMIT)
+    return fail(PP_ERR_ROUND_LIMIT, "pp_iblt_decode_signed: stopped after max_rounds=%u rounds",
                 t->opt.max_rounds);
   return PP_OK;
 }

@@ -28,7 +28,7 @@ struct DecodeCtl {
   u32 more;             // 1 while another round must run
   u32 stats_rounds;     // batch: per-table per-round counter slots
   u32 apply_next;       // binned rounds: next chunk of update records to apply
-  u32 pad_;
+  u32 n_neg;            // signed decode: keys recovered with sign -1
 };
 
 // Per-round device statistics (index t-1 for round t).
@@ -172,6 +172,7 @@ struct IbltKernels {
   const void *claim, *apply_round;   // binned decode round
   int nr;  // compile-time rank (PP_MAX_R for the generic instance)
   const void *sub_scan = nullptr, *sub_filter = nullptr, *sub_peel = nullptr;  // sub-rounds (plain only)
+  const void *sg_scan = nullptr, *sg_peel = nullptr, *sg_filter = nullptr;     // signed (plain only)
 };
 
 // The kernel set for a rank code: 3 or 4 = that r; -4 = any r <= 4 (batched
