@@ -795,7 +795,8 @@ pp_status pp_iblt_decode(pp_iblt *t, uint64_t *d_out_keys, uint64_t out_cap, pp_
     t->exec = nullptr;
   }
   t->binned_rounds = want_bins;
-  PP_CUDA(cudaMemcpyAsync(t->ctl, t->h_ctl, sizeof(DecodeCtl), cudaMemcpyHostToDevice, s));
+  k_ctl_init<<<1, 32, 0, s>>>(t->ctl, *t->h_ctl);
+  PP_CUDA(cudaGetLastError());
   if (t->opt.host_loop) {
     pp_status st = run_host_loop(t, s);
     if (st != PP_OK) return st;
@@ -914,7 +915,8 @@ pp_status pp_iblt_decode_signed(pp_iblt *t, uint64_t *d_out_keys, int8_t *d_out_
   t->h_ctl->out = reinterpret_cast<u64 *>(d_out_keys);
   t->h_ctl->out_cap = out_cap;
   t->h_ctl->max_rounds = t->opt.max_rounds;
-  PP_CUDA(cudaMemcpyAsync(t->ctl, t->h_ctl, sizeof(DecodeCtl), cudaMemcpyHostToDevice, s));
+  k_ctl_init<<<1, 32, 0, s>>>(t->ctl, *t->h_ctl);
+  PP_CUDA(cudaGetLastError());
   // kernel arguments (the output sign pointer is one of them)
   const Cell *cells_c = t->cells;
   Cell *cells = t->cells;

@@ -392,6 +392,13 @@ __global__ void __launch_bounds__(kBlock) k_filter(const Cell *__restrict__ cell
 // The first iteration after the scan has an empty frontier and only promotes
 // F_1; it is not a round.
 // --------------------------------------------------------------------------
+// Start of a decode: the control block takes its initial value from the
+// launch (a kernel rather than a host-to-device copy, so the decode never
+// queues behind a bulk upload on the copy engine).
+__global__ void k_ctl_init(DecodeCtl *__restrict__ ctl, DecodeCtl init) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) *ctl = init;
+}
+
 __global__ void k_round_end(DecodeCtl *__restrict__ ctl, RoundStats st, int set_cond,
                             cudaGraphConditionalHandle cond) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
