@@ -164,7 +164,7 @@ pp_status ensure_round_bins(pp_batch *b, cudaStream_t s) {
   b->n_bins = nb;
   b->bin_cap = (uint32_t)cap;
   b->bin_shift = shift;
-  b->smem_claim = claim_smem_bytes(b->k.nr, nb);
+  b->smem_claim = claim_smem_bytes(b->k.nr, true, nb);
   b->smem_apply_round = apply_round_smem_bytes(true, nb);
   b->grid_claim = persistent_grid(b->k.claim, kBlock, b->smem_claim, b->opt.ctas_per_sm);
   b->grid_apply_round = persistent_grid(b->k.apply_round, kBlock, b->smem_apply_round, kApplyRoundCtas);

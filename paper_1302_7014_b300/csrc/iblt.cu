@@ -65,9 +65,9 @@ const void *bins_reset_kernel() { return (const void *)k_bins_reset; }
 
 const void *residual_kernel() { return (const void *)k_residual; }
 
-size_t claim_smem_bytes(int nr, uint32_t n_bins) {
+size_t claim_smem_bytes(int nr, bool batch, uint32_t n_bins) {
   const size_t cap = (size_t)kClaimChunk * nr;
-  return cap * 8 + (size_t)kClaimChunk * 8 + cap * 4 * 3 + 3 * (size_t)n_bins * 4;
+  return cap * (8 + 4 + (batch ? 4 : 0)) + (size_t)kClaimChunk * 8 + 3 * (size_t)n_bins * 4;
 }
 
 size_t apply_round_smem_bytes(bool batch, uint32_t n_bins) {
@@ -633,7 +633,7 @@ pp_status ensure_round_bins(pp_iblt *t, cudaStream_t s) {
   t->n_bins = nb;
   t->bin_cap = (uint32_t)cap;
   t->bin_shift = shift;
-  t->smem_claim = claim_smem_bytes(t->k.nr, nb);
+  t->smem_claim = claim_smem_bytes(t->k.nr, false, nb);
   t->smem_apply_round = apply_round_smem_bytes(false, nb);
   t->grid_claim = persistent_grid(t->k.claim, kBlock, t->smem_claim, t->opt.ctas_per_sm);
   t->grid_apply_round = persistent_grid(t->k.apply_round, kBlock, t->smem_apply_round, kApplyRoundCtas);

@@ -31,11 +31,15 @@ __device__ __forceinline__ int remove_key(Cell *cells, u32 c, u64 x, u64 cx) {
   return old;
 }
 
-// Shared memory of k_claim: staged records (4 arrays of kClaimChunk*NR) + 3 *
-// n_bins u32 + the plain decode's output staging (kClaimChunk u64).
+// Shared memory of k_claim: staged records (keys and cells, plus tables in a
+// batch: kClaimChunk*NR each) + the plain decode's output staging (kClaimChunk
+// u64) + 3 * n_bins u32.
 
+// Registers capped for 5 resident CTAs per SM for plain tables of rank 3 or 4
+// (48 per thread, a few spilled, beat 4 CTAs at 64) and for 4 otherwise (the
+// generic and batched instances would take 106-154 registers uncapped).
 template <int R, bool BATCH>
-__global__ void __launch_bounds__(kBlock) k_claim(Cell *__restrict__ cells, const TableArgs tab0,
+__global__ void __launch_bounds__(kBlock, (!BATCH && R >= 3) ? 5 : 4) k_claim(Cell *__restrict__ cells, const TableArgs tab0,
                                                   const TableArgs *__restrict__ tabs,
                                                   const u64 *__restrict__ fkey, const u32 *__restrict__ fcell,
                                                   const u32 *__restrict__ ftab, const u32 *__restrict__ bitmap,
@@ -48,9 +52,8 @@ __global__ void __launch_bounds__(kBlock) k_claim(Cell *__restrict__ cells, cons
   u64 *s_key = reinterpret_cast<u64 *>(smem);       // CAP
   u64 *s_out = s_key + CAP;                         // kClaimChunk (plain)
   u32 *s_cell = reinterpret_cast<u32 *>(s_out + kClaimChunk);
-  u32 *s_bin = s_cell + CAP;
-  u32 *s_tab = s_bin + CAP;
-  u32 *s_hist = s_tab + CAP;                        // n_bins
+  u32 *s_tab = s_cell + CAP;                        // CAP (batch)
+  u32 *s_hist = s_tab + (BATCH ? CAP : 0);          // n_bins
   u32 *s_scan = s_hist + rb.n_bins;
   u32 *s_base = s_scan + rb.n_bins;
   __shared__ u32 s_wt[33];
@@ -184,7 +187,6 @@ __global__ void __launch_bounds__(kBlock) k_claim(Cell *__restrict__ cells, cons
             const u32 pos = s_scan[bn] + rank[it][j];
             s_key[pos] = x[it];
             s_cell[pos] = cj[it][j];
-            s_bin[pos] = bn;
             if (BATCH) s_tab[pos] = tb[it];
           }
         }
@@ -193,7 +195,7 @@ __global__ void __launch_bounds__(kBlock) k_claim(Cell *__restrict__ cells, cons
     __syncthreads();
     const u32 total = s_total;
     for (u32 p = tid; p < total; p += kBlock) {
-      const u32 bn = s_bin[p];
+      const u32 bn = s_cell[p] >> rb.shift;
       const u32 slot = s_base[bn] + (p - s_scan[bn]);
       if (slot < rb.cap) {
         const u64 dst = (u64)bn * rb.cap + slot;

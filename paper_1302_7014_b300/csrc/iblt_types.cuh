@@ -8,7 +8,10 @@ namespace pp {
 constexpr int kBlock = 256;       // threads per CTA of the staged kernels
 constexpr int kScanItems = 4;     // cells per thread per scan chunk
 constexpr int kPeelItems = 2;     // frontier entries per thread per peel chunk
-constexpr int kFilterItems = 2;   // candidates per thread per filter chunk
+#ifndef PP_FILTER_ITEMS
+#define PP_FILTER_ITEMS 4
+#endif
+constexpr int kFilterItems = PP_FILTER_ITEMS;  // candidates per thread per filter chunk
 
 // Decode state on the device.  One instance per decode (plain or batched).
 struct DecodeCtl {
@@ -186,7 +189,7 @@ size_t peel_smem_bytes(int nr, bool batch);
 size_t bin_smem_bytes(int nr, bool batch, uint32_t n_slabs);
 
 // Dynamic shared memory of the binned round's claim and apply kernels.
-size_t claim_smem_bytes(int nr, uint32_t n_bins);
+size_t claim_smem_bytes(int nr, bool batch, uint32_t n_bins);
 size_t apply_round_smem_bytes(bool batch, uint32_t n_bins);
 
 // The bin-reset kernel that ends a binned round.
