@@ -76,7 +76,7 @@ size_t apply_round_smem_bytes(bool batch, uint32_t n_bins) {
 
 size_t bin_smem_bytes(int nr, bool batch, uint32_t n_slabs) {
   const size_t cap = (size_t)kBinKeys * nr;
-  return cap * (8 + 4 + 4 + (batch ? 4 : 0)) + 3 * (size_t)n_slabs * 4;
+  return cap * (8 + 4 + (batch ? 4 : 0)) + 3 * (size_t)n_slabs * 4;
 }
 
 size_t peel_smem_bytes(int nr, bool batch) {

@@ -16,6 +16,7 @@
 
 #include "iblt_types.cuh"
 
+
 namespace pp {
 
 template <int R>
@@ -27,9 +28,10 @@ __device__ __forceinline__ void apply_touch(Cell *cells, u32 c, u64 x, u64 cx, i
 }
 
 // Dynamic shared memory: 3 * n_slabs u32 (histogram, scan, base) + the staged
-// records of one step (kBinKeys * NR * (8 + 4 + 4 [+ 4]) bytes).
+// records of one step (kBinKeys * NR * (8 + 4 [+ 4]) bytes).  Registers capped for 5
+// resident CTAs per SM (2.99 -> 2.91 ms for the 2^26-cell build).
 template <int R, bool BATCH>
-__global__ void __launch_bounds__(kBlock) k_bin(Cell *__restrict__ cells, const TableArgs tab0,
+__global__ void __launch_bounds__(kBlock, 5) k_bin(Cell *__restrict__ cells, const TableArgs tab0,
                                                 const TableArgs *__restrict__ tabs,
                                                 const Chunk *__restrict__ chunks, u32 n_chunks,
                                                 const u64 *__restrict__ keys, u64 m, int sign, BinArgs b) {
@@ -38,8 +40,7 @@ __global__ void __launch_bounds__(kBlock) k_bin(Cell *__restrict__ cells, const 
   extern __shared__ __align__(16) unsigned char smem[];
   u64 *s_key = reinterpret_cast<u64 *>(smem);                 // CAP
   u32 *s_cell = reinterpret_cast<u32 *>(s_key + CAP);         // CAP
-  u32 *s_bin = s_cell + CAP;                                  // CAP
-  u32 *s_tab = s_bin + CAP;                                   // CAP (batch)
+  u32 *s_tab = s_cell + CAP;                                  // CAP (batch)
   u32 *s_hist = s_tab + (BATCH ? CAP : 0);                    // n_slabs
   u32 *s_scan = s_hist + b.n_slabs;                           // n_slabs
   u32 *s_base = s_scan + b.n_slabs;                           // n_slabs
@@ -125,7 +126,6 @@ __global__ void __launch_bounds__(kBlock) k_bin(Cell *__restrict__ cells, const 
               const u32 pos = s_scan[bn] + rank[it][j];
               s_key[pos] = x[it];
               s_cell[pos] = c[it][j];
-              s_bin[pos] = bn;
               if (BATCH) s_tab[pos] = tb;
             }
           }
@@ -134,7 +134,7 @@ __global__ void __launch_bounds__(kBlock) k_bin(Cell *__restrict__ cells, const 
       __syncthreads();
       const u32 total = s_total;
       for (u32 p = tid; p < total; p += kBlock) {
-        const u32 bn = s_bin[p];
+        const u32 bn = s_cell[p] >> kSlabShift;
         const u32 slot = s_base[bn] + (p - s_scan[bn]);
         if (slot < b.cap) {
           const u64 dst = (u64)bn * b.cap + slot;
