@@ -320,6 +320,44 @@ def bench_subrounds(pp, torch, table, dkeys, out, stream, m, steps):
             "recovered_per_subround_first": res.recovered_per_round[:6]}
 
 
+def bench_signed(pp, torch, args):
+    """Sparse recovery (Sec. 6 "Motivation"): 2^26 cells hold the difference of
+    two key sets, 0.45 n keys only in A and 0.30 n only in B (plus 0.25 n in
+    both, which cancel); decode_signed recovers A \\ B with sign +1 and B \\ A
+    with sign -1."""
+    n, r = 1 << 26, 3
+    na, nb, nc = int(0.45 * n), int(0.30 * n), int(0.25 * n)
+    keys = ppgen.distinct_keys(na + nb + nc, 31)
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        dk = torch.from_numpy(keys.view(np.int64)).cuda()
+        out = torch.empty(na + nb, dtype=torch.int64, device="cuda")
+        sg = torch.empty(na + nb, dtype=torch.int8, device="cuda")
+    stream.synchronize()
+    t = pp.IBLT(n, r, 0x5195)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    ms = []
+    for it in range(3 + max(3, min(args.steps, 5))):
+        t.build(dk[:nc + na], stream)               # A = common + only-A
+        t.delete(dk[:nc], stream)                   # B = common + only-B
+        t.delete(dk[nc + na:], stream)
+        ev[0].record(stream)
+        res = t.decode_signed(out, sg, stream=stream)
+        ev[1].record(stream)
+        stream.synchronize()
+        if it >= 3:
+            ms.append(ev[0].elapsed_time(ev[1]))
+    neg = int((sg[: res.recovered] < 0).sum().item())
+    assert res.recovered == na + nb and neg == nb and res.residual_cells == 0
+    d = float(np.mean(ms))
+    t.close()
+    del dk, out, sg
+    torch.cuda.empty_cache()
+    return {"workload": "2^26 cells, r=3: |A \\ B| = 0.45 n, |B \\ A| = 0.30 n, |A & B| = 0.25 n",
+            "decode_ms": d, "keys_per_s": res.recovered / (d * 1e-3), "rounds": res.rounds,
+            "recovered_plus": res.recovered - neg, "recovered_minus": neg}
+
+
 def bench_kcore(pp, torch, args):
     """k-core peeling of the density sweep (n = 2^25 vertices in 4 parts, r = 4,
     k = 2, one vertex per part per edge): the whole call (incidence build +
@@ -602,7 +640,7 @@ def main():
                 "kernel": dk["kernel"], "peak_source": f"{peak_kind} hbm_gbs",
                 "model": "sector floor: 32 B/cell scan + (64r+8) B/key decode; (8+64r) B/key build"}
 
-    batched = served = subrounds = kcore = tables = None
+    batched = served = subrounds = kcore = tables = signed = None
     if world == 1 and not args.no_extra:
         subrounds = bench_subrounds(pp, torch, table, dkeys, out, stream, m, max(3, min(args.steps, 5)))
         table.close()
@@ -613,6 +651,7 @@ def main():
         served = bench_served(pp, torch, args)
         torch.cuda.empty_cache()
         kcore = bench_kcore(pp, torch, args)
+        signed = bench_signed(pp, torch, args)
         tables = bench_tables(pp, torch, args)
 
     cpu = None
@@ -634,7 +673,7 @@ def main():
                 "decode_keys_per_s": m / (d_ms * 1e-3),
                 "kernels": kernels, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
                 "batched": batched, "served": served, "subrounds": subrounds, "kcore": kcore,
-                "paper_tables": tables,
+                "paper_tables": tables, "signed": signed,
                 "gpu_launches": args.steps * launches_per_step, "clocks": clk}
         print(json.dumps(line), flush=True)
     if batched is None:
