@@ -77,11 +77,15 @@ def traffic_for(kernel: str):
 
 
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+    """nvidia-smi clocks and throttle reasons, sampled every 50 ms from before
+    the warm-up; stop() keeps the samples stamped inside the timed region
+    (wall clock), or the two nearest ones when the region is shorter than the
+    sampling period."""
 
-    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+    FIELDS = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    REASONS = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
 
     def __init__(self, gpu_index: int):
         self.gpu = gpu_index
@@ -93,12 +97,13 @@ class ClockSampler:
             self.out = open(self.path, "w")
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", "50"],
                 stdout=self.out, stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
 
-    def stop(self):
+    def stop(self, t0: float, t1: float):
+        """Samples between wall-clock times t0 and t1 (time.time())."""
         if self.proc is None:
             return None
         self.proc.terminate()
@@ -107,26 +112,29 @@ class ClockSampler:
         except Exception:
             self.proc.kill()
         self.out.close()
-        sm, smax, reasons = [], 0.0, set()
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        import datetime
+        rows = []
         with open(self.path) as f:
             for line in f:
                 p = [x.strip() for x in line.split(",")]
-                if len(p) < 9:
+                if len(p) < 10:
                     continue
                 try:
-                    sm.append(float(p[1]))
-                    smax = max(smax, float(p[2]))
+                    ts = datetime.datetime.strptime(p[0], "%Y/%m/%d %H:%M:%S.%f").timestamp()
+                    rows.append((ts, float(p[2]), float(p[3]), p[6:10]))
                 except ValueError:
                     continue
-                for name, v in zip(names, p[5:9]):
-                    if v.lower().startswith("active"):
-                        reasons.add(name)
         os.unlink(self.path)
-        if not sm:
+        if not rows:
             return None
-        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": smax, "reasons": sorted(reasons),
-                "samples": len(sm)}
+        inside = [x for x in rows if t0 <= x[0] <= t1]
+        window = "timed region"
+        if not inside:
+            inside = sorted(rows, key=lambda x: min(abs(x[0] - t0), abs(x[0] - t1)))[:2]
+            window = "nearest samples"
+        reasons = sorted({n for x in inside for n, v in zip(self.REASONS, x[3]) if v.lower().startswith("active")})
+        return {"sm_mhz": float(np.median([x[1] for x in inside])), "sm_max_mhz": max(x[2] for x in inside),
+                "reasons": reasons, "samples": len(inside), "window": window}
 
 
 def dist_setup():
@@ -134,6 +142,32 @@ def dist_setup():
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     return world, rank, local
+
+
+def rank_workload(cfg, rank: int):
+    """(key seed, table seed) of this rank's replica: every rank decodes its own
+    table of the same shape with its own keys (weak scaling, no exchange)."""
+    return cfg["key_seed"] + 7919 * rank, cfg["table_seed"] + rank
+
+
+def max_over_ranks(x: float, dist, device) -> float:
+    """The job's time: the slowest rank's."""
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sum_over_ranks(x: int, dist, device) -> int:
+    """Units processed by the whole job."""
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.int64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return int(t.item())
 
 
 def oracle_sample(n_cells: int, r: int, c: float, key_seed: int, table_seed: int):
@@ -440,7 +474,7 @@ def bench_tables(pp, torch, args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=30)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -476,18 +510,12 @@ def main():
         if dist is not None:
             dist.barrier()
 
-    def max_over_ranks(x: float) -> float:
-        if dist is None:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
-
     n, r, c = cfg["n_cells"], cfg["r"], cfg["c"]
     m = ppgen.edges_from_c(c, n)
-    keys_h = ppgen.distinct_keys(m, cfg["key_seed"] + 7919 * rank)
+    key_seed, table_seed = rank_workload(cfg, rank)
+    keys_h = ppgen.distinct_keys(m, key_seed)
     stream = torch.cuda.Stream()
-    table = pp.IBLT(n, r, cfg["table_seed"] + rank, pp.options(host_loop=1) if args.host_loop else None)
+    table = pp.IBLT(n, r, table_seed, pp.options(host_loop=1) if args.host_loop else None)
     with torch.cuda.stream(stream):
         dkeys = torch.from_numpy(keys_h.view(np.int64)).cuda()
         out = torch.empty(m, dtype=torch.int64, device="cuda")
@@ -504,6 +532,8 @@ def main():
             ev[2].record(stream)
         return res
 
+    clocks = ClockSampler(local)
+    clocks.start()   # from before the warm-up: nvidia-smi takes a moment to start
     for _ in range(args.warmup):
         res = step()
     assert res.recovered == m and res.residual_cells == 0, "decode did not recover every key"
@@ -511,8 +541,7 @@ def main():
     evs = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
     barrier()
     torch.cuda.synchronize()
-    clocks = ClockSampler(local)
-    clocks.start()
+    w0 = time.time()
     t_start = torch.cuda.Event(enable_timing=True)
     t_end = torch.cuda.Event(enable_timing=True)
     t_start.record(stream)
@@ -522,15 +551,16 @@ def main():
         recovered += res.recovered
     t_end.record(stream)
     stream.synchronize()
+    w1 = time.time()
     barrier()
     torch.cuda.synchronize()
-    clk = clocks.stop()
+    clk = clocks.stop(w0, w1)
     total_ms = t_start.elapsed_time(t_end)
     build_ms = [e[0].elapsed_time(e[1]) for e in evs]
     decode_ms = [e[1].elapsed_time(e[2]) for e in evs]
-    total_ms = max_over_ranks(total_ms)
+    total_ms = max_over_ranks(total_ms, dist, "cuda")
     ms_per_step = total_ms / args.steps
-    value = recovered * world / (total_ms / 1000.0)
+    value = sum_over_ranks(recovered, dist, "cuda") / (total_ms / 1000.0)
 
     # end to end through the public API: pinned host keys in, recovered keys out.
     # Every step copies its keys host -> device and its recovered keys back;
@@ -608,8 +638,8 @@ def main():
         torch.cuda.synchronize()
         last = out_pinned[(args.steps - 1) % 2].numpy().view(np.uint64)
         assert np.bitwise_xor.reduce(last) == np.bitwise_xor.reduce(keys_h) and last.sum() == keys_h.sum()
-        e_ms = max_over_ranks(e0.elapsed_time(e1))
-        e2e = {"value": got * world / (e_ms / 1000.0), "unit": UNIT,
+        e_ms = max_over_ranks(e0.elapsed_time(e1), dist, "cuda")
+        e2e = {"value": sum_over_ranks(got, dist, "cuda") / (e_ms / 1000.0), "unit": UNIT,
                "h2d_bytes_per_step": int(m * 8), "d2h_bytes_per_step": int(m * 8),
                "ms_per_step": e_ms / args.steps,
                "pipeline": "upload of step k+1 and download of step k-1 overlap step k's compute (3 streams)"}
