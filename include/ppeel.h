@@ -131,6 +131,21 @@ pp_status pp_iblt_create(pp_iblt **out, uint64_t n_cells, uint32_t r, uint64_t s
 /* Frees the table and its workspace (synchronizes the device first).  NULL is a no-op. */
 pp_status pp_iblt_destroy(pp_iblt *t);
 
+/* Device memory of a table of n_cells cells and r hash functions (host only,
+ * no device call; opt as for pp_iblt_create, NULL = defaults):
+ *   *table_bytes  the cells, 32 B each;
+ *   *fixed_bytes  the decode workspace allocated by pp_iblt_create;
+ *   *peak_bytes   all the handle holds after pp_iblt_create, a pp_iblt_build
+ *                 or pp_iblt_insert of m_keys keys and a pp_iblt_decode: the
+ *                 above plus the update records of the slab-binned build and
+ *                 of the binned rounds (one shared buffer, sized for the
+ *                 larger) and the build's tile buffers.
+ * Not counted: what pp_iblt_decode_subrounds (a few hundred bytes) and
+ * pp_iblt_decode_signed (n_cells + 4 r n_cells bytes) add on first use.
+ * Any output pointer may be NULL.  Errors: INVALID_ARG as pp_iblt_create. */
+pp_status pp_workspace_size(uint64_t n_cells, uint32_t r, uint64_t m_keys, const pp_options *opt,
+                            uint64_t *table_bytes, uint64_t *fixed_bytes, uint64_t *peak_bytes);
+
 /* Zeroes every cell (enqueued on `stream`). */
 pp_status pp_iblt_clear(pp_iblt *t, void *stream);
 

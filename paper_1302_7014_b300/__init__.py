@@ -24,7 +24,7 @@ from ._lib import PP_MAX_R, Cell, DecodeResult, Options, PeelResult
 
 __all__ = ["PPError", "IBLT", "iblt_create", "iblt_insert", "iblt_delete", "iblt_build", "iblt_decode",
            "iblt_decode_subrounds", "iblt_decode_signed", "peel_kcore", "peel_kcore_subrounds", "options",
-           "PP_MAX_R"]
+           "workspace_size", "PP_MAX_R"]
 
 
 class PPError(RuntimeError):
@@ -38,6 +38,15 @@ def _check(status: int, fn: str):
     if status != 0:
         msg = _lib.load().pp_last_error()
         raise PPError(status, fn, msg.decode() if msg else "")
+
+
+def workspace_size(n_cells: int, r: int, m_keys: int = 0, opts: Options | None = None) -> dict:
+    """Device bytes of a table (pp_workspace_size): dict(table, fixed, peak)."""
+    t, f, p = ctypes.c_uint64(), ctypes.c_uint64(), ctypes.c_uint64()
+    _check(_lib.load().pp_workspace_size(int(n_cells), int(r), int(m_keys),
+                                         ctypes.byref(opts) if opts is not None else None,
+                                         ctypes.byref(t), ctypes.byref(f), ctypes.byref(p)), "pp_workspace_size")
+    return {"table": t.value, "fixed": f.value, "peak": p.value}
 
 
 def options(**kw) -> Options:

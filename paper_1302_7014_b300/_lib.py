@@ -59,6 +59,8 @@ _SIGNATURES = {
     "pp_peel_kcore": (ctypes.c_int, [u32, u32, u32, vp, u64, vp, vp, ctypes.POINTER(PeelResult),
                                      ctypes.POINTER(Options), vp]),
     "pp_iblt_decode_subrounds": (ctypes.c_int, [vp, vp, u64, ctypes.POINTER(DecodeResult), vp]),
+    "pp_workspace_size": (ctypes.c_int, [u64, u32, u64, ctypes.POINTER(Options), ctypes.POINTER(u64),
+                                         ctypes.POINTER(u64), ctypes.POINTER(u64)]),
     "pp_iblt_decode_signed": (ctypes.c_int, [vp, vp, vp, u64, ctypes.POINTER(DecodeResult), vp]),
     "pp_peel_kcore_subrounds": (ctypes.c_int, [u32, u32, u32, vp, u64, u32, ctypes.POINTER(u32), vp, vp,
                                                ctypes.POINTER(PeelResult), ctypes.POINTER(Options), vp]),

@@ -533,8 +533,7 @@ static pp_status batch_bin_pass(pp_batch *b, const uint64_t *d_keys, const uint6
 
 // Pass 2: slab by slab (zero-filled first when building from scratch).
 static pp_status batch_apply_pass(pp_batch *b, BinArgs &ba, int sign, bool zero_fill, cudaStream_t s) {
-  const uint64_t tile_cap = (uint64_t)((double)ba.cap / kTilesPerSlab * 1.15) + 256;
-  pp_status st = ensure_tiles(b->tiles, tile_cap, ba.cap, ba.n_slabs, true, s);
+  pp_status st = ensure_tiles(b->tiles, tile_cap_for(ba.cap), ba.cap, ba.n_slabs, true, s);
   if (st != PP_OK) return st;
   TableArgs t0{};
   return tile_apply_pass(b->cells, t0, b->tabs, ba, b->tiles, b->total_cells, sign, zero_fill, s);

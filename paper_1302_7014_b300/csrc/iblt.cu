@@ -588,13 +588,27 @@ pp_status ensure_records(pp_iblt *t, uint64_t records, uint32_t counts, cudaStre
   return PP_OK;
 }
 
+// Record capacity of one slab's list for a binned update of m keys: the
+// updates are uniform over the cells, so the expected count plus slack.
+uint64_t slab_record_cap(uint64_t n, uint32_t r, uint64_t m) {
+  const double per = (double)m * r * ((double)kSlabCells / (double)n);
+  return (uint64_t)(per * 1.05) + 4096;
+}
+
+// Bins of the binned decode rounds: count, capacity per bin (records), shift.
+void round_bin_layout(uint64_t n, uint32_t r, uint32_t *nb, uint64_t *cap, u32 *shift) {
+  const u32 sh = round_bin_shift(n);
+  const uint64_t span = n < (1ull << sh) ? n : (1ull << sh);
+  *nb = (uint32_t)((n + (1ull << sh) - 1) >> sh);
+  *cap = (uint64_t)((double)r * (double)span * 0.525) + 4096;
+  *shift = sh;
+}
+
 // Pass 1 of a binned build: route every (cell, key) update into its slab's list.
 pp_status bin_pass(pp_iblt *t, const uint64_t *d_keys, uint64_t m, int sign, int direct_overflow,
                    cudaStream_t s, BinArgs &ba) {
   const uint32_t ns = (uint32_t)((t->n + kSlabCells - 1) / kSlabCells);
-  // updates are uniform over the cells: expected count per slab plus slack
-  const double per = (double)m * t->r * ((double)kSlabCells / (double)t->n);
-  const uint64_t cap = (uint64_t)(per * 1.05) + 4096;
+  const uint64_t cap = slab_record_cap(t->n, t->r, m);
   if (cap > 0xFFFFFFF0ull) return fail(PP_ERR_INVALID_ARG, "pp_iblt_insert: too many keys for one call");
   pp_status st = ensure_records(t, cap * ns, ns, s);
   if (st != PP_OK) return st;
@@ -624,10 +638,10 @@ pp_status bin_pass(pp_iblt *t, const uint64_t *d_keys, uint64_t m, int sign, int
 // updates of half its cells' worth of recovered keys (a round recovers far
 // fewer; a fuller bin applies the excess directly).
 pp_status ensure_round_bins(pp_iblt *t, cudaStream_t s) {
-  const u32 shift = round_bin_shift(t->n);
-  const uint32_t nb = (uint32_t)((t->n + (1ull << shift) - 1) >> shift);
-  const uint64_t span = t->n < (1ull << shift) ? t->n : (1ull << shift);
-  const uint64_t cap = (uint64_t)((double)t->r * (double)span * 0.525) + 4096;
+  uint32_t nb;
+  uint64_t cap;
+  u32 shift;
+  round_bin_layout(t->n, t->r, &nb, &cap, &shift);
   pp_status st = ensure_records(t, cap * nb, nb, s);
   if (st != PP_OK) return st;
   t->n_bins = nb;
@@ -642,10 +656,7 @@ pp_status ensure_round_bins(pp_iblt *t, cudaStream_t s) {
 
 // Pass 2: slab by slab (zero-filled first when building from scratch).
 pp_status apply_pass(pp_iblt *t, BinArgs &ba, int sign, bool zero_fill, cudaStream_t s) {
-  // a tile's expected share of a slab's list, with slack (a fuller tile overflows
-  // to the slab's overflow list, which holds a whole slab)
-  const uint64_t tile_cap = (uint64_t)((double)ba.cap / kTilesPerSlab * 1.15) + 256;
-  pp_status st = ensure_tiles(t->tiles, tile_cap, ba.cap, ba.n_slabs, false, s);
+  pp_status st = ensure_tiles(t->tiles, tile_cap_for(ba.cap), ba.cap, ba.n_slabs, false, s);
   if (st != PP_OK) return st;
   return tile_apply_pass(t->cells, t->args, nullptr, ba, t->tiles, t->n, sign, zero_fill, s);
 }
@@ -710,6 +721,42 @@ pp_status pp_iblt_create(pp_iblt **out, uint64_t n_cells, uint32_t r, uint64_t s
   t->grid_filter = persistent_grid(t->k.filter, kBlock, 0, t->opt.ctas_per_sm);
   t->grid_insert = persistent_grid(t->k.insert, kBlock, 0, 8) * 4;
   *out = t;
+  return PP_OK;
+}
+
+pp_status pp_workspace_size(uint64_t n_cells, uint32_t r, uint64_t m_keys, const pp_options *opt,
+                            uint64_t *table_bytes, uint64_t *fixed_bytes, uint64_t *peak_bytes) {
+  if (r < 2 || r > PP_MAX_R || n_cells < r || n_cells > 0xFFFFFFFFull - 64)
+    return fail(PP_ERR_INVALID_ARG, "pp_workspace_size: r=%u or n_cells=%llu out of range", r,
+                (unsigned long long)n_cells);
+  const pp_options o = resolve_options(opt);
+  const uint64_t n = n_cells, mr = o.max_rounds;
+  const uint64_t table = n * sizeof(Cell);
+  const uint64_t fixed = n * (sizeof(u64) + 2 * sizeof(u32)) + ((n + 31) / 32 + 1) * sizeof(u32) +
+                         sizeof(DecodeCtl) + mr * (2 * sizeof(u64) + sizeof(u32));
+  // the update records are shared by binned builds and binned rounds: the larger need
+  uint64_t records = 0, counts = 0, tiles = 0;
+  const uint32_t ns = (uint32_t)((n + kSlabCells - 1) / kSlabCells);
+  const bool build_binned = m_keys && o.binned != 2 && (o.binned == 1 || (n >= (1ull << 23) && m_keys * r >= n / 4));
+  if (build_binned) {
+    const uint64_t cap = slab_record_cap(n, r, m_keys);
+    records = cap * ns;
+    counts = ns;
+    tiles = tile_pass_bytes(tile_cap_for(cap), cap, ns, false);
+  }
+  const bool rounds_binned = o.binned == 1 || (o.binned == 0 && n >= (1ull << 21));
+  if (rounds_binned) {
+    uint32_t nb;
+    uint64_t cap;
+    u32 shift;
+    round_bin_layout(n, r, &nb, &cap, &shift);
+    if (cap * nb > records) records = cap * nb;
+    if (nb > counts) counts = nb;
+  }
+  const uint64_t rec_bytes = records ? records * (sizeof(u64) + sizeof(u32)) + (counts + 1) * sizeof(u32) : 0;
+  if (table_bytes) *table_bytes = table;
+  if (fixed_bytes) *fixed_bytes = fixed;
+  if (peak_bytes) *peak_bytes = table + fixed + rec_bytes + tiles;
   return PP_OK;
 }
 

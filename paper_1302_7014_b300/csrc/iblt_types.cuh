@@ -157,6 +157,11 @@ struct TileBufs {
   bool batch = false;
 };
 
+// Records per tile for a slab list of slab_cap records, and the bytes of the
+// tile-pass buffers (pp_workspace_size reports them).
+uint64_t tile_cap_for(uint64_t slab_cap);
+uint64_t tile_pass_bytes(uint64_t tile_cap, uint64_t o_cap, uint32_t n_slabs, bool batch);
+
 // Grows the buffers to tile_cap records per tile, o_cap per slab's overflow,
 // n_slabs overflow counters.
 pp_status ensure_tiles(TileBufs &tb, uint64_t tile_cap, uint64_t o_cap, uint32_t n_slabs, bool batch,

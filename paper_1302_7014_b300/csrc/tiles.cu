@@ -32,6 +32,20 @@ static const void *tile_step_fn(bool batch) {
   return batch ? (const void *)k_tile_step<true> : (const void *)k_tile_step<false>;
 }
 
+uint64_t tile_cap_for(uint64_t slab_cap) {
+  // a tile's expected share of its slab's list with slack, a multiple of 32
+  // records so that every tile's region starts on a 128-byte line (a fuller
+  // tile spills to the overflow list, which holds a whole slab)
+  const uint64_t c = (uint64_t)((double)slab_cap / kTilesPerSlab * 1.15) + 256;
+  return (c + 31) / 32 * 32;
+}
+
+uint64_t tile_pass_bytes(uint64_t tile_cap, uint64_t o_cap, uint32_t n_slabs, bool batch) {
+  const uint64_t per = sizeof(u64) + sizeof(u32) + (batch ? sizeof(u32) : 0);
+  return 2 * tile_cap * kTilesPerSlab * per + 2 * kTilesPerSlab * sizeof(u32) + 3 * o_cap * per +
+         (uint64_t)n_slabs * sizeof(u32);
+}
+
 pp_status ensure_tiles(TileBufs &tb, uint64_t tile_cap, uint64_t o_cap, uint32_t n_slabs, bool batch,
                        cudaStream_t s) {
   if (tile_cap > 0xFFFFFFF0ull || o_cap > 0xFFFFFFF0ull)
@@ -39,8 +53,7 @@ pp_status ensure_tiles(TileBufs &tb, uint64_t tile_cap, uint64_t o_cap, uint32_t
   if (tb.key && tile_cap <= tb.cap && o_cap <= tb.o_cap && n_slabs <= tb.o_slabs && batch == tb.batch)
     return PP_OK;
   PP_CUDA(cudaStreamSynchronize(s));
-  // a multiple of 32 records: every tile's region starts on a 128-byte line
-  const uint64_t cap = ((tile_cap > tb.cap ? tile_cap : tb.cap) + 31) / 32 * 32;
+  const uint64_t cap = tile_cap > tb.cap ? tile_cap : tb.cap;  // tile_cap_for: multiples of 32
   const uint64_t ocap = o_cap > tb.o_cap ? o_cap : tb.o_cap;
   const uint32_t ns = n_slabs > tb.o_slabs ? n_slabs : tb.o_slabs;
   free_tiles(tb);

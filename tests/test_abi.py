@@ -8,6 +8,8 @@ import os
 import re
 import subprocess
 
+import pytest
+
 from conftest import ROOT
 
 
@@ -90,3 +92,19 @@ def test_product_path_does_not_touch_the_oracle():
             src = open(p).read()
             assert "import oracle" not in src and "from oracle" not in src, p
             assert "liboracle" not in src and "peel_oracle" not in src, p
+
+
+def test_workspace_size_host_only(ppeel_lib):
+    import paper_1302_7014_b300 as pp
+    small = pp.workspace_size(1 << 20, 3, 1000)
+    assert small["table"] == 32 << 20
+    # below 2^21 cells nothing is binned: only what create allocates
+    assert small["peak"] == small["table"] + small["fixed"]
+    big = pp.workspace_size(1 << 24, 3, int(0.75 * (1 << 24)))
+    assert big["table"] == 32 << 24 and big["fixed"] > 16 << 24
+    assert big["peak"] > big["table"] + big["fixed"] + 12 * 3 * int(0.75 * (1 << 24))
+    # binned=2 switches the binning off
+    plain = pp.workspace_size(1 << 24, 3, int(0.75 * (1 << 24)), pp.options(binned=2))
+    assert plain["peak"] == plain["table"] + plain["fixed"]
+    with pytest.raises(pp.PPError):
+        pp.workspace_size(10, 9)

@@ -345,3 +345,25 @@ def test_binned_rounds_after_workspace_growth(pp):
         assert res.rounds == ores["rounds"]
         assert res.recovered_per_round == [k.size for k in ores["keys"]]
         _assert_cells_equal(gt.cells(), ot)
+
+
+def test_workspace_size_matches_allocations(pp):
+    """pp_workspace_size against the device memory a handle really takes."""
+    n, r = 1 << 24, 3
+    m = int(0.75 * n)
+    ws = pp.workspace_size(n, r, m)
+    keys = _dev(ppgen.distinct_keys(m, 71))
+    out = torch.zeros(m, dtype=torch.int64, device="cuda")
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    t = pp.IBLT(n, r, 72)
+    free1 = torch.cuda.mem_get_info()[0]
+    t.build(keys)
+    res = t.decode(out)
+    torch.cuda.synchronize()
+    free2 = torch.cuda.mem_get_info()[0]
+    assert res.recovered == m
+    slack = (64 << 20) + ws["peak"] // 50   # allocation granularity, graph and context memory
+    assert abs((free0 - free1) - (ws["table"] + ws["fixed"])) < slack
+    assert abs((free0 - free2) - ws["peak"]) < slack
+    t.close()
