@@ -28,6 +28,10 @@ static IbltKernels iblt_kernels_t() {
                          200 * 1024);
     cudaFuncSetAttribute((const void *)k_claim<R, B>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          200 * 1024);
+    if constexpr (!B) {
+      cudaFuncSetAttribute((const void *)k_claim<R, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           200 * 1024);
+    }
     cudaFuncSetAttribute((const void *)k_apply_round<R, B>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          200 * 1024);
     attr_set = true;
@@ -39,6 +43,7 @@ static IbltKernels iblt_kernels_t() {
     k.sub_scan = (const void *)k_sscan<R>;
     k.sub_filter = (const void *)k_sfilter<R>;
     k.sub_peel = (const void *)k_speel<R>;
+    k.sub_claim = (const void *)k_claim<R, false, false>;
     k.sg_scan = (const void *)k_sgscan<R>;
     k.sg_peel = (const void *)k_sgpeel<R>;
     k.sg_filter = (const void *)k_sgfilter<R>;
@@ -121,8 +126,10 @@ struct pp_iblt {
   TileBufs tiles;  // tile pass of the binned build (allocated on first use)
   // decode with sub-tables (allocated on first use)
   SubDecCtl *sctl = nullptr, *h_sctl = nullptr;
-  cudaGraphExec_t sub_exec = nullptr;
-  int grid_sscan = 0, grid_sfilter = 0, grid_speel = 0;
+  u32 *squeue = nullptr;  // the per-sub-table queues (n entries)
+  cudaGraphExec_t sub_exec = nullptr, sub_exec_binned = nullptr;
+  uint32_t sub_graph_gen = 0;
+  int grid_sscan = 0, grid_sfilter = 0, grid_speel = 0, grid_sdist = 0;
   // signed decode (allocated on first use)
   signed char *fsign = nullptr;
   u32 *sg_cand = nullptr;  // r pushes per recovered key at most: r * n entries
@@ -138,6 +145,8 @@ void free_all(pp_iblt *t) {
   if (!t) return;
   if (t->exec) cudaGraphExecDestroy(t->exec);
   if (t->sub_exec) cudaGraphExecDestroy(t->sub_exec);
+  if (t->sub_exec_binned) cudaGraphExecDestroy(t->sub_exec_binned);
+  cudaFree(t->squeue);
   if (t->sg_exec) cudaGraphExecDestroy(t->sg_exec);
   cudaFree(t->fsign);
   cudaFree(t->sg_cand);
@@ -386,6 +395,10 @@ done:
 }
 
 // ---- decode with sub-tables ----------------------------------------------
+// Plain:  sscan -> while (more) { sfilter -> speel -> send }
+// Binned (tables of 2^21 cells or more, as the full-round decode):
+//         sscan -> while (more) { sfilter -> claim without the claim check ->
+//                                 apply_round -> sdistribute -> send_binned }
 struct SubArgs {
   // k_sscan
   const Cell *cells_c;
@@ -396,38 +409,55 @@ struct SubArgs {
   // k_sfilter
   u64 *fkey;
   u32 *fcell;
-  void *filter[6];
+  u32 *front_count;
+  void *filter[7];
   // k_speel
   Cell *cells;
   void *peel[6];
-  // k_send
+  // k_send / k_send_binned
   u64 *st_rec;
   int set_cond;
   cudaGraphConditionalHandle cond;
   void *end[4];
+  // binned: k_sdistribute, k_send_binned (claim and apply take ClaimArgs / ApplyRArgs)
+  const u32 *cand_c;
+  DecodeCtl *rctl;
+  const DecodeCtl *rctl_c;
+  RoundBins rb;
+  void *dist[5];
+  void *end_b[6];
   void bind() {
     void *a[4] = {&cells_c, &tab, &queue, &ctl};
     memcpy(scan, a, sizeof a);
-    void *b[6] = {&cells_c, &tab, &queue, &fkey, &fcell, &ctl};
+    void *b[7] = {&cells_c, &tab, &queue, &fkey, &fcell, &ctl, &front_count};
     memcpy(filter, b, sizeof b);
     void *c[6] = {&cells, &tab, &fkey, &fcell, &queue, &ctl};
     memcpy(peel, c, sizeof c);
     void *d[4] = {&ctl, &st_rec, &set_cond, &cond};
     memcpy(end, d, sizeof d);
+    void *e[5] = {&tab, &cand_c, &rctl_c, &queue, &ctl};
+    memcpy(dist, e, sizeof e);
+    void *f[6] = {&ctl, &rctl, &rb, &st_rec, &set_cond, &cond};
+    memcpy(end_b, f, sizeof f);
   }
 };
 
-void fill_sub_args(pp_iblt *t, SubArgs &a) {
+void fill_sub_args(pp_iblt *t, SubArgs &a, bool binned) {
   a.cells_c = t->cells;
   a.tab = t->args;
-  a.queue = t->cand;  // the candidate list doubles as the per-sub-table queues
+  a.queue = t->squeue;
   a.ctl = t->sctl;
   a.fkey = t->fkey;
   a.fcell = t->fcell;
+  a.front_count = binned ? &t->ctl->n_front : &t->sctl->n_front;
   a.cells = t->cells;
   a.st_rec = t->st_rec;
   a.set_cond = 0;
   a.cond = 0;
+  a.cand_c = t->cand;
+  a.rctl = t->ctl;
+  a.rctl_c = t->ctl;
+  a.rb = RoundBins{t->rec_key, t->rec_cell, nullptr, t->bin_count, t->bin_cap, t->n_bins, t->bin_shift, 0};
   a.bind();
 }
 
@@ -436,21 +466,35 @@ pp_status sub_prepare(pp_iblt *t) {
   if (!t->sctl) {
     PP_CUDA(cudaMalloc((void **)&t->sctl, sizeof(SubDecCtl)));
     PP_CUDA(cudaMallocHost((void **)&t->h_sctl, sizeof(SubDecCtl)));
+    PP_CUDA(cudaMalloc((void **)&t->squeue, t->n * sizeof(u32)));
     t->grid_sscan = persistent_grid(t->k.sub_scan, kBlock, 0, t->opt.ctas_per_sm);
     t->grid_sfilter = persistent_grid(t->k.sub_filter, kBlock, 0, t->opt.ctas_per_sm);
     t->grid_speel = persistent_grid(t->k.sub_peel, kBlock, 0, t->opt.ctas_per_sm);
+    t->grid_sdist = persistent_grid((const void *)k_sdistribute, kBlock, 0, t->opt.ctas_per_sm);
   }
   return PP_OK;
 }
 
-pp_status sub_host_loop(pp_iblt *t, cudaStream_t s) {
+pp_status sub_host_loop(pp_iblt *t, bool binned, cudaStream_t s) {
   SubArgs a;
-  fill_sub_args(t, a);
+  fill_sub_args(t, a, binned);
+  ClaimArgs ca;
+  ApplyRArgs aa;
+  ResetArgs ra;
+  if (binned) fill_round_args(t, ca, aa, ra);
   PP_CUDA(cudaLaunchKernel(t->k.sub_scan, dim3(t->grid_sscan), dim3(kBlock), a.scan, 0, s));
   for (;;) {
     PP_CUDA(cudaLaunchKernel(t->k.sub_filter, dim3(t->grid_sfilter), dim3(kBlock), a.filter, 0, s));
-    PP_CUDA(cudaLaunchKernel(t->k.sub_peel, dim3(t->grid_speel), dim3(kBlock), a.peel, 0, s));
-    PP_CUDA(cudaLaunchKernel((const void *)k_send, dim3(1), dim3(32), a.end, 0, s));
+    if (binned) {
+      PP_CUDA(cudaLaunchKernel(t->k.sub_claim, dim3(t->grid_claim), dim3(kBlock), ca.p, t->smem_claim, s));
+      PP_CUDA(cudaLaunchKernel(t->k.apply_round, dim3(t->grid_apply_round), dim3(kBlock), aa.p,
+                               t->smem_apply_round, s));
+      PP_CUDA(cudaLaunchKernel((const void *)k_sdistribute, dim3(t->grid_sdist), dim3(kBlock), a.dist, 0, s));
+      PP_CUDA(cudaLaunchKernel((const void *)k_send_binned, dim3(1), dim3(32), a.end_b, 0, s));
+    } else {
+      PP_CUDA(cudaLaunchKernel(t->k.sub_peel, dim3(t->grid_speel), dim3(kBlock), a.peel, 0, s));
+      PP_CUDA(cudaLaunchKernel((const void *)k_send, dim3(1), dim3(32), a.end, 0, s));
+    }
     PP_CUDA(cudaMemcpyAsync(&t->h_sctl->more, &t->sctl->more, sizeof(u32), cudaMemcpyDeviceToHost, s));
     PP_CUDA(cudaStreamSynchronize(s));
     if (!t->h_sctl->more) break;
@@ -458,16 +502,26 @@ pp_status sub_host_loop(pp_iblt *t, cudaStream_t s) {
   return PP_OK;
 }
 
-// sscan -> while (more) { sfilter -> speel -> send }; every pointer it holds
-// lives as long as the handle, so the graph is built once.
-pp_status sub_graph_launch(pp_iblt *t, cudaStream_t s) {
-  if (!t->sub_exec) {
+// Every pointer the plain graph holds lives as long as the handle, so it is
+// built once; the binned one also holds the record buffers and is rebuilt
+// when they move.
+pp_status sub_graph_launch(pp_iblt *t, bool binned, cudaStream_t s) {
+  cudaGraphExec_t &exec = binned ? t->sub_exec_binned : t->sub_exec;
+  if (binned && exec && t->sub_graph_gen != t->rec_gen) {
+    cudaGraphExecDestroy(exec);
+    exec = nullptr;
+  }
+  if (!exec) {
     SubArgs a;
-    fill_sub_args(t, a);
+    fill_sub_args(t, a, binned);
+    ClaimArgs ca;
+    ApplyRArgs aa;
+    ResetArgs ra;
+    if (binned) fill_round_args(t, ca, aa, ra);
     cudaGraph_t g = nullptr;
     PP_CUDA(cudaGraphCreate(&g, 0));
     pp_status st = PP_OK;
-    cudaGraphNode_t n_scan, n_cond, n_filter, n_peel, n_end;
+    cudaGraphNode_t n_scan, n_cond, n_filter, n_peel, n_apply, n_dist, n_end;
     cudaGraphConditionalHandle h;
     cudaGraphNodeParams cp{};
     cudaGraph_t body;
@@ -490,19 +544,32 @@ pp_status sub_graph_launch(pp_iblt *t, cudaStream_t s) {
     a.cond = h;
     st = add_kernel(&n_filter, body, nullptr, 0, t->k.sub_filter, t->grid_sfilter, kBlock, 0, a.filter);
     if (st != PP_OK) goto done;
-    st = add_kernel(&n_peel, body, &n_filter, 1, t->k.sub_peel, t->grid_speel, kBlock, 0, a.peel);
-    if (st != PP_OK) goto done;
-    st = add_kernel(&n_end, body, &n_peel, 1, (const void *)k_send, 1, 32, 0, a.end);
-    if (st != PP_OK) goto done;
-    if (cudaGraphInstantiate(&t->sub_exec, g, 0) != cudaSuccess) {
-      st = fail(PP_ERR_CUDA, "cudaGraphInstantiate failed: %s", cudaGetErrorString(cudaGetLastError()));
-      t->sub_exec = nullptr;
+    if (binned) {
+      st = add_kernel(&n_peel, body, &n_filter, 1, t->k.sub_claim, t->grid_claim, kBlock, t->smem_claim, ca.p);
+      if (st != PP_OK) goto done;
+      st = add_kernel(&n_apply, body, &n_peel, 1, t->k.apply_round, t->grid_apply_round, kBlock,
+                      t->smem_apply_round, aa.p);
+      if (st != PP_OK) goto done;
+      st = add_kernel(&n_dist, body, &n_apply, 1, (const void *)k_sdistribute, t->grid_sdist, kBlock, 0, a.dist);
+      if (st != PP_OK) goto done;
+      st = add_kernel(&n_end, body, &n_dist, 1, (const void *)k_send_binned, 1, 32, 0, a.end_b);
+      if (st != PP_OK) goto done;
+    } else {
+      st = add_kernel(&n_peel, body, &n_filter, 1, t->k.sub_peel, t->grid_speel, kBlock, 0, a.peel);
+      if (st != PP_OK) goto done;
+      st = add_kernel(&n_end, body, &n_peel, 1, (const void *)k_send, 1, 32, 0, a.end);
+      if (st != PP_OK) goto done;
     }
+    if (cudaGraphInstantiate(&exec, g, 0) != cudaSuccess) {
+      st = fail(PP_ERR_CUDA, "cudaGraphInstantiate failed: %s", cudaGetErrorString(cudaGetLastError()));
+      exec = nullptr;
+    }
+    if (binned) t->sub_graph_gen = t->rec_gen;
   done:
     cudaGraphDestroy(g);
     if (st != PP_OK) return st;
   }
-  PP_CUDA(cudaGraphLaunch(t->sub_exec, s));
+  PP_CUDA(cudaGraphLaunch(exec, s));
   return PP_OK;
 }
 
@@ -899,6 +966,19 @@ pp_status pp_iblt_decode_subrounds(pp_iblt *t, uint64_t *d_out_keys, uint64_t ou
   cudaStream_t s = as_stream(stream);
   pp_status st = sub_prepare(t);
   if (st != PP_OK) return st;
+  const bool binned = t->opt.binned == 1 || (t->opt.binned == 0 && t->n >= (1ull << 21));
+  if (binned) {
+    st = ensure_round_bins(t, s);
+    if (st != PP_OK) return st;
+    PP_CUDA(cudaMemsetAsync(t->bin_count, 0, t->n_bins * sizeof(u32), s));
+    // the round kernels' control block: output, counters
+    memset(t->h_ctl, 0, sizeof(DecodeCtl));
+    t->h_ctl->out = reinterpret_cast<u64 *>(d_out_keys);
+    t->h_ctl->out_cap = out_cap;
+    t->h_ctl->max_rounds = t->opt.max_rounds;
+    k_ctl_init<<<1, 32, 0, s>>>(t->ctl, *t->h_ctl);
+    PP_CUDA(cudaGetLastError());
+  }
   SubDecCtl &h = *t->h_sctl;
   memset(&h, 0, sizeof h);
   h.out = reinterpret_cast<u64 *>(d_out_keys);
@@ -907,7 +987,7 @@ pp_status pp_iblt_decode_subrounds(pp_iblt *t, uint64_t *d_out_keys, uint64_t ou
   h.r = t->r;
   h.part = t->r - 1;  // the first sub-round looks at sub-table 0
   PP_CUDA(cudaMemcpyAsync(t->sctl, t->h_sctl, sizeof(SubDecCtl), cudaMemcpyHostToDevice, s));
-  st = t->opt.host_loop ? sub_host_loop(t, s) : sub_graph_launch(t, s);
+  st = t->opt.host_loop ? sub_host_loop(t, binned, s) : sub_graph_launch(t, binned, s);
   if (st != PP_OK) return st;
   PP_CUDA(cudaMemcpyAsync(t->h_sctl, t->sctl, sizeof(SubDecCtl), cudaMemcpyDeviceToHost, s));
   PP_CUDA(cudaStreamSynchronize(s));

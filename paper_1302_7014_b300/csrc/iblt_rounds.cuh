@@ -38,7 +38,9 @@ __device__ __forceinline__ int remove_key(Cell *cells, u32 c, u64 x, u64 cx) {
 // Registers capped for 5 resident CTAs per SM for plain tables of rank 3 or 4
 // (48 per thread, a few spilled, beat 4 CTAs at 64) and for 4 otherwise (the
 // generic and batched instances would take 106-154 registers uncapped).
-template <int R, bool BATCH>
+// CLAIM = false (decode with sub-tables): every frontier entry recovers its key
+// -- within one sub-table no key is found twice -- so the bitmap is not read.
+template <int R, bool BATCH, bool CLAIM = true>
 __global__ void __launch_bounds__(kBlock, (!BATCH && R >= 3) ? 5 : 4) k_claim(Cell *__restrict__ cells, const TableArgs tab0,
                                                   const TableArgs *__restrict__ tabs,
                                                   const u64 *__restrict__ fkey, const u32 *__restrict__ fcell,
@@ -104,7 +106,7 @@ __global__ void __launch_bounds__(kBlock, (!BATCH && R >= 3) ? 5 : 4) k_claim(Ce
       // the lowest-index cell of x that was pure at the round's start wins
 #pragma unroll
       for (int j = 0; j < NR - 1; ++j) {
-        if (win[it] && j < jstar) {
+        if (CLAIM && win[it] && j < jstar) {
           const u32 w = __ldcg(bitmap + (cj[it][j] >> 5));
           if ((w >> (cj[it][j] & 31u)) & 1u) win[it] = false;
         }

@@ -139,10 +139,13 @@ __global__ void __launch_bounds__(kBlock) k_sscan(const Cell *__restrict__ cells
 }
 
 // Phase A of a sub-round: the queued cells of its sub-table that are pure now.
+// front_count: where the frontier's size goes (ctl->n_front, or the round
+// control block of the binned sub-rounds).
 template <int R>
 __global__ void __launch_bounds__(kBlock) k_sfilter(const Cell *__restrict__ cells, const TableArgs tab0,
                                                     const u32 *__restrict__ queue, u64 *__restrict__ fkey,
-                                                    u32 *__restrict__ fcell, SubDecCtl *__restrict__ ctl) {
+                                                    u32 *__restrict__ fcell, SubDecCtl *__restrict__ ctl,
+                                                    u32 *__restrict__ front_count) {
   constexpr int CH = kBlock * kFilterItems;
   __shared__ u64 s_key[CH];
   __shared__ u32 s_cell[CH];
@@ -176,7 +179,7 @@ __global__ void __launch_bounds__(kBlock) k_sfilter(const Cell *__restrict__ cel
     }
     __syncthreads();
     const u32 nn = s_n;
-    if (threadIdx.x == 0 && nn) s_base = atomicAdd(&ctl->n_front, nn);
+    if (threadIdx.x == 0 && nn) s_base = atomicAdd(front_count, nn);
     __syncthreads();
     for (u32 p = threadIdx.x; p < nn; p += kBlock) {
       fkey[s_base + p] = s_key[p];
@@ -261,6 +264,80 @@ __global__ void __launch_bounds__(kBlock) k_speel(Cell *__restrict__ cells, cons
   const u64 e = block_sum<u64, kBlock>(emptied, s_red);
   if (threadIdx.x == 0 && e) atomicAdd(&ctl->emptied, e);
   if (flags) atomicOr(&ctl->flags, flags);
+}
+
+// Binned sub-rounds: the candidates that k_apply_round collected (cells whose
+// count fell from 2 to 1) join the queues of their sub-tables.
+__global__ void __launch_bounds__(kBlock) k_sdistribute(const TableArgs tab0, const u32 *__restrict__ cand,
+                                                        const DecodeCtl *__restrict__ rctl, u32 *__restrict__ queue,
+                                                        SubDecCtl *__restrict__ ctl) {
+  constexpr int CH = kBlock * kScanItems;
+  __shared__ u32 s_cell[CH], s_part[CH], s_rank[CH];
+  __shared__ u32 s_cnt[PP_MAX_R], s_base[PP_MAX_R], s_n;
+  SubStage S{s_cell, s_part, s_rank, s_cnt, s_base, &s_n, (u32)CH};
+  if (threadIdx.x < PP_MAX_R) s_cnt[threadIdx.x] = 0;
+  if (threadIdx.x == 0) s_n = 0;
+  __syncthreads();
+  const u32 n = *(volatile const u32 *)&rctl->n_cand;
+  for (u64 c0 = (u64)blockIdx.x * CH; c0 < n; c0 += (u64)gridDim.x * CH) {
+#pragma unroll
+    for (int it = 0; it < kScanItems; ++it) {
+      const u64 i = c0 + (u64)it * kBlock + threadIdx.x;
+      if (i < n) {
+        const u32 c = __ldcs(cand + i);
+        sub_stage_push(S, tab0, queue, ctl, c, subtable_of(tab0, c));
+      }
+    }
+    sub_stage_flush(S, tab0, queue, ctl);
+  }
+}
+
+// End of a binned sub-round (one thread): the sub-round's bookkeeping as in
+// k_send, reading the recovered keys from the round control block, then that
+// block, the bins and the apply counter reset for the next sub-round.
+__global__ void k_send_binned(SubDecCtl *__restrict__ ctl, DecodeCtl *__restrict__ rctl, RoundBins rb,
+                              u64 *__restrict__ st_rec, int set_cond, cudaGraphConditionalHandle cond) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  SubDecCtl &c = *ctl;
+  DecodeCtl &d = *rctl;
+  const u32 t = c.sub;
+  if (t > 0) {
+    const u64 rec = d.n_out - c.out_start;
+    st_rec[t - 1] = rec;
+    if (rec) c.last = t;
+    c.head[c.part] = c.fe;
+  }
+  c.out_start = d.n_out;
+  c.n_out = d.n_out;
+  c.emptied = d.emptied;
+  d.n_front = 0;
+  d.n_cand = 0;
+  d.apply_next = 0;
+  for (u32 i = 0; i < rb.n_bins; ++i) rb.count[i] = 0;
+  c.flags |= d.flags;
+  u32 more = 0, dd = 1;
+  for (; dd <= c.r; ++dd) {
+    const u32 j = (c.part + dd) % c.r;
+    if (c.tail[j] > c.head[j]) {
+      more = 1;
+      break;
+    }
+  }
+  if (c.flags & (FLAG_CAPACITY | FLAG_INTERNAL)) more = 0;
+  if (more && (u64)t + dd > c.max_sub) {
+    c.flags |= FLAG_ROUND_LIMIT;
+    more = 0;
+  }
+  if (more) {
+    for (u32 q = 1; q < dd; ++q) st_rec[t + q - 1] = 0;  // idle sub-rounds
+    const u32 j = (c.part + dd) % c.r;
+    c.sub = t + dd;
+    c.part = j;
+    c.fb = c.head[j];
+    c.fe = c.tail[j];
+  }
+  c.more = more;
+  if (set_cond) cudaGraphSetConditional(cond, more);
 }
 
 // End of a sub-round (one thread).

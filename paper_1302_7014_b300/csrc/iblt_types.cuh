@@ -180,6 +180,7 @@ struct IbltKernels {
   const void *claim, *apply_round;   // binned decode round
   int nr;  // compile-time rank (PP_MAX_R for the generic instance)
   const void *sub_scan = nullptr, *sub_filter = nullptr, *sub_peel = nullptr;  // sub-rounds (plain only)
+  const void *sub_claim = nullptr;  // binned sub-rounds: k_claim without the claim check
   const void *sg_scan = nullptr, *sg_peel = nullptr, *sg_filter = nullptr;     // signed (plain only)
 };
 

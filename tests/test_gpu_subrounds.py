@@ -217,6 +217,17 @@ def test_iblt_subrounds_with_deletions(pp):
     run_iblt(pp, n, r, keys, 11, deletes=dels)
 
 
+@pytest.mark.parametrize("n,r,c,binned,host_loop", [
+    (50021, 3, 0.78, 1, 0),     # binned sub-rounds forced on a small table
+    (50021, 3, 0.78, 1, 1),
+    (1 << 21, 4, 0.72, 0, 1),   # binned by size, rounds driven from the host
+    (1 << 22, 3, 0.75, 2, 0),   # plain kernels forced on a large table
+])
+def test_iblt_subrounds_both_kernel_paths(pp, n, r, c, binned, host_loop):
+    keys = ppgen.distinct_keys(ppgen.edges_from_c(c, n), 30 + r)
+    run_iblt(pp, n, r, keys, 31, opts=pp.options(binned=binned, host_loop=host_loop))
+
+
 def test_iblt_subrounds_binned_table_size(pp):
     # 2^22 cells: the size where the full-round decode switches to binned rounds
     n, r = 1 << 22, 3
