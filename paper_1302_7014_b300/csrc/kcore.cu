@@ -25,6 +25,7 @@
 #include <string.h>
 
 #include "host.cuh"
+#include "kcore_csr.cuh"
 #include "scan.cuh"
 
 using namespace pp;
@@ -552,6 +553,96 @@ done:
 
 }  // namespace
 
+// The incidence scatter: tiled (kcore_csr.cuh) for large inputs, with the
+// plain atomic scatter as the fallback when a slab's record list is full.
+static pp_status scatter_incidences(const u32 *edges, uint64_t m, uint32_t r, uint32_t n, u32 *cursor, u32 *inc,
+                                    int egrid, cudaStream_t s) {
+  if (m * r < (1ull << 22)) {
+    k_scatter<<<egrid, kKBlock, 0, s>>>(edges, m, r, n, cursor, inc);
+    PP_CUDA(cudaGetLastError());
+    return PP_OK;
+  }
+  const uint32_t ns = (uint32_t)(((uint64_t)n + kVSlabVerts - 1) / kVSlabVerts);
+  const double span = (double)((uint64_t)n < kVSlabVerts ? n : kVSlabVerts);
+  const uint64_t cap = (uint64_t)((double)m * r * span / (double)n * 1.1) + 4096;
+  const uint64_t tcap = ((uint64_t)((double)cap / kVTilesPerSlab * 1.15) + 256 + 31) / 32 * 32;
+  if (cap > 0xFFFFFFF0ull || tcap * kVTilesPerSlab * 2 > 0xFFFFFFFFull) {
+    k_scatter<<<egrid, kKBlock, 0, s>>>(edges, m, r, n, cursor, inc);
+    PP_CUDA(cudaGetLastError());
+    return PP_OK;
+  }
+  u32 *rec_v = nullptr, *rec_e = nullptr, *count = nullptr, *flag = nullptr, *tv = nullptr, *te = nullptr;
+  u32 *tcount = nullptr, *ov = nullptr, *oe = nullptr, *o_count = nullptr;
+  cudaError_t e = cudaSuccess;
+  auto al = [&](u32 **p, uint64_t words) {
+    if (e == cudaSuccess) e = cudaMallocAsync((void **)p, (words ? words : 1) * 4, s);
+  };
+  al(&rec_v, cap * ns);
+  al(&rec_e, cap * ns);
+  al(&count, ns);
+  al(&flag, 1);
+  al(&tv, 2 * tcap * kVTilesPerSlab);
+  al(&te, 2 * tcap * kVTilesPerSlab);
+  al(&tcount, 2 * kVTilesPerSlab);
+  al(&ov, 3 * cap);
+  al(&oe, 3 * cap);
+  al(&o_count, ns);
+  pp_status st = PP_OK;
+  uint32_t h_flag = 0;
+  if (e == cudaSuccess) e = cudaMemsetAsync(count, 0, ns * 4, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(flag, 0, 4, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(tcount, 0, 2 * kVTilesPerSlab * 4, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(o_count, 0, ns * 4, s);
+  if (e != cudaSuccess) {
+    st = cuda_fail(e, "pp_peel_kcore tiled scatter buffers", __FILE__, __LINE__);
+  } else {
+    VBinArgs vb{rec_v, rec_e, count, flag, (u32)cap, ns};
+    const size_t smem_bin = (size_t)kVBinEdges * r * 8 + 3 * (size_t)ns * 4;
+    static bool attr = false;
+    if (!attr) {
+      cudaFuncSetAttribute((const void *)k_vbin, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
+      cudaFuncSetAttribute((const void *)k_vtile_step, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)(kVTileVerts * 4));
+      attr = true;
+    }
+    const uint64_t steps = (m + kVBinEdges - 1) / kVBinEdges;
+    const int pgrid = persistent_grid((const void *)k_vbin, kVThreads, smem_bin, 4);
+    const int bgrid = (int)(steps < (uint64_t)pgrid ? steps : (uint64_t)pgrid);
+    k_vbin<<<bgrid, kVThreads, smem_bin, s>>>(edges, m, r, n, vb);
+    if ((e = cudaGetLastError()) != cudaSuccess ||
+        (e = cudaMemcpyAsync(&h_flag, flag, 4, cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
+        (e = cudaStreamSynchronize(s)) != cudaSuccess) {
+      st = cuda_fail(e, "pp_peel_kcore incidence binning", __FILE__, __LINE__);
+    } else if (h_flag) {
+      // a slab got more incidences than its list holds (skewed degrees)
+      k_scatter<<<egrid, kKBlock, 0, s>>>(edges, m, r, n, cursor, inc);
+      if ((e = cudaGetLastError()) != cudaSuccess) st = cuda_fail(e, "pp_peel_kcore scatter", __FILE__, __LINE__);
+    } else {
+      VTileArgs ta{tv, te, tcount, tcap * kVTilesPerSlab, (u32)tcap, (u32)cap, ov, oe, o_count};
+      const u32 sms = (u32)sm_count();
+      for (u32 step = 0; step <= ns + 1 && st == PP_OK; ++step) {
+        const u32 n_bin = step < ns ? 2 * sms : 0u;
+        const u32 n_apply = (step >= 1 && step - 1 < ns) ? kVTilesPerSlab : (step == ns + 1 ? 2 * sms : 0u);
+        if (n_apply + n_bin == 0) continue;
+        k_vtile_step<<<n_apply + n_bin, kVThreads, kVTileVerts * 4, s>>>(vb, ta, cursor, inc, step, n_apply,
+                                                                         n_bin, n);
+        if ((e = cudaGetLastError()) != cudaSuccess) st = cuda_fail(e, "pp_peel_kcore tile scatter", __FILE__, __LINE__);
+      }
+    }
+  }
+  cudaFreeAsync(rec_v, s);
+  cudaFreeAsync(rec_e, s);
+  cudaFreeAsync(count, s);
+  cudaFreeAsync(flag, s);
+  cudaFreeAsync(tv, s);
+  cudaFreeAsync(te, s);
+  cudaFreeAsync(tcount, s);
+  cudaFreeAsync(ov, s);
+  cudaFreeAsync(oe, s);
+  cudaFreeAsync(o_count, s);
+  return st;
+}
+
 static pp_status peel_kcore_impl(uint32_t n, uint32_t r, uint32_t k, const uint32_t *d_edges, uint64_t m,
                           const Parts *parts, int32_t *d_vertex_round, int32_t *d_edge_round,
                           pp_peel_result *res, const pp_options *opt, void *stream) {
@@ -608,7 +699,10 @@ static pp_status peel_kcore_impl(uint32_t n, uint32_t r, uint32_t k, const uint3
       status = cuda_fail(e, "pp_peel_kcore cursor copy", __FILE__, __LINE__);
       goto cleanup;
     }
-    if (m) k_scatter<<<egrid, kKBlock, 0, s>>>(d_edges, m, r, n, w.cursor, w.inc);
+    if (m) {
+      status = scatter_incidences(d_edges, m, r, n, w.cursor, w.inc, egrid, s);
+      if (status != PP_OK) goto cleanup;
+    }
     if (parts) {
       k_kinit_sub<<<1, 32, 0, s>>>(w.sub, n, m, k, o.max_rounds, parts->p);
       if (n) k_kscan_sub<<<vgrid, kKBlock, 0, s>>>(w.deg, n, *parts, w.f0, d_vertex_round, w.sub);
