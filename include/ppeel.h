@@ -253,8 +253,10 @@ typedef struct pp_peel_result {
  * every edge touching one of them.
  * d_vertex_round (n int32, or NULL): round each vertex was removed in, 0 = in
  * the k-core.  d_edge_round (m int32, or NULL): the same for edges.
- * Workspace (~16 B per vertex + 4 B per incidence) is taken from the stream's
- * memory pool and returned before the call ends.
+ * Workspace (~16 B per vertex + 4 B per incidence, plus ~16 B per incidence
+ * for the tiled incidence scatter of large inputs) comes from a memory pool
+ * the library keeps per device; it goes back to that pool when the call ends
+ * and stays mapped for the next call.
  * Errors: INVALID_ARG (k < 1, r outside 2..PP_MAX_R, a vertex id >= n -- the
  * id check runs on the device), ROUND_LIMIT, OUT_OF_MEMORY, CUDA.
  * Synchronizes `stream`. */
