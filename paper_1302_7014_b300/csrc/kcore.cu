@@ -127,7 +127,41 @@ __global__ void __launch_bounds__(kKBlock) k_kscan(const u32 *__restrict__ deg, 
   }
 }
 
+// Degrees during the rounds: one u32 per vertex, or (D16, every degree below
+// 2^16) two 16-bit halves per u32 word, which halves the array so it stays in
+// L2 (64 MB at 2^25 vertices).  A half never underflows -- each incidence is
+// removed once -- so subtracting 1 from it never borrows from its neighbour.
+template <bool D16>
+__device__ __forceinline__ u32 deg_dec(u32 *deg, u32 u) {
+  if constexpr (D16) {
+    const u32 sh = (u & 1u) << 4;
+    return (atomicSub(deg + (u >> 1), 1u << sh) >> sh) & 0xffffu;
+  } else {
+    return atomicSub(deg + u, 1u);
+  }
+}
+
+// Largest degree (decides whether the rounds run on 16-bit degrees).
+__global__ void __launch_bounds__(kKBlock) k_degmax(const u32 *__restrict__ deg, u32 n, u32 *__restrict__ out) {
+  u32 mx = 0;
+  for (u64 v = (u64)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (u64)gridDim.x * blockDim.x)
+    mx = max(mx, __ldcs(deg + v));
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(kFull, mx, o));
+  if (lane_id() == 0 && mx) atomicMax(out, mx);
+}
+
+// deg16 word w = deg[2w] | deg[2w+1] << 16.
+__global__ void __launch_bounds__(kKBlock) k_deg16(const u32 *__restrict__ deg, u32 n, u32 *__restrict__ deg16) {
+  for (u64 w = (u64)blockIdx.x * blockDim.x + threadIdx.x; w < ((u64)n + 1) / 2; w += (u64)gridDim.x * blockDim.x) {
+    const u32 lo = __ldcs(deg + 2 * w);
+    const u32 hi = 2 * w + 1 < n ? __ldcs(deg + 2 * w + 1) : 0u;
+    deg16[w] = lo | (hi << 16);
+  }
+}
+
 // One round: remove F_t and its edges.
+template <bool D16>
 __global__ void __launch_bounds__(kKBlock) k_kpeel(const u32 *__restrict__ edges, u32 r, u32 n,
                                                    const u32 *__restrict__ off, const u32 *__restrict__ inc,
                                                    u32 *__restrict__ alive, u32 *__restrict__ deg,
@@ -160,7 +194,7 @@ __global__ void __launch_bounds__(kKBlock) k_kpeel(const u32 *__restrict__ edges
         for (u32 j = 0; j < r; ++j) {
           const u32 u = edges[(u64)e * r + j];
           if (u >= n) continue;
-          const u32 od = atomicSub(deg + u, 1u);
+          const u32 od = deg_dec<D16>(deg, u);
           if (od == k) {
             if (vround) vround[u] = (int)t + 1;
             const u32 q = atomicAdd(&s_n, 1u);
@@ -331,6 +365,7 @@ __global__ void __launch_bounds__(kKBlock) k_kscan_sub(const u32 *__restrict__ d
 }
 
 // One sub-round: remove the frontier of the current part and its edges.
+template <bool D16>
 __global__ void __launch_bounds__(kKBlock) k_kpeel_sub(const u32 *__restrict__ edges, u32 r, u32 n,
                                                        const u32 *__restrict__ off, const u32 *__restrict__ inc,
                                                        u32 *__restrict__ alive, u32 *__restrict__ deg,
@@ -361,7 +396,7 @@ __global__ void __launch_bounds__(kKBlock) k_kpeel_sub(const u32 *__restrict__ e
         for (u32 h = 0; h < r; ++h) {
           const u32 u = edges[(u64)e * r + h];
           if (u >= n) continue;
-          const u32 od = atomicSub(deg + u, 1u);
+          const u32 od = deg_dec<D16>(deg, u);
           if (od == k) stage_push(S, P, queue, ctl, u);
         }
       }
@@ -421,6 +456,7 @@ namespace {
 struct KWork {
   u32 *deg = nullptr, *off = nullptr, *cursor = nullptr, *inc = nullptr, *alive = nullptr;
   u32 *f0 = nullptr, *f1 = nullptr;
+  u32 *deg16 = nullptr, *dmax = nullptr;
   PeelCtl *ctl = nullptr;
   SubCtl *sub = nullptr;
   u64 *st_s = nullptr, *st_m = nullptr;
@@ -699,6 +735,7 @@ static pp_status peel_kcore_impl(uint32_t n, uint32_t r, uint32_t k, const uint3
   al((void **)&w.f0, nn * 4);
   al((void **)&w.f1, nn * 4);
   al((void **)&w.ctl, sizeof(PeelCtl));
+  al((void **)&w.dmax, sizeof(u32));
   if (parts) al((void **)&w.sub, sizeof(SubCtl));
   al((void **)&w.st_s, (size_t)o.max_rounds * 8);
   al((void **)&w.st_m, (size_t)o.max_rounds * 8);
@@ -744,23 +781,48 @@ static pp_status peel_kcore_impl(uint32_t n, uint32_t r, uint32_t k, const uint3
       status = cuda_fail(e, "pp_peel_kcore build kernels", __FILE__, __LINE__);
       goto cleanup;
     }
+    // 16-bit degrees for the rounds when every degree fits
+    {
+      uint32_t h_dmax = 0;
+      if ((e = cudaMemsetAsync(w.dmax, 0, sizeof(u32), s)) != cudaSuccess) {
+        status = cuda_fail(e, "pp_peel_kcore memset", __FILE__, __LINE__);
+        goto cleanup;
+      }
+      if (n) k_degmax<<<vgrid, kKBlock, 0, s>>>(w.deg, n, w.dmax);
+      if ((e = cudaMemcpyAsync(&h_dmax, w.dmax, sizeof(u32), cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
+          (e = cudaStreamSynchronize(s)) != cudaSuccess) {
+        status = cuda_fail(e, "pp_peel_kcore degree readback", __FILE__, __LINE__);
+        goto cleanup;
+      }
+      if (n && h_dmax < (1u << 16)) {
+        if ((e = ws_alloc((void **)&w.deg16, ((nn + 1) / 2) * 4, s)) != cudaSuccess) {
+          status = cuda_fail(e, "pp_peel_kcore workspace", __FILE__, __LINE__);
+          goto cleanup;
+        }
+        k_deg16<<<vgrid, kKBlock, 0, s>>>(w.deg, n, w.deg16);
+      }
+    }
+    const bool d16 = w.deg16 != nullptr;
+    u32 *rdeg = d16 ? w.deg16 : w.deg;
     if (parts) {
-      KSubPeelArgs pa{d_edges, r, n, w.off, w.inc, w.alive, w.deg, *parts, w.f0, d_vertex_round,
+      KSubPeelArgs pa{d_edges, r, n, w.off, w.inc, w.alive, rdeg, *parts, w.f0, d_vertex_round,
                       d_edge_round, w.sub, {}};
       pa.bind();
       KSubEndArgs ea{w.sub, PeelStats{w.st_s, w.st_m}, *parts, 0, 0, {}};
       ea.bind();
-      const int pgrid = persistent_grid((const void *)k_kpeel_sub, kKBlock, 0, o.ctas_per_sm);
-      status = run_rounds((const void *)k_kpeel_sub, pa.p, (const void *)k_kround_end_sub, ea, pgrid,
+      const void *peel = d16 ? (const void *)k_kpeel_sub<true> : (const void *)k_kpeel_sub<false>;
+      const int pgrid = persistent_grid(peel, kKBlock, 0, o.ctas_per_sm);
+      status = run_rounds(peel, pa.p, (const void *)k_kround_end_sub, ea, pgrid,
                           o.host_loop != 0, s, &w.sub->more);
     } else {
-      KPeelArgs pa{d_edges, r, n, w.off, w.inc, w.alive, w.deg, w.f0, w.f1, d_vertex_round, d_edge_round,
+      KPeelArgs pa{d_edges, r, n, w.off, w.inc, w.alive, rdeg, w.f0, w.f1, d_vertex_round, d_edge_round,
                    w.ctl, {}};
       pa.bind();
       KEndArgs ea{w.ctl, PeelStats{w.st_s, w.st_m}, 0, 0, {}};
       ea.bind();
-      const int pgrid = persistent_grid((const void *)k_kpeel, kKBlock, 0, o.ctas_per_sm);
-      status = run_rounds((const void *)k_kpeel, pa.p, (const void *)k_kround_end, ea, pgrid,
+      const void *peel = d16 ? (const void *)k_kpeel<true> : (const void *)k_kpeel<false>;
+      const int pgrid = persistent_grid(peel, kKBlock, 0, o.ctas_per_sm);
+      status = run_rounds(peel, pa.p, (const void *)k_kround_end, ea, pgrid,
                           o.host_loop != 0, s, &w.ctl->more);
     }
     if (status != PP_OK) goto cleanup;
@@ -798,6 +860,8 @@ static pp_status peel_kcore_impl(uint32_t n, uint32_t r, uint32_t k, const uint3
   }
 cleanup:
   cudaFreeAsync(w.deg, s);
+  cudaFreeAsync(w.deg16, s);
+  cudaFreeAsync(w.dmax, s);
   cudaFreeAsync(w.off, s);
   cudaFreeAsync(w.cursor, s);
   cudaFreeAsync(w.inc, s);
