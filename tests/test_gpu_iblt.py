@@ -164,13 +164,18 @@ def test_deleting_keys_never_inserted(pp, n, binned):
     assert res.residual_cells == ot.residual_cells()
 
 
-def test_round_limit(pp):
+@pytest.mark.parametrize("binned,host_loop", [(2, 0), (1, 0), (1, 1)], ids=["rounds", "binned", "binned-hostloop"])
+def test_round_limit(pp, binned, host_loop):
+    """A decode stopped by the round limit leaves the table as the oracle's after that round.
+    In the binned decode this also checks the end-of-decode clearing of the winners' cells:
+    the frontier that was found but not processed must stay untouched."""
     keys = ppgen.distinct_keys(ppgen.edges_from_c(0.80, 100000), 41)
+    opts = pp.options(max_rounds=3, binned=binned, host_loop=host_loop)
     with pytest.raises(pp.PPError) as ei:
-        run_case(pp, 100000, 3, keys, 41, opts=pp.options(max_rounds=3), max_rounds=3)
+        run_case(pp, 100000, 3, keys, 41, opts=opts, max_rounds=3)
     assert ei.value.name == "PP_ERR_ROUND_LIMIT"
     # the table is left after round 3, like the oracle's
-    gt = pp.IBLT(100000, 3, 41, pp.options(max_rounds=3))
+    gt = pp.IBLT(100000, 3, 41, opts)
     ot = oracle.IBLT(100000, 3, 41)
     gt.insert(_dev(keys))
     ot.insert(keys)
