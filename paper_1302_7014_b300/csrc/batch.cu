@@ -68,6 +68,11 @@ struct pp_batch {
   size_t smem_claim = 0, smem_apply_round = 0, smem_bin = 0;
   int grid_claim = 0, grid_apply_round = 0, grid_bin = 0;
   TileBufs tiles;  // tile pass of the binned build (allocated on first use)
+  // binned updates fed from the keys (every table lies within two slabs)
+  bool keys_tiles = false;
+  int krank = 0;                 // kernel rank, as passed to iblt_kernels
+  u32 *slab_chunk = nullptr, *h_slab_chunk = nullptr;
+  uint32_t slab_chunk_cap = 0;   // slabs
 };
 
 namespace {
@@ -112,6 +117,8 @@ void free_batch(pp_batch *b) {
   cudaFree(b->bin_count);
   cudaFree(b->bin_overflow);
   free_tiles(b->tiles);
+  cudaFree(b->slab_chunk);
+  cudaFreeHost(b->h_slab_chunk);
   delete b;
 }
 
@@ -359,7 +366,11 @@ pp_status pp_batch_create(pp_batch **out, uint32_t n_tables, const uint64_t *n_c
   b->n_scan_chunks = (u32)chunks.size();
   uint32_t max_r = 0;
   for (uint32_t i = 0; i < n_tables; ++i) max_r = r[i] > max_r ? r[i] : max_r;
-  b->k = iblt_kernels(common_r ? (int)common_r : (max_r <= 4 ? -4 : 0), true);
+  b->krank = common_r ? (int)common_r : (max_r <= 4 ? -4 : 0);
+  b->k = iblt_kernels(b->krank, true);
+  b->keys_tiles = true;
+  for (uint32_t i = 0; i < n_tables; ++i)
+    if (n_cells[i] > kSlabCells) b->keys_tiles = false;
   b->smem_peel = peel_smem_bytes(b->k.nr, true);
   const uint64_t N = base;
   const uint32_t mr = b->opt.max_rounds;
@@ -531,6 +542,65 @@ static pp_status batch_bin_pass(pp_batch *b, const uint64_t *d_keys, const uint6
   return PP_OK;
 }
 
+// Binned update without slab lists, for batches whose tables each lie within
+// two slabs: the tile pass hashes the keys of each slab's tables itself
+// (k_tile_step_keys), so no slab list is written or read back.  Tiles are
+// sized for the expected records of the fullest slab, the overflow sets for
+// the most records a slab can receive (every key of every table it overlaps).
+static pp_status batch_keys_pass(pp_batch *b, const uint64_t *d_keys, const uint64_t *h_key_offsets, u32 nch,
+                                 int sign, bool zero_fill, cudaStream_t s) {
+  const uint32_t ns = (uint32_t)((b->total_cells + kSlabCells - 1) / kSlabCells);
+  std::vector<double> expect(ns, 0.0);
+  std::vector<uint64_t> bound(ns, 0);
+  for (uint32_t i = 0; i < b->n_tables; ++i) {
+    const TableArgs &t = b->h_tabs[i];
+    const uint64_t rec = (h_key_offsets[i + 1] - h_key_offsets[i]) * t.r;
+    if (rec == 0) continue;
+    const uint64_t c0 = t.base, c1 = (uint64_t)t.base + t.n_cells;
+    for (uint64_t sl = c0 / kSlabCells; sl * kSlabCells < c1; ++sl) {
+      const uint64_t a0 = sl * kSlabCells > c0 ? sl * kSlabCells : c0;
+      const uint64_t a1 = (sl + 1) * kSlabCells < c1 ? (sl + 1) * kSlabCells : c1;
+      expect[sl] += (double)rec * (double)(a1 - a0) / (double)t.n_cells;
+      bound[sl] += rec;
+    }
+  }
+  double mx = 0;
+  uint64_t ocap = 0;
+  for (uint32_t sl = 0; sl < ns; ++sl) {
+    mx = expect[sl] > mx ? expect[sl] : mx;
+    ocap = bound[sl] > ocap ? bound[sl] : ocap;
+  }
+  // each slab's range of the (table-ordered) chunk list
+  if (ns > b->slab_chunk_cap) {
+    PP_CUDA(cudaStreamSynchronize(s));
+    cudaFree(b->slab_chunk);
+    cudaFreeHost(b->h_slab_chunk);
+    b->slab_chunk = nullptr;
+    b->h_slab_chunk = nullptr;
+    b->slab_chunk_cap = 0;
+    PP_CUDA(cudaMalloc((void **)&b->slab_chunk, 2 * (size_t)ns * sizeof(u32)));
+    PP_CUDA(cudaMallocHost((void **)&b->h_slab_chunk, 2 * (size_t)ns * sizeof(u32)));
+    b->slab_chunk_cap = ns;
+  }
+  u32 *sc = b->h_slab_chunk;  // upload_chunks synchronized the stream: no copy reads it
+  for (uint32_t sl = 0; sl < ns; ++sl) sc[2 * sl] = 0xffffffffu, sc[2 * sl + 1] = 0;
+  for (u32 ch = 0; ch < nch; ++ch) {
+    const TableArgs &t = b->h_tabs[b->h_ins_chunks[ch].table];
+    const uint64_t c0 = t.base, c1 = (uint64_t)t.base + t.n_cells;
+    for (uint64_t sl = c0 / kSlabCells; sl * kSlabCells < c1; ++sl) {
+      if (ch < sc[2 * sl]) sc[2 * sl] = ch;
+      sc[2 * sl + 1] = ch + 1;
+    }
+  }
+  for (uint32_t sl = 0; sl < ns; ++sl)
+    if (sc[2 * sl] == 0xffffffffu) sc[2 * sl] = 0;
+  PP_CUDA(cudaMemcpyAsync(b->slab_chunk, sc, 2 * (size_t)ns * sizeof(u32), cudaMemcpyHostToDevice, s));
+  pp_status st = ensure_tiles(b->tiles, tile_cap_for((uint64_t)mx + 1), ocap, ns, true, s);
+  if (st != PP_OK) return st;
+  return tile_keys_pass(b->cells, b->tabs, reinterpret_cast<const u64 *>(d_keys), b->ins_chunks, b->slab_chunk,
+                        ns, b->krank, b->tiles, b->total_cells, sign, zero_fill, s);
+}
+
 // Pass 2: slab by slab (zero-filled first when building from scratch).
 static pp_status batch_apply_pass(pp_batch *b, BinArgs &ba, int sign, bool zero_fill, cudaStream_t s) {
   pp_status st = ensure_tiles(b->tiles, tile_cap_for(ba.cap), ba.cap, ba.n_slabs, true, s);
@@ -555,7 +625,9 @@ static pp_status batch_update(pp_batch *b, const uint64_t *d_keys, const uint64_
   pp_status st = upload_chunks(b, h_key_offsets, s, &nch, &records);
   if (st != PP_OK || nch == 0) return st;
   if (!d_keys) return fail(PP_ERR_INVALID_ARG, "pp_batch_insert: NULL keys");
-  if (use_binned(b, records)) {
+  if (use_binned(b, records) && b->keys_tiles) {
+    st = batch_keys_pass(b, d_keys, h_key_offsets, nch, sign, false, s);
+  } else if (use_binned(b, records)) {
     BinArgs ba;
     st = batch_bin_pass(b, d_keys, h_key_offsets, nch, sign, 1, s, ba);
     if (st == PP_OK) st = batch_apply_pass(b, ba, sign, false, s);
@@ -590,6 +662,8 @@ pp_status pp_batch_build(pp_batch *b, const uint64_t *d_keys, const uint64_t *h_
   if (nch == 0 || !use_binned(b, records)) {
     PP_CUDA(cudaMemsetAsync(b->cells, 0, b->total_cells * sizeof(Cell), s));
     if (nch) st = direct_update(b, d_keys, nch, +1, s);
+  } else if (b->keys_tiles) {
+    st = batch_keys_pass(b, d_keys, h_key_offsets, nch, +1, true, s);
   } else {
     BinArgs ba;
     st = batch_bin_pass(b, d_keys, h_key_offsets, nch, +1, 0, s, ba);

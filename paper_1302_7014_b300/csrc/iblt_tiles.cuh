@@ -200,6 +200,130 @@ __device__ __forceinline__ void tile_apply(unsigned char *smem, Cell *cells, con
   }
 }
 
+// Role "bin" of a batched update taken straight from the keys (no slab
+// lists): a batch's keys are ordered by table and its tables by arena
+// position, so the tables that overlap slab `slab` own one contiguous range
+// of the insert chunks.  Every key of that range is hashed here and those of
+// its cells that fall in the slab are sorted into the slab's tiles, exactly as
+// tile_bin sorts the slab's records.  A table that straddles two slabs is
+// hashed in both passes, each keeping its own cells.
+struct TileKeysArgs {
+  const u64 *keys;
+  const Chunk *chunks;    // key ranges of one table each, in table order
+  const u32 *slab_chunk;  // per slab: first and one-past-last chunk of its tables
+  u32 n_slabs;
+};
+
+template <int R>
+__device__ __forceinline__ void tile_bin_keys(unsigned char *smem, const TableArgs *tabs, const TileKeysArgs &ka,
+                                              const TileArgs &ta, u32 slab, u32 bi, u32 nb) {
+  constexpr int NR = nr_of<R>();
+  constexpr int KPT = kTileBinItems / NR > 0 ? kTileBinItems / NR : 1;  // keys per thread per step
+  static_assert(KPT * NR * kTileThreads <= kTileBinChunk, "a step's records exceed the staging");
+  constexpr u32 KEYS = (u32)KPT * kTileThreads;
+  u64 *s_key = reinterpret_cast<u64 *>(smem);  // kTileBinChunk
+  u32 *s_cell = reinterpret_cast<u32 *>(s_key + kTileBinChunk);
+  __shared__ u32 s_hist[kTilesPerSlab], s_scan[kTilesPerSlab], s_base[kTilesPerSlab];
+  __shared__ u32 s_wt[kTileThreads / 32];
+  __shared__ u32 s_total;
+  const u32 tid = threadIdx.x;
+  const u64 keep = l2_evict_last_policy();
+  const u32 set = slab & 1u;
+  u64 *tkey = ta.key + set * ta.set_stride;
+  u32 *tcell = ta.cell + set * ta.set_stride;
+  u32 *ttab = ta.tab + set * ta.set_stride;
+  u32 *tcount = ta.count + set * kTilesPerSlab;
+  const u64 oset = (u64)(slab % 3u) * ta.o_cap;
+  const u32 cbase = slab << kSlabShift;
+  const u32 cb = ka.slab_chunk[2 * slab], ce = ka.slab_chunk[2 * slab + 1];
+  for (u32 ch = cb + bi; ch < ce; ch += nb) {
+    const Chunk k = ka.chunks[ch];
+    const TableArgs &T = tabs[k.table];
+    const int r = rank_of<R>(T);
+    for (u32 k0 = k.begin; k0 < k.end; k0 += KEYS) {
+      s_hist[tid] = 0;
+      __syncthreads();
+      u64 x[KPT];
+      u32 c[KPT][NR], rk[KPT][NR];
+#pragma unroll
+      for (int it = 0; it < KPT; ++it) {
+        const u32 i = k0 + (u32)it * kTileThreads + tid;
+        x[it] = i < k.end ? __ldcs(ka.keys + i) : 0ull;
+      }
+#pragma unroll
+      for (int it = 0; it < KPT; ++it) {
+        const bool v = k0 + (u32)it * kTileThreads + tid < k.end;
+        cells_of<NR>(x[it], T, c[it]);
+#pragma unroll
+        for (int j = 0; j < NR; ++j) {
+          const bool in = v && j < r && c[it][j] - cbase < kSlabCells;
+          if (!in) c[it][j] = 0xffffffffu;  // no cell has this index
+          rk[it][j] = in ? atomicAdd(s_hist + ((c[it][j] - cbase) >> kTileShift), 1u) : 0u;
+        }
+      }
+      __syncthreads();
+      // exclusive scan of the 512-entry histogram: one entry per thread
+      const u32 own = s_hist[tid];
+      u32 inc = own;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const u32 y = __shfl_up_sync(kFull, inc, o);
+        if ((int)lane_id() >= o) inc += y;
+      }
+      if (lane_id() == 31) s_wt[tid >> 5] = inc;
+      __syncthreads();
+      if (tid < 32) {
+        const u32 w = tid < kTileThreads / 32 ? s_wt[tid] : 0;
+        u32 wi = w;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const u32 y = __shfl_up_sync(kFull, wi, o);
+          if ((int)tid >= o) wi += y;
+        }
+        if (tid < kTileThreads / 32) s_wt[tid] = wi - w;
+      }
+      __syncthreads();
+      s_scan[tid] = s_wt[tid >> 5] + inc - own;
+      s_base[tid] = own ? atomicAdd(tcount + tid, own) : 0u;
+      if (tid == kTileThreads - 1) s_total = s_scan[tid] + own;
+      __syncthreads();
+      // order the step's records by tile in shared memory
+#pragma unroll
+      for (int it = 0; it < KPT; ++it) {
+#pragma unroll
+        for (int j = 0; j < NR; ++j) {
+          if (c[it][j] != 0xffffffffu) {
+            const u32 pos = s_scan[(c[it][j] - cbase) >> kTileShift] + rk[it][j];
+            s_key[pos] = x[it];
+            s_cell[pos] = c[it][j];
+          }
+        }
+      }
+      __syncthreads();
+      // contiguous runs per tile; a full tile spills to the overflow list
+      const u32 total = s_total;
+      for (u32 p = tid; p < total; p += kTileThreads) {
+        const u32 tile = (s_cell[p] - cbase) >> kTileShift;
+        const u32 slot = s_base[tile] + (p - s_scan[tile]);
+        if (slot < ta.cap) {
+          const u64 dst = (u64)tile * ta.cap + slot;
+          st_l2_policy(tkey + dst, s_key[p], keep);
+          st_l2_policy(tcell + dst, s_cell[p], keep);
+          st_l2_policy(ttab + dst, k.table, keep);
+        } else {
+          const u32 q = atomicAdd(ta.o_count + slab, 1u);
+          if (q < ta.o_cap) {  // o_cap bounds the slab's records: always true
+            ta.o_key[oset + q] = s_key[p];
+            ta.o_cell[oset + q] = s_cell[p];
+            ta.o_tab[oset + q] = k.table;
+          }
+        }
+      }
+      __syncthreads();
+    }
+  }
+}
+
 // Launch s (0 <= s <= n_slabs + 1):
 //   apply role  (s >= 1 and s - 1 < n_slabs): the overflow of slab s - 2, then
 //               the tiles of slab s - 1;  for s = n_slabs + 1: the overflow of
@@ -242,6 +366,46 @@ __global__ void __launch_bounds__(kTileThreads, 2) k_tile_step(Cell *__restrict_
     }
   }
   if (s >= 1 && s - 1 < b.n_slabs) tile_apply<BATCH>(smem, cells, tab0, tabs, ta, s - 1, idx, n_cells, sign, zero);
+}
+
+// The batched tile step with the bin role taken from the keys (tile_bin_keys);
+// the apply role is k_tile_step's.
+template <int R>
+__global__ void __launch_bounds__(kTileThreads, 2) k_tile_step_keys(Cell *__restrict__ cells,
+                                                           const TableArgs *__restrict__ tabs, TileKeysArgs ka,
+                                                           TileArgs ta, u32 s, u32 n_apply, u32 n_bin,
+                                                           u64 n_cells, int sign, int zero) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const u32 both = n_apply < n_bin ? n_apply : n_bin;
+  const u32 blk = blockIdx.x;
+  bool apply;
+  u32 idx;
+  if (blk < 2 * both) {
+    apply = (blk & 1u) == 0;
+    idx = blk >> 1;
+  } else {
+    apply = n_apply > n_bin;
+    idx = blk - both;
+  }
+  if (!apply) {
+    tile_bin_keys<R>(smem, tabs, ka, ta, s, idx, n_bin);
+    return;
+  }
+  if (s >= 2) {
+    const u32 os = s - 2;
+    const u64 oset = (u64)(os % 3u) * ta.o_cap;
+    const u32 no = min(ta.o_count[os], (u32)ta.o_cap);
+    for (u32 i = idx * kTileThreads + threadIdx.x; i < no; i += n_apply * kTileThreads) {
+      const u64 x = ta.o_key[oset + i];
+      Cell *p = cells + ta.o_cell[oset + i];
+      const TableArgs &T = tabs[ta.o_tab[oset + i]];
+      atomicAdd(&p->count, sign);
+      atomicXor(&p->key, x);
+      atomicXor(&p->chk, mix64(x ^ chk_seed_of(T)));
+    }
+  }
+  const TableArgs t0{};
+  if (s >= 1 && s - 1 < ka.n_slabs) tile_apply<true>(smem, cells, t0, tabs, ta, s - 1, idx, n_cells, sign, zero);
 }
 
 }  // namespace pp

@@ -172,6 +172,12 @@ void free_tiles(TileBufs &tb);
 // k_tile_apply (zero = build from empty cells), then the last overflow flush.
 pp_status tile_apply_pass(Cell *cells, const TableArgs &tab0, const TableArgs *tabs, const BinArgs &ba,
                           TileBufs &tb, uint64_t n_cells, int sign, bool zero, cudaStream_t s);
+// Batched tile pass with the bin role fed from the keys: slab_chunk (device,
+// 2 * n_slabs) holds each slab's range of `chunks`; rank as for iblt_kernels.
+// Every record of a slab must fit its overflow set (tb.o_cap).
+pp_status tile_keys_pass(Cell *cells, const TableArgs *tabs, const u64 *keys, const Chunk *chunks,
+                         const u32 *slab_chunk, uint32_t n_slabs, int rank, TileBufs &tb, uint64_t n_cells,
+                         int sign, bool zero, cudaStream_t s);
 
 // Entry points of one instantiation of the IBLT kernels (plain or batched).
 struct IbltKernels {

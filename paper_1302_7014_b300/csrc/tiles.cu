@@ -32,6 +32,18 @@ static const void *tile_step_fn(bool batch) {
   return batch ? (const void *)k_tile_step<true> : (const void *)k_tile_step<false>;
 }
 
+// rank as for iblt_kernels: 3, 4, -4 (any r <= 4) or 0 (any r)
+static const void *tile_keys_fn(int rank) {
+  static bool attr = false;
+  const void *f[4] = {(const void *)k_tile_step_keys<3>, (const void *)k_tile_step_keys<4>,
+                      (const void *)k_tile_step_keys<-4>, (const void *)k_tile_step_keys<0>};
+  if (!attr) {
+    for (const void *p : f) cudaFuncSetAttribute(p, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tile_step_smem());
+    attr = true;
+  }
+  return rank == 3 ? f[0] : rank == 4 ? f[1] : rank == -4 ? f[2] : f[3];
+}
+
 uint64_t tile_cap_for(uint64_t slab_cap) {
   // a tile's expected share of its slab's list with slack, a multiple of 32
   // records so that every tile's region starts on a 128-byte line (a fuller
@@ -109,6 +121,31 @@ pp_status tile_apply_pass(Cell *cells, const TableArgs &tab0, const TableArgs *t
     if (n_apply + n_bin == 0) continue;
     PP_CUDA(cudaLaunchKernel(tile_step_fn(tb.batch), dim3(n_apply + n_bin), dim3(kTileThreads), args,
                              tile_step_smem(), s));
+  }
+  return PP_OK;
+}
+
+pp_status tile_keys_pass(Cell *cells, const TableArgs *tabs, const u64 *keys, const Chunk *chunks,
+                         const u32 *slab_chunk, uint32_t n_slabs, int rank, TileBufs &tb, uint64_t n_cells,
+                         int sign, bool zero, cudaStream_t s) {
+  if (!tb.batch) return fail(PP_ERR_INVALID_ARG, "tile pass: batch buffers expected");
+  PP_CUDA(cudaMemsetAsync(tb.o_count, 0, (size_t)n_slabs * 4, s));
+  TileArgs ta{tb.key, tb.cell, tb.tab, tb.count, tb.cap * kTilesPerSlab, (u32)tb.cap, (u32)tb.o_cap,
+              tb.o_key, tb.o_cell, tb.o_tab, tb.o_count};
+  TileKeysArgs ka{keys, chunks, slab_chunk, n_slabs};
+  Cell *c = cells;
+  const TableArgs *tp = tabs;
+  u32 step = 0, n_apply = 0, n_bin = 0;
+  u64 n = n_cells;
+  int sg = sign, z = zero ? 1 : 0;
+  void *args[] = {&c, &tp, &ka, &ta, &step, &n_apply, &n_bin, &n, &sg, &z};
+  const void *fn = tile_keys_fn(rank);
+  const u32 sms = (u32)sm_count();
+  for (step = 0; step <= n_slabs + 1; ++step) {
+    n_bin = step < n_slabs ? sms : 0u;
+    n_apply = (step >= 1 && step - 1 < n_slabs) ? kTilesPerSlab : (step == n_slabs + 1 ? 2 * sms : 0u);
+    if (n_apply + n_bin == 0) continue;
+    PP_CUDA(cudaLaunchKernel(fn, dim3(n_apply + n_bin), dim3(kTileThreads), args, tile_step_smem(), s));
   }
   return PP_OK;
 }

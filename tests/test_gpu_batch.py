@@ -182,6 +182,50 @@ def test_binned_batch_build_and_rounds(ppb, rs):
         assert (cells["key_xor"] == ot.keyx).all()
 
 
+@pytest.mark.parametrize("rs,big", [((3, 4), False), ((2, 5, 6), False), ((3, 4), True)],
+                         ids=["keys-r3-4", "keys-r2-6", "slab-lists"])
+def test_binned_batch_build_across_slabs(ppb, rs, big):
+    """Tables spread over several 2^21-cell slabs, some straddling two.  Such
+    a batch is built with each slab's keys hashed inside the tile pass; with
+    one table larger than a slab it takes the slab-list build instead.  Build,
+    insert and delete cell for cell, and the decode, against the oracle."""
+    pp, bm = ppb
+    specs = _specs(24, 131 + len(rs), rs=rs, lo=17, hi=20.6, c_lo=0.5, c_hi=0.9)
+    if big:
+        s5 = specs[5]
+        specs[5] = ((1 << 21) + 4099, 3, 0.7, s5[3], s5[4])
+    n_cells = [s[0] for s in specs]
+    assert sum(n_cells) > 4 * (1 << 21)
+    keys = [ppgen.distinct_keys(ppgen.edges_from_c(s[2], s[0]), s[4]) for s in specs]
+    koff = np.concatenate([[0], np.cumsum([k.size for k in keys])]).astype(np.uint64)
+    dk = torch.from_numpy(np.concatenate(keys).view(np.int64)).cuda()
+    b = bm.Batch(n_cells, [s[1] for s in specs], [s[3] for s in specs], pp.options(binned=1))
+    b.insert(torch.from_numpy(ppgen.distinct_keys(int(koff[-1]), 5).view(np.int64)).cuda(), koff)  # junk
+    b.build(dk, koff)                       # must wipe the junk
+    ots = []
+    for i, s in enumerate(specs):
+        ot = oracle.IBLT(s[0], s[1], s[3])
+        ot.insert(keys[i])
+        ots.append(ot)
+        cells = b.cells(i)
+        assert (cells["count"].astype(np.int64) == ot.count).all(), i
+        assert (cells["key_xor"] == ot.keyx).all() and (cells["chk_xor"] == ot.chkx).all(), i
+    out = torch.full((int(koff[-1]),), -1, dtype=torch.int64, device="cuda")
+    res = b.decode(out, koff)
+    check_against_oracle(specs, keys, koff, res, out.cpu().numpy().view(np.uint64), b, cells_every=4)
+    # incremental insert + delete through the same path
+    b.clear()
+    b.insert(dk, koff)
+    dele = [k[::5] for k in keys]
+    doff = np.concatenate([[0], np.cumsum([d.size for d in dele])]).astype(np.uint64)
+    b.delete(torch.from_numpy(np.concatenate(dele).view(np.int64)).cuda(), doff)
+    for i in range(0, len(specs), 3):
+        ots[i].insert(dele[i], sign=-1)
+        cells = b.cells(i)
+        assert (cells["count"].astype(np.int64) == ots[i].count).all(), i
+        assert (cells["key_xor"] == ots[i].keyx).all() and (cells["chk_xor"] == ots[i].chkx).all(), i
+
+
 def test_binned_batch_decode_after_deletions(ppb):
     """Residue counted by the scan (no shortcut once keys were deleted)."""
     pp, bm = ppb
