@@ -142,21 +142,38 @@ __device__ __forceinline__ u32 deg_dec(u32 *deg, u32 u) {
 }
 
 // Largest degree (decides whether the rounds run on 16-bit degrees).
-__global__ void __launch_bounds__(kKBlock) k_degmax(const u32 *__restrict__ deg, u32 n, u32 *__restrict__ out) {
-  u32 mx = 0;
-  for (u64 v = (u64)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (u64)gridDim.x * blockDim.x)
-    mx = max(mx, __ldcs(deg + v));
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(kFull, mx, o));
-  if (lane_id() == 0 && mx) atomicMax(out, mx);
+// Degree histogram in 16-bit halves (vertex v in half v & 1 of word v >> 1),
+// which are also the degrees the rounds decrement: half the bytes of 32-bit
+// counts, so the counters stay in L2.  An increment that finds a half at
+// 0xFFFF carried out of it; *ovf is then set and the caller counts in 32 bits
+// instead.  Zeroes the edge-round output.
+__global__ void __launch_bounds__(kKBlock) k_hist16(const u32 *__restrict__ edges, u64 m, u32 r, u32 n,
+                                                    u32 *__restrict__ deg16, int *__restrict__ eround,
+                                                    u32 *__restrict__ ovf, PeelCtl *__restrict__ ctl) {
+  u32 bad = 0, carry = 0;
+  const u64 stride = (u64)gridDim.x * blockDim.x;
+  for (u64 e = (u64)blockIdx.x * blockDim.x + threadIdx.x; e < m; e += stride) {
+    for (u32 j = 0; j < r; ++j) {
+      const u32 v = edges[e * r + j];
+      if (v < n) {
+        const u32 sh = (v & 1u) << 4;
+        carry |= ((atomicAdd(deg16 + (v >> 1), 1u << sh) >> sh) & 0xffffu) == 0xffffu;
+      } else {
+        bad = 1;
+      }
+    }
+    if (eround) eround[e] = 0;
+  }
+  if (bad) atomicOr(&ctl->flags, (u32)FLAG_BAD_ID);
+  if (carry) atomicOr(ovf, 1u);
 }
 
-// deg16 word w = deg[2w] | deg[2w+1] << 16.
-__global__ void __launch_bounds__(kKBlock) k_deg16(const u32 *__restrict__ deg, u32 n, u32 *__restrict__ deg16) {
+// deg[v] = half v & 1 of deg16[v >> 1] (the CSR build reads 32-bit degrees).
+__global__ void __launch_bounds__(kKBlock) k_unpack16(const u32 *__restrict__ deg16, u32 n, u32 *__restrict__ deg) {
   for (u64 w = (u64)blockIdx.x * blockDim.x + threadIdx.x; w < ((u64)n + 1) / 2; w += (u64)gridDim.x * blockDim.x) {
-    const u32 lo = __ldcs(deg + 2 * w);
-    const u32 hi = 2 * w + 1 < n ? __ldcs(deg + 2 * w + 1) : 0u;
-    deg16[w] = lo | (hi << 16);
+    const u32 x = deg16[w];
+    deg[2 * w] = x & 0xffffu;
+    if (2 * w + 1 < n) deg[2 * w + 1] = x >> 16;
   }
 }
 
@@ -456,7 +473,7 @@ namespace {
 struct KWork {
   u32 *deg = nullptr, *off = nullptr, *cursor = nullptr, *inc = nullptr, *alive = nullptr;
   u32 *f0 = nullptr, *f1 = nullptr;
-  u32 *deg16 = nullptr, *dmax = nullptr;
+  u32 *deg16 = nullptr, *ovf = nullptr;
   PeelCtl *ctl = nullptr;
   SubCtl *sub = nullptr;
   u64 *st_s = nullptr, *st_m = nullptr;
@@ -735,7 +752,8 @@ static pp_status peel_kcore_impl(uint32_t n, uint32_t r, uint32_t k, const uint3
   al((void **)&w.f0, nn * 4);
   al((void **)&w.f1, nn * 4);
   al((void **)&w.ctl, sizeof(PeelCtl));
-  al((void **)&w.dmax, sizeof(u32));
+  al((void **)&w.deg16, ((nn + 1) / 2) * 4);
+  al((void **)&w.ovf, sizeof(u32));
   if (parts) al((void **)&w.sub, sizeof(SubCtl));
   al((void **)&w.st_s, (size_t)o.max_rounds * 8);
   al((void **)&w.st_m, (size_t)o.max_rounds * 8);
@@ -754,13 +772,32 @@ static pp_status peel_kcore_impl(uint32_t n, uint32_t r, uint32_t k, const uint3
     const int egrid = (int)(eb < (u64)sms * 16 ? (eb ? eb : 1) : (u64)sms * 16);
     const u64 vb = (nn + kKBlock * 4 - 1) / (kKBlock * 4);
     const int vgrid = (int)(vb < (u64)sms * 8 ? vb : (u64)sms * 8);
-    if ((e = cudaMemsetAsync(w.deg, 0, nn * 4, s)) != cudaSuccess ||
+    if ((e = cudaMemsetAsync(w.deg16, 0, ((nn + 1) / 2) * 4, s)) != cudaSuccess ||
+        (e = cudaMemsetAsync(w.ovf, 0, sizeof(u32), s)) != cudaSuccess ||
         (e = cudaMemsetAsync(w.alive, 0xff, ((mm + 31) / 32) * 4, s)) != cudaSuccess) {
       status = cuda_fail(e, "pp_peel_kcore memset", __FILE__, __LINE__);
       goto cleanup;
     }
     k_kinit<<<1, 32, 0, s>>>(w.ctl, n, m, k, o.max_rounds);
-    if (m) k_hist<<<egrid, kKBlock, 0, s>>>(d_edges, m, r, n, w.deg, d_edge_round, w.ctl);
+    // degrees in 16-bit counters, which the rounds then decrement in place;
+    // a degree above 0xFFFF sends the call to 32-bit counters
+    if (m) k_hist16<<<egrid, kKBlock, 0, s>>>(d_edges, m, r, n, w.deg16, d_edge_round, w.ovf, w.ctl);
+    uint32_t h_ovf = 0;
+    if ((e = cudaMemcpyAsync(&h_ovf, w.ovf, sizeof(u32), cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
+        (e = cudaStreamSynchronize(s)) != cudaSuccess) {
+      status = cuda_fail(e, "pp_peel_kcore degree readback", __FILE__, __LINE__);
+      goto cleanup;
+    }
+    const bool d16 = h_ovf == 0;
+    if (d16) {
+      if (n) k_unpack16<<<vgrid, kKBlock, 0, s>>>(w.deg16, n, w.deg);
+    } else {
+      if ((e = cudaMemsetAsync(w.deg, 0, nn * 4, s)) != cudaSuccess) {
+        status = cuda_fail(e, "pp_peel_kcore memset", __FILE__, __LINE__);
+        goto cleanup;
+      }
+      k_hist<<<egrid, kKBlock, 0, s>>>(d_edges, m, r, n, w.deg, d_edge_round, w.ctl);
+    }
     status = exclusive_scan(w.deg, w.off, n, w.scan_tmp, s);
     if (status != PP_OK) goto cleanup;
     if (n && (e = cudaMemcpyAsync(w.cursor, w.off, (size_t)n * 4, cudaMemcpyDeviceToDevice, s)) != cudaSuccess) {
@@ -781,28 +818,6 @@ static pp_status peel_kcore_impl(uint32_t n, uint32_t r, uint32_t k, const uint3
       status = cuda_fail(e, "pp_peel_kcore build kernels", __FILE__, __LINE__);
       goto cleanup;
     }
-    // 16-bit degrees for the rounds when every degree fits
-    {
-      uint32_t h_dmax = 0;
-      if ((e = cudaMemsetAsync(w.dmax, 0, sizeof(u32), s)) != cudaSuccess) {
-        status = cuda_fail(e, "pp_peel_kcore memset", __FILE__, __LINE__);
-        goto cleanup;
-      }
-      if (n) k_degmax<<<vgrid, kKBlock, 0, s>>>(w.deg, n, w.dmax);
-      if ((e = cudaMemcpyAsync(&h_dmax, w.dmax, sizeof(u32), cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
-          (e = cudaStreamSynchronize(s)) != cudaSuccess) {
-        status = cuda_fail(e, "pp_peel_kcore degree readback", __FILE__, __LINE__);
-        goto cleanup;
-      }
-      if (n && h_dmax < (1u << 16)) {
-        if ((e = ws_alloc((void **)&w.deg16, ((nn + 1) / 2) * 4, s)) != cudaSuccess) {
-          status = cuda_fail(e, "pp_peel_kcore workspace", __FILE__, __LINE__);
-          goto cleanup;
-        }
-        k_deg16<<<vgrid, kKBlock, 0, s>>>(w.deg, n, w.deg16);
-      }
-    }
-    const bool d16 = w.deg16 != nullptr;
     u32 *rdeg = d16 ? w.deg16 : w.deg;
     if (parts) {
       KSubPeelArgs pa{d_edges, r, n, w.off, w.inc, w.alive, rdeg, *parts, w.f0, d_vertex_round,
@@ -861,7 +876,7 @@ static pp_status peel_kcore_impl(uint32_t n, uint32_t r, uint32_t k, const uint3
 cleanup:
   cudaFreeAsync(w.deg, s);
   cudaFreeAsync(w.deg16, s);
-  cudaFreeAsync(w.dmax, s);
+  cudaFreeAsync(w.ovf, s);
   cudaFreeAsync(w.off, s);
   cudaFreeAsync(w.cursor, s);
   cudaFreeAsync(w.inc, s);

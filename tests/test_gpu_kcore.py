@@ -83,6 +83,29 @@ def test_host_loop_matches(pp):
     check(pp, 70000, 2, edges, opts=pp.options(ctas_per_sm=1))
 
 
+def _hub_edges(n, r, hub, hub_deg, seed):
+    """hub_deg edges through vertex `hub` plus filler edges; no other edge
+    touches vertices 0 and 1, so deg(hub) == hub_deg exactly."""
+    rng = np.random.default_rng(seed)
+    e = rng.integers(2, n, size=(hub_deg, r), dtype=np.uint64).astype(np.uint32)
+    e[:, 0] = hub
+    filler = (ppgen.uniform_edges(n - 2, r, 20000, seed).astype(np.uint64) + 2).astype(np.uint32)
+    return np.concatenate([e, filler])
+
+
+@pytest.mark.parametrize("hub", [0, 1], ids=["low-half", "high-half"])
+@pytest.mark.parametrize("hub_deg", [65535, 65536, 70001])
+def test_high_degree_vertex(pp, hub_deg, hub):
+    """Degrees are counted in the 16-bit halves of 32-bit words; a degree of
+    65536 or more carries out of its half and the call counts again in 32
+    bits.  Both sides of that boundary, for a vertex in either half."""
+    n, r = 50000, 3
+    edges = _hub_edges(n, r, hub, hub_deg, hub_deg + hub)
+    assert int((edges == hub).sum()) == hub_deg
+    for k in (2, 3):
+        check(pp, n, k, edges)
+
+
 def test_plain_peel_config(pp):
     cfg = ppgen.PLAIN_PEEL
     n, r, k = cfg["n"], cfg["r"], cfg["k"]

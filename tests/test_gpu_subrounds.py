@@ -129,6 +129,19 @@ def test_kcore_full_size_properties(pp):
         torch.cuda.empty_cache()
 
 
+@pytest.mark.parametrize("hub_deg", [65535, 65536])
+def test_kcore_high_degree_vertex(pp, hub_deg):
+    """A vertex of degree 65535 (16-bit counters) and 65536 (32-bit recount)."""
+    n, r = 50000, 3
+    rng = np.random.default_rng(hub_deg)
+    e = rng.integers(2, n, size=(hub_deg, r), dtype=np.uint64).astype(np.uint32)
+    e[:, 0] = 1
+    filler = (ppgen.uniform_edges(n - 2, r, 20000, 5).astype(np.uint64) + 2).astype(np.uint32)
+    edges = np.concatenate([e, filler])
+    assert int((edges == 1).sum()) == hub_deg
+    check_kcore(pp, n, 2, edges, _offsets(n, 3))
+
+
 def test_kcore_round_limit(pp):
     n, r = 20000, 4
     e = ppgen.partitioned_edges(n, r, ppgen.edges_from_c(0.7, n), 5)
