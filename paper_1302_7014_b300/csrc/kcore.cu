@@ -177,8 +177,64 @@ __global__ void __launch_bounds__(kKBlock) k_unpack16(const u32 *__restrict__ de
   }
 }
 
+// Removal of one frontier vertex v in round t (Sec. 1, step (B)): every edge
+// of v still alive is claimed through its alive bit (the first of its
+// vertices to get there removes it), its round is recorded, and the degrees
+// of its r endpoints are decremented; push(u) for each endpoint whose degree
+// falls from k to k - 1.  Up to four incidences are read and claimed at once,
+// and a claimed edge's row is read in one load (R = 4: 16 bytes, R = 2: 8
+// bytes; rows aligned to that) with its R decrements issued together.  R = 0:
+// any r, one endpoint at a time.  Returns the number of edges claimed.
+template <int R, bool D16, typename Push>
+__device__ __forceinline__ u32 remove_edges_of(u32 v, u32 t, const u32 *__restrict__ edges, u32 r, u32 n, u32 k,
+                                               const u32 *__restrict__ off, const u32 *__restrict__ inc,
+                                               u32 *__restrict__ alive, u32 *__restrict__ deg,
+                                               int *__restrict__ eround, Push push) {
+  u32 claimed = 0;
+  const u32 b = off[v], e_end = off[v + 1];
+  for (u32 p0 = b; p0 < e_end; p0 += 4) {
+    u32 ev[4], old[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) ev[q] = p0 + q < e_end ? inc[p0 + q] : 0xffffffffu;  // edge ids are < 2^31
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+      old[q] = ev[q] != 0xffffffffu ? atomicAnd(alive + (ev[q] >> 5), ~(1u << (ev[q] & 31u))) : 0u;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      if (ev[q] == 0xffffffffu || !((old[q] >> (ev[q] & 31u)) & 1u)) continue;  // taken by another vertex
+      const u32 e = ev[q];
+      ++claimed;
+      if (eround) eround[e] = (int)t;
+      if constexpr (R == 0) {
+        for (u32 h = 0; h < r; ++h) {
+          const u32 u = edges[(u64)e * r + h];
+          if (u < n && deg_dec<D16>(deg, u) == k) push(u);
+        }
+      } else {
+        u32 u[R], od[R];
+        if constexpr (R == 4) {
+          const uint4 w = reinterpret_cast<const uint4 *>(edges)[e];
+          u[0] = w.x, u[1] = w.y, u[2] = w.z, u[3] = w.w;
+        } else if constexpr (R == 2) {
+          const uint2 w = reinterpret_cast<const uint2 *>(edges)[e];
+          u[0] = w.x, u[1] = w.y;
+        } else {
+#pragma unroll
+          for (int h = 0; h < R; ++h) u[h] = edges[(u64)e * R + h];
+        }
+#pragma unroll
+        for (int h = 0; h < R; ++h) od[h] = u[h] < n ? deg_dec<D16>(deg, u[h]) : 0u;
+#pragma unroll
+        for (int h = 0; h < R; ++h)
+          if (u[h] < n && od[h] == k) push(u[h]);
+      }
+    }
+  }
+  return claimed;
+}
+
 // One round: remove F_t and its edges.
-template <bool D16>
+template <int R, bool D16>
 __global__ void __launch_bounds__(kKBlock) k_kpeel(const u32 *__restrict__ edges, u32 r, u32 n,
                                                    const u32 *__restrict__ off, const u32 *__restrict__ inc,
                                                    u32 *__restrict__ alive, u32 *__restrict__ deg,
@@ -199,27 +255,12 @@ __global__ void __launch_bounds__(kKBlock) k_kpeel(const u32 *__restrict__ edges
   for (u64 c0 = (u64)blockIdx.x * kKBlock; c0 < nf; c0 += (u64)gridDim.x * kKBlock) {
     const u64 i = c0 + threadIdx.x;
     if (i < nf) {
-      const u32 v = fin[i];
-      const u32 b = off[v], e_end = off[v + 1];
-      for (u32 p = b; p < e_end; ++p) {
-        const u32 e = inc[p];
-        const u32 bit = 1u << (e & 31u);
-        const u32 old = atomicAnd(alive + (e >> 5), ~bit);
-        if (!(old & bit)) continue;  // another vertex of this round took it
-        ++claimed;
-        if (eround) eround[e] = (int)t;
-        for (u32 j = 0; j < r; ++j) {
-          const u32 u = edges[(u64)e * r + j];
-          if (u >= n) continue;
-          const u32 od = deg_dec<D16>(deg, u);
-          if (od == k) {
-            if (vround) vround[u] = (int)t + 1;
-            const u32 q = atomicAdd(&s_n, 1u);
-            if (q < (u32)kKStage) s_buf[q] = u;
-            else fout[atomicAdd(&ctl->n_next, 1u)] = u;
-          }
-        }
-      }
+      claimed += remove_edges_of<R, D16>(fin[i], t, edges, r, n, k, off, inc, alive, deg, eround, [&](u32 u) {
+        if (vround) vround[u] = (int)t + 1;
+        const u32 q = atomicAdd(&s_n, 1u);
+        if (q < (u32)kKStage) s_buf[q] = u;
+        else fout[atomicAdd(&ctl->n_next, 1u)] = u;
+      });
     }
     __syncthreads();
     const u32 nn = min(s_n, (u32)kKStage);
@@ -382,7 +423,7 @@ __global__ void __launch_bounds__(kKBlock) k_kscan_sub(const u32 *__restrict__ d
 }
 
 // One sub-round: remove the frontier of the current part and its edges.
-template <bool D16>
+template <int R, bool D16>
 __global__ void __launch_bounds__(kKBlock) k_kpeel_sub(const u32 *__restrict__ edges, u32 r, u32 n,
                                                        const u32 *__restrict__ off, const u32 *__restrict__ inc,
                                                        u32 *__restrict__ alive, u32 *__restrict__ deg,
@@ -402,21 +443,8 @@ __global__ void __launch_bounds__(kKBlock) k_kpeel_sub(const u32 *__restrict__ e
     if (i < fe) {
       const u32 v = front[i];
       if (vround) vround[v] = (int)t;
-      const u32 b = off[v], e_end = off[v + 1];
-      for (u32 q = b; q < e_end; ++q) {
-        const u32 e = inc[q];
-        const u32 bit = 1u << (e & 31u);
-        const u32 old = atomicAnd(alive + (e >> 5), ~bit);
-        if (!(old & bit)) continue;  // another vertex of this sub-round took it
-        ++claimed;
-        if (eround) eround[e] = (int)t;
-        for (u32 h = 0; h < r; ++h) {
-          const u32 u = edges[(u64)e * r + h];
-          if (u >= n) continue;
-          const u32 od = deg_dec<D16>(deg, u);
-          if (od == k) stage_push(S, P, queue, ctl, u);
-        }
-      }
+      claimed += remove_edges_of<R, D16>(v, t, edges, r, n, k, off, inc, alive, deg, eround,
+                                         [&](u32 u) { stage_push(S, P, queue, ctl, u); });
     }
     stage_flush(S, P, queue, ctl);
   }
@@ -534,6 +562,22 @@ struct KSubEndArgs {
     memcpy(p, q, sizeof q);
   }
 };
+
+template <int R>
+const void *peel_kernel(bool sub, bool d16) {
+  if (sub) return d16 ? (const void *)k_kpeel_sub<R, true> : (const void *)k_kpeel_sub<R, false>;
+  return d16 ? (const void *)k_kpeel<R, true> : (const void *)k_kpeel<R, false>;
+}
+
+// round kernel for rank rk (2, 3, 4, or 0 = any) and the degree width
+const void *pick_peel(bool sub, int rk, bool d16) {
+  switch (rk) {
+    case 2: return peel_kernel<2>(sub, d16);
+    case 3: return peel_kernel<3>(sub, d16);
+    case 4: return peel_kernel<4>(sub, d16);
+    default: return peel_kernel<0>(sub, d16);
+  }
+}
 
 // The round loop: a CUDA graph whose while node runs peel -> round_end until
 // round_end clears the condition, or the same kernels driven from the host.
@@ -819,13 +863,16 @@ static pp_status peel_kcore_impl(uint32_t n, uint32_t r, uint32_t k, const uint3
       goto cleanup;
     }
     u32 *rdeg = d16 ? w.deg16 : w.deg;
+    // rank-specialised rounds where the edge rows allow their vector loads
+    const uintptr_t ea = (uintptr_t)d_edges;
+    const int rk = (r == 4 && ea % 16 == 0) || (r == 2 && ea % 8 == 0) || r == 3 ? (int)r : 0;
     if (parts) {
       KSubPeelArgs pa{d_edges, r, n, w.off, w.inc, w.alive, rdeg, *parts, w.f0, d_vertex_round,
                       d_edge_round, w.sub, {}};
       pa.bind();
       KSubEndArgs ea{w.sub, PeelStats{w.st_s, w.st_m}, *parts, 0, 0, {}};
       ea.bind();
-      const void *peel = d16 ? (const void *)k_kpeel_sub<true> : (const void *)k_kpeel_sub<false>;
+      const void *peel = pick_peel(true, rk, d16);
       const int pgrid = persistent_grid(peel, kKBlock, 0, o.ctas_per_sm);
       status = run_rounds(peel, pa.p, (const void *)k_kround_end_sub, ea, pgrid,
                           o.host_loop != 0, s, &w.sub->more);
@@ -835,7 +882,7 @@ static pp_status peel_kcore_impl(uint32_t n, uint32_t r, uint32_t k, const uint3
       pa.bind();
       KEndArgs ea{w.ctl, PeelStats{w.st_s, w.st_m}, 0, 0, {}};
       ea.bind();
-      const void *peel = d16 ? (const void *)k_kpeel<true> : (const void *)k_kpeel<false>;
+      const void *peel = pick_peel(false, rk, d16);
       const int pgrid = persistent_grid(peel, kKBlock, 0, o.ctas_per_sm);
       status = run_rounds(peel, pa.p, (const void *)k_kround_end, ea, pgrid,
                           o.host_loop != 0, s, &w.ctl->more);
