@@ -48,6 +48,7 @@ pp_options resolve_options(const pp_options *opt) {
     o.host_loop = opt->host_loop;
     if (opt->stats_rounds) o.stats_rounds = opt->stats_rounds;
     o.binned = opt->binned;
+    o.kcore_mode = opt->kcore_mode;
   }
   return o;
 }

@@ -10,6 +10,12 @@
 //           decrement that takes a degree from k to k-1 pushes that endpoint
 //           into F_{t+1} (its degree was >= k at the start of round t, and is
 //           < k at its end: exactly the vertices round t+1 removes).
+// While the frontier is large the full rounds run edge-centric instead
+// (k_eround): one pass over the edges still alive removes those with a vertex
+// in F_t (a bitmap), with the same decrements and pushes, and needs no
+// incidence lists.  Once the frontier is small against the edges left, the
+// lists are built for those edges only and the vertex-centric rounds finish.
+// Either way round t removes exactly the edges that touch F_t.
 //
 // Sub-round mode (App. B, pp_peel_kcore_subrounds): the vertices are split into
 // p parts and each round runs one sub-round per part; a sub-round removes the
@@ -36,6 +42,13 @@ namespace pp {
 
 constexpr int kKBlock = 256;
 constexpr int kKStage = 2048;  // staged pushes per CTA before spilling to global atomics
+// Edge-centric rounds run while the frontier holds at least 1 / kSwitchRatio
+// vertices per edge left: each such round removes a large share of the list.
+// Below that, a pass over every edge left costs more than the incidence lists
+// (their build included): measured at 2^25 vertices, r = 4, an edge-centric
+// round is latency-bound at about 0.7 TB/s on the list, four random bitmap
+// probes per edge.
+constexpr u32 kSwitchRatio = 2;
 
 struct PeelCtl {
   u64 claimed;  // edges removed in the current round
@@ -48,7 +61,13 @@ struct PeelCtl {
   u32 max_rounds;
   u32 more;
   u32 k;
-  u32 pad;
+  // edge-centric rounds
+  u32 src;       // edge list of the next round: 0 or 1 (compacted), 2 = the caller's array
+  u32 compact;   // the next round copies its surviving edges to the other list
+  u32 sw;        // hand the rounds over to the incidence lists
+  u32 econt;     // another edge-centric round follows
+  u32 len_next;  // survivors written by a compacting round
+  u64 len;       // entries in the list (removed ones included until it is compacted)
 };
 
 struct PeelStats {
@@ -64,6 +83,9 @@ __global__ void k_kinit(PeelCtl *ctl, u64 n, u64 m, u32 k, u32 max_rounds) {
     c.m = m;
     c.k = k;
     c.max_rounds = max_rounds;
+    c.src = 2;
+    c.compact = 1;
+    c.len = m;
     *ctl = c;
   }
 }
@@ -96,10 +118,11 @@ __global__ void __launch_bounds__(kKBlock) k_scatter(const u32 *__restrict__ edg
   }
 }
 
-// F_1 = {v : deg(v) < k}; writes every vertex's round (1 or 0).
+// F_1 = {v : deg(v) < k}; writes every vertex's round (1 or 0) and, if fb is
+// given, every word of the F_1 bitmap.
 __global__ void __launch_bounds__(kKBlock) k_kscan(const u32 *__restrict__ deg, u32 n,
                                                    u32 *__restrict__ f0, int *__restrict__ vround,
-                                                   PeelCtl *__restrict__ ctl) {
+                                                   u32 *__restrict__ fb, PeelCtl *__restrict__ ctl) {
   __shared__ u32 s_buf[kKBlock * 4];
   __shared__ u32 s_n, s_base;
   const u32 k = ctl->k;
@@ -113,6 +136,8 @@ __global__ void __launch_bounds__(kKBlock) k_kscan(const u32 *__restrict__ deg, 
       const bool valid = v < n;
       const bool low = valid && deg[v] < k;
       if (valid && vround) vround[v] = low ? 1 : 0;
+      const u32 ball = __ballot_sync(kFull, low);  // 32 consecutive vertices per warp
+      if (fb && lane_id() == 0 && v - lane_id() < n) fb[v >> 5] = ball;
       const u32 p = warp_reserve<u32>(low, &s_n);
       if (low) s_buf[p] = (u32)v;
     }
@@ -184,12 +209,13 @@ __global__ void __launch_bounds__(kKBlock) k_unpack16(const u32 *__restrict__ de
 // falls from k to k - 1.  Up to four incidences are read and claimed at once,
 // and a claimed edge's row is read in one load (R = 4: 16 bytes, R = 2: 8
 // bytes; rows aligned to that) with its R decrements issued together.  R = 0:
-// any r, one endpoint at a time.  Returns the number of edges claimed.
+// any r, one endpoint at a time.  eid (if given) maps a row to the caller's
+// edge id for the edge-round output.  Returns the number of edges claimed.
 template <int R, bool D16, typename Push>
 __device__ __forceinline__ u32 remove_edges_of(u32 v, u32 t, const u32 *__restrict__ edges, u32 r, u32 n, u32 k,
                                                const u32 *__restrict__ off, const u32 *__restrict__ inc,
                                                u32 *__restrict__ alive, u32 *__restrict__ deg,
-                                               int *__restrict__ eround, Push push) {
+                                               const u32 *__restrict__ eid, int *__restrict__ eround, Push push) {
   u32 claimed = 0;
   const u32 b = off[v], e_end = off[v + 1];
   for (u32 p0 = b; p0 < e_end; p0 += 4) {
@@ -204,7 +230,7 @@ __device__ __forceinline__ u32 remove_edges_of(u32 v, u32 t, const u32 *__restri
       if (ev[q] == 0xffffffffu || !((old[q] >> (ev[q] & 31u)) & 1u)) continue;  // taken by another vertex
       const u32 e = ev[q];
       ++claimed;
-      if (eround) eround[e] = (int)t;
+      if (eround) eround[eid ? eid[e] : e] = (int)t;
       if constexpr (R == 0) {
         for (u32 h = 0; h < r; ++h) {
           const u32 u = edges[(u64)e * r + h];
@@ -235,7 +261,8 @@ __device__ __forceinline__ u32 remove_edges_of(u32 v, u32 t, const u32 *__restri
 
 // One round: remove F_t and its edges.
 template <int R, bool D16>
-__global__ void __launch_bounds__(kKBlock) k_kpeel(const u32 *__restrict__ edges, u32 r, u32 n,
+__global__ void __launch_bounds__(kKBlock) k_kpeel(const u32 *__restrict__ edges, const u32 *__restrict__ eid,
+                                                   u32 r, u32 n,
                                                    const u32 *__restrict__ off, const u32 *__restrict__ inc,
                                                    u32 *__restrict__ alive, u32 *__restrict__ deg,
                                                    u32 *__restrict__ f0, u32 *__restrict__ f1,
@@ -255,7 +282,7 @@ __global__ void __launch_bounds__(kKBlock) k_kpeel(const u32 *__restrict__ edges
   for (u64 c0 = (u64)blockIdx.x * kKBlock; c0 < nf; c0 += (u64)gridDim.x * kKBlock) {
     const u64 i = c0 + threadIdx.x;
     if (i < nf) {
-      claimed += remove_edges_of<R, D16>(fin[i], t, edges, r, n, k, off, inc, alive, deg, eround, [&](u32 u) {
+      claimed += remove_edges_of<R, D16>(fin[i], t, edges, r, n, k, off, inc, alive, deg, eid, eround, [&](u32 u) {
         if (vround) vround[u] = (int)t + 1;
         const u32 q = atomicAdd(&s_n, 1u);
         if (q < (u32)kKStage) s_buf[q] = u;
@@ -297,6 +324,208 @@ __global__ void k_kround_end(PeelCtl *__restrict__ ctl, PeelStats st, int set_co
   if (more) c.round = t + 1;
   c.more = more;
   if (set_cond) cudaGraphSetConditional(cond, more);
+}
+
+// ---- edge-centric full rounds ------------------------------------------------
+constexpr u32 kDead = 0xffffffffu;  // id of a list entry whose edge was removed in place
+constexpr int kEItems = 4;          // list entries per thread per step
+
+// The edge list of the edge-centric rounds: the caller's array at first (ids
+// = positions), then two compacted copies (rows of r vertex ids + the
+// caller's edge id of each row).  F_t is bitmap fb[t & 1] and list
+// f[(t - 1) & 1], the same list convention as k_kpeel.
+struct EdgeLists {
+  const u32 *user;
+  u32 *rows[2], *ids[2];
+  u32 *fb[2];
+  u32 *f[2];
+};
+
+template <int R>
+__device__ __forceinline__ void load_row(const u32 *rows, u64 i, u32 (&u)[R]) {
+  if constexpr (R == 4) {
+    const uint4 w = __ldcs(reinterpret_cast<const uint4 *>(rows) + i);
+    u[0] = w.x, u[1] = w.y, u[2] = w.z, u[3] = w.w;
+  } else if constexpr (R == 2) {
+    const uint2 w = __ldcs(reinterpret_cast<const uint2 *>(rows) + i);
+    u[0] = w.x, u[1] = w.y;
+  } else {
+#pragma unroll
+    for (int h = 0; h < R; ++h) u[h] = __ldcs(rows + i * R + h);
+  }
+}
+
+template <int R>
+__device__ __forceinline__ void store_row(u32 *rows, u64 i, const u32 (&u)[R]) {
+  if constexpr (R == 4) {
+    reinterpret_cast<uint4 *>(rows)[i] = make_uint4(u[0], u[1], u[2], u[3]);
+  } else if constexpr (R == 2) {
+    reinterpret_cast<uint2 *>(rows)[i] = make_uint2(u[0], u[1]);
+  } else {
+#pragma unroll
+    for (int h = 0; h < R; ++h) rows[i * R + h] = u[h];
+  }
+}
+
+// Round t, edge-centric: every listed edge with a vertex in F_t is removed --
+// round recorded, one degree taken from each endpoint (with multiplicity), an
+// endpoint whose degree falls from k to k - 1 pushed into F_{t+1} (bitmap,
+// list, vertex round t + 1).  A compacting round copies the surviving edges to
+// the other list; otherwise a removed edge's entry is marked dead in place.
+// Entries are read kEItems per thread at once: ids, rows, then the frontier
+// bits of every endpoint, so the loads of a step are all in flight together.
+template <int R, bool D16>
+__global__ void __launch_bounds__(kKBlock) k_eround(EdgeLists L, u32 n, u32 *__restrict__ deg,
+                                                    int *__restrict__ vround, int *__restrict__ eround,
+                                                    PeelCtl *__restrict__ ctl) {
+  __shared__ u32 s_buf[kKStage];
+  __shared__ u32 s_n, s_base;
+  __shared__ u64 s_red[kKBlock / 32];
+  const u32 t = *(volatile u32 *)&ctl->round;
+  const u32 nf = *(volatile u32 *)&ctl->n_front;
+  if (nf == 0) return;  // the iteration that only promotes F_1 (uniform)
+  const u32 k = ctl->k;
+  const u32 src = ctl->src;
+  const u64 len = ctl->len;
+  const bool compact = ctl->compact != 0;
+  const u32 *srows = src == 2 ? L.user : L.rows[src];
+  u32 *sids = src == 2 ? nullptr : L.ids[src];
+  const u32 d = src == 0 ? 1u : 0u;
+  u32 *drows = L.rows[d], *dids = L.ids[d];
+  const u32 *ft = L.fb[t & 1u];
+  u32 *fn = L.fb[(t + 1) & 1u];
+  u32 *fout = L.f[t & 1u];
+  u64 claimed = 0;
+  if (threadIdx.x == 0) s_n = 0;
+  __syncthreads();
+  auto push = [&](u32 v) {
+    if (vround) vround[v] = (int)t + 1;
+    atomicOr(fn + (v >> 5), 1u << (v & 31u));
+    const u32 q = atomicAdd(&s_n, 1u);
+    if (q < (u32)kKStage) s_buf[q] = v;
+    else fout[atomicAdd(&ctl->n_next, 1u)] = v;
+  };
+  constexpr u32 CH = kKBlock * kEItems;
+  for (u64 c0 = (u64)blockIdx.x * CH; c0 < len; c0 += (u64)gridDim.x * CH) {
+    u32 id[kEItems], u[kEItems][R], w[kEItems][R];
+#pragma unroll
+    for (int it = 0; it < kEItems; ++it) {
+      const u64 i = c0 + (u64)it * kKBlock + threadIdx.x;
+      id[it] = i < len ? (sids ? __ldcs(sids + i) : (u32)i) : kDead;
+    }
+#pragma unroll
+    for (int it = 0; it < kEItems; ++it) {
+      if (id[it] != kDead) {
+        load_row<R>(srows, c0 + (u64)it * kKBlock + threadIdx.x, u[it]);
+      } else {
+#pragma unroll
+        for (int h = 0; h < R; ++h) u[it][h] = kDead;
+      }
+    }
+#pragma unroll
+    for (int it = 0; it < kEItems; ++it)
+#pragma unroll
+      for (int h = 0; h < R; ++h) w[it][h] = u[it][h] < n ? __ldcg(ft + (u[it][h] >> 5)) : 0u;
+#pragma unroll
+    for (int it = 0; it < kEItems; ++it) {
+      bool hit = false;
+#pragma unroll
+      for (int h = 0; h < R; ++h) hit |= u[it][h] < n && ((w[it][h] >> (u[it][h] & 31u)) & 1u);
+      if (hit) {
+        ++claimed;
+        if (eround) eround[id[it]] = (int)t;
+        u32 od[R];
+#pragma unroll
+        for (int h = 0; h < R; ++h) od[h] = u[it][h] < n ? deg_dec<D16>(deg, u[it][h]) : 0u;
+#pragma unroll
+        for (int h = 0; h < R; ++h)
+          if (u[it][h] < n && od[h] == k) push(u[it][h]);
+        if (!compact) sids[c0 + (u64)it * kKBlock + threadIdx.x] = kDead;  // src != 2 here
+      }
+      const bool keep = compact && id[it] != kDead && !hit;
+      const u32 pos = warp_reserve<u32>(keep, &ctl->len_next);
+      if (keep) {
+        store_row<R>(drows, pos, u[it]);
+        dids[pos] = id[it];
+      }
+    }
+    __syncthreads();
+    const u32 nn = min(s_n, (u32)kKStage);
+    if (threadIdx.x == 0 && nn) s_base = atomicAdd(&ctl->n_next, nn);
+    __syncthreads();
+    for (u32 q = threadIdx.x; q < nn; q += kKBlock) fout[s_base + q] = s_buf[q];
+    __syncthreads();
+    if (threadIdx.x == 0) s_n = 0;
+    __syncthreads();
+  }
+  const u64 c = block_sum<u64, kKBlock>(claimed, s_red);
+  if (threadIdx.x == 0 && c) atomicAdd(&ctl->claimed, c);
+}
+
+// After round t's pass: F_t leaves its bitmap (which holds F_{t+2} next).
+__global__ void __launch_bounds__(kKBlock) k_eclear(EdgeLists L, const PeelCtl *__restrict__ ctl) {
+  const u32 t = *(volatile const u32 *)&ctl->round;
+  const u32 nf = *(volatile const u32 *)&ctl->n_front;
+  if (t == 0) return;
+  const u32 *fin = L.f[(t - 1) & 1u];
+  u32 *fb = L.fb[t & 1u];
+  for (u32 i = blockIdx.x * blockDim.x + threadIdx.x; i < nf; i += gridDim.x * blockDim.x) fb[fin[i] >> 5] = 0;
+}
+
+// End of an edge-centric round: the statistics and promotion of k_kround_end,
+// then the list (switch to the compacted copy), whether the next round
+// compacts (half of the list is dead, or it is still the caller's array), and
+// whether the incidence-list rounds take over: F_{t+1} holds fewer than
+// 1 / sw_ratio vertices per edge left (sw_ratio = 0: never).
+__global__ void k_eround_end(PeelCtl *__restrict__ ctl, PeelStats st, u32 sw_ratio, int set_cond,
+                             cudaGraphConditionalHandle cond) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  PeelCtl &c = *ctl;
+  const u32 t = c.round;
+  if (c.n_front > 0 && t > 0) {
+    c.s -= c.n_front;
+    c.m -= c.claimed;
+    st.s[t - 1] = c.s;
+    st.m[t - 1] = c.m;
+    if (c.compact) {
+      c.src = c.src == 0 ? 1u : 0u;
+      c.len = c.len_next;
+    }
+  }
+  c.len_next = 0;
+  c.claimed = 0;
+  c.n_front = c.n_next;
+  c.n_next = 0;
+  u32 more = c.n_front > 0;
+  if (more && t >= c.max_rounds) {
+    c.flags |= FLAG_ROUND_LIMIT;
+    more = 0;
+  }
+  if (more) c.round = t + 1;
+  c.compact = c.src == 2 || c.m * 2 <= c.len;
+  c.sw = more && sw_ratio && (u64)c.n_front * sw_ratio < c.m;
+  c.more = more;
+  c.econt = more && !c.sw;
+  if (set_cond) cudaGraphSetConditional(cond, c.econt);
+}
+
+// Before the hand-over: the live entries of list `from` (len entries) copied
+// to the other list.
+template <int R>
+__global__ void __launch_bounds__(kKBlock) k_ecompact(EdgeLists L, u32 from, u64 len, PeelCtl *__restrict__ ctl) {
+  const u32 *srows = L.rows[from], *sids = L.ids[from];
+  u32 *drows = L.rows[from ^ 1u], *dids = L.ids[from ^ 1u];
+  for (u64 c0 = (u64)blockIdx.x * kKBlock; c0 < len; c0 += (u64)gridDim.x * kKBlock) {
+    const u64 i = c0 + threadIdx.x;
+    const u32 id = i < len ? sids[i] : kDead;
+    u32 u[R];
+    if (id != kDead) load_row<R>(srows, i, u);
+    const u32 pos = warp_reserve<u32>(id != kDead, &ctl->len_next);
+    if (id != kDead) {
+      store_row<R>(drows, pos, u);
+      dids[pos] = id;
+    }
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -443,7 +672,7 @@ __global__ void __launch_bounds__(kKBlock) k_kpeel_sub(const u32 *__restrict__ e
     if (i < fe) {
       const u32 v = front[i];
       if (vround) vround[v] = (int)t;
-      claimed += remove_edges_of<R, D16>(v, t, edges, r, n, k, off, inc, alive, deg, eround,
+      claimed += remove_edges_of<R, D16>(v, t, edges, r, n, k, off, inc, alive, deg, nullptr, eround,
                                          [&](u32 u) { stage_push(S, P, queue, ctl, u); });
     }
     stage_flush(S, P, queue, ctl);
@@ -502,6 +731,7 @@ struct KWork {
   u32 *deg = nullptr, *off = nullptr, *cursor = nullptr, *inc = nullptr, *alive = nullptr;
   u32 *f0 = nullptr, *f1 = nullptr;
   u32 *deg16 = nullptr, *ovf = nullptr;
+  u32 *rows[2] = {nullptr, nullptr}, *ids[2] = {nullptr, nullptr}, *fb[2] = {nullptr, nullptr};
   PeelCtl *ctl = nullptr;
   SubCtl *sub = nullptr;
   u64 *st_s = nullptr, *st_m = nullptr;
@@ -509,18 +739,62 @@ struct KWork {
 };
 
 struct KPeelArgs {
-  const u32 *edges;
+  const u32 *edges, *eid;
   u32 r, n;
   const u32 *off, *inc;
   u32 *alive, *deg, *f0, *f1;
   int *vround, *eround;
   PeelCtl *ctl;
-  void *p[12];
+  void *p[13];
   void bind() {
-    void *q[12] = {&edges, &r, &n, &off, &inc, &alive, &deg, &f0, &f1, &vround, &eround, &ctl};
+    void *q[13] = {&edges, &eid, &r, &n, &off, &inc, &alive, &deg, &f0, &f1, &vround, &eround, &ctl};
     memcpy(p, q, sizeof q);
   }
 };
+
+struct KEdgeArgs {
+  EdgeLists L;
+  u32 n;
+  u32 *deg;
+  int *vround, *eround;
+  PeelCtl *ctl;
+  void *p[6], *pc[2];
+  void bind() {
+    void *q[6] = {&L, &n, &deg, &vround, &eround, &ctl};
+    void *qc[2] = {&L, &ctl};
+    memcpy(p, q, sizeof q);
+    memcpy(pc, qc, sizeof qc);
+  }
+};
+
+struct KEEndArgs {
+  PeelCtl *ctl;
+  PeelStats st;
+  u32 sw_ratio;
+  int set_cond;
+  cudaGraphConditionalHandle cond;
+  void *p[5];
+  void bind() {
+    void *q[5] = {&ctl, &st, &sw_ratio, &set_cond, &cond};
+    memcpy(p, q, sizeof q);
+  }
+};
+
+const void *pick_eround(int rk, bool d16) {
+  switch (rk) {
+    case 2: return d16 ? (const void *)k_eround<2, true> : (const void *)k_eround<2, false>;
+    case 3: return d16 ? (const void *)k_eround<3, true> : (const void *)k_eround<3, false>;
+    default: return d16 ? (const void *)k_eround<4, true> : (const void *)k_eround<4, false>;
+  }
+}
+
+const void *pick_ecompact(int rk) {
+  switch (rk) {
+    case 2: return (const void *)k_ecompact<2>;
+    case 3: return (const void *)k_ecompact<3>;
+    default: return (const void *)k_ecompact<4>;
+  }
+}
 
 struct KEndArgs {
   PeelCtl *ctl;
@@ -583,11 +857,13 @@ const void *pick_peel(bool sub, int rk, bool d16) {
 // round_end clears the condition, or the same kernels driven from the host.
 template <class EndArgs>
 pp_status run_rounds(const void *peel_fn, void **peel_p, const void *end_fn, EndArgs &ea, int grid,
-                     bool host_loop, cudaStream_t s, const u32 *d_more) {
+                     bool host_loop, cudaStream_t s, const u32 *d_more, const void *mid_fn = nullptr,
+                     void **mid_p = nullptr, int mid_grid = 0) {
   if (host_loop) {
     u32 more = 0;
     for (;;) {
       PP_CUDA(cudaLaunchKernel(peel_fn, dim3(grid), dim3(kKBlock), peel_p, 0, s));
+      if (mid_fn) PP_CUDA(cudaLaunchKernel(mid_fn, dim3(mid_grid), dim3(kKBlock), mid_p, 0, s));
       PP_CUDA(cudaLaunchKernel(end_fn, dim3(1), dim3(32), ea.p, 0, s));
       PP_CUDA(cudaMemcpyAsync(&more, d_more, sizeof more, cudaMemcpyDeviceToHost, s));
       PP_CUDA(cudaStreamSynchronize(s));
@@ -599,7 +875,7 @@ pp_status run_rounds(const void *peel_fn, void **peel_p, const void *end_fn, End
   cudaGraphExec_t exec = nullptr;
   cudaGraphConditionalHandle h;
   cudaGraphNodeParams cp{};
-  cudaGraphNode_t n_cond, n_peel, n_end;
+  cudaGraphNode_t n_cond, n_peel, n_mid, n_end;
   cudaKernelNodeParams kp{};
   pp_status st = PP_OK;
   PP_CUDA(cudaGraphCreate(&g, 0));
@@ -627,11 +903,21 @@ pp_status run_rounds(const void *peel_fn, void **peel_p, const void *end_fn, End
     st = fail(PP_ERR_CUDA, "cudaGraphAddKernelNode(peel) failed");
     goto done;
   }
+  if (mid_fn) {
+    kp.func = (void *)mid_fn;
+    kp.gridDim = dim3(mid_grid);
+    kp.blockDim = dim3(kKBlock);
+    kp.kernelParams = mid_p;
+    if (cudaGraphAddKernelNode(&n_mid, body, &n_peel, 1, &kp) != cudaSuccess) {
+      st = fail(PP_ERR_CUDA, "cudaGraphAddKernelNode(round middle) failed");
+      goto done;
+    }
+  }
   kp.func = (void *)end_fn;
   kp.gridDim = dim3(1);
   kp.blockDim = dim3(32);
   kp.kernelParams = ea.p;
-  if (cudaGraphAddKernelNode(&n_end, body, &n_peel, 1, &kp) != cudaSuccess) {
+  if (cudaGraphAddKernelNode(&n_end, body, mid_fn ? &n_mid : &n_peel, 1, &kp) != cudaSuccess) {
     st = fail(PP_ERR_CUDA, "cudaGraphAddKernelNode(round_end) failed");
     goto done;
   }
@@ -842,50 +1128,132 @@ static pp_status peel_kcore_impl(uint32_t n, uint32_t r, uint32_t k, const uint3
       }
       k_hist<<<egrid, kKBlock, 0, s>>>(d_edges, m, r, n, w.deg, d_edge_round, w.ctl);
     }
-    status = exclusive_scan(w.deg, w.off, n, w.scan_tmp, s);
-    if (status != PP_OK) goto cleanup;
-    if (n && (e = cudaMemcpyAsync(w.cursor, w.off, (size_t)n * 4, cudaMemcpyDeviceToDevice, s)) != cudaSuccess) {
-      status = cuda_fail(e, "pp_peel_kcore cursor copy", __FILE__, __LINE__);
-      goto cleanup;
-    }
-    if (m) {
-      status = scatter_incidences(d_edges, m, r, n, w.cursor, w.inc, egrid, s);
-      if (status != PP_OK) goto cleanup;
+    // rank-specialised rounds where the edge rows allow their vector loads
+    const uintptr_t ea = (uintptr_t)d_edges;
+    const int rk = (r == 4 && ea % 16 == 0) || (r == 2 && ea % 8 == 0) || r == 3 ? (int)r : 0;
+    // edge-centric rounds are possible; they start if F_1 is large (or mode 2)
+    const bool edge_ok = !parts && o.kcore_mode != 1 && rk != 0 && m > 0 && n > 0;
+    bool edge_mode = false;
+    u32 *rdeg = d16 ? w.deg16 : w.deg;
+    // incidence lists of edges[0, me) (row i = edge i), from the current degrees
+    auto build_csr = [&](const u32 *edges, uint64_t me) -> pp_status {
+      pp_status st = exclusive_scan(w.deg, w.off, n, w.scan_tmp, s);
+      if (st != PP_OK) return st;
+      if (n && (e = cudaMemcpyAsync(w.cursor, w.off, (size_t)n * 4, cudaMemcpyDeviceToDevice, s)) != cudaSuccess)
+        return cuda_fail(e, "pp_peel_kcore cursor copy", __FILE__, __LINE__);
+      if (me) return scatter_incidences(edges, me, r, n, w.cursor, w.inc, egrid, s);
+      return PP_OK;
+    };
+    // vertex-centric rounds over edges[0, me), eid mapping rows to the caller's edge ids
+    auto vertex_rounds = [&](const u32 *edges, const u32 *eid, uint64_t me) -> pp_status {
+      if ((e = cudaMemsetAsync(w.alive, 0xff, ((me + 31) / 32 ? (me + 31) / 32 : 1) * 4, s)) != cudaSuccess)
+        return cuda_fail(e, "pp_peel_kcore memset", __FILE__, __LINE__);
+      KPeelArgs pa{edges, eid, r, n, w.off, w.inc, w.alive, rdeg, w.f0, w.f1, d_vertex_round, d_edge_round,
+                   w.ctl, {}};
+      pa.bind();
+      KEndArgs kea{w.ctl, PeelStats{w.st_s, w.st_m}, 0, 0, {}};
+      kea.bind();
+      const void *peel = pick_peel(false, rk, d16);
+      const int pgrid = persistent_grid(peel, kKBlock, 0, o.ctas_per_sm);
+      return run_rounds(peel, pa.p, (const void *)k_kround_end, kea, pgrid, o.host_loop != 0, s, &w.ctl->more);
+    };
+    if (edge_ok) {
+      const uint64_t words = ((uint64_t)nn + 31) / 32;
+      for (int b = 0; b < 2 && e == cudaSuccess; ++b) e = ws_alloc((void **)&w.fb[b], words * 4, s);
+      if (e == cudaSuccess) e = cudaMemsetAsync(w.fb[0], 0, words * 4, s);  // k_kscan writes fb[1]
+      if (e != cudaSuccess) {
+        status = cuda_fail(e, "pp_peel_kcore frontier bitmaps", __FILE__, __LINE__);
+        goto cleanup;
+      }
     }
     if (parts) {
       k_kinit_sub<<<1, 32, 0, s>>>(w.sub, n, m, k, o.max_rounds, parts->p);
       if (n) k_kscan_sub<<<vgrid, kKBlock, 0, s>>>(w.deg, n, *parts, w.f0, d_vertex_round, w.sub);
     } else if (n) {
-      k_kscan<<<vgrid, kKBlock, 0, s>>>(w.deg, n, w.f0, d_vertex_round, w.ctl);
+      k_kscan<<<vgrid, kKBlock, 0, s>>>(w.deg, n, w.f0, d_vertex_round, edge_ok ? w.fb[1] : nullptr, w.ctl);
     }
     if ((e = cudaGetLastError()) != cudaSuccess) {
       status = cuda_fail(e, "pp_peel_kcore build kernels", __FILE__, __LINE__);
       goto cleanup;
     }
-    u32 *rdeg = d16 ? w.deg16 : w.deg;
-    // rank-specialised rounds where the edge rows allow their vector loads
-    const uintptr_t ea = (uintptr_t)d_edges;
-    const int rk = (r == 4 && ea % 16 == 0) || (r == 2 && ea % 8 == 0) || r == 3 ? (int)r : 0;
+    if (edge_ok) {
+      if ((e = cudaMemcpyAsync(&hc, w.ctl, sizeof hc, cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
+          (e = cudaStreamSynchronize(s)) != cudaSuccess) {
+        status = cuda_fail(e, "pp_peel_kcore frontier readback", __FILE__, __LINE__);
+        goto cleanup;
+      }
+      edge_mode = o.kcore_mode == 2 || (uint64_t)hc.n_next * kSwitchRatio >= m;
+    }
+    if (edge_mode) {
+      for (int b = 0; b < 2 && e == cudaSuccess; ++b) {
+        e = ws_alloc((void **)&w.rows[b], mm * r * 4, s);
+        if (e == cudaSuccess) e = ws_alloc((void **)&w.ids[b], mm * 4, s);
+      }
+      if (e != cudaSuccess) {
+        status = cuda_fail(e, "pp_peel_kcore edge lists", __FILE__, __LINE__);
+        goto cleanup;
+      }
+    } else {
+      status = build_csr(d_edges, m);
+      if (status != PP_OK) goto cleanup;
+    }
     if (parts) {
       KSubPeelArgs pa{d_edges, r, n, w.off, w.inc, w.alive, rdeg, *parts, w.f0, d_vertex_round,
                       d_edge_round, w.sub, {}};
       pa.bind();
-      KSubEndArgs ea{w.sub, PeelStats{w.st_s, w.st_m}, *parts, 0, 0, {}};
-      ea.bind();
+      KSubEndArgs kea{w.sub, PeelStats{w.st_s, w.st_m}, *parts, 0, 0, {}};
+      kea.bind();
       const void *peel = pick_peel(true, rk, d16);
       const int pgrid = persistent_grid(peel, kKBlock, 0, o.ctas_per_sm);
-      status = run_rounds(peel, pa.p, (const void *)k_kround_end_sub, ea, pgrid,
+      status = run_rounds(peel, pa.p, (const void *)k_kround_end_sub, kea, pgrid,
                           o.host_loop != 0, s, &w.sub->more);
+    } else if (!edge_mode) {
+      status = vertex_rounds(d_edges, nullptr, m);
     } else {
-      KPeelArgs pa{d_edges, r, n, w.off, w.inc, w.alive, rdeg, w.f0, w.f1, d_vertex_round, d_edge_round,
-                   w.ctl, {}};
-      pa.bind();
-      KEndArgs ea{w.ctl, PeelStats{w.st_s, w.st_m}, 0, 0, {}};
-      ea.bind();
-      const void *peel = pick_peel(false, rk, d16);
-      const int pgrid = persistent_grid(peel, kKBlock, 0, o.ctas_per_sm);
-      status = run_rounds(peel, pa.p, (const void *)k_kround_end, ea, pgrid,
-                          o.host_loop != 0, s, &w.ctl->more);
+      // edge-centric rounds while the frontier is large
+      EdgeLists L{d_edges, {w.rows[0], w.rows[1]}, {w.ids[0], w.ids[1]}, {w.fb[0], w.fb[1]}, {w.f0, w.f1}};
+      KEdgeArgs ka{L, n, rdeg, d_vertex_round, d_edge_round, w.ctl, {}, {}};
+      ka.bind();
+      KEEndArgs kea{w.ctl, PeelStats{w.st_s, w.st_m}, o.kcore_mode == 2 ? 0u : kSwitchRatio, 0, 0, {}};
+      kea.bind();
+      const void *er = pick_eround(rk, d16);
+      const int pgrid = persistent_grid(er, kKBlock, 0, o.ctas_per_sm);
+      const int cgrid = persistent_grid((const void *)k_eclear, kKBlock, 0, o.ctas_per_sm);
+      status = run_rounds(er, ka.p, (const void *)k_eround_end, kea, pgrid, o.host_loop != 0, s, &w.ctl->econt,
+                          (const void *)k_eclear, ka.pc, cgrid);
+      if (status != PP_OK) goto cleanup;
+      if ((e = cudaMemcpyAsync(&hc, w.ctl, sizeof hc, cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
+          (e = cudaStreamSynchronize(s)) != cudaSuccess) {
+        status = cuda_fail(e, "pp_peel_kcore readback", __FILE__, __LINE__);
+        goto cleanup;
+      }
+      if (hc.more && hc.sw) {
+        // hand-over: incidence lists for the edges left, vertex-centric rounds
+        const u32 *edges = d_edges, *eid = nullptr;
+        uint64_t me = m;
+        if (hc.src != 2) {
+          u32 cur = hc.src;
+          if (hc.len > hc.m) {  // entries removed in place: copy the live ones
+            const int g = (int)((hc.len + kKBlock - 1) / kKBlock < (uint64_t)sm_count() * 8
+                                    ? (hc.len + kKBlock - 1) / kKBlock : (uint64_t)sm_count() * 8);
+            u32 from = cur;
+            u64 len = hc.len;
+            PeelCtl *ctl = w.ctl;
+            void *cp[4] = {&L, &from, &len, &ctl};
+            if ((e = cudaLaunchKernel(pick_ecompact(rk), dim3(g), dim3(kKBlock), cp, 0, s)) != cudaSuccess) {
+              status = cuda_fail(e, "pp_peel_kcore list compaction", __FILE__, __LINE__);
+              goto cleanup;
+            }
+            cur ^= 1u;
+          }
+          edges = w.rows[cur];
+          eid = w.ids[cur];
+          me = hc.m;
+        }
+        if (d16 && n) k_unpack16<<<vgrid, kKBlock, 0, s>>>(w.deg16, n, w.deg);
+        status = build_csr(edges, me);
+        if (status == PP_OK) status = vertex_rounds(edges, eid, me);
+      }
     }
     if (status != PP_OK) goto cleanup;
     if ((e = cudaMemcpyAsync(&hc, w.ctl, sizeof hc, cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
@@ -921,20 +1289,28 @@ static pp_status peel_kcore_impl(uint32_t n, uint32_t r, uint32_t k, const uint3
       status = fail(PP_ERR_ROUND_LIMIT, "pp_peel_kcore: stopped after max_rounds=%u (sub-)rounds", o.max_rounds);
   }
 cleanup:
-  cudaFreeAsync(w.deg, s);
-  cudaFreeAsync(w.deg16, s);
-  cudaFreeAsync(w.ovf, s);
-  cudaFreeAsync(w.off, s);
-  cudaFreeAsync(w.cursor, s);
-  cudaFreeAsync(w.inc, s);
-  cudaFreeAsync(w.alive, s);
-  cudaFreeAsync(w.f0, s);
-  cudaFreeAsync(w.f1, s);
-  cudaFreeAsync(w.ctl, s);
-  cudaFreeAsync(w.sub, s);
-  cudaFreeAsync(w.st_s, s);
-  cudaFreeAsync(w.st_m, s);
-  cudaFreeAsync(w.scan_tmp, s);
+  auto fr = [&](void *p) {
+    if (p) cudaFreeAsync(p, s);
+  };
+  fr(w.deg);
+  fr(w.deg16);
+  fr(w.ovf);
+  for (int b = 0; b < 2; ++b) {
+    fr(w.rows[b]);
+    fr(w.ids[b]);
+    fr(w.fb[b]);
+  }
+  fr(w.off);
+  fr(w.cursor);
+  fr(w.inc);
+  fr(w.alive);
+  fr(w.f0);
+  fr(w.f1);
+  fr(w.ctl);
+  fr(w.sub);
+  fr(w.st_s);
+  fr(w.st_m);
+  fr(w.scan_tmp);
   cudaStreamSynchronize(s);
   return status;
 }

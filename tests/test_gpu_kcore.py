@@ -106,6 +106,80 @@ def test_high_degree_vertex(pp, hub_deg, hub):
         check(pp, n, k, edges)
 
 
+MODES = [0, 1, 2]  # auto (edge-centric, then incidence lists), incidence lists only, edge-centric only
+
+
+@pytest.mark.parametrize("mode", MODES, ids=["auto", "lists", "edges"])
+def test_round_modes_random(pp, mode):
+    """Every way of running the full rounds gives the oracle's rounds exactly."""
+    rng = np.random.default_rng(77 + mode)
+    for trial in range(30):
+        n = int(rng.integers(2, 5000))
+        r = int(rng.choice([2, 3, 4]))
+        k = int(rng.choice([1, 2, 3]))
+        c = float(rng.uniform(0.2, 1.8))
+        edges = ppgen.uniform_edges(n, r, int(c * n), 3100 + trial)
+        check(pp, n, k, edges, opts=pp.options(kcore_mode=mode))
+
+
+@pytest.mark.parametrize("mode", MODES, ids=["auto", "lists", "edges"])
+@pytest.mark.parametrize("c", [0.70, 0.76, 0.78, 0.85])
+def test_round_modes_density_sweep(pp, mode, c):
+    """The density sweep's recipe at 2^20 vertices: below the threshold the
+    core is empty after many rounds, above it most edges stay; the automatic
+    mode hands over to incidence lists part way (with or without removed
+    entries still in the edge list)."""
+    cfg = ppgen.DENSITY_SWEEP
+    n, r, k = 1 << 20, cfg["r"], cfg["k"]
+    edges = ppgen.partitioned_edges(n, r, ppgen.edges_from_c(c, n), cfg["seed"])
+    check(pp, n, k, edges, opts=pp.options(kcore_mode=mode))
+    if mode == 0:
+        check(pp, n, k, edges, opts=pp.options(kcore_mode=mode, host_loop=1))
+
+
+@pytest.mark.parametrize("dense_c,seed", [(0.85, 1), (0.9, 2), (1.0, 3), (1.3, 4)])
+def test_round_modes_mixed_density(pp, dense_c, seed):
+    """A sparse part (most vertices go in round 1, so the automatic mode starts
+    edge-centric) joined to a dense part that leaves a slowly peeling core (so
+    it hands over to incidence lists part way, with the edge list compacted or
+    holding removed entries, depending on the rounds before)."""
+    n1, n2, r = 150000, 50000, 3
+    sparse = ppgen.uniform_edges(n1, r, int(0.3 * n1), 40 + seed)
+    dense = (ppgen.uniform_edges(n2, r, int(dense_c * n2), 50 + seed).astype(np.uint64) + n1).astype(np.uint32)
+    edges = np.concatenate([sparse, dense])
+    edges = edges[np.random.default_rng(seed).permutation(edges.shape[0])]
+    for mode in MODES:
+        check(pp, n1 + n2, 2, edges, opts=pp.options(kcore_mode=mode))
+    check(pp, n1 + n2, 2, edges, opts=pp.options(kcore_mode=0, host_loop=1))
+
+
+def test_round_modes_small_first_frontier(pp):
+    """A dense graph whose F_1 is tiny: the automatic mode hands over before
+    round 1, on the caller's own edge array."""
+    n, r = 20000, 3
+    edges = ppgen.partitioned_edges(n, r, int(1.5 * n), 11)
+    for mode in MODES:
+        check(pp, n, 2, edges, opts=pp.options(kcore_mode=mode))
+
+
+def test_misaligned_edge_array(pp):
+    """Rows not 16-byte aligned (an offset view): the generic round kernels run."""
+    n, r = 30000, 4
+    edges = ppgen.partitioned_edges(n, r, int(0.7 * n), 13)
+    m = edges.shape[0]
+    buf = torch.zeros(m * r + 1, dtype=torch.int32, device="cuda")
+    buf[1:] = torch.from_numpy(np.ascontiguousarray(edges, dtype=np.uint32).view(np.int32).reshape(-1)).cuda()
+    d_edges = buf[1:].view(m, r)
+    assert d_edges.data_ptr() % 16 != 0
+    o = oracle.kcore_rounds(n, 2, edges)
+    for mode in MODES:
+        vr = torch.full((n,), -7, dtype=torch.int32, device="cuda")
+        er = torch.full((m,), -7, dtype=torch.int32, device="cuda")
+        res = pp.peel_kcore(n, r, 2, d_edges, vr, er, pp.options(kcore_mode=mode))
+        assert res.rounds == o["rounds"]
+        assert (vr.cpu().numpy() == o["vround"]).all() and (er.cpu().numpy() == o["eround"]).all()
+
+
 def test_plain_peel_config(pp):
     cfg = ppgen.PLAIN_PEEL
     n, r, k = cfg["n"], cfg["r"], cfg["k"]
