@@ -447,9 +447,30 @@ def bench_kcore(pp, torch, args):
                                        and sub.core_edges == full.core_edges)})
         del d
         torch.cuda.empty_cache()
+    # the plain-peel configuration: 2^14 vertices, launch-latency bound (microseconds)
+    pc = ppgen.PLAIN_PEEL
+    pe = ppgen.partitioned_edges(pc["n"], pc["r"], ppgen.edges_from_c(pc["c"], pc["n"]), pc["seed"])
+    with torch.cuda.stream(stream):
+        pd = torch.from_numpy(pe.view(np.int32)).cuda()
+    stream.synchronize()
+    for _ in range(5):
+        pres = pp.peel_kcore(pc["n"], pc["r"], pc["k"], pd, stream=stream)
+    us = []
+    for _ in range(50):
+        ev[0].record(stream)
+        pres = pp.peel_kcore(pc["n"], pc["r"], pc["k"], pd, stream=stream)
+        ev[1].record(stream)
+        stream.synchronize()
+        us.append(ev[0].elapsed_time(ev[1]) * 1e3)
+    plain = {"workload": "plain peel n=2^14 r=3 k=2 c=0.7 (%d edges)" % pe.shape[0], "rounds": pres.rounds,
+             "core_vertices": pres.core_vertices, "us_median": float(np.median(us)),
+             "us_p10": float(np.percentile(us, 10)), "us_p90": float(np.percentile(us, 90)),
+             "timed": "one pp_peel_kcore call, graph-driven rounds"}
     return {"workload": cfg["name"], "k": k, "parts": r,
-            "timed": "one pp_peel_kcore call: degree histogram, scan, incidence scatter, rounds",
-            "densities": rows}
+            "timed": "one pp_peel_kcore call: degree histogram, then edge-centric rounds while the frontier "
+                     "is at least half the edges left, incidence lists for the edges left and "
+                     "vertex-centric rounds after that",
+            "densities": rows, "plain_peel": plain}
 
 
 def bench_tables(pp, torch, args):

@@ -31,6 +31,12 @@ static IbltKernels iblt_kernels_t() {
     if constexpr (!B) {
       cudaFuncSetAttribute((const void *)k_claim<R, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            200 * 1024);
+      if constexpr (R >= 0) {
+        cudaFuncSetAttribute((const void *)k_claim<R, false, true, true>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        cudaFuncSetAttribute((const void *)k_apply_round<R, false, true>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+      }
     }
     cudaFuncSetAttribute((const void *)k_apply_round<R, B>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          200 * 1024);
@@ -47,6 +53,8 @@ static IbltKernels iblt_kernels_t() {
     k.sg_scan = (const void *)k_sgscan<R>;
     k.sg_peel = (const void *)k_sgpeel<R>;
     k.sg_filter = (const void *)k_sgfilter<R>;
+    k.sg_claim = (const void *)k_claim<R, false, true, true>;
+    k.sg_apply = (const void *)k_apply_round<R, false, true>;
   }
   return k;
 }
@@ -70,9 +78,10 @@ const void *bins_reset_kernel() { return (const void *)k_bins_reset; }
 
 const void *residual_kernel() { return (const void *)k_residual; }
 
-size_t claim_smem_bytes(int nr, bool batch, uint32_t n_bins) {
+size_t claim_smem_bytes(int nr, bool batch, uint32_t n_bins, bool sgn) {
   const size_t cap = (size_t)kClaimChunk * nr;
-  return cap * (8 + 4 + (batch ? 4 : 0)) + (size_t)kClaimChunk * 8 + 3 * (size_t)n_bins * 4;
+  return cap * (8 + 4 + (batch ? 4 : 0)) + (size_t)kClaimChunk * 8 + 3 * (size_t)n_bins * 4 +
+         (sgn ? (size_t)kClaimChunk : 0);
 }
 
 size_t apply_round_smem_bytes(bool batch, uint32_t n_bins) {
@@ -134,9 +143,12 @@ struct pp_iblt {
   signed char *fsign = nullptr;
   u32 *sg_cand = nullptr;  // r pushes per recovered key at most: r * n entries
   cudaGraphExec_t sg_exec = nullptr;
-  int grid_sgscan = 0, grid_sgpeel = 0, grid_sgfilter = 0;
+  int grid_sgscan = 0, grid_sgpeel = 0, grid_sgfilter = 0, grid_sgclaim = 0;
+  size_t smem_sgclaim = 0;
   signed char *sg_graph_out = nullptr;  // output sign pointer the graph was built with
   bool sg_graph_built = false;
+  bool sg_graph_binned = false;         // the graph's round kind
+  uint32_t sg_graph_gen = 0;            // rec_gen the binned graph was built with
 };
 
 namespace {
@@ -1038,6 +1050,15 @@ pp_status pp_iblt_decode_signed(pp_iblt *t, uint64_t *d_out_keys, int8_t *d_out_
     t->grid_sgpeel = persistent_grid(t->k.sg_peel, kBlock, 0, t->opt.ctas_per_sm);
     t->grid_sgfilter = persistent_grid(t->k.sg_filter, kBlock, 0, t->opt.ctas_per_sm);
   }
+  // binned rounds for large tables, as in the unsigned decode
+  const bool binned = t->opt.binned == 1 || (t->opt.binned == 0 && t->n >= (1ull << 21));
+  if (binned) {
+    pp_status st = ensure_round_bins(t, s);
+    if (st != PP_OK) return st;
+    PP_CUDA(cudaMemsetAsync(t->bin_count, 0, t->n_bins * sizeof(u32), s));
+    t->smem_sgclaim = claim_smem_bytes(t->k.nr, false, t->n_bins, true);
+    t->grid_sgclaim = persistent_grid(t->k.sg_claim, kBlock, t->smem_sgclaim, t->opt.ctas_per_sm);
+  }
   memset(t->h_ctl, 0, sizeof(DecodeCtl));
   t->h_ctl->out = reinterpret_cast<u64 *>(d_out_keys);
   t->h_ctl->out_cap = out_cap;
@@ -1063,27 +1084,49 @@ pp_status pp_iblt_decode_signed(pp_iblt *t, uint64_t *d_out_keys, int8_t *d_out_
   void *peel_p[] = {&cells, &tab, &fkey_c, &fcell_c, &fsign_c, &bitmap_c, &cand, &cand_cap, &osign, &ctl};
   void *filt_p[] = {&cells_c, &tab, &cand_c, &fkey, &fcell, &fsign, &bitmap, &ctl};
   void *end_p[] = {&ctl, &rs, &set_cond, &cond};
+  // binned rounds: claim (records carry the sign) -> apply -> filter -> reset bins
+  ClaimArgs ca;
+  ApplyRArgs aa;
+  ResetArgs ra;
+  if (binned) {
+    fill_round_args(t, ca, aa, ra);
+    ca.rb.fsign = t->fsign;
+    ca.rb.osign = osign;
+    ca.rb.cand_cap = cand_cap;
+    ca.cand = t->sg_cand;
+    aa.rb.cand_cap = cand_cap;
+    aa.cand = t->sg_cand;
+  }
   if (t->opt.host_loop) {
     PP_CUDA(cudaLaunchKernel(t->k.sg_scan, dim3(t->grid_sgscan), dim3(kBlock), scan_p, 0, s));
     for (;;) {
-      PP_CUDA(cudaLaunchKernel(t->k.sg_peel, dim3(t->grid_sgpeel), dim3(kBlock), peel_p, 0, s));
+      if (binned) {
+        PP_CUDA(cudaLaunchKernel(t->k.sg_claim, dim3(t->grid_sgclaim), dim3(kBlock), ca.p, t->smem_sgclaim, s));
+        PP_CUDA(cudaLaunchKernel(t->k.sg_apply, dim3(t->grid_apply_round), dim3(kBlock), aa.p,
+                                 t->smem_apply_round, s));
+      } else {
+        PP_CUDA(cudaLaunchKernel(t->k.sg_peel, dim3(t->grid_sgpeel), dim3(kBlock), peel_p, 0, s));
+      }
       PP_CUDA(cudaLaunchKernel(t->k.sg_filter, dim3(t->grid_sgfilter), dim3(kBlock), filt_p, 0, s));
+      if (binned) PP_CUDA(cudaLaunchKernel((const void *)k_bins_reset, dim3(1), dim3(256), ra.p, 0, s));
       PP_CUDA(cudaLaunchKernel((const void *)k_round_end, dim3(1), dim3(32), end_p, 0, s));
       PP_CUDA(cudaMemcpyAsync(&t->h_ctl->more, &t->ctl->more, sizeof(u32), cudaMemcpyDeviceToHost, s));
       PP_CUDA(cudaStreamSynchronize(s));
       if (!t->h_ctl->more) break;
     }
   } else {
-    if (t->sg_exec && t->sg_graph_out != osign) {
+    if (t->sg_exec && (t->sg_graph_out != osign || t->sg_graph_binned != binned ||
+                       (binned && t->sg_graph_gen != t->rec_gen))) {
       cudaGraphExecDestroy(t->sg_exec);
       t->sg_exec = nullptr;
     }
     if (!t->sg_exec) {
-      // sgscan -> while (more) { sgpeel -> sgfilter -> round_end }
+      // sgscan -> while (more) { sgpeel -> sgfilter -> round_end }, or with
+      // binned rounds { claim -> apply -> sgfilter -> reset bins -> round_end }
       cudaGraph_t g = nullptr;
       PP_CUDA(cudaGraphCreate(&g, 0));
       pp_status st = PP_OK;
-      cudaGraphNode_t n_scan, n_cond, n_peel, n_filter, n_end;
+      cudaGraphNode_t n_scan, n_cond, n_peel, n_apply, n_filter, n_reset, n_end;
       cudaGraphNodeParams cp{};
       cudaGraph_t body;
       st = add_kernel(&n_scan, g, nullptr, 0, t->k.sg_scan, t->grid_sgscan, kBlock, 0, scan_p);
@@ -1102,17 +1145,33 @@ pp_status pp_iblt_decode_signed(pp_iblt *t, uint64_t *d_out_keys, int8_t *d_out_
       }
       body = cp.conditional.phGraph_out[0];
       set_cond = 1;
-      st = add_kernel(&n_peel, body, nullptr, 0, t->k.sg_peel, t->grid_sgpeel, kBlock, 0, peel_p);
-      if (st != PP_OK) goto sg_done;
-      st = add_kernel(&n_filter, body, &n_peel, 1, t->k.sg_filter, t->grid_sgfilter, kBlock, 0, filt_p);
-      if (st != PP_OK) goto sg_done;
-      st = add_kernel(&n_end, body, &n_filter, 1, (const void *)k_round_end, 1, 32, 0, end_p);
-      if (st != PP_OK) goto sg_done;
+      if (binned) {
+        st = add_kernel(&n_peel, body, nullptr, 0, t->k.sg_claim, t->grid_sgclaim, kBlock, t->smem_sgclaim, ca.p);
+        if (st != PP_OK) goto sg_done;
+        st = add_kernel(&n_apply, body, &n_peel, 1, t->k.sg_apply, t->grid_apply_round, kBlock,
+                        t->smem_apply_round, aa.p);
+        if (st != PP_OK) goto sg_done;
+        st = add_kernel(&n_filter, body, &n_apply, 1, t->k.sg_filter, t->grid_sgfilter, kBlock, 0, filt_p);
+        if (st != PP_OK) goto sg_done;
+        st = add_kernel(&n_reset, body, &n_filter, 1, (const void *)k_bins_reset, 1, 256, 0, ra.p);
+        if (st != PP_OK) goto sg_done;
+        st = add_kernel(&n_end, body, &n_reset, 1, (const void *)k_round_end, 1, 32, 0, end_p);
+        if (st != PP_OK) goto sg_done;
+      } else {
+        st = add_kernel(&n_peel, body, nullptr, 0, t->k.sg_peel, t->grid_sgpeel, kBlock, 0, peel_p);
+        if (st != PP_OK) goto sg_done;
+        st = add_kernel(&n_filter, body, &n_peel, 1, t->k.sg_filter, t->grid_sgfilter, kBlock, 0, filt_p);
+        if (st != PP_OK) goto sg_done;
+        st = add_kernel(&n_end, body, &n_filter, 1, (const void *)k_round_end, 1, 32, 0, end_p);
+        if (st != PP_OK) goto sg_done;
+      }
       if (cudaGraphInstantiate(&t->sg_exec, g, 0) != cudaSuccess) {
         st = fail(PP_ERR_CUDA, "cudaGraphInstantiate failed: %s", cudaGetErrorString(cudaGetLastError()));
         t->sg_exec = nullptr;
       }
       t->sg_graph_out = osign;
+      t->sg_graph_binned = binned;
+      t->sg_graph_gen = t->rec_gen;
     sg_done:
       cudaGraphDestroy(g);
       if (st != PP_OK) return st;

@@ -23,12 +23,21 @@
 
 namespace pp {
 
-__device__ __forceinline__ int remove_key(Cell *cells, u32 c, u64 x, u64 cx) {
+__device__ __forceinline__ int remove_key(Cell *cells, u32 c, u64 x, u64 cx, int sg = 1) {
   Cell *p = cells + c;
-  const int old = atomicSub(&p->count, 1);
+  const int old = atomicSub(&p->count, sg);
   atomicXor(&p->key, x);
   atomicXor(&p->chk, cx);
   return old;
+}
+
+// A cell becomes a candidate for the next frontier when its count reaches 1
+// (2 -> 1 in the plain decode; +-1 from any count in the signed one, where a
+// cell may get there more than once and the filter keeps its first entry).
+template <bool SIGNED>
+__device__ __forceinline__ bool becomes_candidate(int old, int sg) {
+  const int now = old - sg;
+  return SIGNED ? (now == 1 || now == -1) : old == 2;
 }
 
 // Shared memory of k_claim: staged records (keys and cells, plus tables in a
@@ -40,7 +49,10 @@ __device__ __forceinline__ int remove_key(Cell *cells, u32 c, u64 x, u64 cx) {
 // generic and batched instances would take 106-154 registers uncapped).
 // CLAIM = false (decode with sub-tables): every frontier entry recovers its key
 // -- within one sub-table no key is found twice -- so the bitmap is not read.
-template <int R, bool BATCH, bool CLAIM = true>
+// SIGNED (sparse recovery, plain tables): each frontier entry carries the sign
+// of its cell's count; the winner outputs it, and its records carry it in bit
+// 31 of the cell (signed tables have fewer than 2^31 cells).
+template <int R, bool BATCH, bool CLAIM = true, bool SIGNED = false>
 __global__ void __launch_bounds__(kBlock, (!BATCH && R >= 3) ? 5 : 4) k_claim(Cell *__restrict__ cells, const TableArgs tab0,
                                                   const TableArgs *__restrict__ tabs,
                                                   const u64 *__restrict__ fkey, const u32 *__restrict__ fcell,
@@ -50,6 +62,7 @@ __global__ void __launch_bounds__(kBlock, (!BATCH && R >= 3) ? 5 : 4) k_claim(Ce
                                                   BatchCounters bc) {
   constexpr int NR = nr_of<R>();
   constexpr int CAP = kClaimChunk * NR;
+  constexpr u32 kCellMask = SIGNED ? 0x7fffffffu : 0xffffffffu;
   extern __shared__ __align__(16) unsigned char smem[];
   u64 *s_key = reinterpret_cast<u64 *>(smem);       // CAP
   u64 *s_out = s_key + CAP;                         // kClaimChunk (plain)
@@ -58,6 +71,7 @@ __global__ void __launch_bounds__(kBlock, (!BATCH && R >= 3) ? 5 : 4) k_claim(Ce
   u32 *s_hist = s_tab + (BATCH ? CAP : 0);          // n_bins
   u32 *s_scan = s_hist + rb.n_bins;
   u32 *s_base = s_scan + rb.n_bins;
+  signed char *s_osign = reinterpret_cast<signed char *>(s_base + rb.n_bins);  // kClaimChunk (signed)
   __shared__ u32 s_wt[33];
   __shared__ u32 s_total, s_nout;
   __shared__ u64 s_obase;
@@ -68,7 +82,7 @@ __global__ void __launch_bounds__(kBlock, (!BATCH && R >= 3) ? 5 : 4) k_claim(Ce
   u64 *out = BATCH ? bout : ctl->out;
   const u64 out_cap = BATCH ? 0 : ctl->out_cap;
   const u32 stats_rounds = BATCH ? ctl->stats_rounds : 0;
-  u32 flags = 0;
+  u32 flags = 0, n_neg = 0;
   u64 ovf_emptied = 0;
   for (u64 c0 = (u64)blockIdx.x * kClaimChunk; c0 < n; c0 += (u64)gridDim.x * kClaimChunk) {
     for (u32 i = tid; i < nb; i += kBlock) s_hist[i] = 0;
@@ -78,6 +92,7 @@ __global__ void __launch_bounds__(kBlock, (!BATCH && R >= 3) ? 5 : 4) k_claim(Ce
     u32 cj[kClaimItems][NR], rank[kClaimItems][NR], tb[kClaimItems];
     bool win[kClaimItems];
     int rr[kClaimItems];
+    signed char sg[kClaimItems];
     // load every entry of this thread first (independent loads in flight)
     u32 c[kClaimItems];
 #pragma unroll
@@ -87,6 +102,7 @@ __global__ void __launch_bounds__(kBlock, (!BATCH && R >= 3) ? 5 : 4) k_claim(Ce
       x[it] = valid ? __ldcs(fkey + i) : 0ull;
       c[it] = valid ? __ldcs(fcell + i) : 0u;
       tb[it] = (BATCH && valid) ? __ldcs(ftab + i) : 0u;
+      sg[it] = (SIGNED && valid) ? rb.fsign[i] : (signed char)1;
       win[it] = valid;
     }
 #pragma unroll
@@ -117,7 +133,11 @@ __global__ void __launch_bounds__(kBlock, (!BATCH && R >= 3) ? 5 : 4) k_claim(Ce
       // recovered key
       if constexpr (!BATCH) {
         const u32 p = warp_reserve<u32>(win[it], &s_nout);
-        if (win[it]) s_out[p] = x[it];
+        if (win[it]) {
+          s_out[p] = x[it];
+          if (SIGNED) s_osign[p] = sg[it];
+        }
+        if (SIGNED) n_neg += win[it] && sg[it] < 0;
       } else {
         const TableArgs &T = tabs[tb[it]];
         const u32 label = win[it] ? tb[it] : 0xffffffffu;
@@ -188,7 +208,7 @@ __global__ void __launch_bounds__(kBlock, (!BATCH && R >= 3) ? 5 : 4) k_claim(Ce
             const u32 bn = cj[it][j] >> rb.shift;
             const u32 pos = s_scan[bn] + rank[it][j];
             s_key[pos] = x[it];
-            s_cell[pos] = cj[it][j];
+            s_cell[pos] = cj[it][j] | ((SIGNED && sg[it] < 0) ? 0x80000000u : 0u);
             if (BATCH) s_tab[pos] = tb[it];
           }
         }
@@ -197,7 +217,7 @@ __global__ void __launch_bounds__(kBlock, (!BATCH && R >= 3) ? 5 : 4) k_claim(Ce
     __syncthreads();
     const u32 total = s_total;
     for (u32 p = tid; p < total; p += kBlock) {
-      const u32 bn = s_cell[p] >> rb.shift;
+      const u32 bn = (s_cell[p] & kCellMask) >> rb.shift;
       const u32 slot = s_base[bn] + (p - s_scan[bn]);
       if (slot < rb.cap) {
         const u64 dst = (u64)bn * rb.cap + slot;
@@ -209,33 +229,40 @@ __global__ void __launch_bounds__(kBlock, (!BATCH && R >= 3) ? 5 : 4) k_claim(Ce
         const u32 t2 = BATCH ? s_tab[p] : 0u;
         const u64 seed_chk = BATCH ? bc.chk_seed[t2] : tab0.seed[rank_of<R>(tab0)];
         const u64 xx = s_key[p];
-        const u32 cc = s_cell[p];
-        const int old = remove_key(cells, cc, xx, mix64(xx ^ seed_chk));
-        if (old == 2) {
+        const u32 cc = s_cell[p] & kCellMask;
+        const int sgn = (SIGNED && (s_cell[p] >> 31)) ? -1 : 1;
+        const int old = remove_key(cells, cc, xx, mix64(xx ^ seed_chk), sgn);
+        if (becomes_candidate<SIGNED>(old, sgn)) {
           const u32 q = atomicAdd(&ctl->n_cand, 1u);
-          cand[q] = cc;
+          if (!SIGNED || q < rb.cand_cap) cand[q] = cc;
+          else flags |= FLAG_INTERNAL;
           if (BATCH) ctab[q] = t2;
         }
-        if (!BATCH) ovf_emptied += (u64)(long long)((old == 1) - (old == 0));
+        if (!BATCH) ovf_emptied += (u64)(long long)((old != 0) - (old - sgn != 0));
       }
     }
     if constexpr (!BATCH) {
       const u32 no = s_nout;
       const u64 ob = s_obase;
       for (u32 q = tid; q < no; q += kBlock) {
-        if (ob + q < out_cap) out[ob + q] = s_out[q];
-        else flags |= FLAG_CAPACITY;
+        if (ob + q < out_cap) {
+          out[ob + q] = s_out[q];
+          if (SIGNED && rb.osign) rb.osign[ob + q] = s_osign[q];
+        } else {
+          flags |= FLAG_CAPACITY;
+        }
       }
     }
     __syncthreads();
   }
+  if (SIGNED && n_neg) atomicAdd(&ctl->n_neg, n_neg);
   if (ovf_emptied) atomicAdd(&ctl->emptied, ovf_emptied);
   if (flags) atomicOr(&ctl->flags, flags);
 }
 
 // Shared memory of k_apply_round: chunk prefix (n_bins + 1 u32) + pushes
 // (kApplyChunk cells [+ tables]).
-template <int R, bool BATCH>
+template <int R, bool BATCH, bool SIGNED = false>
 __global__ void __launch_bounds__(kBlock) k_apply_round(Cell *__restrict__ cells, const TableArgs tab0,
                                                         const TableArgs *__restrict__ tabs, RoundBins rb,
                                                         u32 *__restrict__ cand, u32 *__restrict__ ctab,
@@ -311,7 +338,7 @@ __global__ void __launch_bounds__(kBlock) k_apply_round(Cell *__restrict__ cells
     u64 x[kApplyPer], seed_chk[kApplyPer];
     u32 c[kApplyPer], tb[kApplyPer];
     bool v[kApplyPer];
-    int old[kApplyPer];
+    int old[kApplyPer], sg[kApplyPer];
 #pragma unroll
     for (int k = 0; k < kApplyPer; ++k) {
       const u32 i = first + (u32)k * kBlock + tid;
@@ -319,29 +346,35 @@ __global__ void __launch_bounds__(kBlock) k_apply_round(Cell *__restrict__ cells
       x[k] = v[k] ? __ldcs(rb.rec_key + base + i) : 0ull;
       c[k] = v[k] ? __ldcs(rb.rec_cell + base + i) : 0u;
       tb[k] = (BATCH && v[k]) ? __ldcs(rb.rec_tab + base + i) : 0u;
+      sg[k] = (SIGNED && (c[k] >> 31)) ? -1 : 1;
+      if (SIGNED) c[k] &= 0x7fffffffu;
     }
 #pragma unroll
     for (int k = 0; k < kApplyPer; ++k)
       seed_chk[k] = BATCH ? (v[k] ? bc.chk_seed[tb[k]] : 0ull) : tab0.seed[rank_of<R>(tab0)];
 #pragma unroll
     for (int k = 0; k < kApplyPer; ++k)
-      old[k] = v[k] ? remove_key(cells, c[k], x[k], mix64(x[k] ^ seed_chk[k])) : 0;
+      old[k] = v[k] ? remove_key(cells, c[k], x[k], mix64(x[k] ^ seed_chk[k]), sg[k]) : 0;
 #pragma unroll
     for (int k = 0; k < kApplyPer; ++k) {
-      const bool push = old[k] == 2;
+      const bool push = v[k] && becomes_candidate<SIGNED>(old[k], sg[k]);
       const u32 q = warp_reserve<u32>(push, &s_ncand);
       if (push) {
         s_cand[q] = c[k];
         if (BATCH) s_ctab[q] = tb[k];
       }
       // batched decodes count their residue with k_residual afterwards
-      if (!BATCH && v[k]) emptied += (u64)(long long)((old[k] == 1) - (old[k] == 0));
+      if (!BATCH && v[k]) emptied += (u64)(long long)((old[k] != 0) - (old[k] - sg[k] != 0));
     }
     __syncthreads();
     const u32 nc = s_ncand;
     if (tid == 0 && nc) s_cbase = atomicAdd(&ctl->n_cand, nc);
     __syncthreads();
     for (u32 q = tid; q < nc; q += kBlock) {
+      if (SIGNED && (u64)s_cbase + q >= rb.cand_cap) {
+        atomicOr(&ctl->flags, (u32)FLAG_INTERNAL);
+        continue;
+      }
       cand[s_cbase + q] = s_cand[q];
       if (BATCH) ctab[s_cbase + q] = s_ctab[q];
     }

@@ -127,13 +127,17 @@ constexpr int kApplyChunk = kBlock * kApplyPer;
 // Record lists of one round: bin b owns records [b*cap, b*cap + min(count[b], cap)).
 struct RoundBins {
   u64 *rec_key;
-  u32 *rec_cell;
+  u32 *rec_cell;  // signed decode: bit 31 set for a key removed with sign -1
   u32 *rec_tab;   // batch only
   u32 *count;
   u32 cap;
   u32 n_bins;
   u32 shift;      // bin of cell c = c >> shift
   u32 pad;
+  // signed decode only
+  const signed char *fsign = nullptr;  // sign of each frontier entry
+  signed char *osign = nullptr;        // sign of each recovered key (may be null)
+  u64 cand_cap = 0;                    // candidate list capacity
 };
 
 // Bin shift for a table (or arena) of n cells: bins of 2^19 cells or more, at
@@ -188,6 +192,7 @@ struct IbltKernels {
   const void *sub_scan = nullptr, *sub_filter = nullptr, *sub_peel = nullptr;  // sub-rounds (plain only)
   const void *sub_claim = nullptr;  // binned sub-rounds: k_claim without the claim check
   const void *sg_scan = nullptr, *sg_peel = nullptr, *sg_filter = nullptr;     // signed (plain only)
+  const void *sg_claim = nullptr, *sg_apply = nullptr;                         // signed, binned rounds
 };
 
 // The kernel set for a rank code: 3 or 4 = that r; -4 = any r <= 4 (batched
@@ -201,7 +206,7 @@ size_t peel_smem_bytes(int nr, bool batch);
 size_t bin_smem_bytes(int nr, bool batch, uint32_t n_slabs);
 
 // Dynamic shared memory of the binned round's claim and apply kernels.
-size_t claim_smem_bytes(int nr, bool batch, uint32_t n_bins);
+size_t claim_smem_bytes(int nr, bool batch, uint32_t n_bins, bool sgn = false);
 size_t apply_round_smem_bytes(bool batch, uint32_t n_bins);
 
 // The bin-reset kernel that ends a binned round.

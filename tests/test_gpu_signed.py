@@ -72,9 +72,12 @@ def run_signed(pp, n, r, A, B, seed, opts=None, with_signs=True):
     (30011, 5, 0.30, 0.30, 5000, 6),     # generic kernel
     (20000, 2, 0.20, 0.20, 5000, 7),
 ])
-def test_set_difference(pp, n, r, fa, fb, common, seed):
+@pytest.mark.parametrize("binned", [0, 1], ids=["direct", "binned"])
+def test_set_difference(pp, n, r, fa, fb, common, seed, binned):
+    """binned=1 forces the binned rounds (claim records carry the sign) on
+    tables that would otherwise apply their updates directly."""
     A, B = _sets(int(fa * n), int(fb * n), common, 10 + seed)
-    run_signed(pp, n, r, A, B, seed)
+    run_signed(pp, n, r, A, B, seed, opts=pp.options(binned=binned))
 
 
 def test_insert_only_matches_unsigned(pp):
@@ -88,24 +91,50 @@ def test_insert_only_matches_unsigned(pp):
     assert u.rounds == res.rounds and u.recovered_per_round == res.recovered_per_round
 
 
-def test_large_table(pp):
+@pytest.mark.parametrize("binned", [0, 2], ids=["binned", "direct"])
+def test_large_table(pp, binned):
     n, r = 1 << 22, 3
     A, B = _sets(int(0.45 * n), int(0.3 * n), 1 << 20, 22)
-    run_signed(pp, n, r, A, B, 23)
+    run_signed(pp, n, r, A, B, 23, opts=pp.options(binned=binned))
 
 
-def test_host_loop_and_no_signs(pp):
+@pytest.mark.parametrize("binned", [0, 1], ids=["direct", "binned"])
+def test_host_loop_and_no_signs(pp, binned):
     n, r = 30000, 4
     A, B = _sets(9000, 9000, 3000, 24)
-    a = run_signed(pp, n, r, A, B, 25, opts=pp.options(host_loop=1))
-    b = run_signed(pp, n, r, A, B, 25, with_signs=False)
+    a = run_signed(pp, n, r, A, B, 25, opts=pp.options(host_loop=1, binned=binned))
+    b = run_signed(pp, n, r, A, B, 25, opts=pp.options(binned=binned), with_signs=False)
     assert a.recovered_per_round == b.recovered_per_round
 
 
-def test_capacity_error(pp):
+def test_signed_then_unsigned_on_one_handle(pp):
+    """The signed and unsigned decodes share the round bins and the bitmap."""
+    n, r = 1 << 21, 3
+    A, B = _sets(int(0.4 * n), int(0.3 * n), 1000, 28)
+    gt = pp.IBLT(n, r, 29)
+    for rep in range(2):
+        gt.clear()
+        gt.insert(_dev(A))
+        gt.delete(_dev(B))
+        out = torch.zeros(len(A) + len(B), dtype=torch.int64, device="cuda")
+        sg = torch.zeros(len(A) + len(B), dtype=torch.int8, device="cuda")
+        res = gt.decode_signed(out, sg)
+        assert res.recovered == len(A) + len(B) - 2000 and res.residual_cells == 0
+        got = out[: res.recovered].cpu().numpy().view(np.uint64)
+        neg = sg[: res.recovered].cpu().numpy() < 0
+        assert np.array_equal(np.sort(got[~neg]), np.sort(A[1000:]))
+        assert np.array_equal(np.sort(got[neg]), np.sort(B[1000:]))
+        gt.clear()
+        gt.insert(_dev(A))
+        u = gt.decode(torch.zeros(len(A), dtype=torch.int64, device="cuda"))
+        assert u.recovered == len(A) and u.residual_cells == 0
+
+
+@pytest.mark.parametrize("binned", [0, 1], ids=["direct", "binned"])
+def test_capacity_error(pp, binned):
     n, r = 20000, 3
     A, B = _sets(6000, 4000, 1000, 26)
-    gt = pp.IBLT(n, r, 27)
+    gt = pp.IBLT(n, r, 27, pp.options(binned=binned))
     gt.insert(_dev(A))
     gt.delete(_dev(B))
     out = torch.zeros(100, dtype=torch.int64, device="cuda")
