@@ -63,10 +63,14 @@ typedef struct pp_options {
   uint32_t stats_rounds; /* batch: per-table per-round counters kept (default 128) */
   uint32_t binned;       /* IBLT build/insert: 0 = slab-binned when the table is at least
                             2^23 cells (default), 1 = always binned, 2 = never */
-  uint32_t kcore_mode;   /* pp_peel_kcore full rounds: 0 = edge-centric rounds while the
-                            frontier is large, then rounds over incidence lists built for
-                            the edges left (default); 1 = incidence lists from round 1;
-                            2 = edge-centric rounds only.  r > 4 always uses 1. */
+  uint32_t kcore_mode;   /* pp_peel_kcore full rounds: 0 = for graphs of 2^20 edges or
+                            more, edge-centric rounds while the frontier holds at least
+                            half as many vertices as there are edges left, then rounds
+                            over incidence lists built for the edges left; smaller graphs
+                            use incidence lists (default); 1 = incidence lists from round
+                            1; 2 = edge-centric rounds to the end.  r > 4 and edge
+                            rows that are not 16-byte (r = 4) or 8-byte (r = 2) aligned
+                            always use 1. */
   uint32_t reserved;
 } pp_options;
 

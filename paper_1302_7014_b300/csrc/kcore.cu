@@ -30,7 +30,10 @@
 // are skipped on the device (their statistics are still written).
 #include <string.h>
 
+#include <algorithm>
+#include <map>
 #include <mutex>
+#include <tuple>
 
 #include "host.cuh"
 #include "kcore_csr.cuh"
@@ -853,8 +856,43 @@ const void *pick_peel(bool sub, int rk, bool d16) {
   }
 }
 
-// The round loop: a CUDA graph whose while node runs peel -> round_end until
-// round_end clears the condition, or the same kernels driven from the host.
+// Round-loop graphs, instantiated once per thread and kernel/grid set and kept:
+// a call only rewrites the kernel nodes' arguments before launching
+// (instantiating costs more than a whole peel of a small graph).  Never freed:
+// their number is bounded by the kernel variants and the CUDA context may be
+// gone by the time the thread exits.
+struct LoopGraph {
+  cudaGraph_t g = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  cudaGraphNode_t peel = nullptr, mid = nullptr, end = nullptr;
+  cudaGraphConditionalHandle h = 0;
+};
+
+struct LoopKey {
+  const void *peel, *mid, *end;
+  int grid, mid_grid, dev;
+  bool operator<(const LoopKey &o) const {
+    return std::tie(peel, mid, end, grid, mid_grid, dev) < std::tie(o.peel, o.mid, o.end, o.grid, o.mid_grid, o.dev);
+  }
+};
+
+std::map<LoopKey, LoopGraph> &loop_graphs() {
+  static thread_local std::map<LoopKey, LoopGraph> *m = new std::map<LoopKey, LoopGraph>();
+  return *m;
+}
+
+inline cudaKernelNodeParams kernel_node(const void *fn, int grid, int block, void **args) {
+  cudaKernelNodeParams kp{};
+  kp.func = const_cast<void *>(fn);
+  kp.gridDim = dim3((unsigned)grid);
+  kp.blockDim = dim3((unsigned)block);
+  kp.kernelParams = args;
+  return kp;
+}
+
+// The round loop: a CUDA graph whose while node runs peel -> [mid ->]
+// round_end until round_end clears the condition, or the same kernels driven
+// from the host.
 template <class EndArgs>
 pp_status run_rounds(const void *peel_fn, void **peel_p, const void *end_fn, EndArgs &ea, int grid,
                      bool host_loop, cudaStream_t s, const u32 *d_more, const void *mid_fn = nullptr,
@@ -871,68 +909,91 @@ pp_status run_rounds(const void *peel_fn, void **peel_p, const void *end_fn, End
     }
     return PP_OK;
   }
-  cudaGraph_t g = nullptr, body;
-  cudaGraphExec_t exec = nullptr;
-  cudaGraphConditionalHandle h;
+  int dev = 0;
+  PP_CUDA(cudaGetDevice(&dev));
+  const LoopKey key{peel_fn, mid_fn, end_fn, grid, mid_fn ? mid_grid : 0, dev};
+  auto &cache = loop_graphs();
+  auto it = cache.find(key);
+  if (it != cache.end()) {
+    LoopGraph &lg = it->second;
+    ea.set_cond = 1;
+    ea.cond = lg.h;
+    ea.bind();
+    cudaKernelNodeParams kp = kernel_node(peel_fn, grid, kKBlock, peel_p);
+    bool ok = cudaGraphExecKernelNodeSetParams(lg.exec, lg.peel, &kp) == cudaSuccess;
+    if (ok && mid_fn) {
+      kp = kernel_node(mid_fn, mid_grid, kKBlock, mid_p);
+      ok = cudaGraphExecKernelNodeSetParams(lg.exec, lg.mid, &kp) == cudaSuccess;
+    }
+    if (ok) {
+      kp = kernel_node(end_fn, 1, 32, ea.p);
+      ok = cudaGraphExecKernelNodeSetParams(lg.exec, lg.end, &kp) == cudaSuccess;
+    }
+    if (ok) {
+      PP_CUDA(cudaGraphLaunch(lg.exec, s));
+      return PP_OK;
+    }
+    cudaGetLastError();  // the update was refused: build the graph again
+    cudaStreamSynchronize(s);
+    cudaGraphExecDestroy(lg.exec);
+    cudaGraphDestroy(lg.g);
+    cache.erase(it);
+  }
+  LoopGraph lg;
+  cudaGraph_t body;
   cudaGraphNodeParams cp{};
-  cudaGraphNode_t n_cond, n_peel, n_mid, n_end;
+  cudaGraphNode_t n_cond;
   cudaKernelNodeParams kp{};
   pp_status st = PP_OK;
-  PP_CUDA(cudaGraphCreate(&g, 0));
-  if (cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault) != cudaSuccess) {
+  PP_CUDA(cudaGraphCreate(&lg.g, 0));
+  if (cudaGraphConditionalHandleCreate(&lg.h, lg.g, 1, cudaGraphCondAssignDefault) != cudaSuccess) {
     st = fail(PP_ERR_CUDA, "cudaGraphConditionalHandleCreate failed");
-    goto done;
+    goto fail_out;
   }
   cp.type = cudaGraphNodeTypeConditional;
-  cp.conditional.handle = h;
+  cp.conditional.handle = lg.h;
   cp.conditional.type = cudaGraphCondTypeWhile;
   cp.conditional.size = 1;
-  if (cudaGraphAddNode(&n_cond, g, nullptr, nullptr, 0, &cp) != cudaSuccess) {
+  if (cudaGraphAddNode(&n_cond, lg.g, nullptr, nullptr, 0, &cp) != cudaSuccess) {
     st = fail(PP_ERR_CUDA, "cudaGraphAddNode(conditional while) failed");
-    goto done;
+    goto fail_out;
   }
   body = cp.conditional.phGraph_out[0];
   ea.set_cond = 1;
-  ea.cond = h;
+  ea.cond = lg.h;
   ea.bind();
-  kp.func = (void *)peel_fn;
-  kp.gridDim = dim3(grid);
-  kp.blockDim = dim3(kKBlock);
-  kp.kernelParams = peel_p;
-  if (cudaGraphAddKernelNode(&n_peel, body, nullptr, 0, &kp) != cudaSuccess) {
+  kp = kernel_node(peel_fn, grid, kKBlock, peel_p);
+  if (cudaGraphAddKernelNode(&lg.peel, body, nullptr, 0, &kp) != cudaSuccess) {
     st = fail(PP_ERR_CUDA, "cudaGraphAddKernelNode(peel) failed");
-    goto done;
+    goto fail_out;
   }
   if (mid_fn) {
-    kp.func = (void *)mid_fn;
-    kp.gridDim = dim3(mid_grid);
-    kp.blockDim = dim3(kKBlock);
-    kp.kernelParams = mid_p;
-    if (cudaGraphAddKernelNode(&n_mid, body, &n_peel, 1, &kp) != cudaSuccess) {
+    kp = kernel_node(mid_fn, mid_grid, kKBlock, mid_p);
+    if (cudaGraphAddKernelNode(&lg.mid, body, &lg.peel, 1, &kp) != cudaSuccess) {
       st = fail(PP_ERR_CUDA, "cudaGraphAddKernelNode(round middle) failed");
-      goto done;
+      goto fail_out;
     }
   }
-  kp.func = (void *)end_fn;
-  kp.gridDim = dim3(1);
-  kp.blockDim = dim3(32);
-  kp.kernelParams = ea.p;
-  if (cudaGraphAddKernelNode(&n_end, body, mid_fn ? &n_mid : &n_peel, 1, &kp) != cudaSuccess) {
+  kp = kernel_node(end_fn, 1, 32, ea.p);
+  if (cudaGraphAddKernelNode(&lg.end, body, mid_fn ? &lg.mid : &lg.peel, 1, &kp) != cudaSuccess) {
     st = fail(PP_ERR_CUDA, "cudaGraphAddKernelNode(round_end) failed");
-    goto done;
+    goto fail_out;
   }
-  if (cudaGraphInstantiate(&exec, g, 0) != cudaSuccess) {
+  if (cudaGraphInstantiate(&lg.exec, lg.g, 0) != cudaSuccess) {
     st = fail(PP_ERR_CUDA, "cudaGraphInstantiate failed");
-    exec = nullptr;
-    goto done;
+    lg.exec = nullptr;
+    goto fail_out;
   }
-  if (cudaGraphLaunch(exec, s) != cudaSuccess) st = fail(PP_ERR_CUDA, "cudaGraphLaunch failed");
-done:
-  if (exec) {
+  if (cudaGraphLaunch(lg.exec, s) != cudaSuccess) {
+    st = fail(PP_ERR_CUDA, "cudaGraphLaunch failed");
     cudaStreamSynchronize(s);
-    cudaGraphExecDestroy(exec);
+    cudaGraphExecDestroy(lg.exec);
+    goto fail_out;
   }
-  cudaGraphDestroy(g);
+  cache.emplace(key, lg);
+  return PP_OK;
+fail_out:
+  cudaGraphDestroy(lg.g);
   return st;
 }
 
@@ -1131,8 +1192,10 @@ static pp_status peel_kcore_impl(uint32_t n, uint32_t r, uint32_t k, const uint3
     // rank-specialised rounds where the edge rows allow their vector loads
     const uintptr_t ea = (uintptr_t)d_edges;
     const int rk = (r == 4 && ea % 16 == 0) || (r == 2 && ea % 8 == 0) || r == 3 ? (int)r : 0;
-    // edge-centric rounds are possible; they start if F_1 is large (or mode 2)
-    const bool edge_ok = !parts && o.kcore_mode != 1 && rk != 0 && m > 0 && n > 0;
+    // edge-centric rounds are possible; they start if F_1 is large (or mode 2).
+    // Below 2^20 edges the incidence lists cost little and mode 0 keeps them.
+    const bool edge_ok = !parts && rk != 0 && m > 0 && n > 0 &&
+                         (o.kcore_mode == 2 || (o.kcore_mode == 0 && m >= (1ull << 20)));
     bool edge_mode = false;
     u32 *rdeg = d16 ? w.deg16 : w.deg;
     // incidence lists of edges[0, me) (row i = edge i), from the current degrees
@@ -1154,7 +1217,9 @@ static pp_status peel_kcore_impl(uint32_t n, uint32_t r, uint32_t k, const uint3
       KEndArgs kea{w.ctl, PeelStats{w.st_s, w.st_m}, 0, 0, {}};
       kea.bind();
       const void *peel = pick_peel(false, rk, d16);
-      const int pgrid = persistent_grid(peel, kKBlock, 0, o.ctas_per_sm);
+      // no more blocks than a frontier of every vertex needs
+      const int pgrid = (int)std::min<uint64_t>((uint64_t)persistent_grid(peel, kKBlock, 0, o.ctas_per_sm),
+                                                (nn + kKBlock - 1) / kKBlock);
       return run_rounds(peel, pa.p, (const void *)k_kround_end, kea, pgrid, o.host_loop != 0, s, &w.ctl->more);
     };
     if (edge_ok) {
@@ -1204,7 +1269,8 @@ static pp_status peel_kcore_impl(uint32_t n, uint32_t r, uint32_t k, const uint3
       KSubEndArgs kea{w.sub, PeelStats{w.st_s, w.st_m}, *parts, 0, 0, {}};
       kea.bind();
       const void *peel = pick_peel(true, rk, d16);
-      const int pgrid = persistent_grid(peel, kKBlock, 0, o.ctas_per_sm);
+      const int pgrid = (int)std::min<uint64_t>((uint64_t)persistent_grid(peel, kKBlock, 0, o.ctas_per_sm),
+                                                (nn + kKBlock - 1) / kKBlock);
       status = run_rounds(peel, pa.p, (const void *)k_kround_end_sub, kea, pgrid,
                           o.host_loop != 0, s, &w.sub->more);
     } else if (!edge_mode) {
@@ -1217,8 +1283,10 @@ static pp_status peel_kcore_impl(uint32_t n, uint32_t r, uint32_t k, const uint3
       KEEndArgs kea{w.ctl, PeelStats{w.st_s, w.st_m}, o.kcore_mode == 2 ? 0u : kSwitchRatio, 0, 0, {}};
       kea.bind();
       const void *er = pick_eround(rk, d16);
-      const int pgrid = persistent_grid(er, kKBlock, 0, o.ctas_per_sm);
-      const int cgrid = persistent_grid((const void *)k_eclear, kKBlock, 0, o.ctas_per_sm);
+      const int pgrid = (int)std::min<uint64_t>((uint64_t)persistent_grid(er, kKBlock, 0, o.ctas_per_sm),
+                                                (mm + kKBlock * kEItems - 1) / (kKBlock * kEItems));
+      const int cgrid = (int)std::min<uint64_t>(
+          (uint64_t)persistent_grid((const void *)k_eclear, kKBlock, 0, o.ctas_per_sm), (nn + kKBlock - 1) / kKBlock);
       status = run_rounds(er, ka.p, (const void *)k_eround_end, kea, pgrid, o.host_loop != 0, s, &w.ctl->econt,
                           (const void *)k_eclear, ka.pc, cgrid);
       if (status != PP_OK) goto cleanup;

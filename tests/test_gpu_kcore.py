@@ -137,20 +137,36 @@ def test_round_modes_density_sweep(pp, mode, c):
         check(pp, n, k, edges, opts=pp.options(kcore_mode=mode, host_loop=1))
 
 
+def check_modes(pp, n, k, edges, modes=MODES, host_loop=True):
+    """check() for every mode against one oracle run."""
+    edges = np.ascontiguousarray(edges, dtype=np.uint32)
+    r = edges.shape[1]
+    o = oracle.kcore_rounds(n, k, edges)
+    runs = [pp.options(kcore_mode=md) for md in modes]
+    if host_loop:
+        runs.append(pp.options(kcore_mode=0, host_loop=1))
+    for opts in runs:
+        res, vr, er = gpu_peel(pp, n, r, k, edges, opts)
+        assert res.rounds == o["rounds"]
+        assert (vr == o["vround"]).all()
+        assert (er == o["eround"]).all()
+        assert res.vertices_left == o["s"] and res.edges_left == o["m"]
+
+
 @pytest.mark.parametrize("dense_c,seed", [(0.85, 1), (0.9, 2), (1.0, 3), (1.3, 4)])
 def test_round_modes_mixed_density(pp, dense_c, seed):
     """A sparse part (most vertices go in round 1, so the automatic mode starts
-    edge-centric) joined to a dense part that leaves a slowly peeling core (so
-    it hands over to incidence lists part way, with the edge list compacted or
-    holding removed entries, depending on the rounds before)."""
-    n1, n2, r = 150000, 50000, 3
+    edge-centric; over 2^20 edges in all) joined to a dense part that leaves a
+    slowly peeling core (so it hands over to incidence lists part way, with the
+    edge list compacted or holding removed entries, depending on the rounds
+    before)."""
+    n1, n2, r = 2_000_000, 700_000, 3
     sparse = ppgen.uniform_edges(n1, r, int(0.3 * n1), 40 + seed)
     dense = (ppgen.uniform_edges(n2, r, int(dense_c * n2), 50 + seed).astype(np.uint64) + n1).astype(np.uint32)
     edges = np.concatenate([sparse, dense])
     edges = edges[np.random.default_rng(seed).permutation(edges.shape[0])]
-    for mode in MODES:
-        check(pp, n1 + n2, 2, edges, opts=pp.options(kcore_mode=mode))
-    check(pp, n1 + n2, 2, edges, opts=pp.options(kcore_mode=0, host_loop=1))
+    assert edges.shape[0] >= 1 << 20
+    check_modes(pp, n1 + n2, 2, edges)
 
 
 def test_round_modes_small_first_frontier(pp):
