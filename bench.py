@@ -53,12 +53,20 @@ def hbm_peak():
         return FALLBACK_HBM_GBS, "fallback"
 
 
+# The sources the headline table's build and decode are compiled from (the
+# k-core, batch and server files do not reach those kernels).
+HEADLINE_SOURCES = ("common.cu", "device.cuh", "host.cuh", "iblt.cu", "iblt_binned.cuh", "iblt_kernels.cuh",
+                    "iblt_rounds.cuh", "iblt_tiles.cuh", "iblt_types.cuh", "tiles.cu")
+
+
 def csrc_digest() -> str:
     h = hashlib.sha256()
     d = os.path.join(ROOT, "paper_1302_7014_b300", "csrc")
-    for name in sorted(os.listdir(d)):
+    for name in HEADLINE_SOURCES:
         with open(os.path.join(d, name), "rb") as f:
             h.update(name.encode() + f.read())
+    with open(os.path.join(ROOT, "include", "ppeel.h"), "rb") as f:
+        h.update(b"ppeel.h" + f.read())
     return h.hexdigest()[:16]
 
 
@@ -509,6 +517,59 @@ def bench_tables(pp, torch, args):
     return out
 
 
+def profile_case(pp, torch, args, cfg):
+    """One call of a secondary workload, two warm-up calls before it, for a
+    profiler's launch list or capture (--host-loop drives its rounds from the
+    host, which ncu needs to see the round kernels one by one)."""
+    opts = pp.options(host_loop=1 if args.host_loop else 0)
+    stream = torch.cuda.Stream()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    if args.profile_case == "kcore":
+        sw = ppgen.DENSITY_SWEEP
+        n, r, k = sw["n"], sw["r"], sw["k"]
+        e = ppgen.partitioned_edges(n, r, ppgen.edges_from_c(args.profile_c, n), sw["seed"])
+        d = torch.from_numpy(e.view(np.int32)).cuda()
+        call = lambda: pp.peel_kcore(n, r, k, d, opts=opts, stream=stream)
+        what = f"pp_peel_kcore, {sw['name']}, c={args.profile_c}"
+    elif args.profile_case == "batched":
+        import paper_1302_7014_b300.batch as pb
+        tabs = ppgen.batch_tables(4096)
+        keys = [t.keys() for t in tabs]
+        koff = np.concatenate([[0], np.cumsum([x.size for x in keys])]).astype(np.uint64)
+        dk = torch.from_numpy(np.concatenate(keys).view(np.int64)).cuda()
+        out = torch.empty(int(koff[-1]), dtype=torch.int64, device="cuda")
+        b = pb.Batch([t.n_cells for t in tabs], [t.r for t in tabs], [t.table_seed for t in tabs], opts)
+
+        def call():
+            b.build(dk, koff, stream)
+            return b.decode(out, koff, stream=stream)
+        what = "pp_batch_build + pp_batch_decode, 4096 tables"
+    else:
+        n, r = cfg["n_cells"], cfg["r"]
+        na, nb, nc = int(0.45 * n), int(0.30 * n), int(0.25 * n)
+        keys = ppgen.distinct_keys(na + nb + nc, 31)
+        dk = torch.from_numpy(keys.view(np.int64)).cuda()
+        out = torch.empty(na + nb, dtype=torch.int64, device="cuda")
+        sg = torch.empty(na + nb, dtype=torch.int8, device="cuda")
+        t = pp.IBLT(n, r, 0x5195, opts)
+
+        def call():
+            t.build(dk[:nc + na], stream)
+            t.delete(dk[:nc], stream)
+            t.delete(dk[nc + na:], stream)
+            return t.decode_signed(out, sg, stream=stream)
+        what = f"build + pp_iblt_decode_signed, 2^{args.cells_log2} cells"
+    for _ in range(2):
+        call()
+    torch.cuda.synchronize()
+    ev[0].record(stream)
+    call()
+    ev[1].record(stream)
+    stream.synchronize()
+    print(json.dumps({"profile_case": args.profile_case, "call": what, "ms": ev[0].elapsed_time(ev[1]),
+                      "host_loop": bool(args.host_loop)}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -525,6 +586,10 @@ def main():
                     help="drive rounds from the host (kernels launched one by one, as profilers need)")
     ap.add_argument("--cells-log2", type=int, default=26,
                     help="table size for profiling runs (the benchmark itself is 2^26)")
+    ap.add_argument("--profile-case", choices=["kcore", "batched", "signed"],
+                    help="for profilers: run one call of a secondary workload after two warm-up "
+                         "calls, print its time and exit (no benchmark line)")
+    ap.add_argument("--profile-c", type=float, default=0.70, help="density of --profile-case kcore")
     args = ap.parse_args()
     cfg = dict(ppgen.IBLT_HEADLINE)
     if args.cells_log2 != 26:
@@ -536,6 +601,10 @@ def main():
 
     import torch
     import paper_1302_7014_b300 as pp
+
+    if args.profile_case:
+        profile_case(pp, torch, args, cfg)
+        return
 
     world, rank, local = dist_setup()
     torch.cuda.set_device(local)
