@@ -524,6 +524,23 @@ def profile_case(pp, torch, args, cfg):
     opts = pp.options(host_loop=1 if args.host_loop else 0)
     stream = torch.cuda.Stream()
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    if args.profile_case == "served":
+        # a burst of 2000 requests of the served mix, submitted at once
+        import paper_1302_7014_b300.server as ps
+        srv = ps.Server(arena_cells=1 << 29, arena_keys=1 << 29, max_slots=8192, r=3)
+        reqs = ppgen.serving_requests(2000)
+        for at, spec in reqs[:4]:
+            srv.wait(srv.submit(spec.n_cells, 3, spec.table_seed, spec.m, key_seed=spec.key_seed), 120.0)
+        it0 = srv.stats()["iterations"]
+        t0 = time.time()
+        tickets = [srv.submit(spec.n_cells, 3, spec.table_seed, spec.m, key_seed=spec.key_seed) for _, spec in reqs]
+        keys = sum(srv.wait(t, 600.0)["recovered"] for t in tickets)
+        dt = time.time() - t0
+        its = srv.stats()["iterations"] - it0
+        srv.stop()
+        print(json.dumps({"profile_case": "served", "requests": len(reqs), "s": dt, "keys_per_s": keys / dt,
+                          "iterations": its, "ms_per_iteration": dt * 1e3 / max(its, 1)}))
+        return
     if args.profile_case == "kcore":
         sw = ppgen.DENSITY_SWEEP
         n, r, k = sw["n"], sw["r"], sw["k"]
@@ -586,7 +603,7 @@ def main():
                     help="drive rounds from the host (kernels launched one by one, as profilers need)")
     ap.add_argument("--cells-log2", type=int, default=26,
                     help="table size for profiling runs (the benchmark itself is 2^26)")
-    ap.add_argument("--profile-case", choices=["kcore", "batched", "signed"],
+    ap.add_argument("--profile-case", choices=["kcore", "batched", "signed", "served"],
                     help="for profilers: run one call of a secondary workload after two warm-up "
                          "calls, print its time and exit (no benchmark line)")
     ap.add_argument("--profile-c", type=float, default=0.70, help="density of --profile-case kcore")
