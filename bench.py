@@ -531,15 +531,18 @@ def profile_case(pp, torch, args, cfg):
         reqs = ppgen.serving_requests(2000)
         for at, spec in reqs[:4]:
             srv.wait(srv.submit(spec.n_cells, 3, spec.table_seed, spec.m, key_seed=spec.key_seed), 120.0)
-        it0 = srv.stats()["iterations"]
+        st0 = srv.stats()
         t0 = time.time()
         tickets = [srv.submit(spec.n_cells, 3, spec.table_seed, spec.m, key_seed=spec.key_seed) for _, spec in reqs]
         keys = sum(srv.wait(t, 600.0)["recovered"] for t in tickets)
         dt = time.time() - t0
-        its = srv.stats()["iterations"] - it0
+        st = srv.stats()
+        its = st["iterations"] - st0["iterations"]
+        it_us = st["iteration_us"] - st0["iteration_us"]
         srv.stop()
         print(json.dumps({"profile_case": "served", "requests": len(reqs), "s": dt, "keys_per_s": keys / dt,
-                          "iterations": its, "ms_per_iteration": dt * 1e3 / max(its, 1)}))
+                          "iterations": its, "ms_per_iteration": dt * 1e3 / max(its, 1),
+                          "gpu_wait_share": (st["gpu_wait_us"] - st0["gpu_wait_us"]) / max(it_us, 1)}))
         return
     if args.profile_case == "kcore":
         sw = ppgen.DENSITY_SWEEP

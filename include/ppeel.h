@@ -413,6 +413,8 @@ typedef struct pp_request_result {
 
 typedef struct pp_server_stats {
   uint64_t submitted, admitted, completed, rejected, pending, active, iterations, keys_recovered;
+  uint64_t iteration_us;  /* time spent in device iterations (launch to completion handling) */
+  uint64_t gpu_wait_us;   /* part of it the server thread spent waiting for the GPU */
 } pp_server_stats;
 
 /* Monotonic clock (seconds) used for arrival and completion times. */

@@ -158,6 +158,7 @@ struct pp_server {
   pp_status failed = PP_OK;
   std::string fail_msg;
   pp_server_stats stats{};
+  double iter_s = 0, gpu_wait_s = 0;  // server thread only
   std::thread thread;
 };
 
@@ -352,7 +353,11 @@ bool iterate(pp_server *s, std::vector<Job *> &admit, pp_status &err) {
   SV_CUDA(cudaMemcpyAsync(s->h_recovered, s->bc.recovered, S * sizeof(u64), cudaMemcpyDeviceToHost, st));
   SV_CUDA(cudaMemcpyAsync(s->h_nonempty, s->bc.nonempty, S * sizeof(u64), cudaMemcpyDeviceToHost, st));
   SV_CUDA(cudaMemcpyAsync(s->h_emptied, s->bc.emptied, S * sizeof(u64), cudaMemcpyDeviceToHost, st));
-  SV_CUDA(cudaStreamSynchronize(st));
+  {
+    const double w0 = now_s();
+    SV_CUDA(cudaStreamSynchronize(st));
+    s->gpu_wait_s += now_s() - w0;
+  }
   if (s->h_ctl->flags & (FLAG_CAPACITY | FLAG_INTERNAL)) {
     err = fail(PP_ERR_CUDA, "server: device flags 0x%x", s->h_ctl->flags);
     return false;
@@ -440,12 +445,15 @@ void server_main(pp_server *s) {
       s->stats.pending = s->queue.size();
     }
     for (Job *j : admit) s->active.push_back(j);
+    const double t0 = now_s();
     if (!iterate(s, admit, err)) break;
+    complete_finished(s, err);
     {
       std::lock_guard<std::mutex> lock(s->mu);
       s->stats.iterations++;
+      s->stats.iteration_us = (uint64_t)((s->iter_s += now_s() - t0) * 1e6);
+      s->stats.gpu_wait_us = (uint64_t)(s->gpu_wait_s * 1e6);
     }
-    complete_finished(s, err);
     if (err != PP_OK) break;
   }
   std::lock_guard<std::mutex> lock(s->mu);

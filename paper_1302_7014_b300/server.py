@@ -28,7 +28,7 @@ class RequestResult(ctypes.Structure):
 
 class ServerStats(ctypes.Structure):
     _fields_ = [(n, u64) for n in ("submitted", "admitted", "completed", "rejected", "pending", "active",
-                                   "iterations", "keys_recovered")]
+                                   "iterations", "keys_recovered", "iteration_us", "gpu_wait_us")]
 
 
 _lib.declare("pp_server_now", dbl, [])
