@@ -65,8 +65,6 @@ def csrc_digest() -> str:
     for name in HEADLINE_SOURCES:
         with open(os.path.join(d, name), "rb") as f:
             h.update(name.encode() + f.read())
-    with open(os.path.join(ROOT, "include", "ppeel.h"), "rb") as f:
-        h.update(b"ppeel.h" + f.read())
     return h.hexdigest()[:16]
 
 
