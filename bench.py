@@ -790,10 +790,16 @@ def main():
     }
     dom = "decode" if d_ms >= b_ms else "build"
     dk = kernels[dom]
+    traffic = traffic_for(dom)
     roofline = {"bound": "hbm", "achieved": dk["achieved_gbs"], "peak": peak, "unit": "GB/s",
-                "frac": dk["achieved_gbs"] / peak, "traffic": traffic_for(dom),
+                "frac": dk["achieved_gbs"] / peak, "traffic": traffic,
                 "kernel": dk["kernel"], "peak_source": f"{peak_kind} hbm_gbs",
                 "model": "sector floor: 32 B/cell scan + (64r+8) B/key decode; (8+64r) B/key build"}
+    if traffic:
+        # DRAM bytes the unit actually moves (ncu, committed summary) over the same time:
+        # a random 32 B touch costs a 64 B read and its write-back, twice the model
+        roofline["dram_gbs"] = traffic / (dk["ms"] * 1e-3) / 1e9
+        roofline["dram_frac"] = roofline["dram_gbs"] / peak
 
     batched = served = subrounds = kcore = tables = signed = None
     if world == 1 and not args.no_extra:
