@@ -95,6 +95,8 @@ def test_admission_by_free_memory(srv_mod):
         _check(s.wait(t, 60.0), sp, keys)
     st = s.stats()
     assert st["admitted"] == 40 and st["iterations"] > 40
+    # time accounting: every iteration waits on the GPU for part of its time
+    assert 0 < st["gpu_wait_us"] <= st["iteration_us"]
     s.stop()
 
 
