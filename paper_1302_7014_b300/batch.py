@@ -19,6 +19,36 @@ class TableResult(ctypes.Structure):
                 ("recovered_per_round", ctypes.POINTER(u64))]
 
 
+# The same record as a NumPy dtype: a batch's results are filled and read as
+# columns instead of one ctypes object per table.
+_RESULT_DTYPE = np.dtype([("rounds", "<u4"), ("stats_complete", "<u4"), ("recovered", "<u8"),
+                          ("items_before", "<u8"), ("residual_cells", "<u8"), ("round_cap", "<u4"),
+                          ("pad", "<u4"), ("recovered_per_round", "<u8")])
+assert _RESULT_DTYPE.itemsize == ctypes.sizeof(TableResult)
+assert all(_RESULT_DTYPE.fields[name][1] == getattr(TableResult, name).offset
+           for name, _ in TableResult._fields_)
+
+
+class PerRoundCounts:
+    """recovered_per_round of a batch: entry i is table i's list of per-round
+    counts, sliced from one (tables x round_cap) array when it is read."""
+
+    def __init__(self, per_round: np.ndarray, rounds: np.ndarray):
+        self._a = per_round
+        self._n = np.minimum(rounds, per_round.shape[1])
+
+    def __len__(self):
+        return self._a.shape[0]
+
+    def __getitem__(self, i):
+        if isinstance(i, slice):
+            return [self[j] for j in range(*i.indices(len(self)))]
+        return self._a[i, : self._n[i]].tolist()
+
+    def __iter__(self):
+        return (self[i] for i in range(len(self)))
+
+
 _lib.declare("pp_batch_create", ctypes.c_int, [ctypes.POINTER(vp), u32, ctypes.POINTER(u64),
                                                ctypes.POINTER(u32), ctypes.POINTER(u64),
                                                ctypes.POINTER(Options)])
@@ -38,7 +68,7 @@ class BatchOutcome:
     recovered: np.ndarray
     items_before: np.ndarray
     residual_cells: np.ndarray
-    recovered_per_round: list   # per table: list of per-round counts
+    recovered_per_round: PerRoundCounts   # per table: list of per-round counts
     stats_complete: np.ndarray
 
 
@@ -101,22 +131,23 @@ class Batch:
     def decode(self, out, out_offsets, round_cap: int = 256, stream=None) -> BatchOutcome:
         off, off_p = _u64_array(out_offsets)
         n = self.n_tables
-        results = (TableResult * n)()
         per_round = np.zeros((n, round_cap), dtype=np.uint64)
-        for i in range(n):
-            results[i].round_cap = round_cap
-            results[i].recovered_per_round = per_round[i].ctypes.data_as(ctypes.POINTER(u64))
+        results = np.zeros(n, dtype=_RESULT_DTYPE)
+        results["round_cap"] = round_cap
+        results["recovered_per_round"] = (np.uint64(per_round.ctypes.data)
+                                          + np.arange(n, dtype=np.uint64) * np.uint64(round_cap * 8))
         ptr = _dev_ptr(out, 8, "out") if out is not None and out.numel() else None
-        _check(_lib.load().pp_batch_decode(self._h, ptr, off_p, results, _stream_ptr(stream)),
-               "pp_batch_decode")
-        rounds = np.array([results[i].rounds for i in range(n)], dtype=np.int64)
+        _check(_lib.load().pp_batch_decode(self._h, ptr, off_p,
+                                           ctypes.cast(results.ctypes.data, ctypes.POINTER(TableResult)),
+                                           _stream_ptr(stream)), "pp_batch_decode")
+        rounds = results["rounds"].astype(np.int64)
         return BatchOutcome(
             rounds=rounds,
-            recovered=np.array([results[i].recovered for i in range(n)], dtype=np.int64),
-            items_before=np.array([results[i].items_before for i in range(n)], dtype=np.int64),
-            residual_cells=np.array([results[i].residual_cells for i in range(n)], dtype=np.int64),
-            recovered_per_round=[per_round[i, : min(rounds[i], round_cap)].tolist() for i in range(n)],
-            stats_complete=np.array([results[i].stats_complete for i in range(n)], dtype=bool))
+            recovered=results["recovered"].astype(np.int64),
+            items_before=results["items_before"].astype(np.int64),
+            residual_cells=results["residual_cells"].astype(np.int64),
+            recovered_per_round=PerRoundCounts(per_round, rounds),
+            stats_complete=results["stats_complete"].astype(bool))
 
     def cells(self, table: int):
         dt = np.dtype([("key_xor", "<u8"), ("chk_xor", "<u8"), ("count", "<i4"), ("reserved", "<u4", 3)])
