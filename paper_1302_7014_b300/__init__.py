@@ -159,20 +159,20 @@ class IBLT:
                             "pp_iblt_decode_signed", out, round_cap, stream)
 
     def _decode(self, fn, name, out, round_cap, stream) -> DecodeOutcome:
-        rec = (ctypes.c_uint64 * round_cap)()
-        rem = (ctypes.c_uint64 * round_cap)()
-        alive = (ctypes.c_uint64 * round_cap)()
+        import numpy as np
+        stats = np.empty((3, round_cap), dtype=np.uint64)  # filled up to the round count
+        base = stats.ctypes.data
         res = DecodeResult()
         res.round_cap = round_cap
-        res.recovered_per_round = ctypes.cast(rec, ctypes.POINTER(ctypes.c_uint64))
-        res.remaining_per_round = ctypes.cast(rem, ctypes.POINTER(ctypes.c_uint64))
-        res.alive_cells_per_round = ctypes.cast(alive, ctypes.POINTER(ctypes.c_uint64))
+        res.recovered_per_round = ctypes.cast(base, ctypes.POINTER(ctypes.c_uint64))
+        res.remaining_per_round = ctypes.cast(base + round_cap * 8, ctypes.POINTER(ctypes.c_uint64))
+        res.alive_cells_per_round = ctypes.cast(base + 2 * round_cap * 8, ctypes.POINTER(ctypes.c_uint64))
         st = fn(self._h, _dev_ptr(out, 8, "out"), out.numel() if out is not None else 0, ctypes.byref(res),
                 _stream_ptr(stream))
         _check(st, name)
         n = min(res.rounds, round_cap)
         return DecodeOutcome(res.rounds, res.recovered, res.items_before, res.residual_cells,
-                             res.status_flags, list(rec[:n]), list(rem[:n]), list(alive[:n]))
+                             res.status_flags, stats[0, :n].tolist(), stats[1, :n].tolist(), stats[2, :n].tolist())
 
     def cells(self, stream=None):
         """Host copy of the table as a numpy structured array (key_xor, chk_xor, count)."""
@@ -239,12 +239,12 @@ def _peel(n, r, k, edges, part_off, vertex_round, edge_round, opts, round_cap, s
     m = edges.shape[0] if edges is not None and edges.numel() else 0
     if edges is not None and edges.numel() and (edges.dim() != 2 or edges.shape[1] != r):
         raise ValueError("edges must have shape (m, r)")
-    s_left = (ctypes.c_uint64 * round_cap)()
-    m_left = (ctypes.c_uint64 * round_cap)()
+    import numpy as np
+    stats = np.empty((2, round_cap), dtype=np.uint64)  # filled up to the round count
     res = PeelResult()
     res.round_cap = round_cap
-    res.vertices_left = ctypes.cast(s_left, ctypes.POINTER(ctypes.c_uint64))
-    res.edges_left = ctypes.cast(m_left, ctypes.POINTER(ctypes.c_uint64))
+    res.vertices_left = ctypes.cast(stats.ctypes.data, ctypes.POINTER(ctypes.c_uint64))
+    res.edges_left = ctypes.cast(stats.ctypes.data + round_cap * 8, ctypes.POINTER(ctypes.c_uint64))
     common = (_dev_ptr(vertex_round, 4, "vertex_round"), _dev_ptr(edge_round, 4, "edge_round"),
               ctypes.byref(res), ctypes.byref(opts) if opts is not None else None, _stream_ptr(stream))
     e_ptr = _dev_ptr(edges, 4, "edges") if m else None
@@ -259,4 +259,4 @@ def _peel(n, r, k, edges, part_off, vertex_round, edge_round, opts, round_cap, s
         _check(st, "pp_peel_kcore_subrounds")
     nr = min(res.rounds, round_cap)
     return PeelOutcome(res.rounds, res.core_vertices, res.core_edges, res.status_flags,
-                       list(s_left[:nr]), list(m_left[:nr]))
+                       stats[0, :nr].tolist(), stats[1, :nr].tolist())
