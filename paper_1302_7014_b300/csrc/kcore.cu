@@ -734,6 +734,7 @@ struct KWork {
   u32 *deg = nullptr, *off = nullptr, *cursor = nullptr, *inc = nullptr, *alive = nullptr;
   u32 *f0 = nullptr, *f1 = nullptr;
   u32 *deg16 = nullptr, *ovf = nullptr;
+  void *block = nullptr;  // the buffers below up to scan_tmp live in it
   u32 *rows[2] = {nullptr, nullptr}, *ids[2] = {nullptr, nullptr}, *fb[2] = {nullptr, nullptr};
   PeelCtl *ctl = nullptr;
   SubCtl *sub = nullptr;
@@ -1132,9 +1133,14 @@ static pp_status peel_kcore_impl(uint32_t n, uint32_t r, uint32_t k, const uint3
   KWork w;
   const u64 nn = n ? n : 1, mm = m ? m : 1;
   cudaError_t e = cudaSuccess;
-  auto al = [&](void **p, size_t b) {
-    if (e == cudaSuccess) e = ws_alloc(p, b, s);
+  // one workspace block, carved into 256-byte aligned buffers
+  struct Part {
+    void **p;
+    size_t bytes;
   };
+  Part parts_list[16];
+  int np_ = 0;
+  auto al = [&](void **p, size_t b) { parts_list[np_++] = Part{p, (b + 255) & ~(size_t)255}; };
   al((void **)&w.deg, nn * 4);
   al((void **)&w.off, (nn + 1) * 4);
   al((void **)&w.cursor, nn * 4);
@@ -1149,6 +1155,18 @@ static pp_status peel_kcore_impl(uint32_t n, uint32_t r, uint32_t k, const uint3
   al((void **)&w.st_s, (size_t)o.max_rounds * 8);
   al((void **)&w.st_m, (size_t)o.max_rounds * 8);
   al(&w.scan_tmp, exclusive_scan_temp_bytes(nn));
+  {
+    size_t total = 0;
+    for (int i = 0; i < np_; ++i) total += parts_list[i].bytes;
+    e = ws_alloc(&w.block, total, s);
+    if (e == cudaSuccess) {
+      char *q = static_cast<char *>(w.block);
+      for (int i = 0; i < np_; ++i) {
+        *parts_list[i].p = q;
+        q += parts_list[i].bytes;
+      }
+    }
+  }
   pp_status status = PP_OK;
   PeelCtl hc{};
   SubCtl hsub{};
@@ -1360,25 +1378,12 @@ cleanup:
   auto fr = [&](void *p) {
     if (p) cudaFreeAsync(p, s);
   };
-  fr(w.deg);
-  fr(w.deg16);
-  fr(w.ovf);
   for (int b = 0; b < 2; ++b) {
     fr(w.rows[b]);
     fr(w.ids[b]);
     fr(w.fb[b]);
   }
-  fr(w.off);
-  fr(w.cursor);
-  fr(w.inc);
-  fr(w.alive);
-  fr(w.f0);
-  fr(w.f1);
-  fr(w.ctl);
-  fr(w.sub);
-  fr(w.st_s);
-  fr(w.st_m);
-  fr(w.scan_tmp);
+  fr(w.block);
   cudaStreamSynchronize(s);
   return status;
 }
