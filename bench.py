@@ -787,7 +787,7 @@ def main():
     # roofline of the two halves of a step (sector-floor byte model)
     peak, peak_kind = hbm_peak()
     build_bytes = m * (8 + 64 * r)                 # key read + r cell sectors read+written
-    decode_bytes = n * 32 + m * (64 * r + 8)       # one full scan + r sector RMW + key out
+    decode_bytes = n * 16 + m * (64 * r + 8)       # one full scan of the 16 B cells + r sector RMW + key out
     b_ms, d_ms = float(np.mean(build_ms)), float(np.mean(decode_ms))
     kernels = {
         "build": {"kernel": "k_bin + k_tile_step per slab (slab-binned, tiles in shared memory)", "ms": b_ms,
@@ -802,10 +802,10 @@ def main():
     roofline = {"bound": "hbm", "achieved": dk["achieved_gbs"], "peak": peak, "unit": "GB/s",
                 "frac": dk["achieved_gbs"] / peak, "traffic": traffic,
                 "kernel": dk["kernel"], "peak_source": f"{peak_kind} hbm_gbs",
-                "model": "sector floor: 32 B/cell scan + (64r+8) B/key decode; (8+64r) B/key build"}
+                "model": "sector floor: 16 B/cell scan + (64r+8) B/key decode; (8+64r) B/key build"}
     if traffic:
         # DRAM bytes the unit actually moves (ncu, committed summary) over the same time:
-        # a random 32 B touch costs a 64 B read and its write-back, twice the model
+        # a random touch of a 32 B sector costs a 64 B read and its write-back, twice the model
         roofline["dram_gbs"] = traffic / (dk["ms"] * 1e-3) / 1e9
         roofline["dram_frac"] = roofline["dram_gbs"] / peak
 

@@ -86,26 +86,31 @@ const char *pp_last_error(void);
 /* ------------------------------------------------------------------------
  * IBLT (Sec. 6 "Motivation" and "Implementation Details"; App. B layout)
  *
- * Cell layout in device memory (32 bytes, 32-byte aligned, cell i at
- * byte 32*i of the table):
- *     uint64 key_xor;   XOR of the keys in the cell
- *     uint64 chk_xor;   XOR of checkSum(key) of those keys
- *     int32  count;     number of keys in the cell (inserts - deletes)
- *     uint32 reserved[3];
+ * Cell layout in device memory (16 bytes, 16-byte aligned, cell i at
+ * byte 16*i of the table):
+ *     uint64 key_xor;    XOR of the keys in the cell
+ *     uint64 count_chk;  the count and the checksum sum in one word: the sum,
+ *                        mod 2^64, of s * (checkSum(x) * 2^32 + 1) over the
+ *                        cell's keys x, s = +1 for an insertion and -1 for a
+ *                        deletion.  Its low 32 bits are the count (inserts -
+ *                        deletes, two's complement int32); the checksum sum
+ *                        S = sum of s * checkSum(x) mod 2^32 is
+ *                        (count_chk - (int64)count) >> 32.
  * Cells are split into r sub-tables, in order; sub-table j holds
  * floor(n/r) + [j < n mod r] cells.  Key x lives in cell
  *     off_j + floor(mix64(x ^ s_j) * size_j / 2^64)   of each sub-table j,
- * and checkSum(x) = mix64(x ^ s_r), where mix64 is the SplitMix64 finaliser
- * and s_0..s_r are outputs 1..r+1 of SplitMix64 started at the table seed.
- * A cell is pure iff count == 1 and chk_xor == checkSum(key_xor).
+ * and checkSum(x) = the upper 32 bits of mix64(x ^ s_r), where mix64 is the
+ * SplitMix64 finaliser and s_0..s_r are outputs 1..r+1 of SplitMix64 started
+ * at the table seed.  A cell is pure iff count == 1 and S == checkSum(key_xor),
+ * that is iff count_chk == checkSum(key_xor) * 2^32 + 1.  The signed decode
+ * also takes count == -1 with S == -checkSum(key_xor) mod 2^32 (count_chk ==
+ * -(checkSum(key_xor) * 2^32 + 1) mod 2^64).
  * ------------------------------------------------------------------------ */
 typedef struct pp_iblt pp_iblt;
 
 typedef struct pp_cell {
   uint64_t key_xor;
-  uint64_t chk_xor;
-  int32_t count;
-  uint32_t reserved[3];
+  uint64_t count_chk;
 } pp_cell;
 
 /* Result of a decode.  The caller sets round_cap and the three array pointers
@@ -130,7 +135,7 @@ typedef struct pp_decode_result {
 } pp_decode_result;
 
 /* Creates an empty (all-zero) table of n_cells cells for r hash functions.
- * Allocates the table (32 B/cell) and the decode workspace (~17 B/cell).
+ * Allocates the table (16 B/cell) and the decode workspace (~17 B/cell).
  * Errors: INVALID_ARG (r outside 2..PP_MAX_R, n_cells < r or too large),
  * OUT_OF_MEMORY, CUDA. */
 pp_status pp_iblt_create(pp_iblt **out, uint64_t n_cells, uint32_t r, uint64_t seed,
@@ -141,7 +146,7 @@ pp_status pp_iblt_destroy(pp_iblt *t);
 
 /* Device memory of a table of n_cells cells and r hash functions (host only,
  * no device call; opt as for pp_iblt_create, NULL = defaults):
- *   *table_bytes  the cells, 32 B each;
+ *   *table_bytes  the cells, 16 B each;
  *   *fixed_bytes  the decode workspace allocated by pp_iblt_create;
  *   *peak_bytes   all the handle holds after pp_iblt_create, a pp_iblt_build
  *                 or pp_iblt_insert of m_keys keys and a pp_iblt_decode: the

@@ -24,7 +24,7 @@ from ._lib import PP_MAX_R, Cell, DecodeResult, Options, PeelResult
 
 __all__ = ["PPError", "IBLT", "iblt_create", "iblt_insert", "iblt_delete", "iblt_build", "iblt_decode",
            "iblt_decode_subrounds", "iblt_decode_signed", "peel_kcore", "peel_kcore_subrounds", "options",
-           "workspace_size", "PP_MAX_R"]
+           "workspace_size", "PP_MAX_R", "CELL_DTYPE", "unpack_cells"]
 
 
 class PPError(RuntimeError):
@@ -32,6 +32,25 @@ class PPError(RuntimeError):
         self.status = status
         self.name = _lib.STATUS.get(status, f"status {status}")
         super().__init__(f"{fn}: {self.name}: {msg}")
+
+
+# A pp_cell as stored on the device, and its fields split out for reading.
+CELL_DTYPE = [("key_xor", "<u8"), ("count_chk", "<u8")]
+CELL_FIELDS_DTYPE = [("key_xor", "<u8"), ("count", "<i4"), ("chk_sum", "<u4")]
+
+
+def unpack_cells(raw):
+    """Splits stored cells (CELL_DTYPE) into key_xor, count and chk_sum: count is
+    the low 32 bits of count_chk, chk_sum = (count_chk - count) >> 32."""
+    import numpy as np
+    raw = np.asarray(raw).view(np.dtype(CELL_DTYPE))
+    cc = raw["count_chk"]
+    count = (cc & np.uint64(0xFFFFFFFF)).astype(np.uint32).view(np.int32)
+    out = np.empty(raw.shape, dtype=np.dtype(CELL_FIELDS_DTYPE))
+    out["key_xor"] = raw["key_xor"]
+    out["count"] = count
+    out["chk_sum"] = ((cc - count.astype(np.int64).view(np.uint64)) >> np.uint64(32)).astype(np.uint32)
+    return out
 
 
 def _check(status: int, fn: str):
@@ -175,14 +194,14 @@ class IBLT:
                              res.status_flags, stats[0, :n].tolist(), stats[1, :n].tolist(), stats[2, :n].tolist())
 
     def cells(self, stream=None):
-        """Host copy of the table as a numpy structured array (key_xor, chk_xor, count)."""
+        """Host copy of the table as a numpy structured array (key_xor, count,
+        chk_sum); see unpack_cells."""
         import numpy as np
-        dt = np.dtype([("key_xor", "<u8"), ("chk_xor", "<u8"), ("count", "<i4"), ("reserved", "<u4", 3)])
-        out = np.zeros(self.n_cells, dtype=dt)
+        out = np.zeros(self.n_cells, dtype=np.dtype(CELL_DTYPE))
         _check(_lib.load().pp_iblt_copy_cells(self._h, ctypes.c_void_p(out.ctypes.data), 0,
                                               self.n_cells, 1, _stream_ptr(stream)),
                "pp_iblt_copy_cells")
-        return out
+        return unpack_cells(out)
 
     def seeds(self) -> list[int]:
         n = ctypes.c_uint64()

@@ -40,7 +40,8 @@ class PeelResult(ctypes.Structure):
 
 
 class Cell(ctypes.Structure):
-    _fields_ = [("key_xor", u64), ("chk_xor", u64), ("count", i32), ("reserved", u32 * 3)]
+    # count_chk: the count (low 32 bits) and the checksum sum in one word, see pp_cell
+    _fields_ = [("key_xor", u64), ("count_chk", u64)]
 
 
 _SIGNATURES = {

@@ -7,7 +7,7 @@ from dataclasses import dataclass
 import numpy as np
 
 from . import _lib
-from . import _check, _dev_ptr, _stream_ptr
+from . import CELL_DTYPE, _check, _dev_ptr, _stream_ptr, unpack_cells
 from ._lib import Options
 
 u32, u64, vp = ctypes.c_uint32, ctypes.c_uint64, ctypes.c_void_p
@@ -150,11 +150,10 @@ class Batch:
             stats_complete=results["stats_complete"].astype(bool))
 
     def cells(self, table: int):
-        dt = np.dtype([("key_xor", "<u8"), ("chk_xor", "<u8"), ("count", "<i4"), ("reserved", "<u4", 3)])
-        out = np.zeros(self.n_cells[table], dtype=dt)
+        out = np.zeros(self.n_cells[table], dtype=np.dtype(CELL_DTYPE))
         _check(_lib.load().pp_batch_copy_cells(self._h, table, ctypes.c_void_p(out.ctypes.data), 1,
                                                _stream_ptr(None)), "pp_batch_copy_cells")
-        return out
+        return unpack_cells(out)
 
 
 # Function-style names matching the C ABI.

@@ -22,15 +22,18 @@ enum : u32 {
   FLAG_INTERNAL = 8u      // an invariant failed (frontier cell not among its key's cells)
 };
 
-// One IBLT cell: 32 bytes, so a random touch costs one DRAM sector.
-struct __align__(32) Cell {
-  u64 key;    // XOR of the keys in the cell
-  u64 chk;    // XOR of checkSum(key)
-  int count;  // keys in the cell
-  u32 pad[3];
+// One IBLT cell: 16 bytes, two to a 32-byte sector.  cw holds the count and
+// the checksum sum in one word: sum of s * (checkSum(x) * 2^32 + 1) mod 2^64
+// over the cell's keys (s = +1 inserted, -1 deleted), so its low 32 bits are
+// the count and one 64-bit atomic add updates both fields.
+struct __align__(16) Cell {
+  u64 key;  // XOR of the keys in the cell
+  u64 cw;   // count (low 32 bits) and checksum sum, see above
 };
-static_assert(sizeof(Cell) == 32, "cell must be one 32-byte sector");
+static_assert(sizeof(Cell) == 16, "cell must be 16 bytes");
 static_assert(sizeof(Cell) == sizeof(pp_cell), "public and device cell layouts differ");
+
+__host__ __device__ __forceinline__ int cell_count(u64 cw) { return (int)(u32)cw; }
 
 // SplitMix64 output finaliser (Steele, Lea & Flood 2014): the hash family of
 // the IBLT (cell positions and checksums).
@@ -38,6 +41,13 @@ __host__ __device__ __forceinline__ u64 mix64(u64 z) {
   z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
   z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
   return z ^ (z >> 31);
+}
+
+// The word one inserted key adds to its cells' cw: checkSum(x) * 2^32 + 1,
+// checkSum(x) being the upper 32 bits of mix64(x ^ seed_chk).  A cell holding
+// exactly x has cw == cell_word(x); holding exactly a deleted x, cw == -cell_word(x).
+__host__ __device__ __forceinline__ u64 cell_word(u64 x, u64 seed_chk) {
+  return (mix64(x ^ seed_chk) & 0xFFFFFFFF00000000ULL) | 1ULL;
 }
 
 // Per-table constants.  Sub-table j is cells base+off[j] .. base+off[j+1]-1.

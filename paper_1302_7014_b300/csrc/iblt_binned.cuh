@@ -20,11 +20,10 @@
 namespace pp {
 
 template <int R>
-__device__ __forceinline__ void apply_touch(Cell *cells, u32 c, u64 x, u64 cx, int sign) {
+__device__ __forceinline__ void apply_touch(Cell *cells, u32 c, u64 x, u64 w, int sign) {
   Cell *p = cells + c;
-  atomicAdd(&p->count, sign);
+  atomicAdd(&p->cw, sign > 0 ? w : 0ull - w);
   atomicXor(&p->key, x);
-  atomicXor(&p->chk, cx);
 }
 
 // Dynamic shared memory: 3 * n_slabs u32 (histogram, scan, base) + the staged
@@ -144,7 +143,7 @@ __global__ void __launch_bounds__(kBlock, 5) k_bin(Cell *__restrict__ cells, con
         } else if (b.direct_overflow) {
           const TableArgs &TT = BATCH ? tabs[s_tab[p]] : tab0;
           const u64 xx = s_key[p];
-          apply_touch<R>(cells, s_cell[p], xx, mix64(xx ^ TT.seed[rank_of<R>(TT)]), sign);
+          apply_touch<R>(cells, s_cell[p], xx, cell_word(xx, TT.seed[rank_of<R>(TT)]), sign);
         } else {
           *b.overflow = 1u;
         }

@@ -82,7 +82,7 @@ __global__ void k_count_sum(const Cell *__restrict__ cells, u64 n, long long *__
   __shared__ long long s_red[kBlock / 32];
   long long v = 0;
   for (u64 i = (u64)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (u64)gridDim.x * blockDim.x)
-    v += cells[i].count;
+    v += cell_count(cells[i].cw);
   const long long b = block_sum<long long, kBlock>(v, s_red);
   if (threadIdx.x == 0 && b) atomicAdd(reinterpret_cast<unsigned long long *>(sum), (unsigned long long)b);
 }

@@ -6,14 +6,15 @@
 //            was pure at the round's start (the same lowest-index rule as
 //            k_peel).  A winner writes x to the output and one update record
 //            (cell, key) per cell of x into the bin of that cell: bins are
-//            2^19 consecutive cells (16 MB).  Records are ordered by bin inside
+//            2^19 consecutive cells (8 MB).  Records are ordered by bin inside
 //            the block and leave it as contiguous runs.
 //   k_apply_round (phase B2) walks the records bin by bin: blocks take the next
 //            chunk of 1024 records from an atomic counter, so at any moment the
 //            whole GPU updates a narrow, moving window of the table and HBM
-//            sees near-sequential traffic.  Each update is atomicSub(count)
-//            and atomicXor(key, checksum); a count that drops from 2 to 1
-//            makes the cell a candidate for the next frontier.
+//            sees near-sequential traffic.  Each update is one 64-bit
+//            atomicAdd on the cell's count-and-checksum word and one
+//            atomicXor on its key; a count that drops from 2 to 1 makes the
+//            cell a candidate for the next frontier.
 // Updates commute, so the order of application does not change the state at
 // the end of the round; the claim decisions are all taken in B1, before any
 // update of the round lands.
@@ -23,11 +24,12 @@
 
 namespace pp {
 
-__device__ __forceinline__ int remove_key(Cell *cells, u32 c, u64 x, u64 cx, int sg = 1) {
+// Removes key x (cell word w = cell_word(x), sign sg) from cell c; returns the
+// cell's count before the removal.
+__device__ __forceinline__ int remove_key(Cell *cells, u32 c, u64 x, u64 w, int sg = 1) {
   Cell *p = cells + c;
-  const int old = atomicSub(&p->count, sg);
+  const int old = cell_count(atomicAdd(&p->cw, sg > 0 ? 0ull - w : w));
   atomicXor(&p->key, x);
-  atomicXor(&p->chk, cx);
   return old;
 }
 
@@ -231,7 +233,7 @@ __global__ void __launch_bounds__(kBlock, (!BATCH && R >= 3) ? 5 : 4) k_claim(Ce
         const u64 xx = s_key[p];
         const u32 cc = s_cell[p] & kCellMask;
         const int sgn = (SIGNED && (s_cell[p] >> 31)) ? -1 : 1;
-        const int old = remove_key(cells, cc, xx, mix64(xx ^ seed_chk), sgn);
+        const int old = remove_key(cells, cc, xx, cell_word(xx, seed_chk), sgn);
         if (becomes_candidate<SIGNED>(old, sgn)) {
           const u32 q = atomicAdd(&ctl->n_cand, 1u);
           if (!SIGNED || q < rb.cand_cap) cand[q] = cc;
@@ -354,7 +356,7 @@ __global__ void __launch_bounds__(kBlock) k_apply_round(Cell *__restrict__ cells
       seed_chk[k] = BATCH ? (v[k] ? bc.chk_seed[tb[k]] : 0ull) : tab0.seed[rank_of<R>(tab0)];
 #pragma unroll
     for (int k = 0; k < kApplyPer; ++k)
-      old[k] = v[k] ? remove_key(cells, c[k], x[k], mix64(x[k] ^ seed_chk[k]), sg[k]) : 0;
+      old[k] = v[k] ? remove_key(cells, c[k], x[k], cell_word(x[k], seed_chk[k]), sg[k]) : 0;
 #pragma unroll
     for (int k = 0; k < kApplyPer; ++k) {
       const bool push = v[k] && becomes_candidate<SIGNED>(old[k], sg[k]);
@@ -398,7 +400,7 @@ __global__ void __launch_bounds__(kBlock) k_residual(const Cell *__restrict__ ce
     const Chunk k = chunks[ch];
     if (bc.skip_full && bc.recovered[k.table] >= bc.items[k.table]) continue;  // uniform per block
     u64 nz = 0;
-    for (u32 c = k.begin + threadIdx.x; c < k.end; c += kBlock) nz += cells[c].count != 0;
+    for (u32 c = k.begin + threadIdx.x; c < k.end; c += kBlock) nz += cell_count(cells[c].cw) != 0;
     const u64 t = block_sum<u64, kBlock>(nz, s_red);
     if (threadIdx.x == 0 && t) atomicAdd(bc.residual + k.table, t);
   }

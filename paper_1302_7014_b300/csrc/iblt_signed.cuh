@@ -23,8 +23,10 @@
 
 namespace pp {
 
-__device__ __forceinline__ bool signed_pure(int cnt, u64 key, u64 chk, u64 seed_chk) {
-  return (cnt == 1 || cnt == -1) && chk == mix64(key ^ seed_chk);
+// Pure with sign +1 or -1: the cell's word is that of key alone, inserted or deleted.
+__device__ __forceinline__ bool signed_pure(u64 cw, u64 key, u64 seed_chk) {
+  const u64 w = cell_word(key, seed_chk);
+  return cw == w || cw == 0ull - w;
 }
 
 template <int R>
@@ -53,10 +55,9 @@ __global__ void __launch_bounds__(kBlock) k_sgscan(const Cell *__restrict__ cell
       int cnt = 0;
       if (c < end) {
         const uint4 a = __ldcs(reinterpret_cast<const uint4 *>(cells + c));
-        const uint4 b = __ldcs(reinterpret_cast<const uint4 *>(cells + c) + 1);
         key = ((u64)a.y << 32) | a.x;
-        cnt = (int)b.x;
-        pure = signed_pure(cnt, key, ((u64)a.w << 32) | a.z, seed_chk);
+        cnt = (int)a.z;
+        pure = signed_pure(((u64)a.w << 32) | a.z, key, seed_chk);
         nonempty += cnt != 0;
       }
       const u32 ball = __ballot_sync(kFull, pure);
@@ -143,14 +144,13 @@ __global__ void __launch_bounds__(kBlock) k_sgpeel(Cell *__restrict__ cells, con
       }
       if (win) {
         n_neg += sg < 0;
-        const u64 cx = mix64(x ^ tab0.seed[r]);
+        const u64 w = cell_word(x, tab0.seed[r]);
 #pragma unroll
         for (int j = 0; j < NR; ++j) {
           if (j < r) {
             Cell *p = cells + cj[j];
-            const int old = atomicSub(&p->count, sg);
+            const int old = cell_count(atomicAdd(&p->cw, sg > 0 ? 0ull - w : w));
             atomicXor(&p->key, x);
-            atomicXor(&p->chk, cx);
             const int now = old - sg;
             emptied += (u64)(long long)((old != 0) - (now != 0));
             if (now == 1 || now == -1) s_cand[atomicAdd(&s_ncand, 1u)] = cj[j];
@@ -218,10 +218,9 @@ __global__ void __launch_bounds__(kBlock) k_sgfilter(const Cell *__restrict__ ce
       if (i < n) {
         c = __ldcs(cand + i);
         const uint4 a = __ldcg(reinterpret_cast<const uint4 *>(cells + c));
-        const uint4 b = __ldcg(reinterpret_cast<const uint4 *>(cells + c) + 1);
         key = ((u64)a.y << 32) | a.x;
-        cnt = (int)b.x;
-        if (signed_pure(cnt, key, ((u64)a.w << 32) | a.z, seed_chk)) {
+        cnt = (int)a.z;
+        if (signed_pure(((u64)a.w << 32) | a.z, key, seed_chk)) {
           const u32 bit = 1u << (c & 31u);
           keep = (atomicOr(bitmap + (c >> 5), bit) & bit) == 0;  // first entry of this cell
         }

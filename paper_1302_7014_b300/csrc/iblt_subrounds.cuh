@@ -123,12 +123,10 @@ __global__ void __launch_bounds__(kBlock) k_sscan(const Cell *__restrict__ cells
       const u64 c = c0 + (u64)it * kBlock + threadIdx.x;
       if (c < tab0.n_cells) {
         const uint4 a = __ldcs(reinterpret_cast<const uint4 *>(cells + c));
-        const uint4 b = __ldcs(reinterpret_cast<const uint4 *>(cells + c) + 1);
         const u64 key = ((u64)a.y << 32) | a.x;
-        const u64 chk = ((u64)a.w << 32) | a.z;
-        const int cnt = (int)b.x;
-        nonempty += cnt != 0;
-        if (cnt == 1 && chk == mix64(key ^ seed_chk))
+        const u64 cw = ((u64)a.w << 32) | a.z;
+        nonempty += (int)a.z != 0;
+        if (cw == cell_word(key, seed_chk))
           sub_stage_push(S, tab0, queue, ctl, (u32)c, subtable_of(tab0, (u32)c));
       }
     }
@@ -166,10 +164,8 @@ __global__ void __launch_bounds__(kBlock) k_sfilter(const Cell *__restrict__ cel
       if (i < fe) {
         c = __ldcs(q + i);
         const uint4 a = __ldcg(reinterpret_cast<const uint4 *>(cells + c));
-        const uint4 b = __ldcg(reinterpret_cast<const uint4 *>(cells + c) + 1);
         key = ((u64)a.y << 32) | a.x;
-        const u64 chk = ((u64)a.w << 32) | a.z;
-        pure = (int)b.x == 1 && chk == mix64(key ^ seed_chk);
+        pure = (((u64)a.w << 32) | a.z) == cell_word(key, seed_chk);
       }
       const u32 p = warp_reserve<u32>(pure, &s_n);
       if (pure) {
@@ -233,14 +229,13 @@ __global__ void __launch_bounds__(kBlock) k_speel(Cell *__restrict__ cells, cons
         if (!ok) flags |= FLAG_INTERNAL;
       }
       if (ok) {
-        const u64 cx = mix64(x ^ tab0.seed[r]);
+        const u64 w = cell_word(x, tab0.seed[r]);
 #pragma unroll
         for (int h = 0; h < NR; ++h) {
           if (h < r) {
             Cell *p = cells + cj[h];
-            const int old = atomicSub(&p->count, 1);
+            const int old = cell_count(atomicAdd(&p->cw, 0ull - w));
             atomicXor(&p->key, x);
-            atomicXor(&p->chk, cx);
             emptied += (u64)(long long)((old == 1) - (old == 0));
             if (old == 2) sub_stage_push(S, tab0, queue, ctl, cj[h], (u32)h);
           }

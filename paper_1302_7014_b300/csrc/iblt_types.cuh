@@ -64,7 +64,7 @@ struct Chunk {
 };
 
 // Slab-binned build (iblt_binned.cuh).
-constexpr int kSlabShift = 21;               // 2^21 cells = 64 MB per slab
+constexpr int kSlabShift = 21;               // 2^21 cells = 32 MB per slab
 constexpr u32 kSlabCells = 1u << kSlabShift;
 constexpr int kBinItems = 4;                 // keys per thread per partition step
 constexpr int kBinKeys = kBlock * kBinItems; // keys per block per partition step
@@ -74,7 +74,7 @@ constexpr int kBinKeys = kBlock * kBinItems; // keys per block per partition ste
 // re-sorted into tiles of 2^12 cells, and each tile is updated in shared
 // memory and written out whole.
 constexpr int kTileShift = 12;
-constexpr u32 kTileCells = 1u << kTileShift;               // 4096 cells, 80 KB of shared state
+constexpr u32 kTileCells = 1u << kTileShift;               // 4096 cells, 64 KB of shared state
 constexpr u32 kTilesPerSlab = kSlabCells >> kTileShift;    // 512
 constexpr int kTileThreads = 512;                          // threads per CTA of both tile kernels
 constexpr int kTileBinItems = 8;                           // records per thread per chunk

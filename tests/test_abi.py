@@ -97,11 +97,11 @@ def test_product_path_does_not_touch_the_oracle():
 def test_workspace_size_host_only(ppeel_lib):
     import paper_1302_7014_b300 as pp
     small = pp.workspace_size(1 << 20, 3, 1000)
-    assert small["table"] == 32 << 20
+    assert small["table"] == 16 << 20   # 16-byte cells
     # below 2^21 cells nothing is binned: only what create allocates
     assert small["peak"] == small["table"] + small["fixed"]
     big = pp.workspace_size(1 << 24, 3, int(0.75 * (1 << 24)))
-    assert big["table"] == 32 << 24 and big["fixed"] > 16 << 24
+    assert big["table"] == 16 << 24 and big["fixed"] > 16 << 24
     assert big["peak"] > big["table"] + big["fixed"] + 12 * 3 * int(0.75 * (1 << 24))
     # binned=2 switches the binning off
     plain = pp.workspace_size(1 << 24, 3, int(0.75 * (1 << 24)), pp.options(binned=2))

@@ -33,11 +33,17 @@ MUTANTS = [
      "uint64_t h = mix64(x ^ seeds[j]);",
      "uint64_t h = mix64(x ^ seeds[0]);"),
     ("checksum not removed on recovery",
-     "        keyx[c] ^= x;\n        chkx[c] ^= cs;\n      }\n      out_keys[total + i] = x;",
+     "        keyx[c] ^= x;\n        chks[c] -= cs;\n      }\n      out_keys[total + i] = x;",
      "        keyx[c] ^= x;\n      }\n      out_keys[total + i] = x;"),
     ("pure test drops the checksum comparison",
-     "return count[c] == 1 && chkx[c] == checksum_of(keyx[c], seeds, r);",
-     "return count[c] == 1 || chkx[c] == checksum_of(keyx[c], seeds, r);"),
+     "return count[c] == 1 && chks[c] == checksum_of(keyx[c], seeds, r);",
+     "return count[c] == 1 || chks[c] == checksum_of(keyx[c], seeds, r);"),
+    ("checksum is the lower half of mix64",
+     "return (uint32_t)(mix64(x ^ seeds[r]) >> 32);",
+     "return (uint32_t)mix64(x ^ seeds[r]);"),
+    ("insertion adds the checksum without its sign",
+     "chks[c] += (uint32_t)sign * cs;",
+     "chks[c] += cs;"),
     ("a key pure in two cells is recovered twice",
      "if (i == 0 || pure_keys[i] != pure_keys[i - 1]) pure_keys[nk++] = pure_keys[i];",
      "pure_keys[nk++] = pure_keys[i];"),
@@ -66,11 +72,17 @@ MUTANTS = [
      "        count[c] -= sg;",
      "        count[c] -= 1;"),
     ("signed purity misses negative counts",
-     "if ((count[c] == 1 || count[c] == -1) && chkx[c] == checksum_of(keyx[c], seeds, r)) {",
-     "if (count[c] == 1 && chkx[c] == checksum_of(keyx[c], seeds, r)) {"),
+     "if ((count[c] == 1 || count[c] == -1) &&",
+     "if ((count[c] == 1) &&"),
+    ("signed purity ignores the sign of the checksum",
+     "chks[c] == (uint32_t)count[c] * checksum_of(keyx[c], seeds, r)) {",
+     "chks[c] == checksum_of(keyx[c], seeds, r)) {"),
     ("signed recovery leaves the checksum in",
-     "        chkx[c] ^= cs;\n      }\n    }\n    total += nk;",
+     "        chks[c] -= (uint32_t)sg * cs;\n      }\n    }\n    total += nk;",
      "      }\n    }\n    total += nk;"),
+    ("signed removal subtracts the checksum without its sign",
+     "        chks[c] -= (uint32_t)sg * cs;\n      }\n    }\n    total += nk;",
+     "        chks[c] -= cs;\n      }\n    }\n    total += nk;"),
     ("mix64 shift constant off by one",
      "z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;",
      "z = (z ^ (z >> 28)) * 0x94D049BB133111EBULL;"),

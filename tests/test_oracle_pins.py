@@ -204,17 +204,20 @@ def test_iblt_build_definition():
     cells = oracle.key_cells(n, r, seed, keys)
     cnt = np.zeros(n, np.int64)
     kx = np.zeros(n, np.uint64)
-    cx = np.zeros(n, np.uint64)
+    cx = [0] * n
+    s_chk = int(oracle.hash_seeds(seed, r)[r])
     for x, row in zip(keys, cells):
-        cs = np.uint64(oracle.checksum(seed, r, int(x)))
+        # checkSum(x) is the upper half of the (published-pinned) mix64 finaliser
+        cs = oracle.mix64(int(x) ^ s_chk) >> 32
+        assert oracle.checksum(seed, r, int(x)) == cs
         for c in row:
             cnt[c] += 1
             kx[c] ^= x
-            cx[c] ^= cs
-    assert (t.count == cnt).all() and (t.keyx == kx).all() and (t.chkx == cx).all()
-    # insertion and deletion are the same XOR; deleting everything empties the table
+            cx[c] = (cx[c] + cs) % (1 << 32)
+    assert (t.count == cnt).all() and (t.keyx == kx).all() and t.chks.tolist() == cx
+    # deletion undoes insertion; deleting everything empties the table
     t.insert(keys, sign=-1)
-    assert not t.count.any() and not t.keyx.any() and not t.chkx.any()
+    assert not t.count.any() and not t.keyx.any() and not t.chks.any()
 
 
 @pytest.mark.parametrize("n,r,c", [(3000, 3, 0.6), (3000, 4, 0.7), (2048, 3, 0.75), (999, 5, 0.6)])
@@ -268,13 +271,11 @@ def test_iblt_residue_invariants_above_threshold():
         for k in left:
             x ^= k
         assert int(np.bitwise_xor.reduce(t.keyx[part])) == x
-        cx = 0
-        for k in left:
-            cx ^= oracle.checksum(seed, r, k)
-        assert int(np.bitwise_xor.reduce(t.chkx[part])) == cx
+        cx = sum(oracle.checksum(seed, r, k) for k in left) % (1 << 32)
+        assert sum(int(v) for v in t.chks[part]) % (1 << 32) == cx
     # no pure cell is left
     for c in range(n):
-        assert not (t.count[c] == 1 and int(t.chkx[c]) == oracle.checksum(seed, r, int(t.keyx[c])))
+        assert not (t.count[c] == 1 and int(t.chks[c]) == oracle.checksum(seed, r, int(t.keyx[c])))
 
 
 def test_iblt_queue_and_rounds_agree():
@@ -333,7 +334,7 @@ def test_iblt_checksum_rejects_impure_count_one():
     t.insert(dele, sign=-1)
     mixed = 0
     for c in range(n):
-        if t.count[c] == 1 and int(t.chkx[c]) != oracle.checksum(seed, r, int(t.keyx[c])):
+        if t.count[c] == 1 and int(t.chks[c]) != oracle.checksum(seed, r, int(t.keyx[c])):
             mixed += 1
     assert mixed > 0
     res = t.decode_rounds()

@@ -44,7 +44,7 @@ def _one_case(lib, pp, n, r, c, seed, key_seed):
     ref = pp.IBLT(n, r, seed)
     ref.insert(dkeys)
     # the caller's own copy of the built table, in caller-owned device memory
-    cells = torch.empty(n * 32, dtype=torch.uint8, device="cuda")
+    cells = torch.empty(n * ctypes.sizeof(pp._lib.Cell), dtype=torch.uint8, device="cuda")
     stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
     assert lib.pp_iblt_copy_cells(ref.handle, ctypes.c_void_p(cells.data_ptr()), 0, n, 0, stream) == 0
     # existing entry point
@@ -69,8 +69,7 @@ def _one_case(lib, pp, n, r, c, seed, key_seed):
     for a, b in zip(_by_round(got, want.recovered_per_round), _by_round(ref_keys, want.recovered_per_round)):
         assert (a == b).all()
     # the decoded-in-place tables are identical too
-    dt = np.dtype([("key_xor", "<u8"), ("chk_xor", "<u8"), ("count", "<i4"), ("reserved", "<u4", 3)])
-    after = cells.cpu().numpy().view(dt)
+    after = pp.unpack_cells(cells.cpu().numpy().view(np.dtype(pp.CELL_DTYPE)))
     assert (after == ref.cells()).all()
     ref.close()
 
