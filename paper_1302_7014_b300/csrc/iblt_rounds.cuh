@@ -9,7 +9,7 @@
 //            2^19 consecutive cells (8 MB).  Records are ordered by bin inside
 //            the block and leave it as contiguous runs.
 //   k_apply_round (phase B2) walks the records bin by bin: blocks take the next
-//            chunk of 1024 records from an atomic counter, so at any moment the
+//            chunk of 2048 records from an atomic counter, so at any moment the
 //            whole GPU updates a narrow, moving window of the table and HBM
 //            sees near-sequential traffic.  Each update is one 64-bit
 //            atomicAdd on the cell's count-and-checksum word and one

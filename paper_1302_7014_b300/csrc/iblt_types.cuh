@@ -115,7 +115,7 @@ constexpr u32 kMaxRoundBins = 128;         // ... and there are at most this man
 // Records per thread per grab of k_apply_round, and its resident CTAs per SM
 // (together they set the width of the table window that is being updated).
 #ifndef PP_APPLY_PER
-#define PP_APPLY_PER 4
+#define PP_APPLY_PER 8
 #endif
 #ifndef PP_APPLY_CTAS
 #define PP_APPLY_CTAS 3
