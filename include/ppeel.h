@@ -66,8 +66,10 @@ typedef struct pp_options {
   uint32_t kcore_mode;   /* pp_peel_kcore full rounds: 0 = for graphs of 2^20 edges or
                             more, edge-centric rounds while the frontier holds at least
                             half as many vertices as there are edges left, then rounds
-                            over incidence lists built for the edges left; smaller graphs
-                            use incidence lists (default); 1 = incidence lists from round
+                            over incidence lists built for the edges left; graphs of at
+                            most 2^14 vertices and 2^16 edges (host_loop 0) run every
+                            round inside one thread block; other graphs use incidence
+                            lists (default); 1 = incidence lists from round
                             1; 2 = edge-centric rounds to the end.  r > 4 and edge
                             rows that are not 16-byte (r = 4) or 8-byte (r = 2) aligned
                             always use 1. */
@@ -265,7 +267,13 @@ typedef struct pp_peel_result {
  * Round t removes every vertex whose degree is < k at the start of round t and
  * every edge touching one of them.
  * d_vertex_round (n int32, or NULL): round each vertex was removed in, 0 = in
- * the k-core.  d_edge_round (m int32, or NULL): the same for edges.
+ * the k-core.  d_edge_round (m int32, or NULL): the same for edges.  When the
+ * call stops at opt.max_rounds (ROUND_LIMIT), both hold rounds 1..max_rounds,
+ * the vertices that round max_rounds + 1 would remove hold max_rounds + 1, and
+ * everything else holds 0.
+ * Graphs of at most 2^14 vertices and 2^16 edges peel inside one thread block
+ * (automatic mode, rounds on the device); larger ones use incidence lists or
+ * edge-centric rounds.
  * Workspace (~16 B per vertex + 4 B per incidence, plus ~16 B per incidence
  * for the tiled incidence scatter of large inputs) comes from a memory pool
  * the library keeps per device; it goes back to that pool when the call ends

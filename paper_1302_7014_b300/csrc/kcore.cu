@@ -1119,6 +1119,144 @@ static pp_status scatter_incidences(const u32 *edges, uint64_t m, uint32_t r, ui
   return st;
 }
 
+// ---- one-block rounds for small graphs ----------------------------------------
+// A graph of at most kSmallV vertices and kSmallE edges peels inside one CTA:
+// the degrees and each vertex's removal round live in shared memory, and round
+// t is two passes separated by block barriers (Sec. 1's round rule):
+//   R_t = the vertices still present whose degree is < k (marked with t);
+//   D_t = the edges still present with an endpoint marked t; each is removed
+//         and its endpoints lose one degree per incidence.
+// Rescanning all n vertices and m edges per round costs less than the
+// launches and host round trips of the general path at this size.
+constexpr u32 kSmallV = 1u << 14;
+constexpr u32 kSmallE = 1u << 16;
+constexpr int kSmallThreads = 1024;
+
+static size_t small_peel_smem(u32 n, u32 m) {
+  return (size_t)n * 4 + (size_t)((n + 1) & ~1u) * 2 + (size_t)((m + 31) / 32) * 4;
+}
+
+__device__ __forceinline__ u32 block_sum_small(u32 v, u32 *acc) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+  if (lane_id() == 0 && v) atomicAdd(acc, v);
+  __syncthreads();
+  return *acc;
+}
+
+// R = 3 or 4: rows of that rank, unrolled; R = 0: any r <= PP_MAX_R.  Each
+// thread loads the rows of B edges before testing them, so B rows per thread
+// are in flight at once.
+template <int R>
+__global__ void __launch_bounds__(kSmallThreads, 1)
+    k_small_peel(const u32 *__restrict__ edges, u32 m, u32 r, u32 n, u32 k, u32 max_rounds,
+                 int *__restrict__ vround, int *__restrict__ eround, PeelCtl *__restrict__ ctl, PeelStats st) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  u32 *deg = reinterpret_cast<u32 *>(smem);                                   // n
+  unsigned short *vr = reinterpret_cast<unsigned short *>(deg + n);           // n (even count)
+  u32 *ealive = reinterpret_cast<u32 *>(vr + ((n + 1) & ~1u));               // (m + 31) / 32
+  __shared__ u32 s_acc[3], s_flags;
+  const u32 tid = threadIdx.x, lane = lane_id();
+  const u32 words = (m + 31) / 32;
+  for (u32 v = tid; v < n; v += kSmallThreads) deg[v] = 0, vr[v] = 0;
+  for (u32 w = tid; w < words; w += kSmallThreads)
+    ealive[w] = (w + 1) * 32 <= m ? kFull : (1u << (m & 31u)) - 1u;
+  if (tid == 0) s_flags = 0;
+  __syncthreads();
+  // degrees with multiplicity; the edge-round output starts at 0 (in the core)
+  u32 bad = 0;
+  for (u32 e = tid; e < m; e += kSmallThreads) {
+    for (u32 j = 0; j < r; ++j) {
+      const u32 v = edges[(u64)e * r + j];
+      if (v < n) atomicAdd(deg + v, 1u);
+      else bad = 1;
+    }
+    if (eround) eround[e] = 0;
+  }
+  if (bad) atomicOr(&s_flags, (u32)FLAG_BAD_ID);
+  __syncthreads();
+  u64 s_left = n, m_left = m;
+  u32 t = 1;
+  if (!(s_flags & FLAG_BAD_ID)) {
+    for (;; ++t) {
+      if (tid < 3) s_acc[tid] = 0;
+      __syncthreads();
+      // past the limit R_t is marked (as the pending frontier of the other
+      // paths is) but not removed
+      const bool run = t <= max_rounds;
+      u32 nr = 0;
+      for (u32 v = tid; v < n; v += kSmallThreads) {
+        if (vr[v] == 0 && deg[v] < k) {
+          ++nr;
+          vr[v] = (unsigned short)t;
+        }
+      }
+      const u32 removed = block_sum_small(nr, &s_acc[0]);
+      if (removed == 0) break;
+      if (!run) {
+        if (tid == 0) s_flags |= FLAG_ROUND_LIMIT;
+        break;
+      }
+      // one warp per 32-edge word of the alive bitmap
+      constexpr int NR = R ? R : PP_MAX_R;
+      constexpr int B = R ? 4 : 2;
+      const u32 rr = R ? (u32)R : r;
+      u32 ne = 0;
+      for (u32 b0 = tid & ~31u; b0 < m; b0 += kSmallThreads * B) {
+        u32 row[B][NR], word[B];
+#pragma unroll
+        for (int q = 0; q < B; ++q) {
+          const u32 base = b0 + (u32)q * kSmallThreads, e = base + lane;
+          word[q] = base < m ? ealive[base >> 5] : 0u;
+          const bool live = e < m && ((word[q] >> lane) & 1u);
+#pragma unroll
+          for (int j = 0; j < NR; ++j) row[q][j] = (live && (u32)j < rr) ? edges[(u64)e * rr + j] : 0u;
+        }
+#pragma unroll
+        for (int q = 0; q < B; ++q) {
+          const u32 base = b0 + (u32)q * kSmallThreads, e = base + lane;
+          bool hit = false;
+          if (e < m && ((word[q] >> lane) & 1u)) {
+#pragma unroll
+            for (int j = 0; j < NR; ++j)
+              if ((u32)j < rr) hit |= vr[row[q][j]] == t;
+            if (hit) {
+#pragma unroll
+              for (int j = 0; j < NR; ++j)
+                if ((u32)j < rr) atomicSub(deg + row[q][j], 1u);
+              if (eround) eround[e] = (int)t;
+            }
+          }
+          const u32 ball = __ballot_sync(kFull, hit);
+          if (lane == 0 && ball) ealive[base >> 5] = word[q] & ~ball;
+          ne += hit;
+        }
+      }
+      const u32 gone = block_sum_small(ne, &s_acc[1]);
+      s_left -= removed;
+      m_left -= gone;
+      if (tid == 0) {
+        st.s[t - 1] = s_left;
+        st.m[t - 1] = m_left;
+      }
+      __syncthreads();  // s_acc is reset for the next round
+    }
+  }
+  __syncthreads();
+  if (vround && !(s_flags & FLAG_BAD_ID))
+    for (u32 v = tid; v < n; v += kSmallThreads) vround[v] = (int)vr[v];
+  if (tid == 0) {
+    PeelCtl c;
+    memset(&c, 0, sizeof c);
+    c.s = s_left;
+    c.m = m_left;
+    c.k = k;
+    c.max_rounds = max_rounds;
+    c.round = t - 1;
+    c.flags = s_flags;
+    *ctl = c;
+  }
+}
+
 static pp_status peel_kcore_impl(uint32_t n, uint32_t r, uint32_t k, const uint32_t *d_edges, uint64_t m,
                           const Parts *parts, int32_t *d_vertex_round, int32_t *d_edge_round,
                           pp_peel_result *res, const pp_options *opt, void *stream) {
@@ -1141,20 +1279,25 @@ static pp_status peel_kcore_impl(uint32_t n, uint32_t r, uint32_t k, const uint3
   Part parts_list[16];
   int np_ = 0;
   auto al = [&](void **p, size_t b) { parts_list[np_++] = Part{p, (b + 255) & ~(size_t)255}; };
-  al((void **)&w.deg, nn * 4);
-  al((void **)&w.off, (nn + 1) * 4);
-  al((void **)&w.cursor, nn * 4);
-  al((void **)&w.inc, mm * r * 4);
-  al((void **)&w.alive, ((mm + 31) / 32) * 4);
-  al((void **)&w.f0, nn * 4);
-  al((void **)&w.f1, nn * 4);
+  // small graphs in automatic mode peel in one block (k_small_peel)
+  const bool small = !parts && n > 0 && m > 0 && n <= kSmallV && m <= kSmallE && o.kcore_mode == 0 &&
+                     o.host_loop == 0;
+  if (!small) {
+    al((void **)&w.deg, nn * 4);
+    al((void **)&w.off, (nn + 1) * 4);
+    al((void **)&w.cursor, nn * 4);
+    al((void **)&w.inc, mm * r * 4);
+    al((void **)&w.alive, ((mm + 31) / 32) * 4);
+    al((void **)&w.f0, nn * 4);
+    al((void **)&w.f1, nn * 4);
+    al((void **)&w.deg16, ((nn + 1) / 2) * 4);
+    al((void **)&w.ovf, sizeof(u32));
+    al(&w.scan_tmp, exclusive_scan_temp_bytes(nn));
+  }
   al((void **)&w.ctl, sizeof(PeelCtl));
-  al((void **)&w.deg16, ((nn + 1) / 2) * 4);
-  al((void **)&w.ovf, sizeof(u32));
   if (parts) al((void **)&w.sub, sizeof(SubCtl));
   al((void **)&w.st_s, (size_t)o.max_rounds * 8);
   al((void **)&w.st_m, (size_t)o.max_rounds * 8);
-  al(&w.scan_tmp, exclusive_scan_temp_bytes(nn));
   {
     size_t total = 0;
     for (int i = 0; i < np_; ++i) total += parts_list[i].bytes;
@@ -1181,6 +1324,26 @@ static pp_status peel_kcore_impl(uint32_t n, uint32_t r, uint32_t k, const uint3
     const int egrid = (int)(eb < (u64)sms * 16 ? (eb ? eb : 1) : (u64)sms * 16);
     const u64 vb = (nn + kKBlock * 4 - 1) / (kKBlock * 4);
     const int vgrid = (int)(vb < (u64)sms * 8 ? vb : (u64)sms * 8);
+    if (small) {
+      static std::once_flag small_attr;
+      const void *fns[3] = {(const void *)k_small_peel<3>, (const void *)k_small_peel<4>,
+                            (const void *)k_small_peel<0>};
+      std::call_once(small_attr, [&fns] {
+        for (const void *f : fns)
+          cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)small_peel_smem(kSmallV, kSmallE));
+      });
+      const void *fn = r == 3 ? fns[0] : r == 4 ? fns[1] : fns[2];
+      u32 mm32 = (u32)m, n32 = n, r32 = r, k32 = k, mr32 = o.max_rounds;
+      int *vr_out = d_vertex_round, *er_out = d_edge_round;
+      PeelCtl *ctlp = w.ctl;
+      PeelStats pst{w.st_s, w.st_m};
+      void *kargs[] = {(void *)&d_edges, &mm32, &r32, &n32, &k32, &mr32, &vr_out, &er_out, &ctlp, &pst};
+      e = cudaLaunchKernel(fn, dim3(1), dim3(kSmallThreads), kargs, small_peel_smem(n, (u32)m), s);
+      if (e != cudaSuccess) {
+        status = cuda_fail(e, "pp_peel_kcore small-graph launch", __FILE__, __LINE__);
+        goto cleanup;
+      }
+    } else {
     if ((e = cudaMemsetAsync(w.deg16, 0, ((nn + 1) / 2) * 4, s)) != cudaSuccess ||
         (e = cudaMemsetAsync(w.ovf, 0, sizeof(u32), s)) != cudaSuccess ||
         (e = cudaMemsetAsync(w.alive, 0xff, ((mm + 31) / 32) * 4, s)) != cudaSuccess) {
@@ -1342,6 +1505,7 @@ static pp_status peel_kcore_impl(uint32_t n, uint32_t r, uint32_t k, const uint3
       }
     }
     if (status != PP_OK) goto cleanup;
+    }  // general path
     if ((e = cudaMemcpyAsync(&hc, w.ctl, sizeof hc, cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
         (parts && (e = cudaMemcpyAsync(&hsub, w.sub, sizeof hsub, cudaMemcpyDeviceToHost, s)) != cudaSuccess) ||
         (e = cudaStreamSynchronize(s)) != cudaSuccess) {

@@ -223,6 +223,47 @@ def test_round_limit(pp):
     assert ei.value.name == "PP_ERR_ROUND_LIMIT"
 
 
+@pytest.mark.parametrize("n,r,m,k", [(16384, 4, 65536, 2), (16385, 3, 11000, 2), (16384, 3, 65537, 3),
+                                     (1, 2, 3, 1), (300, 8, 700, 2), (4096, 5, 3000, 4)])
+def test_small_graph_limits(pp, n, r, m, k):
+    # graphs of at most 2^14 vertices and 2^16 edges peel in one block; the
+    # cases at and just past both limits take the two paths
+    edges = ppgen.uniform_edges(n, r, m, 77 + n + m)
+    check(pp, n, k, edges)
+
+
+@pytest.mark.parametrize("max_rounds", [1, 2, 3])
+def test_small_graph_round_limit_matches_lists(pp, max_rounds):
+    # the same partial peel from the one-block path (automatic mode), the
+    # incidence lists and the edge-centric rounds: rounds 1..max_rounds as the
+    # oracle has them, the vertices round max_rounds + 1 would remove marked
+    # with that round, everything else 0; the same error from each
+    n, r = 12000, 3
+    edges = ppgen.partitioned_edges(n, r, 8400, 5)
+    d_edges = torch.from_numpy(edges.view(np.int32)).cuda()
+    o = oracle.kcore_rounds(n, 2, edges)
+    vr_o = np.where(o["vround"] <= max_rounds + 1, o["vround"], 0)
+    er_o = np.where(o["eround"] <= max_rounds, o["eround"], 0)
+    for mode in (0, 1, 2):
+        vr = torch.full((n,), -7, dtype=torch.int32, device="cuda")
+        er = torch.full((edges.shape[0],), -7, dtype=torch.int32, device="cuda")
+        with pytest.raises(pp.PPError) as ei:
+            pp.peel_kcore(n, r, 2, d_edges, vr, er, pp.options(max_rounds=max_rounds, kcore_mode=mode))
+        assert ei.value.name == "PP_ERR_ROUND_LIMIT"
+        assert (vr.cpu().numpy() == vr_o).all(), mode
+        assert (er.cpu().numpy() == er_o).all(), mode
+
+
+def test_small_graph_without_outputs(pp):
+    cfg = ppgen.PLAIN_PEEL
+    n, r, k = cfg["n"], cfg["r"], cfg["k"]
+    edges = ppgen.partitioned_edges(n, r, ppgen.edges_from_c(cfg["c"], n), cfg["seed"])
+    d_edges = torch.from_numpy(edges.view(np.int32)).cuda()
+    res = pp.peel_kcore(n, r, k, d_edges)
+    o = oracle.kcore_rounds(n, k, edges)
+    assert res.rounds == o["rounds"] and res.vertices_left == o["s"] and res.edges_left == o["m"]
+
+
 def test_iblt_decode_is_the_k2_peel(pp):
     # Sec. 6: recovery is peeling at k = 2 on the key hypergraph; both GPU paths agree
     n, r, seed = 120000, 3, 88
