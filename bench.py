@@ -495,7 +495,7 @@ def bench_kcore(pp, torch, args):
     plain = {"workload": "plain peel n=2^14 r=3 k=2 c=0.7 (%d edges)" % pe.shape[0], "rounds": pres.rounds,
              "core_vertices": pres.core_vertices, "us_median": float(np.median(us)),
              "us_p10": float(np.percentile(us, 10)), "us_p90": float(np.percentile(us, 90)),
-             "timed": "one pp_peel_kcore call, graph-driven rounds"}
+             "timed": "one pp_peel_kcore call (automatic mode: every round inside one thread block)"}
     return {"workload": cfg["name"], "k": k, "parts": r,
             "timed": "one pp_peel_kcore call: degree histogram, then edge-centric rounds while the frontier "
                      "is at least half the edges left, incidence lists for the edges left and "
