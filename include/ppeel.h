@@ -272,8 +272,10 @@ typedef struct pp_peel_result {
  * the vertices that round max_rounds + 1 would remove hold max_rounds + 1, and
  * everything else holds 0.
  * Graphs of at most 2^14 vertices and 2^16 edges peel inside one thread block
- * (automatic mode, rounds on the device); larger ones use incidence lists or
- * edge-centric rounds.
+ * (automatic mode, rounds on the device) with no device workspace; their
+ * statistics come back through a 260 KB pinned buffer that the calling thread
+ * keeps for its next call.  Larger graphs use incidence lists or edge-centric
+ * rounds.
  * Workspace (~16 B per vertex + 4 B per incidence, plus ~16 B per incidence
  * for the tiled incidence scatter of large inputs) comes from a memory pool
  * the library keeps per device; it goes back to that pool when the call ends

@@ -1257,6 +1257,65 @@ __global__ void __launch_bounds__(kSmallThreads, 1)
   }
 }
 
+// The one-block path's results go to mapped pinned memory owned by the calling
+// thread (control block, then s_t and m_t for up to n rounds): the call
+// allocates nothing and synchronizes once.  Calls return only after that
+// synchronization, so one buffer per thread is never shared by two calls.
+static pp_status peel_small(uint32_t n, uint32_t r, uint32_t k, const uint32_t *d_edges, uint64_t m,
+                            int32_t *d_vertex_round, int32_t *d_edge_round, pp_peel_result *res,
+                            const pp_options &o, cudaStream_t s) {
+  struct Stage {
+    void *h = nullptr;
+    size_t bytes = 0;
+  };
+  thread_local Stage stage;
+  const size_t ctl_bytes = (sizeof(PeelCtl) + 255) & ~(size_t)255;
+  const size_t bytes = ctl_bytes + 2 * ((size_t)kSmallV + 1) * 8;
+  if (stage.bytes < bytes) {
+    void *h = nullptr;
+    const cudaError_t e = cudaHostAlloc(&h, bytes, cudaHostAllocMapped | cudaHostAllocPortable);
+    if (e != cudaSuccess) return cuda_fail(e, "pp_peel_kcore pinned stage", __FILE__, __LINE__);
+    stage.h = h;
+    stage.bytes = bytes;
+  }
+  char *hb = static_cast<char *>(stage.h);
+  void *db = nullptr;
+  cudaError_t e = cudaHostGetDevicePointer(&db, stage.h, 0);
+  if (e != cudaSuccess) return cuda_fail(e, "pp_peel_kcore pinned stage", __FILE__, __LINE__);
+  static std::once_flag small_attr;
+  const void *fns[3] = {(const void *)k_small_peel<3>, (const void *)k_small_peel<4>,
+                        (const void *)k_small_peel<0>};
+  std::call_once(small_attr, [&fns] {
+    for (const void *f : fns)
+      cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)small_peel_smem(kSmallV, kSmallE));
+  });
+  const void *fn = r == 3 ? fns[0] : r == 4 ? fns[1] : fns[2];
+  u32 m32 = (u32)m, n32 = n, r32 = r, k32 = k, mr32 = o.max_rounds;
+  int *vr_out = d_vertex_round, *er_out = d_edge_round;
+  PeelCtl *ctlp = reinterpret_cast<PeelCtl *>(db);
+  u64 *ss = reinterpret_cast<u64 *>(static_cast<char *>(db) + ctl_bytes);
+  PeelStats pst{ss, ss + kSmallV + 1};
+  void *kargs[] = {(void *)&d_edges, &m32, &r32, &n32, &k32, &mr32, &vr_out, &er_out, &ctlp, &pst};
+  e = cudaLaunchKernel(fn, dim3(1), dim3(kSmallThreads), kargs, small_peel_smem(n, m32), s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail(e, "pp_peel_kcore small-graph path", __FILE__, __LINE__);
+  PeelCtl hc;
+  memcpy(&hc, hb, sizeof hc);
+  const u64 *hs = reinterpret_cast<const u64 *>(hb + ctl_bytes);
+  const uint32_t T = hc.round;
+  const uint32_t ncopy = T < res->round_cap ? T : res->round_cap;
+  if (ncopy && res->vertices_left) memcpy(res->vertices_left, hs, (size_t)ncopy * 8);
+  if (ncopy && res->edges_left) memcpy(res->edges_left, hs + kSmallV + 1, (size_t)ncopy * 8);
+  res->rounds = T;
+  res->status_flags = hc.flags;
+  res->core_vertices = hc.s;
+  res->core_edges = hc.m;
+  if (hc.flags & FLAG_BAD_ID) return fail(PP_ERR_INVALID_ARG, "pp_peel_kcore: a vertex id is >= n=%u", n);
+  if (hc.flags & FLAG_ROUND_LIMIT)
+    return fail(PP_ERR_ROUND_LIMIT, "pp_peel_kcore: stopped after max_rounds=%u (sub-)rounds", o.max_rounds);
+  return PP_OK;
+}
+
 static pp_status peel_kcore_impl(uint32_t n, uint32_t r, uint32_t k, const uint32_t *d_edges, uint64_t m,
                           const Parts *parts, int32_t *d_vertex_round, int32_t *d_edge_round,
                           pp_peel_result *res, const pp_options *opt, void *stream) {
@@ -1280,9 +1339,9 @@ static pp_status peel_kcore_impl(uint32_t n, uint32_t r, uint32_t k, const uint3
   int np_ = 0;
   auto al = [&](void **p, size_t b) { parts_list[np_++] = Part{p, (b + 255) & ~(size_t)255}; };
   // small graphs in automatic mode peel in one block (k_small_peel)
-  const bool small = !parts && n > 0 && m > 0 && n <= kSmallV && m <= kSmallE && o.kcore_mode == 0 &&
-                     o.host_loop == 0;
-  if (!small) {
+  if (!parts && n > 0 && m > 0 && n <= kSmallV && m <= kSmallE && o.kcore_mode == 0 && o.host_loop == 0)
+    return peel_small(n, r, k, d_edges, m, d_vertex_round, d_edge_round, res, o, s);
+  {
     al((void **)&w.deg, nn * 4);
     al((void **)&w.off, (nn + 1) * 4);
     al((void **)&w.cursor, nn * 4);
@@ -1324,26 +1383,7 @@ static pp_status peel_kcore_impl(uint32_t n, uint32_t r, uint32_t k, const uint3
     const int egrid = (int)(eb < (u64)sms * 16 ? (eb ? eb : 1) : (u64)sms * 16);
     const u64 vb = (nn + kKBlock * 4 - 1) / (kKBlock * 4);
     const int vgrid = (int)(vb < (u64)sms * 8 ? vb : (u64)sms * 8);
-    if (small) {
-      static std::once_flag small_attr;
-      const void *fns[3] = {(const void *)k_small_peel<3>, (const void *)k_small_peel<4>,
-                            (const void *)k_small_peel<0>};
-      std::call_once(small_attr, [&fns] {
-        for (const void *f : fns)
-          cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)small_peel_smem(kSmallV, kSmallE));
-      });
-      const void *fn = r == 3 ? fns[0] : r == 4 ? fns[1] : fns[2];
-      u32 mm32 = (u32)m, n32 = n, r32 = r, k32 = k, mr32 = o.max_rounds;
-      int *vr_out = d_vertex_round, *er_out = d_edge_round;
-      PeelCtl *ctlp = w.ctl;
-      PeelStats pst{w.st_s, w.st_m};
-      void *kargs[] = {(void *)&d_edges, &mm32, &r32, &n32, &k32, &mr32, &vr_out, &er_out, &ctlp, &pst};
-      e = cudaLaunchKernel(fn, dim3(1), dim3(kSmallThreads), kargs, small_peel_smem(n, (u32)m), s);
-      if (e != cudaSuccess) {
-        status = cuda_fail(e, "pp_peel_kcore small-graph launch", __FILE__, __LINE__);
-        goto cleanup;
-      }
-    } else {
+    {
     if ((e = cudaMemsetAsync(w.deg16, 0, ((nn + 1) / 2) * 4, s)) != cudaSuccess ||
         (e = cudaMemsetAsync(w.ovf, 0, sizeof(u32), s)) != cudaSuccess ||
         (e = cudaMemsetAsync(w.alive, 0xff, ((mm + 31) / 32) * 4, s)) != cudaSuccess) {
