@@ -574,6 +574,12 @@ def profile_case(pp, torch, args, cfg):
         d = torch.from_numpy(e.view(np.int32)).cuda()
         call = lambda: pp.peel_kcore(n, r, k, d, opts=opts, stream=stream)
         what = f"pp_peel_kcore, {sw['name']}, c={args.profile_c}"
+    elif args.profile_case == "plain":
+        pc = ppgen.PLAIN_PEEL
+        e = ppgen.partitioned_edges(pc["n"], pc["r"], ppgen.edges_from_c(pc["c"], pc["n"]), pc["seed"])
+        d = torch.from_numpy(e.view(np.int32)).cuda()
+        call = lambda: pp.peel_kcore(pc["n"], pc["r"], pc["k"], d, opts=opts, stream=stream)
+        what = "pp_peel_kcore, plain peel n=2^14 r=3 k=2 c=0.7"
     elif args.profile_case == "batched":
         import paper_1302_7014_b300.batch as pb
         tabs = ppgen.batch_tables(4096)
@@ -631,7 +637,7 @@ def main():
                     help="drive rounds from the host (kernels launched one by one, as profilers need)")
     ap.add_argument("--cells-log2", type=int, default=26,
                     help="table size for profiling runs (the benchmark itself is 2^26)")
-    ap.add_argument("--profile-case", choices=["kcore", "batched", "signed", "served"],
+    ap.add_argument("--profile-case", choices=["kcore", "plain", "batched", "signed", "served"],
                     help="for profilers: run one call of a secondary workload after two warm-up "
                          "calls, print its time and exit (no benchmark line)")
     ap.add_argument("--profile-c", type=float, default=0.70, help="density of --profile-case kcore")
