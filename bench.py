@@ -477,7 +477,7 @@ def bench_kcore(pp, torch, args):
                                        and sub.core_edges == full.core_edges)})
         del d
         torch.cuda.empty_cache()
-    # the plain-peel configuration: 2^14 vertices, launch-latency bound (microseconds)
+    # the plain-peel configuration: 2^14 vertices (microseconds)
     pc = ppgen.PLAIN_PEEL
     pe = ppgen.partitioned_edges(pc["n"], pc["r"], ppgen.edges_from_c(pc["c"], pc["n"]), pc["seed"])
     with torch.cuda.stream(stream):
