@@ -1267,6 +1267,9 @@ static pp_status peel_small(uint32_t n, uint32_t r, uint32_t k, const uint32_t *
   struct Stage {
     void *h = nullptr;
     size_t bytes = 0;
+    ~Stage() {
+      if (h) cudaFreeHost(h);  // at thread exit; an error at process teardown is ignored
+    }
   };
   thread_local Stage stage;
   const size_t ctl_bytes = (sizeof(PeelCtl) + 255) & ~(size_t)255;

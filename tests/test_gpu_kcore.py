@@ -264,6 +264,40 @@ def test_small_graph_without_outputs(pp):
     assert res.rounds == o["rounds"] and res.vertices_left == o["s"] and res.edges_left == o["m"]
 
 
+def test_small_graph_from_several_threads(pp):
+    # the one-block path keeps its result buffer per calling thread: calls from
+    # threads of their own (each on its own stream) give the oracle's result,
+    # and the threads exit (freeing their buffers) cleanly
+    import threading
+    cases = [(3000 + 500 * i, 3 + (i % 2), 2, 0.6 + 0.05 * i) for i in range(4)]
+    want, got = {}, {}
+    for i, (n, r, k, c) in enumerate(cases):
+        edges = ppgen.uniform_edges(n, r, int(c * n), 300 + i)
+        want[i] = (edges, oracle.kcore_rounds(n, k, edges))
+
+    def work(i):
+        n, r, k, _ = cases[i]
+        edges = want[i][0]
+        s = torch.cuda.Stream()
+        with torch.cuda.stream(s):
+            d = torch.from_numpy(edges.view(np.int32)).cuda()
+            vr = torch.empty(n, dtype=torch.int32, device="cuda")
+        s.synchronize()
+        for _ in range(20):
+            res = pp.peel_kcore(n, r, k, d, vr, None, stream=s)
+        got[i] = (res, vr.cpu().numpy())
+
+    ts = [threading.Thread(target=work, args=(i,)) for i in range(len(cases))]
+    for t in ts:
+        t.start()
+    for t in ts:
+        t.join()
+    for i in range(len(cases)):
+        res, vr = got[i]
+        o = want[i][1]
+        assert res.rounds == o["rounds"] and res.vertices_left == o["s"] and (vr == o["vround"]).all()
+
+
 def test_iblt_decode_is_the_k2_peel(pp):
     # Sec. 6: recovery is peeling at k = 2 on the key hypergraph; both GPU paths agree
     n, r, seed = 120000, 3, 88
