@@ -114,7 +114,7 @@ pp_status tile_apply_pass(Cell *cells, const TableArgs &tab0, const TableArgs *t
   const u32 sms = (u32)sm_count();
   // launch s: sort slab s while slab s - 1 is applied tile by tile
   for (step = 0; step <= ns + 1; ++step) {
-    n_bin = step < ns ? sms : 0u;
+    n_bin = step < ns ? 3 * sms : 0u;
     n_apply = (step >= 1 && step - 1 < ns) ? kTilesPerSlab : (step == ns + 1 ? 2 * sms : 0u);
     if (n_apply + n_bin == 0) continue;
     PP_CUDA(cudaLaunchKernel(tile_step_fn(tb.batch), dim3(n_apply + n_bin), dim3(kTileThreads), args,
@@ -140,7 +140,7 @@ pp_status tile_keys_pass(Cell *cells, const TableArgs *tabs, const u64 *keys, co
   const void *fn = tile_keys_fn(rank);
   const u32 sms = (u32)sm_count();
   for (step = 0; step <= n_slabs + 1; ++step) {
-    n_bin = step < n_slabs ? sms : 0u;
+    n_bin = step < n_slabs ? 3 * sms : 0u;
     n_apply = (step >= 1 && step - 1 < n_slabs) ? kTilesPerSlab : (step == n_slabs + 1 ? 2 * sms : 0u);
     if (n_apply + n_bin == 0) continue;
     PP_CUDA(cudaLaunchKernel(fn, dim3(n_apply + n_bin), dim3(kTileThreads), args, tile_step_smem(), s));
