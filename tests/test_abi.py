@@ -108,3 +108,21 @@ def test_workspace_size_host_only(ppeel_lib):
     assert plain["peak"] == plain["table"] + plain["fixed"]
     with pytest.raises(pp.PPError):
         pp.workspace_size(10, 9)
+
+
+def test_unpack_cells_splits_count_and_checksum():
+    # count_chk = S * 2^32 + count mod 2^64: the low half is the count (int32),
+    # the checksum sum S comes back exactly for negative counts too (borrow)
+    import numpy as np
+    import paper_1302_7014_b300 as pp
+    rng = np.random.default_rng(5)
+    count = np.concatenate([rng.integers(-(1 << 31), 1 << 31, 1000), [0, 1, -1, (1 << 31) - 1, -(1 << 31)]])
+    S = rng.integers(0, 1 << 32, count.size, dtype=np.uint64)
+    key = rng.integers(0, 1 << 63, count.size, dtype=np.uint64)
+    raw = np.zeros(count.size, dtype=np.dtype(pp.CELL_DTYPE))
+    raw["key_xor"] = key
+    raw["count_chk"] = [((int(s) << 32) + int(c)) % (1 << 64) for s, c in zip(S, count)]
+    out = pp.unpack_cells(raw)
+    assert (out["key_xor"] == key).all()
+    assert (out["count"].astype(np.int64) == count).all()
+    assert (out["chk_sum"].astype(np.uint64) == S).all()
