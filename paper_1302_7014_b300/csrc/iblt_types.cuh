@@ -148,7 +148,7 @@ inline u32 round_bin_shift(uint64_t n) {
   return sh;
 }
 
-constexpr int kClaimItems = 4;                  // frontier entries per thread per chunk
+constexpr int kClaimItems = 2;                  // frontier entries per thread per chunk
 constexpr int kClaimChunk = kBlock * kClaimItems;
 
 // Tile-pass buffers of one handle (host side; csrc/tiles.cu).
