@@ -62,7 +62,7 @@ def configure(so):
         so.orc_part_offsets.argtypes = [u64, u32, vp]
         so.orc_key_cells.argtypes = [u64, u32, u64, vp, u64, vp]
         so.orc_checksum.argtypes = [u64, u32, u64]
-        so.orc_checksum.restype = u32
+        so.orc_checksum.restype = u64
         so.orc_iblt_insert.argtypes = [u64, u32, u64, vp, u64, i64, vp, vp, vp]
         so.orc_iblt_decode_rounds.argtypes = [u64, u32, u64, vp, vp, vp, u32, vp, u64, vp, vp, vp]
         so.orc_iblt_decode_queue.argtypes = [u64, u32, u64, vp, vp, vp, vp, u64, vp]
@@ -117,30 +117,31 @@ def key_cells(n: int, r: int, table_seed: int, keys: np.ndarray) -> np.ndarray:
 
 
 def checksum(table_seed: int, r: int, x: int) -> int:
-    """checkSum(x): the upper 32 bits of mix64(x ^ checksum seed)."""
+    """checkSum(x) = mix64(x ^ checksum seed), 64 bits."""
     return int(lib().orc_checksum(table_seed, r, x))
 
 
 class IBLT:
     """A CPU IBLT: per cell the count (int64), the XOR of its keys (uint64) and
-    the signed sum of their 32-bit checksums mod 2^32 (uint32)."""
+    the XOR of their 64-bit checksums (uint64), as Sec. 6 "Motivation" defines
+    the cell's fields."""
 
     def __init__(self, n_cells: int, r: int, table_seed: int):
         self.n, self.r, self.seed = int(n_cells), int(r), int(table_seed)
         self.count = np.zeros(self.n, dtype=np.int64)
         self.keyx = np.zeros(self.n, dtype=np.uint64)
-        self.chks = np.zeros(self.n, dtype=np.uint32)
+        self.chkx = np.zeros(self.n, dtype=np.uint64)
 
     def copy(self) -> "IBLT":
         t = IBLT.__new__(IBLT)
         t.n, t.r, t.seed = self.n, self.r, self.seed
-        t.count, t.keyx, t.chks = self.count.copy(), self.keyx.copy(), self.chks.copy()
+        t.count, t.keyx, t.chkx = self.count.copy(), self.keyx.copy(), self.chkx.copy()
         return t
 
     def insert(self, keys: np.ndarray, sign: int = 1) -> None:
         keys = np.ascontiguousarray(keys, dtype=np.uint64)
         st = lib().orc_iblt_insert(self.n, self.r, self.seed, _ptr(keys), keys.size, sign,
-                                   _ptr(self.count), _ptr(self.keyx), _ptr(self.chks))
+                                   _ptr(self.count), _ptr(self.keyx), _ptr(self.chkx))
         if st != OK:
             raise ValueError(f"orc_iblt_insert status {st}")
 
@@ -157,7 +158,7 @@ class IBLT:
         alive = np.zeros(mr + 1, dtype=np.uint64)
         T = np.zeros(1, dtype=np.uint32)
         st = lib().orc_iblt_decode_rounds(self.n, self.r, self.seed, _ptr(self.count),
-                                          _ptr(self.keyx), _ptr(self.chks), mr, _ptr(out), cap,
+                                          _ptr(self.keyx), _ptr(self.chkx), mr, _ptr(out), cap,
                                           _ptr(round_end), _ptr(alive), _ptr(T))
         T = int(T[0])
         ends = [0] + [int(x) for x in round_end[:T]]
@@ -170,7 +171,7 @@ class IBLT:
         out = np.zeros(cap, dtype=np.uint64)
         got = np.zeros(1, dtype=np.uint64)
         st = lib().orc_iblt_decode_queue(self.n, self.r, self.seed, _ptr(self.count),
-                                         _ptr(self.keyx), _ptr(self.chks), _ptr(out), cap,
+                                         _ptr(self.keyx), _ptr(self.chkx), _ptr(out), cap,
                                          _ptr(got))
         return out[: int(got[0])].copy(), st
 
@@ -185,7 +186,7 @@ class IBLT:
         sub_end = np.zeros(ms + 1, dtype=np.uint64)
         S = np.zeros(1, dtype=np.uint32)
         st = lib().orc_iblt_decode_subrounds(self.n, self.r, self.seed, _ptr(self.count),
-                                             _ptr(self.keyx), _ptr(self.chks), ms, _ptr(out), cap,
+                                             _ptr(self.keyx), _ptr(self.chkx), ms, _ptr(out), cap,
                                              _ptr(sub_end), _ptr(S))
         S = int(S[0])
         ends = [0] + [int(x) for x in sub_end[:S]]
@@ -204,7 +205,7 @@ class IBLT:
         round_end = np.zeros(mr + 1, dtype=np.uint64)
         T = np.zeros(1, dtype=np.uint32)
         st = lib().orc_iblt_decode_signed(self.n, self.r, self.seed, _ptr(self.count), _ptr(self.keyx),
-                                          _ptr(self.chks), mr, _ptr(out), _ptr(sg), cap, _ptr(round_end),
+                                          _ptr(self.chkx), mr, _ptr(out), _ptr(sg), cap, _ptr(round_end),
                                           _ptr(T))
         T = int(T[0])
         ends = [0] + [int(x) for x in round_end[:T]]

@@ -31,12 +31,15 @@
  *     1..r+1 of SplitMix64 started at the table seed;
  *   - sub-table j holds floor(n/r) + [j < n mod r] cells, laid out in order;
  *   - cell_j(x) = off_j + floor(mix64(x ^ seed_j) * size_j / 2^64);
- *   - checkSum(x) = the upper 32 bits of mix64(x ^ seed_chk); a cell's
- *     checksum field is the sum, mod 2^32, of checkSum(x) over its keys,
- *     each taken with the sign of its insertion (+1) or deletion (-1);
+ *   - checkSum(x) = mix64(x ^ seed_chk), a 64-bit value;
  *   - a cell is pure iff count == 1 and its checksum field equals
- *     checkSum(key field) (signed recovery: count == s for s = +1 or -1 and
- *     the checksum field equals s * checkSum(key field) mod 2^32);
+ *     checkSum(key field) (signed recovery: count == +1 or -1 and the same
+ *     checksum test).
+ *
+ * Fixed by the paper, not a convention: the key field and the checksum field
+ * are XORs (Sec. 6 "Motivation": an inserted key is XORed into the key field
+ * of each of its cells and checkSum(x) into the checksum field; a deletion is
+ * the same XORs with the count decremented instead of incremented).
  *   - a vertex's degree counts incidences, so an edge that names a vertex
  *     twice contributes 2 to its degree and takes 2 when it is removed.
  */
@@ -74,8 +77,8 @@ static uint64_t cell_of(uint64_t x, uint32_t j, const uint64_t *seeds, const uin
   return off[j] + (uint64_t)(((unsigned __int128)h * size) >> 64);
 }
 
-static uint32_t checksum_of(uint64_t x, const uint64_t *seeds, uint32_t r) {
-  return (uint32_t)(mix64(x ^ seeds[r]) >> 32);
+static uint64_t checksum_of(uint64_t x, const uint64_t *seeds, uint32_t r) {
+  return mix64(x ^ seeds[r]);
 }
 
 /* The r cells of each key (row-major m x r), for building the key hypergraph. */
@@ -88,39 +91,38 @@ void orc_key_cells(uint64_t n, uint32_t r, uint64_t table_seed, const uint64_t *
     for (uint32_t j = 0; j < r; ++j) cells[i * r + j] = cell_of(keys[i], j, seeds, off);
 }
 
-uint32_t orc_checksum(uint64_t table_seed, uint32_t r, uint64_t x) {
+uint64_t orc_checksum(uint64_t table_seed, uint32_t r, uint64_t x) {
   uint64_t seeds[17];
   orc_hash_seeds(table_seed, r, seeds);
   return checksum_of(x, seeds, r);
 }
 
 /* IBLT insertion (sign = +1) or deletion (sign = -1), Sec. 6 "Motivation":
- * for each of the key's r cells, XOR the key into the key field, add
- * sign * checkSum(key) to the checksum field (mod 2^32) and add sign to the
- * count. */
+ * for each of the key's r cells, XOR the key into the key field, XOR
+ * checkSum(key) into the checksum field and add sign to the count. */
 int orc_iblt_insert(uint64_t n, uint32_t r, uint64_t table_seed, const uint64_t *keys,
                     uint64_t m, int64_t sign, int64_t *count, uint64_t *keyx,
-                    uint32_t *chks) {
+                    uint64_t *chkx) {
   if (r < 2 || r > 16 || n < r) return ORC_INVALID;
   uint64_t seeds[17], off[17];
   orc_hash_seeds(table_seed, r, seeds);
   orc_part_offsets(n, r, off);
   for (uint64_t i = 0; i < m; ++i) {
     uint64_t x = keys[i];
-    uint32_t cs = checksum_of(x, seeds, r);
+    uint64_t cs = checksum_of(x, seeds, r);
     for (uint32_t j = 0; j < r; ++j) {
       uint64_t c = cell_of(x, j, seeds, off);
       count[c] += sign;
       keyx[c] ^= x;
-      chks[c] += (uint32_t)sign * cs;
+      chkx[c] ^= cs;
     }
   }
   return ORC_OK;
 }
 
-static int is_pure(uint64_t c, const int64_t *count, const uint64_t *keyx, const uint32_t *chks,
+static int is_pure(uint64_t c, const int64_t *count, const uint64_t *keyx, const uint64_t *chkx,
                    const uint64_t *seeds, uint32_t r) {
-  return count[c] == 1 && chks[c] == checksum_of(keyx[c], seeds, r);
+  return count[c] == 1 && chkx[c] == checksum_of(keyx[c], seeds, r);
 }
 
 static int cmp_u64(const void *a, const void *b) {
@@ -146,7 +148,7 @@ static int cmp_u64(const void *a, const void *b) {
  * Returns ORC_CAPACITY if out_cap is too small and ORC_ROUND_LIMIT if K_t is
  * still non-empty at t = max_rounds + 1. */
 int orc_iblt_decode_rounds(uint64_t n, uint32_t r, uint64_t table_seed, int64_t *count,
-                           uint64_t *keyx, uint32_t *chks, uint32_t max_rounds,
+                           uint64_t *keyx, uint64_t *chkx, uint32_t max_rounds,
                            uint64_t *out_keys, uint64_t out_cap, uint64_t *round_end,
                            uint64_t *cells_alive, uint32_t *rounds_out) {
   if (r < 2 || r > 16 || n < r) return ORC_INVALID;
@@ -164,7 +166,7 @@ int orc_iblt_decode_rounds(uint64_t n, uint32_t r, uint64_t table_seed, int64_t 
     uint64_t np = 0, alive = 0;
     for (uint64_t c = 0; c < n; ++c) {
       if (count[c] >= 2) ++alive;
-      if (is_pure(c, count, keyx, chks, seeds, r)) pure_keys[np++] = keyx[c];
+      if (is_pure(c, count, keyx, chkx, seeds, r)) pure_keys[np++] = keyx[c];
     }
     if (np == 0) break;
     if (t == max_rounds) { status = ORC_ROUND_LIMIT; break; }
@@ -177,12 +179,12 @@ int orc_iblt_decode_rounds(uint64_t n, uint32_t r, uint64_t table_seed, int64_t 
     /* Delete every key of K_t from its r cells. */
     for (uint64_t i = 0; i < nk; ++i) {
       const uint64_t x = pure_keys[i];
-      const uint32_t cs = checksum_of(x, seeds, r);
+      const uint64_t cs = checksum_of(x, seeds, r);
       for (uint32_t j = 0; j < r; ++j) {
         uint64_t c = cell_of(x, j, seeds, off);
         count[c] -= 1;
         keyx[c] ^= x;
-        chks[c] -= cs;
+        chkx[c] ^= cs;
       }
       out_keys[total + i] = x;
     }
@@ -200,7 +202,7 @@ int orc_iblt_decode_rounds(uint64_t n, uint32_t r, uint64_t table_seed, int64_t 
  * key and delete it from its r cells, until no pure cell is left.  Keys come out
  * in the order found; the recovered set is order-independent. */
 int orc_iblt_decode_queue(uint64_t n, uint32_t r, uint64_t table_seed, int64_t *count,
-                          uint64_t *keyx, uint32_t *chks, uint64_t *out_keys,
+                          uint64_t *keyx, uint64_t *chkx, uint64_t *out_keys,
                           uint64_t out_cap, uint64_t *n_out) {
   if (r < 2 || r > 16 || n < r) return ORC_INVALID;
   uint64_t seeds[17], off[17];
@@ -211,21 +213,21 @@ int orc_iblt_decode_queue(uint64_t n, uint32_t r, uint64_t table_seed, int64_t *
   uint64_t *stack = (uint64_t *)malloc(cap * sizeof(uint64_t));
   if (!stack) return ORC_NOMEM;
   for (uint64_t c = 0; c < n; ++c)
-    if (is_pure(c, count, keyx, chks, seeds, r)) stack[top++] = c;
+    if (is_pure(c, count, keyx, chkx, seeds, r)) stack[top++] = c;
   uint64_t got = 0;
   int status = ORC_OK;
   while (top > 0) {
     uint64_t c = stack[--top];
-    if (!is_pure(c, count, keyx, chks, seeds, r)) continue;
+    if (!is_pure(c, count, keyx, chkx, seeds, r)) continue;
     const uint64_t x = keyx[c];
-    const uint32_t cs = checksum_of(x, seeds, r);
+    const uint64_t cs = checksum_of(x, seeds, r);
     if (got == out_cap) { status = ORC_CAPACITY; break; }
     out_keys[got++] = x;
     for (uint32_t j = 0; j < r; ++j) {
       uint64_t d = cell_of(x, j, seeds, off);
       count[d] -= 1;
       keyx[d] ^= x;
-      chks[d] -= cs;
+      chkx[d] ^= cs;
       if (count[d] == 1) {
         if (top == cap) {
           cap *= 2;
@@ -444,7 +446,7 @@ int orc_kcore_subrounds(uint32_t n, uint32_t r, uint32_t k, const uint32_t *edge
  * Returns ORC_CAPACITY if out_cap is too small and ORC_ROUND_LIMIT if a
  * sub-round past max_subrounds would recover a key. */
 int orc_iblt_decode_subrounds(uint64_t n, uint32_t r, uint64_t table_seed, int64_t *count,
-                              uint64_t *keyx, uint32_t *chks, uint32_t max_subrounds,
+                              uint64_t *keyx, uint64_t *chkx, uint32_t max_subrounds,
                               uint64_t *out_keys, uint64_t out_cap, uint64_t *sub_end,
                               uint32_t *S_out) {
   if (r < 2 || r > 16 || n < r) return ORC_INVALID;
@@ -461,7 +463,7 @@ int orc_iblt_decode_subrounds(uint64_t n, uint32_t r, uint64_t table_seed, int64
     /* the pure cells of sub-table j at the start of the sub-round */
     uint64_t nf = 0;
     for (uint64_t c = off[j]; c < off[j + 1]; ++c)
-      if (is_pure(c, count, keyx, chks, seeds, r)) found[nf++] = keyx[c];
+      if (is_pure(c, count, keyx, chkx, seeds, r)) found[nf++] = keyx[c];
     if (nf == 0) {
       if (s < max_subrounds) sub_end[s] = total;
       ++idle;
@@ -474,13 +476,13 @@ int orc_iblt_decode_subrounds(uint64_t n, uint32_t r, uint64_t table_seed, int64
     qsort(found, nf, sizeof(uint64_t), cmp_u64);
     for (uint64_t i = 0; i < nf; ++i) {
       const uint64_t x = found[i];
-      const uint32_t cs = checksum_of(x, seeds, r);
+      const uint64_t cs = checksum_of(x, seeds, r);
       out_keys[total + i] = x;
       for (uint32_t q = 0; q < r; ++q) {
         uint64_t c = cell_of(x, q, seeds, off);
         count[c] -= 1;
         keyx[c] ^= x;
-        chks[c] -= cs;
+        chkx[c] ^= cs;
       }
     }
     total += nf;
@@ -496,14 +498,14 @@ int orc_iblt_decode_subrounds(uint64_t n, uint32_t r, uint64_t table_seed, int64
 /* Signed IBLT recovery: the table holds a set difference (keys inserted with
  * sign +1 and deleted with sign -1 that were never inserted), as in the sparse
  * recovery use of Sec. 6 "Motivation".  A cell is pure when count == s for
- * s = +1 or -1 and its checksum field equals s * checkSum(key field) mod 2^32;
- * its key comes out with the sign s.
+ * s = +1 or -1 and its checksum field equals checkSum(key field) (the field is
+ * an XOR, so it does not carry the sign); its key comes out with the sign s.
  *
  * Round t (Sec. 1's round rule at k = 2 on the hypergraph of the difference):
  *   P_t = every cell pure at the start of round t;
  *   K_t = the distinct (key, sign) pairs found in P_t;
  *   each (x, s) in K_t is removed from its r cells: count -= s, XOR x out
- *   of the key field, subtract s * checkSum(x) from the checksum field.
+ *   of the key field and checkSum(x) out of the checksum field.
  * The loop ends at the first round with K_t empty; *rounds_out counts the
  * rounds that recovered something.  out_keys / out_signs receive K_1, K_2,
  * ... in order, each round sorted by (key, sign); round_end[t-1] = the total
@@ -518,7 +520,7 @@ static int cmp_signed(const void *a, const void *b) {
 }
 
 int orc_iblt_decode_signed(uint64_t n, uint32_t r, uint64_t table_seed, int64_t *count, uint64_t *keyx,
-                           uint32_t *chks, uint32_t max_rounds, uint64_t *out_keys, int8_t *out_signs,
+                           uint64_t *chkx, uint32_t max_rounds, uint64_t *out_keys, int8_t *out_signs,
                            uint64_t out_cap, uint64_t *round_end, uint32_t *rounds_out) {
   if (r < 2 || r > 16 || n < r) return ORC_INVALID;
   uint64_t seeds[17], off[17];
@@ -534,7 +536,7 @@ int orc_iblt_decode_signed(uint64_t n, uint32_t r, uint64_t table_seed, int64_t 
     uint64_t nf = 0;
     for (uint64_t c = 0; c < n; ++c) {
       if ((count[c] == 1 || count[c] == -1) &&
-          chks[c] == (uint32_t)count[c] * checksum_of(keyx[c], seeds, r)) {
+          chkx[c] == checksum_of(keyx[c], seeds, r)) {
         found[nf].x = keyx[c];
         found[nf].s = count[c];
         ++nf;
@@ -549,7 +551,7 @@ int orc_iblt_decode_signed(uint64_t n, uint32_t r, uint64_t table_seed, int64_t 
     if (total + nk > out_cap) { status = ORC_CAPACITY; break; }
     for (uint64_t i = 0; i < nk; ++i) {
       const uint64_t x = found[i].x;
-      const uint32_t cs = checksum_of(x, seeds, r);
+      const uint64_t cs = checksum_of(x, seeds, r);
       const int64_t sg = found[i].s;
       out_keys[total + i] = x;
       out_signs[total + i] = (int8_t)sg;
@@ -557,7 +559,7 @@ int orc_iblt_decode_signed(uint64_t n, uint32_t r, uint64_t table_seed, int64_t 
         const uint64_t c = cell_of(x, q, seeds, off);
         count[c] -= sg;
         keyx[c] ^= x;
-        chks[c] -= (uint32_t)sg * cs;
+        chkx[c] ^= cs;
       }
     }
     total += nk;

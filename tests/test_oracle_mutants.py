@@ -33,17 +33,20 @@ MUTANTS = [
      "uint64_t h = mix64(x ^ seeds[j]);",
      "uint64_t h = mix64(x ^ seeds[0]);"),
     ("checksum not removed on recovery",
-     "        keyx[c] ^= x;\n        chks[c] -= cs;\n      }\n      out_keys[total + i] = x;",
+     "        keyx[c] ^= x;\n        chkx[c] ^= cs;\n      }\n      out_keys[total + i] = x;",
      "        keyx[c] ^= x;\n      }\n      out_keys[total + i] = x;"),
     ("pure test drops the checksum comparison",
-     "return count[c] == 1 && chks[c] == checksum_of(keyx[c], seeds, r);",
-     "return count[c] == 1 || chks[c] == checksum_of(keyx[c], seeds, r);"),
-    ("checksum is the lower half of mix64",
-     "return (uint32_t)(mix64(x ^ seeds[r]) >> 32);",
-     "return (uint32_t)mix64(x ^ seeds[r]);"),
-    ("insertion adds the checksum without its sign",
-     "chks[c] += (uint32_t)sign * cs;",
-     "chks[c] += cs;"),
+     "return count[c] == 1 && chkx[c] == checksum_of(keyx[c], seeds, r);",
+     "return count[c] == 1 || chkx[c] == checksum_of(keyx[c], seeds, r);"),
+    ("checksum keeps only the upper half of mix64",
+     "  return mix64(x ^ seeds[r]);\n}",
+     "  return mix64(x ^ seeds[r]) >> 32;\n}"),
+    ("checksum summed instead of XORed",
+     "      chkx[c] ^= cs;\n    }\n  }\n  return ORC_OK;",
+     "      chkx[c] += (uint64_t)sign * cs;\n    }\n  }\n  return ORC_OK;"),
+    ("checksum taken of the key's cell seed instead of its own",
+     "  return mix64(x ^ seeds[r]);\n}",
+     "  return mix64(x ^ seeds[0]);\n}"),
     ("a key pure in two cells is recovered twice",
      "if (i == 0 || pure_keys[i] != pure_keys[i - 1]) pure_keys[nk++] = pure_keys[i];",
      "pure_keys[nk++] = pure_keys[i];"),
@@ -74,15 +77,12 @@ MUTANTS = [
     ("signed purity misses negative counts",
      "if ((count[c] == 1 || count[c] == -1) &&",
      "if ((count[c] == 1) &&"),
-    ("signed purity ignores the sign of the checksum",
-     "chks[c] == (uint32_t)count[c] * checksum_of(keyx[c], seeds, r)) {",
-     "chks[c] == checksum_of(keyx[c], seeds, r)) {"),
+    ("signed purity compares against a signed checksum",
+     "          chkx[c] == checksum_of(keyx[c], seeds, r)) {",
+     "          chkx[c] == (uint64_t)count[c] * checksum_of(keyx[c], seeds, r)) {"),
     ("signed recovery leaves the checksum in",
-     "        chks[c] -= (uint32_t)sg * cs;\n      }\n    }\n    total += nk;",
-     "      }\n    }\n    total += nk;"),
-    ("signed removal subtracts the checksum without its sign",
-     "        chks[c] -= (uint32_t)sg * cs;\n      }\n    }\n    total += nk;",
-     "        chks[c] -= cs;\n      }\n    }\n    total += nk;"),
+     "        keyx[c] ^= x;\n        chkx[c] ^= cs;\n      }\n    }\n    total += nk;",
+     "        keyx[c] ^= x;\n      }\n    }\n    total += nk;"),
     ("mix64 shift constant off by one",
      "z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;",
      "z = (z ^ (z >> 28)) * 0x94D049BB133111EBULL;"),
@@ -96,6 +96,8 @@ PINS = [
     lambda: pins.test_handmade_expected_values(),
     lambda: pins.test_random_tiny_hypergraphs_vs_brute_force(),
     lambda: pins.test_iblt_build_definition(),
+    lambda: pins.test_iblt_checksum_field_is_an_xor(),
+    lambda: pins.test_cell_map_boundaries(),
     lambda: pins.test_iblt_rounds_equal_kcore_rounds(4000, 3, 0.7, 1),
     lambda: pins.test_iblt_rounds_equal_kcore_rounds(3000, 4, 0.85, 3),
     lambda: pins.test_iblt_below_threshold_recovered_inserted_set_wrapper(),

@@ -6,8 +6,10 @@
 * IBLT: recovered set == inserted set iff the 2-core of the key hypergraph is
   empty (Sec. 6); per-round recovery == per-round edge removal of the k=2 peel
   on the same hypergraph; XOR/count residue invariants after a failed decode.
-* hash convention: the published SplitMix64 vector and the frozen known-answer
-  file.
+* hash convention: the published SplitMix64 vector (finaliser and seed
+  stream), the boundaries of the range map (keys with a chosen hash, made by
+  inverting mix64), and the frozen known-answer file.
+* checksum field: Sec. 6's XOR (insertion and deletion are the same XOR).
 """
 import itertools
 
@@ -41,6 +43,55 @@ def test_mix64_published_splitmix_vector():
 def test_hash_seeds_are_splitmix_outputs():
     seeds = oracle.hash_seeds(0x13027014, 3)
     assert [int(s) for s in seeds] == [int(x) for x in ppgen.splitmix64_stream(0x13027014, 4)]
+    # s_0..s_r are outputs 1..r+1 of SplitMix64 started at the table seed: for
+    # the published generator's seed they are its published outputs
+    row = read_golden("splitmix64_published.txt")[0]
+    assert [int(s) for s in oracle.hash_seeds(int(row[0]), 4)] == [int(x) for x in row[1:6]]
+
+
+_C1, _C2 = 0xBF58476D1CE4E5B9, 0x94D049BB133111EB
+_M64 = (1 << 64) - 1
+
+
+def _unshift_right(y, s):
+    # inverse of z -> z ^ (z >> s) on 64 bits
+    z = y
+    for _ in range(64 // s + 1):
+        z = y ^ (z >> s)
+    return z & _M64
+
+
+def _unmix64(h):
+    # inverse of the SplitMix64 finaliser: undo each xorshift and multiply by
+    # the inverse of each odd constant mod 2^64
+    z = _unshift_right(h, 31)
+    z = (z * pow(_C2, -1, 1 << 64)) & _M64
+    z = _unshift_right(z, 27)
+    z = (z * pow(_C1, -1, 1 << 64)) & _M64
+    return _unshift_right(z, 30)
+
+
+def test_cell_map_boundaries():
+    # The cell map splits the 2^64 hash values of sub-table j into size_j
+    # intervals of equal width, in order: hash 0 goes to the first cell, 2^64-1
+    # to the last, and cell k starts at the first h with h * size >= k * 2^64.
+    # Keys with a chosen hash are made by inverting mix64 (a bijection).
+    for n, r, seed in [(1000, 3, 5), (4096, 4, 7), (257, 5, 9), ((1 << 26), 3, 0x13027014)]:
+        seeds = [int(s) for s in oracle.hash_seeds(seed, r)]
+        offs = [int(o) for o in oracle.part_offsets(n, r)]
+        for j in range(r):
+            size = offs[j + 1] - offs[j]
+            probes = [(0, 0), (_M64, size - 1)]
+            for k in (1, size // 3, size // 2, size - 1):
+                if k <= 0:
+                    continue
+                first = -(-(k << 64) // size)      # ceil(k 2^64 / size)
+                probes += [(first, k), (first - 1, k - 1)]
+            for h, want in probes:
+                x = _unmix64(h) ^ seeds[j]
+                assert oracle.mix64(x ^ seeds[j]) == h
+                got = int(oracle.key_cells(n, r, seed, np.array([x], np.uint64))[0][j])
+                assert got == offs[j] + want, (n, r, j, h)
 
 
 def test_part_offsets_headline():
@@ -198,26 +249,60 @@ def _iblt(n, r, c, seed, key_seed):
 
 
 def test_iblt_build_definition():
-    # count = number of keys per cell, key field = XOR of those keys (Sec. 6)
+    # Sec. 6 "Motivation": inserting x XORs x into the key field and checkSum(x)
+    # into the checksum field of each of its r cells, and adds 1 to the count.
     n, r, seed = 500, 3, 11
     t, keys = _iblt(n, r, 0.6, seed, 12)
     cells = oracle.key_cells(n, r, seed, keys)
     cnt = np.zeros(n, np.int64)
     kx = np.zeros(n, np.uint64)
-    cx = [0] * n
+    cx = np.zeros(n, np.uint64)
     s_chk = int(oracle.hash_seeds(seed, r)[r])
     for x, row in zip(keys, cells):
-        # checkSum(x) is the upper half of the (published-pinned) mix64 finaliser
-        cs = oracle.mix64(int(x) ^ s_chk) >> 32
+        # checkSum(x) is the (published-pinned) mix64 finaliser of x ^ s_chk
+        cs = oracle.mix64(int(x) ^ s_chk)
         assert oracle.checksum(seed, r, int(x)) == cs
         for c in row:
             cnt[c] += 1
             kx[c] ^= x
-            cx[c] = (cx[c] + cs) % (1 << 32)
-    assert (t.count == cnt).all() and (t.keyx == kx).all() and t.chks.tolist() == cx
+            cx[c] ^= np.uint64(cs)
+    assert (t.count == cnt).all() and (t.keyx == kx).all() and (t.chkx == cx).all()
     # deletion undoes insertion; deleting everything empties the table
     t.insert(keys, sign=-1)
-    assert not t.count.any() and not t.keyx.any() and not t.chks.any()
+    assert not t.count.any() and not t.keyx.any() and not t.chkx.any()
+
+
+def test_iblt_checksum_field_is_an_xor():
+    # Insertion and deletion are the same XORs on both fields (Sec. 6
+    # "Motivation"); only the count tells them apart.  A sum would give
+    # 2 checkSum(x) after a double insertion and -checkSum(x) after a deletion.
+    n, r, seed = 64, 3, 3
+    x = np.array([0x0123456789ABCDEF], np.uint64)
+    cs = oracle.checksum(seed, r, int(x[0]))
+    cells = [int(c) for c in oracle.key_cells(n, r, seed, x)[0]]
+    t = oracle.IBLT(n, r, seed)
+    t.insert(x)
+    assert [int(t.chkx[c]) for c in cells] == [cs] * r
+    t.insert(x)      # the same key twice: both XOR fields cancel, count 2
+    assert [int(t.chkx[c]) for c in cells] == [0] * r
+    assert [int(t.keyx[c]) for c in cells] == [0] * r
+    assert [int(t.count[c]) for c in cells] == [2] * r
+    u = oracle.IBLT(n, r, seed)
+    u.insert(x, sign=-1)     # a deletion of an absent key: same fields, count -1
+    assert [int(u.chkx[c]) for c in cells] == [cs] * r
+    assert [int(u.keyx[c]) for c in cells] == [int(x[0])] * r
+    assert [int(u.count[c]) for c in cells] == [-1] * r
+    # the field is the XOR of the checksums whatever the order of insertion
+    ks = ppgen.distinct_keys(40, 77)
+    a, b = oracle.IBLT(n, r, seed), oracle.IBLT(n, r, seed)
+    a.insert(ks)
+    b.insert(ks[::-1].copy())
+    assert (a.chkx == b.chkx).all()
+    want = 0
+    for k in ks.tolist():
+        if 0 in [int(c) for c in oracle.key_cells(n, r, seed, np.array([k], np.uint64))[0]]:
+            want ^= oracle.checksum(seed, r, k)
+    assert int(a.chkx[0]) == want
 
 
 @pytest.mark.parametrize("n,r,c", [(3000, 3, 0.6), (3000, 4, 0.7), (2048, 3, 0.75), (999, 5, 0.6)])
@@ -271,11 +356,13 @@ def test_iblt_residue_invariants_above_threshold():
         for k in left:
             x ^= k
         assert int(np.bitwise_xor.reduce(t.keyx[part])) == x
-        cx = sum(oracle.checksum(seed, r, k) for k in left) % (1 << 32)
-        assert sum(int(v) for v in t.chks[part]) % (1 << 32) == cx
+        cx = 0
+        for k in left:
+            cx ^= oracle.checksum(seed, r, k)
+        assert int(np.bitwise_xor.reduce(t.chkx[part])) == cx
     # no pure cell is left
     for c in range(n):
-        assert not (t.count[c] == 1 and int(t.chks[c]) == oracle.checksum(seed, r, int(t.keyx[c])))
+        assert not (t.count[c] == 1 and int(t.chkx[c]) == oracle.checksum(seed, r, int(t.keyx[c])))
 
 
 def test_iblt_queue_and_rounds_agree():
@@ -334,7 +421,7 @@ def test_iblt_checksum_rejects_impure_count_one():
     t.insert(dele, sign=-1)
     mixed = 0
     for c in range(n):
-        if t.count[c] == 1 and int(t.chks[c]) != oracle.checksum(seed, r, int(t.keyx[c])):
+        if t.count[c] == 1 and int(t.chkx[c]) != oracle.checksum(seed, r, int(t.keyx[c])):
             mixed += 1
     assert mixed > 0
     res = t.decode_rounds()

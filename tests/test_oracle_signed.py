@@ -59,7 +59,7 @@ def test_set_difference_recovered(n, r, seed):
     signs = np.concatenate(res["signs"])
     assert np.array_equal(np.sort(keys[signs == 1]), np.sort(only_a))
     assert np.array_equal(np.sort(keys[signs == -1]), np.sort(only_b))
-    assert not t.count.any() and not t.keyx.any() and not t.chks.any()
+    assert not t.count.any() and not t.keyx.any() and not t.chkx.any()
 
 
 def test_swap_flips_every_sign():

@@ -210,7 +210,7 @@ def test_iblt_subrounds_same_outcome_as_rounds():
         kb = np.sort(np.concatenate(b["keys"])) if b["keys"] else np.zeros(0, np.uint64)
         assert np.array_equal(ka, kb)
         assert np.array_equal(t.count, u.count)
-        assert np.array_equal(t.keyx, u.keyx) and np.array_equal(t.chks, u.chks)
+        assert np.array_equal(t.keyx, u.keyx) and np.array_equal(t.chkx, u.chkx)
 
 
 def test_iblt_subrounds_recover_inserted_set_below_threshold():
