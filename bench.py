@@ -297,18 +297,18 @@ def bench_batched(pp, torch, args):
     torch.cuda.empty_cache()
     n = len(tabs)
     # sector-floor bytes of one step, as for the headline table: the clear writes
-    # every 16 B cell, the build 8 + 64 r B per key, the decode one scan of the
-    # cells plus 64 r + 8 B per key; the 7.5 GB arena is far larger than L2
+    # every 32 B cell, the build 8 + 64 r B per key, the decode the 4 B count of
+    # every cell plus 64 r + 16 B per key; the arena is far larger than L2
     cells = sum(t.n_cells for t in tabs)
-    step_bytes = 16 * cells + sum(k.size * (8 + 64 * t.r) for k, t in zip(keys, tabs)) + \
-        16 * cells + sum(k.size * (64 * t.r + 8) for k, t in zip(keys, tabs))
+    step_bytes = 32 * cells + sum(k.size * (8 + 64 * t.r) for k, t in zip(keys, tabs)) + \
+        4 * cells + sum(k.size * (64 * t.r + 16) for k, t in zip(keys, tabs))
     peak, peak_kind = hbm_peak()
     achieved = step_bytes / (b_ms * 1e-3) / 1e9
     return {"workload": "4096 IBLTs, cells log-uniform [2^8,2^20), r in {3,4}, load U[0.5, 0.9 c*]",
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "peak_source": f"{peak_kind} hbm_gbs",
-                         "model": "sector floor: 16 B/cell clear + 16 B/cell scan + (8+64r) B/key build "
-                                  "+ (64r+8) B/key decode"},
+                         "model": "sector floor: 32 B/cell clear + (8+64r) B/key build + 4 B/cell scan "
+                                  "+ (64r+16) B/key decode"},
             "tables": n, "cells": int(sum(t.n_cells for t in tabs)), "keys": total_keys,
             "batched_ms": b_ms, "plain_loop_ms": p_ms,
             "batched_tables_per_s": n / (b_ms * 1e-3), "plain_tables_per_s": n / (p_ms * 1e-3),
@@ -812,7 +812,8 @@ def main():
     # roofline of the two halves of a step (sector-floor byte model)
     peak, peak_kind = hbm_peak()
     build_bytes = m * (8 + 64 * r)                 # key read + r cell sectors read+written
-    decode_bytes = n * 16 + m * (64 * r + 8)       # one full scan of the 16 B cells + r sector RMW + key out
+    # the scan's 4 B count per cell + per key r sector RMWs, the key out and its frontier entry
+    decode_bytes = n * 4 + m * (64 * r + 16)
     b_ms, d_ms = float(np.mean(build_ms)), float(np.mean(decode_ms))
     kernels = {
         "build": {"kernel": "k_bin + k_tile_step per slab (slab-binned, tiles in shared memory)", "ms": b_ms,
@@ -827,7 +828,7 @@ def main():
     roofline = {"bound": "hbm", "achieved": dk["achieved_gbs"], "peak": peak, "unit": "GB/s",
                 "frac": dk["achieved_gbs"] / peak, "traffic": traffic,
                 "kernel": dk["kernel"], "peak_source": f"{peak_kind} hbm_gbs",
-                "model": "sector floor: 16 B/cell scan + (64r+8) B/key decode; (8+64r) B/key build"}
+                "model": "sector floor: 4 B/cell scan + (64r+16) B/key decode; (8+64r) B/key build"}
     if traffic:
         # DRAM bytes the unit actually moves (ncu, committed summary) over the same time:
         # a random touch of a 32 B sector costs a 64 B read and its write-back, twice the model
@@ -860,7 +861,8 @@ def main():
                 "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
                 "config": {"workload": cfg["name"], "n_cells": n, "r": r, "load": c, "keys": m,
-                           "rounds": rounds, "l2": f"inputs > L2 ({n * 16 / 1e9:.2f} GB table, {m * 8 / 1e9:.2f} GB keys)",
+                           "rounds": rounds, "l2": f"inputs > L2 ({n * 32 / 1e9:.2f} GB table, {m * 8 / 1e9:.2f} GB keys)",
+                           "cell": "32 B: u64 key XOR, u64 checksum XOR, i32 count, padding",
                            "parallelism": f"replicas x{world}" if world > 1 else "single",
                            "round_loop": "host" if args.host_loop else "graph"},
                 "build_ms": b_ms, "decode_ms": d_ms, "peel_ms": d_ms,

@@ -88,31 +88,31 @@ const char *pp_last_error(void);
 /* ------------------------------------------------------------------------
  * IBLT (Sec. 6 "Motivation" and "Implementation Details"; App. B layout)
  *
- * Cell layout in device memory (16 bytes, 16-byte aligned, cell i at
- * byte 16*i of the table):
+ * Cell layout in device memory (32 bytes, 32-byte aligned, cell i at
+ * byte 32*i of the table; one DRAM sector per cell):
  *     uint64 key_xor;    XOR of the keys in the cell
- *     uint64 count_chk;  the count and the checksum sum in one word: the sum,
- *                        mod 2^64, of s * (checkSum(x) * 2^32 + 1) over the
- *                        cell's keys x, s = +1 for an insertion and -1 for a
- *                        deletion.  Its low 32 bits are the count (inserts -
- *                        deletes, two's complement int32); the checksum sum
- *                        S = sum of s * checkSum(x) mod 2^32 is
- *                        (count_chk - (int64)count) >> 32.
+ *     uint64 chk_xor;    XOR of checkSum(x) over the cell's keys
+ *     int32  count;      insertions minus deletions
+ *     uint32 pad0;       0
+ *     uint64 pad1;       0
+ * Insertion and deletion are the same two XORs; only the count tells them
+ * apart (Sec. 6 "Motivation").
  * Cells are split into r sub-tables, in order; sub-table j holds
  * floor(n/r) + [j < n mod r] cells.  Key x lives in cell
  *     off_j + floor(mix64(x ^ s_j) * size_j / 2^64)   of each sub-table j,
- * and checkSum(x) = the upper 32 bits of mix64(x ^ s_r), where mix64 is the
- * SplitMix64 finaliser and s_0..s_r are outputs 1..r+1 of SplitMix64 started
- * at the table seed.  A cell is pure iff count == 1 and S == checkSum(key_xor),
- * that is iff count_chk == checkSum(key_xor) * 2^32 + 1.  The signed decode
- * also takes count == -1 with S == -checkSum(key_xor) mod 2^32 (count_chk ==
- * -(checkSum(key_xor) * 2^32 + 1) mod 2^64).
+ * and checkSum(x) = mix64(x ^ s_r), where mix64 is the SplitMix64 finaliser
+ * and s_0..s_r are outputs 1..r+1 of SplitMix64 started at the table seed.
+ * A cell is pure iff count == 1 and chk_xor == checkSum(key_xor); the signed
+ * decode also takes count == -1 with the same checksum test.
  * ------------------------------------------------------------------------ */
 typedef struct pp_iblt pp_iblt;
 
 typedef struct pp_cell {
   uint64_t key_xor;
-  uint64_t count_chk;
+  uint64_t chk_xor;
+  int32_t count;
+  uint32_t pad0;
+  uint64_t pad1;
 } pp_cell;
 
 /* Result of a decode.  The caller sets round_cap and the three array pointers
@@ -468,8 +468,8 @@ pp_status pp_server_stop(pp_server *s, int drain);
  *
  * Decodes the caller's table in place, exactly as pp_iblt_decode does (same
  * kernels, same rounds, same results); rounds are driven from the host.
- * d_cells: n_cells pp_cell records on the device (layout above), built with
- * the same r and seed.  d_out_keys/out_cap and *res as for pp_iblt_decode;
+ * d_cells: n_cells pp_cell records on the device (layout above, 32-byte
+ * aligned), built with the same r and seed.  d_out_keys/out_cap and *res as for pp_iblt_decode;
  * items_before is computed from the cells (sum of counts / r), and out_cap
  * below it returns CAPACITY before anything is decoded.
  *
@@ -477,10 +477,18 @@ pp_status pp_server_stop(pp_server *s, int drain);
  * code, which each GPU that loads the library keeps until the process exits.
  * It holds tables of at most PP_NOALLOC_MAX_CELLS cells and decodes of at
  * most PP_NOALLOC_MAX_ROUNDS rounds; larger tables give INVALID_ARG, longer
- * decodes ROUND_LIMIT.  The first call on each device looks up that array's
- * device address: make it before any stream capture.  All calls on a device
- * share the array: calls whose GPU work overlaps race and must be serialised.
- * No cudaMalloc/cudaFree or other allocating routine is called.
+ * decodes ROUND_LIMIT.
+ * First call on a device: under the CUDA runtime's default lazy module
+ * loading, the library's device code (and with it the array) is loaded on a
+ * GPU by the first call of this function there, and that load takes device
+ * memory.  Make the first call at start-up, before the host framework
+ * reserves its memory pool and before any stream capture, or run the process
+ * with CUDA_MODULE_LOADING=EAGER.  Every call looks up the array's device
+ * address again (cudaGetSymbolAddress), so nothing stale survives a
+ * cudaDeviceReset.  After that first load no call allocates: no
+ * cudaMalloc/cudaFree or other allocating routine is called.
+ * All calls on a device share the array: calls whose GPU work overlaps race
+ * and must be serialised.  Misaligned d_cells or d_out_keys: INVALID_ARG.
  * Synchronizes `stream`.
  * ------------------------------------------------------------------------ */
 #define PP_NOALLOC_MAX_CELLS (1u << 20)

@@ -34,23 +34,17 @@ class PPError(RuntimeError):
         super().__init__(f"{fn}: {self.name}: {msg}")
 
 
-# A pp_cell as stored on the device, and its fields split out for reading.
-CELL_DTYPE = [("key_xor", "<u8"), ("count_chk", "<u8")]
-CELL_FIELDS_DTYPE = [("key_xor", "<u8"), ("count", "<i4"), ("chk_sum", "<u4")]
+# A pp_cell as stored on the device (32 bytes: key XOR, checksum XOR, count).
+CELL_DTYPE = [("key_xor", "<u8"), ("chk_xor", "<u8"), ("count", "<i4"), ("pad0", "<u4"), ("pad1", "<u8")]
 
 
 def unpack_cells(raw):
-    """Splits stored cells (CELL_DTYPE) into key_xor, count and chk_sum: count is
-    the low 32 bits of count_chk, chk_sum = (count_chk - count) >> 32."""
+    """Stored cells (bytes or a CELL_DTYPE array) as a structured array with the
+    fields key_xor, chk_xor and count."""
     import numpy as np
-    raw = np.asarray(raw).view(np.dtype(CELL_DTYPE))
-    cc = raw["count_chk"]
-    count = (cc & np.uint64(0xFFFFFFFF)).astype(np.uint32).view(np.int32)
-    out = np.empty(raw.shape, dtype=np.dtype(CELL_FIELDS_DTYPE))
-    out["key_xor"] = raw["key_xor"]
-    out["count"] = count
-    out["chk_sum"] = ((cc - count.astype(np.int64).view(np.uint64)) >> np.uint64(32)).astype(np.uint32)
-    return out
+    if isinstance(raw, (bytes, bytearray, memoryview)):
+        return np.frombuffer(raw, dtype=np.dtype(CELL_DTYPE))
+    return np.asarray(raw).view(np.dtype(CELL_DTYPE))
 
 
 def _check(status: int, fn: str):
@@ -194,8 +188,8 @@ class IBLT:
                              res.status_flags, stats[0, :n].tolist(), stats[1, :n].tolist(), stats[2, :n].tolist())
 
     def cells(self, stream=None):
-        """Host copy of the table as a numpy structured array (key_xor, count,
-        chk_sum); see unpack_cells."""
+        """Host copy of the table as a numpy structured array (key_xor, chk_xor,
+        count); see unpack_cells."""
         import numpy as np
         out = np.zeros(self.n_cells, dtype=np.dtype(CELL_DTYPE))
         _check(_lib.load().pp_iblt_copy_cells(self._h, ctypes.c_void_p(out.ctypes.data), 0,

@@ -40,8 +40,8 @@ class PeelResult(ctypes.Structure):
 
 
 class Cell(ctypes.Structure):
-    # count_chk: the count (low 32 bits) and the checksum sum in one word, see pp_cell
-    _fields_ = [("key_xor", u64), ("count_chk", u64)]
+    # see pp_cell: the key XOR, the checksum XOR and the count, one 32-byte sector
+    _fields_ = [("key_xor", u64), ("chk_xor", u64), ("count", ctypes.c_int32), ("pad0", u32), ("pad1", u64)]
 
 
 _SIGNATURES = {

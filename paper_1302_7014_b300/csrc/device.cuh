@@ -22,18 +22,36 @@ enum : u32 {
   FLAG_INTERNAL = 8u      // an invariant failed (frontier cell not among its key's cells)
 };
 
-// One IBLT cell: 16 bytes, two to a 32-byte sector.  cw holds the count and
-// the checksum sum in one word: sum of s * (checkSum(x) * 2^32 + 1) mod 2^64
-// over the cell's keys (s = +1 inserted, -1 deleted), so its low 32 bits are
-// the count and one 64-bit atomic add updates both fields.
-struct __align__(16) Cell {
-  u64 key;  // XOR of the keys in the cell
-  u64 cw;   // count (low 32 bits) and checksum sum, see above
+// One IBLT cell (Sec. 6 "Motivation"): the XOR of its keys, the XOR of their
+// checksums and their count, padded to one 32-byte DRAM sector so that a
+// random touch of a cell costs one sector.
+struct __align__(32) Cell {
+  u64 key;    // XOR of the keys in the cell
+  u64 chk;    // XOR of checkSum(x) over the cell's keys
+  int count;  // keys inserted minus keys deleted
+  u32 pad0;   // always 0
+  u64 pad1;   // always 0
 };
-static_assert(sizeof(Cell) == 16, "cell must be 16 bytes");
+static_assert(sizeof(Cell) == 32, "cell must be one 32-byte sector");
 static_assert(sizeof(Cell) == sizeof(pp_cell), "public and device cell layouts differ");
 
-__host__ __device__ __forceinline__ int cell_count(u64 cw) { return (int)(u32)cw; }
+// Whole-cell loads and stores: one 256-bit access each.  cs = streaming (read
+// or written once), cg = cached in L2 only.
+__device__ __forceinline__ void ld_cell_cs(const Cell *p, u64 &key, u64 &chk, int &count) {
+  u64 w2;
+  asm volatile("ld.global.cs.v4.u64 {%0,%1,%2,_}, [%3];" : "=l"(key), "=l"(chk), "=l"(w2) : "l"(p));
+  count = (int)(u32)w2;
+}
+__device__ __forceinline__ void ld_cell_cg(const Cell *p, u64 &key, u64 &chk, int &count) {
+  u64 w2;
+  asm volatile("ld.global.cg.v4.u64 {%0,%1,%2,_}, [%3];" : "=l"(key), "=l"(chk), "=l"(w2) : "l"(p));
+  count = (int)(u32)w2;
+}
+__device__ __forceinline__ void st_cell_cs(Cell *p, u64 key, u64 chk, int count) {
+  asm volatile("st.global.cs.v4.u64 [%0], {%1,%2,%3,%4};" ::"l"(p), "l"(key), "l"(chk), "l"((u64)(u32)count),
+               "l"(0ull)
+               : "memory");
+}
 
 // SplitMix64 output finaliser (Steele, Lea & Flood 2014): the hash family of
 // the IBLT (cell positions and checksums).
@@ -43,11 +61,30 @@ __host__ __device__ __forceinline__ u64 mix64(u64 z) {
   return z ^ (z >> 31);
 }
 
-// The word one inserted key adds to its cells' cw: checkSum(x) * 2^32 + 1,
-// checkSum(x) being the upper 32 bits of mix64(x ^ seed_chk).  A cell holding
-// exactly x has cw == cell_word(x); holding exactly a deleted x, cw == -cell_word(x).
-__host__ __device__ __forceinline__ u64 cell_word(u64 x, u64 seed_chk) {
-  return (mix64(x ^ seed_chk) & 0xFFFFFFFF00000000ULL) | 1ULL;
+// checkSum(x) of Sec. 6: mix64(x ^ seed_chk), 64 bits.  A cell holding exactly
+// x (inserted or deleted) has chk == checksum(x).
+__host__ __device__ __forceinline__ u64 checksum(u64 x, u64 seed_chk) { return mix64(x ^ seed_chk); }
+
+// Pure (holds exactly one key, Sec. 6): count == 1 and chk == checkSum(key).
+__host__ __device__ __forceinline__ bool cell_pure(int count, u64 key, u64 chk, u64 seed_chk) {
+  return count == 1 && chk == checksum(key, seed_chk);
+}
+
+// Adds key x (checksum cs) to cell c with sign sg (+1 insert, -1 delete): the
+// count moves by sg, both XOR fields take the key.  Returns the old count.
+__device__ __forceinline__ int touch_cell(Cell *cells, u32 c, u64 x, u64 cs, int sg) {
+  Cell *p = cells + c;
+  const int old = atomicAdd(&p->count, sg);
+  atomicXor(&p->key, x);
+  atomicXor(&p->chk, cs);
+  return old;
+}
+// The same with nothing read back (fire-and-forget reductions).
+__device__ __forceinline__ void touch_cell_nr(Cell *cells, u32 c, u64 x, u64 cs, int sg) {
+  Cell *p = cells + c;
+  atomicAdd(&p->count, sg);
+  atomicXor(&p->key, x);
+  atomicXor(&p->chk, cs);
 }
 
 // Per-table constants.  Sub-table j is cells base+off[j] .. base+off[j+1]-1.

@@ -20,10 +20,8 @@
 namespace pp {
 
 template <int R>
-__device__ __forceinline__ void apply_touch(Cell *cells, u32 c, u64 x, u64 w, int sign) {
-  Cell *p = cells + c;
-  atomicAdd(&p->cw, sign > 0 ? w : 0ull - w);
-  atomicXor(&p->key, x);
+__device__ __forceinline__ void apply_touch(Cell *cells, u32 c, u64 x, u64 cs, int sign) {
+  touch_cell_nr(cells, c, x, cs, sign);
 }
 
 // Dynamic shared memory: 3 * n_slabs u32 (histogram, scan, base) + the staged
@@ -143,7 +141,7 @@ __global__ void __launch_bounds__(kBlock, 5) k_bin(Cell *__restrict__ cells, con
         } else if (b.direct_overflow) {
           const TableArgs &TT = BATCH ? tabs[s_tab[p]] : tab0;
           const u64 xx = s_key[p];
-          apply_touch<R>(cells, s_cell[p], xx, cell_word(xx, TT.seed[rank_of<R>(TT)]), sign);
+          apply_touch<R>(cells, s_cell[p], xx, checksum(xx, TT.seed[rank_of<R>(TT)]), sign);
         } else {
           *b.overflow = 1u;
         }

@@ -42,15 +42,10 @@ __global__ void __launch_bounds__(kBlock) k_insert(Cell *__restrict__ cells, con
       const u64 x = __ldcs(keys + i);
       u32 c[NR];
       cells_of<NR>(x, tab0, c);
-      const u64 w = sign > 0 ? cell_word(x, tab0.seed[r]) : 0ull - cell_word(x, tab0.seed[r]);
+      const u64 cs = checksum(x, tab0.seed[r]);
 #pragma unroll
-      for (int j = 0; j < NR; ++j) {
-        if (j < r) {
-          Cell *p = cells + c[j];
-          atomicAdd(&p->cw, w);
-          atomicXor(&p->key, x);
-        }
-      }
+      for (int j = 0; j < NR; ++j)
+        if (j < r) touch_cell_nr(cells, c[j], x, cs, sign);
     }
   } else {
     for (u32 ch = blockIdx.x; ch < n_chunks; ch += gridDim.x) {
@@ -61,15 +56,10 @@ __global__ void __launch_bounds__(kBlock) k_insert(Cell *__restrict__ cells, con
         const u64 x = __ldcs(keys + i);
         u32 c[NR];
         cells_of<NR>(x, T, c);
-        const u64 w = sign > 0 ? cell_word(x, T.seed[r]) : 0ull - cell_word(x, T.seed[r]);
+        const u64 cs = checksum(x, T.seed[r]);
 #pragma unroll
-        for (int j = 0; j < NR; ++j) {
-          if (j < r) {
-            Cell *p = cells + c[j];
-            atomicAdd(&p->cw, w);
-            atomicXor(&p->key, x);
-          }
-        }
+        for (int j = 0; j < NR; ++j)
+          if (j < r) touch_cell_nr(cells, c[j], x, cs, sign);
       }
     }
   }
@@ -116,11 +106,10 @@ __global__ void __launch_bounds__(kBlock) k_scan(const Cell *__restrict__ cells,
       bool pure = false;
       u64 key = 0;
       if (valid) {
-        const uint4 a = __ldcs(reinterpret_cast<const uint4 *>(cells + c));
-        key = ((u64)a.y << 32) | a.x;
-        const u64 cw = ((u64)a.w << 32) | a.z;
-        const int cnt = (int)a.z;
-        pure = cw == cell_word(key, seed_chk);
+        u64 chk;
+        int cnt;
+        ld_cell_cs(cells + c, key, chk, cnt);
+        pure = cell_pure(cnt, key, chk, seed_chk);
         c_alive += cnt >= 2;
         c_nonempty += cnt != 0;
       }
@@ -229,14 +218,12 @@ __global__ void __launch_bounds__(kBlock) k_peel(Cell *__restrict__ cells, const
       int old[NR];
       u32 n_empty = 0;
       if (win) {
-        const u64 w = cell_word(x, T.seed[r]);
+        const u64 cs = checksum(x, T.seed[r]);
 #pragma unroll
         for (int j = 0; j < NR; ++j) {
           old[j] = 0;
           if (j < r) {
-            Cell *p = cells + cj[j];
-            old[j] = cell_count(atomicAdd(&p->cw, 0ull - w));
-            atomicXor(&p->key, x);
+            old[j] = touch_cell(cells, cj[j], x, cs, -1);
             n_empty += (u32)((old[j] == 1) - (old[j] == 0));  // net change of non-zero counts
           }
         }
@@ -341,9 +328,9 @@ __global__ void __launch_bounds__(kBlock) k_filter(const Cell *__restrict__ cell
       if (valid) {
         c = __ldcs(cand + i);
         if (BATCH) tb = __ldcs(ctab + i);
-        const uint4 a = __ldcg(reinterpret_cast<const uint4 *>(cells + c));
-        key = ((u64)a.y << 32) | a.x;
-        const u64 cw = ((u64)a.w << 32) | a.z;
+        u64 chk;
+        int cnt;
+        ld_cell_cg(cells + c, key, chk, cnt);
         u64 seed_chk;
         if (BATCH && bc.chk_seed) {
           seed_chk = bc.chk_seed[tb];
@@ -351,7 +338,7 @@ __global__ void __launch_bounds__(kBlock) k_filter(const Cell *__restrict__ cell
           const TableArgs &T = BATCH ? tabs[tb] : tab0;
           seed_chk = T.seed[rank_of<R>(T)];
         }
-        pure = cw == cell_word(key, seed_chk);
+        pure = cell_pure(cnt, key, chk, seed_chk);
         if (pure) atomicOr(bitmap + (c >> 5), 1u << (c & 31u));
       }
       const u32 p = warp_reserve<u32>(pure, &s_n);

@@ -9,13 +9,19 @@
 // entry point brings its own working memory.
 //
 // Where the working memory lives: one file-scope __device__ array of fixed
-// size (g_noalloc_scratch below).  The CUDA runtime creates it when the
-// library's device code is loaded on a GPU, and every GPU that loads the
-// library keeps it until the process exits.  Host code cannot use the array's
-// name as a device address (on the host it names a stand-in object), so each
-// device's real address is looked up once with cudaGetSymbolAddress and cached.
-// That look-up happens inside the first call made on each device: make that
-// first call before any stream capture begins.
+// size (g_noalloc_scratch below).  It exists on a GPU once the library's
+// device code is loaded there, and stays until the process exits.  With the
+// CUDA runtime's default lazy module loading, that load happens inside the
+// first call of this entry point on each device (the cudaGetSymbolAddress
+// below triggers it), and loading does take device memory: the array plus the
+// module's code.  So the first call on each device must come at start-up,
+// before the caller's framework reserves its memory pool and before any
+// stream capture; or the process runs with CUDA_MODULE_LOADING=EAGER, which
+// loads the module when the CUDA context is created.  Later calls allocate
+// nothing.  Host code cannot use the array's name as a device address (on the
+// host it names a stand-in object), so every call looks the current device's
+// address up with cudaGetSymbolAddress (cheap once the module is loaded); no
+// address is cached, so a cudaDeviceReset between calls leaves nothing stale.
 //
 // Sharing: every call on a device uses the same array and finds the previous
 // call's data in it.  The parts that must start at zero are cleared at the
@@ -26,7 +32,7 @@
 // The decode itself runs the same scan / peel / filter / round-end kernels as
 // pp_iblt_decode, driven from the host one round at a time (no graph is built,
 // since instantiating one allocates).
-#include <mutex>
+#include <stdint.h>
 #include <string.h>
 
 #include "host.cuh"
@@ -56,24 +62,13 @@ static_assert(sizeof(DecodeCtl) <= kOffSum, "DecodeCtl outgrew its slot");
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 
-constexpr int kMaxDevices = 64;
-std::mutex g_mu;
-unsigned char *g_scratch_ptr[kMaxDevices] = {};
-
-// Device address of the scratch array on the current device (looked up once).
+// Device address of the scratch array on the current device, looked up on
+// every call (the first call on a device also loads the module there).
 pp_status scratch_for_current_device(unsigned char **out) {
-  int dev = 0;
-  PP_CUDA(cudaGetDevice(&dev));
-  if (dev < 0 || dev >= kMaxDevices)
-    return fail(PP_ERR_INVALID_ARG, "pp_iblt_decode_noalloc: device %d out of range", dev);
-  std::lock_guard<std::mutex> lock(g_mu);
-  if (!g_scratch_ptr[dev]) {
-    void *p = nullptr;
-    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-    if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(g_noalloc_scratch)", __FILE__, __LINE__);
-    g_scratch_ptr[dev] = static_cast<unsigned char *>(p);
-  }
-  *out = g_scratch_ptr[dev];
+  void *p = nullptr;
+  const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(g_noalloc_scratch)", __FILE__, __LINE__);
+  *out = static_cast<unsigned char *>(p);
   return PP_OK;
 }
 
@@ -82,7 +77,7 @@ __global__ void k_count_sum(const Cell *__restrict__ cells, u64 n, long long *__
   __shared__ long long s_red[kBlock / 32];
   long long v = 0;
   for (u64 i = (u64)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (u64)gridDim.x * blockDim.x)
-    v += cell_count(cells[i].cw);
+    v += cells[i].count;
   const long long b = block_sum<long long, kBlock>(v, s_red);
   if (threadIdx.x == 0 && b) atomicAdd(reinterpret_cast<unsigned long long *>(sum), (unsigned long long)b);
 }
@@ -101,6 +96,8 @@ extern "C" pp_status pp_iblt_decode_noalloc(pp_cell *d_cells, uint64_t n_cells, 
                 "PP_NOALLOC_MAX_CELLS cells)",
                 (unsigned long long)n_cells, (unsigned long long)kMaxCells);
   if (out_cap && !d_out_keys) return fail(PP_ERR_INVALID_ARG, "pp_iblt_decode_noalloc: NULL output");
+  if (reinterpret_cast<uintptr_t>(d_cells) % 32 != 0 || reinterpret_cast<uintptr_t>(d_out_keys) % 8 != 0)
+    return fail(PP_ERR_INVALID_ARG, "pp_iblt_decode_noalloc: d_cells must be 32-byte and d_out_keys 8-byte aligned");
   unsigned char *scratch = nullptr;
   pp_status st = scratch_for_current_device(&scratch);
   if (st != PP_OK) return st;

@@ -11,9 +11,9 @@
 //   k_apply_round (phase B2) walks the records bin by bin: blocks take the next
 //            chunk of 2048 records from an atomic counter, so at any moment the
 //            whole GPU updates a narrow, moving window of the table and HBM
-//            sees near-sequential traffic.  Each update is one 64-bit
-//            atomicAdd on the cell's count-and-checksum word and one
-//            atomicXor on its key; a count that drops from 2 to 1 makes the
+//            sees near-sequential traffic.  Each update is an atomicAdd on
+//            the cell's count and an atomicXor on each of its key and
+//            checksum fields; a count that drops from 2 to 1 makes the
 //            cell a candidate for the next frontier.
 // Updates commute, so the order of application does not change the state at
 // the end of the round; the claim decisions are all taken in B1, before any
@@ -24,13 +24,10 @@
 
 namespace pp {
 
-// Removes key x (cell word w = cell_word(x), sign sg) from cell c; returns the
+// Removes key x (checksum cs) taken with sign sg from cell c; returns the
 // cell's count before the removal.
-__device__ __forceinline__ int remove_key(Cell *cells, u32 c, u64 x, u64 w, int sg = 1) {
-  Cell *p = cells + c;
-  const int old = cell_count(atomicAdd(&p->cw, sg > 0 ? 0ull - w : w));
-  atomicXor(&p->key, x);
-  return old;
+__device__ __forceinline__ int remove_key(Cell *cells, u32 c, u64 x, u64 cs, int sg = 1) {
+  return touch_cell(cells, c, x, cs, -sg);
 }
 
 // A cell becomes a candidate for the next frontier when its count reaches 1
@@ -233,7 +230,7 @@ __global__ void __launch_bounds__(kBlock, (!BATCH && R >= 3) ? 5 : 4) k_claim(Ce
         const u64 xx = s_key[p];
         const u32 cc = s_cell[p] & kCellMask;
         const int sgn = (SIGNED && (s_cell[p] >> 31)) ? -1 : 1;
-        const int old = remove_key(cells, cc, xx, cell_word(xx, seed_chk), sgn);
+        const int old = remove_key(cells, cc, xx, checksum(xx, seed_chk), sgn);
         if (becomes_candidate<SIGNED>(old, sgn)) {
           const u32 q = atomicAdd(&ctl->n_cand, 1u);
           if (!SIGNED || q < rb.cand_cap) cand[q] = cc;
@@ -356,7 +353,7 @@ __global__ void __launch_bounds__(kBlock) k_apply_round(Cell *__restrict__ cells
       seed_chk[k] = BATCH ? (v[k] ? bc.chk_seed[tb[k]] : 0ull) : tab0.seed[rank_of<R>(tab0)];
 #pragma unroll
     for (int k = 0; k < kApplyPer; ++k)
-      old[k] = v[k] ? remove_key(cells, c[k], x[k], cell_word(x[k], seed_chk[k]), sg[k]) : 0;
+      old[k] = v[k] ? remove_key(cells, c[k], x[k], checksum(x[k], seed_chk[k]), sg[k]) : 0;
 #pragma unroll
     for (int k = 0; k < kApplyPer; ++k) {
       const bool push = v[k] && becomes_candidate<SIGNED>(old[k], sg[k]);
@@ -400,7 +397,7 @@ __global__ void __launch_bounds__(kBlock) k_residual(const Cell *__restrict__ ce
     const Chunk k = chunks[ch];
     if (bc.skip_full && bc.recovered[k.table] >= bc.items[k.table]) continue;  // uniform per block
     u64 nz = 0;
-    for (u32 c = k.begin + threadIdx.x; c < k.end; c += kBlock) nz += cell_count(cells[c].cw) != 0;
+    for (u32 c = k.begin + threadIdx.x; c < k.end; c += kBlock) nz += cells[c].count != 0;
     const u64 t = block_sum<u64, kBlock>(nz, s_red);
     if (threadIdx.x == 0 && t) atomicAdd(bc.residual + k.table, t);
   }

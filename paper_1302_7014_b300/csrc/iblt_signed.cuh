@@ -23,10 +23,10 @@
 
 namespace pp {
 
-// Pure with sign +1 or -1: the cell's word is that of key alone, inserted or deleted.
-__device__ __forceinline__ bool signed_pure(u64 cw, u64 key, u64 seed_chk) {
-  const u64 w = cell_word(key, seed_chk);
-  return cw == w || cw == 0ull - w;
+// Pure with sign +1 or -1: count +-1 and the checksum field is that of the key
+// field alone (an XOR, the same for an inserted and a deleted key).
+__device__ __forceinline__ bool signed_pure(int cnt, u64 key, u64 chk, u64 seed_chk) {
+  return (cnt == 1 || cnt == -1) && chk == checksum(key, seed_chk);
 }
 
 template <int R>
@@ -54,10 +54,9 @@ __global__ void __launch_bounds__(kBlock) k_sgscan(const Cell *__restrict__ cell
       u64 key = 0;
       int cnt = 0;
       if (c < end) {
-        const uint4 a = __ldcs(reinterpret_cast<const uint4 *>(cells + c));
-        key = ((u64)a.y << 32) | a.x;
-        cnt = (int)a.z;
-        pure = signed_pure(((u64)a.w << 32) | a.z, key, seed_chk);
+        u64 chk;
+        ld_cell_cs(cells + c, key, chk, cnt);
+        pure = signed_pure(cnt, key, chk, seed_chk);
         nonempty += cnt != 0;
       }
       const u32 ball = __ballot_sync(kFull, pure);
@@ -144,13 +143,11 @@ __global__ void __launch_bounds__(kBlock) k_sgpeel(Cell *__restrict__ cells, con
       }
       if (win) {
         n_neg += sg < 0;
-        const u64 w = cell_word(x, tab0.seed[r]);
+        const u64 cs = checksum(x, tab0.seed[r]);
 #pragma unroll
         for (int j = 0; j < NR; ++j) {
           if (j < r) {
-            Cell *p = cells + cj[j];
-            const int old = cell_count(atomicAdd(&p->cw, sg > 0 ? 0ull - w : w));
-            atomicXor(&p->key, x);
+            const int old = touch_cell(cells, cj[j], x, cs, -sg);
             const int now = old - sg;
             emptied += (u64)(long long)((old != 0) - (now != 0));
             if (now == 1 || now == -1) s_cand[atomicAdd(&s_ncand, 1u)] = cj[j];
@@ -217,10 +214,9 @@ __global__ void __launch_bounds__(kBlock) k_sgfilter(const Cell *__restrict__ ce
       int cnt = 0;
       if (i < n) {
         c = __ldcs(cand + i);
-        const uint4 a = __ldcg(reinterpret_cast<const uint4 *>(cells + c));
-        key = ((u64)a.y << 32) | a.x;
-        cnt = (int)a.z;
-        if (signed_pure(((u64)a.w << 32) | a.z, key, seed_chk)) {
+        u64 chk;
+        ld_cell_cg(cells + c, key, chk, cnt);
+        if (signed_pure(cnt, key, chk, seed_chk)) {
           const u32 bit = 1u << (c & 31u);
           keep = (atomicOr(bitmap + (c >> 5), bit) & bit) == 0;  // first entry of this cell
         }

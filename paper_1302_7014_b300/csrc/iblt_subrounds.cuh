@@ -122,11 +122,11 @@ __global__ void __launch_bounds__(kBlock) k_sscan(const Cell *__restrict__ cells
     for (int it = 0; it < kScanItems; ++it) {
       const u64 c = c0 + (u64)it * kBlock + threadIdx.x;
       if (c < tab0.n_cells) {
-        const uint4 a = __ldcs(reinterpret_cast<const uint4 *>(cells + c));
-        const u64 key = ((u64)a.y << 32) | a.x;
-        const u64 cw = ((u64)a.w << 32) | a.z;
-        nonempty += (int)a.z != 0;
-        if (cw == cell_word(key, seed_chk))
+        u64 key, chk;
+        int cnt;
+        ld_cell_cs(cells + c, key, chk, cnt);
+        nonempty += cnt != 0;
+        if (cell_pure(cnt, key, chk, seed_chk))
           sub_stage_push(S, tab0, queue, ctl, (u32)c, subtable_of(tab0, (u32)c));
       }
     }
@@ -163,9 +163,10 @@ __global__ void __launch_bounds__(kBlock) k_sfilter(const Cell *__restrict__ cel
       u32 c = 0;
       if (i < fe) {
         c = __ldcs(q + i);
-        const uint4 a = __ldcg(reinterpret_cast<const uint4 *>(cells + c));
-        key = ((u64)a.y << 32) | a.x;
-        pure = (((u64)a.w << 32) | a.z) == cell_word(key, seed_chk);
+        u64 chk;
+        int cnt;
+        ld_cell_cg(cells + c, key, chk, cnt);
+        pure = cell_pure(cnt, key, chk, seed_chk);
       }
       const u32 p = warp_reserve<u32>(pure, &s_n);
       if (pure) {
@@ -229,13 +230,11 @@ __global__ void __launch_bounds__(kBlock) k_speel(Cell *__restrict__ cells, cons
         if (!ok) flags |= FLAG_INTERNAL;
       }
       if (ok) {
-        const u64 w = cell_word(x, tab0.seed[r]);
+        const u64 cs = checksum(x, tab0.seed[r]);
 #pragma unroll
         for (int h = 0; h < NR; ++h) {
           if (h < r) {
-            Cell *p = cells + cj[h];
-            const int old = cell_count(atomicAdd(&p->cw, 0ull - w));
-            atomicXor(&p->key, x);
+            const int old = touch_cell(cells, cj[h], x, cs, -1);
             emptied += (u64)(long long)((old == 1) - (old == 0));
             if (old == 2) sub_stage_push(S, tab0, queue, ctl, cj[h], (u32)h);
           }

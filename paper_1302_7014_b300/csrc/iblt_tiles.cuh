@@ -1,7 +1,7 @@
 // Tile pass of the slab-binned IBLT build.
 //
 // Applying a slab's updates with L2 atomics is bound by the L2's atomic
-// throughput: every update is two atomics on one 16-byte cell.  The tile
+// throughput: every update is three atomics on one 32-byte cell.  The tile
 // pass replaces them with shared-memory atomics, in two roles:
 //   bin    sorts a slab's update records into the slab's 512 tiles of 4096
 //          cells (per-block histogram in shared memory, one atomic per tile
@@ -129,12 +129,11 @@ template <bool BATCH>
 __device__ __forceinline__ void tile_apply(unsigned char *smem, Cell *cells, const TableArgs &tab0,
                                            const TableArgs *tabs, const TileArgs &ta, u32 slab, u32 tile,
                                            u64 n_cells, int sign, int zero) {
-  // A cell's word cw = S * 2^32 + count mod 2^64 is held as its two 32-bit
-  // sums: the checksum sum S and the count.
   u64 *s_key = reinterpret_cast<u64 *>(smem);                 // kTileCells
-  u32 *s_sum = reinterpret_cast<u32 *>(s_key + kTileCells);   // kTileCells
-  int *s_cnt = reinterpret_cast<int *>(s_sum + kTileCells);   // kTileCells
+  u64 *s_chk = s_key + kTileCells;                            // kTileCells
+  int *s_cnt = reinterpret_cast<int *>(s_chk + kTileCells);   // kTileCells
   u32 *s_key32 = reinterpret_cast<u32 *>(s_key);  // XOR works on each 32-bit half
+  u32 *s_chk32 = reinterpret_cast<u32 *>(s_chk);
   const u64 c0 = ((u64)slab << kSlabShift) + ((u64)tile << kTileShift);
   if (c0 >= n_cells) return;  // uniform per block
   const u32 nc = (u32)(c0 + kTileCells <= n_cells ? kTileCells : n_cells - c0);
@@ -144,14 +143,14 @@ __device__ __forceinline__ void tile_apply(unsigned char *smem, Cell *cells, con
   for (u32 i = threadIdx.x; i < nc; i += kTileThreads) {
     if (zero) {
       s_key[i] = 0;
-      s_sum[i] = 0;
+      s_chk[i] = 0;
       s_cnt[i] = 0;
     } else {
-      const uint4 a = __ldcs(reinterpret_cast<const uint4 *>(cells + c0 + i));
-      const u64 cw = ((u64)a.w << 32) | a.z;
-      const int cnt = cell_count(cw);
-      s_key[i] = ((u64)a.y << 32) | a.x;
-      s_sum[i] = (u32)((cw - (u64)(long long)cnt) >> 32);
+      u64 k, ch;
+      int cnt;
+      ld_cell_cs(cells + c0 + i, k, ch, cnt);
+      s_key[i] = k;
+      s_chk[i] = ch;
       s_cnt[i] = cnt;
     }
   }
@@ -174,9 +173,10 @@ __device__ __forceinline__ void tile_apply(unsigned char *smem, Cell *cells, con
     for (int it = 0; it < kTileApplyItems; ++it) {
       if (off[it] != 0xffffffffu) {
         const u32 o = off[it];
-        const u32 cs = (u32)(cell_word(x[it], seed[it]) >> 32);
+        const u64 cs = checksum(x[it], seed[it]);
         atomicAdd(s_cnt + o, sign);
-        atomicAdd(s_sum + o, sign > 0 ? cs : 0u - cs);
+        atomicXor(s_chk32 + 2 * o, (u32)cs);
+        atomicXor(s_chk32 + 2 * o + 1, (u32)(cs >> 32));
         atomicXor(s_key32 + 2 * o, (u32)x[it]);
         atomicXor(s_key32 + 2 * o + 1, (u32)(x[it] >> 32));
       }
@@ -190,13 +190,7 @@ __device__ __forceinline__ void tile_apply(unsigned char *smem, Cell *cells, con
   for (u32 l = threadIdx.x; l < (n * 4 + 127) / 128; l += kTileThreads) l2_discard(ta.cell + src + l * 32);
   if (BATCH)
     for (u32 l = threadIdx.x; l < (n * 4 + 127) / 128; l += kTileThreads) l2_discard(ta.tab + src + l * 32);
-  for (u32 i = threadIdx.x; i < nc; i += kTileThreads) {
-    const u64 k = s_key[i];
-    const u64 cw = ((u64)s_sum[i] << 32) + (u64)(long long)s_cnt[i];
-    uint4 a;
-    a.x = (u32)k, a.y = (u32)(k >> 32), a.z = (u32)cw, a.w = (u32)(cw >> 32);
-    __stcs(reinterpret_cast<uint4 *>(cells + c0 + i), a);
-  }
+  for (u32 i = threadIdx.x; i < nc; i += kTileThreads) st_cell_cs(cells + c0 + i, s_key[i], s_chk[i], s_cnt[i]);
 }
 
 // Role "bin" of a batched update taken straight from the keys (no slab
@@ -357,11 +351,8 @@ __global__ void __launch_bounds__(kTileThreads, 2) k_tile_step(Cell *__restrict_
     const u32 no = min(ta.o_count[os], (u32)ta.o_cap);
     for (u32 i = idx * kTileThreads + threadIdx.x; i < no; i += n_apply * kTileThreads) {
       const u64 x = ta.o_key[oset + i];
-      Cell *p = cells + ta.o_cell[oset + i];
       const TableArgs &T = BATCH ? tabs[ta.o_tab[oset + i]] : tab0;
-      const u64 w = cell_word(x, chk_seed_of(T));
-      atomicAdd(&p->cw, sign > 0 ? w : 0ull - w);
-      atomicXor(&p->key, x);
+      touch_cell_nr(cells, ta.o_cell[oset + i], x, checksum(x, chk_seed_of(T)), sign);
     }
   }
   if (s >= 1 && s - 1 < b.n_slabs) tile_apply<BATCH>(smem, cells, tab0, tabs, ta, s - 1, idx, n_cells, sign, zero);
@@ -396,11 +387,8 @@ __global__ void __launch_bounds__(kTileThreads, 2) k_tile_step_keys(Cell *__rest
     const u32 no = min(ta.o_count[os], (u32)ta.o_cap);
     for (u32 i = idx * kTileThreads + threadIdx.x; i < no; i += n_apply * kTileThreads) {
       const u64 x = ta.o_key[oset + i];
-      Cell *p = cells + ta.o_cell[oset + i];
       const TableArgs &T = tabs[ta.o_tab[oset + i]];
-      const u64 w = cell_word(x, chk_seed_of(T));
-      atomicAdd(&p->cw, sign > 0 ? w : 0ull - w);
-      atomicXor(&p->key, x);
+      touch_cell_nr(cells, ta.o_cell[oset + i], x, checksum(x, chk_seed_of(T)), sign);
     }
   }
   const TableArgs t0{};

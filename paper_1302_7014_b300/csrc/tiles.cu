@@ -22,7 +22,7 @@ void free_tiles(TileBufs &tb) {
 // dynamic shared memory of k_tile_step: the larger of the two roles
 static size_t tile_step_smem() {
   const size_t bin = (size_t)kTileBinChunk * (8 + 4 + 4 + 4);  // a batch bin step (plain: 4 B less per record)
-  const size_t apply = (size_t)kTileCells * (8 + 4 + 4);
+  const size_t apply = (size_t)kTileCells * (8 + 8 + 4);
   return bin > apply ? bin : apply;
 }
 

@@ -64,7 +64,7 @@ def check_against_oracle(specs, keys, ooff, res, got, b=None, cells_every=1):
         if b is not None and i % cells_every == 0:
             cells = b.cells(i)
             assert (cells["count"].astype(np.int64) == ot.count).all(), i
-            assert (cells["key_xor"] == ot.keyx).all() and (cells["chk_sum"] == ot.chks).all(), i
+            assert (cells["key_xor"] == ot.keyx).all() and (cells["chk_xor"] == ot.chkx).all(), i
 
 
 def test_mixed_ranks(ppb):
@@ -163,7 +163,7 @@ def test_binned_batch_build_and_rounds(ppb, rs):
         ot.insert(keys[i])
         cells = b.cells(i)
         assert (cells["count"].astype(np.int64) == ot.count).all()
-        assert (cells["key_xor"] == ot.keyx).all() and (cells["chk_sum"] == ot.chks).all()
+        assert (cells["key_xor"] == ot.keyx).all() and (cells["chk_xor"] == ot.chkx).all()
     out = torch.full((int(koff[-1]),), -1, dtype=torch.int64, device="cuda")
     res = b.decode(out, koff)
     check_against_oracle(specs, keys, koff, res, out.cpu().numpy().view(np.uint64), b, cells_every=3)
@@ -209,7 +209,7 @@ def test_binned_batch_build_across_slabs(ppb, rs, big):
         ots.append(ot)
         cells = b.cells(i)
         assert (cells["count"].astype(np.int64) == ot.count).all(), i
-        assert (cells["key_xor"] == ot.keyx).all() and (cells["chk_sum"] == ot.chks).all(), i
+        assert (cells["key_xor"] == ot.keyx).all() and (cells["chk_xor"] == ot.chkx).all(), i
     out = torch.full((int(koff[-1]),), -1, dtype=torch.int64, device="cuda")
     res = b.decode(out, koff)
     check_against_oracle(specs, keys, koff, res, out.cpu().numpy().view(np.uint64), b, cells_every=4)
@@ -223,7 +223,7 @@ def test_binned_batch_build_across_slabs(ppb, rs, big):
         ots[i].insert(dele[i], sign=-1)
         cells = b.cells(i)
         assert (cells["count"].astype(np.int64) == ots[i].count).all(), i
-        assert (cells["key_xor"] == ots[i].keyx).all() and (cells["chk_sum"] == ots[i].chks).all(), i
+        assert (cells["key_xor"] == ots[i].keyx).all() and (cells["chk_xor"] == ots[i].chkx).all(), i
 
 
 def test_binned_batch_decode_after_deletions(ppb):

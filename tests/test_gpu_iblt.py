@@ -39,7 +39,7 @@ def _split_rounds(out_keys, rec_per_round):
 def _assert_cells_equal(cells, ot):
     assert (cells["count"].astype(np.int64) == ot.count).all()
     assert (cells["key_xor"] == ot.keyx).all()
-    assert (cells["chk_sum"] == ot.chks).all()
+    assert (cells["chk_xor"] == ot.chkx).all()
 
 
 def run_case(pp, n, r, keys, seed, opts=None, deletes=None, max_rounds=None):

@@ -57,7 +57,7 @@ def run_signed(pp, n, r, A, B, seed, opts=None, with_signs=True):
             assert np.array_equal(signs[ends[t]:ends[t + 1]][o], ws), t + 1
     cells = gt.cells()
     assert (cells["count"].astype(np.int64) == ot.count).all()
-    assert (cells["key_xor"] == ot.keyx).all() and (cells["chk_sum"] == ot.chks).all()
+    assert (cells["key_xor"] == ot.keyx).all() and (cells["chk_xor"] == ot.chkx).all()
     assert res.residual_cells == ot.residual_cells()
     gt.close()
     return res

@@ -175,7 +175,7 @@ def _dev(keys):
 def _assert_cells_equal(cells, ot):
     assert (cells["count"].astype(np.int64) == ot.count).all()
     assert (cells["key_xor"] == ot.keyx).all()
-    assert (cells["chk_sum"] == ot.chks).all()
+    assert (cells["chk_xor"] == ot.chkx).all()
 
 
 def run_iblt(pp, n, r, keys, seed, opts=None, deletes=None, max_sub=None):

@@ -11,6 +11,7 @@ This file is collected last on purpose; it must pass both on its own in a
 fresh process and after the other tests.
 """
 import ctypes
+import gc
 
 import numpy as np
 import pytest
@@ -81,6 +82,56 @@ def test_noalloc_matches_decode_two_calls_in_a_row(ppeel_lib):
     _one_case(lib, pp, 300007, 3, 0.75, 17, 18)
     _one_case(lib, pp, 65539, 4, 0.85, 19, 20)   # above threshold: non-empty residue
     _one_case(lib, pp, 1 << 20, 3, 0.80, 21, 22)  # the largest table it accepts
+
+
+def test_noalloc_calls_allocate_no_device_memory(ppeel_lib):
+    # After the first call on the device (which loads the library's device
+    # code, see the header), further calls leave the free device memory and
+    # torch's own allocations exactly as they were.
+    import paper_1302_7014_b300 as pp
+    lib = ppeel_lib
+    n, r, seed = 200003, 3, 29
+    keys = ppgen.distinct_keys(ppgen.edges_from_c(0.75, n), 30)
+    dkeys = torch.from_numpy(keys.view(np.int64)).cuda()
+    ref = pp.IBLT(n, r, seed)
+    ref.insert(dkeys)
+    cells = torch.empty(n * ctypes.sizeof(pp._lib.Cell), dtype=torch.uint8, device="cuda")
+    out = torch.zeros(keys.size, dtype=torch.int64, device="cuda")
+    stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    res, _ = _result(1024)
+
+    def call():
+        assert lib.pp_iblt_copy_cells(ref.handle, ctypes.c_void_p(cells.data_ptr()), 0, n, 0, stream) == 0
+        st = lib.pp_iblt_decode_noalloc(ctypes.c_void_p(cells.data_ptr()), n, r, seed,
+                                        ctypes.c_void_p(out.data_ptr()), keys.size, ctypes.byref(res), stream)
+        assert st == 0, lib.pp_last_error()
+        assert res.recovered == keys.size
+        torch.cuda.synchronize()
+
+    call()   # warm-up: the first call may load the module
+    # no Python garbage collection (which could free unrelated tensors) while measuring
+    gc.collect()
+    gc.disable()
+    try:
+        free0, alloc0 = torch.cuda.mem_get_info()[0], torch.cuda.memory_allocated()
+        for _ in range(3):
+            call()
+            assert torch.cuda.mem_get_info()[0] == free0
+            assert torch.cuda.memory_allocated() == alloc0
+    finally:
+        gc.enable()
+    ref.close()
+
+
+def test_noalloc_rejects_misaligned_cells(ppeel_lib):
+    res, _ = _result(16)
+    buf = torch.zeros(64 * 32 + 16, dtype=torch.uint8, device="cuda")
+    out = torch.zeros(8, dtype=torch.int64, device="cuda")
+    st = ppeel_lib.pp_iblt_decode_noalloc(ctypes.c_void_p(buf.data_ptr() + 16), 64, 3, 1,
+                                          ctypes.c_void_p(out.data_ptr()), 8, ctypes.byref(res), None)
+    from paper_1302_7014_b300 import _lib
+    assert _lib.STATUS[st] == "PP_ERR_INVALID_ARG"
+    assert b"aligned" in ppeel_lib.pp_last_error()
 
 
 def test_noalloc_rejects_oversized_table(ppeel_lib):
