@@ -73,7 +73,12 @@ typedef struct pp_options {
                             1; 2 = edge-centric rounds to the end.  r > 4 and edge
                             rows that are not 16-byte (r = 4) or 8-byte (r = 2) aligned
                             always use 1. */
-  uint32_t reserved;
+  uint32_t rounds;       /* IBLT decode rounds of pp_iblt_decode: 0 = tile rounds for
+                            tables of at least 2^21 cells that saw no deletion (each
+                            round's updates folded per 4096-cell tile in shared
+                            memory), binned atomic rounds for other large tables,
+                            direct atomics below 2^21 cells (default); 1 = never tile
+                            rounds; 2 = tile rounds for any table without deletions */
 } pp_options;
 
 /* Fills *opt with the defaults above. */
@@ -148,13 +153,15 @@ pp_status pp_iblt_destroy(pp_iblt *t);
 
 /* Device memory of a table of n_cells cells and r hash functions (host only,
  * no device call; opt as for pp_iblt_create, NULL = defaults):
- *   *table_bytes  the cells, 16 B each;
+ *   *table_bytes  the cells, 32 B each;
  *   *fixed_bytes  the decode workspace allocated by pp_iblt_create;
  *   *peak_bytes   all the handle holds after pp_iblt_create, a pp_iblt_build
  *                 or pp_iblt_insert of m_keys keys and a pp_iblt_decode: the
  *                 above plus the update records of the slab-binned build and
  *                 of the binned rounds (one shared buffer, sized for the
- *                 larger) and the build's tile buffers.
+ *                 larger), the build's tile buffers, and the tile rounds'
+ *                 record regions (10 B per key and cell, for a table that saw
+ *                 no deletion).
  * Not counted: what pp_iblt_decode_subrounds (a few hundred bytes) and
  * pp_iblt_decode_signed (n_cells + 4 r n_cells bytes) add on first use.
  * Any output pointer may be NULL.  Errors: INVALID_ARG as pp_iblt_create. */

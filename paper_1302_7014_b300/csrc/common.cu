@@ -49,6 +49,7 @@ pp_options resolve_options(const pp_options *opt) {
     if (opt->stats_rounds) o.stats_rounds = opt->stats_rounds;
     o.binned = opt->binned;
     o.kcore_mode = opt->kcore_mode;
+    o.rounds = opt->rounds;
   }
   return o;
 }

@@ -10,6 +10,7 @@ namespace pp {
 
 typedef unsigned long long u64;
 typedef unsigned int u32;
+typedef unsigned short u16;
 
 constexpr u32 kFull = 0xffffffffu;
 constexpr u64 kGamma = 0x9E3779B97F4A7C15ULL;

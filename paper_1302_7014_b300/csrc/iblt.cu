@@ -14,6 +14,7 @@
 #include "iblt_rounds.cuh"
 #include "iblt_subrounds.cuh"
 #include "iblt_signed.cuh"
+#include "iblt_trounds.cuh"
 
 using namespace pp;
 
@@ -55,6 +56,16 @@ static IbltKernels iblt_kernels_t() {
     k.sg_filter = (const void *)k_sgfilter<R>;
     k.sg_claim = (const void *)k_claim<R, false, true, true>;
     k.sg_apply = (const void *)k_apply_round<R, false, true>;
+    k.tscan = (const void *)k_tscan<R>;
+    k.tclaim = (const void *)k_tclaim<R>;
+    k.tapply = (const void *)k_tapply<R>;
+    k.tapply_sparse = (const void *)k_tapply_sparse<R>;
+    static bool tattr = false;
+    if (!tattr) {
+      cudaFuncSetAttribute((const void *)k_tapply<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)kTApplySmem);
+      tattr = true;
+    }
   }
   return k;
 }
@@ -146,6 +157,12 @@ struct pp_iblt {
   int grid_sgscan = 0, grid_sgpeel = 0, grid_sgfilter = 0, grid_sgclaim = 0;
   size_t smem_sgclaim = 0;
   signed char *sg_graph_out = nullptr;  // output sign pointer the graph was built with
+  // tile rounds (allocated on first use)
+  TileRoundBufs trb{};
+  bool tile_rounds = false;   // the round kind the graph was built with
+  bool has_deletes = false;   // a deletion since the last clear/build: no tile rounds
+  int grid_tscan = 0, grid_tclaim = 0, grid_tapply = 0, grid_tsparse = 0;
+  uint64_t front_cap = 0;     // entries of fkey / fcell
   bool sg_graph_built = false;
   bool sg_graph_binned = false;         // the graph's round kind
   uint32_t sg_graph_gen = 0;            // rec_gen the binned graph was built with
@@ -181,6 +198,17 @@ void free_all(pp_iblt *t) {
   cudaFree(t->bin_count);
   cudaFree(t->bin_overflow);
   free_tiles(t->tiles);
+  cudaFree(t->trb.rec_key);
+  cudaFree(t->trb.rec_off);
+  cudaFree(t->trb.base);
+  cudaFree(t->trb.pos);
+  cudaFree(t->trb.base64);
+  cudaFree(t->trb.done);
+  cudaFree(t->trb.sum);
+  cudaFree(t->trb.act);
+  cudaFree(t->trb.act_d);
+  cudaFree(t->trb.fseg);
+  cudaFree(const_cast<u64 *>(t->trb.fstart));
   delete t;
 }
 
@@ -585,6 +613,197 @@ pp_status sub_graph_launch(pp_iblt *t, bool binned, cudaStream_t s) {
   return PP_OK;
 }
 
+// ---- tile rounds ---------------------------------------------------------
+// Buffers: a record region per tile (its counts' sum, rounded up to
+// kTRAlign), r * items + kTRAlign * tiles records in all.
+pp_status ensure_tile_rounds(pp_iblt *t, cudaStream_t s) {
+  TileRoundBufs &b = t->trb;
+  const uint32_t nt = (uint32_t)((t->n + kTRCells - 1) / kTRCells);
+  if (!b.base) {
+    // frontier segments: one per block of k_tscan / k_tapply (n_seg_d, each
+    // at most 4096 pushes per tile it takes) and of k_tapply_sparse (n_seg_s,
+    // at most kTSCap pushes per tile)
+    t->grid_tapply = persistent_grid(t->k.tapply, kTRThreads, kTApplySmem, 2);
+    t->grid_tsparse = persistent_grid(t->k.tapply_sparse, kTSThreads, 0, 6);
+    t->grid_tscan = t->grid_tapply;
+    const uint32_t nd = (uint32_t)t->grid_tapply, nsp = (uint32_t)t->grid_tsparse;
+    const uint64_t cap_d = (uint64_t)kTRCells * ((nt + nd - 1) / nd);
+    const uint64_t cap_s = (uint64_t)kTSCap * ((nt + nsp - 1) / nsp);
+    const uint64_t front = nd * cap_d + nsp * cap_s;
+    uint64_t *h_start = (uint64_t *)malloc((size_t)(nd + nsp) * sizeof(uint64_t));
+    if (!h_start) return fail(PP_ERR_OUT_OF_MEMORY, "tile round segment table");
+    for (uint32_t k = 0; k < nd + nsp; ++k) h_start[k] = k < nd ? k * cap_d : nd * cap_d + (k - nd) * cap_s;
+    u64 *d_start = nullptr;
+    cudaError_t e = cudaMalloc((void **)&b.base, ((size_t)nt + 1) * sizeof(u64));
+    if (e == cudaSuccess) e = cudaMalloc((void **)&b.pos, (size_t)nt * kTRPosStride * sizeof(u32));
+    if (e == cudaSuccess) e = cudaMalloc((void **)&b.base64, (size_t)nt * sizeof(u32));
+    if (e == cudaSuccess) e = cudaMalloc((void **)&b.done, (size_t)nt * sizeof(u32));
+    if (e == cudaSuccess) e = cudaMalloc((void **)&b.sum, (size_t)nt * sizeof(u32));
+    if (e == cudaSuccess) e = cudaMalloc((void **)&b.act, (size_t)nt * sizeof(TileAct));
+    if (e == cudaSuccess) e = cudaMalloc((void **)&b.act_d, (size_t)nt * sizeof(TileAct));
+    if (e == cudaSuccess) e = cudaMalloc((void **)&b.fseg, (size_t)(nd + nsp) * sizeof(u32));
+    if (e == cudaSuccess) e = cudaMalloc((void **)&d_start, (size_t)(nd + nsp) * sizeof(u64));
+    if (e == cudaSuccess)
+      e = cudaMemcpy(d_start, h_start, (size_t)(nd + nsp) * sizeof(u64), cudaMemcpyHostToDevice);
+    free(h_start);
+    b.fstart = d_start;
+    if (e != cudaSuccess) return cuda_fail(e, "tile round buffers", __FILE__, __LINE__);
+    b.n_tiles = nt;
+    b.n_seg_d = nd;
+    b.n_seg_s = nsp;
+    b.cap_d = (u32)cap_d;
+    b.cap_s = (u32)cap_s;
+    // the frontier arrays hold every segment
+    if (front > t->front_cap) {
+      PP_CUDA(cudaStreamSynchronize(s));
+      cudaFree(t->fkey);
+      cudaFree(t->fcell);
+      t->fkey = nullptr;
+      t->fcell = nullptr;
+      PP_CUDA(cudaMalloc((void **)&t->fkey, front * sizeof(u64)));
+      PP_CUDA(cudaMalloc((void **)&t->fcell, front * sizeof(u32)));
+      t->front_cap = front;
+      // every graph holds the frontier pointers
+      if (t->sub_exec) cudaGraphExecDestroy(t->sub_exec);
+      if (t->sub_exec_binned) cudaGraphExecDestroy(t->sub_exec_binned);
+      if (t->sg_exec) cudaGraphExecDestroy(t->sg_exec);
+      t->sub_exec = t->sub_exec_binned = t->sg_exec = nullptr;
+    }
+    t->grid_tclaim = persistent_grid(t->k.tclaim, kBlock, ((size_t)nd + nsp + 1) * sizeof(u32), t->opt.ctas_per_sm);
+    ++t->rec_gen;
+  }
+  const uint64_t items = t->items > 0 ? (uint64_t)t->items : 0;
+  const uint64_t need = (uint64_t)t->r * items + (uint64_t)kTRAlign * nt;
+  if (need > b.rec_cap) {
+    PP_CUDA(cudaStreamSynchronize(s));
+    cudaFree(b.rec_key);
+    cudaFree(b.rec_off);
+    b.rec_key = nullptr;
+    b.rec_off = nullptr;
+    b.rec_cap = 0;
+    PP_CUDA(cudaMalloc((void **)&b.rec_key, need * sizeof(u64)));
+    PP_CUDA(cudaMalloc((void **)&b.rec_off, need * sizeof(u16)));
+    b.rec_cap = need;
+    ++t->rec_gen;
+  }
+  return PP_OK;
+}
+
+struct TileArgsSet {
+  const Cell *cells_c;
+  Cell *cells;
+  TableArgs tab0;
+  u64 *fkey;
+  u32 *fcell, *bitmap;
+  const u64 *fkey_c;
+  const u32 *fcell_c, *bitmap_c;
+  TileRoundBufs tb;
+  DecodeCtl *ctl;
+  void *scan[7], *prefix[2], *claim[7], *active[2], *apply[7];
+  void bind() {
+    void *a[7] = {&cells_c, &tab0, &fkey, &fcell, &bitmap, &tb, &ctl};
+    memcpy(scan, a, sizeof a);
+    void *b[2] = {&tb, &ctl};
+    memcpy(prefix, b, sizeof b);
+    memcpy(active, b, sizeof b);
+    void *c[7] = {&cells, &tab0, &fkey_c, &fcell_c, &bitmap_c, &tb, &ctl};
+    memcpy(claim, c, sizeof c);
+    void *d[7] = {&cells, &tab0, &tb, &fkey, &fcell, &bitmap, &ctl};
+    memcpy(apply, d, sizeof d);
+  }
+};
+
+void fill_tile_args(pp_iblt *t, TileArgsSet &a) {
+  a.cells_c = t->cells;
+  a.cells = t->cells;
+  a.tab0 = t->args;
+  a.fkey = t->fkey;
+  a.fcell = t->fcell;
+  a.bitmap = t->bitmap;
+  a.fkey_c = t->fkey;
+  a.fcell_c = t->fcell;
+  a.bitmap_c = t->bitmap;
+  a.tb = t->trb;
+  a.ctl = t->ctl;
+  a.bind();
+}
+
+// tscan -> tprefix -> while (more) { tclaim -> tapply -> round_end }
+pp_status build_tile_graph(pp_iblt *t) {
+  TileArgsSet ta;
+  fill_tile_args(t, ta);
+  EndArgs ea{t->ctl, RoundStats{t->st_rec, t->st_alive, t->st_front}, 1, 0, {}};
+  cudaGraph_t g = nullptr;
+  PP_CUDA(cudaGraphCreate(&g, 0));
+  pp_status st = PP_OK;
+  cudaGraphNode_t n_scan, n_pre, n_cond, n_claim, n_act, n_apply[2], n_end;
+  const int grid_act = (int)((t->trb.n_tiles + kBlock - 1) / kBlock);
+  const size_t smem_claim = ((size_t)t->trb.n_seg_d + t->trb.n_seg_s + 1) * sizeof(u32);
+  cudaGraphConditionalHandle h;
+  cudaGraphNodeParams cp{};
+  cudaGraph_t body;
+  st = add_kernel(&n_scan, g, nullptr, 0, t->k.tscan, t->grid_tscan, kTRThreads, 0, ta.scan);
+  if (st != PP_OK) goto done;
+  st = add_kernel(&n_pre, g, &n_scan, 1, (const void *)k_tprefix, 1, 1024, 0, ta.prefix);
+  if (st != PP_OK) goto done;
+  if (cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault) != cudaSuccess) {
+    st = fail(PP_ERR_CUDA, "cudaGraphConditionalHandleCreate failed");
+    goto done;
+  }
+  cp.type = cudaGraphNodeTypeConditional;
+  cp.conditional.handle = h;
+  cp.conditional.type = cudaGraphCondTypeWhile;
+  cp.conditional.size = 1;
+  if (cudaGraphAddNode(&n_cond, g, &n_pre, nullptr, 1, &cp) != cudaSuccess) {
+    st = fail(PP_ERR_CUDA, "cudaGraphAddNode(conditional while) failed");
+    goto done;
+  }
+  body = cp.conditional.phGraph_out[0];
+  ea.cond = h;
+  ea.bind();
+  st = add_kernel(&n_claim, body, nullptr, 0, t->k.tclaim, t->grid_tclaim, kBlock, smem_claim, ta.claim);
+  if (st != PP_OK) goto done;
+  st = add_kernel(&n_act, body, &n_claim, 1, (const void *)k_tactive, grid_act, kBlock, 0, ta.active);
+  if (st != PP_OK) goto done;
+  // dense and sparse tiles in two kernels that may run side by side
+  st = add_kernel(&n_apply[0], body, &n_act, 1, t->k.tapply, t->grid_tapply, kTRThreads, kTApplySmem, ta.apply);
+  if (st != PP_OK) goto done;
+  st = add_kernel(&n_apply[1], body, &n_act, 1, t->k.tapply_sparse, t->grid_tsparse, kTSThreads, 0, ta.apply);
+  if (st != PP_OK) goto done;
+  st = add_kernel(&n_end, body, n_apply, 2, (const void *)k_round_end, 1, 32, 0, ea.p);
+  if (st != PP_OK) goto done;
+  if (cudaGraphInstantiate(&t->exec, g, 0) != cudaSuccess) {
+    st = fail(PP_ERR_CUDA, "cudaGraphInstantiate failed: %s", cudaGetErrorString(cudaGetLastError()));
+    t->exec = nullptr;
+  }
+  t->graph_gen = t->rec_gen;
+done:
+  cudaGraphDestroy(g);
+  return st;
+}
+
+pp_status run_tile_host_loop(pp_iblt *t, cudaStream_t s) {
+  TileArgsSet ta;
+  fill_tile_args(t, ta);
+  EndArgs ea{t->ctl, RoundStats{t->st_rec, t->st_alive, t->st_front}, 0, 0, {}};
+  ea.bind();
+  const int grid_act = (int)((t->trb.n_tiles + kBlock - 1) / kBlock);
+  const size_t smem_claim = ((size_t)t->trb.n_seg_d + t->trb.n_seg_s + 1) * sizeof(u32);
+  PP_CUDA(cudaLaunchKernel(t->k.tscan, dim3(t->grid_tscan), dim3(kTRThreads), ta.scan, 0, s));
+  PP_CUDA(cudaLaunchKernel((const void *)k_tprefix, dim3(1), dim3(1024), ta.prefix, 0, s));
+  for (;;) {
+    PP_CUDA(cudaLaunchKernel(t->k.tclaim, dim3(t->grid_tclaim), dim3(kBlock), ta.claim, smem_claim, s));
+    PP_CUDA(cudaLaunchKernel((const void *)k_tactive, dim3(grid_act), dim3(kBlock), ta.active, 0, s));
+    PP_CUDA(cudaLaunchKernel(t->k.tapply, dim3(t->grid_tapply), dim3(kTRThreads), ta.apply, kTApplySmem, s));
+    PP_CUDA(cudaLaunchKernel(t->k.tapply_sparse, dim3(t->grid_tsparse), dim3(kTSThreads), ta.apply, 0, s));
+    PP_CUDA(cudaLaunchKernel((const void *)k_round_end, dim3(1), dim3(32), ea.p, 0, s));
+    PP_CUDA(cudaMemcpyAsync(&t->h_ctl->more, &t->ctl->more, sizeof(u32), cudaMemcpyDeviceToHost, s));
+    PP_CUDA(cudaStreamSynchronize(s));
+    if (!t->h_ctl->more) break;
+  }
+  return PP_OK;
+}
+
 pp_status run_host_loop(pp_iblt *t, cudaStream_t s) {
   ScanArgs sa;
   PeelArgs pa;
@@ -777,6 +996,7 @@ pp_status pp_iblt_create(pp_iblt **out, uint64_t n_cells, uint32_t r, uint64_t s
   };
   al((void **)&t->cells, n_cells * sizeof(Cell));
   al((void **)&t->fkey, n_cells * sizeof(u64));
+  t->front_cap = n_cells;
   al((void **)&t->fcell, n_cells * sizeof(u32));
   al((void **)&t->cand, n_cells * sizeof(u32));
   al((void **)&t->bitmap, words * sizeof(u32));
@@ -823,7 +1043,17 @@ pp_status pp_workspace_size(uint64_t n_cells, uint32_t r, uint64_t m_keys, const
     counts = ns;
     tiles = tile_pass_bytes(tile_cap_for(cap), cap, ns, false);
   }
-  const bool rounds_binned = o.binned == 1 || (o.binned == 0 && n >= (1ull << 21));
+  // decode rounds for a table of m_keys insertions: tile rounds (their own
+  // record regions, r * m_keys + slack) or binned rounds (shared records)
+  const bool rounds_tiles = o.rounds == 2 || (o.rounds == 0 && n >= (1ull << 21) && o.binned != 2);
+  uint64_t tile_round_bytes = 0;
+  if (rounds_tiles) {
+    const uint64_t nt = (n + kTRCells - 1) / kTRCells;
+    tile_round_bytes = ((uint64_t)r * m_keys + (uint64_t)kTRAlign * nt) * (sizeof(u64) + sizeof(u16)) +
+                       (nt + 1) * sizeof(u64) + nt * (kTRPosStride * sizeof(u32) + 2 * sizeof(u32) +
+                                                      2 * sizeof(TileAct));
+  }
+  const bool rounds_binned = !rounds_tiles && (o.binned == 1 || (o.binned == 0 && n >= (1ull << 21)));
   if (rounds_binned) {
     uint32_t nb;
     uint64_t cap;
@@ -835,7 +1065,7 @@ pp_status pp_workspace_size(uint64_t n_cells, uint32_t r, uint64_t m_keys, const
   const uint64_t rec_bytes = records ? records * (sizeof(u64) + sizeof(u32)) + (counts + 1) * sizeof(u32) : 0;
   if (table_bytes) *table_bytes = table;
   if (fixed_bytes) *fixed_bytes = fixed;
-  if (peak_bytes) *peak_bytes = table + fixed + rec_bytes + tiles;
+  if (peak_bytes) *peak_bytes = table + fixed + rec_bytes + tiles + tile_round_bytes;
   return PP_OK;
 }
 
@@ -850,6 +1080,7 @@ pp_status pp_iblt_clear(pp_iblt *t, void *stream) {
   if (!t) return fail(PP_ERR_INVALID_ARG, "pp_iblt_clear: NULL table");
   PP_CUDA(cudaMemsetAsync(t->cells, 0, t->n * sizeof(Cell), as_stream(stream)));
   t->items = 0;
+  t->has_deletes = false;
   return PP_OK;
 }
 
@@ -866,6 +1097,7 @@ pp_status pp_iblt_delete(pp_iblt *t, const uint64_t *d_keys, uint64_t m, void *s
   if (m && !d_keys) return fail(PP_ERR_INVALID_ARG, "pp_iblt_delete: NULL keys");
   pp_status st = update(t, d_keys, m, -1, as_stream(stream));
   if (st == PP_OK) t->items -= (int64_t)m;
+  if (m) t->has_deletes = true;
   return st;
 }
 
@@ -874,6 +1106,7 @@ pp_status pp_iblt_build(pp_iblt *t, const uint64_t *d_keys, uint64_t m, void *st
   if (m && !d_keys) return fail(PP_ERR_INVALID_ARG, "pp_iblt_build: NULL keys");
   cudaStream_t s = as_stream(stream);
   t->items = 0;
+  t->has_deletes = false;
   if (!use_binned(t, m)) {
     PP_CUDA(cudaMemsetAsync(t->cells, 0, t->n * sizeof(Cell), s));
     pp_status st = launch_insert(t, d_keys, m, +1, s);
@@ -909,26 +1142,37 @@ pp_status pp_iblt_decode(pp_iblt *t, uint64_t *d_out_keys, uint64_t out_cap, pp_
   t->h_ctl->out = reinterpret_cast<u64 *>(d_out_keys);
   t->h_ctl->out_cap = out_cap;
   t->h_ctl->max_rounds = t->opt.max_rounds;
-  const bool want_bins = t->opt.binned == 1 || (t->opt.binned == 0 && t->n >= (1ull << 21));
+  // round kind: tile rounds (large tables built from insertions only), binned
+  // atomic rounds (other large tables), direct atomics (small tables)
+  const bool large = t->n >= (1ull << 21);
+  const bool want_tiles = t->k.tscan && !t->has_deletes &&
+                          (t->opt.rounds == 2 || (t->opt.rounds == 0 && large && t->opt.binned != 2));
+  const bool want_bins = !want_tiles && (t->opt.binned == 1 || (t->opt.binned == 0 && large));
+  if (want_tiles) {
+    pp_status st = ensure_tile_rounds(t, s);
+    if (st != PP_OK) return st;
+  }
   if (want_bins) {
     pp_status st = ensure_round_bins(t, s);
     if (st != PP_OK) return st;
     PP_CUDA(cudaMemsetAsync(t->bin_count, 0, t->n_bins * sizeof(u32), s));
   }
   // the graph holds buffer pointers: rebuild it when they moved or the round kind changed
-  if (t->exec && (want_bins != t->binned_rounds || (want_bins && t->graph_gen != t->rec_gen))) {
+  if (t->exec && (want_bins != t->binned_rounds || want_tiles != t->tile_rounds ||
+                  ((want_bins || want_tiles) && t->graph_gen != t->rec_gen))) {
     cudaGraphExecDestroy(t->exec);
     t->exec = nullptr;
   }
   t->binned_rounds = want_bins;
+  t->tile_rounds = want_tiles;
   k_ctl_init<<<1, 32, 0, s>>>(t->ctl, *t->h_ctl);
   PP_CUDA(cudaGetLastError());
   if (t->opt.host_loop) {
-    pp_status st = run_host_loop(t, s);
+    pp_status st = want_tiles ? run_tile_host_loop(t, s) : run_host_loop(t, s);
     if (st != PP_OK) return st;
   } else {
     if (!t->exec) {
-      pp_status st = build_graph(t);
+      pp_status st = want_tiles ? build_tile_graph(t) : build_graph(t);
       if (st != PP_OK) return st;
     }
     PP_CUDA(cudaGraphLaunch(t->exec, s));
@@ -960,7 +1204,8 @@ pp_status pp_iblt_decode(pp_iblt *t, uint64_t *d_out_keys, uint64_t out_cap, pp_
     return fail(PP_ERR_CAPACITY, "pp_iblt_decode: more keys recovered than out_cap=%llu",
                 (unsigned long long)out_cap);
   if (c.flags & FLAG_INTERNAL)
-    return fail(PP_ERR_INVALID_ARG, "pp_iblt_decode: a pure cell's key does not hash to it");
+    return fail(PP_ERR_INVALID_ARG,
+                "pp_iblt_decode: a pure cell's key does not hash to it, or the table holds a negative count");
   if (c.flags & FLAG_ROUND_LIMIT)
     return fail(PP_ERR_ROUND_LIMIT, "pp_iblt_decode: stopped after max_rounds=%u rounds",
                 t->opt.max_rounds);

@@ -397,6 +397,8 @@ __global__ void k_round_end(DecodeCtl *__restrict__ ctl, RoundStats st, int set_
   c.n_front = c.n_next;
   c.n_next = 0;
   c.n_cand = 0;
+  c.n_act = 0;
+  c.n_act_dense = 0;
   u32 more = c.n_front > 0 && (c.flags & (FLAG_CAPACITY | FLAG_INTERNAL)) == 0;
   if (more && t >= c.max_rounds) {
     c.flags |= FLAG_ROUND_LIMIT;

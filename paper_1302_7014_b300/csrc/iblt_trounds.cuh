@@ -1,0 +1,674 @@
+// Tile rounds: the IBLT decode's rounds (Sec. 1 at k = 2 on the hypergraph of
+// Sec. 6) with each round's cell updates applied tile by tile.
+//
+// The table is cut into tiles of 4096 consecutive cells.  Per round:
+//   k_tclaim  for every frontier entry (cell c, key x snapshotted at the
+//             round's start) decides, as k_claim does, whether c is the
+//             lowest-index cell of x that was pure at the round's start.  A
+//             winner outputs x and empties its own cell c with one plain
+//             store: c held exactly x, so (0, 0, 0) is its state once x is
+//             deleted (any other update to c this round is applied on top of
+//             that store by k_tapply).  For each of the key's other cells it
+//             appends one record (x, offset of the cell in its tile) to that
+//             tile's record region.
+//   k_tactive lists the tiles that received records, split into sparse
+//             (at most kTSCap records) and dense ones.
+//   k_tapply_sparse / k_tapply  one block per tile: the round's records of
+//             the tile are folded in shared memory into one update per
+//             touched cell (count decrement, key XOR, checksum XOR) -- in a
+//             small hash table for sparse tiles, in per-cell arrays for dense
+//             ones; then every touched cell is read, updated and written back
+//             once with plain 256-bit accesses and no global atomics.  A cell
+//             that is pure after the update joins the next frontier right
+//             there (key snapshot and bitmap bit), so no separate pass
+//             re-reads it.
+// Records of a tile over the whole decode never exceed the sum of the tile's
+// counts at the decode's start (each key leaves each of its cells once), so
+// every tile owns a fixed region of that size, filled round after round.  That
+// bound holds for tables built from insertions only; the host sends tables
+// that saw deletions to the binned rounds instead.
+//
+// The frontier is kept in segments, one per block of k_tscan / k_tapply /
+// k_tapply_sparse: a block writes the cells it finds pure into its own
+// segment with a cursor in shared memory (no global atomic per push).
+#pragma once
+
+#include "iblt_types.cuh"
+
+namespace pp {
+
+constexpr int kTRShift = 12;
+constexpr u32 kTRCells = 1u << kTRShift;     // cells per tile
+constexpr int kTRThreads = 512;              // threads per block of k_tscan / k_tapply
+constexpr int kTRScanItems = kTRCells / kTRThreads;
+constexpr u32 kTRAlign = 64;                 // records: tile regions start on 128-byte lines
+constexpr int kTRPosStride = 8;              // write cursors (u32) one per 32-byte sector
+constexpr int kTRCellsPerThread = 4;         // touched cells per thread per step of k_tapply
+constexpr int kTSThreads = 256;              // threads per block of k_tapply_sparse
+constexpr u32 kTSCap = 512;                  // records of a sparse tile (at most)
+constexpr u32 kTSSlots = 1024;               // hash slots of k_tapply_sparse
+constexpr u32 kTSEmpty = 0xffffffffu;
+
+// A tile with records in the current round: records [lo, lo + n) (absolute slots).
+struct TileAct {
+  u64 lo;
+  u32 tile;
+  u32 n;
+};
+
+struct TileRoundBufs {
+  u64 *rec_key;   // records: the key
+  u16 *rec_off;   // records: cell offset in its tile
+  u64 *base;      // per tile: first record slot of its region (n_tiles + 1 entries)
+  u32 *base64;    // per tile: base / kTRAlign (regions start on multiples of kTRAlign)
+  u32 *pos;       // per tile (stride kTRPosStride): records written this decode
+  u32 *done;      // per tile: records applied this decode
+  u32 *sum;       // per tile: sum of counts at the decode's start (scan output)
+  TileAct *act;   // sparse tiles with records this round (n_tiles entries)
+  TileAct *act_d; // dense tiles with records this round (n_tiles entries)
+  u32 *fseg;      // per frontier segment: entries
+  const u64 *fstart;  // per frontier segment: first entry in fkey / fcell
+  u64 rec_cap;    // slots in rec_key / rec_off
+  u32 n_tiles;
+  u32 n_seg_d;    // segments of k_tscan / k_tapply blocks (first)
+  u32 n_seg_s;    // segments of k_tapply_sparse blocks (after those)
+  u32 cap_d;      // entries of a k_tscan / k_tapply segment: 4096 * ceil(n_tiles / n_seg_d)
+  u32 cap_s;      // entries of a k_tapply_sparse segment: kTSCap * ceil(n_tiles / n_seg_s)
+  u32 pad;
+};
+
+// Initial full scan, one tile per block step: F_1 (cells pure before any
+// round) with their bitmap bits, the sum of each tile's counts, and the
+// decode's alive / nonempty counters.  Every bitmap word is written here.
+// Runs n_seg_d blocks; block b takes tiles b, b + n_seg_d, ... (at most
+// 4096 pushes each) and writes segment b.
+template <int R>
+__global__ void __launch_bounds__(kTRThreads) k_tscan(const Cell *__restrict__ cells, const TableArgs tab0,
+                                                      u64 *__restrict__ fkey, u32 *__restrict__ fcell,
+                                                      u32 *__restrict__ bitmap, TileRoundBufs tb,
+                                                      DecodeCtl *__restrict__ ctl) {
+  __shared__ u32 s_seg, s_neg;
+  __shared__ u64 s_red[kTRThreads / 32];
+  const u32 tid = threadIdx.x;
+  const u64 seed_chk = tab0.seed[rank_of<R>(tab0)];
+  const u32 n = tab0.n_cells;
+  const u64 seg0 = tb.fstart[blockIdx.x];
+  u64 alive = 0, nonempty = 0;
+  if (tid == 0) s_seg = 0, s_neg = 0;
+  __syncthreads();
+  for (u32 t = blockIdx.x; t < tb.n_tiles; t += gridDim.x) {
+    const u32 c0 = t << kTRShift;
+    long long sum = 0;
+#pragma unroll 4
+    for (int it = 0; it < kTRScanItems; ++it) {
+      const u32 c = c0 + (u32)it * kTRThreads + tid;
+      const bool valid = c < n;
+      bool pure = false;
+      u64 key = 0;
+      if (valid) {
+        u64 chk;
+        int cnt;
+        ld_cell_cs(cells + c, key, chk, cnt);
+        pure = cell_pure(cnt, key, chk, seed_chk);
+        alive += cnt >= 2;
+        nonempty += cnt != 0;
+        sum += cnt;
+        if (cnt < 0) s_neg = 1;
+      }
+      const u32 ball = __ballot_sync(kFull, pure);
+      const u32 first = c0 + (u32)it * kTRThreads + (tid & ~31u);
+      if (lane_id() == 0 && first < n) bitmap[first >> 5] = ball;
+      const u32 p = warp_reserve<u32>(pure, &s_seg);
+      if (pure && p < tb.cap_d) {
+        fkey[seg0 + p] = key;
+        fcell[seg0 + p] = c;
+      }
+    }
+    const long long sm = block_sum<long long, kTRThreads>(sum, reinterpret_cast<long long *>(s_red));
+    if (tid == 0) tb.sum[t] = sm > 0 ? (u32)sm : 0u;
+  }
+  const u64 a = block_sum<u64, kTRThreads>(alive, s_red);
+  const u64 ne = block_sum<u64, kTRThreads>(nonempty, s_red);
+  if (tid == 0) {
+    if (a) atomicAdd(&ctl->alive, a);
+    if (ne) atomicAdd(&ctl->nonempty, ne);
+    if (s_neg) atomicOr(&ctl->flags, (u32)FLAG_INTERNAL);  // a negative count: not an insert-only table
+    tb.fseg[blockIdx.x] = s_seg;
+    if (s_seg) atomicAdd(&ctl->n_next, s_seg);
+  }
+}
+
+// Tile regions: base[t] = sum over t' < t of the tile sums, each rounded up to
+// kTRAlign records; cursors at 0; every sparse segment empty.  One block;
+// flags FLAG_CAPACITY if the regions exceed the record buffers.
+__global__ void __launch_bounds__(1024) k_tprefix(TileRoundBufs tb, DecodeCtl *__restrict__ ctl) {
+  __shared__ u64 s_w[33];
+  const u32 tid = threadIdx.x;
+  const u32 per = (tb.n_tiles + 1023) / 1024;
+  const u32 lo = tid * per, hi = min(lo + per, tb.n_tiles);
+  u64 own = 0;
+  for (u32 t = lo; t < hi; ++t) own += (tb.sum[t] + kTRAlign - 1) / kTRAlign * kTRAlign;
+  u64 inc = own;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const u64 y = __shfl_up_sync(kFull, inc, o);
+    if ((int)lane_id() >= o) inc += y;
+  }
+  if (lane_id() == 31) s_w[tid >> 5] = inc;
+  __syncthreads();
+  if (tid < 32) {
+    const u64 w = s_w[tid];
+    u64 wi = w;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const u64 y = __shfl_up_sync(kFull, wi, o);
+      if ((int)tid >= o) wi += y;
+    }
+    s_w[tid] = wi - w;
+    if (tid == 31) s_w[32] = wi;
+  }
+  __syncthreads();
+  u64 run = s_w[tid >> 5] + inc - own;
+  for (u32 t = lo; t < hi; ++t) {
+    tb.base[t] = run;
+    tb.base64[t] = (u32)(run / kTRAlign);
+    tb.pos[(u64)t * kTRPosStride] = 0;
+    tb.done[t] = 0;
+    run += (tb.sum[t] + kTRAlign - 1) / kTRAlign * kTRAlign;
+  }
+  for (u32 k = tid; k < tb.n_seg_s; k += 1024) tb.fseg[tb.n_seg_d + k] = 0;
+  if (tid == 0) {
+    tb.base[tb.n_tiles] = s_w[32];
+    if (s_w[32] > tb.rec_cap) atomicOr(&ctl->flags, (u32)FLAG_CAPACITY);
+  }
+}
+
+// Phase B1 of round t (see the file comment).  Dynamic shared memory: the
+// prefix of the frontier's segment sizes (n_seg_d + n_seg_s + 1 u32).
+template <int R>
+__global__ void __launch_bounds__(kBlock, 4) k_tclaim(Cell *__restrict__ cells, const TableArgs tab0,
+                                                      const u64 *__restrict__ fkey,
+                                                      const u32 *__restrict__ fcell,
+                                                      const u32 *__restrict__ bitmap, TileRoundBufs tb,
+                                                      DecodeCtl *__restrict__ ctl) {
+  constexpr int NR = nr_of<R>();
+  extern __shared__ __align__(16) unsigned char smem[];
+  u32 *s_pre = reinterpret_cast<u32 *>(smem);
+  __shared__ u64 s_out[kClaimChunk];
+  __shared__ u32 s_nout, s_wt[kBlock / 32], s_seg0;
+  __shared__ u64 s_obase;
+  __shared__ u64 s_red[kBlock / 32];
+  const u32 tid = threadIdx.x;
+  const u32 n = *(volatile u32 *)&ctl->n_front;
+  if (n == 0) return;  // uniform: nothing to claim
+  u64 *out = ctl->out;
+  const u64 out_cap = ctl->out_cap;
+  const u64 keep = l2_evict_last_policy();
+  const int r = rank_of<R>(tab0);
+  const u32 ns = tb.n_seg_d + tb.n_seg_s;
+  // exclusive prefix of the segment sizes: thread i owns segments [i*per, (i+1)*per)
+  {
+    const u32 per = (ns + kBlock - 1) / kBlock;
+    const u32 lo = tid * per, hi = min(lo + per, ns);
+    u32 own = 0;
+    for (u32 k = lo; k < hi; ++k) own += tb.fseg[k];
+    u32 inc = own;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const u32 y = __shfl_up_sync(kFull, inc, o);
+      if ((int)lane_id() >= o) inc += y;
+    }
+    if (lane_id() == 31) s_wt[tid >> 5] = inc;
+    __syncthreads();
+    if (tid < 32) {
+      const u32 w = tid < kBlock / 32 ? s_wt[tid] : 0;
+      u32 wi = w;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const u32 y = __shfl_up_sync(kFull, wi, o);
+        if ((int)tid >= o) wi += y;
+      }
+      if (tid < kBlock / 32) s_wt[tid] = wi - w;
+      if (tid == kBlock / 32 - 1) s_pre[ns] = wi;
+    }
+    __syncthreads();
+    u32 run = s_wt[tid >> 5] + inc - own;
+    for (u32 k = lo; k < hi; ++k) {
+      s_pre[k] = run;
+      run += tb.fseg[k];
+    }
+    __syncthreads();
+  }
+  u32 flags = 0;
+  u64 emptied = 0;
+  for (u64 c0 = (u64)blockIdx.x * kClaimChunk; c0 < n; c0 += (u64)gridDim.x * kClaimChunk) {
+    if (tid == 0) {
+      s_nout = 0;
+      // segment of the chunk's first entry: the last k with s_pre[k] <= c0
+      u32 a = 0, b = ns;
+      while (b - a > 1) {
+        const u32 mid = (a + b) >> 1;
+        if (s_pre[mid] <= (u32)c0) a = mid;
+        else b = mid;
+      }
+      s_seg0 = a;
+    }
+    __syncthreads();
+    u64 x[kClaimItems];
+    u32 c[kClaimItems], cj[kClaimItems][NR];
+    bool win[kClaimItems];
+    int jstar[kClaimItems];
+    const u32 a0 = s_seg0;
+#pragma unroll
+    for (int it = 0; it < kClaimItems; ++it) {
+      const u32 i = (u32)(c0 + (u64)it * kBlock + tid);
+      win[it] = i < n;
+      u64 src = 0;
+      if (win[it]) {
+        // segments hold thousands of entries: a chunk spans one or two
+        u32 a = a0;
+        while (a + 1 < ns && s_pre[a + 1] <= i) ++a;
+        src = tb.fstart[a] + (i - s_pre[a]);
+      }
+      x[it] = win[it] ? __ldcs(fkey + src) : 0ull;
+      c[it] = win[it] ? __ldcs(fcell + src) : 0u;
+    }
+#pragma unroll
+    for (int it = 0; it < kClaimItems; ++it) {
+      cells_of<NR>(x[it], tab0, cj[it]);
+      int js = -1;
+#pragma unroll
+      for (int j = NR - 1; j >= 0; --j)
+        if (j < r && cj[it][j] == c[it]) js = j;
+      jstar[it] = js;
+      if (win[it] && js < 0) {
+        flags |= FLAG_INTERNAL;
+        win[it] = false;
+      }
+      // the lowest-index cell of x that was pure at the round's start wins
+#pragma unroll
+      for (int j = 0; j < NR - 1; ++j) {
+        if (win[it] && j < js) {
+          const u32 w = __ldcg(bitmap + (cj[it][j] >> 5));
+          if ((w >> (cj[it][j] & 31u)) & 1u) win[it] = false;
+        }
+      }
+    }
+#pragma unroll
+    for (int it = 0; it < kClaimItems; ++it) {
+      const u32 p = warp_reserve<u32>(win[it], &s_nout);
+      if (win[it]) {
+        s_out[p] = x[it];
+        st_cell_cs(cells + c[it], 0ull, 0ull, 0);  // the winner's own cell held exactly x
+        emptied += 1;
+      }
+    }
+    // records for the other cells: every cursor atomic of this thread in flight
+    // at once.  A record past its tile's region would mean a cell held more
+    // keys than its count; k_tactive checks that per tile, so only the
+    // buffer's end is checked here.
+    u32 at[kClaimItems][NR], b0[kClaimItems][NR];
+#pragma unroll
+    for (int it = 0; it < kClaimItems; ++it) {
+#pragma unroll
+      for (int j = 0; j < NR; ++j) {
+        if (win[it] && j < r && j != jstar[it]) {
+          const u32 t = cj[it][j] >> kTRShift;
+          b0[it][j] = tb.base64[t];
+          at[it][j] = atomicAdd(tb.pos + (u64)t * kTRPosStride, 1u);
+        }
+      }
+    }
+#pragma unroll
+    for (int it = 0; it < kClaimItems; ++it) {
+#pragma unroll
+      for (int j = 0; j < NR; ++j) {
+        if (win[it] && j < r && j != jstar[it]) {
+          const u64 q = (u64)b0[it][j] * kTRAlign + at[it][j];
+          if (q < tb.rec_cap) {
+            st_l2_policy(tb.rec_key + q, x[it], keep);
+            tb.rec_off[q] = (u16)(cj[it][j] & (kTRCells - 1));
+          } else {
+            flags |= FLAG_INTERNAL;
+          }
+        }
+      }
+    }
+    __syncthreads();
+    const u32 no = s_nout;
+    if (tid == 0 && no) s_obase = atomicAdd(&ctl->n_out, (u64)no);
+    __syncthreads();
+    const u64 ob = s_obase;
+    for (u32 q = tid; q < no; q += kBlock) {
+      if (ob + q < out_cap) out[ob + q] = s_out[q];
+      else flags |= FLAG_CAPACITY;
+    }
+    __syncthreads();
+  }
+  const u64 e = block_sum<u64, kBlock>(emptied, s_red);
+  if (tid == 0 && e) atomicAdd(&ctl->emptied, e);
+  if (flags) atomicOr(&ctl->flags, flags);
+}
+
+// The tiles with records in the current round (one thread per tile), split
+// into sparse (at most kTSCap records) and dense ones.
+__global__ void __launch_bounds__(kBlock) k_tactive(TileRoundBufs tb, DecodeCtl *__restrict__ ctl) {
+  if (*(volatile u32 *)&ctl->round == 0) return;  // the first loop iteration only promotes F_1
+  for (u32 t0 = blockIdx.x * kBlock; t0 < tb.n_tiles; t0 += gridDim.x * kBlock) {
+    const u32 t = t0 + threadIdx.x;
+    u32 lo = 0, hi = 0;
+    u64 b = 0;
+    if (t < tb.n_tiles) {
+      lo = tb.done[t];
+      b = tb.base[t];
+      const u32 p = tb.pos[(u64)t * kTRPosStride], lim = (u32)(tb.base[t + 1] - b);
+      hi = p < lim ? p : lim;
+      // more records than the tile's counts allow (only a table with deletions
+      // could do that): the extra ones landed in the next region
+      if (p > lim) atomicOr(&ctl->flags, (u32)FLAG_INTERNAL);
+    }
+    const bool any = hi > lo;
+    const bool dense = any && hi - lo > kTSCap;
+    const u32 kd = warp_reserve<u32>(dense, &ctl->n_act_dense);
+    const u32 ks = warp_reserve<u32>(any && !dense, &ctl->n_act);
+    if (dense) tb.act_d[kd] = TileAct{b + lo, t, hi - lo};
+    else if (any) tb.act[ks] = TileAct{b + lo, t, hi - lo};
+  }
+}
+
+// Drops the L2 lines of consumed records unwritten (tile regions start on
+// 128-byte lines of both record arrays, so no line holds another tile's).
+__device__ __forceinline__ void discard_records(const TileRoundBufs &tb, u64 b, u32 n, u32 tid, u32 nthreads) {
+  const u64 k0 = (b * 8) & ~127ull, k1 = ((b + n) * 8 + 127) & ~127ull;
+  for (u64 a = k0 + (u64)tid * 128; a < k1; a += (u64)nthreads * 128)
+    l2_discard(reinterpret_cast<const unsigned char *>(tb.rec_key) + a);
+  const u64 o0 = (b * 2) & ~127ull, o1 = ((b + n) * 2 + 127) & ~127ull;
+  for (u64 a = o0 + (u64)tid * 128; a < o1; a += (u64)nthreads * 128)
+    l2_discard(reinterpret_cast<const unsigned char *>(tb.rec_off) + a);
+}
+
+// Shared memory of k_tapply: per cell of a tile the folded key XOR and
+// checksum XOR (u64 each), the record count (u32) and the list of touched
+// cells (u16).
+constexpr size_t kTApplySmem = (size_t)kTRCells * (8 + 8 + 4 + 2);
+
+// Phase B2 of round t + phase A of round t + 1 for the dense tiles (see the
+// file comment).  Runs n_seg_d blocks; block b takes the dense tiles b,
+// b + n_seg_d, ... and writes frontier segment b.
+template <int R>
+__global__ void __launch_bounds__(kTRThreads, 2) k_tapply(Cell *__restrict__ cells, const TableArgs tab0,
+                                                          TileRoundBufs tb, u64 *__restrict__ fkey,
+                                                          u32 *__restrict__ fcell, u32 *__restrict__ bitmap,
+                                                          DecodeCtl *__restrict__ ctl) {
+  if (*(volatile u32 *)&ctl->round == 0) return;  // the first loop iteration only promotes F_1
+  extern __shared__ __align__(16) unsigned char smem[];
+  u64 *s_dkey = reinterpret_cast<u64 *>(smem);
+  u64 *s_dchk = s_dkey + kTRCells;
+  u32 *s_dcnt = reinterpret_cast<u32 *>(s_dchk + kTRCells);
+  u16 *s_touch = reinterpret_cast<u16 *>(s_dcnt + kTRCells);
+  u32 *s_dkey32 = reinterpret_cast<u32 *>(s_dkey);
+  u32 *s_dchk32 = reinterpret_cast<u32 *>(s_dchk);
+  __shared__ u32 s_nt, s_seg;
+  __shared__ u64 s_red[kTRThreads / 32];
+  const u32 tid = threadIdx.x;
+  const u64 seed_chk = tab0.seed[rank_of<R>(tab0)];
+  const u32 n_act = *(volatile u32 *)&ctl->n_act_dense;
+  const u64 seg0 = tb.fstart[blockIdx.x];
+  u64 emptied = 0, dropped = 0;
+  if (blockIdx.x < n_act) {  // uniform: blocks with no dense tile skip the set-up
+    for (u32 i = tid; i < kTRCells; i += kTRThreads) {
+      s_dkey[i] = 0;
+      s_dchk[i] = 0;
+      s_dcnt[i] = 0;
+    }
+  }
+  if (tid == 0) s_nt = 0, s_seg = 0;
+  __syncthreads();
+  TileAct nxt{};
+  if (blockIdx.x < n_act) nxt = tb.act_d[blockIdx.x];
+  for (u32 ai = blockIdx.x; ai < n_act; ai += gridDim.x) {
+    const TileAct cur = nxt;
+    if (ai + gridDim.x < n_act) nxt = tb.act_d[ai + gridDim.x];  // the next tile's entry, early
+    const u64 b = cur.lo;
+    const u32 nrec = cur.n, t = cur.tile;
+    // fold the records into one update per cell (4 records per thread in flight)
+    for (u32 i0 = 0; i0 < nrec; i0 += 4 * kTRThreads) {
+      u64 x[4];
+      u32 o[4];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const u32 i = i0 + (u32)k * kTRThreads + tid;
+        o[k] = i < nrec ? (u32)__ldcs(tb.rec_off + b + i) : 0xffffffffu;
+        x[k] = i < nrec ? __ldcs(tb.rec_key + b + i) : 0ull;
+      }
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const bool v = o[k] != 0xffffffffu;
+        const u32 off = o[k] & (kTRCells - 1);
+        bool first = false;
+        if (v) {
+          const u64 cs = checksum(x[k], seed_chk);
+          first = atomicAdd(s_dcnt + off, 1u) == 0;
+          atomicXor(s_dkey32 + 2 * off, (u32)x[k]);
+          atomicXor(s_dkey32 + 2 * off + 1, (u32)(x[k] >> 32));
+          atomicXor(s_dchk32 + 2 * off, (u32)cs);
+          atomicXor(s_dchk32 + 2 * off + 1, (u32)(cs >> 32));
+        }
+        const u32 q = warp_reserve<u32>(first, &s_nt);
+        if (first) s_touch[q] = (u16)off;
+      }
+    }
+    __syncthreads();
+    discard_records(tb, b, nrec, tid, kTRThreads);
+    // one read-modify-write per touched cell (the loads of a thread's cells in
+    // flight together); pure results join F_{t+1} in this block's segment
+    const u32 nt = s_nt;
+    const u32 c0 = t << kTRShift;
+    for (u32 k0 = 0; k0 < nt; k0 += kTRCellsPerThread * kTRThreads) {
+      u32 off[kTRCellsPerThread];
+      bool v[kTRCellsPerThread];
+      u64 key[kTRCellsPerThread], chk[kTRCellsPerThread];
+      int cnt[kTRCellsPerThread];
+#pragma unroll
+      for (int q = 0; q < kTRCellsPerThread; ++q) {
+        const u32 k = k0 + (u32)q * kTRThreads + tid;
+        v[q] = k < nt;
+        off[q] = v[q] ? s_touch[k] : 0u;
+        key[q] = chk[q] = 0;
+        cnt[q] = 0;
+        if (v[q]) ld_cell_cg(cells + c0 + off[q], key[q], chk[q], cnt[q]);
+      }
+#pragma unroll
+      for (int q = 0; q < kTRCellsPerThread; ++q) {
+        bool pure = false;
+        u64 nk = 0;
+        if (v[q]) {
+          const u32 c = c0 + off[q];
+          const int nc = cnt[q] - (int)s_dcnt[off[q]];
+          nk = key[q] ^ s_dkey[off[q]];
+          const u64 nchk = chk[q] ^ s_dchk[off[q]];
+          st_cell_cs(cells + c, nk, nchk, nc);
+          emptied += (u64)(long long)((cnt[q] != 0) - (nc != 0));
+          dropped += cnt[q] >= 2 && nc < 2;
+          pure = cell_pure(nc, nk, nchk, seed_chk);
+          s_dcnt[off[q]] = 0;
+          s_dkey[off[q]] = 0;
+          s_dchk[off[q]] = 0;
+        }
+        const u32 p = warp_reserve<u32>(pure, &s_seg);
+        if (pure && p < tb.cap_d) {
+          const u32 c = c0 + off[q];
+          fkey[seg0 + p] = nk;
+          fcell[seg0 + p] = c;
+          atomicOr(bitmap + (c >> 5), 1u << (c & 31u));
+        }
+      }
+    }
+    __syncthreads();
+    if (tid == 0) {
+      tb.done[t] += nrec;
+      s_nt = 0;
+    }
+    __syncthreads();
+  }
+  const u64 e = block_sum<u64, kTRThreads>(emptied, s_red);
+  const u64 d = block_sum<u64, kTRThreads>(dropped, s_red);
+  if (tid == 0) {
+    if (e) atomicAdd(&ctl->emptied, e);
+    if (d) atomicAdd(&ctl->n_cand, (u32)d);
+    tb.fseg[blockIdx.x] = s_seg;
+    if (s_seg) atomicAdd(&ctl->n_next, s_seg);
+  }
+}
+
+// The same for the sparse tiles, with a small hash table (open addressing on
+// the cell offset) in place of the per-cell arrays, so that many tiles are in
+// flight per SM.  Runs n_seg_s blocks; block b takes the sparse tiles b,
+// b + n_seg_s, ... (at most kTSCap records, hence pushes, each) and writes
+// frontier segment n_seg_d + b.
+template <int R>
+__global__ void __launch_bounds__(kTSThreads, 6) k_tapply_sparse(Cell *__restrict__ cells, const TableArgs tab0,
+                                                                 TileRoundBufs tb, u64 *__restrict__ fkey,
+                                                                 u32 *__restrict__ fcell, u32 *__restrict__ bitmap,
+                                                                 DecodeCtl *__restrict__ ctl) {
+  if (*(volatile u32 *)&ctl->round == 0) return;  // the first loop iteration only promotes F_1
+  __shared__ u32 h_off[kTSSlots];   // cell offset of the slot, kTSEmpty if free
+  __shared__ u64 h_key[kTSSlots], h_chk[kTSSlots];
+  __shared__ u32 h_cnt[kTSSlots];
+  __shared__ u16 s_slot[kTSCap];    // the slots in use
+  __shared__ u32 s_ns, s_seg;
+  __shared__ u64 s_red[kTSThreads / 32];
+  const u32 tid = threadIdx.x;
+  const u64 seed_chk = tab0.seed[rank_of<R>(tab0)];
+  const u32 n_act = *(volatile u32 *)&ctl->n_act;
+  const u64 seg0 = tb.fstart[tb.n_seg_d + blockIdx.x];
+  u32 flags = 0;
+  for (u32 i = tid; i < kTSSlots; i += kTSThreads) {
+    h_off[i] = kTSEmpty;
+    h_key[i] = 0;
+    h_chk[i] = 0;
+    h_cnt[i] = 0;
+  }
+  if (tid == 0) s_ns = 0, s_seg = 0;
+  __syncthreads();
+  u64 emptied = 0, dropped = 0;
+  constexpr int PER = kTSCap / kTSThreads;
+  // the records of the block's next tile are loaded while the current one's
+  // cells are updated
+  TileAct nxt{};
+  u64 nx[PER];
+  u32 no[PER];
+  auto load_tile = [&](u32 ai) {
+    if (ai < n_act) nxt = tb.act[ai];
+    else nxt.n = 0;
+#pragma unroll
+    for (int k = 0; k < PER; ++k) {
+      const u32 i = (u32)k * kTSThreads + tid;
+      no[k] = i < nxt.n ? (u32)__ldcs(tb.rec_off + nxt.lo + i) : kTSEmpty;
+      nx[k] = i < nxt.n ? __ldcs(tb.rec_key + nxt.lo + i) : 0ull;
+    }
+  };
+  load_tile(blockIdx.x);
+  for (u32 ai = blockIdx.x; ai < n_act; ai += gridDim.x) {
+    const TileAct cur = nxt;
+    const u64 b = cur.lo;
+    const u32 nrec = cur.n, t = cur.tile;
+    u64 x[PER];
+    u32 o[PER];
+#pragma unroll
+    for (int k = 0; k < PER; ++k) {
+      x[k] = nx[k];
+      o[k] = no[k];
+    }
+#pragma unroll
+    for (int k = 0; k < PER; ++k) {
+      bool fresh = false;
+      u32 slot = 0;
+      if (o[k] != kTSEmpty) {
+        const u32 off = o[k] & (kTRCells - 1);
+        slot = off & (kTSSlots - 1);
+        // at most kTSCap of the kTSSlots slots are taken, so a free or matching
+        // slot is found within kTSCap + 1 probes
+        bool found = false;
+        for (u32 probe = 0; probe <= kTSCap; ++probe) {
+          const u32 prev = atomicCAS(h_off + slot, kTSEmpty, off);
+          if (prev == kTSEmpty || prev == off) {
+            fresh = prev == kTSEmpty;
+            found = true;
+            break;
+          }
+          slot = (slot + 1) & (kTSSlots - 1);
+        }
+        if (!found) {
+          flags |= FLAG_INTERNAL;
+          o[k] = kTSEmpty;
+        }
+      }
+      if (o[k] != kTSEmpty) {
+        const u64 cs = checksum(x[k], seed_chk);
+        atomicAdd(h_cnt + slot, 1u);
+        atomicXor(reinterpret_cast<u32 *>(h_key + slot), (u32)x[k]);
+        atomicXor(reinterpret_cast<u32 *>(h_key + slot) + 1, (u32)(x[k] >> 32));
+        atomicXor(reinterpret_cast<u32 *>(h_chk + slot), (u32)cs);
+        atomicXor(reinterpret_cast<u32 *>(h_chk + slot) + 1, (u32)(cs >> 32));
+      }
+      const u32 q = warp_reserve<u32>(fresh, &s_ns);
+      if (fresh) s_slot[q] = (u16)slot;
+    }
+    __syncthreads();
+    discard_records(tb, b, nrec, tid, kTSThreads);
+    load_tile(ai + gridDim.x);
+    const u32 ns = s_ns;
+    const u32 c0 = t << kTRShift;
+#pragma unroll
+    for (int k = 0; k < PER; ++k) {
+      const u32 q = (u32)k * kTSThreads + tid;
+      const bool v = q < ns;
+      u32 slot = 0, c = 0;
+      u64 key = 0, chk = 0;
+      int cnt = 0;
+      if (v) {
+        slot = s_slot[q];
+        c = c0 + h_off[slot];
+        ld_cell_cg(cells + c, key, chk, cnt);
+      }
+      bool pure = false;
+      if (v) {
+        const int nc = cnt - (int)h_cnt[slot];
+        key ^= h_key[slot];
+        chk ^= h_chk[slot];
+        st_cell_cs(cells + c, key, chk, nc);
+        emptied += (u64)(long long)((cnt != 0) - (nc != 0));
+        dropped += cnt >= 2 && nc < 2;
+        pure = cell_pure(nc, key, chk, seed_chk);
+        h_off[slot] = kTSEmpty;
+        h_key[slot] = 0;
+        h_chk[slot] = 0;
+        h_cnt[slot] = 0;
+      }
+      const u32 p = warp_reserve<u32>(pure, &s_seg);
+      if (pure && p < tb.cap_s) {
+        fkey[seg0 + p] = key;
+        fcell[seg0 + p] = c;
+        atomicOr(bitmap + (c >> 5), 1u << (c & 31u));
+      }
+    }
+    __syncthreads();
+    if (tid == 0) {
+      tb.done[t] += nrec;
+      s_ns = 0;
+    }
+    __syncthreads();
+  }
+  const u64 e = block_sum<u64, kTSThreads>(emptied, s_red);
+  const u64 d = block_sum<u64, kTSThreads>(dropped, s_red);
+  if (tid == 0) {
+    if (e) atomicAdd(&ctl->emptied, e);
+    if (d) atomicAdd(&ctl->n_cand, (u32)d);
+    tb.fseg[tb.n_seg_d + blockIdx.x] = s_seg;
+    if (s_seg) atomicAdd(&ctl->n_next, s_seg);
+  }
+  if (flags) atomicOr(&ctl->flags, flags);
+}
+
+}  // namespace pp

@@ -32,6 +32,8 @@ struct DecodeCtl {
   u32 stats_rounds;     // batch: per-table per-round counter slots
   u32 apply_next;       // binned rounds: next chunk of update records to apply
   u32 n_neg;            // signed decode: keys recovered with sign -1
+  u32 n_act;            // tile rounds: sparse tiles with records in the current round
+  u32 n_act_dense;      // tile rounds: dense tiles with records in the current round
 };
 
 // Per-round device statistics (index t-1 for round t).
@@ -193,6 +195,8 @@ struct IbltKernels {
   const void *sub_claim = nullptr;  // binned sub-rounds: k_claim without the claim check
   const void *sg_scan = nullptr, *sg_peel = nullptr, *sg_filter = nullptr;     // signed (plain only)
   const void *sg_claim = nullptr, *sg_apply = nullptr;                         // signed, binned rounds
+  const void *tscan = nullptr, *tclaim = nullptr, *tapply = nullptr;           // tile rounds (plain only)
+  const void *tapply_sparse = nullptr;
 };
 
 // The kernel set for a rank code: 3 or 4 = that r; -4 = any r <= 4 (batched

@@ -164,13 +164,14 @@ def test_deleting_keys_never_inserted(pp, n, binned):
     assert res.residual_cells == ot.residual_cells()
 
 
-@pytest.mark.parametrize("binned,host_loop", [(2, 0), (1, 0), (1, 1)], ids=["rounds", "binned", "binned-hostloop"])
-def test_round_limit(pp, binned, host_loop):
+@pytest.mark.parametrize("binned,host_loop,rounds", [(2, 0, 0), (1, 0, 1), (1, 1, 1), (0, 0, 2), (0, 1, 2)],
+                         ids=["rounds", "binned", "binned-hostloop", "tiles", "tiles-hostloop"])
+def test_round_limit(pp, binned, host_loop, rounds):
     """A decode stopped by the round limit leaves the table as the oracle's after that round.
     In the binned decode this also checks the end-of-decode clearing of the winners' cells:
     the frontier that was found but not processed must stay untouched."""
     keys = ppgen.distinct_keys(ppgen.edges_from_c(0.80, 100000), 41)
-    opts = pp.options(max_rounds=3, binned=binned, host_loop=host_loop)
+    opts = pp.options(max_rounds=3, binned=binned, host_loop=host_loop, rounds=rounds)
     with pytest.raises(pp.PPError) as ei:
         run_case(pp, 100000, 3, keys, 41, opts=opts, max_rounds=3)
     assert ei.value.name == "PP_ERR_ROUND_LIMIT"
@@ -325,20 +326,20 @@ BINNED_CASES = CASES + [(3 * (1 << 19) + 17, 3, 0.75, 31), ((1 << 21) + 1, 4, 0.
 def test_iblt_parity_binned_rounds(pp, n, r, c, seed):
     """Rounds split into claim + address-ordered apply (forced on) against the oracle."""
     keys = ppgen.distinct_keys(ppgen.edges_from_c(c, n), 3000 + seed)
-    run_case(pp, n, r, keys, seed, opts=pp.options(binned=1))
+    run_case(pp, n, r, keys, seed, opts=pp.options(binned=1, rounds=1))
 
 
 @pytest.mark.parametrize("n,r,c,seed", BINNED_CASES[-3:], ids=[f"binned-hostloop-n{n}" for n, r, c, _ in BINNED_CASES[-3:]])
 def test_iblt_parity_binned_rounds_host_loop(pp, n, r, c, seed):
     keys = ppgen.distinct_keys(ppgen.edges_from_c(c, n), 4000 + seed)
-    run_case(pp, n, r, keys, seed, opts=pp.options(binned=1, host_loop=1, ctas_per_sm=1))
+    run_case(pp, n, r, keys, seed, opts=pp.options(binned=1, host_loop=1, ctas_per_sm=1, rounds=1))
 
 
 def test_binned_rounds_after_workspace_growth(pp):
     # a small build first, then a bigger one: the record buffers move and the
     # decode graph must follow them
     n, r = 3 * (1 << 19) + 5, 3
-    gt = pp.IBLT(n, r, 5, pp.options(binned=1))
+    gt = pp.IBLT(n, r, 5, pp.options(binned=1, rounds=1))
     for m_frac in (0.1, 0.8, 0.75):
         keys = ppgen.distinct_keys(ppgen.edges_from_c(m_frac, n), int(m_frac * 100))
         gt.build(_dev(keys))
@@ -372,3 +373,85 @@ def test_workspace_size_matches_allocations(pp):
     assert abs((free0 - free1) - (ws["table"] + ws["fixed"])) < slack
     assert abs((free0 - free2) - ws["peak"]) < slack
     t.close()
+
+
+# ---- tile rounds: each round's updates folded per 4096-cell tile ------------
+TILE_CASES = CASES + [((1 << 21) + 1, 4, 0.85, 32), (3 * (1 << 21) + 17, 3, 0.75, 34)]
+
+
+@pytest.mark.parametrize("n,r,c,seed", TILE_CASES, ids=[f"tiles-n{n}-r{r}-c{c}" for n, r, c, _ in TILE_CASES])
+def test_iblt_parity_tile_rounds(pp, n, r, c, seed):
+    """Tile rounds (forced on for any size) against the oracle: per-round key
+    sets, survivors, the residue cell for cell."""
+    keys = ppgen.distinct_keys(ppgen.edges_from_c(c, n), 5000 + seed)
+    run_case(pp, n, r, keys, seed, opts=pp.options(rounds=2))
+
+
+@pytest.mark.parametrize("n,r,c,seed", TILE_CASES[:6] + TILE_CASES[-2:],
+                         ids=[f"tiles-hostloop-n{n}-r{r}" for n, r, c, _ in TILE_CASES[:6] + TILE_CASES[-2:]])
+def test_iblt_parity_tile_rounds_host_loop(pp, n, r, c, seed):
+    keys = ppgen.distinct_keys(ppgen.edges_from_c(c, n), 6000 + seed)
+    run_case(pp, n, r, keys, seed, opts=pp.options(rounds=2, host_loop=1, ctas_per_sm=1))
+
+
+def test_tile_rounds_skip_tables_with_deletions(pp):
+    """A table that saw a deletion may hold more keys in a cell than its count:
+    the decode takes the binned rounds instead, with the same results."""
+    n = (1 << 21) + 3
+    keys = ppgen.distinct_keys(ppgen.edges_from_c(0.7, n), 71)
+    run_case(pp, n, 3, keys, 71, deletes=keys[::7].copy())
+    ghost = ppgen.distinct_keys(1000, 72)   # deletions of keys never inserted: negative counts
+    gt = pp.IBLT(n, 3, 73, pp.options(rounds=2))
+    ot = oracle.IBLT(n, 3, 73)
+    gt.insert(_dev(keys))
+    gt.delete(_dev(ghost))
+    ot.insert(keys)
+    ot.insert(ghost, sign=-1)
+    out = torch.zeros(keys.size, dtype=torch.int64, device="cuda")
+    res = gt.decode(out)
+    ores = ot.decode_rounds()
+    assert res.rounds == ores["rounds"]
+    assert res.recovered_per_round == [k.size for k in ores["keys"]]
+    _assert_cells_equal(gt.cells(), ot)
+
+
+def test_tile_rounds_residue_then_more_keys(pp):
+    """Decode above the threshold (a residue is left), insert more keys, decode
+    again: the record regions are sized from the counts at each decode's start."""
+    n, r, seed = (1 << 21) + 7, 3, 81
+    gt = pp.IBLT(n, r, seed)
+    ot = oracle.IBLT(n, r, seed)
+    k1 = ppgen.distinct_keys(ppgen.edges_from_c(0.9, n), 82)
+    gt.insert(_dev(k1))
+    ot.insert(k1)
+    out = torch.zeros(k1.size * 2, dtype=torch.int64, device="cuda")
+    res = gt.decode(out)
+    ores = ot.decode_rounds()
+    assert res.rounds == ores["rounds"] and res.residual_cells == ot.residual_cells() > 0
+    _assert_cells_equal(gt.cells(), ot)
+    k2 = ppgen.distinct_keys(ppgen.edges_from_c(0.05, n), 83)
+    gt.insert(_dev(k2))
+    ot.insert(k2)
+    res = gt.decode(out)
+    ores = ot.decode_rounds()
+    assert res.rounds == ores["rounds"]
+    assert res.recovered_per_round == [k.size for k in ores["keys"]]
+    assert res.alive_cells_per_round == ores["cells_alive"]
+    _assert_cells_equal(gt.cells(), ot)
+    gt.close()
+
+
+def test_tile_rounds_after_workspace_growth(pp):
+    n, r = 3 * (1 << 19) + 5, 3
+    gt = pp.IBLT(n, r, 5, pp.options(rounds=2))
+    for m_frac in (0.1, 0.8, 0.75):
+        keys = ppgen.distinct_keys(ppgen.edges_from_c(m_frac, n), int(m_frac * 100) + 7)
+        gt.build(_dev(keys))
+        out = torch.zeros(keys.size, dtype=torch.int64, device="cuda")
+        res = gt.decode(out)
+        ot = oracle.IBLT(n, r, 5)
+        ot.insert(keys)
+        ores = ot.decode_rounds()
+        assert res.rounds == ores["rounds"]
+        assert res.recovered_per_round == [k.size for k in ores["keys"]]
+        _assert_cells_equal(gt.cells(), ot)
