@@ -79,6 +79,12 @@ typedef struct pp_options {
                             memory), binned atomic rounds for other large tables,
                             direct atomics below 2^21 cells (default); 1 = never tile
                             rounds; 2 = tile rounds for any table without deletions */
+  uint32_t apply_ctas;   /* resident blocks per SM of the binned rounds' apply kernel
+                            (default 3; sets the width of the table window updated at once) */
+  uint32_t frontier_switch; /* pp_peel_kcore, kcore_mode 0: edge-centric rounds run while
+                            |frontier| * frontier_switch >= edges left (default 2) */
+  uint32_t insert_chunk; /* batches: keys per insert work item (default 4096) */
+  uint32_t reserved;     /* 0 */
 } pp_options;
 
 /* Fills *opt with the defaults above. */
@@ -377,6 +383,43 @@ pp_status pp_batch_decode(pp_batch *b, uint64_t *d_out_keys, const uint64_t *h_o
 /* Copies table `table`'s cells to dst (host if to_host, else device). */
 pp_status pp_batch_copy_cells(pp_batch *b, uint32_t table, void *dst, int to_host, void *stream);
 
+/* Replaces the batch's run-time options (max_rounds and stats_rounds keep the
+ * values given at creation, which sized the statistics buffers).  Synchronizes
+ * the device; the next decode rebuilds its graph. */
+pp_status pp_batch_set_options(pp_batch *b, const pp_options *opt);
+
+/* The batch's current options. */
+pp_status pp_batch_get_options(const pp_batch *b, pp_options *opt);
+
+/* Autotuner of the batched form (the paper has no counterpart: the knobs are
+ * this implementation's).  Searches the batch's run-time knobs -- ctas_per_sm,
+ * apply_ctas, binned (1 = address-ordered records, 2 = direct atomics) and
+ * insert_chunk -- on the caller's own batch and keys: each candidate runs
+ * pp_batch_build + pp_batch_decode once untimed and `reps` times timed (CUDA
+ * events on `stream`, median).  Candidate 0 is the batch's options as they
+ * were.  A candidate whose per-table rounds, recovered counts or residues
+ * differ from candidate 0's is discarded and counted in report->mismatches.
+ * On return the batch holds the fastest candidate's options, also copied to
+ * *best; h_ms (host, PP_TUNE_MAX_CANDIDATES floats, or NULL) receives every
+ * candidate's median time (-1 for a discarded one).  The batch's tables are
+ * left decoded.  d_keys / h_key_offsets as for pp_batch_build, d_out_keys /
+ * h_out_offsets as for pp_batch_decode.  INVALID_ARG for NULL arguments or reps
+ * outside 1..64; errors of the build or decode are passed through (the batch
+ * then gets its previous options back). */
+#define PP_TUNE_MAX_CANDIDATES 32u
+typedef struct pp_tune_report {
+  uint32_t n_candidates;
+  uint32_t best_index;
+  float default_ms;   /* candidate 0: the options the batch had */
+  float best_ms;
+  uint32_t mismatches;
+  uint32_t pad;
+} pp_tune_report;
+
+pp_status pp_tune_batch(pp_batch *b, const uint64_t *d_keys, const uint64_t *h_key_offsets, uint64_t *d_out_keys,
+                        const uint64_t *h_out_offsets, uint32_t reps, pp_options *best, pp_tune_report *report,
+                        float *h_ms, void *stream);
+
 /* Number of tables, arena cells (with alignment padding), rounds of the last decode. */
 pp_status pp_batch_info(const pp_batch *b, uint32_t *n_tables, uint64_t *total_cells,
                         uint32_t *last_rounds);
@@ -504,6 +547,19 @@ pp_status pp_server_stop(pp_server *s, int drain);
 pp_status pp_iblt_decode_noalloc(pp_cell *d_cells, uint64_t n_cells, uint32_t r, uint64_t seed,
                                  uint64_t *d_out_keys, uint64_t out_cap, pp_decode_result *res,
                                  void *stream);
+
+/* ------------------------------------------------------------------------
+ * Measurement helper (no counterpart in the paper): the rate at which this GPU
+ * serves scattered whole-cell accesses, the access pattern of the IBLT rounds.
+ * For each i < m, cell d_idx[i] of d_cells (n_cells pp_cell records, 32-byte
+ * aligned, device) is read with one 256-bit load and written back changed
+ * (mode 0), only read (mode 1) or only overwritten (mode 2); indices >= n_cells
+ * are skipped.  The cells' contents are scratch afterwards.  Enqueued on
+ * `stream`; time it with events on that stream.  INVALID_ARG for NULL pointers,
+ * a mode outside 0..2 or misaligned cells.
+ * ------------------------------------------------------------------------ */
+pp_status pp_probe_scatter(pp_cell *d_cells, uint64_t n_cells, const uint32_t *d_idx, uint64_t m, int mode,
+                           void *stream);
 
 #ifdef __cplusplus
 }

@@ -60,6 +60,8 @@ _lib.declare("pp_batch_build", ctypes.c_int, [vp, vp, ctypes.POINTER(u64), vp])
 _lib.declare("pp_batch_decode", ctypes.c_int, [vp, vp, ctypes.POINTER(u64), ctypes.POINTER(TableResult), vp])
 _lib.declare("pp_batch_copy_cells", ctypes.c_int, [vp, u32, vp, ctypes.c_int, vp])
 _lib.declare("pp_batch_info", ctypes.c_int, [vp, ctypes.POINTER(u32), ctypes.POINTER(u64), ctypes.POINTER(u32)])
+_lib.declare("pp_batch_set_options", ctypes.c_int, [vp, ctypes.POINTER(Options)])
+_lib.declare("pp_batch_get_options", ctypes.c_int, [vp, ctypes.POINTER(Options)])
 
 
 @dataclass
@@ -148,6 +150,24 @@ class Batch:
             residual_cells=results["residual_cells"].astype(np.int64),
             recovered_per_round=PerRoundCounts(per_round, rounds),
             stats_complete=results["stats_complete"].astype(bool))
+
+    def set_options(self, opts: Options) -> None:
+        _check(_lib.load().pp_batch_set_options(self._h, ctypes.byref(opts)), "pp_batch_set_options")
+
+    def options(self) -> Options:
+        o = Options()
+        _check(_lib.load().pp_batch_get_options(self._h, ctypes.byref(o)), "pp_batch_get_options")
+        return o
+
+    @property
+    def handle(self):
+        return self._h
+
+    def total_cells(self) -> int:
+        n = u32()
+        c = u64()
+        _check(_lib.load().pp_batch_info(self._h, ctypes.byref(n), ctypes.byref(c), None), "pp_batch_info")
+        return int(c.value)
 
     def cells(self, table: int):
         out = np.zeros(self.n_cells[table], dtype=np.dtype(CELL_DTYPE))

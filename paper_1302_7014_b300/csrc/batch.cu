@@ -21,7 +21,6 @@ using namespace pp;
 
 namespace {
 
-constexpr u32 kInsertChunk = 4096;        // keys per insert work item
 constexpr u32 kScanChunk = kBlock * kScanItems;
 
 }  // namespace
@@ -174,7 +173,7 @@ pp_status ensure_round_bins(pp_batch *b, cudaStream_t s) {
   b->smem_claim = claim_smem_bytes(b->k.nr, true, nb);
   b->smem_apply_round = apply_round_smem_bytes(true, nb);
   b->grid_claim = persistent_grid(b->k.claim, kBlock, b->smem_claim, b->opt.ctas_per_sm);
-  b->grid_apply_round = persistent_grid(b->k.apply_round, kBlock, b->smem_apply_round, kApplyRoundCtas);
+  b->grid_apply_round = persistent_grid(b->k.apply_round, kBlock, b->smem_apply_round, b->opt.apply_ctas);
   return PP_OK;
 }
 
@@ -450,7 +449,7 @@ pp_status pp_batch_clear(pp_batch *b, void *stream) {
   return PP_OK;
 }
 
-// Uploads the insert work list (key ranges of at most kInsertChunk keys, one table each).
+// Uploads the insert work list (key ranges of at most opt.insert_chunk keys, one table each).
 static pp_status upload_chunks(pp_batch *b, const uint64_t *h_key_offsets, cudaStream_t s, u32 *n_chunks,
                                uint64_t *records) {
   std::vector<Chunk> chunks;
@@ -459,8 +458,9 @@ static pp_status upload_chunks(pp_batch *b, const uint64_t *h_key_offsets, cudaS
     const uint64_t k0 = h_key_offsets[i], k1 = h_key_offsets[i + 1];
     if (k1 < k0) return fail(PP_ERR_INVALID_ARG, "pp_batch_insert: key offsets decrease at table %u", i);
     if (k1 > 0xFFFFFFFFull) return fail(PP_ERR_INVALID_ARG, "pp_batch_insert: more than 2^32 keys");
-    for (uint64_t k = k0; k < k1; k += kInsertChunk)
-      chunks.push_back(Chunk{i, (u32)k, (u32)(k + kInsertChunk < k1 ? k + kInsertChunk : k1)});
+    const uint64_t ck = b->opt.insert_chunk;
+    for (uint64_t k = k0; k < k1; k += ck)
+      chunks.push_back(Chunk{i, (u32)k, (u32)(k + ck < k1 ? k + ck : k1)});
     rec += (k1 - k0) * b->h_tabs[i].r;
   }
   *n_chunks = (u32)chunks.size();
@@ -805,6 +805,31 @@ pp_status pp_batch_copy_cells(pp_batch *b, uint32_t table, void *dst, int to_hos
   PP_CUDA(cudaMemcpyAsync(dst, b->cells + t.base, (size_t)t.n_cells * sizeof(Cell),
                           to_host ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, s));
   PP_CUDA(cudaStreamSynchronize(s));
+  return PP_OK;
+}
+
+pp_status pp_batch_set_options(pp_batch *b, const pp_options *opt) {
+  if (!b) return fail(PP_ERR_INVALID_ARG, "pp_batch_set_options: NULL batch");
+  PP_CUDA(cudaDeviceSynchronize());
+  const pp_options old = b->opt;
+  b->opt = resolve_options(opt);
+  // the per-table statistics and round buffers were sized at creation
+  b->opt.max_rounds = old.max_rounds;
+  b->opt.stats_rounds = old.stats_rounds;
+  b->grid_scan = persistent_grid(b->k.scan, kBlock, 0, b->opt.ctas_per_sm);
+  b->grid_peel = persistent_grid(b->k.peel, kBlock, b->smem_peel, b->opt.ctas_per_sm);
+  b->grid_filter = persistent_grid(b->k.filter, kBlock, 0, b->opt.ctas_per_sm);
+  b->n_slabs = 0;  // the binning grid is recomputed on the next binned update
+  if (b->exec) {
+    cudaGraphExecDestroy(b->exec);
+    b->exec = nullptr;
+  }
+  return PP_OK;
+}
+
+pp_status pp_batch_get_options(const pp_batch *b, pp_options *opt) {
+  if (!b || !opt) return fail(PP_ERR_INVALID_ARG, "pp_batch_get_options: NULL argument");
+  *opt = b->opt;
   return PP_OK;
 }
 

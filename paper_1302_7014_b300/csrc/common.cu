@@ -50,6 +50,9 @@ pp_options resolve_options(const pp_options *opt) {
     o.binned = opt->binned;
     o.kcore_mode = opt->kcore_mode;
     o.rounds = opt->rounds;
+    if (opt->apply_ctas) o.apply_ctas = opt->apply_ctas;
+    if (opt->frontier_switch) o.frontier_switch = opt->frontier_switch;
+    if (opt->insert_chunk) o.insert_chunk = opt->insert_chunk;
   }
   return o;
 }
@@ -86,6 +89,9 @@ void pp_options_default(pp_options *opt) {
   opt->max_rounds = 65535;
   opt->host_loop = 0;
   opt->stats_rounds = 128;
+  opt->apply_ctas = 3;
+  opt->frontier_switch = 2;
+  opt->insert_chunk = 4096;
 }
 
 const char *pp_status_string(pp_status s) {

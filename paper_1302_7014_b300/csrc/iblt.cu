@@ -948,7 +948,7 @@ pp_status ensure_round_bins(pp_iblt *t, cudaStream_t s) {
   t->smem_claim = claim_smem_bytes(t->k.nr, false, nb);
   t->smem_apply_round = apply_round_smem_bytes(false, nb);
   t->grid_claim = persistent_grid(t->k.claim, kBlock, t->smem_claim, t->opt.ctas_per_sm);
-  t->grid_apply_round = persistent_grid(t->k.apply_round, kBlock, t->smem_apply_round, kApplyRoundCtas);
+  t->grid_apply_round = persistent_grid(t->k.apply_round, kBlock, t->smem_apply_round, t->opt.apply_ctas);
   return PP_OK;
 }
 

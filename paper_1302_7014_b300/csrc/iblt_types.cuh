@@ -114,16 +114,12 @@ struct BinArgs {
 #endif
 constexpr int kRoundShiftMin = PP_ROUND_SHIFT_MIN;  // bins hold at least 2^19 cells
 constexpr u32 kMaxRoundBins = 128;         // ... and there are at most this many
-// Records per thread per grab of k_apply_round, and its resident CTAs per SM
-// (together they set the width of the table window that is being updated).
+// Records per thread per grab of k_apply_round (with its resident CTAs per SM,
+// pp_options.apply_ctas, it sets the width of the table window being updated).
 #ifndef PP_APPLY_PER
 #define PP_APPLY_PER 8
 #endif
-#ifndef PP_APPLY_CTAS
-#define PP_APPLY_CTAS 3
-#endif
 constexpr int kApplyPer = PP_APPLY_PER;
-constexpr int kApplyRoundCtas = PP_APPLY_CTAS;
 constexpr int kApplyChunk = kBlock * kApplyPer;
 
 // Record lists of one round: bin b owns records [b*cap, b*cap + min(count[b], cap)).

@@ -45,13 +45,12 @@ namespace pp {
 
 constexpr int kKBlock = 256;
 constexpr int kKStage = 2048;  // staged pushes per CTA before spilling to global atomics
-// Edge-centric rounds run while the frontier holds at least 1 / kSwitchRatio
-// vertices per edge left: each such round removes a large share of the list.
-// Below that, a pass over every edge left costs more than the incidence lists
-// (their build included): measured at 2^25 vertices, r = 4, an edge-centric
-// round is latency-bound at about 0.7 TB/s on the list, four random bitmap
-// probes per edge.
-constexpr u32 kSwitchRatio = 2;
+// Edge-centric rounds run while the frontier holds at least 1 / frontier_switch
+// (pp_options, default 2) vertices per edge left: each such round removes a
+// large share of the list.  Below that, a pass over every edge left costs more
+// than the incidence lists (their build included): measured at 2^25 vertices,
+// r = 4, an edge-centric round is latency-bound at about 0.7 TB/s on the list,
+// four random bitmap probes per edge.
 
 struct PeelCtl {
   u64 claimed;  // edges removed in the current round
@@ -1471,7 +1470,7 @@ static pp_status peel_kcore_impl(uint32_t n, uint32_t r, uint32_t k, const uint3
         status = cuda_fail(e, "pp_peel_kcore frontier readback", __FILE__, __LINE__);
         goto cleanup;
       }
-      edge_mode = o.kcore_mode == 2 || (uint64_t)hc.n_next * kSwitchRatio >= m;
+      edge_mode = o.kcore_mode == 2 || (uint64_t)hc.n_next * o.frontier_switch >= m;
     }
     if (edge_mode) {
       for (int b = 0; b < 2 && e == cudaSuccess; ++b) {
@@ -1504,7 +1503,7 @@ static pp_status peel_kcore_impl(uint32_t n, uint32_t r, uint32_t k, const uint3
       EdgeLists L{d_edges, {w.rows[0], w.rows[1]}, {w.ids[0], w.ids[1]}, {w.fb[0], w.fb[1]}, {w.f0, w.f1}};
       KEdgeArgs ka{L, n, rdeg, d_vertex_round, d_edge_round, w.ctl, {}, {}};
       ka.bind();
-      KEEndArgs kea{w.ctl, PeelStats{w.st_s, w.st_m}, o.kcore_mode == 2 ? 0u : kSwitchRatio, 0, 0, {}};
+      KEEndArgs kea{w.ctl, PeelStats{w.st_s, w.st_m}, o.kcore_mode == 2 ? 0u : o.frontier_switch, 0, 0, {}};
       kea.bind();
       const void *er = pick_eround(rk, d16);
       const int pgrid = (int)std::min<uint64_t>((uint64_t)persistent_grid(er, kKBlock, 0, o.ctas_per_sm),

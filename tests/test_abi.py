@@ -44,7 +44,7 @@ def test_library_exports_every_declared_function(ppeel_lib):
 def test_binding_declares_what_the_header_declares(ppeel_lib):
     import importlib
     import importlib.util
-    for mod in ("paper_1302_7014_b300.batch", "paper_1302_7014_b300.server"):
+    for mod in ("paper_1302_7014_b300.batch", "paper_1302_7014_b300.server", "paper_1302_7014_b300.tune"):
         if importlib.util.find_spec(mod) is not None:
             importlib.import_module(mod)   # declares its entry points
     from paper_1302_7014_b300 import _lib
