@@ -208,6 +208,37 @@ pp_status pp_iblt_build(pp_iblt *t, const uint64_t *d_keys, uint64_t m, void *st
 pp_status pp_iblt_decode(pp_iblt *t, uint64_t *d_out_keys, uint64_t out_cap,
                          pp_decode_result *res, void *stream);
 
+/* Build and decode from HOST buffers (Sec. 6: insert the keys, then recover
+ * them), with the host<->device copies inside the call: the paper's GPU insert
+ * times include the upload of the items.
+ *   pp_iblt_submit_host  enqueues, for the m keys at h_keys: their upload (on
+ *                        an upload stream the table owns), the build of
+ *                        pp_iblt_build, the decode of pp_iblt_decode, and the
+ *                        download of the recovered keys into h_out (on a
+ *                        download stream; out_cap >= m, else CAPACITY), then
+ *                        returns a ticket without waiting for the GPU.
+ *   pp_iblt_finish_host  waits for that job and fills *res as pp_iblt_decode
+ *                        does (per-round figures for at most the first 4096
+ *                        rounds); h_out[0 .. res->recovered) hold the keys,
+ *                        grouped by round.
+ * At most three jobs are in flight per table (INVALID_ARG for a fourth): jobs
+ * upload while earlier ones decode and download while later ones build and
+ * decode; each has its own device buffers (2 m keys, kept for reuse).  Should
+ * a slab of a job's build overflow its list (keys crowding one slab far beyond
+ * the uniform share), pp_iblt_finish_host rebuilds and decodes that job again,
+ * synchronously, before returning.
+ * h_keys and h_out stay in use until the job is finished; pinned memory
+ * (cudaMallocHost / cudaHostRegister) is copied directly, pageable memory is
+ * registered for the job's duration, which costs time.  One cudaMemcpyAsync
+ * per copy.  The job's table is decoded in place, as by pp_iblt_decode. */
+pp_status pp_iblt_submit_host(pp_iblt *t, const uint64_t *h_keys, uint64_t m, uint64_t *h_out, uint64_t out_cap,
+                              uint64_t *ticket, void *stream);
+pp_status pp_iblt_finish_host(pp_iblt *t, uint64_t ticket, pp_decode_result *res);
+
+/* pp_iblt_submit_host + pp_iblt_finish_host of one job. */
+pp_status pp_iblt_build_decode_host(pp_iblt *t, const uint64_t *h_keys, uint64_t m, uint64_t *h_out,
+                                    uint64_t out_cap, pp_decode_result *res, void *stream);
+
 /* Recovery with sub-tables, the order of the paper's GPU implementation
  * (Sec. 6 "Implementation Details"; analysed in App. B): every round visits
  * the r sub-tables in order, and the sub-round of sub-table j recovers the key

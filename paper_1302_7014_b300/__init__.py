@@ -171,6 +171,36 @@ class IBLT:
         return self._decode(lambda h, o, cap, res, st: _lib.load().pp_iblt_decode_signed(h, o, sp, cap, res, st),
                             "pp_iblt_decode_signed", out, round_cap, stream)
 
+    def submit_host(self, keys, out, stream=None) -> int:
+        """Build from the host array ``keys`` (uint64) and decode, the recovered
+        keys landing in the host array ``out``; returns a ticket for
+        finish_host.  Both arrays must stay alive until then (pinned memory,
+        e.g. a torch tensor made with pin_memory=True, is copied directly)."""
+        import numpy as np
+        keys = np.asarray(keys)
+        out = np.asarray(out)
+        if keys.dtype.itemsize != 8 or out.dtype.itemsize != 8 or not keys.flags.c_contiguous \
+                or not out.flags.c_contiguous:
+            raise ValueError("keys and out must be contiguous arrays of 8-byte elements")
+        t = ctypes.c_uint64()
+        _check(_lib.load().pp_iblt_submit_host(self._h, ctypes.c_void_p(keys.ctypes.data), keys.size,
+                                               ctypes.c_void_p(out.ctypes.data), out.size, ctypes.byref(t),
+                                               _stream_ptr(stream)), "pp_iblt_submit_host")
+        self._host_jobs = getattr(self, "_host_jobs", {})
+        self._host_jobs[t.value] = (keys, out)
+        return t.value
+
+    def finish_host(self, ticket: int, round_cap: int = 4096) -> DecodeOutcome:
+        """Waits for a submit_host job; its outcome as decode() returns it."""
+        try:
+            return self._decode(lambda h, o, cap, res, st: _lib.load().pp_iblt_finish_host(h, ticket, res),
+                                "pp_iblt_finish_host", None, round_cap, None)
+        finally:
+            getattr(self, "_host_jobs", {}).pop(ticket, None)
+
+    def build_decode_host(self, keys, out, round_cap: int = 4096, stream=None) -> DecodeOutcome:
+        return self.finish_host(self.submit_host(keys, out, stream), round_cap)
+
     def _decode(self, fn, name, out, round_cap, stream) -> DecodeOutcome:
         import numpy as np
         stats = np.empty((3, round_cap), dtype=np.uint64)  # filled up to the round count

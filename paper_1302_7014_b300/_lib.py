@@ -69,6 +69,9 @@ _SIGNATURES = {
     "pp_iblt_decode_noalloc": (ctypes.c_int, [vp, u64, u32, u64, vp, u64,
                                               ctypes.POINTER(DecodeResult), vp]),
     "pp_probe_scatter": (ctypes.c_int, [vp, u64, vp, u64, ctypes.c_int, vp]),
+    "pp_iblt_submit_host": (ctypes.c_int, [vp, vp, u64, vp, u64, ctypes.POINTER(u64), vp]),
+    "pp_iblt_finish_host": (ctypes.c_int, [vp, u64, ctypes.POINTER(DecodeResult)]),
+    "pp_iblt_build_decode_host": (ctypes.c_int, [vp, vp, u64, vp, u64, ctypes.POINTER(DecodeResult), vp]),
 }
 
 PP_NOALLOC_MAX_CELLS = 1 << 20

@@ -111,6 +111,32 @@ size_t peel_smem_bytes(int nr, bool batch) {
 
 }  // namespace pp
 
+namespace pp {
+
+// One build + decode from host buffers in flight (pp_iblt_submit_host): its
+// own device key and output buffers, pinned copies of the decode's control
+// block and statistics, and the events that order the copies around it.
+constexpr uint32_t kJobStatRounds = 4096;  // per-round statistics kept per job
+constexpr uint32_t kHostJobs = 3;          // jobs in flight per table
+struct HostJob {
+  u64 *d_keys = nullptr, *d_out = nullptr;
+  uint64_t cap = 0;                    // keys the device buffers hold
+  DecodeCtl *h_ctl = nullptr;          // mapped pinned (d_ctl: its device address)
+  u64 *h_stats = nullptr;              // mapped pinned: recovered, then alive, kJobStatRounds each
+  u32 *h_flag = nullptr;               // mapped pinned: the build's slab overflow flag
+  DecodeCtl *d_ctl = nullptr;
+  u64 *d_stats = nullptr;
+  u32 *d_flag = nullptr;
+  cudaStream_t s = nullptr;            // the caller's stream the job ran on
+  cudaEvent_t up = nullptr, built = nullptr, dec = nullptr, done = nullptr;
+  const uint64_t *h_keys = nullptr;
+  uint64_t *h_out = nullptr;
+  uint64_t m = 0, out_cap = 0, ticket = 0;
+  bool busy = false, reg_keys = false, reg_out = false;
+};
+
+}  // namespace pp
+
 struct pp_iblt {
   uint64_t n = 0;
   uint32_t r = 0;
@@ -163,6 +189,11 @@ struct pp_iblt {
   bool has_deletes = false;   // a deletion since the last clear/build: no tile rounds
   int grid_tscan = 0, grid_tclaim = 0, grid_tapply = 0, grid_tsparse = 0;
   uint64_t front_cap = 0;     // entries of fkey / fcell
+  // host-buffer jobs: at most two in flight
+  HostJob jobs[kHostJobs];
+  cudaStream_t up_s = nullptr, down_s = nullptr;  // uploads and downloads: one copy engine each
+  u32 *h_flag = nullptr, *d_flag = nullptr;       // mapped pinned word: the build's overflow flag
+  uint64_t next_ticket = 1;
   bool sg_graph_built = false;
   bool sg_graph_binned = false;         // the graph's round kind
   uint32_t sg_graph_gen = 0;            // rec_gen the binned graph was built with
@@ -198,6 +229,22 @@ void free_all(pp_iblt *t) {
   cudaFree(t->bin_count);
   cudaFree(t->bin_overflow);
   free_tiles(t->tiles);
+  for (HostJob &j : t->jobs) {
+    cudaFree(j.d_keys);
+    cudaFree(j.d_out);
+    cudaFreeHost(j.h_ctl);
+    cudaFreeHost(j.h_stats);
+    cudaFreeHost(j.h_flag);
+    if (j.built) cudaEventDestroy(j.built);
+    if (j.up) cudaEventDestroy(j.up);
+    if (j.dec) cudaEventDestroy(j.dec);
+    if (j.done) cudaEventDestroy(j.done);
+    if (j.reg_keys) cudaHostUnregister(const_cast<uint64_t *>(j.h_keys));
+    if (j.reg_out) cudaHostUnregister(j.h_out);
+  }
+  cudaFreeHost(t->h_flag);
+  if (t->up_s) cudaStreamDestroy(t->up_s);
+  if (t->down_s) cudaStreamDestroy(t->down_s);
   cudaFree(t->trb.rec_key);
   cudaFree(t->trb.rec_off);
   cudaFree(t->trb.base);
@@ -969,6 +1016,85 @@ pp_status update(pp_iblt *t, const uint64_t *d_keys, uint64_t m, int sign, cudaS
 
 }  // namespace
 
+namespace {
+
+// Enqueues a whole decode on s (control block set up, round loop launched);
+// nothing is read back.
+pp_status decode_enqueue(pp_iblt *t, uint64_t *d_out_keys, uint64_t out_cap, cudaStream_t s) {
+  memset(t->h_ctl, 0, sizeof(DecodeCtl));
+  t->h_ctl->out = reinterpret_cast<u64 *>(d_out_keys);
+  t->h_ctl->out_cap = out_cap;
+  t->h_ctl->max_rounds = t->opt.max_rounds;
+  // round kind: tile rounds (large tables built from insertions only), binned
+  // atomic rounds (other large tables), direct atomics (small tables)
+  const bool large = t->n >= (1ull << 21);
+  const bool want_tiles = t->k.tscan && !t->has_deletes &&
+                          (t->opt.rounds == 2 || (t->opt.rounds == 0 && large && t->opt.binned != 2));
+  const bool want_bins = !want_tiles && (t->opt.binned == 1 || (t->opt.binned == 0 && large));
+  if (want_tiles) {
+    pp_status st = ensure_tile_rounds(t, s);
+    if (st != PP_OK) return st;
+  }
+  if (want_bins) {
+    pp_status st = ensure_round_bins(t, s);
+    if (st != PP_OK) return st;
+    PP_CUDA(cudaMemsetAsync(t->bin_count, 0, t->n_bins * sizeof(u32), s));
+  }
+  // the graph holds buffer pointers: rebuild it when they moved or the round kind changed
+  if (t->exec && (want_bins != t->binned_rounds || want_tiles != t->tile_rounds ||
+                  ((want_bins || want_tiles) && t->graph_gen != t->rec_gen))) {
+    cudaGraphExecDestroy(t->exec);
+    t->exec = nullptr;
+  }
+  t->binned_rounds = want_bins;
+  t->tile_rounds = want_tiles;
+  k_ctl_init<<<1, 32, 0, s>>>(t->ctl, *t->h_ctl);
+  PP_CUDA(cudaGetLastError());
+  if (t->opt.host_loop) {
+    pp_status st = want_tiles ? run_tile_host_loop(t, s) : run_host_loop(t, s);
+    if (st != PP_OK) return st;
+  } else {
+    if (!t->exec) {
+      pp_status st = want_tiles ? build_tile_graph(t) : build_graph(t);
+      if (st != PP_OK) return st;
+    }
+    PP_CUDA(cudaGraphLaunch(t->exec, s));
+  }
+  return PP_OK;
+}
+
+// Fills *res from the control block c after a decode and the first ncopy
+// per-round statistics.
+pp_status decode_collect(const DecodeCtl &c, const u64 *h_rec, const u64 *h_alive, uint32_t ncopy,
+                         uint64_t items, uint64_t out_cap, pp_decode_result *res, uint32_t max_rounds,
+                         const char *fn) {
+  const uint32_t T = c.round;
+  ncopy = ncopy < T ? ncopy : T;
+  ncopy = ncopy < res->round_cap ? ncopy : res->round_cap;
+  uint64_t left = items;
+  for (uint32_t i = 0; i < ncopy; ++i) {
+    left -= h_rec[i] <= left ? h_rec[i] : left;
+    if (res->recovered_per_round) res->recovered_per_round[i] = h_rec[i];
+    if (res->remaining_per_round) res->remaining_per_round[i] = left;
+    if (res->alive_cells_per_round) res->alive_cells_per_round[i] = h_alive[i];
+  }
+  res->rounds = T;
+  res->status_flags = c.flags;
+  res->recovered = c.n_out < out_cap ? c.n_out : out_cap;
+  res->items_before = items;
+  res->residual_cells = c.nonempty - c.emptied;
+  if (c.flags & FLAG_CAPACITY)
+    return fail(PP_ERR_CAPACITY, "%s: more keys recovered than out_cap=%llu", fn, (unsigned long long)out_cap);
+  if (c.flags & FLAG_INTERNAL)
+    return fail(PP_ERR_INVALID_ARG,
+                "%s: a pure cell's key does not hash to it, or the table holds a negative count", fn);
+  if (c.flags & FLAG_ROUND_LIMIT)
+    return fail(PP_ERR_ROUND_LIMIT, "%s: stopped after max_rounds=%u rounds", fn, max_rounds);
+  return PP_OK;
+}
+
+}  // namespace
+
 extern "C" {
 
 pp_status pp_iblt_create(pp_iblt **out, uint64_t n_cells, uint32_t r, uint64_t seed,
@@ -1116,9 +1242,16 @@ pp_status pp_iblt_build(pp_iblt *t, const uint64_t *d_keys, uint64_t m, void *st
   BinArgs ba;
   pp_status st = bin_pass(t, d_keys, m, +1, 0, s, ba);
   if (st != PP_OK) return st;
-  PP_CUDA(cudaMemcpyAsync(&t->h_ctl->more, t->bin_overflow, sizeof(u32), cudaMemcpyDeviceToHost, s));
+  // the flag comes back through mapped memory, not a copy engine that may be
+  // busy with another stream's bulk copy
+  if (!t->h_flag) {
+    PP_CUDA(cudaHostAlloc((void **)&t->h_flag, sizeof(u32), cudaHostAllocMapped | cudaHostAllocPortable));
+    PP_CUDA(cudaHostGetDevicePointer((void **)&t->d_flag, t->h_flag, 0));
+  }
+  k_flag_to_host<<<1, 32, 0, s>>>(t->bin_overflow, t->d_flag);
+  PP_CUDA(cudaGetLastError());
   PP_CUDA(cudaStreamSynchronize(s));
-  if (t->h_ctl->more) {
+  if (*(volatile u32 *)t->h_flag) {
     // a slab got more updates than its list holds: build the plain way
     PP_CUDA(cudaMemsetAsync(t->cells, 0, t->n * sizeof(Cell), s));
     st = launch_insert(t, d_keys, m, +1, s);
@@ -1138,45 +1271,8 @@ pp_status pp_iblt_decode(pp_iblt *t, uint64_t *d_out_keys, uint64_t out_cap, pp_
                 (unsigned long long)out_cap, (unsigned long long)items);
   if (out_cap && !d_out_keys) return fail(PP_ERR_INVALID_ARG, "pp_iblt_decode: NULL output");
   cudaStream_t s = as_stream(stream);
-  memset(t->h_ctl, 0, sizeof(DecodeCtl));
-  t->h_ctl->out = reinterpret_cast<u64 *>(d_out_keys);
-  t->h_ctl->out_cap = out_cap;
-  t->h_ctl->max_rounds = t->opt.max_rounds;
-  // round kind: tile rounds (large tables built from insertions only), binned
-  // atomic rounds (other large tables), direct atomics (small tables)
-  const bool large = t->n >= (1ull << 21);
-  const bool want_tiles = t->k.tscan && !t->has_deletes &&
-                          (t->opt.rounds == 2 || (t->opt.rounds == 0 && large && t->opt.binned != 2));
-  const bool want_bins = !want_tiles && (t->opt.binned == 1 || (t->opt.binned == 0 && large));
-  if (want_tiles) {
-    pp_status st = ensure_tile_rounds(t, s);
-    if (st != PP_OK) return st;
-  }
-  if (want_bins) {
-    pp_status st = ensure_round_bins(t, s);
-    if (st != PP_OK) return st;
-    PP_CUDA(cudaMemsetAsync(t->bin_count, 0, t->n_bins * sizeof(u32), s));
-  }
-  // the graph holds buffer pointers: rebuild it when they moved or the round kind changed
-  if (t->exec && (want_bins != t->binned_rounds || want_tiles != t->tile_rounds ||
-                  ((want_bins || want_tiles) && t->graph_gen != t->rec_gen))) {
-    cudaGraphExecDestroy(t->exec);
-    t->exec = nullptr;
-  }
-  t->binned_rounds = want_bins;
-  t->tile_rounds = want_tiles;
-  k_ctl_init<<<1, 32, 0, s>>>(t->ctl, *t->h_ctl);
-  PP_CUDA(cudaGetLastError());
-  if (t->opt.host_loop) {
-    pp_status st = want_tiles ? run_tile_host_loop(t, s) : run_host_loop(t, s);
-    if (st != PP_OK) return st;
-  } else {
-    if (!t->exec) {
-      pp_status st = want_tiles ? build_tile_graph(t) : build_graph(t);
-      if (st != PP_OK) return st;
-    }
-    PP_CUDA(cudaGraphLaunch(t->exec, s));
-  }
+  pp_status st = decode_enqueue(t, d_out_keys, out_cap, s);
+  if (st != PP_OK) return st;
   PP_CUDA(cudaMemcpyAsync(t->h_ctl, t->ctl, sizeof(DecodeCtl), cudaMemcpyDeviceToHost, s));
   PP_CUDA(cudaStreamSynchronize(s));
   const DecodeCtl c = *t->h_ctl;
@@ -1186,30 +1282,10 @@ pp_status pp_iblt_decode(pp_iblt *t, uint64_t *d_out_keys, uint64_t out_cap, pp_
     PP_CUDA(cudaMemcpyAsync(t->h_rec, t->st_rec, ncopy * sizeof(u64), cudaMemcpyDeviceToHost, s));
     PP_CUDA(cudaMemcpyAsync(t->h_alive, t->st_alive, ncopy * sizeof(u64), cudaMemcpyDeviceToHost, s));
     PP_CUDA(cudaStreamSynchronize(s));
-    uint64_t left = items;
-    for (uint32_t i = 0; i < ncopy; ++i) {
-      left -= t->h_rec[i] <= left ? t->h_rec[i] : left;
-      if (res->recovered_per_round) res->recovered_per_round[i] = t->h_rec[i];
-      if (res->remaining_per_round) res->remaining_per_round[i] = left;
-      if (res->alive_cells_per_round) res->alive_cells_per_round[i] = t->h_alive[i];
-    }
   }
-  res->rounds = T;
-  res->status_flags = c.flags;
-  res->recovered = c.n_out < out_cap ? c.n_out : out_cap;
-  res->items_before = items;
-  res->residual_cells = c.nonempty - c.emptied;
+  st = decode_collect(c, t->h_rec, t->h_alive, ncopy, items, out_cap, res, t->opt.max_rounds, "pp_iblt_decode");
   t->items -= (int64_t)res->recovered;
-  if (c.flags & FLAG_CAPACITY)
-    return fail(PP_ERR_CAPACITY, "pp_iblt_decode: more keys recovered than out_cap=%llu",
-                (unsigned long long)out_cap);
-  if (c.flags & FLAG_INTERNAL)
-    return fail(PP_ERR_INVALID_ARG,
-                "pp_iblt_decode: a pure cell's key does not hash to it, or the table holds a negative count");
-  if (c.flags & FLAG_ROUND_LIMIT)
-    return fail(PP_ERR_ROUND_LIMIT, "pp_iblt_decode: stopped after max_rounds=%u rounds",
-                t->opt.max_rounds);
-  return PP_OK;
+  return st;
 }
 
 pp_status pp_iblt_decode_subrounds(pp_iblt *t, uint64_t *d_out_keys, uint64_t out_cap,
@@ -1450,6 +1526,186 @@ pp_status pp_iblt_decode_signed(pp_iblt *t, uint64_t *d_out_keys, int8_t *d_out_
     return fail(PP_ERR_ROUND_LIMIT, "pp_iblt_decode_signed: stopped after max_rounds=%u rounds",
                 t->opt.max_rounds);
   return PP_OK;
+}
+
+// ---- build + decode from host buffers -------------------------------------
+namespace {
+
+// Pins a host range for the job unless it is pinned already.
+pp_status pin_host(void *p, size_t bytes, bool *registered) {
+  *registered = false;
+  if (!p || !bytes) return PP_OK;
+  cudaPointerAttributes a{};
+  if (cudaPointerGetAttributes(&a, p) == cudaSuccess && a.type == cudaMemoryTypeHost) return PP_OK;
+  cudaGetLastError();  // a pageable pointer may leave an error behind
+  PP_CUDA(cudaHostRegister(p, bytes, cudaHostRegisterDefault));
+  *registered = true;
+  return PP_OK;
+}
+
+// pp_iblt_build without its flag check: the slab-binned build is enqueued as
+// if no slab list overflowed (*binned tells whether the flag is meaningful).
+pp_status build_enqueue(pp_iblt *t, const uint64_t *d_keys, uint64_t m, cudaStream_t s, bool *binned) {
+  t->items = 0;
+  t->has_deletes = false;
+  *binned = use_binned(t, m);
+  pp_status st;
+  if (!*binned) {
+    PP_CUDA(cudaMemsetAsync(t->cells, 0, t->n * sizeof(Cell), s));
+    st = launch_insert(t, d_keys, m, +1, s);
+  } else {
+    BinArgs ba;
+    st = bin_pass(t, d_keys, m, +1, 0, s, ba);
+    if (st == PP_OK) st = apply_pass(t, ba, +1, true, s);
+  }
+  if (st == PP_OK) t->items = (int64_t)m;
+  return st;
+}
+
+}  // namespace
+
+pp_status pp_iblt_submit_host(pp_iblt *t, const uint64_t *h_keys, uint64_t m, uint64_t *h_out, uint64_t out_cap,
+                              uint64_t *ticket, void *stream) {
+  if (!t || !ticket) return fail(PP_ERR_INVALID_ARG, "pp_iblt_submit_host: NULL table or ticket");
+  if (m && (!h_keys || !h_out)) return fail(PP_ERR_INVALID_ARG, "pp_iblt_submit_host: NULL keys or output");
+  if (out_cap < m)
+    return fail(PP_ERR_CAPACITY, "pp_iblt_submit_host: out_cap=%llu < %llu keys", (unsigned long long)out_cap,
+                (unsigned long long)m);
+  HostJob &j = t->jobs[t->next_ticket % kHostJobs];
+  if (j.busy)
+    return fail(PP_ERR_INVALID_ARG, "pp_iblt_submit_host: %u jobs in flight; finish one first", kHostJobs);
+  cudaStream_t s = as_stream(stream);
+  if (!t->up_s) PP_CUDA(cudaStreamCreateWithFlags(&t->up_s, cudaStreamNonBlocking));
+  if (!t->down_s) PP_CUDA(cudaStreamCreateWithFlags(&t->down_s, cudaStreamNonBlocking));
+  if (!j.up) {
+    PP_CUDA(cudaEventCreateWithFlags(&j.up, cudaEventDisableTiming));
+    PP_CUDA(cudaEventCreateWithFlags(&j.built, cudaEventDisableTiming));
+    PP_CUDA(cudaEventCreateWithFlags(&j.dec, cudaEventDisableTiming));
+    PP_CUDA(cudaEventCreateWithFlags(&j.done, cudaEventDisableTiming));
+    const unsigned fl = cudaHostAllocMapped | cudaHostAllocPortable;
+    PP_CUDA(cudaHostAlloc((void **)&j.h_ctl, sizeof(DecodeCtl), fl));
+    PP_CUDA(cudaHostAlloc((void **)&j.h_stats, 2 * (size_t)kJobStatRounds * sizeof(u64), fl));
+    PP_CUDA(cudaHostAlloc((void **)&j.h_flag, sizeof(u32), fl));
+    PP_CUDA(cudaHostGetDevicePointer((void **)&j.d_ctl, j.h_ctl, 0));
+    PP_CUDA(cudaHostGetDevicePointer((void **)&j.d_stats, j.h_stats, 0));
+    PP_CUDA(cudaHostGetDevicePointer((void **)&j.d_flag, j.h_flag, 0));
+  }
+  if (m > j.cap) {
+    PP_CUDA(cudaEventSynchronize(j.done));
+    cudaFree(j.d_keys);
+    cudaFree(j.d_out);
+    j.d_keys = j.d_out = nullptr;
+    j.cap = 0;
+    PP_CUDA(cudaMalloc((void **)&j.d_keys, m * sizeof(u64)));
+    PP_CUDA(cudaMalloc((void **)&j.d_out, m * sizeof(u64)));
+    j.cap = m;
+  }
+  pp_status st = pin_host(const_cast<uint64_t *>(h_keys), m * sizeof(u64), &j.reg_keys);
+  if (st == PP_OK) st = pin_host(h_out, m * sizeof(u64), &j.reg_out);
+  if (st != PP_OK) {
+    if (j.reg_keys) cudaHostUnregister(const_cast<uint64_t *>(h_keys));
+    j.reg_keys = false;
+    return st;
+  }
+  j.h_keys = h_keys;
+  j.h_out = h_out;
+  j.m = m;
+  j.out_cap = out_cap;
+  j.s = s;
+  *j.h_flag = 0;
+  // Three streams: uploads, the caller's (build and decode), downloads.  The
+  // upload into this slot waits only for the slot's previous build (its reader),
+  // the decode into the slot's output only for the slot's previous download.
+  PP_CUDA(cudaStreamWaitEvent(t->up_s, j.built, 0));
+  if (m) PP_CUDA(cudaMemcpyAsync(j.d_keys, h_keys, m * sizeof(u64), cudaMemcpyHostToDevice, t->up_s));
+  PP_CUDA(cudaEventRecord(j.up, t->up_s));
+  PP_CUDA(cudaStreamWaitEvent(s, j.up, 0));
+  // The build is enqueued without waiting for its slab-overflow flag: the flag
+  // travels with the job, and pp_iblt_finish_host redoes the job in the rare
+  // case it is set.
+  bool binned = false;
+  st = build_enqueue(t, reinterpret_cast<const uint64_t *>(j.d_keys), m, s, &binned);
+  if (st == PP_OK && binned) {
+    k_flag_to_host<<<1, 32, 0, s>>>(t->bin_overflow, j.d_flag);
+    if (cudaGetLastError() != cudaSuccess) st = fail(PP_ERR_CUDA, "pp_iblt_submit_host: flag copy launch failed");
+  }
+  if (st == PP_OK && cudaEventRecord(j.built, s) != cudaSuccess) st = fail(PP_ERR_CUDA, "event record failed");
+  if (st == PP_OK && cudaStreamWaitEvent(s, j.done, 0) != cudaSuccess) st = fail(PP_ERR_CUDA, "event wait failed");
+  if (st == PP_OK) st = decode_enqueue(t, reinterpret_cast<uint64_t *>(j.d_out), m, s);
+  if (st != PP_OK) {
+    cudaStreamSynchronize(t->up_s);
+    if (j.reg_keys) cudaHostUnregister(const_cast<uint64_t *>(h_keys));
+    if (j.reg_out) cudaHostUnregister(h_out);
+    j.reg_keys = j.reg_out = false;
+    return st;
+  }
+  const uint32_t ns = t->opt.max_rounds < kJobStatRounds ? t->opt.max_rounds : kJobStatRounds;
+  // the decode's results reach the host through mapped memory, never queued
+  // behind another job's download on a copy engine
+  k_to_host<<<1, 128, 0, s>>>(reinterpret_cast<const u64 *>(t->ctl), reinterpret_cast<u64 *>(j.d_ctl),
+                              (u32)(sizeof(DecodeCtl) / sizeof(u64)));
+  k_to_host<<<8, 256, 0, s>>>(t->st_rec, j.d_stats, ns);
+  k_to_host<<<8, 256, 0, s>>>(t->st_alive, j.d_stats + kJobStatRounds, ns);
+  PP_CUDA(cudaGetLastError());
+  PP_CUDA(cudaEventRecord(j.dec, s));
+  // download every slot a recovered key may use
+  PP_CUDA(cudaStreamWaitEvent(t->down_s, j.dec, 0));
+  if (m) PP_CUDA(cudaMemcpyAsync(h_out, j.d_out, m * sizeof(u64), cudaMemcpyDeviceToHost, t->down_s));
+  PP_CUDA(cudaEventRecord(j.done, t->down_s));
+  j.ticket = t->next_ticket++;
+  j.busy = true;
+  *ticket = j.ticket;
+  return PP_OK;
+}
+
+pp_status pp_iblt_finish_host(pp_iblt *t, uint64_t ticket, pp_decode_result *res) {
+  if (!t || !res) return fail(PP_ERR_INVALID_ARG, "pp_iblt_finish_host: NULL table or result");
+  HostJob *j = nullptr;
+  for (HostJob &x : t->jobs)
+    if (x.busy && x.ticket == ticket) j = &x;
+  if (!j) return fail(PP_ERR_INVALID_ARG, "pp_iblt_finish_host: no job with ticket %llu in flight",
+                      (unsigned long long)ticket);
+  cudaError_t e = cudaEventSynchronize(j->done);
+  pp_status st = PP_OK;
+  if (e == cudaSuccess && *(volatile u32 *)j->h_flag) {
+    // a slab of the build got more updates than its list holds: the job's
+    // table was incomplete.  Redo it on its stream (after any later job's
+    // work there), with the build that checks the flag, then copy its keys.
+    const uint64_t *dk = reinterpret_cast<const uint64_t *>(j->d_keys);
+    st = pp_iblt_build(t, dk, j->m, j->s);
+    if (st == PP_OK) st = decode_enqueue(t, reinterpret_cast<uint64_t *>(j->d_out), j->m, j->s);
+    if (st == PP_OK) {
+      const uint32_t ns = t->opt.max_rounds < kJobStatRounds ? t->opt.max_rounds : kJobStatRounds;
+      k_to_host<<<1, 128, 0, j->s>>>(reinterpret_cast<const u64 *>(t->ctl), reinterpret_cast<u64 *>(j->d_ctl),
+                                     (u32)(sizeof(DecodeCtl) / sizeof(u64)));
+      k_to_host<<<8, 256, 0, j->s>>>(t->st_rec, j->d_stats, ns);
+      k_to_host<<<8, 256, 0, j->s>>>(t->st_alive, j->d_stats + kJobStatRounds, ns);
+      e = cudaGetLastError();
+      if (e == cudaSuccess && j->m)
+        e = cudaMemcpyAsync(j->h_out, j->d_out, j->m * sizeof(u64), cudaMemcpyDeviceToHost, j->s);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(j->s);
+    }
+  }
+  if (j->reg_keys) cudaHostUnregister(const_cast<uint64_t *>(j->h_keys));
+  if (j->reg_out) cudaHostUnregister(j->h_out);
+  j->reg_keys = j->reg_out = false;
+  j->busy = false;
+  if (st != PP_OK) return st;
+  if (e != cudaSuccess) return cuda_fail(e, "pp_iblt_finish_host", __FILE__, __LINE__);
+  const uint32_t ns = t->opt.max_rounds < kJobStatRounds ? t->opt.max_rounds : kJobStatRounds;
+  st = decode_collect(*j->h_ctl, j->h_stats, j->h_stats + kJobStatRounds, ns, j->m, j->m, res,
+                      t->opt.max_rounds, "pp_iblt_finish_host");
+  if (j->ticket + 1 == t->next_ticket) t->items = (int64_t)j->m - (int64_t)res->recovered;  // the latest build
+  return st;
+}
+
+pp_status pp_iblt_build_decode_host(pp_iblt *t, const uint64_t *h_keys, uint64_t m, uint64_t *h_out,
+                                    uint64_t out_cap, pp_decode_result *res, void *stream) {
+  if (!res) return fail(PP_ERR_INVALID_ARG, "pp_iblt_build_decode_host: NULL result");
+  uint64_t ticket = 0;
+  pp_status st = pp_iblt_submit_host(t, h_keys, m, h_out, out_cap, &ticket, stream);
+  if (st != PP_OK) return st;
+  return pp_iblt_finish_host(t, ticket, res);
 }
 
 pp_status pp_iblt_copy_cells(pp_iblt *t, void *dst, uint64_t first, uint64_t count, int to_host,

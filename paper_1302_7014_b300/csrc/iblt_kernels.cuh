@@ -381,6 +381,19 @@ __global__ void k_ctl_init(DecodeCtl *__restrict__ ctl, DecodeCtl init) {
   if (threadIdx.x == 0 && blockIdx.x == 0) *ctl = init;
 }
 
+// Copies n words into mapped pinned host memory with stores from the GPU, so
+// that a small result reaches the host without a copy engine (where it would
+// queue behind any bulk copy that engine is running).
+__global__ void k_to_host(const u64 *__restrict__ src, u64 *__restrict__ dst, u32 n) {
+  for (u32 i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) dst[i] = src[i];
+  __threadfence_system();
+}
+
+__global__ void k_flag_to_host(const u32 *__restrict__ src, u32 *__restrict__ dst) {
+  if (threadIdx.x == 0) *dst = *src;
+  __threadfence_system();
+}
+
 __global__ void k_round_end(DecodeCtl *__restrict__ ctl, RoundStats st, int set_cond,
                             cudaGraphConditionalHandle cond) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
