@@ -23,7 +23,7 @@ u32, u64, i32, vp = ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int32, ctypes.c_v
 class Options(ctypes.Structure):
     _fields_ = [("block", u32), ("ctas_per_sm", u32), ("max_rounds", u32), ("host_loop", u32),
                 ("stats_rounds", u32), ("binned", u32), ("kcore_mode", u32), ("rounds", u32), ("apply_ctas", u32),
-                ("frontier_switch", u32), ("insert_chunk", u32), ("reserved", u32)]
+                ("frontier_switch", u32), ("insert_chunk", u32), ("l2_fetch", u32)]
 
 
 class DecodeResult(ctypes.Structure):

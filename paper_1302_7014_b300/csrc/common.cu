@@ -53,6 +53,7 @@ pp_options resolve_options(const pp_options *opt) {
     if (opt->apply_ctas) o.apply_ctas = opt->apply_ctas;
     if (opt->frontier_switch) o.frontier_switch = opt->frontier_switch;
     if (opt->insert_chunk) o.insert_chunk = opt->insert_chunk;
+    if (opt->l2_fetch) o.l2_fetch = opt->l2_fetch;
   }
   return o;
 }
@@ -92,6 +93,7 @@ void pp_options_default(pp_options *opt) {
   opt->apply_ctas = 3;
   opt->frontier_switch = 2;
   opt->insert_chunk = 4096;
+  opt->l2_fetch = 1;
 }
 
 const char *pp_status_string(pp_status s) {

@@ -64,6 +64,8 @@ static IbltKernels iblt_kernels_t() {
     if (!tattr) {
       cudaFuncSetAttribute((const void *)k_tapply<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)kTApplySmem);
+      cudaFuncSetAttribute((const void *)k_tclaim<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+      cudaFuncSetAttribute((const void *)k_tsort, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
       tattr = true;
     }
   }
@@ -187,7 +189,8 @@ struct pp_iblt {
   TileRoundBufs trb{};
   bool tile_rounds = false;   // the round kind the graph was built with
   bool has_deletes = false;   // a deletion since the last clear/build: no tile rounds
-  int grid_tscan = 0, grid_tclaim = 0, grid_tapply = 0, grid_tsparse = 0;
+  int grid_tscan = 0, grid_tclaim = 0, grid_tapply = 0, grid_tsparse = 0, grid_tsort = 0;
+  size_t smem_tclaim = 0, smem_tsort = 0;
   uint64_t front_cap = 0;     // entries of fkey / fcell
   // host-buffer jobs: at most two in flight
   HostJob jobs[kHostJobs];
@@ -247,6 +250,10 @@ void free_all(pp_iblt *t) {
   if (t->down_s) cudaStreamDestroy(t->down_s);
   cudaFree(t->trb.rec_key);
   cudaFree(t->trb.rec_off);
+  cudaFree(t->trb.crec_key);
+  cudaFree(t->trb.crec_cell);
+  cudaFree(t->trb.cpos);
+  cudaFree(t->trb.cdone);
   cudaFree(t->trb.base);
   cudaFree(t->trb.pos);
   cudaFree(t->trb.base64);
@@ -689,6 +696,13 @@ pp_status ensure_tile_rounds(pp_iblt *t, cudaStream_t s) {
     if (e == cudaSuccess) e = cudaMalloc((void **)&b.act, (size_t)nt * sizeof(TileAct));
     if (e == cudaSuccess) e = cudaMalloc((void **)&b.act_d, (size_t)nt * sizeof(TileAct));
     if (e == cudaSuccess) e = cudaMalloc((void **)&b.fseg, (size_t)(nd + nsp) * sizeof(u32));
+    // coarse bins of the claim: at most 128 when a bin of 512 tiles allows it
+    uint32_t bsh = 0;
+    while (bsh < 9 && ((nt + (1u << bsh) - 1) >> bsh) > 128) ++bsh;
+    b.bin_tshift = bsh;
+    b.n_bins = (nt + (1u << bsh) - 1) >> bsh;
+    if (e == cudaSuccess) e = cudaMalloc((void **)&b.cpos, (size_t)b.n_bins * kTRPosStride * sizeof(u32));
+    if (e == cudaSuccess) e = cudaMalloc((void **)&b.cdone, (size_t)b.n_bins * sizeof(u32));
     if (e == cudaSuccess) e = cudaMalloc((void **)&d_start, (size_t)(nd + nsp) * sizeof(u64));
     if (e == cudaSuccess)
       e = cudaMemcpy(d_start, h_start, (size_t)(nd + nsp) * sizeof(u64), cudaMemcpyHostToDevice);
@@ -716,7 +730,10 @@ pp_status ensure_tile_rounds(pp_iblt *t, cudaStream_t s) {
       if (t->sg_exec) cudaGraphExecDestroy(t->sg_exec);
       t->sub_exec = t->sub_exec_binned = t->sg_exec = nullptr;
     }
-    t->grid_tclaim = persistent_grid(t->k.tclaim, kBlock, ((size_t)nd + nsp + 1) * sizeof(u32), t->opt.ctas_per_sm);
+    t->smem_tclaim = (size_t)kTClaimChunk * t->k.nr * 12 + ((size_t)nd + nsp + 1) * 4 + (3 * (size_t)b.n_bins + 1) * 4;
+    t->grid_tclaim = persistent_grid(t->k.tclaim, kBlock, t->smem_tclaim, t->opt.ctas_per_sm);
+    t->smem_tsort = tsort_smem_bytes(b.n_bins);
+    t->grid_tsort = persistent_grid((const void *)k_tsort, kTSortThreads, t->smem_tsort, 8);
     ++t->rec_gen;
   }
   const uint64_t items = t->items > 0 ? (uint64_t)t->items : 0;
@@ -725,11 +742,16 @@ pp_status ensure_tile_rounds(pp_iblt *t, cudaStream_t s) {
     PP_CUDA(cudaStreamSynchronize(s));
     cudaFree(b.rec_key);
     cudaFree(b.rec_off);
-    b.rec_key = nullptr;
+    cudaFree(b.crec_key);
+    cudaFree(b.crec_cell);
+    b.rec_key = b.crec_key = nullptr;
     b.rec_off = nullptr;
+    b.crec_cell = nullptr;
     b.rec_cap = 0;
     PP_CUDA(cudaMalloc((void **)&b.rec_key, need * sizeof(u64)));
     PP_CUDA(cudaMalloc((void **)&b.rec_off, need * sizeof(u16)));
+    PP_CUDA(cudaMalloc((void **)&b.crec_key, need * sizeof(u64)));
+    PP_CUDA(cudaMalloc((void **)&b.crec_cell, need * sizeof(u32)));
     b.rec_cap = need;
     ++t->rec_gen;
   }
@@ -746,13 +768,14 @@ struct TileArgsSet {
   const u32 *fcell_c, *bitmap_c;
   TileRoundBufs tb;
   DecodeCtl *ctl;
-  void *scan[7], *prefix[2], *claim[7], *active[2], *apply[7];
+  void *scan[7], *prefix[2], *claim[7], *active[2], *apply[7], *sort[2];
   void bind() {
     void *a[7] = {&cells_c, &tab0, &fkey, &fcell, &bitmap, &tb, &ctl};
     memcpy(scan, a, sizeof a);
     void *b[2] = {&tb, &ctl};
     memcpy(prefix, b, sizeof b);
     memcpy(active, b, sizeof b);
+    memcpy(sort, b, sizeof b);
     void *c[7] = {&cells, &tab0, &fkey_c, &fcell_c, &bitmap_c, &tb, &ctl};
     memcpy(claim, c, sizeof c);
     void *d[7] = {&cells, &tab0, &tb, &fkey, &fcell, &bitmap, &ctl};
@@ -783,9 +806,9 @@ pp_status build_tile_graph(pp_iblt *t) {
   cudaGraph_t g = nullptr;
   PP_CUDA(cudaGraphCreate(&g, 0));
   pp_status st = PP_OK;
-  cudaGraphNode_t n_scan, n_pre, n_cond, n_claim, n_act, n_apply[2], n_end;
+  cudaGraphNode_t n_scan, n_pre, n_cond, n_claim, n_sort, n_act, n_apply[2], n_end;
   const int grid_act = (int)((t->trb.n_tiles + kBlock - 1) / kBlock);
-  const size_t smem_claim = ((size_t)t->trb.n_seg_d + t->trb.n_seg_s + 1) * sizeof(u32);
+  const size_t smem_claim = t->smem_tclaim;
   cudaGraphConditionalHandle h;
   cudaGraphNodeParams cp{};
   cudaGraph_t body;
@@ -810,7 +833,10 @@ pp_status build_tile_graph(pp_iblt *t) {
   ea.bind();
   st = add_kernel(&n_claim, body, nullptr, 0, t->k.tclaim, t->grid_tclaim, kBlock, smem_claim, ta.claim);
   if (st != PP_OK) goto done;
-  st = add_kernel(&n_act, body, &n_claim, 1, (const void *)k_tactive, grid_act, kBlock, 0, ta.active);
+  st = add_kernel(&n_sort, body, &n_claim, 1, (const void *)k_tsort, t->grid_tsort, kTSortThreads, t->smem_tsort,
+                  ta.sort);
+  if (st != PP_OK) goto done;
+  st = add_kernel(&n_act, body, &n_sort, 1, (const void *)k_tactive, grid_act, kBlock, 0, ta.active);
   if (st != PP_OK) goto done;
   // dense and sparse tiles in two kernels that may run side by side
   st = add_kernel(&n_apply[0], body, &n_act, 1, t->k.tapply, t->grid_tapply, kTRThreads, kTApplySmem, ta.apply);
@@ -835,11 +861,13 @@ pp_status run_tile_host_loop(pp_iblt *t, cudaStream_t s) {
   EndArgs ea{t->ctl, RoundStats{t->st_rec, t->st_alive, t->st_front}, 0, 0, {}};
   ea.bind();
   const int grid_act = (int)((t->trb.n_tiles + kBlock - 1) / kBlock);
-  const size_t smem_claim = ((size_t)t->trb.n_seg_d + t->trb.n_seg_s + 1) * sizeof(u32);
+  const size_t smem_claim = t->smem_tclaim;
   PP_CUDA(cudaLaunchKernel(t->k.tscan, dim3(t->grid_tscan), dim3(kTRThreads), ta.scan, 0, s));
   PP_CUDA(cudaLaunchKernel((const void *)k_tprefix, dim3(1), dim3(1024), ta.prefix, 0, s));
   for (;;) {
     PP_CUDA(cudaLaunchKernel(t->k.tclaim, dim3(t->grid_tclaim), dim3(kBlock), ta.claim, smem_claim, s));
+    PP_CUDA(cudaLaunchKernel((const void *)k_tsort, dim3(t->grid_tsort), dim3(kTSortThreads), ta.sort,
+                             t->smem_tsort, s));
     PP_CUDA(cudaLaunchKernel((const void *)k_tactive, dim3(grid_act), dim3(kBlock), ta.active, 0, s));
     PP_CUDA(cudaLaunchKernel(t->k.tapply, dim3(t->grid_tapply), dim3(kTRThreads), ta.apply, kTApplySmem, s));
     PP_CUDA(cudaLaunchKernel(t->k.tapply_sparse, dim3(t->grid_tsparse), dim3(kTSThreads), ta.apply, 0, s));
@@ -1141,6 +1169,8 @@ pp_status pp_iblt_create(pp_iblt **out, uint64_t n_cells, uint32_t r, uint64_t s
     free_all(t);
     return st;
   }
+  // scattered 32-byte cell reads: one sector fetched from DRAM, not two
+  if (t->opt.l2_fetch == 1) cudaDeviceSetLimit(cudaLimitMaxL2FetchGranularity, 32);
   t->grid_scan = persistent_grid(t->k.scan, kBlock, 0, t->opt.ctas_per_sm);
   t->grid_peel = persistent_grid(t->k.peel, kBlock, t->smem_peel, t->opt.ctas_per_sm);
   t->grid_filter = persistent_grid(t->k.filter, kBlock, 0, t->opt.ctas_per_sm);
@@ -1175,7 +1205,7 @@ pp_status pp_workspace_size(uint64_t n_cells, uint32_t r, uint64_t m_keys, const
   uint64_t tile_round_bytes = 0;
   if (rounds_tiles) {
     const uint64_t nt = (n + kTRCells - 1) / kTRCells;
-    tile_round_bytes = ((uint64_t)r * m_keys + (uint64_t)kTRAlign * nt) * (sizeof(u64) + sizeof(u16)) +
+    tile_round_bytes = ((uint64_t)r * m_keys + (uint64_t)kTRAlign * nt) * (2 * sizeof(u64) + sizeof(u16) + sizeof(u32)) +
                        (nt + 1) * sizeof(u64) + nt * (kTRPosStride * sizeof(u32) + 2 * sizeof(u32) +
                                                       2 * sizeof(TileAct));
   }

@@ -48,6 +48,14 @@ constexpr int kTSThreads = 256;              // threads per block of k_tapply_sp
 constexpr u32 kTSCap = 512;                  // records of a sparse tile (at most)
 constexpr u32 kTSSlots = 1024;               // hash slots of k_tapply_sparse
 constexpr u32 kTSEmpty = 0xffffffffu;
+#ifndef PP_TCLAIM_ITEMS
+#define PP_TCLAIM_ITEMS 2
+#endif
+#ifndef PP_TCLAIM_CTAS
+#define PP_TCLAIM_CTAS 4
+#endif
+constexpr int kTClaimItems = PP_TCLAIM_ITEMS;            // frontier entries per thread per chunk
+constexpr int kTClaimChunk = kBlock * kTClaimItems;
 
 // A tile with records in the current round: records [lo, lo + n) (absolute slots).
 struct TileAct {
@@ -68,7 +76,13 @@ struct TileRoundBufs {
   TileAct *act_d; // dense tiles with records this round (n_tiles entries)
   u32 *fseg;      // per frontier segment: entries
   const u64 *fstart;  // per frontier segment: first entry in fkey / fcell
-  u64 rec_cap;    // slots in rec_key / rec_off
+  u64 *crec_key;  // coarse records (claim -> k_tsort): the key
+  u32 *crec_cell; // coarse records: the cell
+  u32 *cpos;      // per coarse bin (stride kTRPosStride): coarse records written this decode
+  u32 *cdone;     // per coarse bin: coarse records sorted into tiles this decode
+  u64 rec_cap;    // slots in rec_key / rec_off (and crec_key / crec_cell)
+  u32 n_bins;     // coarse bins of 2^bin_tshift tiles each
+  u32 bin_tshift;
   u32 n_tiles;
   u32 n_seg_d;    // segments of k_tscan / k_tapply blocks (first)
   u32 n_seg_s;    // segments of k_tapply_sparse blocks (after those)
@@ -76,6 +90,45 @@ struct TileRoundBufs {
   u32 cap_s;      // entries of a k_tapply_sparse segment: kTSCap * ceil(n_tiles / n_seg_s)
   u32 pad;
 };
+
+// Exclusive prefix of in[0..n) into out[0..n) and the total into out[n], by
+// one block of B threads (thread i takes a contiguous share).  in may be
+// global or shared; s_wt holds B / 32 words.
+template <int B>
+__device__ __forceinline__ void block_exclusive_scan(const u32 *in, u32 *out, u32 n, u32 *s_wt) {
+  const u32 tid = threadIdx.x;
+  const u32 per = (n + B - 1) / B;
+  const u32 lo = tid * per, hi = min(lo + per, n);
+  u32 own = 0;
+  for (u32 k = lo; k < hi; ++k) own += in[k];
+  u32 inc = own;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const u32 y = __shfl_up_sync(kFull, inc, o);
+    if ((int)lane_id() >= o) inc += y;
+  }
+  if (lane_id() == 31) s_wt[tid >> 5] = inc;
+  __syncthreads();
+  if (tid < 32) {
+    const u32 w = tid < B / 32 ? s_wt[tid] : 0;
+    u32 wi = w;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const u32 y = __shfl_up_sync(kFull, wi, o);
+      if ((int)tid >= o) wi += y;
+    }
+    if (tid < B / 32) s_wt[tid] = wi - w;
+    if (tid == B / 32 - 1) out[n] = wi;
+  }
+  __syncthreads();
+  u32 run = s_wt[tid >> 5] + inc - own;
+  for (u32 k = lo; k < hi; ++k) {
+    const u32 v = in[k];
+    out[k] = run;
+    run += v;
+  }
+  __syncthreads();
+}
 
 // Initial full scan, one tile per block step: F_1 (cells pure before any
 // round) with their bitmap bits, the sum of each tile's counts, and the
@@ -177,24 +230,41 @@ __global__ void __launch_bounds__(1024) k_tprefix(TileRoundBufs tb, DecodeCtl *_
     run += (tb.sum[t] + kTRAlign - 1) / kTRAlign * kTRAlign;
   }
   for (u32 k = tid; k < tb.n_seg_s; k += 1024) tb.fseg[tb.n_seg_d + k] = 0;
+  for (u32 k = tid; k < tb.n_bins; k += 1024) {
+    tb.cpos[(u64)k * kTRPosStride] = 0;
+    tb.cdone[k] = 0;
+  }
   if (tid == 0) {
     tb.base[tb.n_tiles] = s_w[32];
     if (s_w[32] > tb.rec_cap) atomicOr(&ctl->flags, (u32)FLAG_CAPACITY);
   }
 }
 
-// Phase B1 of round t (see the file comment).  Dynamic shared memory: the
-// prefix of the frontier's segment sizes (n_seg_d + n_seg_s + 1 u32).
+// Phase B1 of round t (see the file comment).  The records leave the block
+// sorted by coarse bin (2^bin_tshift tiles), in contiguous runs with one cursor
+// atomic per bin per chunk; k_tsort then sorts each bin's records into its
+// tiles.  Dynamic shared memory: the prefix of the frontier's segment sizes
+// (n_seg + 1 u32), the chunk's records (kTClaimChunk * NR keys and cells), and
+// per bin its count, its offset in the chunk and its run's first slot
+// (3 * n_bins + 1 u32).
 template <int R>
-__global__ void __launch_bounds__(kBlock, 4) k_tclaim(Cell *__restrict__ cells, const TableArgs tab0,
+__global__ void __launch_bounds__(kBlock, PP_TCLAIM_CTAS) k_tclaim(Cell *__restrict__ cells, const TableArgs tab0,
                                                       const u64 *__restrict__ fkey,
                                                       const u32 *__restrict__ fcell,
                                                       const u32 *__restrict__ bitmap, TileRoundBufs tb,
                                                       DecodeCtl *__restrict__ ctl) {
   constexpr int NR = nr_of<R>();
+  constexpr int CAP = kTClaimChunk * NR;
   extern __shared__ __align__(16) unsigned char smem[];
-  u32 *s_pre = reinterpret_cast<u32 *>(smem);
-  __shared__ u64 s_out[kClaimChunk];
+  const u32 ns = tb.n_seg_d + tb.n_seg_s;
+  const u32 nb = tb.n_bins;
+  u64 *s_key = reinterpret_cast<u64 *>(smem);           // CAP
+  u32 *s_cell = reinterpret_cast<u32 *>(s_key + CAP);   // CAP
+  u32 *s_pre = s_cell + CAP;                            // ns + 1
+  u32 *s_hist = s_pre + ns + 1;                         // nb
+  u32 *s_scan = s_hist + nb;                            // nb + 1
+  u32 *s_base = s_scan + nb + 1;                        // nb
+  __shared__ u64 s_out[kTClaimChunk];
   __shared__ u32 s_nout, s_wt[kBlock / 32], s_seg0;
   __shared__ u64 s_obase;
   __shared__ u64 s_red[kBlock / 32];
@@ -205,43 +275,12 @@ __global__ void __launch_bounds__(kBlock, 4) k_tclaim(Cell *__restrict__ cells, 
   const u64 out_cap = ctl->out_cap;
   const u64 keep = l2_evict_last_policy();
   const int r = rank_of<R>(tab0);
-  const u32 ns = tb.n_seg_d + tb.n_seg_s;
-  // exclusive prefix of the segment sizes: thread i owns segments [i*per, (i+1)*per)
-  {
-    const u32 per = (ns + kBlock - 1) / kBlock;
-    const u32 lo = tid * per, hi = min(lo + per, ns);
-    u32 own = 0;
-    for (u32 k = lo; k < hi; ++k) own += tb.fseg[k];
-    u32 inc = own;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const u32 y = __shfl_up_sync(kFull, inc, o);
-      if ((int)lane_id() >= o) inc += y;
-    }
-    if (lane_id() == 31) s_wt[tid >> 5] = inc;
-    __syncthreads();
-    if (tid < 32) {
-      const u32 w = tid < kBlock / 32 ? s_wt[tid] : 0;
-      u32 wi = w;
-#pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const u32 y = __shfl_up_sync(kFull, wi, o);
-        if ((int)tid >= o) wi += y;
-      }
-      if (tid < kBlock / 32) s_wt[tid] = wi - w;
-      if (tid == kBlock / 32 - 1) s_pre[ns] = wi;
-    }
-    __syncthreads();
-    u32 run = s_wt[tid >> 5] + inc - own;
-    for (u32 k = lo; k < hi; ++k) {
-      s_pre[k] = run;
-      run += tb.fseg[k];
-    }
-    __syncthreads();
-  }
+  const u32 bsh = kTRShift + tb.bin_tshift;  // cell -> coarse bin
+  block_exclusive_scan<kBlock>(tb.fseg, s_pre, ns, s_wt);
   u32 flags = 0;
   u64 emptied = 0;
-  for (u64 c0 = (u64)blockIdx.x * kClaimChunk; c0 < n; c0 += (u64)gridDim.x * kClaimChunk) {
+  for (u64 c0 = (u64)blockIdx.x * kTClaimChunk; c0 < n; c0 += (u64)gridDim.x * kTClaimChunk) {
+    for (u32 i = tid; i < nb; i += kBlock) s_hist[i] = 0;
     if (tid == 0) {
       s_nout = 0;
       // segment of the chunk's first entry: the last k with s_pre[k] <= c0
@@ -254,13 +293,13 @@ __global__ void __launch_bounds__(kBlock, 4) k_tclaim(Cell *__restrict__ cells, 
       s_seg0 = a;
     }
     __syncthreads();
-    u64 x[kClaimItems];
-    u32 c[kClaimItems], cj[kClaimItems][NR];
-    bool win[kClaimItems];
-    int jstar[kClaimItems];
+    u64 x[kTClaimItems];
+    u32 c[kTClaimItems], cj[kTClaimItems][NR], rk[kTClaimItems][NR];
+    bool win[kTClaimItems];
+    int jstar[kTClaimItems];
     const u32 a0 = s_seg0;
 #pragma unroll
-    for (int it = 0; it < kClaimItems; ++it) {
+    for (int it = 0; it < kTClaimItems; ++it) {
       const u32 i = (u32)(c0 + (u64)it * kBlock + tid);
       win[it] = i < n;
       u64 src = 0;
@@ -274,7 +313,7 @@ __global__ void __launch_bounds__(kBlock, 4) k_tclaim(Cell *__restrict__ cells, 
       c[it] = win[it] ? __ldcs(fcell + src) : 0u;
     }
 #pragma unroll
-    for (int it = 0; it < kClaimItems; ++it) {
+    for (int it = 0; it < kTClaimItems; ++it) {
       cells_of<NR>(x[it], tab0, cj[it]);
       int js = -1;
 #pragma unroll
@@ -295,49 +334,53 @@ __global__ void __launch_bounds__(kBlock, 4) k_tclaim(Cell *__restrict__ cells, 
       }
     }
 #pragma unroll
-    for (int it = 0; it < kClaimItems; ++it) {
+    for (int it = 0; it < kTClaimItems; ++it) {
       const u32 p = warp_reserve<u32>(win[it], &s_nout);
       if (win[it]) {
         s_out[p] = x[it];
         st_cell_cs(cells + c[it], 0ull, 0ull, 0);  // the winner's own cell held exactly x
         emptied += 1;
       }
-    }
-    // records for the other cells: every cursor atomic of this thread in flight
-    // at once.  A record past its tile's region would mean a cell held more
-    // keys than its count; k_tactive checks that per tile, so only the
-    // buffer's end is checked here.
-    u32 at[kClaimItems][NR], b0[kClaimItems][NR];
+      // records for the other cells, counted per coarse bin
 #pragma unroll
-    for (int it = 0; it < kClaimItems; ++it) {
+      for (int j = 0; j < NR; ++j)
+        rk[it][j] = (win[it] && j < r && j != jstar[it]) ? atomicAdd(s_hist + (cj[it][j] >> bsh), 1u) : 0u;
+    }
+    __syncthreads();
+    block_exclusive_scan<kBlock>(s_hist, s_scan, nb, s_wt);
+    for (u32 k = tid; k < nb; k += kBlock) {
+      const u32 h = s_hist[k];
+      s_base[k] = h ? atomicAdd(tb.cpos + (u64)k * kTRPosStride, h) : 0u;
+    }
+    if (tid == 0 && s_nout) s_obase = atomicAdd(&ctl->n_out, (u64)s_nout);
+    __syncthreads();
+#pragma unroll
+    for (int it = 0; it < kTClaimItems; ++it) {
 #pragma unroll
       for (int j = 0; j < NR; ++j) {
         if (win[it] && j < r && j != jstar[it]) {
-          const u32 t = cj[it][j] >> kTRShift;
-          b0[it][j] = tb.base64[t];
-          at[it][j] = atomicAdd(tb.pos + (u64)t * kTRPosStride, 1u);
-        }
-      }
-    }
-#pragma unroll
-    for (int it = 0; it < kClaimItems; ++it) {
-#pragma unroll
-      for (int j = 0; j < NR; ++j) {
-        if (win[it] && j < r && j != jstar[it]) {
-          const u64 q = (u64)b0[it][j] * kTRAlign + at[it][j];
-          if (q < tb.rec_cap) {
-            st_l2_policy(tb.rec_key + q, x[it], keep);
-            tb.rec_off[q] = (u16)(cj[it][j] & (kTRCells - 1));
-          } else {
-            flags |= FLAG_INTERNAL;
-          }
+          const u32 pos = s_scan[cj[it][j] >> bsh] + rk[it][j];
+          s_key[pos] = x[it];
+          s_cell[pos] = cj[it][j];
         }
       }
     }
     __syncthreads();
+    // contiguous runs per coarse bin; the bin's region is its tiles' regions
+    const u32 total = s_scan[nb];
+    for (u32 p = tid; p < total; p += kBlock) {
+      const u32 bn = s_cell[p] >> bsh;
+      const u64 rb = tb.base[(u64)bn << tb.bin_tshift];
+      const u32 te = min((bn + 1) << tb.bin_tshift, tb.n_tiles);
+      const u64 dst = rb + s_base[bn] + (p - s_scan[bn]);
+      if (dst < tb.base[te] && dst < tb.rec_cap) {
+        st_l2_policy(tb.crec_key + dst, s_key[p], keep);
+        st_l2_policy(tb.crec_cell + dst, s_cell[p], keep);
+      } else {
+        flags |= FLAG_INTERNAL;  // more records than the bin's counts allow
+      }
+    }
     const u32 no = s_nout;
-    if (tid == 0 && no) s_obase = atomicAdd(&ctl->n_out, (u64)no);
-    __syncthreads();
     const u64 ob = s_obase;
     for (u32 q = tid; q < no; q += kBlock) {
       if (ob + q < out_cap) out[ob + q] = s_out[q];
@@ -350,10 +393,132 @@ __global__ void __launch_bounds__(kBlock, 4) k_tclaim(Cell *__restrict__ cells, 
   if (flags) atomicOr(&ctl->flags, flags);
 }
 
+constexpr int kTSortThreads = 256;
+#ifndef PP_TSORT_PER
+#define PP_TSORT_PER 8
+#endif
+constexpr int kTSortPer = PP_TSORT_PER;
+constexpr u32 kTSortChunk = kTSortThreads * kTSortPer;  // coarse records per work item
+constexpr u32 kMaxBinTiles = 512;                         // tiles per coarse bin (at most)
+
+// Dynamic shared memory of k_tsort: the chunk prefix over the bins (n_bins + 1
+// u32) and the chunk's records sorted by tile (kTSortChunk keys and offsets).
+inline size_t tsort_smem_bytes(u32 n_bins) {
+  return ((size_t)n_bins + 1) * 4 + (size_t)kTSortChunk * (8 + 2);
+}
+
+// Phase B1': the round's coarse records of each bin, sorted into its tiles'
+// record regions (one cursor atomic per tile per chunk of kTSortChunk records).
+__global__ void __launch_bounds__(kTSortThreads, 4) k_tsort(TileRoundBufs tb, DecodeCtl *__restrict__ ctl) {
+  if (*(volatile u32 *)&ctl->round == 0) return;  // the first loop iteration only promotes F_1
+  extern __shared__ __align__(16) unsigned char smem[];
+  const u32 nb = tb.n_bins;
+  u32 *s_pre = reinterpret_cast<u32 *>(smem);             // nb + 1: chunks before bin b
+  u64 *s_key = reinterpret_cast<u64 *>(smem + (((size_t)nb + 1) * 4 + 15) / 16 * 16);  // kTSortChunk
+  u16 *s_off = reinterpret_cast<u16 *>(s_key + kTSortChunk);                           // kTSortChunk
+  __shared__ u32 s_cnt[kMaxBinTiles], s_scan[kMaxBinTiles + 1], s_tb[kMaxBinTiles];
+  __shared__ u32 s_wt[kTSortThreads / 32];
+  __shared__ u32 s_nchunk[1];
+  const u32 tid = threadIdx.x;
+  const u64 keep = l2_evict_last_policy();
+  const u32 ntile = 1u << tb.bin_tshift;
+  // chunk counts per bin into s_scan's space first, then their prefix
+  // a bin's records end at its cursor, clamped to its region (the claim
+  // flagged any record that did not fit, and wrote none past the region)
+  auto bin_end = [&](u32 b) -> u32 {
+    const u64 rb = tb.base[(u64)b << tb.bin_tshift];
+    const u64 re = tb.base[min((b + 1) << tb.bin_tshift, tb.n_tiles)];
+    const u32 p = tb.cpos[(u64)b * kTRPosStride];
+    return (u64)p < re - rb ? p : (u32)(re - rb);
+  };
+  for (u32 b = tid; b < nb; b += kTSortThreads) {
+    const u32 lo = tb.cdone[b], hi = bin_end(b);
+    s_pre[b] = hi > lo ? (hi - lo + kTSortChunk - 1) / kTSortChunk : 0u;
+  }
+  __syncthreads();
+  block_exclusive_scan<kTSortThreads>(s_pre, s_pre, nb, s_wt);
+  (void)s_nchunk;
+  const u32 total = s_pre[nb];
+  u32 flags = 0;
+  for (u32 ch = blockIdx.x; ch < total; ch += gridDim.x) {
+    // bin of this chunk: the last b with s_pre[b] <= ch
+    u32 a = 0, bb = nb;
+    while (bb - a > 1) {
+      const u32 mid = (a + bb) >> 1;
+      if (s_pre[mid] <= ch) a = mid;
+      else bb = mid;
+    }
+    const u32 b = a;
+    const u64 rb = tb.base[(u64)b << tb.bin_tshift];
+    const u32 lo = tb.cdone[b] + (ch - s_pre[b]) * kTSortChunk;
+    const u32 hi = min(lo + kTSortChunk, bin_end(b));
+    const u32 t0 = b << tb.bin_tshift;
+    for (u32 i = tid; i < ntile; i += kTSortThreads) s_cnt[i] = 0;
+    __syncthreads();
+    u64 x[kTSortPer];
+    u32 lt[kTSortPer], rk[kTSortPer], cl[kTSortPer];
+#pragma unroll
+    for (int k = 0; k < kTSortPer; ++k) {
+      const u32 i = lo + (u32)k * kTSortThreads + tid;
+      const bool v = i < hi;
+      x[k] = v ? __ldcs(tb.crec_key + rb + i) : 0ull;
+      cl[k] = v ? __ldcs(tb.crec_cell + rb + i) : 0xffffffffu;
+    }
+#pragma unroll
+    for (int k = 0; k < kTSortPer; ++k) {
+      lt[k] = cl[k] != 0xffffffffu ? (cl[k] >> kTRShift) - t0 : 0u;
+      rk[k] = cl[k] != 0xffffffffu ? atomicAdd(s_cnt + lt[k], 1u) : 0u;
+    }
+    __syncthreads();
+    block_exclusive_scan<kTSortThreads>(s_cnt, s_scan, ntile, s_wt);
+    for (u32 i = tid; i < ntile; i += kTSortThreads) {
+      const u32 h = s_cnt[i];
+      s_tb[i] = h ? atomicAdd(tb.pos + (u64)(t0 + i) * kTRPosStride, h) : 0u;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < kTSortPer; ++k) {
+      if (cl[k] != 0xffffffffu) {
+        const u32 p = s_scan[lt[k]] + rk[k];
+        s_key[p] = x[k];
+        s_off[p] = (u16)(cl[k] & (kTRCells - 1));
+      }
+    }
+    __syncthreads();
+    const u32 nrec = hi > lo ? hi - lo : 0u;
+    for (u32 p = tid; p < nrec; p += kTSortThreads) {
+      // tile of slot p: the last tile whose run starts at or before p
+      u32 l = 0, h2 = ntile;
+      while (h2 - l > 1) {
+        const u32 mid = (l + h2) >> 1;
+        if (s_scan[mid] <= p) l = mid;
+        else h2 = mid;
+      }
+      const u32 t = t0 + l;
+      const u64 dst = tb.base[t] + s_tb[l] + (p - s_scan[l]);
+      if (dst < tb.base[t + 1] && dst < tb.rec_cap) {
+        st_l2_policy(tb.rec_key + dst, s_key[p], keep);
+        tb.rec_off[dst] = s_off[p];
+      } else {
+        flags |= FLAG_INTERNAL;  // more records than the tile's counts allow
+      }
+    }
+    __syncthreads();
+  }
+  if (flags) atomicOr(&ctl->flags, flags);
+}
+
 // The tiles with records in the current round (one thread per tile), split
 // into sparse (at most kTSCap records) and dense ones.
 __global__ void __launch_bounds__(kBlock) k_tactive(TileRoundBufs tb, DecodeCtl *__restrict__ ctl) {
   if (*(volatile u32 *)&ctl->round == 0) return;  // the first loop iteration only promotes F_1
+  // the coarse records of this round are all in their tiles now
+  for (u32 b = blockIdx.x * kBlock + threadIdx.x; b < tb.n_bins; b += gridDim.x * kBlock) {
+    const u64 rb = tb.base[(u64)b << tb.bin_tshift];
+    const u64 re = tb.base[min((b + 1) << tb.bin_tshift, tb.n_tiles)];
+    const u32 p = tb.cpos[(u64)b * kTRPosStride];
+    tb.cdone[b] = (u64)p < re - rb ? p : (u32)(re - rb);
+  }
   for (u32 t0 = blockIdx.x * kBlock; t0 < tb.n_tiles; t0 += gridDim.x * kBlock) {
     const u32 t = t0 + threadIdx.x;
     u32 lo = 0, hi = 0;
