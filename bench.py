@@ -60,11 +60,14 @@ HEADLINE_SOURCES = ("common.cu", "device.cuh", "host.cuh", "iblt.cu", "iblt_binn
 
 
 def csrc_digest() -> str:
+    """Digest of the headline sources' code: line comments and blank lines are
+    left out, so that a comment edit does not void the stored traffic."""
     h = hashlib.sha256()
     d = os.path.join(ROOT, "paper_1302_7014_b300", "csrc")
     for name in HEADLINE_SOURCES:
         with open(os.path.join(d, name), "rb") as f:
-            h.update(name.encode() + f.read())
+            lines = (ln.split(b"//", 1)[0].rstrip() for ln in f.read().splitlines())
+            h.update(name.encode() + b"\n".join(ln for ln in lines if ln))
     return h.hexdigest()[:16]
 
 
@@ -916,11 +919,12 @@ def main():
         del outs
         torch.cuda.empty_cache()
 
-    # kernels of one step: the binned build (k_bin, then n_slabs + 2 launches of
-    # the tile step for the 2^21-cell slabs); the decode's k_ctl_init, k_tscan
-    # and k_tprefix, then five kernels per loop iteration (rounds + the first
-    # promote-only iteration)
-    launches_per_step = 1 + (-(-n // (1 << 21)) + 2) + 3 + 5 * (rounds + 1)
+    # kernels of one step: the binned build (k_bin, k_flag_to_host, then
+    # n_slabs + 2 launches of the tile step for the 2^21-cell slabs); the
+    # decode's k_ctl_init, k_tscan and k_tprefix, six kernels per round
+    # (k_tclaim, k_tsort, k_tactive, k_tapply, k_tapply_sparse, k_round_end)
+    # and k_trestore
+    launches_per_step = 2 + (-(-n // (1 << 21)) + 2) + 3 + 6 * rounds + 1
 
     # roofline of the two halves of a step (sector-floor byte model)
     peak, peak_kind = hbm_peak()

@@ -16,11 +16,12 @@ seeded input generators in ``ppgen``.
   hypergraphs (pins for the C code).
 
 Parity unpinned: the IBLT cell map and the split of n cells into r
-sub-tables are conventions the paper leaves open (it asks only for r hash
-functions and 'some simple pseudorandom function').  They are fixed in
-``peel_oracle.c`` and frozen by the known-answer file
-``tests/golden/hash_kat.txt``, which the CUDA side must reproduce; only the
-mix64 finaliser inside them is pinned to a published vector.
+sub-tables are conventions the paper leaves open (Sec. 6 asks for r hash
+functions and a pseudorandom checksum without fixing them).  They are fixed
+in ``peel_oracle.c`` and frozen by the known-answer file
+``tests/golden/hash_kat.txt``, which the CUDA side must reproduce.  The mix64
+finaliser inside them is pinned to a published vector, and the range map to
+the edges of its equal-width intervals.
 """
 from __future__ import annotations
 

@@ -60,6 +60,7 @@ static IbltKernels iblt_kernels_t() {
     k.tclaim = (const void *)k_tclaim<R>;
     k.tapply = (const void *)k_tapply<R>;
     k.tapply_sparse = (const void *)k_tapply_sparse<R>;
+    k.trestore = (const void *)k_trestore<R>;
     static bool tattr = false;
     if (!tattr) {
       cudaFuncSetAttribute((const void *)k_tapply<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -759,7 +760,6 @@ pp_status ensure_tile_rounds(pp_iblt *t, cudaStream_t s) {
 }
 
 struct TileArgsSet {
-  const Cell *cells_c;
   Cell *cells;
   TableArgs tab0;
   u64 *fkey;
@@ -768,9 +768,9 @@ struct TileArgsSet {
   const u32 *fcell_c, *bitmap_c;
   TileRoundBufs tb;
   DecodeCtl *ctl;
-  void *scan[7], *prefix[2], *claim[7], *active[2], *apply[7], *sort[2];
+  void *scan[7], *prefix[2], *claim[7], *active[2], *apply[7], *sort[2], *restore[6];
   void bind() {
-    void *a[7] = {&cells_c, &tab0, &fkey, &fcell, &bitmap, &tb, &ctl};
+    void *a[7] = {&cells, &tab0, &fkey, &fcell, &bitmap, &tb, &ctl};
     memcpy(scan, a, sizeof a);
     void *b[2] = {&tb, &ctl};
     memcpy(prefix, b, sizeof b);
@@ -780,11 +780,12 @@ struct TileArgsSet {
     memcpy(claim, c, sizeof c);
     void *d[7] = {&cells, &tab0, &tb, &fkey, &fcell, &bitmap, &ctl};
     memcpy(apply, d, sizeof d);
+    void *e[6] = {&cells, &tab0, &fkey_c, &fcell_c, &tb, &ctl};
+    memcpy(restore, e, sizeof e);
   }
 };
 
 void fill_tile_args(pp_iblt *t, TileArgsSet &a) {
-  a.cells_c = t->cells;
   a.cells = t->cells;
   a.tab0 = t->args;
   a.fkey = t->fkey;
@@ -798,7 +799,8 @@ void fill_tile_args(pp_iblt *t, TileArgsSet &a) {
   a.bind();
 }
 
-// tscan -> tprefix -> while (more) { tclaim -> tapply -> round_end }
+// tscan -> tprefix -> while (more) { tclaim -> tsort -> tactive -> tapply || tapply_sparse -> round_end }
+// -> trestore
 pp_status build_tile_graph(pp_iblt *t) {
   TileArgsSet ta;
   fill_tile_args(t, ta);
@@ -806,7 +808,8 @@ pp_status build_tile_graph(pp_iblt *t) {
   cudaGraph_t g = nullptr;
   PP_CUDA(cudaGraphCreate(&g, 0));
   pp_status st = PP_OK;
-  cudaGraphNode_t n_scan, n_pre, n_cond, n_claim, n_sort, n_act, n_apply[2], n_end;
+  cudaGraphNode_t n_scan, n_pre, n_cond, n_claim, n_sort, n_act, n_apply[2], n_end, n_restore;
+  const int grid_restore = t->grid_tapply + t->grid_tsparse;  // one block per frontier segment
   const int grid_act = (int)((t->trb.n_tiles + kBlock - 1) / kBlock);
   const size_t smem_claim = t->smem_tclaim;
   cudaGraphConditionalHandle h;
@@ -829,6 +832,8 @@ pp_status build_tile_graph(pp_iblt *t) {
     goto done;
   }
   body = cp.conditional.phGraph_out[0];
+  st = add_kernel(&n_restore, g, &n_cond, 1, t->k.trestore, grid_restore, kBlock, 0, ta.restore);
+  if (st != PP_OK) goto done;
   ea.cond = h;
   ea.bind();
   st = add_kernel(&n_claim, body, nullptr, 0, t->k.tclaim, t->grid_tclaim, kBlock, smem_claim, ta.claim);
@@ -876,6 +881,7 @@ pp_status run_tile_host_loop(pp_iblt *t, cudaStream_t s) {
     PP_CUDA(cudaStreamSynchronize(s));
     if (!t->h_ctl->more) break;
   }
+  PP_CUDA(cudaLaunchKernel(t->k.trestore, dim3(t->grid_tapply + t->grid_tsparse), dim3(kBlock), ta.restore, 0, s));
   return PP_OK;
 }
 

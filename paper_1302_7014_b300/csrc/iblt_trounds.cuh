@@ -2,15 +2,16 @@
 // Sec. 6) with each round's cell updates applied tile by tile.
 //
 // The table is cut into tiles of 4096 consecutive cells.  Per round:
-//   k_tclaim  for every frontier entry (cell c, key x snapshotted at the
-//             round's start) decides, as k_claim does, whether c is the
+//   k_tclaim  for every frontier entry (cell c, key x snapshotted when c
+//             became pure) decides, as k_claim does, whether c is the
 //             lowest-index cell of x that was pure at the round's start.  A
-//             winner outputs x and empties its own cell c with one plain
-//             store: c held exactly x, so (0, 0, 0) is its state once x is
-//             deleted (any other update to c this round is applied on top of
-//             that store by k_tapply).  For each of the key's other cells it
-//             appends one record (x, offset of the cell in its tile) to that
-//             tile's record region.
+//             winner outputs x, and for each of x's cells that was not pure at
+//             the round's start writes one record (x, cell) into the region of
+//             the cell's coarse bin (2^bin_tshift tiles, at most 128 bins).
+//   k_tsort   sorts each coarse bin's records of the round into its tiles'
+//             regions as (x, offset of the cell in its tile).  Two passes keep
+//             the claim's shared-memory sort small (128 bins, not 16384 tiles)
+//             and give every tile's cursor one atomic per chunk.
 //   k_tactive lists the tiles that received records, split into sparse
 //             (at most kTSCap records) and dense ones.
 //   k_tapply_sparse / k_tapply  one block per tile: the round's records of
@@ -22,6 +23,14 @@
 //             that is pure after the update joins the next frontier right
 //             there (key snapshot and bitmap bit), so no separate pass
 //             re-reads it.
+// A pure cell is written as (0, 0, 0) at the moment it joins the frontier (by
+// k_tscan or the apply).  In a table built from insertions only, count 1 means
+// the cell holds exactly one key x, so it is (x, checkSum(x), 1); x is
+// recovered in the next round, and deleting it leaves (0, 0, 0).  The frontier
+// entry keeps x, no record is ever sent to a cell that was pure at its round's
+// start, and the claim touches no cell.  A decode that stops with a frontier
+// pending (round limit, error) puts (x, checkSum(x), 1) back into each of its
+// cells (k_trestore), so the table is left as after its last completed round.
 // Records of a tile over the whole decode never exceed the sum of the tile's
 // counts at the decode's start (each key leaves each of its cells once), so
 // every tile owns a fixed region of that size, filled round after round.  That
@@ -133,10 +142,11 @@ __device__ __forceinline__ void block_exclusive_scan(const u32 *in, u32 *out, u3
 // Initial full scan, one tile per block step: F_1 (cells pure before any
 // round) with their bitmap bits, the sum of each tile's counts, and the
 // decode's alive / nonempty counters.  Every bitmap word is written here.
+// The cells of F_1 are emptied as they are found (see the file comment).
 // Runs n_seg_d blocks; block b takes tiles b, b + n_seg_d, ... (at most
 // 4096 pushes each) and writes segment b.
 template <int R>
-__global__ void __launch_bounds__(kTRThreads) k_tscan(const Cell *__restrict__ cells, const TableArgs tab0,
+__global__ void __launch_bounds__(kTRThreads) k_tscan(Cell *__restrict__ cells, const TableArgs tab0,
                                                       u64 *__restrict__ fkey, u32 *__restrict__ fcell,
                                                       u32 *__restrict__ bitmap, TileRoundBufs tb,
                                                       DecodeCtl *__restrict__ ctl) {
@@ -146,7 +156,7 @@ __global__ void __launch_bounds__(kTRThreads) k_tscan(const Cell *__restrict__ c
   const u64 seed_chk = tab0.seed[rank_of<R>(tab0)];
   const u32 n = tab0.n_cells;
   const u64 seg0 = tb.fstart[blockIdx.x];
-  u64 alive = 0, nonempty = 0;
+  u64 alive = 0, nonempty = 0, emptied = 0;
   if (tid == 0) s_seg = 0, s_neg = 0;
   __syncthreads();
   for (u32 t = blockIdx.x; t < tb.n_tiles; t += gridDim.x) {
@@ -167,6 +177,10 @@ __global__ void __launch_bounds__(kTRThreads) k_tscan(const Cell *__restrict__ c
         nonempty += cnt != 0;
         sum += cnt;
         if (cnt < 0) s_neg = 1;
+        if (pure) {
+          st_cell_cs(cells + c, 0ull, 0ull, 0);
+          emptied += 1;
+        }
       }
       const u32 ball = __ballot_sync(kFull, pure);
       const u32 first = c0 + (u32)it * kTRThreads + (tid & ~31u);
@@ -175,6 +189,8 @@ __global__ void __launch_bounds__(kTRThreads) k_tscan(const Cell *__restrict__ c
       if (pure && p < tb.cap_d) {
         fkey[seg0 + p] = key;
         fcell[seg0 + p] = c;
+      } else if (pure) {
+        s_neg = 1;  // cannot happen: a segment holds every push of its block's tiles
       }
     }
     const long long sm = block_sum<long long, kTRThreads>(sum, reinterpret_cast<long long *>(s_red));
@@ -182,10 +198,13 @@ __global__ void __launch_bounds__(kTRThreads) k_tscan(const Cell *__restrict__ c
   }
   const u64 a = block_sum<u64, kTRThreads>(alive, s_red);
   const u64 ne = block_sum<u64, kTRThreads>(nonempty, s_red);
+  const u64 em = block_sum<u64, kTRThreads>(emptied, s_red);
   if (tid == 0) {
     if (a) atomicAdd(&ctl->alive, a);
     if (ne) atomicAdd(&ctl->nonempty, ne);
-    if (s_neg) atomicOr(&ctl->flags, (u32)FLAG_INTERNAL);  // a negative count: not an insert-only table
+    if (em) atomicAdd(&ctl->emptied, em);
+    // a negative count (not an insert-only table) or a full segment
+    if (s_neg) atomicOr(&ctl->flags, (u32)FLAG_INTERNAL);
     tb.fseg[blockIdx.x] = s_seg;
     if (s_seg) atomicAdd(&ctl->n_next, s_seg);
   }
@@ -193,7 +212,10 @@ __global__ void __launch_bounds__(kTRThreads) k_tscan(const Cell *__restrict__ c
 
 // Tile regions: base[t] = sum over t' < t of the tile sums, each rounded up to
 // kTRAlign records; cursors at 0; every sparse segment empty.  One block;
-// flags FLAG_CAPACITY if the regions exceed the record buffers.
+// flags FLAG_CAPACITY if the regions exceed the record buffers.  Then F_1
+// becomes the current frontier, so that the first loop iteration is round 1
+// (unless F_1 is empty or an error was flagged: the loop then runs one
+// iteration with round 0, which does nothing but end the decode).
 __global__ void __launch_bounds__(1024) k_tprefix(TileRoundBufs tb, DecodeCtl *__restrict__ ctl) {
   __shared__ u64 s_w[33];
   const u32 tid = threadIdx.x;
@@ -236,8 +258,48 @@ __global__ void __launch_bounds__(1024) k_tprefix(TileRoundBufs tb, DecodeCtl *_
   }
   if (tid == 0) {
     tb.base[tb.n_tiles] = s_w[32];
-    if (s_w[32] > tb.rec_cap) atomicOr(&ctl->flags, (u32)FLAG_CAPACITY);
+    u32 fl = *(volatile u32 *)&ctl->flags;
+    if (s_w[32] > tb.rec_cap) {
+      atomicOr(&ctl->flags, (u32)FLAG_CAPACITY);
+      fl |= FLAG_CAPACITY;
+    }
+    DecodeCtl &c = *ctl;
+    const u32 f1 = *(volatile u32 *)&c.n_next;
+    if ((fl & (FLAG_CAPACITY | FLAG_INTERNAL)) == 0 && f1 > 0) {
+      c.out_round_start = c.n_out;
+      c.n_front = f1;
+      c.n_next = 0;
+      c.n_cand = 0;
+      c.round = 1;
+    }
   }
+}
+
+// After the round loop: a decode that stopped with a frontier pending (round
+// limit, error) puts (x, checkSum(x), 1) back into each cell that frontier
+// emptied (see the file comment), so the table is left as after its last
+// completed round.  The pending frontier is n_front entries in the segments.
+template <int R>
+__global__ void __launch_bounds__(kBlock) k_trestore(Cell *__restrict__ cells, const TableArgs tab0,
+                                                     const u64 *__restrict__ fkey, const u32 *__restrict__ fcell,
+                                                     TileRoundBufs tb, DecodeCtl *__restrict__ ctl) {
+  __shared__ u64 s_red[kBlock / 32];
+  if (*(volatile u32 *)&ctl->n_front == 0) return;  // uniform: the decode finished
+  const u64 seed_chk = tab0.seed[rank_of<R>(tab0)];
+  const u32 ns = tb.n_seg_d + tb.n_seg_s;
+  u64 put = 0;
+  for (u32 sg = blockIdx.x; sg < ns; sg += gridDim.x) {
+    const u32 cap = sg < tb.n_seg_d ? tb.cap_d : tb.cap_s;
+    const u32 k = min(tb.fseg[sg], cap);
+    const u64 a = tb.fstart[sg];
+    for (u32 i = threadIdx.x; i < k; i += kBlock) {
+      const u64 x = fkey[a + i];
+      st_cell_cs(cells + fcell[a + i], x, checksum(x, seed_chk), 1);
+      ++put;
+    }
+  }
+  const u64 p = block_sum<u64, kBlock>(put, s_red);
+  if (threadIdx.x == 0 && p) atomicAdd(&ctl->emptied, 0ull - p);
 }
 
 // Phase B1 of round t (see the file comment).  The records leave the block
@@ -267,7 +329,6 @@ __global__ void __launch_bounds__(kBlock, PP_TCLAIM_CTAS) k_tclaim(Cell *__restr
   __shared__ u64 s_out[kTClaimChunk];
   __shared__ u32 s_nout, s_wt[kBlock / 32], s_seg0;
   __shared__ u64 s_obase;
-  __shared__ u64 s_red[kBlock / 32];
   const u32 tid = threadIdx.x;
   const u32 n = *(volatile u32 *)&ctl->n_front;
   if (n == 0) return;  // uniform: nothing to claim
@@ -278,7 +339,6 @@ __global__ void __launch_bounds__(kBlock, PP_TCLAIM_CTAS) k_tclaim(Cell *__restr
   const u32 bsh = kTRShift + tb.bin_tshift;  // cell -> coarse bin
   block_exclusive_scan<kBlock>(tb.fseg, s_pre, ns, s_wt);
   u32 flags = 0;
-  u64 emptied = 0;
   for (u64 c0 = (u64)blockIdx.x * kTClaimChunk; c0 < n; c0 += (u64)gridDim.x * kTClaimChunk) {
     for (u32 i = tid; i < nb; i += kBlock) s_hist[i] = 0;
     if (tid == 0) {
@@ -296,7 +356,7 @@ __global__ void __launch_bounds__(kBlock, PP_TCLAIM_CTAS) k_tclaim(Cell *__restr
     u64 x[kTClaimItems];
     u32 c[kTClaimItems], cj[kTClaimItems][NR], rk[kTClaimItems][NR];
     bool win[kTClaimItems];
-    int jstar[kTClaimItems];
+    u32 need[kTClaimItems];  // bit j: x's cell in sub-table j gets a record
     const u32 a0 = s_seg0;
 #pragma unroll
     for (int it = 0; it < kTClaimItems; ++it) {
@@ -319,32 +379,31 @@ __global__ void __launch_bounds__(kBlock, PP_TCLAIM_CTAS) k_tclaim(Cell *__restr
 #pragma unroll
       for (int j = NR - 1; j >= 0; --j)
         if (j < r && cj[it][j] == c[it]) js = j;
-      jstar[it] = js;
       if (win[it] && js < 0) {
         flags |= FLAG_INTERNAL;
         win[it] = false;
       }
-      // the lowest-index cell of x that was pure at the round's start wins
+      // the lowest-index cell of x that was pure at the round's start wins;
+      // x's cells that were pure at the round's start are empty already
+      u32 pure_at_start = 0;
 #pragma unroll
-      for (int j = 0; j < NR - 1; ++j) {
-        if (win[it] && j < js) {
+      for (int j = 0; j < NR; ++j) {
+        if (win[it] && j < r && j != js) {
           const u32 w = __ldcg(bitmap + (cj[it][j] >> 5));
-          if ((w >> (cj[it][j] & 31u)) & 1u) win[it] = false;
+          if ((w >> (cj[it][j] & 31u)) & 1u) pure_at_start |= 1u << j;
         }
       }
+      if (win[it] && (pure_at_start & ((1u << (js < 0 ? 0 : js)) - 1u))) win[it] = false;
+      need[it] = win[it] ? (((1u << r) - 1u) & ~pure_at_start & ~(1u << (js < 0 ? 0 : js))) : 0u;
     }
 #pragma unroll
     for (int it = 0; it < kTClaimItems; ++it) {
       const u32 p = warp_reserve<u32>(win[it], &s_nout);
-      if (win[it]) {
-        s_out[p] = x[it];
-        st_cell_cs(cells + c[it], 0ull, 0ull, 0);  // the winner's own cell held exactly x
-        emptied += 1;
-      }
+      if (win[it]) s_out[p] = x[it];
       // records for the other cells, counted per coarse bin
 #pragma unroll
       for (int j = 0; j < NR; ++j)
-        rk[it][j] = (win[it] && j < r && j != jstar[it]) ? atomicAdd(s_hist + (cj[it][j] >> bsh), 1u) : 0u;
+        rk[it][j] = ((need[it] >> j) & 1u) ? atomicAdd(s_hist + (cj[it][j] >> bsh), 1u) : 0u;
     }
     __syncthreads();
     block_exclusive_scan<kBlock>(s_hist, s_scan, nb, s_wt);
@@ -358,7 +417,7 @@ __global__ void __launch_bounds__(kBlock, PP_TCLAIM_CTAS) k_tclaim(Cell *__restr
     for (int it = 0; it < kTClaimItems; ++it) {
 #pragma unroll
       for (int j = 0; j < NR; ++j) {
-        if (win[it] && j < r && j != jstar[it]) {
+        if ((need[it] >> j) & 1u) {
           const u32 pos = s_scan[cj[it][j] >> bsh] + rk[it][j];
           s_key[pos] = x[it];
           s_cell[pos] = cj[it][j];
@@ -388,8 +447,6 @@ __global__ void __launch_bounds__(kBlock, PP_TCLAIM_CTAS) k_tclaim(Cell *__restr
     }
     __syncthreads();
   }
-  const u64 e = block_sum<u64, kBlock>(emptied, s_red);
-  if (tid == 0 && e) atomicAdd(&ctl->emptied, e);
   if (flags) atomicOr(&ctl->flags, flags);
 }
 
@@ -410,7 +467,7 @@ inline size_t tsort_smem_bytes(u32 n_bins) {
 // Phase B1': the round's coarse records of each bin, sorted into its tiles'
 // record regions (one cursor atomic per tile per chunk of kTSortChunk records).
 __global__ void __launch_bounds__(kTSortThreads, 4) k_tsort(TileRoundBufs tb, DecodeCtl *__restrict__ ctl) {
-  if (*(volatile u32 *)&ctl->round == 0) return;  // the first loop iteration only promotes F_1
+  if (*(volatile u32 *)&ctl->round == 0) return;  // round 0: F_1 empty or an error, no work
   extern __shared__ __align__(16) unsigned char smem[];
   const u32 nb = tb.n_bins;
   u32 *s_pre = reinterpret_cast<u32 *>(smem);             // nb + 1: chunks before bin b
@@ -511,7 +568,7 @@ __global__ void __launch_bounds__(kTSortThreads, 4) k_tsort(TileRoundBufs tb, De
 // The tiles with records in the current round (one thread per tile), split
 // into sparse (at most kTSCap records) and dense ones.
 __global__ void __launch_bounds__(kBlock) k_tactive(TileRoundBufs tb, DecodeCtl *__restrict__ ctl) {
-  if (*(volatile u32 *)&ctl->round == 0) return;  // the first loop iteration only promotes F_1
+  if (*(volatile u32 *)&ctl->round == 0) return;  // round 0: F_1 empty or an error, no work
   // the coarse records of this round are all in their tiles now
   for (u32 b = blockIdx.x * kBlock + threadIdx.x; b < tb.n_bins; b += gridDim.x * kBlock) {
     const u64 rb = tb.base[(u64)b << tb.bin_tshift];
@@ -565,7 +622,7 @@ __global__ void __launch_bounds__(kTRThreads, 2) k_tapply(Cell *__restrict__ cel
                                                           TileRoundBufs tb, u64 *__restrict__ fkey,
                                                           u32 *__restrict__ fcell, u32 *__restrict__ bitmap,
                                                           DecodeCtl *__restrict__ ctl) {
-  if (*(volatile u32 *)&ctl->round == 0) return;  // the first loop iteration only promotes F_1
+  if (*(volatile u32 *)&ctl->round == 0) return;  // round 0: F_1 empty or an error, no work
   extern __shared__ __align__(16) unsigned char smem[];
   u64 *s_dkey = reinterpret_cast<u64 *>(smem);
   u64 *s_dchk = s_dkey + kTRCells;
@@ -580,6 +637,7 @@ __global__ void __launch_bounds__(kTRThreads, 2) k_tapply(Cell *__restrict__ cel
   const u32 n_act = *(volatile u32 *)&ctl->n_act_dense;
   const u64 seg0 = tb.fstart[blockIdx.x];
   u64 emptied = 0, dropped = 0;
+  u32 flags = 0;
   if (blockIdx.x < n_act) {  // uniform: blocks with no dense tile skip the set-up
     for (u32 i = tid; i < kTRCells; i += kTRThreads) {
       s_dkey[i] = 0;
@@ -652,10 +710,12 @@ __global__ void __launch_bounds__(kTRThreads, 2) k_tapply(Cell *__restrict__ cel
           const int nc = cnt[q] - (int)s_dcnt[off[q]];
           nk = key[q] ^ s_dkey[off[q]];
           const u64 nchk = chk[q] ^ s_dchk[off[q]];
-          st_cell_cs(cells + c, nk, nchk, nc);
-          emptied += (u64)(long long)((cnt[q] != 0) - (nc != 0));
-          dropped += cnt[q] >= 2 && nc < 2;
           pure = cell_pure(nc, nk, nchk, seed_chk);
+          // a pure cell is stored empty: its one key leaves it next round
+          if (pure) st_cell_cs(cells + c, 0ull, 0ull, 0);
+          else st_cell_cs(cells + c, nk, nchk, nc);
+          emptied += (u64)(long long)((cnt[q] != 0) - (!pure && nc != 0));
+          dropped += cnt[q] >= 2 && nc < 2;
           s_dcnt[off[q]] = 0;
           s_dkey[off[q]] = 0;
           s_dchk[off[q]] = 0;
@@ -666,6 +726,8 @@ __global__ void __launch_bounds__(kTRThreads, 2) k_tapply(Cell *__restrict__ cel
           fkey[seg0 + p] = nk;
           fcell[seg0 + p] = c;
           atomicOr(bitmap + (c >> 5), 1u << (c & 31u));
+        } else if (pure) {
+          flags |= FLAG_INTERNAL;  // cannot happen: a segment holds every push of its block's tiles
         }
       }
     }
@@ -684,6 +746,7 @@ __global__ void __launch_bounds__(kTRThreads, 2) k_tapply(Cell *__restrict__ cel
     tb.fseg[blockIdx.x] = s_seg;
     if (s_seg) atomicAdd(&ctl->n_next, s_seg);
   }
+  if (flags) atomicOr(&ctl->flags, flags);
 }
 
 // The same for the sparse tiles, with a small hash table (open addressing on
@@ -696,7 +759,7 @@ __global__ void __launch_bounds__(kTSThreads, 6) k_tapply_sparse(Cell *__restric
                                                                  TileRoundBufs tb, u64 *__restrict__ fkey,
                                                                  u32 *__restrict__ fcell, u32 *__restrict__ bitmap,
                                                                  DecodeCtl *__restrict__ ctl) {
-  if (*(volatile u32 *)&ctl->round == 0) return;  // the first loop iteration only promotes F_1
+  if (*(volatile u32 *)&ctl->round == 0) return;  // round 0: F_1 empty or an error, no work
   __shared__ u32 h_off[kTSSlots];   // cell offset of the slot, kTSEmpty if free
   __shared__ u64 h_key[kTSSlots], h_chk[kTSSlots];
   __shared__ u32 h_cnt[kTSSlots];
@@ -802,10 +865,12 @@ __global__ void __launch_bounds__(kTSThreads, 6) k_tapply_sparse(Cell *__restric
         const int nc = cnt - (int)h_cnt[slot];
         key ^= h_key[slot];
         chk ^= h_chk[slot];
-        st_cell_cs(cells + c, key, chk, nc);
-        emptied += (u64)(long long)((cnt != 0) - (nc != 0));
-        dropped += cnt >= 2 && nc < 2;
         pure = cell_pure(nc, key, chk, seed_chk);
+        // a pure cell is stored empty: its one key leaves it next round
+        if (pure) st_cell_cs(cells + c, 0ull, 0ull, 0);
+        else st_cell_cs(cells + c, key, chk, nc);
+        emptied += (u64)(long long)((cnt != 0) - (!pure && nc != 0));
+        dropped += cnt >= 2 && nc < 2;
         h_off[slot] = kTSEmpty;
         h_key[slot] = 0;
         h_chk[slot] = 0;
@@ -816,6 +881,8 @@ __global__ void __launch_bounds__(kTSThreads, 6) k_tapply_sparse(Cell *__restric
         fkey[seg0 + p] = key;
         fcell[seg0 + p] = c;
         atomicOr(bitmap + (c >> 5), 1u << (c & 31u));
+      } else if (pure) {
+        flags |= FLAG_INTERNAL;  // cannot happen: a segment holds every push of its block's tiles
       }
     }
     __syncthreads();

@@ -192,7 +192,7 @@ struct IbltKernels {
   const void *sg_scan = nullptr, *sg_peel = nullptr, *sg_filter = nullptr;     // signed (plain only)
   const void *sg_claim = nullptr, *sg_apply = nullptr;                         // signed, binned rounds
   const void *tscan = nullptr, *tclaim = nullptr, *tapply = nullptr;           // tile rounds (plain only)
-  const void *tapply_sparse = nullptr;
+  const void *tapply_sparse = nullptr, *trestore = nullptr;
 };
 
 // The kernel set for a rank code: 3 or 4 = that r; -4 = any r <= 4 (batched
