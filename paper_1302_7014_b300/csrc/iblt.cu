@@ -679,7 +679,7 @@ pp_status ensure_tile_rounds(pp_iblt *t, cudaStream_t s) {
     // at most 4096 pushes per tile it takes) and of k_tapply_sparse (n_seg_s,
     // at most kTSCap pushes per tile)
     t->grid_tapply = persistent_grid(t->k.tapply, kTRThreads, kTApplySmem, 2);
-    t->grid_tsparse = persistent_grid(t->k.tapply_sparse, kTSThreads, 0, 6);
+    t->grid_tsparse = persistent_grid(t->k.tapply_sparse, kTSThreads, 0, kTSCtas);
     t->grid_tscan = t->grid_tapply;
     const uint32_t nd = (uint32_t)t->grid_tapply, nsp = (uint32_t)t->grid_tsparse;
     const uint64_t cap_d = (uint64_t)kTRCells * ((nt + nd - 1) / nd);

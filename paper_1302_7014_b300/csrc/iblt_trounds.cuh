@@ -57,6 +57,10 @@ constexpr int kTSThreads = 256;              // threads per block of k_tapply_sp
 constexpr u32 kTSCap = 512;                  // records of a sparse tile (at most)
 constexpr u32 kTSSlots = 1024;               // hash slots of k_tapply_sparse
 constexpr u32 kTSEmpty = 0xffffffffu;
+#ifndef PP_TSPARSE_CTAS
+#define PP_TSPARSE_CTAS 6
+#endif
+constexpr int kTSCtas = PP_TSPARSE_CTAS;    // resident blocks per SM of k_tapply_sparse
 #ifndef PP_TCLAIM_ITEMS
 #define PP_TCLAIM_ITEMS 2
 #endif
@@ -475,7 +479,6 @@ __global__ void __launch_bounds__(kTSortThreads, 4) k_tsort(TileRoundBufs tb, De
   u16 *s_off = reinterpret_cast<u16 *>(s_key + kTSortChunk);                           // kTSortChunk
   __shared__ u32 s_cnt[kMaxBinTiles], s_scan[kMaxBinTiles + 1], s_tb[kMaxBinTiles];
   __shared__ u32 s_wt[kTSortThreads / 32];
-  __shared__ u32 s_nchunk[1];
   const u32 tid = threadIdx.x;
   const u64 keep = l2_evict_last_policy();
   const u32 ntile = 1u << tb.bin_tshift;
@@ -494,7 +497,6 @@ __global__ void __launch_bounds__(kTSortThreads, 4) k_tsort(TileRoundBufs tb, De
   }
   __syncthreads();
   block_exclusive_scan<kTSortThreads>(s_pre, s_pre, nb, s_wt);
-  (void)s_nchunk;
   const u32 total = s_pre[nb];
   u32 flags = 0;
   for (u32 ch = blockIdx.x; ch < total; ch += gridDim.x) {
@@ -566,7 +568,8 @@ __global__ void __launch_bounds__(kTSortThreads, 4) k_tsort(TileRoundBufs tb, De
 }
 
 // The tiles with records in the current round (one thread per tile), split
-// into sparse (at most kTSCap records) and dense ones.
+// into sparse (at most kTSCap records) and dense ones; the listed records
+// count as consumed from here on (done[t]).
 __global__ void __launch_bounds__(kBlock) k_tactive(TileRoundBufs tb, DecodeCtl *__restrict__ ctl) {
   if (*(volatile u32 *)&ctl->round == 0) return;  // round 0: F_1 empty or an error, no work
   // the coarse records of this round are all in their tiles now
@@ -595,6 +598,7 @@ __global__ void __launch_bounds__(kBlock) k_tactive(TileRoundBufs tb, DecodeCtl 
     const u32 ks = warp_reserve<u32>(any && !dense, &ctl->n_act);
     if (dense) tb.act_d[kd] = TileAct{b + lo, t, hi - lo};
     else if (any) tb.act[ks] = TileAct{b + lo, t, hi - lo};
+    if (any) tb.done[t] = hi;  // this round's apply consumes [lo, hi)
   }
 }
 
@@ -732,10 +736,7 @@ __global__ void __launch_bounds__(kTRThreads, 2) k_tapply(Cell *__restrict__ cel
       }
     }
     __syncthreads();
-    if (tid == 0) {
-      tb.done[t] += nrec;
-      s_nt = 0;
-    }
+    if (tid == 0) s_nt = 0;
     __syncthreads();
   }
   const u64 e = block_sum<u64, kTRThreads>(emptied, s_red);
@@ -755,7 +756,7 @@ __global__ void __launch_bounds__(kTRThreads, 2) k_tapply(Cell *__restrict__ cel
 // b + n_seg_s, ... (at most kTSCap records, hence pushes, each) and writes
 // frontier segment n_seg_d + b.
 template <int R>
-__global__ void __launch_bounds__(kTSThreads, 6) k_tapply_sparse(Cell *__restrict__ cells, const TableArgs tab0,
+__global__ void __launch_bounds__(kTSThreads, kTSCtas) k_tapply_sparse(Cell *__restrict__ cells, const TableArgs tab0,
                                                                  TileRoundBufs tb, u64 *__restrict__ fkey,
                                                                  u32 *__restrict__ fcell, u32 *__restrict__ bitmap,
                                                                  DecodeCtl *__restrict__ ctl) {
@@ -782,13 +783,15 @@ __global__ void __launch_bounds__(kTSThreads, 6) k_tapply_sparse(Cell *__restric
   u64 emptied = 0, dropped = 0;
   constexpr int PER = kTSCap / kTSThreads;
   // the records of the block's next tile are loaded while the current one's
-  // cells are updated
-  TileAct nxt{};
+  // cells are updated, and the list entry of the tile after it one step
+  // earlier still, so that no load waits on another
+  TileAct nxt{}, nxt2{};
   u64 nx[PER];
   u32 no[PER];
   auto load_tile = [&](u32 ai) {
-    if (ai < n_act) nxt = tb.act[ai];
-    else nxt.n = 0;
+    nxt = nxt2;
+    nxt2.n = 0;
+    if (ai + gridDim.x < n_act) nxt2 = tb.act[ai + gridDim.x];
 #pragma unroll
     for (int k = 0; k < PER; ++k) {
       const u32 i = (u32)k * kTSThreads + tid;
@@ -796,6 +799,7 @@ __global__ void __launch_bounds__(kTSThreads, 6) k_tapply_sparse(Cell *__restric
       nx[k] = i < nxt.n ? __ldcs(tb.rec_key + nxt.lo + i) : 0ull;
     }
   };
+  if (blockIdx.x < n_act) nxt2 = tb.act[blockIdx.x];
   load_tile(blockIdx.x);
   for (u32 ai = blockIdx.x; ai < n_act; ai += gridDim.x) {
     const TileAct cur = nxt;
@@ -886,10 +890,7 @@ __global__ void __launch_bounds__(kTSThreads, 6) k_tapply_sparse(Cell *__restric
       }
     }
     __syncthreads();
-    if (tid == 0) {
-      tb.done[t] += nrec;
-      s_ns = 0;
-    }
+    if (tid == 0) s_ns = 0;
     __syncthreads();
   }
   const u64 e = block_sum<u64, kTSThreads>(emptied, s_red);
