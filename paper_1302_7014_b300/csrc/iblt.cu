@@ -691,7 +691,7 @@ pp_status ensure_tile_rounds(pp_iblt *t, cudaStream_t s) {
     u64 *d_start = nullptr;
     cudaError_t e = cudaMalloc((void **)&b.base, ((size_t)nt + 1) * sizeof(u64));
     if (e == cudaSuccess) e = cudaMalloc((void **)&b.pos, (size_t)nt * kTRPosStride * sizeof(u32));
-    if (e == cudaSuccess) e = cudaMalloc((void **)&b.base64, (size_t)nt * sizeof(u32));
+    if (e == cudaSuccess) e = cudaMalloc((void **)&b.base64, ((size_t)nt + 1) * sizeof(u32));
     if (e == cudaSuccess) e = cudaMalloc((void **)&b.done, (size_t)nt * sizeof(u32));
     if (e == cudaSuccess) e = cudaMalloc((void **)&b.sum, (size_t)nt * sizeof(u32));
     if (e == cudaSuccess) e = cudaMalloc((void **)&b.act, (size_t)nt * sizeof(TileAct));
@@ -731,8 +731,8 @@ pp_status ensure_tile_rounds(pp_iblt *t, cudaStream_t s) {
       if (t->sg_exec) cudaGraphExecDestroy(t->sg_exec);
       t->sub_exec = t->sub_exec_binned = t->sg_exec = nullptr;
     }
-    t->smem_tclaim = (size_t)kTClaimChunk * t->k.nr * 12 + ((size_t)nd + nsp + 1) * 4 + (3 * (size_t)b.n_bins + 1) * 4;
-    t->grid_tclaim = persistent_grid(t->k.tclaim, kBlock, t->smem_tclaim, t->opt.ctas_per_sm);
+    t->smem_tclaim = (size_t)kTClaimChunk * t->k.nr * 12 + ((size_t)nd + nsp + 1) * 4 + (4 * (size_t)b.n_bins + 2) * 4;
+    t->grid_tclaim = persistent_grid(t->k.tclaim, kTClaimThreads, t->smem_tclaim, t->opt.ctas_per_sm);
     t->smem_tsort = tsort_smem_bytes(b.n_bins);
     t->grid_tsort = persistent_grid((const void *)k_tsort, kTSortThreads, t->smem_tsort, 8);
     ++t->rec_gen;
@@ -836,7 +836,7 @@ pp_status build_tile_graph(pp_iblt *t) {
   if (st != PP_OK) goto done;
   ea.cond = h;
   ea.bind();
-  st = add_kernel(&n_claim, body, nullptr, 0, t->k.tclaim, t->grid_tclaim, kBlock, smem_claim, ta.claim);
+  st = add_kernel(&n_claim, body, nullptr, 0, t->k.tclaim, t->grid_tclaim, kTClaimThreads, smem_claim, ta.claim);
   if (st != PP_OK) goto done;
   st = add_kernel(&n_sort, body, &n_claim, 1, (const void *)k_tsort, t->grid_tsort, kTSortThreads, t->smem_tsort,
                   ta.sort);
@@ -870,7 +870,7 @@ pp_status run_tile_host_loop(pp_iblt *t, cudaStream_t s) {
   PP_CUDA(cudaLaunchKernel(t->k.tscan, dim3(t->grid_tscan), dim3(kTRThreads), ta.scan, 0, s));
   PP_CUDA(cudaLaunchKernel((const void *)k_tprefix, dim3(1), dim3(1024), ta.prefix, 0, s));
   for (;;) {
-    PP_CUDA(cudaLaunchKernel(t->k.tclaim, dim3(t->grid_tclaim), dim3(kBlock), ta.claim, smem_claim, s));
+    PP_CUDA(cudaLaunchKernel(t->k.tclaim, dim3(t->grid_tclaim), dim3(kTClaimThreads), ta.claim, smem_claim, s));
     PP_CUDA(cudaLaunchKernel((const void *)k_tsort, dim3(t->grid_tsort), dim3(kTSortThreads), ta.sort,
                              t->smem_tsort, s));
     PP_CUDA(cudaLaunchKernel((const void *)k_tactive, dim3(grid_act), dim3(kBlock), ta.active, 0, s));
@@ -1212,7 +1212,7 @@ pp_status pp_workspace_size(uint64_t n_cells, uint32_t r, uint64_t m_keys, const
   if (rounds_tiles) {
     const uint64_t nt = (n + kTRCells - 1) / kTRCells;
     tile_round_bytes = ((uint64_t)r * m_keys + (uint64_t)kTRAlign * nt) * (2 * sizeof(u64) + sizeof(u16) + sizeof(u32)) +
-                       (nt + 1) * sizeof(u64) + nt * (kTRPosStride * sizeof(u32) + 2 * sizeof(u32) +
+                       (nt + 1) * (sizeof(u64) + sizeof(u32)) + nt * (kTRPosStride * sizeof(u32) + 2 * sizeof(u32) +
                                                       2 * sizeof(TileAct));
   }
   const bool rounds_binned = !rounds_tiles && (o.binned == 1 || (o.binned == 0 && n >= (1ull << 21)));

@@ -65,10 +65,14 @@ constexpr int kTSCtas = PP_TSPARSE_CTAS;    // resident blocks per SM of k_tappl
 #define PP_TCLAIM_ITEMS 2
 #endif
 #ifndef PP_TCLAIM_CTAS
-#define PP_TCLAIM_CTAS 4
+#define PP_TCLAIM_CTAS 2
 #endif
+#ifndef PP_TCLAIM_THREADS
+#define PP_TCLAIM_THREADS 512
+#endif
+constexpr int kTClaimThreads = PP_TCLAIM_THREADS;        // threads per block of k_tclaim
 constexpr int kTClaimItems = PP_TCLAIM_ITEMS;            // frontier entries per thread per chunk
-constexpr int kTClaimChunk = kBlock * kTClaimItems;
+constexpr int kTClaimChunk = kTClaimThreads * kTClaimItems;
 
 // A tile with records in the current round: records [lo, lo + n) (absolute slots).
 struct TileAct {
@@ -81,7 +85,7 @@ struct TileRoundBufs {
   u64 *rec_key;   // records: the key
   u16 *rec_off;   // records: cell offset in its tile
   u64 *base;      // per tile: first record slot of its region (n_tiles + 1 entries)
-  u32 *base64;    // per tile: base / kTRAlign (regions start on multiples of kTRAlign)
+  u32 *base64;    // per tile and one past the last: base / kTRAlign (regions start on multiples of kTRAlign)
   u32 *pos;       // per tile (stride kTRPosStride): records written this decode
   u32 *done;      // per tile: records applied this decode
   u32 *sum;       // per tile: sum of counts at the decode's start (scan output)
@@ -150,7 +154,7 @@ __device__ __forceinline__ void block_exclusive_scan(const u32 *in, u32 *out, u3
 // Runs n_seg_d blocks; block b takes tiles b, b + n_seg_d, ... (at most
 // 4096 pushes each) and writes segment b.
 template <int R>
-__global__ void __launch_bounds__(kTRThreads) k_tscan(Cell *__restrict__ cells, const TableArgs tab0,
+__global__ void __launch_bounds__(kTRThreads, 2) k_tscan(Cell *__restrict__ cells, const TableArgs tab0,
                                                       u64 *__restrict__ fkey, u32 *__restrict__ fcell,
                                                       u32 *__restrict__ bitmap, TileRoundBufs tb,
                                                       DecodeCtl *__restrict__ ctl) {
@@ -166,17 +170,26 @@ __global__ void __launch_bounds__(kTRThreads) k_tscan(Cell *__restrict__ cells, 
   for (u32 t = blockIdx.x; t < tb.n_tiles; t += gridDim.x) {
     const u32 c0 = t << kTRShift;
     long long sum = 0;
-#pragma unroll 4
+    // every load of the tile is issued before its first store (the cell
+    // accesses are volatile asm, kept in program order)
+    u64 keys[kTRScanItems], chks[kTRScanItems];
+    int cnts[kTRScanItems];
+#pragma unroll
+    for (int it = 0; it < kTRScanItems; ++it) {
+      const u32 c = c0 + (u32)it * kTRThreads + tid;
+      keys[it] = chks[it] = 0;
+      cnts[it] = 0;
+      if (c < n) ld_cell_cs(cells + c, keys[it], chks[it], cnts[it]);
+    }
+#pragma unroll
     for (int it = 0; it < kTRScanItems; ++it) {
       const u32 c = c0 + (u32)it * kTRThreads + tid;
       const bool valid = c < n;
       bool pure = false;
-      u64 key = 0;
+      const u64 key = keys[it];
       if (valid) {
-        u64 chk;
-        int cnt;
-        ld_cell_cs(cells + c, key, chk, cnt);
-        pure = cell_pure(cnt, key, chk, seed_chk);
+        const int cnt = cnts[it];
+        pure = cell_pure(cnt, key, chks[it], seed_chk);
         alive += cnt >= 2;
         nonempty += cnt != 0;
         sum += cnt;
@@ -262,6 +275,7 @@ __global__ void __launch_bounds__(1024) k_tprefix(TileRoundBufs tb, DecodeCtl *_
   }
   if (tid == 0) {
     tb.base[tb.n_tiles] = s_w[32];
+    tb.base64[tb.n_tiles] = (u32)(s_w[32] / kTRAlign);
     u32 fl = *(volatile u32 *)&ctl->flags;
     if (s_w[32] > tb.rec_cap) {
       atomicOr(&ctl->flags, (u32)FLAG_CAPACITY);
@@ -310,11 +324,11 @@ __global__ void __launch_bounds__(kBlock) k_trestore(Cell *__restrict__ cells, c
 // sorted by coarse bin (2^bin_tshift tiles), in contiguous runs with one cursor
 // atomic per bin per chunk; k_tsort then sorts each bin's records into its
 // tiles.  Dynamic shared memory: the prefix of the frontier's segment sizes
-// (n_seg + 1 u32), the chunk's records (kTClaimChunk * NR keys and cells), and
-// per bin its count, its offset in the chunk and its run's first slot
-// (3 * n_bins + 1 u32).
+// (n_seg + 1 u32), the chunk's records (kTClaimChunk * NR keys and cells), per
+// bin its count, its offset in the chunk and its run's first slot (3 * n_bins
+// + 1 u32), and the bins' region bounds / kTRAlign (n_bins + 1 u32).
 template <int R>
-__global__ void __launch_bounds__(kBlock, PP_TCLAIM_CTAS) k_tclaim(Cell *__restrict__ cells, const TableArgs tab0,
+__global__ void __launch_bounds__(kTClaimThreads, PP_TCLAIM_CTAS) k_tclaim(Cell *__restrict__ cells, const TableArgs tab0,
                                                       const u64 *__restrict__ fkey,
                                                       const u32 *__restrict__ fcell,
                                                       const u32 *__restrict__ bitmap, TileRoundBufs tb,
@@ -330,8 +344,9 @@ __global__ void __launch_bounds__(kBlock, PP_TCLAIM_CTAS) k_tclaim(Cell *__restr
   u32 *s_hist = s_pre + ns + 1;                         // nb
   u32 *s_scan = s_hist + nb;                            // nb + 1
   u32 *s_base = s_scan + nb + 1;                        // nb
+  u32 *s_bb = s_base + nb;                              // nb + 1
   __shared__ u64 s_out[kTClaimChunk];
-  __shared__ u32 s_nout, s_wt[kBlock / 32], s_seg0;
+  __shared__ u32 s_nout, s_wt[kTClaimThreads / 32], s_seg0;
   __shared__ u64 s_obase;
   const u32 tid = threadIdx.x;
   const u32 n = *(volatile u32 *)&ctl->n_front;
@@ -341,10 +356,11 @@ __global__ void __launch_bounds__(kBlock, PP_TCLAIM_CTAS) k_tclaim(Cell *__restr
   const u64 keep = l2_evict_last_policy();
   const int r = rank_of<R>(tab0);
   const u32 bsh = kTRShift + tb.bin_tshift;  // cell -> coarse bin
-  block_exclusive_scan<kBlock>(tb.fseg, s_pre, ns, s_wt);
+  for (u32 b = tid; b <= nb; b += kTClaimThreads) s_bb[b] = tb.base64[min(b << tb.bin_tshift, tb.n_tiles)];
+  block_exclusive_scan<kTClaimThreads>(tb.fseg, s_pre, ns, s_wt);
   u32 flags = 0;
   for (u64 c0 = (u64)blockIdx.x * kTClaimChunk; c0 < n; c0 += (u64)gridDim.x * kTClaimChunk) {
-    for (u32 i = tid; i < nb; i += kBlock) s_hist[i] = 0;
+    for (u32 i = tid; i < nb; i += kTClaimThreads) s_hist[i] = 0;
     if (tid == 0) {
       s_nout = 0;
       // segment of the chunk's first entry: the last k with s_pre[k] <= c0
@@ -364,7 +380,7 @@ __global__ void __launch_bounds__(kBlock, PP_TCLAIM_CTAS) k_tclaim(Cell *__restr
     const u32 a0 = s_seg0;
 #pragma unroll
     for (int it = 0; it < kTClaimItems; ++it) {
-      const u32 i = (u32)(c0 + (u64)it * kBlock + tid);
+      const u32 i = (u32)(c0 + (u64)it * kTClaimThreads + tid);
       win[it] = i < n;
       u64 src = 0;
       if (win[it]) {
@@ -410,8 +426,8 @@ __global__ void __launch_bounds__(kBlock, PP_TCLAIM_CTAS) k_tclaim(Cell *__restr
         rk[it][j] = ((need[it] >> j) & 1u) ? atomicAdd(s_hist + (cj[it][j] >> bsh), 1u) : 0u;
     }
     __syncthreads();
-    block_exclusive_scan<kBlock>(s_hist, s_scan, nb, s_wt);
-    for (u32 k = tid; k < nb; k += kBlock) {
+    block_exclusive_scan<kTClaimThreads>(s_hist, s_scan, nb, s_wt);
+    for (u32 k = tid; k < nb; k += kTClaimThreads) {
       const u32 h = s_hist[k];
       s_base[k] = h ? atomicAdd(tb.cpos + (u64)k * kTRPosStride, h) : 0u;
     }
@@ -431,12 +447,10 @@ __global__ void __launch_bounds__(kBlock, PP_TCLAIM_CTAS) k_tclaim(Cell *__restr
     __syncthreads();
     // contiguous runs per coarse bin; the bin's region is its tiles' regions
     const u32 total = s_scan[nb];
-    for (u32 p = tid; p < total; p += kBlock) {
+    for (u32 p = tid; p < total; p += kTClaimThreads) {
       const u32 bn = s_cell[p] >> bsh;
-      const u64 rb = tb.base[(u64)bn << tb.bin_tshift];
-      const u32 te = min((bn + 1) << tb.bin_tshift, tb.n_tiles);
-      const u64 dst = rb + s_base[bn] + (p - s_scan[bn]);
-      if (dst < tb.base[te] && dst < tb.rec_cap) {
+      const u64 dst = (u64)s_bb[bn] * kTRAlign + s_base[bn] + (p - s_scan[bn]);
+      if (dst < (u64)s_bb[bn + 1] * kTRAlign && dst < tb.rec_cap) {
         st_l2_policy(tb.crec_key + dst, s_key[p], keep);
         st_l2_policy(tb.crec_cell + dst, s_cell[p], keep);
       } else {
@@ -445,7 +459,7 @@ __global__ void __launch_bounds__(kBlock, PP_TCLAIM_CTAS) k_tclaim(Cell *__restr
     }
     const u32 no = s_nout;
     const u64 ob = s_obase;
-    for (u32 q = tid; q < no; q += kBlock) {
+    for (u32 q = tid; q < no; q += kTClaimThreads) {
       if (ob + q < out_cap) out[ob + q] = s_out[q];
       else flags |= FLAG_CAPACITY;
     }
@@ -463,10 +477,11 @@ constexpr u32 kTSortChunk = kTSortThreads * kTSortPer;  // coarse records per wo
 constexpr u32 kMaxBinTiles = 512;                         // tiles per coarse bin (at most)
 
 // Dynamic shared memory of k_tsort: the chunk prefix over the bins (n_bins + 1
-// u32) and the chunk's records sorted by tile (kTSortChunk keys and offsets).
-inline size_t tsort_smem_bytes(u32 n_bins) {
-  return ((size_t)n_bins + 1) * 4 + (size_t)kTSortChunk * (8 + 2);
-}
+// u32), per bin the round's first and end record and its region's start /
+// kTRAlign (3 n_bins + 1 u32), and the chunk's records sorted by tile
+// (kTSortChunk keys and offsets).
+__host__ __device__ inline size_t tsort_head_bytes(u32 n_bins) { return ((4 * (size_t)n_bins + 2) * 4 + 15) / 16 * 16; }
+inline size_t tsort_smem_bytes(u32 n_bins) { return tsort_head_bytes(n_bins) + (size_t)kTSortChunk * (8 + 2); }
 
 // Phase B1': the round's coarse records of each bin, sorted into its tiles'
 // record regions (one cursor atomic per tile per chunk of kTSortChunk records).
@@ -475,9 +490,13 @@ __global__ void __launch_bounds__(kTSortThreads, 4) k_tsort(TileRoundBufs tb, De
   extern __shared__ __align__(16) unsigned char smem[];
   const u32 nb = tb.n_bins;
   u32 *s_pre = reinterpret_cast<u32 *>(smem);             // nb + 1: chunks before bin b
-  u64 *s_key = reinterpret_cast<u64 *>(smem + (((size_t)nb + 1) * 4 + 15) / 16 * 16);  // kTSortChunk
-  u16 *s_off = reinterpret_cast<u16 *>(s_key + kTSortChunk);                           // kTSortChunk
+  u32 *s_blo = s_pre + nb + 1;                            // nb: the round's first record of bin b
+  u32 *s_bhi = s_blo + nb;                                // nb: its end
+  u32 *s_bb = s_bhi + nb;                                 // nb: region start of bin b / kTRAlign
+  u64 *s_key = reinterpret_cast<u64 *>(smem + tsort_head_bytes(nb));  // kTSortChunk
+  u16 *s_off = reinterpret_cast<u16 *>(s_key + kTSortChunk);          // kTSortChunk
   __shared__ u32 s_cnt[kMaxBinTiles], s_scan[kMaxBinTiles + 1], s_tb[kMaxBinTiles];
+  __shared__ u32 s_tbase[kMaxBinTiles + 1];  // the chunk's bin: region start of each tile / kTRAlign
   __shared__ u32 s_wt[kTSortThreads / 32];
   const u32 tid = threadIdx.x;
   const u64 keep = l2_evict_last_policy();
@@ -494,6 +513,9 @@ __global__ void __launch_bounds__(kTSortThreads, 4) k_tsort(TileRoundBufs tb, De
   for (u32 b = tid; b < nb; b += kTSortThreads) {
     const u32 lo = tb.cdone[b], hi = bin_end(b);
     s_pre[b] = hi > lo ? (hi - lo + kTSortChunk - 1) / kTSortChunk : 0u;
+    s_blo[b] = lo;
+    s_bhi[b] = hi;
+    s_bb[b] = tb.base64[b << tb.bin_tshift];
   }
   __syncthreads();
   block_exclusive_scan<kTSortThreads>(s_pre, s_pre, nb, s_wt);
@@ -508,12 +530,10 @@ __global__ void __launch_bounds__(kTSortThreads, 4) k_tsort(TileRoundBufs tb, De
       else bb = mid;
     }
     const u32 b = a;
-    const u64 rb = tb.base[(u64)b << tb.bin_tshift];
-    const u32 lo = tb.cdone[b] + (ch - s_pre[b]) * kTSortChunk;
-    const u32 hi = min(lo + kTSortChunk, bin_end(b));
+    const u64 rb = (u64)s_bb[b] * kTRAlign;
+    const u32 lo = s_blo[b] + (ch - s_pre[b]) * kTSortChunk;
+    const u32 hi = min(lo + kTSortChunk, s_bhi[b]);
     const u32 t0 = b << tb.bin_tshift;
-    for (u32 i = tid; i < ntile; i += kTSortThreads) s_cnt[i] = 0;
-    __syncthreads();
     u64 x[kTSortPer];
     u32 lt[kTSortPer], rk[kTSortPer], cl[kTSortPer];
 #pragma unroll
@@ -523,6 +543,10 @@ __global__ void __launch_bounds__(kTSortThreads, 4) k_tsort(TileRoundBufs tb, De
       x[k] = v ? __ldcs(tb.crec_key + rb + i) : 0ull;
       cl[k] = v ? __ldcs(tb.crec_cell + rb + i) : 0xffffffffu;
     }
+    // the bin's tile bounds, loaded while the records are in flight
+    for (u32 i = tid; i <= ntile; i += kTSortThreads) s_tbase[i] = tb.base64[min(t0 + i, tb.n_tiles)];
+    for (u32 i = tid; i < ntile; i += kTSortThreads) s_cnt[i] = 0;
+    __syncthreads();
 #pragma unroll
     for (int k = 0; k < kTSortPer; ++k) {
       lt[k] = cl[k] != 0xffffffffu ? (cl[k] >> kTRShift) - t0 : 0u;
@@ -553,9 +577,8 @@ __global__ void __launch_bounds__(kTSortThreads, 4) k_tsort(TileRoundBufs tb, De
         if (s_scan[mid] <= p) l = mid;
         else h2 = mid;
       }
-      const u32 t = t0 + l;
-      const u64 dst = tb.base[t] + s_tb[l] + (p - s_scan[l]);
-      if (dst < tb.base[t + 1] && dst < tb.rec_cap) {
+      const u64 dst = (u64)s_tbase[l] * kTRAlign + s_tb[l] + (p - s_scan[l]);
+      if (dst < (u64)s_tbase[l + 1] * kTRAlign && dst < tb.rec_cap) {
         st_l2_policy(tb.rec_key + dst, s_key[p], keep);
         tb.rec_off[dst] = s_off[p];
       } else {
@@ -852,18 +875,30 @@ __global__ void __launch_bounds__(kTSThreads, kTSCtas) k_tapply_sparse(Cell *__r
     load_tile(ai + gridDim.x);
     const u32 ns = s_ns;
     const u32 c0 = t << kTRShift;
+    // both cells' loads before either store (the cell accesses are volatile
+    // asm, kept in program order)
+    u32 slots[PER], cs[PER];
+    u64 keys[PER], chks[PER];
+    int cnts[PER];
+#pragma unroll
+    for (int k = 0; k < PER; ++k) {
+      const u32 q = (u32)k * kTSThreads + tid;
+      slots[k] = cs[k] = 0;
+      keys[k] = chks[k] = 0;
+      cnts[k] = 0;
+      if (q < ns) {
+        slots[k] = s_slot[q];
+        cs[k] = c0 + h_off[slots[k]];
+        ld_cell_cg(cells + cs[k], keys[k], chks[k], cnts[k]);
+      }
+    }
 #pragma unroll
     for (int k = 0; k < PER; ++k) {
       const u32 q = (u32)k * kTSThreads + tid;
       const bool v = q < ns;
-      u32 slot = 0, c = 0;
-      u64 key = 0, chk = 0;
-      int cnt = 0;
-      if (v) {
-        slot = s_slot[q];
-        c = c0 + h_off[slot];
-        ld_cell_cg(cells + c, key, chk, cnt);
-      }
+      const u32 slot = slots[k], c = cs[k];
+      u64 key = keys[k], chk = chks[k];
+      const int cnt = cnts[k];
       bool pure = false;
       if (v) {
         const int nc = cnt - (int)h_cnt[slot];
