@@ -70,6 +70,17 @@ void make_table_args(TableArgs &a, uint64_t n_cells, uint32_t r, uint64_t seed, 
   a.start_round = 1;
 }
 
+void allow_max_dynamic_smem(const void *fn) {
+  int dev = 0, optin = 0;
+  cudaFuncAttributes fa{};
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess ||
+      cudaFuncGetAttributes(&fa, fn) != cudaSuccess)
+    return;
+  const int room = optin - (int)fa.sharedSizeBytes;
+  if (room > 0) cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, room);
+}
+
 int persistent_grid(const void *fn, int block, size_t smem, uint32_t ctas_per_sm) {
   int occ = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, block, smem) != cudaSuccess || occ < 1)

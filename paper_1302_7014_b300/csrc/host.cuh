@@ -39,4 +39,8 @@ inline cudaStream_t as_stream(void *s) { return reinterpret_cast<cudaStream_t>(s
 // Grid of a persistent kernel: resident CTAs per SM x SMs (at least 1 per SM).
 int persistent_grid(const void *fn, int block, size_t smem, uint32_t ctas_per_sm);
 
+// Lets fn take as much dynamic shared memory as the device allows a block
+// beside fn's static shared memory.
+void allow_max_dynamic_smem(const void *fn);
+
 }  // namespace pp

@@ -65,8 +65,8 @@ static IbltKernels iblt_kernels_t() {
     if (!tattr) {
       cudaFuncSetAttribute((const void *)k_tapply<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)kTApplySmem);
-      cudaFuncSetAttribute((const void *)k_tclaim<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-      cudaFuncSetAttribute((const void *)k_tsort, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+      allow_max_dynamic_smem((const void *)k_tclaim<R>);
+      allow_max_dynamic_smem((const void *)k_tsort);
       tattr = true;
     }
   }

@@ -108,6 +108,26 @@ struct TileRoundBufs {
   u32 pad;
 };
 
+// First entry of frontier segment k: the dense segments (cap_d entries each)
+// come first, then the sparse ones (cap_s each).
+__device__ __forceinline__ u64 seg_start(const TileRoundBufs &tb, u32 k) {
+  return k < tb.n_seg_d ? (u64)k * tb.cap_d : (u64)tb.n_seg_d * tb.cap_d + (u64)(k - tb.n_seg_d) * tb.cap_s;
+}
+
+// Asynchronous global -> shared copies (cp.async): the next chunk's frontier
+// entries are fetched while the current chunk is claimed.
+__device__ __forceinline__ void cp_async_8(void *dst_shared, const void *src) {
+  const u32 d = (u32)__cvta_generic_to_shared(dst_shared);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_4(void *dst_shared, const void *src) {
+  const u32 d = (u32)__cvta_generic_to_shared(dst_shared);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+// waits until at most one group (the most recently committed) is pending
+__device__ __forceinline__ void cp_async_wait_prev() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+
 // Exclusive prefix of in[0..n) into out[0..n) and the total into out[n], by
 // one block of B threads (thread i takes a contiguous share).  in may be
 // global or shared; s_wt holds B / 32 words.
@@ -346,7 +366,9 @@ __global__ void __launch_bounds__(kTClaimThreads, PP_TCLAIM_CTAS) k_tclaim(Cell 
   u32 *s_base = s_scan + nb + 1;                        // nb
   u32 *s_bb = s_base + nb;                              // nb + 1
   __shared__ u64 s_out[kTClaimChunk];
-  __shared__ u32 s_nout, s_wt[kTClaimThreads / 32], s_seg0;
+  __shared__ u64 s_fx[2][kTClaimChunk];   // frontier entries of this chunk and the next
+  __shared__ u32 s_fc[2][kTClaimChunk];
+  __shared__ u32 s_nout, s_wt[kTClaimThreads / 32], s_segn;
   __shared__ u64 s_obase;
   const u32 tid = threadIdx.x;
   const u32 n = *(volatile u32 *)&ctl->n_front;
@@ -358,39 +380,58 @@ __global__ void __launch_bounds__(kTClaimThreads, PP_TCLAIM_CTAS) k_tclaim(Cell 
   const u32 bsh = kTRShift + tb.bin_tshift;  // cell -> coarse bin
   for (u32 b = tid; b <= nb; b += kTClaimThreads) s_bb[b] = tb.base64[min(b << tb.bin_tshift, tb.n_tiles)];
   block_exclusive_scan<kTClaimThreads>(tb.fseg, s_pre, ns, s_wt);
+  // segment of entry c: the last k with s_pre[k] <= c
+  auto seg_of = [&](u64 c) -> u32 {
+    u32 a = 0, b = ns;
+    while (b - a > 1) {
+      const u32 mid = (a + b) >> 1;
+      if (s_pre[mid] <= (u32)c) a = mid;
+      else b = mid;
+    }
+    return a;
+  };
+  // copies this thread's frontier entries of the chunk at c into buffer bf
+  // (segments hold thousands of entries: a chunk spans one or two)
+  auto fetch = [&](u64 c, u32 a0, int bf) {
+#pragma unroll
+    for (int it = 0; it < kTClaimItems; ++it) {
+      const u32 i = (u32)(c + (u64)it * kTClaimThreads + tid);
+      if (i < n) {
+        u32 a = a0;
+        while (a + 1 < ns && s_pre[a + 1] <= i) ++a;
+        const u64 src = seg_start(tb, a) + (i - s_pre[a]);
+        cp_async_8(&s_fx[bf][it * kTClaimThreads + tid], fkey + src);
+        cp_async_4(&s_fc[bf][it * kTClaimThreads + tid], fcell + src);
+      }
+    }
+    cp_async_commit();
+  };
   u32 flags = 0;
-  for (u64 c0 = (u64)blockIdx.x * kTClaimChunk; c0 < n; c0 += (u64)gridDim.x * kTClaimChunk) {
+  const u64 stride = (u64)gridDim.x * kTClaimChunk;
+  int buf = 0;
+  if ((u64)blockIdx.x * kTClaimChunk < n) fetch((u64)blockIdx.x * kTClaimChunk, seg_of((u64)blockIdx.x * kTClaimChunk), 0);
+  for (u64 c0 = (u64)blockIdx.x * kTClaimChunk; c0 < n; c0 += stride, buf ^= 1) {
+    const u64 c1 = c0 + stride;
     for (u32 i = tid; i < nb; i += kTClaimThreads) s_hist[i] = 0;
     if (tid == 0) {
       s_nout = 0;
-      // segment of the chunk's first entry: the last k with s_pre[k] <= c0
-      u32 a = 0, b = ns;
-      while (b - a > 1) {
-        const u32 mid = (a + b) >> 1;
-        if (s_pre[mid] <= (u32)c0) a = mid;
-        else b = mid;
-      }
-      s_seg0 = a;
+      s_segn = c1 < n ? seg_of(c1) : 0u;
     }
     __syncthreads();
+    // the next chunk's entries travel while this one is claimed
+    if (c1 < n) fetch(c1, s_segn, buf ^ 1);
+    else cp_async_commit();  // an empty group keeps the wait below uniform
+    cp_async_wait_prev();
     u64 x[kTClaimItems];
     u32 c[kTClaimItems], cj[kTClaimItems][NR], rk[kTClaimItems][NR];
     bool win[kTClaimItems];
     u32 need[kTClaimItems];  // bit j: x's cell in sub-table j gets a record
-    const u32 a0 = s_seg0;
 #pragma unroll
     for (int it = 0; it < kTClaimItems; ++it) {
       const u32 i = (u32)(c0 + (u64)it * kTClaimThreads + tid);
       win[it] = i < n;
-      u64 src = 0;
-      if (win[it]) {
-        // segments hold thousands of entries: a chunk spans one or two
-        u32 a = a0;
-        while (a + 1 < ns && s_pre[a + 1] <= i) ++a;
-        src = tb.fstart[a] + (i - s_pre[a]);
-      }
-      x[it] = win[it] ? __ldcs(fkey + src) : 0ull;
-      c[it] = win[it] ? __ldcs(fcell + src) : 0u;
+      x[it] = win[it] ? s_fx[buf][it * kTClaimThreads + tid] : 0ull;
+      c[it] = win[it] ? s_fc[buf][it * kTClaimThreads + tid] : 0u;
     }
 #pragma unroll
     for (int it = 0; it < kTClaimItems; ++it) {
@@ -657,7 +698,7 @@ __global__ void __launch_bounds__(kTRThreads, 2) k_tapply(Cell *__restrict__ cel
   u16 *s_touch = reinterpret_cast<u16 *>(s_dcnt + kTRCells);
   u32 *s_dkey32 = reinterpret_cast<u32 *>(s_dkey);
   u32 *s_dchk32 = reinterpret_cast<u32 *>(s_dchk);
-  __shared__ u32 s_nt, s_seg;
+  __shared__ u32 s_nt[2], s_seg;  // touched cells of the current tile: two counters, used in turn
   __shared__ u64 s_red[kTRThreads / 32];
   const u32 tid = threadIdx.x;
   const u64 seed_chk = tab0.seed[rank_of<R>(tab0)];
@@ -672,11 +713,12 @@ __global__ void __launch_bounds__(kTRThreads, 2) k_tapply(Cell *__restrict__ cel
       s_dcnt[i] = 0;
     }
   }
-  if (tid == 0) s_nt = 0, s_seg = 0;
+  if (tid == 0) s_nt[0] = s_nt[1] = 0, s_seg = 0;
   __syncthreads();
   TileAct nxt{};
   if (blockIdx.x < n_act) nxt = tb.act_d[blockIdx.x];
-  for (u32 ai = blockIdx.x; ai < n_act; ai += gridDim.x) {
+  u32 par = 0;
+  for (u32 ai = blockIdx.x; ai < n_act; ai += gridDim.x, par ^= 1) {
     const TileAct cur = nxt;
     if (ai + gridDim.x < n_act) nxt = tb.act_d[ai + gridDim.x];  // the next tile's entry, early
     const u64 b = cur.lo;
@@ -704,7 +746,7 @@ __global__ void __launch_bounds__(kTRThreads, 2) k_tapply(Cell *__restrict__ cel
           atomicXor(s_dchk32 + 2 * off, (u32)cs);
           atomicXor(s_dchk32 + 2 * off + 1, (u32)(cs >> 32));
         }
-        const u32 q = warp_reserve<u32>(first, &s_nt);
+        const u32 q = warp_reserve<u32>(first, &s_nt[par]);
         if (first) s_touch[q] = (u16)off;
       }
     }
@@ -712,7 +754,9 @@ __global__ void __launch_bounds__(kTRThreads, 2) k_tapply(Cell *__restrict__ cel
     discard_records(tb, b, nrec, tid, kTRThreads);
     // one read-modify-write per touched cell (the loads of a thread's cells in
     // flight together); pure results join F_{t+1} in this block's segment
-    const u32 nt = s_nt;
+    const u32 nt = s_nt[par];
+    // the other counter was last read before the barrier above: ready it for the next tile
+    if (tid == 0) s_nt[par ^ 1] = 0;
     const u32 c0 = t << kTRShift;
     for (u32 k0 = 0; k0 < nt; k0 += kTRCellsPerThread * kTRThreads) {
       u32 off[kTRCellsPerThread];
@@ -759,8 +803,6 @@ __global__ void __launch_bounds__(kTRThreads, 2) k_tapply(Cell *__restrict__ cel
       }
     }
     __syncthreads();
-    if (tid == 0) s_nt = 0;
-    __syncthreads();
   }
   const u64 e = block_sum<u64, kTRThreads>(emptied, s_red);
   const u64 d = block_sum<u64, kTRThreads>(dropped, s_red);
@@ -788,7 +830,7 @@ __global__ void __launch_bounds__(kTSThreads, kTSCtas) k_tapply_sparse(Cell *__r
   __shared__ u64 h_key[kTSSlots], h_chk[kTSSlots];
   __shared__ u32 h_cnt[kTSSlots];
   __shared__ u16 s_slot[kTSCap];    // the slots in use
-  __shared__ u32 s_ns, s_seg;
+  __shared__ u32 s_ns[2], s_seg;  // touched cells of the current tile: two counters, used in turn
   __shared__ u64 s_red[kTSThreads / 32];
   const u32 tid = threadIdx.x;
   const u64 seed_chk = tab0.seed[rank_of<R>(tab0)];
@@ -801,7 +843,7 @@ __global__ void __launch_bounds__(kTSThreads, kTSCtas) k_tapply_sparse(Cell *__r
     h_chk[i] = 0;
     h_cnt[i] = 0;
   }
-  if (tid == 0) s_ns = 0, s_seg = 0;
+  if (tid == 0) s_ns[0] = s_ns[1] = 0, s_seg = 0;
   __syncthreads();
   u64 emptied = 0, dropped = 0;
   constexpr int PER = kTSCap / kTSThreads;
@@ -824,7 +866,8 @@ __global__ void __launch_bounds__(kTSThreads, kTSCtas) k_tapply_sparse(Cell *__r
   };
   if (blockIdx.x < n_act) nxt2 = tb.act[blockIdx.x];
   load_tile(blockIdx.x);
-  for (u32 ai = blockIdx.x; ai < n_act; ai += gridDim.x) {
+  u32 par = 0;
+  for (u32 ai = blockIdx.x; ai < n_act; ai += gridDim.x, par ^= 1) {
     const TileAct cur = nxt;
     const u64 b = cur.lo;
     const u32 nrec = cur.n, t = cur.tile;
@@ -867,13 +910,15 @@ __global__ void __launch_bounds__(kTSThreads, kTSCtas) k_tapply_sparse(Cell *__r
         atomicXor(reinterpret_cast<u32 *>(h_chk + slot), (u32)cs);
         atomicXor(reinterpret_cast<u32 *>(h_chk + slot) + 1, (u32)(cs >> 32));
       }
-      const u32 q = warp_reserve<u32>(fresh, &s_ns);
+      const u32 q = warp_reserve<u32>(fresh, &s_ns[par]);
       if (fresh) s_slot[q] = (u16)slot;
     }
     __syncthreads();
     discard_records(tb, b, nrec, tid, kTSThreads);
     load_tile(ai + gridDim.x);
-    const u32 ns = s_ns;
+    const u32 ns = s_ns[par];
+    // the other counter was last read before the barrier above: ready it for the next tile
+    if (tid == 0) s_ns[par ^ 1] = 0;
     const u32 c0 = t << kTRShift;
     // both cells' loads before either store (the cell accesses are volatile
     // asm, kept in program order)
@@ -924,8 +969,6 @@ __global__ void __launch_bounds__(kTSThreads, kTSCtas) k_tapply_sparse(Cell *__r
         flags |= FLAG_INTERNAL;  // cannot happen: a segment holds every push of its block's tiles
       }
     }
-    __syncthreads();
-    if (tid == 0) s_ns = 0;
     __syncthreads();
   }
   const u64 e = block_sum<u64, kTSThreads>(emptied, s_red);
