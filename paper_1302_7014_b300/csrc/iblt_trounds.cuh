@@ -53,7 +53,10 @@ constexpr int kTRScanItems = kTRCells / kTRThreads;
 constexpr u32 kTRAlign = 64;                 // records: tile regions start on 128-byte lines
 constexpr int kTRPosStride = 8;              // write cursors (u32) one per 32-byte sector
 constexpr int kTRCellsPerThread = 4;         // touched cells per thread per step of k_tapply
-constexpr int kTSThreads = 256;              // threads per block of k_tapply_sparse
+#ifndef PP_TSPARSE_THREADS
+#define PP_TSPARSE_THREADS 256
+#endif
+constexpr int kTSThreads = PP_TSPARSE_THREADS;  // threads per block of k_tapply_sparse
 constexpr u32 kTSCap = 512;                  // records of a sparse tile (at most)
 constexpr u32 kTSSlots = 1024;               // hash slots of k_tapply_sparse
 constexpr u32 kTSEmpty = 0xffffffffu;
@@ -509,7 +512,13 @@ __global__ void __launch_bounds__(kTClaimThreads, PP_TCLAIM_CTAS) k_tclaim(Cell 
   if (flags) atomicOr(&ctl->flags, flags);
 }
 
-constexpr int kTSortThreads = 256;
+#ifndef PP_TSORT_THREADS
+#define PP_TSORT_THREADS 256
+#endif
+#ifndef PP_TSORT_CTAS
+#define PP_TSORT_CTAS 4
+#endif
+constexpr int kTSortThreads = PP_TSORT_THREADS;
 #ifndef PP_TSORT_PER
 #define PP_TSORT_PER 8
 #endif
@@ -526,7 +535,7 @@ inline size_t tsort_smem_bytes(u32 n_bins) { return tsort_head_bytes(n_bins) + (
 
 // Phase B1': the round's coarse records of each bin, sorted into its tiles'
 // record regions (one cursor atomic per tile per chunk of kTSortChunk records).
-__global__ void __launch_bounds__(kTSortThreads, 4) k_tsort(TileRoundBufs tb, DecodeCtl *__restrict__ ctl) {
+__global__ void __launch_bounds__(kTSortThreads, PP_TSORT_CTAS) k_tsort(TileRoundBufs tb, DecodeCtl *__restrict__ ctl) {
   if (*(volatile u32 *)&ctl->round == 0) return;  // round 0: F_1 empty or an error, no work
   extern __shared__ __align__(16) unsigned char smem[];
   const u32 nb = tb.n_bins;
@@ -847,6 +856,7 @@ __global__ void __launch_bounds__(kTSThreads, kTSCtas) k_tapply_sparse(Cell *__r
   __syncthreads();
   u64 emptied = 0, dropped = 0;
   constexpr int PER = kTSCap / kTSThreads;
+  static_assert(kTSCap % kTSThreads == 0, "a sparse tile's records split evenly over the threads");
   // the records of the block's next tile are loaded while the current one's
   // cells are updated, and the list entry of the tile after it one step
   // earlier still, so that no load waits on another
