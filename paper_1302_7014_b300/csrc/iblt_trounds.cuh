@@ -394,14 +394,26 @@ __global__ void __launch_bounds__(kTClaimThreads, PP_TCLAIM_CTAS) k_tclaim(Cell 
     return a;
   };
   // copies this thread's frontier entries of the chunk at c into buffer bf
-  // (segments hold thousands of entries: a chunk spans one or two)
+  // (a chunk of a large frontier spans one or two segments; a small frontier
+  // can spread it over many, so a longer step is a binary search)
   auto fetch = [&](u64 c, u32 a0, int bf) {
 #pragma unroll
     for (int it = 0; it < kTClaimItems; ++it) {
       const u32 i = (u32)(c + (u64)it * kTClaimThreads + tid);
       if (i < n) {
         u32 a = a0;
-        while (a + 1 < ns && s_pre[a + 1] <= i) ++a;
+        if (a + 1 < ns && s_pre[a + 1] <= i) {
+          ++a;
+          if (a + 1 < ns && s_pre[a + 1] <= i) {
+            u32 hi = ns;  // s_pre[a + 1] <= i < s_pre[hi] (s_pre[ns] is the total)
+            ++a;
+            while (hi - a > 1) {
+              const u32 mid = (a + hi) >> 1;
+              if (s_pre[mid] <= i) a = mid;
+              else hi = mid;
+            }
+          }
+        }
         const u64 src = seg_start(tb, a) + (i - s_pre[a]);
         cp_async_8(&s_fx[bf][it * kTClaimThreads + tid], fkey + src);
         cp_async_4(&s_fc[bf][it * kTClaimThreads + tid], fcell + src);
