@@ -936,8 +936,8 @@ def main():
         "build": {"kernel": "k_bin + k_tile_step per slab (slab-binned, tiles in shared memory)", "ms": b_ms,
                   "bytes": build_bytes,
                   "achieved_gbs": build_bytes / (b_ms * 1e-3) / 1e9},
-        "decode": {"kernel": "decode graph (k_tscan, k_tprefix; per round k_tclaim, k_tactive, k_tapply + "
-                             "k_tapply_sparse, k_round_end)", "ms": d_ms,
+        "decode": {"kernel": "decode graph (k_tscan, k_tprefix; per round k_tclaim, k_tsort, k_tactive, "
+                             "k_tapply + k_tapply_sparse, k_round_end; k_trestore)", "ms": d_ms,
                    "bytes": decode_bytes, "achieved_gbs": decode_bytes / (d_ms * 1e-3) / 1e9},
     }
     dom = "decode" if d_ms >= b_ms else "build"
