@@ -955,11 +955,12 @@ def main():
 
     if world == 1 and not args.no_extra:
         # the same decode against what the GPU gives for its access pattern: per
-        # recovered key the winner's own cell is written and r - 1 cells are read
-        # and written back, 2 r - 1 scattered 32 B accesses
+        # recovered key r - 1 cells are read and written back, 2 (r - 1)
+        # scattered 32 B accesses (the cell it was found in is emptied by the
+        # write that made it pure, or by the streaming scan)
         sc = bench_scatter(pp, torch)
         rate = sc["tile_sorted_read_write"]["accesses_per_s"]
-        per_key = 2 * r - 1
+        per_key = 2 * (r - 1)
         ceiling = rate / per_key
         roofline["scatter_ceiling"] = {
             "accesses_per_s": rate, "accesses_per_key": per_key, "keys_per_s": ceiling,
