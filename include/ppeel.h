@@ -73,12 +73,13 @@ typedef struct pp_options {
                             1; 2 = edge-centric rounds to the end.  r > 4 and edge
                             rows that are not 16-byte (r = 4) or 8-byte (r = 2) aligned
                             always use 1. */
-  uint32_t rounds;       /* IBLT decode rounds of pp_iblt_decode: 0 = tile rounds for
-                            tables of at least 2^21 cells that saw no deletion (each
-                            round's updates folded per 4096-cell tile in shared
-                            memory), binned atomic rounds for other large tables,
-                            direct atomics below 2^21 cells (default); 1 = never tile
-                            rounds; 2 = tile rounds for any table without deletions */
+  uint32_t rounds;       /* IBLT decode rounds of pp_iblt_decode and pp_batch_decode:
+                            0 = tile rounds for tables (batch: arenas) of at least
+                            2^21 cells that saw no deletion (each round's updates
+                            folded per 4096-cell tile in shared memory), binned
+                            atomic rounds for other large ones, direct atomics below
+                            2^21 cells (default); 1 = never tile rounds; 2 = tile
+                            rounds for any table or batch without deletions */
   uint32_t apply_ctas;   /* resident blocks per SM of the binned rounds' apply kernel
                             (default 3; sets the width of the table window updated at once) */
   uint32_t frontier_switch; /* pp_peel_kcore, kcore_mode 0: edge-centric rounds run while
@@ -362,7 +363,9 @@ pp_status pp_peel_kcore_subrounds(uint32_t n, uint32_t r, uint32_t k, const uint
  * graph launch in which each device-side round peels the current frontier of
  * every table at once (Sec. 1 rounds at k = 2, per table).  Tables never share
  * cells, so every table's rounds, recovered keys and residue equal those of a
- * plain pp_iblt_decode of that table alone.
+ * plain pp_iblt_decode of that table alone.  A batch built from insertions
+ * only decodes in tile rounds over the whole arena (opt.rounds), others in
+ * binned or direct-atomic rounds.
  * ------------------------------------------------------------------------ */
 typedef struct pp_batch pp_batch;
 
@@ -428,8 +431,9 @@ pp_status pp_batch_get_options(const pp_batch *b, pp_options *opt);
 
 /* Autotuner of the batched form (the paper has no counterpart: the knobs are
  * this implementation's).  Searches the batch's run-time knobs -- ctas_per_sm,
- * apply_ctas, binned (1 = address-ordered records, 2 = direct atomics) and
- * insert_chunk -- on the caller's own batch and keys: each candidate runs
+ * apply_ctas, binned (1 = address-ordered records, 2 = direct atomics),
+ * insert_chunk and rounds (2 = tile rounds, 1 = binned or direct rounds) -- on
+ * the caller's own batch and keys: each candidate runs
  * pp_batch_build + pp_batch_decode once untimed and `reps` times timed (CUDA
  * events on `stream`, median).  Candidate 0 is the batch's options as they
  * were.  A candidate whose per-table rounds, recovered counts or residues

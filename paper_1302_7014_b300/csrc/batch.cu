@@ -10,6 +10,12 @@
 // stops contributing entries.  Per-table counters record keys recovered per
 // round (the first stats_rounds rounds), the last productive round, and the
 // residue size.
+//
+// A batch built from insertions only decodes in tile rounds over the whole
+// arena (csrc/iblt_trounds.cuh): the rounds' updates are folded per 4096-cell
+// tile whatever tables the tile's cells belong to.  A per-word table map
+// (every 32-cell word belongs to one table) gives the kernels a cell's table
+// and checksum seed.  Other batches use the binned or direct-atomic rounds.
 #include <string.h>
 
 #include <vector>
@@ -67,6 +73,12 @@ struct pp_batch {
   size_t smem_claim = 0, smem_apply_round = 0, smem_bin = 0;
   int grid_claim = 0, grid_apply_round = 0, grid_bin = 0;
   TileBufs tiles;  // tile pass of the binned build (allocated on first use)
+  // tile rounds (allocated on the first decode that uses them)
+  TileRoundEngine tre;
+  u32 *wtab = nullptr;        // per 32-cell word of the arena: its table
+  u64 *wseed = nullptr;       // per word: its table's checksum seed
+  uint64_t front_cap = 0;     // entries of fkey / fcell
+  bool tile_rounds = false;   // the round kind the graph was built with
   // binned updates fed from the keys (every table lies within two slabs)
   bool keys_tiles = false;
   int krank = 0;                 // kernel rank, as passed to iblt_kernels
@@ -116,6 +128,9 @@ void free_batch(pp_batch *b) {
   cudaFree(b->bin_count);
   cudaFree(b->bin_overflow);
   free_tiles(b->tiles);
+  tre_free(b->tre);
+  cudaFree(b->wtab);
+  cudaFree(b->wseed);
   cudaFree(b->slab_chunk);
   cudaFreeHost(b->h_slab_chunk);
   delete b;
@@ -175,6 +190,51 @@ pp_status ensure_round_bins(pp_batch *b, cudaStream_t s) {
   b->grid_claim = persistent_grid(b->k.claim, kBlock, b->smem_claim, b->opt.ctas_per_sm);
   b->grid_apply_round = persistent_grid(b->k.apply_round, kBlock, b->smem_apply_round, b->opt.apply_ctas);
   return PP_OK;
+}
+
+// Tile rounds over the arena: the engine's buffers, frontier arrays that span
+// its segments, the word maps, and record regions for every key's updates
+// (r keys per table plus kTRAlign slack per tile).
+pp_status ensure_batch_tiles(pp_batch *b, cudaStream_t s) {
+  if (!b->tre.trb.base) {
+    pp_status st = tre_setup(b->tre, b->k, b->total_cells, b->opt.ctas_per_sm);
+    if (st != PP_OK) return st;
+    ++b->rec_gen;
+    PP_CUDA(cudaStreamSynchronize(s));
+    if (b->tre.front > b->front_cap) {
+      cudaFree(b->fkey);
+      cudaFree(b->fcell);
+      b->fkey = nullptr;
+      b->fcell = nullptr;
+      PP_CUDA(cudaMalloc((void **)&b->fkey, b->tre.front * sizeof(u64)));
+      PP_CUDA(cudaMalloc((void **)&b->fcell, b->tre.front * sizeof(u32)));
+      b->front_cap = b->tre.front;
+      if (b->exec) cudaGraphExecDestroy(b->exec);
+      b->exec = nullptr;
+    }
+    // every word of table i (its padding included) maps to i
+    const uint64_t nw = (uint64_t)b->tre.trb.n_tiles * kTRWordsPerTile;
+    std::vector<u32> wt(nw, 0);
+    std::vector<u64> ws(nw, 0);
+    for (uint32_t i = 0; i < b->n_tables; ++i) {
+      const TableArgs &t = b->h_tabs[i];
+      const u64 seed = t.seed[t.r];
+      for (uint64_t w = t.base / 32; w < ((uint64_t)t.base + t.n_cells + 31) / 32; ++w) {
+        wt[w] = i;
+        ws[w] = seed;
+      }
+    }
+    PP_CUDA(cudaMalloc((void **)&b->wtab, nw * sizeof(u32)));
+    PP_CUDA(cudaMalloc((void **)&b->wseed, nw * sizeof(u64)));
+    PP_CUDA(cudaMemcpy(b->wtab, wt.data(), nw * sizeof(u32), cudaMemcpyHostToDevice));
+    PP_CUDA(cudaMemcpy(b->wseed, ws.data(), nw * sizeof(u64), cudaMemcpyHostToDevice));
+  }
+  uint64_t updates = 0;
+  for (uint32_t i = 0; i < b->n_tables; ++i) updates += (uint64_t)b->h_tabs[i].r * b->items[i];
+  bool moved = false;
+  pp_status st = tre_records(b->tre, tre_record_need(b->tre, updates), s, &moved);
+  if (moved) ++b->rec_gen;
+  return st;
 }
 
 struct BatchArgs {
@@ -258,6 +318,14 @@ pp_status add_kernel(cudaGraphNode_t *node, cudaGraph_t g, const cudaGraphNode_t
   kp.kernelParams = args;
   PP_CUDA(cudaGraphAddKernelNode(node, g, dep, ndep, &kp));
   return PP_OK;
+}
+
+void fill_tiles(pp_batch *b, TileRoundLaunch &a, u64 *out) {
+  TableArgs t0{};
+  t0.n_cells = (u32)b->total_cells;  // the tile kernels' bound; tables come from the word map
+  const TRBatch bt{b->tabs, b->wtab, b->wseed, b->bc, out};
+  tre_launch_args(a, b->tre, b->cells, t0, b->fkey, b->fcell, b->bitmap, b->ctl,
+                  RoundStats{b->st_rec, b->st_alive, b->st_front}, bt);
 }
 
 // The output pointer is a kernel argument, so the graph is rebuilt when it
@@ -430,6 +498,7 @@ pp_status pp_batch_create(pp_batch **out, uint32_t n_tables, const uint64_t *n_c
   b->grid_filter = persistent_grid(b->k.filter, kBlock, 0, b->opt.ctas_per_sm);
   b->grid_insert = persistent_grid(b->k.insert, kBlock, 0, 8) * 2;
   b->max_r = max_r;
+  b->front_cap = N;
   *out = b;
   return PP_OK;
 }
@@ -713,20 +782,48 @@ pp_status pp_batch_decode(pp_batch *b, uint64_t *d_out_keys, const uint64_t *h_o
   memset(b->h_ctl, 0, sizeof(DecodeCtl));
   b->h_ctl->max_rounds = b->opt.max_rounds;
   b->h_ctl->stats_rounds = sr;
-  const bool want_bins = b->opt.binned == 1 || (b->opt.binned == 0 && b->total_cells >= (1ull << 21));
+  // round kind: tile rounds (batches built from insertions only), binned
+  // atomic rounds (other large arenas), direct atomics (small arenas)
+  const bool large = b->total_cells >= (1ull << 21);
+  const bool want_tiles = b->k.tscan && !b->had_deletes &&
+                          (b->opt.rounds == 2 || (b->opt.rounds == 0 && large && b->opt.binned != 2));
+  const bool want_bins = !want_tiles && (b->opt.binned == 1 || (b->opt.binned == 0 && large));
+  if (want_tiles) {
+    pp_status st = ensure_batch_tiles(b, s);
+    if (st != PP_OK) return st;
+  }
   if (want_bins) {
     pp_status st = ensure_round_bins(b, s);
     if (st != PP_OK) return st;
     PP_CUDA(cudaMemsetAsync(b->bin_count, 0, b->n_bins * sizeof(u32), s));
   }
-  if (b->exec && (want_bins != b->binned_rounds || (want_bins && b->graph_gen != b->rec_gen))) {
+  if (b->exec && (want_bins != b->binned_rounds || want_tiles != b->tile_rounds ||
+                  ((want_bins || want_tiles) && b->graph_gen != b->rec_gen))) {
     cudaGraphExecDestroy(b->exec);
     b->exec = nullptr;
   }
   b->binned_rounds = want_bins;
+  b->tile_rounds = want_tiles;
   PP_CUDA(cudaMemcpyAsync(b->ctl, b->h_ctl, sizeof(DecodeCtl), cudaMemcpyHostToDevice, s));
   u64 *out = reinterpret_cast<u64 *>(d_out_keys);
-  if (b->opt.host_loop) {
+  if (b->tile_rounds && b->opt.host_loop) {
+    TileRoundLaunch a;
+    fill_tiles(b, a, out);
+    pp_status st = tre_host_loop(b->tre, b->k, a, &b->h_ctl->more, s);
+    if (st != PP_OK) return st;
+  } else if (b->tile_rounds) {
+    if (!b->exec || b->graph_out != out) {
+      if (b->exec) cudaGraphExecDestroy(b->exec);
+      b->exec = nullptr;
+      TileRoundLaunch a;
+      fill_tiles(b, a, out);
+      pp_status st = tre_build_graph(b->tre, b->k, a, &b->exec);
+      if (st != PP_OK) return st;
+      b->graph_out = out;
+      b->graph_gen = b->rec_gen;
+    }
+    PP_CUDA(cudaGraphLaunch(b->exec, s));
+  } else if (b->opt.host_loop) {
     BatchArgs a;
     fill(b, a, out);
     PP_CUDA(cudaLaunchKernel(b->k.scan, dim3(b->grid_scan), dim3(kBlock), a.scan_p, 0, s));
@@ -754,8 +851,9 @@ pp_status pp_batch_decode(pp_batch *b, uint64_t *d_out_keys, const uint64_t *h_o
     }
     PP_CUDA(cudaGraphLaunch(b->exec, s));
   }
-  if (b->binned_rounds) {
-    // the binned rounds do not track emptied cells per table: count the residue
+  const bool scan_residue = b->binned_rounds || b->tile_rounds;
+  if (scan_residue) {
+    // the binned and tile rounds do not track emptied cells per table: count the residue
     for (uint32_t i = 0; i < n; ++i) b->h_items[i] = b->items[i];
     PP_CUDA(cudaMemcpyAsync((void *)b->bc.items, b->h_items, n * sizeof(u64), cudaMemcpyHostToDevice, s));
     PP_CUDA(cudaMemsetAsync(b->bc.residual, 0, n * sizeof(u64), s));
@@ -781,7 +879,7 @@ pp_status pp_batch_decode(pp_batch *b, uint64_t *d_out_keys, const uint64_t *h_o
     r.rounds = b->h_rounds[i];
     r.recovered = b->h_recovered[i];
     r.items_before = b->items[i];
-    r.residual_cells = b->binned_rounds ? b->h_residual[i] : b->h_nonempty[i] - b->h_emptied[i];
+    r.residual_cells = scan_residue ? b->h_residual[i] : b->h_nonempty[i] - b->h_emptied[i];
     const uint32_t nc = r.rounds < r.round_cap ? r.rounds : r.round_cap;
     if (r.recovered_per_round) {
       for (uint32_t t = 0; t < nc; ++t)

@@ -56,16 +56,18 @@ static IbltKernels iblt_kernels_t() {
     k.sg_filter = (const void *)k_sgfilter<R>;
     k.sg_claim = (const void *)k_claim<R, false, true, true>;
     k.sg_apply = (const void *)k_apply_round<R, false, true>;
-    k.tscan = (const void *)k_tscan<R>;
-    k.tclaim = (const void *)k_tclaim<R>;
-    k.tapply = (const void *)k_tapply<R>;
-    k.tapply_sparse = (const void *)k_tapply_sparse<R>;
-    k.trestore = (const void *)k_trestore<R>;
+  }
+  if constexpr (R >= 0 || B) {
+    // tile rounds: plain for a fixed rank or the generic one, batched for every rank code
+    k.tscan = (const void *)k_tscan<R, B>;
+    k.tclaim = (const void *)k_tclaim<R, B>;
+    k.tapply = (const void *)k_tapply<R, B>;
+    k.tapply_sparse = (const void *)k_tapply_sparse<R, B>;
+    k.trestore = (const void *)k_trestore<R, B>;
     static bool tattr = false;
     if (!tattr) {
-      cudaFuncSetAttribute((const void *)k_tapply<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)kTApplySmem);
-      allow_max_dynamic_smem((const void *)k_tclaim<R>);
+      allow_max_dynamic_smem((const void *)k_tapply<R, B>);
+      allow_max_dynamic_smem((const void *)k_tclaim<R, B>);
       allow_max_dynamic_smem((const void *)k_tsort);
       tattr = true;
     }
@@ -140,6 +142,240 @@ struct HostJob {
 
 }  // namespace pp
 
+// ---- tile rounds: the host side shared by the single table and the batch ----
+namespace pp {
+
+namespace {
+
+pp_status tre_node(cudaGraphNode_t *node, cudaGraph_t g, const cudaGraphNode_t *dep, size_t ndep, const void *fn,
+                   int grid, int block, size_t smem, void **args) {
+  cudaKernelNodeParams kp{};
+  kp.func = const_cast<void *>(fn);
+  kp.gridDim = dim3((unsigned)grid);
+  kp.blockDim = dim3((unsigned)block);
+  kp.sharedMemBytes = (unsigned)smem;
+  kp.kernelParams = args;
+  PP_CUDA(cudaGraphAddKernelNode(node, g, dep, ndep, &kp));
+  return PP_OK;
+}
+
+}  // namespace
+
+// Frontier segments: one per block of k_tscan / k_tapply (n_seg_d, each at
+// most 4096 pushes per tile it takes) and of k_tapply_sparse (n_seg_s, at most
+// kTSCap pushes per tile).  Coarse bins of the claim: at most 128 when a bin of
+// 512 tiles allows it, else as many bins of 512 tiles as the tiles need.
+pp_status tre_setup(TileRoundEngine &e, const IbltKernels &k, uint64_t n_cells, uint32_t ctas_per_sm) {
+  TileRoundBufs &b = e.trb;
+  if (b.base) return PP_OK;
+  const uint32_t nt = (uint32_t)((n_cells + kTRCells - 1) / kTRCells);
+  e.grid_tapply = persistent_grid(k.tapply, kTRThreads, kTApplySmem, 2);
+  e.grid_tsparse = persistent_grid(k.tapply_sparse, kTSThreads, 0, kTSCtas);
+  e.grid_tscan = e.grid_tapply;
+  const uint32_t nd = (uint32_t)e.grid_tapply, nsp = (uint32_t)e.grid_tsparse;
+  const uint64_t cap_d = (uint64_t)kTRCells * ((nt + nd - 1) / nd);
+  const uint64_t cap_s = (uint64_t)kTSCap * ((nt + nsp - 1) / nsp);
+  if (cap_d > 0xFFFFFFFFull || cap_s > 0xFFFFFFFFull) return fail(PP_ERR_INVALID_ARG, "tile rounds: table too large");
+  uint64_t *h_start = (uint64_t *)malloc((size_t)(nd + nsp) * sizeof(uint64_t));
+  if (!h_start) return fail(PP_ERR_OUT_OF_MEMORY, "tile round segment table");
+  for (uint32_t s = 0; s < nd + nsp; ++s) h_start[s] = s < nd ? s * cap_d : nd * cap_d + (s - nd) * cap_s;
+  u64 *d_start = nullptr;
+  uint32_t bsh = 0;
+  while (bsh < 9 && ((nt + (1u << bsh) - 1) >> bsh) > 128) ++bsh;
+  b.bin_tshift = bsh;
+  b.n_bins = (nt + (1u << bsh) - 1) >> bsh;
+  cudaError_t err = cudaMalloc((void **)&b.base, ((size_t)nt + 1) * sizeof(u64));
+  if (err == cudaSuccess) err = cudaMalloc((void **)&b.pos, (size_t)nt * kTRPosStride * sizeof(u32));
+  if (err == cudaSuccess) err = cudaMalloc((void **)&b.base64, ((size_t)nt + 1) * sizeof(u32));
+  if (err == cudaSuccess) err = cudaMalloc((void **)&b.done, (size_t)nt * sizeof(u32));
+  if (err == cudaSuccess) err = cudaMalloc((void **)&b.sum, (size_t)nt * sizeof(u32));
+  if (err == cudaSuccess) err = cudaMalloc((void **)&b.act, (size_t)nt * sizeof(TileAct));
+  if (err == cudaSuccess) err = cudaMalloc((void **)&b.act_d, (size_t)nt * sizeof(TileAct));
+  if (err == cudaSuccess) err = cudaMalloc((void **)&b.fseg, (size_t)(nd + nsp) * sizeof(u32));
+  if (err == cudaSuccess) err = cudaMalloc((void **)&b.cpos, (size_t)b.n_bins * kTRPosStride * sizeof(u32));
+  if (err == cudaSuccess) err = cudaMalloc((void **)&b.cdone, (size_t)b.n_bins * sizeof(u32));
+  if (err == cudaSuccess) err = cudaMalloc((void **)&d_start, (size_t)(nd + nsp) * sizeof(u64));
+  if (err == cudaSuccess)
+    err = cudaMemcpy(d_start, h_start, (size_t)(nd + nsp) * sizeof(u64), cudaMemcpyHostToDevice);
+  free(h_start);
+  b.fstart = d_start;
+  if (err != cudaSuccess) {
+    pp_status st = cuda_fail(err, "tile round buffers", __FILE__, __LINE__);
+    tre_free(e);
+    return st;
+  }
+  b.n_tiles = nt;
+  b.n_seg_d = nd;
+  b.n_seg_s = nsp;
+  b.cap_d = (u32)cap_d;
+  b.cap_s = (u32)cap_s;
+  e.front = nd * cap_d + nsp * cap_s;
+  e.smem_tclaim = (size_t)kTClaimChunk * k.nr * 12 + ((size_t)nd + nsp + 1) * 4 + (4 * (size_t)b.n_bins + 2) * 4;
+  e.grid_tclaim = persistent_grid(k.tclaim, kTClaimThreads, e.smem_tclaim, ctas_per_sm);
+  e.smem_tsort = tsort_smem_bytes(b.n_bins);
+  e.grid_tsort = persistent_grid((const void *)k_tsort, kTSortThreads, e.smem_tsort, 8);
+  e.grid_act = (int)((nt + kBlock - 1) / kBlock);
+  return PP_OK;
+}
+
+pp_status tre_records(TileRoundEngine &e, uint64_t need, cudaStream_t s, bool *moved) {
+  TileRoundBufs &b = e.trb;
+  if (moved) *moved = false;
+  if (need <= b.rec_cap) return PP_OK;
+  PP_CUDA(cudaStreamSynchronize(s));
+  cudaFree(b.rec_key);
+  cudaFree(b.rec_off);
+  cudaFree(b.crec_key);
+  cudaFree(b.crec_cell);
+  b.rec_key = b.crec_key = nullptr;
+  b.rec_off = nullptr;
+  b.crec_cell = nullptr;
+  b.rec_cap = 0;
+  PP_CUDA(cudaMalloc((void **)&b.rec_key, need * sizeof(u64)));
+  PP_CUDA(cudaMalloc((void **)&b.rec_off, need * sizeof(u16)));
+  PP_CUDA(cudaMalloc((void **)&b.crec_key, need * sizeof(u64)));
+  PP_CUDA(cudaMalloc((void **)&b.crec_cell, need * sizeof(u32)));
+  b.rec_cap = need;
+  if (moved) *moved = true;
+  return PP_OK;
+}
+
+uint64_t tre_record_need(const TileRoundEngine &e, uint64_t updates) {
+  return updates + (uint64_t)kTRAlign * e.trb.n_tiles;
+}
+
+void tre_free(TileRoundEngine &e) {
+  TileRoundBufs &b = e.trb;
+  cudaFree(b.rec_key);
+  cudaFree(b.rec_off);
+  cudaFree(b.crec_key);
+  cudaFree(b.crec_cell);
+  cudaFree(b.cpos);
+  cudaFree(b.cdone);
+  cudaFree(b.base);
+  cudaFree(b.pos);
+  cudaFree(b.base64);
+  cudaFree(b.done);
+  cudaFree(b.sum);
+  cudaFree(b.act);
+  cudaFree(b.act_d);
+  cudaFree(b.fseg);
+  cudaFree(const_cast<u64 *>(b.fstart));
+  e = TileRoundEngine{};
+}
+
+void TileRoundLaunch::bind() {
+  void *a[8] = {&cells, &tab0, &fkey, &fcell, &bitmap, &tb, &ctl, &bt};
+  memcpy(scan, a, sizeof a);
+  void *b[2] = {&tb, &ctl};
+  memcpy(prefix, b, sizeof b);
+  memcpy(active, b, sizeof b);
+  memcpy(sort, b, sizeof b);
+  void *c[8] = {&cells, &tab0, &fkey_c, &fcell_c, &bitmap_c, &tb, &ctl, &bt};
+  memcpy(claim, c, sizeof c);
+  void *d[8] = {&cells, &tab0, &tb, &fkey, &fcell, &bitmap, &ctl, &bt};
+  memcpy(apply, d, sizeof d);
+  void *r[7] = {&cells, &tab0, &fkey_c, &fcell_c, &tb, &ctl, &bt};
+  memcpy(restore, r, sizeof r);
+  void *x[4] = {&ctl, &st, &set_cond, &cond};
+  memcpy(end, x, sizeof x);
+}
+
+void tre_launch_args(TileRoundLaunch &a, const TileRoundEngine &e, Cell *cells, const TableArgs &tab0, u64 *fkey,
+                     u32 *fcell, u32 *bitmap, DecodeCtl *ctl, const RoundStats &st, const TRBatch &bt) {
+  memset(&a, 0, sizeof a);
+  a.cells = cells;
+  a.tab0 = tab0;
+  a.fkey = fkey;
+  a.fcell = fcell;
+  a.bitmap = bitmap;
+  a.fkey_c = fkey;
+  a.fcell_c = fcell;
+  a.bitmap_c = bitmap;
+  a.tb = e.trb;
+  a.ctl = ctl;
+  a.bt = bt;
+  a.st = st;
+  a.bind();
+}
+
+pp_status tre_build_graph(const TileRoundEngine &e, const IbltKernels &k, TileRoundLaunch &a, cudaGraphExec_t *exec) {
+  *exec = nullptr;
+  cudaGraph_t g = nullptr;
+  PP_CUDA(cudaGraphCreate(&g, 0));
+  pp_status st = PP_OK;
+  cudaGraphNode_t n_scan, n_pre, n_cond, n_claim, n_sort, n_act, n_apply[2], n_end, n_restore;
+  cudaGraphConditionalHandle h;
+  cudaGraphNodeParams cp{};
+  cudaGraph_t body;
+  st = tre_node(&n_scan, g, nullptr, 0, k.tscan, e.grid_tscan, kTRThreads, 0, a.scan);
+  if (st != PP_OK) goto done;
+  st = tre_node(&n_pre, g, &n_scan, 1, (const void *)k_tprefix, 1, 1024, 0, a.prefix);
+  if (st != PP_OK) goto done;
+  if (cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault) != cudaSuccess) {
+    st = fail(PP_ERR_CUDA, "cudaGraphConditionalHandleCreate failed");
+    goto done;
+  }
+  cp.type = cudaGraphNodeTypeConditional;
+  cp.conditional.handle = h;
+  cp.conditional.type = cudaGraphCondTypeWhile;
+  cp.conditional.size = 1;
+  if (cudaGraphAddNode(&n_cond, g, &n_pre, nullptr, 1, &cp) != cudaSuccess) {
+    st = fail(PP_ERR_CUDA, "cudaGraphAddNode(conditional while) failed");
+    goto done;
+  }
+  body = cp.conditional.phGraph_out[0];
+  // one block per frontier segment
+  st = tre_node(&n_restore, g, &n_cond, 1, k.trestore, e.grid_tapply + e.grid_tsparse, kBlock, 0, a.restore);
+  if (st != PP_OK) goto done;
+  a.set_cond = 1;
+  a.cond = h;
+  st = tre_node(&n_claim, body, nullptr, 0, k.tclaim, e.grid_tclaim, kTClaimThreads, e.smem_tclaim, a.claim);
+  if (st != PP_OK) goto done;
+  st = tre_node(&n_sort, body, &n_claim, 1, (const void *)k_tsort, e.grid_tsort, kTSortThreads, e.smem_tsort,
+                a.sort);
+  if (st != PP_OK) goto done;
+  st = tre_node(&n_act, body, &n_sort, 1, (const void *)k_tactive, e.grid_act, kBlock, 0, a.active);
+  if (st != PP_OK) goto done;
+  // dense and sparse tiles in two kernels that may run side by side
+  st = tre_node(&n_apply[0], body, &n_act, 1, k.tapply, e.grid_tapply, kTRThreads, kTApplySmem, a.apply);
+  if (st != PP_OK) goto done;
+  st = tre_node(&n_apply[1], body, &n_act, 1, k.tapply_sparse, e.grid_tsparse, kTSThreads, 0, a.apply);
+  if (st != PP_OK) goto done;
+  st = tre_node(&n_end, body, n_apply, 2, (const void *)k_round_end, 1, 32, 0, a.end);
+  if (st != PP_OK) goto done;
+  if (cudaGraphInstantiate(exec, g, 0) != cudaSuccess) {
+    st = fail(PP_ERR_CUDA, "cudaGraphInstantiate failed: %s", cudaGetErrorString(cudaGetLastError()));
+    *exec = nullptr;
+  }
+done:
+  cudaGraphDestroy(g);
+  return st;
+}
+
+pp_status tre_host_loop(const TileRoundEngine &e, const IbltKernels &k, TileRoundLaunch &a, u32 *h_more,
+                        cudaStream_t s) {
+  a.set_cond = 0;
+  PP_CUDA(cudaLaunchKernel(k.tscan, dim3(e.grid_tscan), dim3(kTRThreads), a.scan, 0, s));
+  PP_CUDA(cudaLaunchKernel((const void *)k_tprefix, dim3(1), dim3(1024), a.prefix, 0, s));
+  for (;;) {
+    PP_CUDA(cudaLaunchKernel(k.tclaim, dim3(e.grid_tclaim), dim3(kTClaimThreads), a.claim, e.smem_tclaim, s));
+    PP_CUDA(cudaLaunchKernel((const void *)k_tsort, dim3(e.grid_tsort), dim3(kTSortThreads), a.sort,
+                             e.smem_tsort, s));
+    PP_CUDA(cudaLaunchKernel((const void *)k_tactive, dim3(e.grid_act), dim3(kBlock), a.active, 0, s));
+    PP_CUDA(cudaLaunchKernel(k.tapply, dim3(e.grid_tapply), dim3(kTRThreads), a.apply, kTApplySmem, s));
+    PP_CUDA(cudaLaunchKernel(k.tapply_sparse, dim3(e.grid_tsparse), dim3(kTSThreads), a.apply, 0, s));
+    PP_CUDA(cudaLaunchKernel((const void *)k_round_end, dim3(1), dim3(32), a.end, 0, s));
+    PP_CUDA(cudaMemcpyAsync(h_more, &a.ctl->more, sizeof(u32), cudaMemcpyDeviceToHost, s));
+    PP_CUDA(cudaStreamSynchronize(s));
+    if (!*h_more) break;
+  }
+  PP_CUDA(cudaLaunchKernel(k.trestore, dim3(e.grid_tapply + e.grid_tsparse), dim3(kBlock), a.restore, 0, s));
+  return PP_OK;
+}
+
+}  // namespace pp
+
 struct pp_iblt {
   uint64_t n = 0;
   uint32_t r = 0;
@@ -187,11 +423,9 @@ struct pp_iblt {
   size_t smem_sgclaim = 0;
   signed char *sg_graph_out = nullptr;  // output sign pointer the graph was built with
   // tile rounds (allocated on first use)
-  TileRoundBufs trb{};
+  TileRoundEngine tre;        // tile rounds (buffers allocated on first use)
   bool tile_rounds = false;   // the round kind the graph was built with
   bool has_deletes = false;   // a deletion since the last clear/build: no tile rounds
-  int grid_tscan = 0, grid_tclaim = 0, grid_tapply = 0, grid_tsparse = 0, grid_tsort = 0;
-  size_t smem_tclaim = 0, smem_tsort = 0;
   uint64_t front_cap = 0;     // entries of fkey / fcell
   // host-buffer jobs: at most two in flight
   HostJob jobs[kHostJobs];
@@ -249,21 +483,7 @@ void free_all(pp_iblt *t) {
   cudaFreeHost(t->h_flag);
   if (t->up_s) cudaStreamDestroy(t->up_s);
   if (t->down_s) cudaStreamDestroy(t->down_s);
-  cudaFree(t->trb.rec_key);
-  cudaFree(t->trb.rec_off);
-  cudaFree(t->trb.crec_key);
-  cudaFree(t->trb.crec_cell);
-  cudaFree(t->trb.cpos);
-  cudaFree(t->trb.cdone);
-  cudaFree(t->trb.base);
-  cudaFree(t->trb.pos);
-  cudaFree(t->trb.base64);
-  cudaFree(t->trb.done);
-  cudaFree(t->trb.sum);
-  cudaFree(t->trb.act);
-  cudaFree(t->trb.act_d);
-  cudaFree(t->trb.fseg);
-  cudaFree(const_cast<u64 *>(t->trb.fstart));
+  tre_free(t->tre);
   delete t;
 }
 
@@ -672,217 +892,51 @@ pp_status sub_graph_launch(pp_iblt *t, bool binned, cudaStream_t s) {
 // Buffers: a record region per tile (its counts' sum, rounded up to
 // kTRAlign), r * items + kTRAlign * tiles records in all.
 pp_status ensure_tile_rounds(pp_iblt *t, cudaStream_t s) {
-  TileRoundBufs &b = t->trb;
-  const uint32_t nt = (uint32_t)((t->n + kTRCells - 1) / kTRCells);
-  if (!b.base) {
-    // frontier segments: one per block of k_tscan / k_tapply (n_seg_d, each
-    // at most 4096 pushes per tile it takes) and of k_tapply_sparse (n_seg_s,
-    // at most kTSCap pushes per tile)
-    t->grid_tapply = persistent_grid(t->k.tapply, kTRThreads, kTApplySmem, 2);
-    t->grid_tsparse = persistent_grid(t->k.tapply_sparse, kTSThreads, 0, kTSCtas);
-    t->grid_tscan = t->grid_tapply;
-    const uint32_t nd = (uint32_t)t->grid_tapply, nsp = (uint32_t)t->grid_tsparse;
-    const uint64_t cap_d = (uint64_t)kTRCells * ((nt + nd - 1) / nd);
-    const uint64_t cap_s = (uint64_t)kTSCap * ((nt + nsp - 1) / nsp);
-    const uint64_t front = nd * cap_d + nsp * cap_s;
-    uint64_t *h_start = (uint64_t *)malloc((size_t)(nd + nsp) * sizeof(uint64_t));
-    if (!h_start) return fail(PP_ERR_OUT_OF_MEMORY, "tile round segment table");
-    for (uint32_t k = 0; k < nd + nsp; ++k) h_start[k] = k < nd ? k * cap_d : nd * cap_d + (k - nd) * cap_s;
-    u64 *d_start = nullptr;
-    cudaError_t e = cudaMalloc((void **)&b.base, ((size_t)nt + 1) * sizeof(u64));
-    if (e == cudaSuccess) e = cudaMalloc((void **)&b.pos, (size_t)nt * kTRPosStride * sizeof(u32));
-    if (e == cudaSuccess) e = cudaMalloc((void **)&b.base64, ((size_t)nt + 1) * sizeof(u32));
-    if (e == cudaSuccess) e = cudaMalloc((void **)&b.done, (size_t)nt * sizeof(u32));
-    if (e == cudaSuccess) e = cudaMalloc((void **)&b.sum, (size_t)nt * sizeof(u32));
-    if (e == cudaSuccess) e = cudaMalloc((void **)&b.act, (size_t)nt * sizeof(TileAct));
-    if (e == cudaSuccess) e = cudaMalloc((void **)&b.act_d, (size_t)nt * sizeof(TileAct));
-    if (e == cudaSuccess) e = cudaMalloc((void **)&b.fseg, (size_t)(nd + nsp) * sizeof(u32));
-    // coarse bins of the claim: at most 128 when a bin of 512 tiles allows it
-    uint32_t bsh = 0;
-    while (bsh < 9 && ((nt + (1u << bsh) - 1) >> bsh) > 128) ++bsh;
-    b.bin_tshift = bsh;
-    b.n_bins = (nt + (1u << bsh) - 1) >> bsh;
-    if (e == cudaSuccess) e = cudaMalloc((void **)&b.cpos, (size_t)b.n_bins * kTRPosStride * sizeof(u32));
-    if (e == cudaSuccess) e = cudaMalloc((void **)&b.cdone, (size_t)b.n_bins * sizeof(u32));
-    if (e == cudaSuccess) e = cudaMalloc((void **)&d_start, (size_t)(nd + nsp) * sizeof(u64));
-    if (e == cudaSuccess)
-      e = cudaMemcpy(d_start, h_start, (size_t)(nd + nsp) * sizeof(u64), cudaMemcpyHostToDevice);
-    free(h_start);
-    b.fstart = d_start;
-    if (e != cudaSuccess) return cuda_fail(e, "tile round buffers", __FILE__, __LINE__);
-    b.n_tiles = nt;
-    b.n_seg_d = nd;
-    b.n_seg_s = nsp;
-    b.cap_d = (u32)cap_d;
-    b.cap_s = (u32)cap_s;
+  if (!t->tre.trb.base) {
+    pp_status st = tre_setup(t->tre, t->k, t->n, t->opt.ctas_per_sm);
+    if (st != PP_OK) return st;
+    ++t->rec_gen;
     // the frontier arrays hold every segment
-    if (front > t->front_cap) {
+    if (t->tre.front > t->front_cap) {
       PP_CUDA(cudaStreamSynchronize(s));
       cudaFree(t->fkey);
       cudaFree(t->fcell);
       t->fkey = nullptr;
       t->fcell = nullptr;
-      PP_CUDA(cudaMalloc((void **)&t->fkey, front * sizeof(u64)));
-      PP_CUDA(cudaMalloc((void **)&t->fcell, front * sizeof(u32)));
-      t->front_cap = front;
+      PP_CUDA(cudaMalloc((void **)&t->fkey, t->tre.front * sizeof(u64)));
+      PP_CUDA(cudaMalloc((void **)&t->fcell, t->tre.front * sizeof(u32)));
+      t->front_cap = t->tre.front;
       // every graph holds the frontier pointers
       if (t->sub_exec) cudaGraphExecDestroy(t->sub_exec);
       if (t->sub_exec_binned) cudaGraphExecDestroy(t->sub_exec_binned);
       if (t->sg_exec) cudaGraphExecDestroy(t->sg_exec);
       t->sub_exec = t->sub_exec_binned = t->sg_exec = nullptr;
     }
-    t->smem_tclaim = (size_t)kTClaimChunk * t->k.nr * 12 + ((size_t)nd + nsp + 1) * 4 + (4 * (size_t)b.n_bins + 2) * 4;
-    t->grid_tclaim = persistent_grid(t->k.tclaim, kTClaimThreads, t->smem_tclaim, t->opt.ctas_per_sm);
-    t->smem_tsort = tsort_smem_bytes(b.n_bins);
-    t->grid_tsort = persistent_grid((const void *)k_tsort, kTSortThreads, t->smem_tsort, 8);
-    ++t->rec_gen;
   }
   const uint64_t items = t->items > 0 ? (uint64_t)t->items : 0;
-  const uint64_t need = (uint64_t)t->r * items + (uint64_t)kTRAlign * nt;
-  if (need > b.rec_cap) {
-    PP_CUDA(cudaStreamSynchronize(s));
-    cudaFree(b.rec_key);
-    cudaFree(b.rec_off);
-    cudaFree(b.crec_key);
-    cudaFree(b.crec_cell);
-    b.rec_key = b.crec_key = nullptr;
-    b.rec_off = nullptr;
-    b.crec_cell = nullptr;
-    b.rec_cap = 0;
-    PP_CUDA(cudaMalloc((void **)&b.rec_key, need * sizeof(u64)));
-    PP_CUDA(cudaMalloc((void **)&b.rec_off, need * sizeof(u16)));
-    PP_CUDA(cudaMalloc((void **)&b.crec_key, need * sizeof(u64)));
-    PP_CUDA(cudaMalloc((void **)&b.crec_cell, need * sizeof(u32)));
-    b.rec_cap = need;
-    ++t->rec_gen;
-  }
-  return PP_OK;
+  bool moved = false;
+  pp_status st = tre_records(t->tre, tre_record_need(t->tre, (uint64_t)t->r * items), s, &moved);
+  if (moved) ++t->rec_gen;
+  return st;
 }
 
-struct TileArgsSet {
-  Cell *cells;
-  TableArgs tab0;
-  u64 *fkey;
-  u32 *fcell, *bitmap;
-  const u64 *fkey_c;
-  const u32 *fcell_c, *bitmap_c;
-  TileRoundBufs tb;
-  DecodeCtl *ctl;
-  void *scan[7], *prefix[2], *claim[7], *active[2], *apply[7], *sort[2], *restore[6];
-  void bind() {
-    void *a[7] = {&cells, &tab0, &fkey, &fcell, &bitmap, &tb, &ctl};
-    memcpy(scan, a, sizeof a);
-    void *b[2] = {&tb, &ctl};
-    memcpy(prefix, b, sizeof b);
-    memcpy(active, b, sizeof b);
-    memcpy(sort, b, sizeof b);
-    void *c[7] = {&cells, &tab0, &fkey_c, &fcell_c, &bitmap_c, &tb, &ctl};
-    memcpy(claim, c, sizeof c);
-    void *d[7] = {&cells, &tab0, &tb, &fkey, &fcell, &bitmap, &ctl};
-    memcpy(apply, d, sizeof d);
-    void *e[6] = {&cells, &tab0, &fkey_c, &fcell_c, &tb, &ctl};
-    memcpy(restore, e, sizeof e);
-  }
-};
-
-void fill_tile_args(pp_iblt *t, TileArgsSet &a) {
-  a.cells = t->cells;
-  a.tab0 = t->args;
-  a.fkey = t->fkey;
-  a.fcell = t->fcell;
-  a.bitmap = t->bitmap;
-  a.fkey_c = t->fkey;
-  a.fcell_c = t->fcell;
-  a.bitmap_c = t->bitmap;
-  a.tb = t->trb;
-  a.ctl = t->ctl;
-  a.bind();
+void fill_tile_args(pp_iblt *t, TileRoundLaunch &a) {
+  tre_launch_args(a, t->tre, t->cells, t->args, t->fkey, t->fcell, t->bitmap, t->ctl,
+                  RoundStats{t->st_rec, t->st_alive, t->st_front}, TRBatch{});
 }
 
-// tscan -> tprefix -> while (more) { tclaim -> tsort -> tactive -> tapply || tapply_sparse -> round_end }
-// -> trestore
 pp_status build_tile_graph(pp_iblt *t) {
-  TileArgsSet ta;
-  fill_tile_args(t, ta);
-  EndArgs ea{t->ctl, RoundStats{t->st_rec, t->st_alive, t->st_front}, 1, 0, {}};
-  cudaGraph_t g = nullptr;
-  PP_CUDA(cudaGraphCreate(&g, 0));
-  pp_status st = PP_OK;
-  cudaGraphNode_t n_scan, n_pre, n_cond, n_claim, n_sort, n_act, n_apply[2], n_end, n_restore;
-  const int grid_restore = t->grid_tapply + t->grid_tsparse;  // one block per frontier segment
-  const int grid_act = (int)((t->trb.n_tiles + kBlock - 1) / kBlock);
-  const size_t smem_claim = t->smem_tclaim;
-  cudaGraphConditionalHandle h;
-  cudaGraphNodeParams cp{};
-  cudaGraph_t body;
-  st = add_kernel(&n_scan, g, nullptr, 0, t->k.tscan, t->grid_tscan, kTRThreads, 0, ta.scan);
-  if (st != PP_OK) goto done;
-  st = add_kernel(&n_pre, g, &n_scan, 1, (const void *)k_tprefix, 1, 1024, 0, ta.prefix);
-  if (st != PP_OK) goto done;
-  if (cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault) != cudaSuccess) {
-    st = fail(PP_ERR_CUDA, "cudaGraphConditionalHandleCreate failed");
-    goto done;
-  }
-  cp.type = cudaGraphNodeTypeConditional;
-  cp.conditional.handle = h;
-  cp.conditional.type = cudaGraphCondTypeWhile;
-  cp.conditional.size = 1;
-  if (cudaGraphAddNode(&n_cond, g, &n_pre, nullptr, 1, &cp) != cudaSuccess) {
-    st = fail(PP_ERR_CUDA, "cudaGraphAddNode(conditional while) failed");
-    goto done;
-  }
-  body = cp.conditional.phGraph_out[0];
-  st = add_kernel(&n_restore, g, &n_cond, 1, t->k.trestore, grid_restore, kBlock, 0, ta.restore);
-  if (st != PP_OK) goto done;
-  ea.cond = h;
-  ea.bind();
-  st = add_kernel(&n_claim, body, nullptr, 0, t->k.tclaim, t->grid_tclaim, kTClaimThreads, smem_claim, ta.claim);
-  if (st != PP_OK) goto done;
-  st = add_kernel(&n_sort, body, &n_claim, 1, (const void *)k_tsort, t->grid_tsort, kTSortThreads, t->smem_tsort,
-                  ta.sort);
-  if (st != PP_OK) goto done;
-  st = add_kernel(&n_act, body, &n_sort, 1, (const void *)k_tactive, grid_act, kBlock, 0, ta.active);
-  if (st != PP_OK) goto done;
-  // dense and sparse tiles in two kernels that may run side by side
-  st = add_kernel(&n_apply[0], body, &n_act, 1, t->k.tapply, t->grid_tapply, kTRThreads, kTApplySmem, ta.apply);
-  if (st != PP_OK) goto done;
-  st = add_kernel(&n_apply[1], body, &n_act, 1, t->k.tapply_sparse, t->grid_tsparse, kTSThreads, 0, ta.apply);
-  if (st != PP_OK) goto done;
-  st = add_kernel(&n_end, body, n_apply, 2, (const void *)k_round_end, 1, 32, 0, ea.p);
-  if (st != PP_OK) goto done;
-  if (cudaGraphInstantiate(&t->exec, g, 0) != cudaSuccess) {
-    st = fail(PP_ERR_CUDA, "cudaGraphInstantiate failed: %s", cudaGetErrorString(cudaGetLastError()));
-    t->exec = nullptr;
-  }
-  t->graph_gen = t->rec_gen;
-done:
-  cudaGraphDestroy(g);
+  TileRoundLaunch a;
+  fill_tile_args(t, a);
+  pp_status st = tre_build_graph(t->tre, t->k, a, &t->exec);
+  if (st == PP_OK) t->graph_gen = t->rec_gen;
   return st;
 }
 
 pp_status run_tile_host_loop(pp_iblt *t, cudaStream_t s) {
-  TileArgsSet ta;
-  fill_tile_args(t, ta);
-  EndArgs ea{t->ctl, RoundStats{t->st_rec, t->st_alive, t->st_front}, 0, 0, {}};
-  ea.bind();
-  const int grid_act = (int)((t->trb.n_tiles + kBlock - 1) / kBlock);
-  const size_t smem_claim = t->smem_tclaim;
-  PP_CUDA(cudaLaunchKernel(t->k.tscan, dim3(t->grid_tscan), dim3(kTRThreads), ta.scan, 0, s));
-  PP_CUDA(cudaLaunchKernel((const void *)k_tprefix, dim3(1), dim3(1024), ta.prefix, 0, s));
-  for (;;) {
-    PP_CUDA(cudaLaunchKernel(t->k.tclaim, dim3(t->grid_tclaim), dim3(kTClaimThreads), ta.claim, smem_claim, s));
-    PP_CUDA(cudaLaunchKernel((const void *)k_tsort, dim3(t->grid_tsort), dim3(kTSortThreads), ta.sort,
-                             t->smem_tsort, s));
-    PP_CUDA(cudaLaunchKernel((const void *)k_tactive, dim3(grid_act), dim3(kBlock), ta.active, 0, s));
-    PP_CUDA(cudaLaunchKernel(t->k.tapply, dim3(t->grid_tapply), dim3(kTRThreads), ta.apply, kTApplySmem, s));
-    PP_CUDA(cudaLaunchKernel(t->k.tapply_sparse, dim3(t->grid_tsparse), dim3(kTSThreads), ta.apply, 0, s));
-    PP_CUDA(cudaLaunchKernel((const void *)k_round_end, dim3(1), dim3(32), ea.p, 0, s));
-    PP_CUDA(cudaMemcpyAsync(&t->h_ctl->more, &t->ctl->more, sizeof(u32), cudaMemcpyDeviceToHost, s));
-    PP_CUDA(cudaStreamSynchronize(s));
-    if (!t->h_ctl->more) break;
-  }
-  PP_CUDA(cudaLaunchKernel(t->k.trestore, dim3(t->grid_tapply + t->grid_tsparse), dim3(kBlock), ta.restore, 0, s));
-  return PP_OK;
+  TileRoundLaunch a;
+  fill_tile_args(t, a);
+  return tre_host_loop(t->tre, t->k, a, &t->h_ctl->more, s);
 }
 
 pp_status run_host_loop(pp_iblt *t, cudaStream_t s) {

@@ -50,6 +50,7 @@ constexpr int kTRShift = 12;
 constexpr u32 kTRCells = 1u << kTRShift;     // cells per tile
 constexpr int kTRThreads = 512;              // threads per block of k_tscan / k_tapply
 constexpr int kTRScanItems = kTRCells / kTRThreads;
+static_assert(kTRCells / 32 == kTRWordsPerTile, "the batch's word maps cover whole tiles");
 constexpr u32 kTRAlign = 64;                 // records: tile regions start on 128-byte lines
 constexpr int kTRPosStride = 8;              // write cursors (u32) one per 32-byte sector
 constexpr int kTRCellsPerThread = 4;         // touched cells per thread per step of k_tapply
@@ -76,40 +77,6 @@ constexpr int kTSCtas = PP_TSPARSE_CTAS;    // resident blocks per SM of k_tappl
 constexpr int kTClaimThreads = PP_TCLAIM_THREADS;        // threads per block of k_tclaim
 constexpr int kTClaimItems = PP_TCLAIM_ITEMS;            // frontier entries per thread per chunk
 constexpr int kTClaimChunk = kTClaimThreads * kTClaimItems;
-
-// A tile with records in the current round: records [lo, lo + n) (absolute slots).
-struct TileAct {
-  u64 lo;
-  u32 tile;
-  u32 n;
-};
-
-struct TileRoundBufs {
-  u64 *rec_key;   // records: the key
-  u16 *rec_off;   // records: cell offset in its tile
-  u64 *base;      // per tile: first record slot of its region (n_tiles + 1 entries)
-  u32 *base64;    // per tile and one past the last: base / kTRAlign (regions start on multiples of kTRAlign)
-  u32 *pos;       // per tile (stride kTRPosStride): records written this decode
-  u32 *done;      // per tile: records applied this decode
-  u32 *sum;       // per tile: sum of counts at the decode's start (scan output)
-  TileAct *act;   // sparse tiles with records this round (n_tiles entries)
-  TileAct *act_d; // dense tiles with records this round (n_tiles entries)
-  u32 *fseg;      // per frontier segment: entries
-  const u64 *fstart;  // per frontier segment: first entry in fkey / fcell
-  u64 *crec_key;  // coarse records (claim -> k_tsort): the key
-  u32 *crec_cell; // coarse records: the cell
-  u32 *cpos;      // per coarse bin (stride kTRPosStride): coarse records written this decode
-  u32 *cdone;     // per coarse bin: coarse records sorted into tiles this decode
-  u64 rec_cap;    // slots in rec_key / rec_off (and crec_key / crec_cell)
-  u32 n_bins;     // coarse bins of 2^bin_tshift tiles each
-  u32 bin_tshift;
-  u32 n_tiles;
-  u32 n_seg_d;    // segments of k_tscan / k_tapply blocks (first)
-  u32 n_seg_s;    // segments of k_tapply_sparse blocks (after those)
-  u32 cap_d;      // entries of a k_tscan / k_tapply segment: 4096 * ceil(n_tiles / n_seg_d)
-  u32 cap_s;      // entries of a k_tapply_sparse segment: kTSCap * ceil(n_tiles / n_seg_s)
-  u32 pad;
-};
 
 // First entry of frontier segment k: the dense segments (cap_d entries each)
 // come first, then the sparse ones (cap_s each).
@@ -175,16 +142,17 @@ __device__ __forceinline__ void block_exclusive_scan(const u32 *in, u32 *out, u3
 // decode's alive / nonempty counters.  Every bitmap word is written here.
 // The cells of F_1 are emptied as they are found (see the file comment).
 // Runs n_seg_d blocks; block b takes tiles b, b + n_seg_d, ... (at most
-// 4096 pushes each) and writes segment b.
-template <int R>
+// 4096 pushes each) and writes segment b.  BATCH: tab0.n_cells is the arena's
+// size, and a cell's checksum seed is its word's (bt.wseed).
+template <int R, bool BATCH>
 __global__ void __launch_bounds__(kTRThreads, 2) k_tscan(Cell *__restrict__ cells, const TableArgs tab0,
                                                       u64 *__restrict__ fkey, u32 *__restrict__ fcell,
                                                       u32 *__restrict__ bitmap, TileRoundBufs tb,
-                                                      DecodeCtl *__restrict__ ctl) {
+                                                      DecodeCtl *__restrict__ ctl, TRBatch bt) {
   __shared__ u32 s_seg, s_neg;
   __shared__ u64 s_red[kTRThreads / 32];
   const u32 tid = threadIdx.x;
-  const u64 seed_chk = tab0.seed[rank_of<R>(tab0)];
+  const u64 seed0 = BATCH ? 0ull : tab0.seed[rank_of<R>(tab0)];
   const u32 n = tab0.n_cells;
   const u64 seg0 = tb.fstart[blockIdx.x];
   u64 alive = 0, nonempty = 0, emptied = 0;
@@ -204,12 +172,20 @@ __global__ void __launch_bounds__(kTRThreads, 2) k_tscan(Cell *__restrict__ cell
       cnts[it] = 0;
       if (c < n) ld_cell_cs(cells + c, keys[it], chks[it], cnts[it]);
     }
+    // BATCH: a warp's 32 cells of item `it` are one word of one table; lane
+    // `it` fetches that word's seed for the whole warp
+    u64 wseed = 0;
+    if (BATCH && lane_id() < (u32)kTRScanItems) {
+      const u32 cw = c0 + lane_id() * kTRThreads + (tid & ~31u);
+      if (cw < n) wseed = bt.wseed[cw >> 5];
+    }
 #pragma unroll
     for (int it = 0; it < kTRScanItems; ++it) {
       const u32 c = c0 + (u32)it * kTRThreads + tid;
       const bool valid = c < n;
       bool pure = false;
       const u64 key = keys[it];
+      const u64 seed_chk = BATCH ? __shfl_sync(kFull, wseed, it) : seed0;
       if (valid) {
         const int cnt = cnts[it];
         pure = cell_pure(cnt, key, chks[it], seed_chk);
@@ -320,13 +296,13 @@ __global__ void __launch_bounds__(1024) k_tprefix(TileRoundBufs tb, DecodeCtl *_
 // limit, error) puts (x, checkSum(x), 1) back into each cell that frontier
 // emptied (see the file comment), so the table is left as after its last
 // completed round.  The pending frontier is n_front entries in the segments.
-template <int R>
+template <int R, bool BATCH>
 __global__ void __launch_bounds__(kBlock) k_trestore(Cell *__restrict__ cells, const TableArgs tab0,
                                                      const u64 *__restrict__ fkey, const u32 *__restrict__ fcell,
-                                                     TileRoundBufs tb, DecodeCtl *__restrict__ ctl) {
+                                                     TileRoundBufs tb, DecodeCtl *__restrict__ ctl, TRBatch bt) {
   __shared__ u64 s_red[kBlock / 32];
   if (*(volatile u32 *)&ctl->n_front == 0) return;  // uniform: the decode finished
-  const u64 seed_chk = tab0.seed[rank_of<R>(tab0)];
+  const u64 seed0 = BATCH ? 0ull : tab0.seed[rank_of<R>(tab0)];
   const u32 ns = tb.n_seg_d + tb.n_seg_s;
   u64 put = 0;
   for (u32 sg = blockIdx.x; sg < ns; sg += gridDim.x) {
@@ -335,7 +311,8 @@ __global__ void __launch_bounds__(kBlock) k_trestore(Cell *__restrict__ cells, c
     const u64 a = tb.fstart[sg];
     for (u32 i = threadIdx.x; i < k; i += kBlock) {
       const u64 x = fkey[a + i];
-      st_cell_cs(cells + fcell[a + i], x, checksum(x, seed_chk), 1);
+      const u32 c = fcell[a + i];
+      st_cell_cs(cells + c, x, checksum(x, BATCH ? bt.wseed[c >> 5] : seed0), 1);
       ++put;
     }
   }
@@ -350,12 +327,14 @@ __global__ void __launch_bounds__(kBlock) k_trestore(Cell *__restrict__ cells, c
 // (n_seg + 1 u32), the chunk's records (kTClaimChunk * NR keys and cells), per
 // bin its count, its offset in the chunk and its run's first slot (3 * n_bins
 // + 1 u32), and the bins' region bounds / kTRAlign (n_bins + 1 u32).
-template <int R>
+// BATCH: an entry's table is its cell's word's (bt.wtab); a table's keys go to
+// its own output range, counted per table and round (bt.bc).
+template <int R, bool BATCH>
 __global__ void __launch_bounds__(kTClaimThreads, PP_TCLAIM_CTAS) k_tclaim(Cell *__restrict__ cells, const TableArgs tab0,
                                                       const u64 *__restrict__ fkey,
                                                       const u32 *__restrict__ fcell,
                                                       const u32 *__restrict__ bitmap, TileRoundBufs tb,
-                                                      DecodeCtl *__restrict__ ctl) {
+                                                      DecodeCtl *__restrict__ ctl, TRBatch bt) {
   constexpr int NR = nr_of<R>();
   constexpr int CAP = kTClaimChunk * NR;
   extern __shared__ __align__(16) unsigned char smem[];
@@ -378,8 +357,9 @@ __global__ void __launch_bounds__(kTClaimThreads, PP_TCLAIM_CTAS) k_tclaim(Cell 
   if (n == 0) return;  // uniform: nothing to claim
   u64 *out = ctl->out;
   const u64 out_cap = ctl->out_cap;
+  const u32 round = *(volatile u32 *)&ctl->round;
+  const u32 stats_rounds = BATCH ? ctl->stats_rounds : 0u;
   const u64 keep = l2_evict_last_policy();
-  const int r = rank_of<R>(tab0);
   const u32 bsh = kTRShift + tb.bin_tshift;  // cell -> coarse bin
   for (u32 b = tid; b <= nb; b += kTClaimThreads) s_bb[b] = tb.base64[min(b << tb.bin_tshift, tb.n_tiles)];
   block_exclusive_scan<kTClaimThreads>(tb.fseg, s_pre, ns, s_wt);
@@ -438,7 +418,7 @@ __global__ void __launch_bounds__(kTClaimThreads, PP_TCLAIM_CTAS) k_tclaim(Cell 
     else cp_async_commit();  // an empty group keeps the wait below uniform
     cp_async_wait_prev();
     u64 x[kTClaimItems];
-    u32 c[kTClaimItems], cj[kTClaimItems][NR], rk[kTClaimItems][NR];
+    u32 c[kTClaimItems], cj[kTClaimItems][NR], rk[kTClaimItems][NR], tbl[kTClaimItems];
     bool win[kTClaimItems];
     u32 need[kTClaimItems];  // bit j: x's cell in sub-table j gets a record
 #pragma unroll
@@ -447,10 +427,13 @@ __global__ void __launch_bounds__(kTClaimThreads, PP_TCLAIM_CTAS) k_tclaim(Cell 
       win[it] = i < n;
       x[it] = win[it] ? s_fx[buf][it * kTClaimThreads + tid] : 0ull;
       c[it] = win[it] ? s_fc[buf][it * kTClaimThreads + tid] : 0u;
+      tbl[it] = (BATCH && win[it]) ? __ldg(bt.wtab + (c[it] >> 5)) : 0u;
     }
 #pragma unroll
     for (int it = 0; it < kTClaimItems; ++it) {
-      cells_of<NR>(x[it], tab0, cj[it]);
+      const TableArgs &T = BATCH ? bt.tabs[tbl[it]] : tab0;
+      const int r = rank_of<R>(T);
+      cells_of<NR>(x[it], T, cj[it]);
       int js = -1;
 #pragma unroll
       for (int j = NR - 1; j >= 0; --j)
@@ -474,8 +457,30 @@ __global__ void __launch_bounds__(kTClaimThreads, PP_TCLAIM_CTAS) k_tclaim(Cell 
     }
 #pragma unroll
     for (int it = 0; it < kTClaimItems; ++it) {
-      const u32 p = warp_reserve<u32>(win[it], &s_nout);
-      if (win[it]) s_out[p] = x[it];
+      if constexpr (!BATCH) {
+        const u32 p = warp_reserve<u32>(win[it], &s_nout);
+        if (win[it]) s_out[p] = x[it];
+      } else {
+        // the warp's winners of one table take one run of its output range
+        const TableArgs &T = bt.tabs[tbl[it]];
+        const u32 grp = __match_any_sync(kFull, win[it] ? tbl[it] : 0xffffffffu);
+        const int leader = __ffs(grp) - 1;
+        u64 base = 0;
+        if (win[it] && (int)lane_id() == leader) {
+          const u32 gsize = __popc(grp);
+          const u32 local = round + 1 - T.start_round;
+          base = atomicAdd(bt.bc.recovered + tbl[it], (u64)gsize);
+          atomicMax(bt.bc.rounds + tbl[it], local);
+          if (local <= stats_rounds)
+            atomicAdd(bt.bc.round_rec + (u64)tbl[it] * stats_rounds + (local - 1), gsize);
+        }
+        base = __shfl_sync(kFull, base, leader);
+        if (win[it]) {
+          const u64 slot = base + __popc(grp & lanemask_lt());
+          if (slot < T.out_cap) bt.out[T.out_base + slot] = x[it];
+          else flags |= FLAG_CAPACITY;
+        }
+      }
       // records for the other cells, counted per coarse bin
 #pragma unroll
       for (int j = 0; j < NR; ++j)
@@ -705,12 +710,13 @@ constexpr size_t kTApplySmem = (size_t)kTRCells * (8 + 8 + 4 + 2);
 
 // Phase B2 of round t + phase A of round t + 1 for the dense tiles (see the
 // file comment).  Runs n_seg_d blocks; block b takes the dense tiles b,
-// b + n_seg_d, ... and writes frontier segment b.
-template <int R>
+// b + n_seg_d, ... and writes frontier segment b.  BATCH: the checksum seeds
+// of the tile's 128 words are read into shared memory first.
+template <int R, bool BATCH>
 __global__ void __launch_bounds__(kTRThreads, 2) k_tapply(Cell *__restrict__ cells, const TableArgs tab0,
                                                           TileRoundBufs tb, u64 *__restrict__ fkey,
                                                           u32 *__restrict__ fcell, u32 *__restrict__ bitmap,
-                                                          DecodeCtl *__restrict__ ctl) {
+                                                          DecodeCtl *__restrict__ ctl, TRBatch bt) {
   if (*(volatile u32 *)&ctl->round == 0) return;  // round 0: F_1 empty or an error, no work
   extern __shared__ __align__(16) unsigned char smem[];
   u64 *s_dkey = reinterpret_cast<u64 *>(smem);
@@ -721,8 +727,9 @@ __global__ void __launch_bounds__(kTRThreads, 2) k_tapply(Cell *__restrict__ cel
   u32 *s_dchk32 = reinterpret_cast<u32 *>(s_dchk);
   __shared__ u32 s_nt[2], s_seg;  // touched cells of the current tile: two counters, used in turn
   __shared__ u64 s_red[kTRThreads / 32];
+  __shared__ u64 s_wseed[BATCH ? kTRCells / 32 : 1];
   const u32 tid = threadIdx.x;
-  const u64 seed_chk = tab0.seed[rank_of<R>(tab0)];
+  const u64 seed0 = BATCH ? 0ull : tab0.seed[rank_of<R>(tab0)];
   const u32 n_act = *(volatile u32 *)&ctl->n_act_dense;
   const u64 seg0 = tb.fstart[blockIdx.x];
   u64 emptied = 0, dropped = 0;
@@ -744,6 +751,11 @@ __global__ void __launch_bounds__(kTRThreads, 2) k_tapply(Cell *__restrict__ cel
     if (ai + gridDim.x < n_act) nxt = tb.act_d[ai + gridDim.x];  // the next tile's entry, early
     const u64 b = cur.lo;
     const u32 nrec = cur.n, t = cur.tile;
+    if constexpr (BATCH) {
+      // the last tile's reads of these seeds ended at its final barrier
+      if (tid < kTRCells / 32) s_wseed[tid] = bt.wseed[((u64)t << (kTRShift - 5)) + tid];
+      __syncthreads();
+    }
     // fold the records into one update per cell (4 records per thread in flight)
     for (u32 i0 = 0; i0 < nrec; i0 += 4 * kTRThreads) {
       u64 x[4];
@@ -760,7 +772,7 @@ __global__ void __launch_bounds__(kTRThreads, 2) k_tapply(Cell *__restrict__ cel
         const u32 off = o[k] & (kTRCells - 1);
         bool first = false;
         if (v) {
-          const u64 cs = checksum(x[k], seed_chk);
+          const u64 cs = checksum(x[k], BATCH ? s_wseed[off >> 5] : seed0);
           first = atomicAdd(s_dcnt + off, 1u) == 0;
           atomicXor(s_dkey32 + 2 * off, (u32)x[k]);
           atomicXor(s_dkey32 + 2 * off + 1, (u32)(x[k] >> 32));
@@ -802,7 +814,7 @@ __global__ void __launch_bounds__(kTRThreads, 2) k_tapply(Cell *__restrict__ cel
           const int nc = cnt[q] - (int)s_dcnt[off[q]];
           nk = key[q] ^ s_dkey[off[q]];
           const u64 nchk = chk[q] ^ s_dchk[off[q]];
-          pure = cell_pure(nc, nk, nchk, seed_chk);
+          pure = cell_pure(nc, nk, nchk, BATCH ? s_wseed[off[q] >> 5] : seed0);
           // a pure cell is stored empty: its one key leaves it next round
           if (pure) st_cell_cs(cells + c, 0ull, 0ull, 0);
           else st_cell_cs(cells + c, nk, nchk, nc);
@@ -840,12 +852,13 @@ __global__ void __launch_bounds__(kTRThreads, 2) k_tapply(Cell *__restrict__ cel
 // the cell offset) in place of the per-cell arrays, so that many tiles are in
 // flight per SM.  Runs n_seg_s blocks; block b takes the sparse tiles b,
 // b + n_seg_s, ... (at most kTSCap records, hence pushes, each) and writes
-// frontier segment n_seg_d + b.
-template <int R>
+// frontier segment n_seg_d + b.  BATCH: the checksum seeds of a tile's 128
+// words travel with its records, into one of two shared buffers.
+template <int R, bool BATCH>
 __global__ void __launch_bounds__(kTSThreads, kTSCtas) k_tapply_sparse(Cell *__restrict__ cells, const TableArgs tab0,
                                                                  TileRoundBufs tb, u64 *__restrict__ fkey,
                                                                  u32 *__restrict__ fcell, u32 *__restrict__ bitmap,
-                                                                 DecodeCtl *__restrict__ ctl) {
+                                                                 DecodeCtl *__restrict__ ctl, TRBatch bt) {
   if (*(volatile u32 *)&ctl->round == 0) return;  // round 0: F_1 empty or an error, no work
   __shared__ u32 h_off[kTSSlots];   // cell offset of the slot, kTSEmpty if free
   __shared__ u64 h_key[kTSSlots], h_chk[kTSSlots];
@@ -853,8 +866,11 @@ __global__ void __launch_bounds__(kTSThreads, kTSCtas) k_tapply_sparse(Cell *__r
   __shared__ u16 s_slot[kTSCap];    // the slots in use
   __shared__ u32 s_ns[2], s_seg;  // touched cells of the current tile: two counters, used in turn
   __shared__ u64 s_red[kTSThreads / 32];
+  constexpr u32 kW = kTRCells / 32;  // words of a tile
+  static_assert(!BATCH || kTSThreads >= (int)kW, "one thread per word of a tile");
+  __shared__ u64 s_wseed[BATCH ? 2 : 1][BATCH ? kW : 1];
   const u32 tid = threadIdx.x;
-  const u64 seed_chk = tab0.seed[rank_of<R>(tab0)];
+  const u64 seed0 = BATCH ? 0ull : tab0.seed[rank_of<R>(tab0)];
   const u32 n_act = *(volatile u32 *)&ctl->n_act;
   const u64 seg0 = tb.fstart[tb.n_seg_d + blockIdx.x];
   u32 flags = 0;
@@ -875,6 +891,7 @@ __global__ void __launch_bounds__(kTSThreads, kTSCtas) k_tapply_sparse(Cell *__r
   TileAct nxt{}, nxt2{};
   u64 nx[PER];
   u32 no[PER];
+  u64 nws = 0;  // BATCH: the next tile's seed of word tid
   auto load_tile = [&](u32 ai) {
     nxt = nxt2;
     nxt2.n = 0;
@@ -885,9 +902,14 @@ __global__ void __launch_bounds__(kTSThreads, kTSCtas) k_tapply_sparse(Cell *__r
       no[k] = i < nxt.n ? (u32)__ldcs(tb.rec_off + nxt.lo + i) : kTSEmpty;
       nx[k] = i < nxt.n ? __ldcs(tb.rec_key + nxt.lo + i) : 0ull;
     }
+    if (BATCH && tid < kW && nxt.n) nws = bt.wseed[((u64)nxt.tile << (kTRShift - 5)) + tid];
   };
   if (blockIdx.x < n_act) nxt2 = tb.act[blockIdx.x];
   load_tile(blockIdx.x);
+  if constexpr (BATCH) {
+    if (tid < kW) s_wseed[0][tid] = nws;
+    __syncthreads();
+  }
   u32 par = 0;
   for (u32 ai = blockIdx.x; ai < n_act; ai += gridDim.x, par ^= 1) {
     const TileAct cur = nxt;
@@ -925,7 +947,7 @@ __global__ void __launch_bounds__(kTSThreads, kTSCtas) k_tapply_sparse(Cell *__r
         }
       }
       if (o[k] != kTSEmpty) {
-        const u64 cs = checksum(x[k], seed_chk);
+        const u64 cs = checksum(x[k], BATCH ? s_wseed[par][(o[k] & (kTRCells - 1)) >> 5] : seed0);
         atomicAdd(h_cnt + slot, 1u);
         atomicXor(reinterpret_cast<u32 *>(h_key + slot), (u32)x[k]);
         atomicXor(reinterpret_cast<u32 *>(h_key + slot) + 1, (u32)(x[k] >> 32));
@@ -971,7 +993,7 @@ __global__ void __launch_bounds__(kTSThreads, kTSCtas) k_tapply_sparse(Cell *__r
         const int nc = cnt - (int)h_cnt[slot];
         key ^= h_key[slot];
         chk ^= h_chk[slot];
-        pure = cell_pure(nc, key, chk, seed_chk);
+        pure = cell_pure(nc, key, chk, BATCH ? s_wseed[par][(c - c0) >> 5] : seed0);
         // a pure cell is stored empty: its one key leaves it next round
         if (pure) st_cell_cs(cells + c, 0ull, 0ull, 0);
         else st_cell_cs(cells + c, key, chk, nc);
@@ -991,6 +1013,9 @@ __global__ void __launch_bounds__(kTSThreads, kTSCtas) k_tapply_sparse(Cell *__r
         flags |= FLAG_INTERNAL;  // cannot happen: a segment holds every push of its block's tiles
       }
     }
+    // the next tile's seeds (loaded with its records) into the other buffer,
+    // whose last reads ended at the previous barrier
+    if (BATCH && tid < kW) s_wseed[par ^ 1][tid] = nws;
     __syncthreads();
   }
   const u64 e = block_sum<u64, kTSThreads>(emptied, s_red);

@@ -181,6 +181,55 @@ pp_status tile_keys_pass(Cell *cells, const TableArgs *tabs, const u64 *keys, co
                          const u32 *slab_chunk, uint32_t n_slabs, int rank, TileBufs &tb, uint64_t n_cells,
                          int sign, bool zero, cudaStream_t s);
 
+// A tile with records in the current round: records [lo, lo + n) (absolute slots).
+struct TileAct {
+  u64 lo;
+  u32 tile;
+  u32 n;
+};
+
+struct TileRoundBufs {
+  u64 *rec_key;   // records: the key
+  u16 *rec_off;   // records: cell offset in its tile
+  u64 *base;      // per tile: first record slot of its region (n_tiles + 1 entries)
+  u32 *base64;    // per tile and one past the last: base / kTRAlign (regions start on multiples of kTRAlign)
+  u32 *pos;       // per tile (stride kTRPosStride): records written this decode
+  u32 *done;      // per tile: records applied this decode
+  u32 *sum;       // per tile: sum of counts at the decode's start (scan output)
+  TileAct *act;   // sparse tiles with records this round (n_tiles entries)
+  TileAct *act_d; // dense tiles with records this round (n_tiles entries)
+  u32 *fseg;      // per frontier segment: entries
+  const u64 *fstart;  // per frontier segment: first entry in fkey / fcell
+  u64 *crec_key;  // coarse records (claim -> k_tsort): the key
+  u32 *crec_cell; // coarse records: the cell
+  u32 *cpos;      // per coarse bin (stride kTRPosStride): coarse records written this decode
+  u32 *cdone;     // per coarse bin: coarse records sorted into tiles this decode
+  u64 rec_cap;    // slots in rec_key / rec_off (and crec_key / crec_cell)
+  u32 n_bins;     // coarse bins of 2^bin_tshift tiles each
+  u32 bin_tshift;
+  u32 n_tiles;
+  u32 n_seg_d;    // segments of k_tscan / k_tapply blocks (first)
+  u32 n_seg_s;    // segments of k_tapply_sparse blocks (after those)
+  u32 cap_d;      // entries of a k_tscan / k_tapply segment: 4096 * ceil(n_tiles / n_seg_d)
+  u32 cap_s;      // entries of a k_tapply_sparse segment: kTSCap * ceil(n_tiles / n_seg_s)
+  u32 pad;
+};
+
+// 32-cell words per 4096-cell tile of the tile rounds (the batch's word maps
+// cover whole tiles).
+constexpr u32 kTRWordsPerTile = 128;
+
+// The tables of a batched tile-round decode: one arena of 32-cell-aligned
+// tables, so that every 32-cell word of it belongs to one table.  All zero in
+// a single-table decode.
+struct TRBatch {
+  const TableArgs *tabs;  // per table
+  const u32 *wtab;        // per 32-cell word of the arena: its table
+  const u64 *wseed;       // per 32-cell word: its table's checksum seed
+  BatchCounters bc;       // per-table output cursors and statistics
+  u64 *out;               // recovered keys (table i writes [out_base, out_base + out_cap))
+};
+
 // Entry points of one instantiation of the IBLT kernels (plain or batched).
 struct IbltKernels {
   const void *insert, *scan, *peel, *filter;
@@ -198,6 +247,56 @@ struct IbltKernels {
 // The kernel set for a rank code: 3 or 4 = that r; -4 = any r <= 4 (batched
 // kernels only); 0 = any r up to PP_MAX_R.
 IbltKernels iblt_kernels(int rank, bool batch);
+
+// Host side of the tile rounds (csrc/iblt.cu), shared by the single-table
+// handle and the batch: the per-tile and per-bin buffers, the frontier
+// segments, the grids of the round kernels.
+struct TileRoundEngine {
+  TileRoundBufs trb{};
+  int grid_tscan = 0, grid_tclaim = 0, grid_tapply = 0, grid_tsparse = 0, grid_tsort = 0, grid_act = 0;
+  size_t smem_tclaim = 0, smem_tsort = 0;
+  uint64_t front = 0;  // frontier entries the segments span (fkey / fcell must hold them)
+};
+
+// Sizes the segments, coarse bins and grids for a table (or arena) of n_cells
+// and allocates the per-tile buffers; nothing to do once set up.
+pp_status tre_setup(TileRoundEngine &e, const IbltKernels &k, uint64_t n_cells, uint32_t ctas_per_sm);
+// Grows the record buffers to `need` records; *moved tells that they were
+// reallocated (graphs that hold them must be rebuilt).
+pp_status tre_records(TileRoundEngine &e, uint64_t need, cudaStream_t s, bool *moved);
+void tre_free(TileRoundEngine &e);
+// Record slots for a decode of `updates` cell updates (r per key): the updates
+// plus the alignment slack of every tile's region.
+uint64_t tre_record_need(const TileRoundEngine &e, uint64_t updates);
+
+// Arguments of one tile-round decode.  tab0: the table (single) or, in a
+// batch, any TableArgs whose n_cells is the arena's size; bt: zero for a
+// single table.  Kernel parameter arrays point into this object.
+struct TileRoundLaunch {
+  Cell *cells;
+  TableArgs tab0;
+  u64 *fkey;
+  u32 *fcell, *bitmap;
+  const u64 *fkey_c;
+  const u32 *fcell_c, *bitmap_c;
+  TileRoundBufs tb;
+  DecodeCtl *ctl;
+  TRBatch bt;
+  RoundStats st;
+  int set_cond;
+  cudaGraphConditionalHandle cond;
+  void *scan[8], *prefix[2], *claim[8], *active[2], *apply[8], *sort[2], *restore[7], *end[4];
+  void bind();
+};
+void tre_launch_args(TileRoundLaunch &a, const TileRoundEngine &e, Cell *cells, const TableArgs &tab0, u64 *fkey,
+                     u32 *fcell, u32 *bitmap, DecodeCtl *ctl, const RoundStats &st, const TRBatch &bt);
+// The decode as a CUDA graph: scan, prefix, a while node over the round
+// kernels, restore.
+pp_status tre_build_graph(const TileRoundEngine &e, const IbltKernels &k, TileRoundLaunch &a, cudaGraphExec_t *exec);
+// The same kernels driven from the host (one synchronisation per round);
+// h_more: pinned copy of ctl->more.
+pp_status tre_host_loop(const TileRoundEngine &e, const IbltKernels &k, TileRoundLaunch &a, u32 *h_more,
+                        cudaStream_t s);
 
 // Dynamic shared memory of the peel kernel.
 size_t peel_smem_bytes(int nr, bool batch);

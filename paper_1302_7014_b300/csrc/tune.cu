@@ -2,7 +2,8 @@
 //
 // The batch's run-time knobs -- resident blocks per SM of the round kernels
 // (ctas_per_sm), of the binned apply (apply_ctas), the kind of update and
-// round (binned = 1: address-ordered records; 2: direct atomics) and the keys
+// round (binned = 1: address-ordered records; 2: direct atomics; rounds = 2:
+// tile rounds, 1: binned or direct rounds) and the keys
 // per insert work item (insert_chunk, which sets how finely a table's keys are
 // spread over blocks) -- are searched on the caller's own batch: every
 // candidate builds and decodes the batch `reps` times, timed with CUDA events
@@ -19,7 +20,7 @@
 namespace {
 
 struct Candidate {
-  uint32_t ctas_per_sm, apply_ctas, binned, insert_chunk;
+  uint32_t ctas_per_sm, apply_ctas, binned, insert_chunk, rounds;
 };
 
 // One build + decode of the batch; per-table results in res.
@@ -59,11 +60,15 @@ extern "C" pp_status pp_tune_batch(pp_batch *b, const uint64_t *d_keys, const ui
   cudaStream_t s = as_stream(stream);
 
   std::vector<Candidate> cands;
-  cands.push_back(Candidate{base.ctas_per_sm, base.apply_ctas, base.binned, base.insert_chunk});  // as configured
+  cands.push_back(Candidate{base.ctas_per_sm, base.apply_ctas, base.binned, base.insert_chunk, base.rounds});
+  // tile rounds (their grids are fixed; the build's work items vary)
+  for (uint32_t k : {1024u, 4096u, 16384u}) cands.push_back(Candidate{base.ctas_per_sm, base.apply_ctas, 1u, k, 2u});
+  // binned rounds
   for (uint32_t c : {2u, 4u, 8u})
-    for (uint32_t a : {2u, 3u, 4u}) cands.push_back(Candidate{c, a, 1u, base.insert_chunk});
+    for (uint32_t a : {2u, 3u, 4u}) cands.push_back(Candidate{c, a, 1u, base.insert_chunk, 1u});
+  // direct-atomic rounds
   for (uint32_t c : {2u, 4u, 8u})
-    for (uint32_t k : {1024u, 4096u, 16384u}) cands.push_back(Candidate{c, base.apply_ctas, 2u, k});
+    for (uint32_t k : {1024u, 4096u, 16384u}) cands.push_back(Candidate{c, base.apply_ctas, 2u, k, 1u});
   if (cands.size() > PP_TUNE_MAX_CANDIDATES) cands.resize(PP_TUNE_MAX_CANDIDATES);
 
   cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -79,6 +84,7 @@ extern "C" pp_status pp_tune_batch(pp_batch *b, const uint64_t *d_keys, const ui
     o.apply_ctas = cands[i].apply_ctas;
     o.binned = cands[i].binned;
     o.insert_chunk = cands[i].insert_chunk;
+    o.rounds = cands[i].rounds;
     st = pp_batch_set_options(b, &o);
     if (st != PP_OK) break;
     st = run_once(b, n_tables, d_keys, h_key_offsets, d_out_keys, h_out_offsets, got, s);  // warm-up, graphs
@@ -124,6 +130,7 @@ extern "C" pp_status pp_tune_batch(pp_batch *b, const uint64_t *d_keys, const ui
   best->apply_ctas = cands[best_i].apply_ctas;
   best->binned = cands[best_i].binned;
   best->insert_chunk = cands[best_i].insert_chunk;
+  best->rounds = cands[best_i].rounds;
   report->n_candidates = (uint32_t)cands.size();
   report->best_index = (uint32_t)best_i;
   report->default_ms = first_ms;

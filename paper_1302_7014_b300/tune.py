@@ -2,7 +2,7 @@
 
 The search itself runs in the library (``csrc/tune.cu``): it times build +
 decode of the caller's batch for each candidate setting of the run-time knobs
-(ctas_per_sm, apply_ctas, binned, insert_chunk) and keeps the fastest one
+(ctas_per_sm, apply_ctas, binned, insert_chunk, rounds) and keeps the fastest one
 whose per-table results equal the untuned run's.  This module remembers the
 winner in a JSON file keyed by the GPU's name, the batch's ranks and size
 buckets (log2 of its total cells and of its table count), so that later
@@ -27,7 +27,7 @@ from .batch import Batch
 
 u32, u64, vp = ctypes.c_uint32, ctypes.c_uint64, ctypes.c_void_p
 
-TUNED_FIELDS = ("ctas_per_sm", "apply_ctas", "binned", "insert_chunk")
+TUNED_FIELDS = ("ctas_per_sm", "apply_ctas", "binned", "insert_chunk", "rounds")
 MAX_CANDIDATES = 32
 
 

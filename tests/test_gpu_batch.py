@@ -146,16 +146,17 @@ def test_empty_tables_in_batch(ppb):
     assert res.rounds[0] == 0 and res.rounds[2] == 0
 
 
-@pytest.mark.parametrize("rs", [(3, 4), (2, 3, 5, 6)], ids=["r3-4", "r2-6"])
-def test_binned_batch_build_and_rounds(ppb, rs):
-    """Slab-binned build and binned rounds over the arena (forced on), mixed ranks."""
+@pytest.mark.parametrize("rs,rounds", [((3, 4), 1), ((2, 3, 5, 6), 1), ((3, 4), 2), ((2, 3, 5, 6), 2)],
+                         ids=["r3-4-binned", "r2-6-binned", "r3-4-tiles", "r2-6-tiles"])
+def test_binned_batch_build_and_rounds(ppb, rs, rounds):
+    """Slab-binned build (forced on) and binned or tile rounds over the arena, mixed ranks."""
     pp, bm = ppb
     specs = _specs(50, 77 + len(rs), rs=rs, lo=10, hi=17, c_lo=0.5, c_hi=0.95)
     n_cells = [s[0] for s in specs]
     keys = [ppgen.distinct_keys(ppgen.edges_from_c(s[2], s[0]), s[4]) for s in specs]
     koff = np.concatenate([[0], np.cumsum([k.size for k in keys])]).astype(np.uint64)
     dk = torch.from_numpy(np.concatenate(keys).view(np.int64)).cuda()
-    b = bm.Batch(n_cells, [s[1] for s in specs], [s[3] for s in specs], pp.options(binned=1))
+    b = bm.Batch(n_cells, [s[1] for s in specs], [s[3] for s in specs], pp.options(binned=1, rounds=rounds))
     b.insert(torch.from_numpy(ppgen.distinct_keys(int(koff[-1]), 3).view(np.int64)).cuda(), koff)  # junk
     b.build(dk, koff)                       # must wipe the junk
     for i in range(0, len(specs), 5):
@@ -182,9 +183,10 @@ def test_binned_batch_build_and_rounds(ppb, rs):
         assert (cells["key_xor"] == ot.keyx).all()
 
 
-@pytest.mark.parametrize("rs,big", [((3, 4), False), ((2, 5, 6), False), ((3, 4), True)],
-                         ids=["keys-r3-4", "keys-r2-6", "slab-lists"])
-def test_binned_batch_build_across_slabs(ppb, rs, big):
+@pytest.mark.parametrize("rs,big,rounds", [((3, 4), False, 1), ((2, 5, 6), False, 1), ((3, 4), True, 1),
+                                           ((3, 4), False, 0), ((2, 5, 6), True, 0)],
+                         ids=["keys-r3-4", "keys-r2-6", "slab-lists", "keys-r3-4-tiles", "slab-lists-r2-6-tiles"])
+def test_binned_batch_build_across_slabs(ppb, rs, big, rounds):
     """Tables spread over several 2^21-cell slabs, some straddling two.  Such
     a batch is built with each slab's keys hashed inside the tile pass; with
     one table larger than a slab it takes the slab-list build instead.  Build,
@@ -199,7 +201,7 @@ def test_binned_batch_build_across_slabs(ppb, rs, big):
     keys = [ppgen.distinct_keys(ppgen.edges_from_c(s[2], s[0]), s[4]) for s in specs]
     koff = np.concatenate([[0], np.cumsum([k.size for k in keys])]).astype(np.uint64)
     dk = torch.from_numpy(np.concatenate(keys).view(np.int64)).cuda()
-    b = bm.Batch(n_cells, [s[1] for s in specs], [s[3] for s in specs], pp.options(binned=1))
+    b = bm.Batch(n_cells, [s[1] for s in specs], [s[3] for s in specs], pp.options(binned=1, rounds=rounds))
     b.insert(torch.from_numpy(ppgen.distinct_keys(int(koff[-1]), 5).view(np.int64)).cuda(), koff)  # junk
     b.build(dk, koff)                       # must wipe the junk
     ots = []
@@ -278,3 +280,77 @@ def test_batch_deleting_keys_never_inserted(ppb, binned):
         assert res.rounds[i] == ores["rounds"], i
         assert res.recovered[i] == sum(k.size for k in ores["keys"]), i
         assert res.residual_cells[i] == ot.residual_cells(), i
+
+
+# ---- tile rounds over the arena ---------------------------------------------
+@pytest.mark.parametrize("opts", [dict(rounds=2), dict(rounds=2, host_loop=1), dict(rounds=2, ctas_per_sm=1)],
+                         ids=["graph", "hostloop", "small-grid"])
+def test_tile_rounds_mixed_ranks(ppb, opts):
+    """Tile rounds (forced on for a small arena) with tables of r = 2..6 sharing
+    tiles: every table against the oracle, cell for cell."""
+    pp, bm = ppb
+    specs = _specs(60, 201, lo=5, hi=15, c_lo=0.3, c_hi=1.05)
+    b, keys, ooff, res, got = run_batch(pp, bm, specs, pp.options(**opts), out_slack=2)
+    check_against_oracle(specs, keys, ooff, res, got, b)
+
+
+@pytest.mark.parametrize("r", [3, 4])
+def test_tile_rounds_uniform_rank(ppb, r):
+    pp, bm = ppb
+    specs = _specs(40, 220 + r, rs=(r,), lo=8, hi=17, c_lo=0.5, c_hi=0.95)
+    b, keys, ooff, res, got = run_batch(pp, bm, specs, pp.options(rounds=2))
+    check_against_oracle(specs, keys, ooff, res, got, b, cells_every=3)
+
+
+@pytest.mark.parametrize("host_loop", [0, 1])
+def test_tile_rounds_round_limit(ppb, host_loop):
+    """A batched decode in tile rounds stopped by the round limit leaves every
+    table as the oracle's after that round (the pending frontier's cells put
+    back), with the per-table statistics of the rounds that ran."""
+    pp, bm = ppb
+    specs = _specs(16, 231, rs=(3, 4), lo=11, hi=15, c_lo=0.7, c_hi=0.8)
+    keys = [ppgen.distinct_keys(ppgen.edges_from_c(s[2], s[0]), s[4]) for s in specs]
+    koff = np.concatenate([[0], np.cumsum([k.size for k in keys])]).astype(np.uint64)
+    b = bm.Batch([s[0] for s in specs], [s[1] for s in specs], [s[3] for s in specs],
+                 pp.options(max_rounds=3, rounds=2, host_loop=host_loop))
+    b.insert(torch.from_numpy(np.concatenate(keys).view(np.int64)).cuda(), koff)
+    out = torch.full((int(koff[-1]),), -1, dtype=torch.int64, device="cuda")
+    with pytest.raises(pp.PPError) as ei:
+        b.decode(out, koff)
+    assert ei.value.name == "PP_ERR_ROUND_LIMIT"
+    for i, s in enumerate(specs):
+        ot = oracle.IBLT(s[0], s[1], s[3])
+        ot.insert(keys[i])
+        ot.decode_rounds(max_rounds=3)
+        cells = b.cells(i)
+        assert (cells["count"].astype(np.int64) == ot.count).all(), i
+        assert (cells["key_xor"] == ot.keyx).all() and (cells["chk_xor"] == ot.chkx).all(), i
+
+
+def test_tile_rounds_fall_back_after_deletions(ppb):
+    """A batch that saw a deletion decodes in binned rounds even when tile
+    rounds are asked for, and still matches the oracle."""
+    pp, bm = ppb
+    specs = _specs(20, 241, rs=(3, 4), lo=10, hi=15, c_lo=0.5, c_hi=0.9)
+    keys = [ppgen.distinct_keys(ppgen.edges_from_c(s[2], s[0]), s[4]) for s in specs]
+    koff = np.concatenate([[0], np.cumsum([k.size for k in keys])]).astype(np.uint64)
+    b = bm.Batch([s[0] for s in specs], [s[1] for s in specs], [s[3] for s in specs], pp.options(rounds=2))
+    b.insert(torch.from_numpy(np.concatenate(keys).view(np.int64)).cuda(), koff)
+    dele = [k[::4] for k in keys]
+    doff = np.concatenate([[0], np.cumsum([d.size for d in dele])]).astype(np.uint64)
+    b.delete(torch.from_numpy(np.concatenate(dele).view(np.int64)).cuda(), doff)
+    left = [np.setdiff1d(k, d) for k, d in zip(keys, dele)]
+    ooff = np.concatenate([[0], np.cumsum([x.size for x in left])]).astype(np.uint64)
+    out = torch.full((max(1, int(ooff[-1])),), -1, dtype=torch.int64, device="cuda")
+    res = b.decode(out, ooff)
+    got = out.cpu().numpy().view(np.uint64)
+    for i, s in enumerate(specs):
+        ot = oracle.IBLT(s[0], s[1], s[3])
+        ot.insert(keys[i])
+        ot.insert(dele[i], sign=-1)
+        ores = ot.decode_rounds()
+        assert res.rounds[i] == ores["rounds"], i
+        assert res.residual_cells[i] == ot.residual_cells(), i
+        region = np.sort(got[int(ooff[i]): int(ooff[i]) + int(res.recovered[i])])
+        want = np.sort(np.concatenate(ores["keys"])) if ores["keys"] else np.zeros(0, np.uint64)
+        assert (region == want).all(), i

@@ -66,7 +66,8 @@ def test_set_options_keeps_results(mods):
     keys, koff, dk, out = _inputs(specs)
     b = bm.Batch([s[0] for s in specs], [s[1] for s in specs], [s[3] for s in specs])
     for o in (pp.options(binned=2, insert_chunk=512, ctas_per_sm=1),
-              pp.options(binned=1, apply_ctas=2, ctas_per_sm=8), pp.options()):
+              pp.options(binned=1, apply_ctas=2, ctas_per_sm=8, rounds=1),
+              pp.options(rounds=2, insert_chunk=1024), pp.options()):
         b.set_options(o)
         b.build(dk, koff)
         out.fill_(-1)
