@@ -884,9 +884,10 @@ def main():
     if not args.no_e2e:
         # through the library's host-buffer entry points: per step one
         # pp_iblt_submit_host (upload, build, decode and download enqueued by the
-        # library, the copies on its own copy stream) and one pp_iblt_finish_host;
-        # two steps in flight, so step k+1's upload overlaps step k's decode and
-        # step k's download overlaps step k+1's build and decode
+        # library, the copies on its own upload and download streams) and one
+        # pp_iblt_finish_host; up to three steps in flight, so step k+1's upload
+        # overlaps step k's decode and step k's download overlaps step k+1's
+        # build and decode
         hk = torch.from_numpy(keys_h.view(np.int64)).pin_memory().numpy().view(np.uint64)
         outs = [torch.empty(m, dtype=torch.int64).pin_memory().numpy().view(np.uint64) for _ in range(3)]
 
@@ -916,7 +917,29 @@ def main():
                "pipeline": "per step one pp_iblt_submit_host and one pp_iblt_finish_host (C ABI, pinned host "
                            "buffers, wall clock), three steps in flight; the library overlaps the uploads and "
                            "downloads of neighbouring steps with each step's build and decode"}
-        del outs
+        # the floor the copies set: the same bytes up and down at once, pinned
+        # memory, no kernels (PCIe and host memory are shared by both directions)
+        d_up = torch.empty(m, dtype=torch.int64, device="cuda")
+        d_dn = torch.zeros(m, dtype=torch.int64, device="cuda")
+        hk_t = torch.from_numpy(hk.view(np.int64))
+        ho_t = torch.from_numpy(outs[0].view(np.int64))
+        cs = [torch.cuda.Stream(), torch.cuda.Stream()]
+        ct = []
+        for _ in range(4):
+            torch.cuda.synchronize()
+            c0 = time.perf_counter()
+            with torch.cuda.stream(cs[0]):
+                d_up.copy_(hk_t, non_blocking=True)
+            with torch.cuda.stream(cs[1]):
+                ho_t.copy_(d_dn, non_blocking=True)
+            torch.cuda.synchronize()
+            ct.append((time.perf_counter() - c0) * 1e3)
+        c_ms = float(np.median(ct[1:]))
+        e2e["copy_floor"] = {"ms": c_ms, "gb_s": 2 * m * 8 / (c_ms * 1e-3) / 1e9,
+                             "frac": c_ms / e2e["ms_per_step"],
+                             "what": "one step's upload and download at once (pinned, two streams, no kernels); "
+                                     "frac = that time / the e2e step"}
+        del outs, d_up, d_dn
         torch.cuda.empty_cache()
 
     # kernels of one step: the binned build (k_bin, k_flag_to_host, then

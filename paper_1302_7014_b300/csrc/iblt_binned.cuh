@@ -28,7 +28,7 @@ __device__ __forceinline__ void apply_touch(Cell *cells, u32 c, u64 x, u64 cs, i
 // records of one step (kBinKeys * NR * (8 + 4 [+ 4]) bytes).  Registers capped for 5
 // resident CTAs per SM (2.99 -> 2.91 ms for the 2^26-cell build).
 template <int R, bool BATCH>
-__global__ void __launch_bounds__(kBlock, 5) k_bin(Cell *__restrict__ cells, const TableArgs tab0,
+__global__ void __launch_bounds__(kBlock, PP_BIN_CTAS) k_bin(Cell *__restrict__ cells, const TableArgs tab0,
                                                 const TableArgs *__restrict__ tabs,
                                                 const Chunk *__restrict__ chunks, u32 n_chunks,
                                                 const u64 *__restrict__ keys, u64 m, int sign, BinArgs b) {

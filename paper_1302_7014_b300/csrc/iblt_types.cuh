@@ -68,7 +68,13 @@ struct Chunk {
 // Slab-binned build (iblt_binned.cuh).
 constexpr int kSlabShift = 21;               // 2^21 cells = 32 MB per slab
 constexpr u32 kSlabCells = 1u << kSlabShift;
-constexpr int kBinItems = 4;                 // keys per thread per partition step
+#ifndef PP_BIN_ITEMS
+#define PP_BIN_ITEMS 4
+#endif
+#ifndef PP_BIN_CTAS
+#define PP_BIN_CTAS 5
+#endif
+constexpr int kBinItems = PP_BIN_ITEMS;       // keys per thread per partition step
 constexpr int kBinKeys = kBlock * kBinItems; // keys per block per partition step
 
 // Record lists of a binned build: slab s owns records [s*cap, s*cap + min(count[s], cap)).
@@ -80,7 +86,10 @@ constexpr u32 kTileCells = 1u << kTileShift;               // 4096 cells, 64 KB 
 constexpr u32 kTilesPerSlab = kSlabCells >> kTileShift;    // 512
 constexpr int kTileThreads = 512;                          // threads per CTA of both tile kernels
 constexpr int kTileBinItems = 8;                           // records per thread per chunk
-constexpr int kTileApplyItems = 8;                         // records per thread per step of the apply
+#ifndef PP_TILE_APPLY_ITEMS
+#define PP_TILE_APPLY_ITEMS 8
+#endif
+constexpr int kTileApplyItems = PP_TILE_APPLY_ITEMS;       // records per thread per step of the apply
 constexpr int kTileBinChunk = kTileThreads * kTileBinItems;  // 4096 records per bin step
 
 struct TileArgs {
