@@ -213,12 +213,24 @@ pp_status pp_iblt_build(pp_iblt *t, const uint64_t *d_keys, uint64_t m, void *st
 pp_status pp_iblt_decode(pp_iblt *t, uint64_t *d_out_keys, uint64_t out_cap,
                          pp_decode_result *res, void *stream);
 
+/* pp_iblt_build of the m keys at d_keys followed by pp_iblt_decode into
+ * d_out_keys (out_cap >= m, else CAPACITY; nothing is built).  Same table,
+ * keys, rounds and *res as the two calls.  When the build is slab-binned and
+ * the decode runs tile rounds (both chosen as in those calls), the build's
+ * write-out of each tile also finds the tile's pure cells (F_1, Sec. 1
+ * round 1), so the decode starts at its first round without reading the
+ * table once more; a tile that keys crowd beyond its list is left to the
+ * decode to scan.  Synchronizes `stream` twice (after sorting the updates
+ * into slabs, and at the end). */
+pp_status pp_iblt_build_decode(pp_iblt *t, const uint64_t *d_keys, uint64_t m, uint64_t *d_out_keys,
+                               uint64_t out_cap, pp_decode_result *res, void *stream);
+
 /* Build and decode from HOST buffers (Sec. 6: insert the keys, then recover
  * them), with the host<->device copies inside the call: the paper's GPU insert
  * times include the upload of the items.
  *   pp_iblt_submit_host  enqueues, for the m keys at h_keys: their upload (on
- *                        an upload stream the table owns), the build of
- *                        pp_iblt_build, the decode of pp_iblt_decode, and the
+ *                        an upload stream the table owns), the build and
+ *                        decode of pp_iblt_build_decode, and the
  *                        download of the recovered keys into h_out (on a
  *                        download stream; out_cap >= m, else CAPACITY), then
  *                        returns a ticket without waiting for the GPU.

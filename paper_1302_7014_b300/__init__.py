@@ -158,6 +158,14 @@ class IBLT:
         """Decode in place; ``out`` (CUDA, 8-byte elements) receives the keys."""
         return self._decode(_lib.load().pp_iblt_decode, "pp_iblt_decode", out, round_cap, stream)
 
+    def build_decode(self, keys, out, round_cap: int = 4096, stream=None) -> DecodeOutcome:
+        """build(keys) then decode(out) in one call; a large table's build
+        then also finds the cells pure before round 1, and the decode does not
+        scan the table again."""
+        kp, n = _dev_ptr(keys, 8, "keys"), keys.numel()
+        return self._decode(lambda h, o, cap, res, st: _lib.load().pp_iblt_build_decode(h, kp, n, o, cap, res, st),
+                            "pp_iblt_build_decode", out, round_cap, stream)
+
     def decode_subrounds(self, out, round_cap: int = 4096, stream=None) -> DecodeOutcome:
         """Decode in place with one sub-table per sub-round (App. B); the per-round
         lists of the outcome are per sub-round."""

@@ -56,6 +56,7 @@ _SIGNATURES = {
     "pp_iblt_delete": (ctypes.c_int, [vp, vp, u64, vp]),
     "pp_iblt_build": (ctypes.c_int, [vp, vp, u64, vp]),
     "pp_iblt_decode": (ctypes.c_int, [vp, vp, u64, ctypes.POINTER(DecodeResult), vp]),
+    "pp_iblt_build_decode": (ctypes.c_int, [vp, vp, u64, vp, u64, ctypes.POINTER(DecodeResult), vp]),
     "pp_iblt_copy_cells": (ctypes.c_int, [vp, vp, u64, u64, ctypes.c_int, vp]),
     "pp_iblt_info": (ctypes.c_int, [vp, ctypes.POINTER(u64), ctypes.POINTER(u32), ctypes.POINTER(u64)]),
     "pp_peel_kcore": (ctypes.c_int, [u32, u32, u32, vp, u64, vp, vp, ctypes.POINTER(PeelResult),

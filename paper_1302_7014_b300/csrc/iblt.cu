@@ -64,6 +64,7 @@ static IbltKernels iblt_kernels_t() {
     k.tapply = (const void *)k_tapply<R, B>;
     k.tapply_sparse = (const void *)k_tapply_sparse<R, B>;
     k.trestore = (const void *)k_trestore<R, B>;
+    if constexpr (!B) k.trescan = (const void *)k_trescan<R>;
     static bool tattr = false;
     if (!tattr) {
       allow_max_dynamic_smem((const void *)k_tapply<R, B>);
@@ -192,6 +193,8 @@ pp_status tre_setup(TileRoundEngine &e, const IbltKernels &k, uint64_t n_cells, 
   if (err == cudaSuccess) err = cudaMalloc((void **)&b.act, (size_t)nt * sizeof(TileAct));
   if (err == cudaSuccess) err = cudaMalloc((void **)&b.act_d, (size_t)nt * sizeof(TileAct));
   if (err == cudaSuccess) err = cudaMalloc((void **)&b.fseg, (size_t)(nd + nsp) * sizeof(u32));
+  if (err == cudaSuccess) err = cudaMalloc((void **)&b.rescan, (size_t)nt * sizeof(u32));
+  if (err == cudaSuccess) err = cudaMalloc((void **)&b.n_rescan, sizeof(u32));
   if (err == cudaSuccess) err = cudaMalloc((void **)&b.cpos, (size_t)b.n_bins * kTRPosStride * sizeof(u32));
   if (err == cudaSuccess) err = cudaMalloc((void **)&b.cdone, (size_t)b.n_bins * sizeof(u32));
   if (err == cudaSuccess) err = cudaMalloc((void **)&d_start, (size_t)(nd + nsp) * sizeof(u64));
@@ -260,6 +263,8 @@ void tre_free(TileRoundEngine &e) {
   cudaFree(b.act);
   cudaFree(b.act_d);
   cudaFree(b.fseg);
+  cudaFree(b.rescan);
+  cudaFree(b.n_rescan);
   cudaFree(const_cast<u64 *>(b.fstart));
   e = TileRoundEngine{};
 }
@@ -299,7 +304,8 @@ void tre_launch_args(TileRoundLaunch &a, const TileRoundEngine &e, Cell *cells, 
   a.bind();
 }
 
-pp_status tre_build_graph(const TileRoundEngine &e, const IbltKernels &k, TileRoundLaunch &a, cudaGraphExec_t *exec) {
+pp_status tre_build_graph(const TileRoundEngine &e, const IbltKernels &k, TileRoundLaunch &a, cudaGraphExec_t *exec,
+                          bool prescanned) {
   *exec = nullptr;
   cudaGraph_t g = nullptr;
   PP_CUDA(cudaGraphCreate(&g, 0));
@@ -308,7 +314,7 @@ pp_status tre_build_graph(const TileRoundEngine &e, const IbltKernels &k, TileRo
   cudaGraphConditionalHandle h;
   cudaGraphNodeParams cp{};
   cudaGraph_t body;
-  st = tre_node(&n_scan, g, nullptr, 0, k.tscan, e.grid_tscan, kTRThreads, 0, a.scan);
+  st = tre_node(&n_scan, g, nullptr, 0, prescanned ? k.trescan : k.tscan, e.grid_tscan, kTRThreads, 0, a.scan);
   if (st != PP_OK) goto done;
   st = tre_node(&n_pre, g, &n_scan, 1, (const void *)k_tprefix, 1, 1024, 0, a.prefix);
   if (st != PP_OK) goto done;
@@ -354,9 +360,9 @@ done:
 }
 
 pp_status tre_host_loop(const TileRoundEngine &e, const IbltKernels &k, TileRoundLaunch &a, u32 *h_more,
-                        cudaStream_t s) {
+                        cudaStream_t s, bool prescanned) {
   a.set_cond = 0;
-  PP_CUDA(cudaLaunchKernel(k.tscan, dim3(e.grid_tscan), dim3(kTRThreads), a.scan, 0, s));
+  PP_CUDA(cudaLaunchKernel(prescanned ? k.trescan : k.tscan, dim3(e.grid_tscan), dim3(kTRThreads), a.scan, 0, s));
   PP_CUDA(cudaLaunchKernel((const void *)k_tprefix, dim3(1), dim3(1024), a.prefix, 0, s));
   for (;;) {
     PP_CUDA(cudaLaunchKernel(k.tclaim, dim3(e.grid_tclaim), dim3(kTClaimThreads), a.claim, e.smem_tclaim, s));
@@ -394,6 +400,8 @@ struct pp_iblt {
   int grid_scan = 0, grid_peel = 0, grid_filter = 0, grid_insert = 0, grid_bin = 0;
   size_t smem_peel = 0, smem_bin = 0;
   cudaGraphExec_t exec = nullptr;
+  cudaGraphExec_t exec_pre = nullptr;  // tile rounds after a build that found F_1
+  uint32_t graph_gen_pre = 0;
   // update records shared by the slab-binned build and the binned decode
   // rounds (allocated on first use, grown as needed)
   uint32_t n_slabs = 0;
@@ -442,6 +450,7 @@ namespace {
 void free_all(pp_iblt *t) {
   if (!t) return;
   if (t->exec) cudaGraphExecDestroy(t->exec);
+  if (t->exec_pre) cudaGraphExecDestroy(t->exec_pre);
   if (t->sub_exec) cudaGraphExecDestroy(t->sub_exec);
   if (t->sub_exec_binned) cudaGraphExecDestroy(t->sub_exec_binned);
   cudaFree(t->squeue);
@@ -933,6 +942,25 @@ pp_status build_tile_graph(pp_iblt *t) {
   return st;
 }
 
+// The tile rounds after a build that found F_1 (k_trescan instead of the scan):
+// their own graph, kept beside the plain decode's.
+pp_status launch_prescanned_rounds(pp_iblt *t, cudaStream_t s) {
+  TileRoundLaunch a;
+  fill_tile_args(t, a);
+  if (t->opt.host_loop) return tre_host_loop(t->tre, t->k, a, &t->h_ctl->more, s, true);
+  if (t->exec_pre && t->graph_gen_pre != t->rec_gen) {
+    cudaGraphExecDestroy(t->exec_pre);
+    t->exec_pre = nullptr;
+  }
+  if (!t->exec_pre) {
+    pp_status st = tre_build_graph(t->tre, t->k, a, &t->exec_pre, true);
+    if (st != PP_OK) return st;
+    t->graph_gen_pre = t->rec_gen;
+  }
+  PP_CUDA(cudaGraphLaunch(t->exec_pre, s));
+  return PP_OK;
+}
+
 pp_status run_tile_host_loop(pp_iblt *t, cudaStream_t s) {
   TileRoundLaunch a;
   fill_tile_args(t, a);
@@ -1088,10 +1116,11 @@ pp_status ensure_round_bins(pp_iblt *t, cudaStream_t s) {
 }
 
 // Pass 2: slab by slab (zero-filled first when building from scratch).
-pp_status apply_pass(pp_iblt *t, BinArgs &ba, int sign, bool zero_fill, cudaStream_t s) {
+pp_status apply_pass(pp_iblt *t, BinArgs &ba, int sign, bool zero_fill, cudaStream_t s,
+                     const PrescanArgs *pre = nullptr) {
   pp_status st = ensure_tiles(t->tiles, tile_cap_for(ba.cap), ba.cap, ba.n_slabs, false, s);
   if (st != PP_OK) return st;
-  return tile_apply_pass(t->cells, t->args, nullptr, ba, t->tiles, t->n, sign, zero_fill, s);
+  return tile_apply_pass(t->cells, t->args, nullptr, ba, t->tiles, t->n, sign, zero_fill, s, pre);
 }
 
 pp_status update(pp_iblt *t, const uint64_t *d_keys, uint64_t m, int sign, cudaStream_t s) {
@@ -1108,16 +1137,25 @@ namespace {
 
 // Enqueues a whole decode on s (control block set up, round loop launched);
 // nothing is read back.
-pp_status decode_enqueue(pp_iblt *t, uint64_t *d_out_keys, uint64_t out_cap, cudaStream_t s) {
+// Round kind: tile rounds (large tables built from insertions only), binned
+// atomic rounds (other large tables), direct atomics (small tables).
+bool want_tile_rounds(const pp_iblt *t) {
+  const bool large = t->n >= (1ull << 21);
+  return t->k.tscan && !t->has_deletes &&
+         (t->opt.rounds == 2 || (t->opt.rounds == 0 && large && t->opt.binned != 2));
+}
+
+void set_host_ctl(pp_iblt *t, uint64_t *d_out_keys, uint64_t out_cap) {
   memset(t->h_ctl, 0, sizeof(DecodeCtl));
   t->h_ctl->out = reinterpret_cast<u64 *>(d_out_keys);
   t->h_ctl->out_cap = out_cap;
   t->h_ctl->max_rounds = t->opt.max_rounds;
-  // round kind: tile rounds (large tables built from insertions only), binned
-  // atomic rounds (other large tables), direct atomics (small tables)
+}
+
+pp_status decode_enqueue(pp_iblt *t, uint64_t *d_out_keys, uint64_t out_cap, cudaStream_t s) {
+  set_host_ctl(t, d_out_keys, out_cap);
   const bool large = t->n >= (1ull << 21);
-  const bool want_tiles = t->k.tscan && !t->has_deletes &&
-                          (t->opt.rounds == 2 || (t->opt.rounds == 0 && large && t->opt.binned != 2));
+  const bool want_tiles = want_tile_rounds(t);
   const bool want_bins = !want_tiles && (t->opt.binned == 1 || (t->opt.binned == 0 && large));
   if (want_tiles) {
     pp_status st = ensure_tile_rounds(t, s);
@@ -1151,6 +1189,14 @@ pp_status decode_enqueue(pp_iblt *t, uint64_t *d_out_keys, uint64_t out_cap, cud
   return PP_OK;
 }
 
+pp_status ensure_flag(pp_iblt *t) {
+  if (!t->h_flag) {
+    PP_CUDA(cudaHostAlloc((void **)&t->h_flag, sizeof(u32), cudaHostAllocMapped | cudaHostAllocPortable));
+    PP_CUDA(cudaHostGetDevicePointer((void **)&t->d_flag, t->h_flag, 0));
+  }
+  return PP_OK;
+}
+
 // Fills *res from the control block c after a decode and the first ncopy
 // per-round statistics.
 pp_status decode_collect(const DecodeCtl &c, const u64 *h_rec, const u64 *h_alive, uint32_t ncopy,
@@ -1179,6 +1225,24 @@ pp_status decode_collect(const DecodeCtl &c, const u64 *h_rec, const u64 *h_aliv
   if (c.flags & FLAG_ROUND_LIMIT)
     return fail(PP_ERR_ROUND_LIMIT, "%s: stopped after max_rounds=%u rounds", fn, max_rounds);
   return PP_OK;
+}
+
+// Reads a finished decode's control block and statistics back into *res.
+pp_status decode_result(pp_iblt *t, uint64_t out_cap, pp_decode_result *res, cudaStream_t s, const char *fn) {
+  const uint64_t items = t->items > 0 ? (uint64_t)t->items : 0;
+  PP_CUDA(cudaMemcpyAsync(t->h_ctl, t->ctl, sizeof(DecodeCtl), cudaMemcpyDeviceToHost, s));
+  PP_CUDA(cudaStreamSynchronize(s));
+  const DecodeCtl c = *t->h_ctl;
+  const uint32_t T = c.round;
+  const uint32_t ncopy = T < res->round_cap ? T : res->round_cap;
+  if (ncopy && (res->recovered_per_round || res->remaining_per_round || res->alive_cells_per_round)) {
+    PP_CUDA(cudaMemcpyAsync(t->h_rec, t->st_rec, ncopy * sizeof(u64), cudaMemcpyDeviceToHost, s));
+    PP_CUDA(cudaMemcpyAsync(t->h_alive, t->st_alive, ncopy * sizeof(u64), cudaMemcpyDeviceToHost, s));
+    PP_CUDA(cudaStreamSynchronize(s));
+  }
+  pp_status st = decode_collect(c, t->h_rec, t->h_alive, ncopy, items, out_cap, res, t->opt.max_rounds, fn);
+  t->items -= (int64_t)res->recovered;
+  return st;
 }
 
 }  // namespace
@@ -1266,7 +1330,7 @@ pp_status pp_workspace_size(uint64_t n_cells, uint32_t r, uint64_t m_keys, const
   if (rounds_tiles) {
     const uint64_t nt = (n + kTRCells - 1) / kTRCells;
     tile_round_bytes = ((uint64_t)r * m_keys + (uint64_t)kTRAlign * nt) * (2 * sizeof(u64) + sizeof(u16) + sizeof(u32)) +
-                       (nt + 1) * (sizeof(u64) + sizeof(u32)) + nt * (kTRPosStride * sizeof(u32) + 2 * sizeof(u32) +
+                       (nt + 1) * (sizeof(u64) + sizeof(u32)) + nt * (kTRPosStride * sizeof(u32) + 3 * sizeof(u32) +
                                                       2 * sizeof(TileAct));
   }
   const bool rounds_binned = !rounds_tiles && (o.binned == 1 || (o.binned == 0 && n >= (1ull << 21)));
@@ -1334,10 +1398,8 @@ pp_status pp_iblt_build(pp_iblt *t, const uint64_t *d_keys, uint64_t m, void *st
   if (st != PP_OK) return st;
   // the flag comes back through mapped memory, not a copy engine that may be
   // busy with another stream's bulk copy
-  if (!t->h_flag) {
-    PP_CUDA(cudaHostAlloc((void **)&t->h_flag, sizeof(u32), cudaHostAllocMapped | cudaHostAllocPortable));
-    PP_CUDA(cudaHostGetDevicePointer((void **)&t->d_flag, t->h_flag, 0));
-  }
+  st = ensure_flag(t);
+  if (st != PP_OK) return st;
   k_flag_to_host<<<1, 32, 0, s>>>(t->bin_overflow, t->d_flag);
   PP_CUDA(cudaGetLastError());
   PP_CUDA(cudaStreamSynchronize(s));
@@ -1363,19 +1425,7 @@ pp_status pp_iblt_decode(pp_iblt *t, uint64_t *d_out_keys, uint64_t out_cap, pp_
   cudaStream_t s = as_stream(stream);
   pp_status st = decode_enqueue(t, d_out_keys, out_cap, s);
   if (st != PP_OK) return st;
-  PP_CUDA(cudaMemcpyAsync(t->h_ctl, t->ctl, sizeof(DecodeCtl), cudaMemcpyDeviceToHost, s));
-  PP_CUDA(cudaStreamSynchronize(s));
-  const DecodeCtl c = *t->h_ctl;
-  const uint32_t T = c.round;
-  const uint32_t ncopy = T < res->round_cap ? T : res->round_cap;
-  if (ncopy && (res->recovered_per_round || res->remaining_per_round || res->alive_cells_per_round)) {
-    PP_CUDA(cudaMemcpyAsync(t->h_rec, t->st_rec, ncopy * sizeof(u64), cudaMemcpyDeviceToHost, s));
-    PP_CUDA(cudaMemcpyAsync(t->h_alive, t->st_alive, ncopy * sizeof(u64), cudaMemcpyDeviceToHost, s));
-    PP_CUDA(cudaStreamSynchronize(s));
-  }
-  st = decode_collect(c, t->h_rec, t->h_alive, ncopy, items, out_cap, res, t->opt.max_rounds, "pp_iblt_decode");
-  t->items -= (int64_t)res->recovered;
-  return st;
+  return decode_result(t, out_cap, res, s, "pp_iblt_decode");
 }
 
 pp_status pp_iblt_decode_subrounds(pp_iblt *t, uint64_t *d_out_keys, uint64_t out_cap,
@@ -1652,7 +1702,93 @@ pp_status build_enqueue(pp_iblt *t, const uint64_t *d_keys, uint64_t m, cudaStre
   return st;
 }
 
+// A build from m keys and its decode, enqueued on s.  When the build is
+// slab-binned and the tile rounds decode the table, the build's tile pass
+// also finds F_1 (PrescanArgs) and the decode skips its scan of the table;
+// otherwise the two run one after the other.  flag_dst null: the build's
+// slab-overflow flag is checked here (a full slab list falls back to the
+// direct build); else it is copied to flag_dst and nothing waits for it.
+// Events (may be null): `built` is recorded once the build has read d_keys;
+// the decode waits for `out_free` before it writes d_out_keys (the build
+// writes none of it).
+pp_status build_decode_enqueue(pp_iblt *t, const uint64_t *d_keys, uint64_t m, uint64_t *d_out_keys,
+                               uint64_t out_cap, cudaStream_t s, u32 *flag_dst, cudaEvent_t built = nullptr,
+                               cudaEvent_t out_free = nullptr) {
+  t->items = 0;
+  t->has_deletes = false;
+  const bool fused = use_binned(t, m) && t->k.trescan && want_tile_rounds(t);
+  if (!fused) {
+    pp_status st;
+    if (flag_dst) {
+      bool binned = false;
+      st = build_enqueue(t, d_keys, m, s, &binned);
+      if (st == PP_OK && binned) {
+        k_flag_to_host<<<1, 32, 0, s>>>(t->bin_overflow, flag_dst);
+        PP_CUDA(cudaGetLastError());
+      }
+    } else {
+      st = pp_iblt_build(t, d_keys, m, s);
+    }
+    if (st != PP_OK) return st;
+    if (built) PP_CUDA(cudaEventRecord(built, s));
+    if (out_free) PP_CUDA(cudaStreamWaitEvent(s, out_free, 0));
+    return decode_enqueue(t, d_out_keys, out_cap, s);
+  }
+  BinArgs ba;
+  pp_status st = bin_pass(t, d_keys, m, +1, 0, s, ba);
+  if (st != PP_OK) return st;
+  if (!flag_dst) {
+    st = ensure_flag(t);
+    if (st != PP_OK) return st;
+    k_flag_to_host<<<1, 32, 0, s>>>(t->bin_overflow, t->d_flag);
+    PP_CUDA(cudaGetLastError());
+    PP_CUDA(cudaStreamSynchronize(s));
+    if (*(volatile u32 *)t->h_flag) {
+      PP_CUDA(cudaMemsetAsync(t->cells, 0, t->n * sizeof(Cell), s));
+      st = launch_insert(t, d_keys, m, +1, s);
+      if (st != PP_OK) return st;
+      t->items = (int64_t)m;
+      if (built) PP_CUDA(cudaEventRecord(built, s));
+      if (out_free) PP_CUDA(cudaStreamWaitEvent(s, out_free, 0));
+      return decode_enqueue(t, d_out_keys, out_cap, s);
+    }
+  } else {
+    k_flag_to_host<<<1, 32, 0, s>>>(t->bin_overflow, flag_dst);
+    PP_CUDA(cudaGetLastError());
+  }
+  t->items = (int64_t)m;
+  st = ensure_tile_rounds(t, s);
+  if (st != PP_OK) return st;
+  // the decode's counters start before the build adds F_1 to them
+  set_host_ctl(t, d_out_keys, out_cap);
+  k_ctl_init<<<1, 32, 0, s>>>(t->ctl, *t->h_ctl);
+  PP_CUDA(cudaGetLastError());
+  const TileRoundBufs &tb = t->tre.trb;
+  PP_CUDA(cudaMemsetAsync(tb.fseg, 0, (size_t)tb.n_seg_d * sizeof(u32), s));
+  PP_CUDA(cudaMemsetAsync(tb.n_rescan, 0, sizeof(u32), s));
+  const PrescanArgs pre{tb, t->fkey, t->fcell, t->bitmap, t->ctl, t->args.seed[t->r]};
+  st = apply_pass(t, ba, +1, true, s, &pre);
+  if (st != PP_OK) return st;
+  if (built) PP_CUDA(cudaEventRecord(built, s));
+  if (out_free) PP_CUDA(cudaStreamWaitEvent(s, out_free, 0));
+  return launch_prescanned_rounds(t, s);
+}
+
 }  // namespace
+
+pp_status pp_iblt_build_decode(pp_iblt *t, const uint64_t *d_keys, uint64_t m, uint64_t *d_out_keys,
+                               uint64_t out_cap, pp_decode_result *res, void *stream) {
+  if (!t || !res) return fail(PP_ERR_INVALID_ARG, "pp_iblt_build_decode: NULL table or result");
+  if (m && !d_keys) return fail(PP_ERR_INVALID_ARG, "pp_iblt_build_decode: NULL keys");
+  if (out_cap < m)
+    return fail(PP_ERR_CAPACITY, "pp_iblt_build_decode: out_cap=%llu < %llu keys", (unsigned long long)out_cap,
+                (unsigned long long)m);
+  if (out_cap && !d_out_keys) return fail(PP_ERR_INVALID_ARG, "pp_iblt_build_decode: NULL output");
+  cudaStream_t s = as_stream(stream);
+  pp_status st = build_decode_enqueue(t, d_keys, m, d_out_keys, out_cap, s, nullptr);
+  if (st != PP_OK) return st;
+  return decode_result(t, out_cap, res, s, "pp_iblt_build_decode");
+}
 
 pp_status pp_iblt_submit_host(pp_iblt *t, const uint64_t *h_keys, uint64_t m, uint64_t *h_out, uint64_t out_cap,
                               uint64_t *ticket, void *stream) {
@@ -1712,16 +1848,10 @@ pp_status pp_iblt_submit_host(pp_iblt *t, const uint64_t *h_keys, uint64_t m, ui
   PP_CUDA(cudaStreamWaitEvent(s, j.up, 0));
   // The build is enqueued without waiting for its slab-overflow flag: the flag
   // travels with the job, and pp_iblt_finish_host redoes the job in the rare
-  // case it is set.
-  bool binned = false;
-  st = build_enqueue(t, reinterpret_cast<const uint64_t *>(j.d_keys), m, s, &binned);
-  if (st == PP_OK && binned) {
-    k_flag_to_host<<<1, 32, 0, s>>>(t->bin_overflow, j.d_flag);
-    if (cudaGetLastError() != cudaSuccess) st = fail(PP_ERR_CUDA, "pp_iblt_submit_host: flag copy launch failed");
-  }
-  if (st == PP_OK && cudaEventRecord(j.built, s) != cudaSuccess) st = fail(PP_ERR_CUDA, "event record failed");
-  if (st == PP_OK && cudaStreamWaitEvent(s, j.done, 0) != cudaSuccess) st = fail(PP_ERR_CUDA, "event wait failed");
-  if (st == PP_OK) st = decode_enqueue(t, reinterpret_cast<uint64_t *>(j.d_out), m, s);
+  // case it is set.  The decode writes the slot's output: it waits for the
+  // slot's previous download.
+  st = build_decode_enqueue(t, reinterpret_cast<const uint64_t *>(j.d_keys), m,
+                            reinterpret_cast<uint64_t *>(j.d_out), m, s, j.d_flag, j.built, j.done);
   if (st != PP_OK) {
     cudaStreamSynchronize(t->up_s);
     if (j.reg_keys) cudaHostUnregister(const_cast<uint64_t *>(h_keys));
@@ -1762,8 +1892,7 @@ pp_status pp_iblt_finish_host(pp_iblt *t, uint64_t ticket, pp_decode_result *res
     // table was incomplete.  Redo it on its stream (after any later job's
     // work there), with the build that checks the flag, then copy its keys.
     const uint64_t *dk = reinterpret_cast<const uint64_t *>(j->d_keys);
-    st = pp_iblt_build(t, dk, j->m, j->s);
-    if (st == PP_OK) st = decode_enqueue(t, reinterpret_cast<uint64_t *>(j->d_out), j->m, j->s);
+    st = build_decode_enqueue(t, dk, j->m, reinterpret_cast<uint64_t *>(j->d_out), j->m, j->s, nullptr);
     if (st == PP_OK) {
       const uint32_t ns = t->opt.max_rounds < kJobStatRounds ? t->opt.max_rounds : kJobStatRounds;
       k_to_host<<<1, 128, 0, j->s>>>(reinterpret_cast<const u64 *>(t->ctl), reinterpret_cast<u64 *>(j->d_ctl),

@@ -124,11 +124,86 @@ __device__ __forceinline__ void tile_bin(unsigned char *smem, const BinArgs &b, 
   }
 }
 
-// Role "apply" for tile `tile` of slab `slab`.
-template <bool BATCH>
+// The write-out of a tile that also finds F_1 (PrescanArgs): a pure cell is
+// stored empty and pushed into the frontier segment of its tile (warp-wide
+// reservations on the segment's count), each warp writes the bitmap word of
+// its 32 cells, and the tile's count sum and the decode's counters are
+// recorded.  The cells' values are the build's, so a cell is pure exactly when
+// a scan of the built table would find it pure.
+__device__ __forceinline__ void prescan_write(Cell *cells, u64 c0, u32 nc, const u64 *s_key, const u64 *s_chk,
+                                              const int *s_cnt, const PrescanArgs &pre) {
+  __shared__ u64 s_red[4][kTileThreads / 32];
+  const u32 T = (u32)(c0 >> kTileShift);
+  const u32 seg = T % pre.tb.n_seg_d;
+  const u64 sbase = (u64)seg * pre.tb.cap_d;
+  const u32 lane = lane_id();
+  u64 alive = 0, nonempty = 0, pushed = 0;
+  long long sum = 0;
+  u32 flags = 0;
+  for (u32 i = threadIdx.x; i < kTileCells; i += kTileThreads) {
+    const bool valid = i < nc;
+    bool pure = false;
+    if (valid) {
+      const u64 key = s_key[i], chk = s_chk[i];
+      const int cnt = s_cnt[i];
+      pure = cell_pure(cnt, key, chk, pre.seed_chk);
+      alive += cnt >= 2;
+      nonempty += cnt != 0;
+      sum += cnt;
+      if (pure) st_cell_cs(cells + c0 + i, 0ull, 0ull, 0);
+      else st_cell_cs(cells + c0 + i, key, chk, cnt);
+    }
+    const u32 ball = __ballot_sync(kFull, pure);
+    if (lane == 0 && c0 + i < c0 + nc) pre.bitmap[(c0 + i) >> 5] = ball;  // i is the warp's first cell
+    u32 base = 0;
+    if (lane == 0 && ball) base = atomicAdd(pre.tb.fseg + seg, (u32)__popc(ball));
+    base = __shfl_sync(kFull, base, 0);
+    if (pure) {
+      const u32 p = base + __popc(ball & lanemask_lt());
+      if (p < pre.tb.cap_d) {
+        pre.fkey[sbase + p] = s_key[i];
+        pre.fcell[sbase + p] = (u32)(c0 + i);
+      } else {
+        flags |= FLAG_INTERNAL;  // cannot happen: a segment holds every push of its tiles
+      }
+      pushed += 1;
+    }
+  }
+  // the four figures in one reduction: shuffles within each warp, then thread
+  // 0 over the warps (two's-complement sums, so the count sum may be signed)
+  u64 v[4] = {(u64)sum, alive, nonempty, pushed};
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_down_sync(kFull, v[k], o);
+    if (lane == 0) s_red[k][threadIdx.x >> 5] = v[k];
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    u64 t[4] = {0, 0, 0, 0};
+    for (int w = 0; w < kTileThreads / 32; ++w)
+#pragma unroll
+      for (int k = 0; k < 4; ++k) t[k] += s_red[k][w];
+    const long long sm = (long long)t[0];
+    pre.tb.sum[T] = sm > 0 ? (u32)sm : 0u;
+    if (t[1]) atomicAdd(&pre.ctl->alive, t[1]);
+    if (t[2]) atomicAdd(&pre.ctl->nonempty, t[2]);
+    if (t[3]) {
+      atomicAdd(&pre.ctl->emptied, t[3]);
+      atomicAdd(&pre.ctl->n_next, (u32)t[3]);
+    }
+  }
+  if (flags) atomicOr(&pre.ctl->flags, flags);
+}
+
+// Role "apply" for tile `tile` of slab `slab`.  PRESCAN (a build from empty
+// cells, single table): the tile's write-out also finds its cells pure before
+// any round (see PrescanArgs), unless overflow records will still change the
+// tile, which then goes to the rescan list.
+template <bool BATCH, bool PRESCAN = false>
 __device__ __forceinline__ void tile_apply(unsigned char *smem, Cell *cells, const TableArgs &tab0,
                                            const TableArgs *tabs, const TileArgs &ta, u32 slab, u32 tile,
-                                           u64 n_cells, int sign, int zero) {
+                                           u64 n_cells, int sign, int zero, const PrescanArgs &pre) {
   u64 *s_key = reinterpret_cast<u64 *>(smem);                 // kTileCells
   u64 *s_chk = s_key + kTileCells;                            // kTileCells
   int *s_cnt = reinterpret_cast<int *>(s_chk + kTileCells);   // kTileCells
@@ -190,6 +265,13 @@ __device__ __forceinline__ void tile_apply(unsigned char *smem, Cell *cells, con
   for (u32 l = threadIdx.x; l < (n * 4 + 127) / 128; l += kTileThreads) l2_discard(ta.cell + src + l * 32);
   if (BATCH)
     for (u32 l = threadIdx.x; l < (n * 4 + 127) / 128; l += kTileThreads) l2_discard(ta.tab + src + l * 32);
+  if constexpr (PRESCAN) {
+    if (cnt <= ta.cap) {
+      prescan_write(cells, c0, nc, s_key, s_chk, s_cnt, pre);
+      return;
+    }
+    if (threadIdx.x == 0) pre.tb.rescan[atomicAdd(pre.tb.n_rescan, 1u)] = (u32)(c0 >> kTileShift);
+  }
   for (u32 i = threadIdx.x; i < nc; i += kTileThreads) st_cell_cs(cells + c0 + i, s_key[i], s_chk[i], s_cnt[i]);
 }
 
@@ -323,11 +405,11 @@ __device__ __forceinline__ void tile_bin_keys(unsigned char *smem, const TableAr
 //               slab s - 2 only;
 //   bin role    (s < n_slabs): slab s.
 // n_apply / n_bin blocks of each role, interleaved by block index.
-template <bool BATCH>
+template <bool BATCH, bool PRESCAN = false>
 __global__ void __launch_bounds__(kTileThreads, 2) k_tile_step(Cell *__restrict__ cells, const TableArgs tab0,
                                                       const TableArgs *__restrict__ tabs, BinArgs b,
                                                       TileArgs ta, u32 s, u32 n_apply, u32 n_bin,
-                                                      u64 n_cells, int sign, int zero) {
+                                                      u64 n_cells, int sign, int zero, PrescanArgs pre) {
   extern __shared__ __align__(16) unsigned char smem[];
   const u32 both = n_apply < n_bin ? n_apply : n_bin;
   const u32 blk = blockIdx.x;
@@ -355,7 +437,8 @@ __global__ void __launch_bounds__(kTileThreads, 2) k_tile_step(Cell *__restrict_
       touch_cell_nr(cells, ta.o_cell[oset + i], x, checksum(x, chk_seed_of(T)), sign);
     }
   }
-  if (s >= 1 && s - 1 < b.n_slabs) tile_apply<BATCH>(smem, cells, tab0, tabs, ta, s - 1, idx, n_cells, sign, zero);
+  if (s >= 1 && s - 1 < b.n_slabs)
+    tile_apply<BATCH, PRESCAN>(smem, cells, tab0, tabs, ta, s - 1, idx, n_cells, sign, zero, pre);
 }
 
 // The batched tile step with the bin role taken from the keys (tile_bin_keys);
@@ -392,7 +475,8 @@ __global__ void __launch_bounds__(kTileThreads, 2) k_tile_step_keys(Cell *__rest
     }
   }
   const TableArgs t0{};
-  if (s >= 1 && s - 1 < ka.n_slabs) tile_apply<true>(smem, cells, t0, tabs, ta, s - 1, idx, n_cells, sign, zero);
+  const PrescanArgs none{};
+  if (s >= 1 && s - 1 < ka.n_slabs) tile_apply<true>(smem, cells, t0, tabs, ta, s - 1, idx, n_cells, sign, zero, none);
 }
 
 }  // namespace pp

@@ -226,6 +226,85 @@ __global__ void __launch_bounds__(kTRThreads, 2) k_tscan(Cell *__restrict__ cell
   }
 }
 
+// The scan of a decode whose build found F_1 (PrescanArgs): only the tiles of
+// tb.rescan, which the build's overflow pass changed after their write-out,
+// are scanned here, with what k_tscan does per tile; their pure cells join
+// the tile's frontier segment (tile % n_seg_d) behind the build's entries.
+// Usually the list is empty.
+template <int R>
+__global__ void __launch_bounds__(kTRThreads, 2) k_trescan(Cell *__restrict__ cells, const TableArgs tab0,
+                                                        u64 *__restrict__ fkey, u32 *__restrict__ fcell,
+                                                        u32 *__restrict__ bitmap, TileRoundBufs tb,
+                                                        DecodeCtl *__restrict__ ctl, TRBatch) {
+  __shared__ u64 s_red[kTRThreads / 32];
+  const u32 nl = *(volatile u32 *)tb.n_rescan;
+  if (blockIdx.x >= nl) return;  // uniform
+  const u32 tid = threadIdx.x, lane = lane_id();
+  const u64 seed_chk = tab0.seed[rank_of<R>(tab0)];
+  const u32 n = tab0.n_cells;
+  u64 alive = 0, nonempty = 0, pushed = 0;
+  u32 flags = 0;
+  for (u32 li = blockIdx.x; li < nl; li += gridDim.x) {
+    const u32 t = tb.rescan[li];
+    const u32 c0 = t << kTRShift;
+    const u32 seg = t % tb.n_seg_d;
+    const u64 sbase = (u64)seg * tb.cap_d;
+    long long sum = 0;
+    u64 keys[kTRScanItems], chks[kTRScanItems];
+    int cnts[kTRScanItems];
+#pragma unroll
+    for (int it = 0; it < kTRScanItems; ++it) {
+      const u32 c = c0 + (u32)it * kTRThreads + tid;
+      keys[it] = chks[it] = 0;
+      cnts[it] = 0;
+      if (c < n) ld_cell_cs(cells + c, keys[it], chks[it], cnts[it]);
+    }
+#pragma unroll
+    for (int it = 0; it < kTRScanItems; ++it) {
+      const u32 c = c0 + (u32)it * kTRThreads + tid;
+      bool pure = false;
+      if (c < n) {
+        const int cnt = cnts[it];
+        pure = cell_pure(cnt, keys[it], chks[it], seed_chk);
+        alive += cnt >= 2;
+        nonempty += cnt != 0;
+        sum += cnt;
+        if (pure) st_cell_cs(cells + c, 0ull, 0ull, 0);
+      }
+      const u32 ball = __ballot_sync(kFull, pure);
+      const u32 first = c0 + (u32)it * kTRThreads + (tid & ~31u);
+      if (lane == 0 && first < n) bitmap[first >> 5] = ball;
+      u32 base = 0;
+      if (lane == 0 && ball) base = atomicAdd(tb.fseg + seg, (u32)__popc(ball));
+      base = __shfl_sync(kFull, base, 0);
+      if (pure) {
+        const u32 p = base + __popc(ball & lanemask_lt());
+        if (p < tb.cap_d) {
+          fkey[sbase + p] = keys[it];
+          fcell[sbase + p] = c;
+        } else {
+          flags |= FLAG_INTERNAL;  // cannot happen: a segment holds every push of its tiles
+        }
+        pushed += 1;
+      }
+    }
+    const long long sm = block_sum<long long, kTRThreads>(sum, reinterpret_cast<long long *>(s_red));
+    if (tid == 0) tb.sum[t] = sm > 0 ? (u32)sm : 0u;
+  }
+  const u64 a = block_sum<u64, kTRThreads>(alive, s_red);
+  const u64 ne = block_sum<u64, kTRThreads>(nonempty, s_red);
+  const u64 pu = block_sum<u64, kTRThreads>(pushed, s_red);
+  if (tid == 0) {
+    if (a) atomicAdd(&ctl->alive, a);
+    if (ne) atomicAdd(&ctl->nonempty, ne);
+    if (pu) {
+      atomicAdd(&ctl->emptied, pu);
+      atomicAdd(&ctl->n_next, (u32)pu);
+    }
+  }
+  if (flags) atomicOr(&ctl->flags, flags);
+}
+
 // Tile regions: base[t] = sum over t' < t of the tile sums, each rounded up to
 // kTRAlign records; cursors at 0; every sparse segment empty.  One block;
 // flags FLAG_CAPACITY if the regions exceed the record buffers.  Then F_1

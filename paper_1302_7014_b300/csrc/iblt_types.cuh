@@ -181,8 +181,10 @@ void free_tiles(TileBufs &tb);
 
 // Pass 2 of a binned update: every slab of `ba` through k_tile_bin and
 // k_tile_apply (zero = build from empty cells), then the last overflow flush.
+struct PrescanArgs;  // below
 pp_status tile_apply_pass(Cell *cells, const TableArgs &tab0, const TableArgs *tabs, const BinArgs &ba,
-                          TileBufs &tb, uint64_t n_cells, int sign, bool zero, cudaStream_t s);
+                          TileBufs &tb, uint64_t n_cells, int sign, bool zero, cudaStream_t s,
+                          const PrescanArgs *pre = nullptr);
 // Batched tile pass with the bin role fed from the keys: slab_chunk (device,
 // 2 * n_slabs) holds each slab's range of `chunks`; rank as for iblt_kernels.
 // Every record of a slab must fit its overflow set (tb.o_cap).
@@ -222,6 +224,21 @@ struct TileRoundBufs {
   u32 cap_d;      // entries of a k_tscan / k_tapply segment: 4096 * ceil(n_tiles / n_seg_d)
   u32 cap_s;      // entries of a k_tapply_sparse segment: kTSCap * ceil(n_tiles / n_seg_s)
   u32 pad;
+  u32 *rescan;    // tiles the decode must scan itself (a build that found F_1 could not finish them)
+  u32 *n_rescan;
+};
+
+// A build whose tile pass also finds F_1 (pp_iblt_build_decode): as it writes
+// a tile out, the apply role stores the tile's pure cells empty and pushes
+// them into the tile's frontier segment (tile % n_seg_d), writes the tile's
+// bitmap words and count sum, and adds to the decode's counters.  A tile whose
+// cells the overflow pass changes after that write goes to tb.rescan instead.
+struct PrescanArgs {
+  TileRoundBufs tb;
+  u64 *fkey;
+  u32 *fcell, *bitmap;
+  DecodeCtl *ctl;
+  u64 seed_chk;
 };
 
 // 32-cell words per 4096-cell tile of the tile rounds (the batch's word maps
@@ -251,6 +268,7 @@ struct IbltKernels {
   const void *sg_claim = nullptr, *sg_apply = nullptr;                         // signed, binned rounds
   const void *tscan = nullptr, *tclaim = nullptr, *tapply = nullptr;           // tile rounds (plain only)
   const void *tapply_sparse = nullptr, *trestore = nullptr;
+  const void *trescan = nullptr;  // tile rounds after a build that found F_1 (plain only)
 };
 
 // The kernel set for a rank code: 3 or 4 = that r; -4 = any r <= 4 (batched
@@ -301,11 +319,14 @@ void tre_launch_args(TileRoundLaunch &a, const TileRoundEngine &e, Cell *cells, 
                      u32 *fcell, u32 *bitmap, DecodeCtl *ctl, const RoundStats &st, const TRBatch &bt);
 // The decode as a CUDA graph: scan, prefix, a while node over the round
 // kernels, restore.
-pp_status tre_build_graph(const TileRoundEngine &e, const IbltKernels &k, TileRoundLaunch &a, cudaGraphExec_t *exec);
+pp_status tre_build_graph(const TileRoundEngine &e, const IbltKernels &k, TileRoundLaunch &a, cudaGraphExec_t *exec,
+                          bool prescanned = false);
 // The same kernels driven from the host (one synchronisation per round);
-// h_more: pinned copy of ctl->more.
+// h_more: pinned copy of ctl->more.  prescanned: the build found F_1, so the
+// decode starts with k_trescan (the tiles the build could not finish) instead
+// of the full scan.
 pp_status tre_host_loop(const TileRoundEngine &e, const IbltKernels &k, TileRoundLaunch &a, u32 *h_more,
-                        cudaStream_t s);
+                        cudaStream_t s, bool prescanned = false);
 
 // Dynamic shared memory of the peel kernel.
 size_t peel_smem_bytes(int nr, bool batch);

@@ -26,7 +26,8 @@ static size_t tile_step_smem() {
   return bin > apply ? bin : apply;
 }
 
-static const void *tile_step_fn(bool batch) {
+static const void *tile_step_fn(bool batch, bool prescan = false) {
+  if (prescan) return (const void *)k_tile_step<false, true>;
   return batch ? (const void *)k_tile_step<true> : (const void *)k_tile_step<false>;
 }
 
@@ -92,13 +93,18 @@ pp_status ensure_tiles(TileBufs &tb, uint64_t tile_cap, uint64_t o_cap, uint32_t
   static bool attr[2] = {false, false};
   if (!attr[batch]) {
     cudaFuncSetAttribute(tile_step_fn(batch), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tile_step_smem());
+    if (!batch)
+      cudaFuncSetAttribute(tile_step_fn(false, true), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)tile_step_smem());
     attr[batch] = true;
   }
   return PP_OK;
 }
 
 pp_status tile_apply_pass(Cell *cells, const TableArgs &tab0, const TableArgs *tabs, const BinArgs &ba,
-                          TileBufs &tb, uint64_t n_cells, int sign, bool zero, cudaStream_t s) {
+                          TileBufs &tb, uint64_t n_cells, int sign, bool zero, cudaStream_t s,
+                          const PrescanArgs *pre) {
+  if (pre && (tb.batch || !zero)) return fail(PP_ERR_INVALID_ARG, "tile pass: F_1 is found only by a plain build");
   PP_CUDA(cudaMemsetAsync(tb.o_count, 0, (size_t)ba.n_slabs * 4, s));
   TileArgs ta{tb.key, tb.cell, tb.tab, tb.count, tb.cap * kTilesPerSlab, (u32)tb.cap, (u32)tb.o_cap,
               tb.o_key, tb.o_cell, tb.o_tab, tb.o_count};
@@ -109,7 +115,9 @@ pp_status tile_apply_pass(Cell *cells, const TableArgs &tab0, const TableArgs *t
   u32 step = 0, n_apply = 0, n_bin = 0;
   u64 n = n_cells;
   int sg = sign, z = zero ? 1 : 0;
-  void *args[] = {&c, &t0, &tp, &b, &ta, &step, &n_apply, &n_bin, &n, &sg, &z};
+  PrescanArgs pa = pre ? *pre : PrescanArgs{};
+  void *args[] = {&c, &t0, &tp, &b, &ta, &step, &n_apply, &n_bin, &n, &sg, &z, &pa};
+  const void *fn = tile_step_fn(tb.batch, pre != nullptr);
   const u32 ns = ba.n_slabs;
   const u32 sms = (u32)sm_count();
   // launch s: sort slab s while slab s - 1 is applied tile by tile
@@ -117,8 +125,7 @@ pp_status tile_apply_pass(Cell *cells, const TableArgs &tab0, const TableArgs *t
     n_bin = step < ns ? 3 * sms : 0u;
     n_apply = (step >= 1 && step - 1 < ns) ? kTilesPerSlab : (step == ns + 1 ? 2 * sms : 0u);
     if (n_apply + n_bin == 0) continue;
-    PP_CUDA(cudaLaunchKernel(tile_step_fn(tb.batch), dim3(n_apply + n_bin), dim3(kTileThreads), args,
-                             tile_step_smem(), s));
+    PP_CUDA(cudaLaunchKernel(fn, dim3(n_apply + n_bin), dim3(kTileThreads), args, tile_step_smem(), s));
   }
   return PP_OK;
 }

@@ -354,3 +354,26 @@ def test_tile_rounds_fall_back_after_deletions(ppb):
         region = np.sort(got[int(ooff[i]): int(ooff[i]) + int(res.recovered[i])])
         want = np.sort(np.concatenate(ores["keys"])) if ores["keys"] else np.zeros(0, np.uint64)
         assert (region == want).all(), i
+
+
+def test_tile_rounds_decode_twice_and_reuse(ppb):
+    """Tile rounds over the arena: a second decode finds nothing left (the
+    residue is a 2-core), and the batch cleared and refilled with other keys
+    decodes them exactly (the graph and buffers are reused or rebuilt)."""
+    pp, bm = ppb
+    specs = _specs(24, 251, rs=(3, 4), lo=10, hi=15, c_lo=0.6, c_hi=1.0)
+    b, keys, ooff, res, got = run_batch(pp, bm, specs, pp.options(rounds=2))
+    check_against_oracle(specs, keys, ooff, res, got, b)
+    out = torch.full((max(1, int(ooff[-1])),), -1, dtype=torch.int64, device="cuda")
+    res2 = b.decode(out, ooff)
+    for i in range(len(specs)):
+        assert res2.rounds[i] == 0 and res2.recovered[i] == 0, i
+        assert res2.residual_cells[i] == res.residual_cells[i], i
+    specs2 = [(s[0], s[1], s[2] * 0.8, s[3], s[4] + 1) for s in specs]
+    keys2 = [ppgen.distinct_keys(ppgen.edges_from_c(s[2], s[0]), s[4]) for s in specs2]
+    koff2 = np.concatenate([[0], np.cumsum([k.size for k in keys2])]).astype(np.uint64)
+    b.clear()
+    b.insert(torch.from_numpy(np.concatenate(keys2).view(np.int64)).cuda(), koff2)
+    out2 = torch.full((max(1, int(koff2[-1])),), -1, dtype=torch.int64, device="cuda")
+    res3 = b.decode(out2, koff2)
+    check_against_oracle(specs2, keys2, koff2, res3, out2.cpu().numpy().view(np.uint64), b, cells_every=2)

@@ -455,3 +455,125 @@ def test_tile_rounds_after_workspace_growth(pp):
         assert res.rounds == ores["rounds"]
         assert res.recovered_per_round == [k.size for k in ores["keys"]]
         _assert_cells_equal(gt.cells(), ot)
+
+
+# ---- build + decode in one call: the build's tile pass finds F_1 -------------
+def run_fused_case(pp, n, r, keys, seed, opts=None, max_rounds=None):
+    """build_decode on the GPU against insert + decode_rounds in the oracle:
+    per-round key sets, survivors and the residue, cell for cell."""
+    gt = pp.IBLT(n, r, seed, opts)
+    ot = oracle.IBLT(n, r, seed)
+    ot.insert(keys)
+    out = torch.zeros(max(1, keys.size), dtype=torch.int64, device="cuda")
+    ores = ot.decode_rounds() if max_rounds is None else ot.decode_rounds(max_rounds=max_rounds)
+    try:
+        res = gt.build_decode(_dev(keys), out)
+    except pp.PPError:
+        _assert_cells_equal(gt.cells(), ot)       # what is left after the last completed round
+        gt.close()
+        raise
+    assert res.rounds == ores["rounds"]
+    got = out[: res.recovered].cpu().numpy().view(np.uint64)
+    rounds = _split_rounds(got, res.recovered_per_round)
+    assert len(rounds) == len(ores["keys"])
+    for t, (a, b) in enumerate(zip(rounds, ores["keys"])):
+        assert a.size == b.size and (a == np.sort(b)).all(), f"round {t + 1}"
+    assert res.alive_cells_per_round == ores["cells_alive"]
+    left = keys.size - np.cumsum([k.size for k in ores["keys"]])
+    assert res.remaining_per_round == [int(x) for x in left]
+    _assert_cells_equal(gt.cells(), ot)
+    assert res.residual_cells == ot.residual_cells()
+    gt.close()
+    return res, ores
+
+
+FUSED_CASES = [
+    # n_cells, r, load c, seed: binned builds (forced on below 2^23 cells) into tile rounds
+    (65541, 3, 0.75, 91),                   # one partial slab
+    ((1 << 21) + 1, 4, 0.85, 92),           # above c*_{2,4}: a residue is left
+    (3 * (1 << 21) + 17, 3, 0.75, 93),      # ragged last slab and tile
+    ((1 << 22), 3, 0.90, 94),               # above c*_{2,3}
+    ((1 << 22) + 5, 5, 0.60, 95),
+]
+
+
+@pytest.mark.parametrize("n,r,c,seed", FUSED_CASES, ids=[f"fused-n{n}-r{r}-c{c}" for n, r, c, _ in FUSED_CASES])
+@pytest.mark.parametrize("host_loop", [0, 1], ids=["graph", "hostloop"])
+def test_build_decode_parity(pp, n, r, c, seed, host_loop):
+    keys = ppgen.distinct_keys(ppgen.edges_from_c(c, n), 9000 + seed)
+    run_fused_case(pp, n, r, keys, seed, opts=pp.options(binned=1, rounds=2, host_loop=host_loop))
+
+
+def test_build_decode_default_options_headline_shape(pp):
+    """Default options at 2^23 cells: the slab-binned build and the tile rounds
+    are both chosen, so the fused path runs."""
+    n, r, seed = 1 << 23, 3, 96
+    keys = ppgen.distinct_keys(ppgen.edges_from_c(0.75, n), 9096)
+    res, _ = run_fused_case(pp, n, r, keys, seed)
+    assert res.recovered == keys.size
+
+
+@pytest.mark.parametrize("host_loop", [0, 1], ids=["graph", "hostloop"])
+def test_build_decode_crowded_tile_is_rescanned(pp, host_loop):
+    """Keys whose first cell falls in one 4096-cell tile push that tile's update
+    list past its share (the mean tile's, with 15 % slack and 256 records), so
+    the build cannot find F_1 there when it writes the tile out; the decode
+    scans that tile itself and the results still match the oracle."""
+    n, r, seed = 1 << 22, 3, 97
+    base = ppgen.distinct_keys(ppgen.edges_from_c(0.6, n), 9097)
+    cand = ppgen.distinct_keys(2_000_000, 9098)
+    cand = np.setdiff1d(cand, base)
+    first = oracle.key_cells(n, r, seed, cand)[:, 0].astype(np.int64)
+    tile = 5
+    crowd = cand[(first >> 12) == tile][:4000]
+    keys = np.concatenate([base, crowd])
+    cells = oracle.key_cells(n, r, seed, keys).astype(np.int64)
+    per_tile = np.bincount((cells >> 12).ravel(), minlength=(n + 4095) >> 12)
+    assert per_tile[tile] > 1.3 * per_tile.mean() + 256
+    run_fused_case(pp, n, r, keys, seed, opts=pp.options(binned=1, rounds=2, host_loop=host_loop))
+
+
+def test_build_decode_round_limit(pp):
+    n, r, seed = (1 << 21) + 3, 3, 98
+    keys = ppgen.distinct_keys(ppgen.edges_from_c(0.80, n), 9099)
+    with pytest.raises(pp.PPError) as ei:
+        run_fused_case(pp, n, r, keys, seed, opts=pp.options(binned=1, rounds=2, max_rounds=3), max_rounds=3)
+    assert ei.value.name == "PP_ERR_ROUND_LIMIT"
+
+
+def test_build_decode_repeated_with_growth_and_plain_calls(pp):
+    """build_decode with growing key counts (record buffers reallocated, the
+    graphs rebuilt), mixed with plain build/insert/decode calls on the same
+    table; also small tables and empty inputs, which take the unfused path."""
+    n, r, seed = 3 * (1 << 20) + 11, 3, 99
+    gt = pp.IBLT(n, r, seed, pp.options(binned=1, rounds=2))
+    for i, c in enumerate((0.1, 0.8, 0.5, 0.0)):
+        keys = ppgen.distinct_keys(ppgen.edges_from_c(c, n), 9100 + i)
+        out = torch.zeros(max(1, keys.size), dtype=torch.int64, device="cuda")
+        res = gt.build_decode(_dev(keys), out)
+        ot = oracle.IBLT(n, r, seed)
+        ot.insert(keys)
+        ores = ot.decode_rounds()
+        assert res.rounds == ores["rounds"]
+        assert res.recovered_per_round == [k.size for k in ores["keys"]]
+        got = np.sort(out[: res.recovered].cpu().numpy().view(np.uint64))
+        want = np.sort(np.concatenate(ores["keys"])) if ores["keys"] else np.zeros(0, np.uint64)
+        assert (got == want).all()
+        _assert_cells_equal(gt.cells(), ot)
+        # a plain decode of more keys inserted on top uses the other graph
+        more = ppgen.distinct_keys(ppgen.edges_from_c(0.05, n), 9200 + i)
+        gt.insert(_dev(more))
+        ot.insert(more)
+        res = gt.decode(torch.zeros(more.size + keys.size, dtype=torch.int64, device="cuda"))
+        ores = ot.decode_rounds()
+        assert res.recovered_per_round == [k.size for k in ores["keys"]]
+        _assert_cells_equal(gt.cells(), ot)
+    gt.close()
+    small = pp.IBLT(5000, 3, 7)
+    keys = ppgen.distinct_keys(3000, 9300)
+    out = torch.zeros(keys.size, dtype=torch.int64, device="cuda")
+    res, _ = run_fused_case(pp, 5000, 3, keys, 7)
+    with pytest.raises(pp.PPError) as ei:
+        small.build_decode(_dev(keys), out[:10])
+    assert ei.value.name == "PP_ERR_CAPACITY"
+    small.close()
