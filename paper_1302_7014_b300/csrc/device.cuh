@@ -88,6 +88,21 @@ __device__ __forceinline__ void touch_cell_nr(Cell *cells, u32 c, u64 x, u64 cs,
   atomicXor(&p->chk, cs);
 }
 
+// XOR of v into the 64-bit word at p in shared memory: one 64-bit atomic
+// (PP_SMEM_XOR64=1) or one 32-bit atomic per half (XOR acts bitwise, so the
+// halves are independent).
+#ifndef PP_SMEM_XOR64
+#define PP_SMEM_XOR64 0
+#endif
+__device__ __forceinline__ void smem_xor64(u64 *p, u64 v) {
+#if PP_SMEM_XOR64
+  atomicXor(reinterpret_cast<unsigned long long *>(p), (unsigned long long)v);
+#else
+  atomicXor(reinterpret_cast<u32 *>(p), (u32)v);
+  atomicXor(reinterpret_cast<u32 *>(p) + 1, (u32)(v >> 32));
+#endif
+}
+
 // Per-table constants.  Sub-table j is cells base+off[j] .. base+off[j+1]-1.
 struct __align__(16) TableArgs {
   u64 seed[PP_MAX_R + 1];  // hash seeds s_0..s_{r-1}, checksum seed at [r]

@@ -207,8 +207,6 @@ __device__ __forceinline__ void tile_apply(unsigned char *smem, Cell *cells, con
   u64 *s_key = reinterpret_cast<u64 *>(smem);                 // kTileCells
   u64 *s_chk = s_key + kTileCells;                            // kTileCells
   int *s_cnt = reinterpret_cast<int *>(s_chk + kTileCells);   // kTileCells
-  u32 *s_key32 = reinterpret_cast<u32 *>(s_key);  // XOR works on each 32-bit half
-  u32 *s_chk32 = reinterpret_cast<u32 *>(s_chk);
   const u64 c0 = ((u64)slab << kSlabShift) + ((u64)tile << kTileShift);
   if (c0 >= n_cells) return;  // uniform per block
   const u32 nc = (u32)(c0 + kTileCells <= n_cells ? kTileCells : n_cells - c0);
@@ -250,10 +248,8 @@ __device__ __forceinline__ void tile_apply(unsigned char *smem, Cell *cells, con
         const u32 o = off[it];
         const u64 cs = checksum(x[it], seed[it]);
         atomicAdd(s_cnt + o, sign);
-        atomicXor(s_chk32 + 2 * o, (u32)cs);
-        atomicXor(s_chk32 + 2 * o + 1, (u32)(cs >> 32));
-        atomicXor(s_key32 + 2 * o, (u32)x[it]);
-        atomicXor(s_key32 + 2 * o + 1, (u32)(x[it] >> 32));
+        smem_xor64(s_chk + o, cs);
+        smem_xor64(s_key + o, x[it]);
       }
     }
   }

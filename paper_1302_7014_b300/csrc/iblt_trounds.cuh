@@ -137,6 +137,54 @@ __device__ __forceinline__ void block_exclusive_scan(const u32 *in, u32 *out, u3
   __syncthreads();
 }
 
+// By one warp: the exclusive prefix of cnt[0..n) into scan[0..n] (scan[n] =
+// the total), for every k with cnt[k] > 0 a run of cnt[k] slots reserved at
+// *cursor(k) (its first slot into base[k]), and cnt[k] set back to 0 for the
+// next chunk.  Lane l takes a contiguous share; the reservations of a lane's
+// share (at most 4 when n <= 128) are all in flight at once.  The rest of the
+// block needs none of this until the next barrier, so a chunk of a
+// partitioning kernel spends two barriers on its histogram, not five.
+template <class Cursor>
+__device__ __forceinline__ void warp_scan_reserve(u32 *cnt, u32 *scan, u32 *base, u32 n, Cursor cursor) {
+  const u32 lane = lane_id();
+  const u32 per = (n + 31) / 32;
+  const u32 lo = min(lane * per, n), hi = min(lo + per, n);
+  u32 own = 0;
+  for (u32 k = lo; k < hi; ++k) own += cnt[k];
+  u32 inc = own;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const u32 y = __shfl_up_sync(kFull, inc, o);
+    if ((int)lane >= o) inc += y;
+  }
+  u32 run = inc - own;
+  if (per <= 4) {
+    u32 c[4], b[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) c[q] = lo + q < hi ? cnt[lo + q] : 0u;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) b[q] = c[q] ? atomicAdd(cursor(lo + q), c[q]) : 0u;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      if (lo + q < hi) {
+        scan[lo + q] = run;
+        run += c[q];
+        base[lo + q] = b[q];
+        cnt[lo + q] = 0;
+      }
+    }
+  } else {
+    for (u32 k = lo; k < hi; ++k) {
+      const u32 c = cnt[k];
+      scan[k] = run;
+      run += c;
+      base[k] = c ? atomicAdd(cursor(k), c) : 0u;
+      cnt[k] = 0;
+    }
+  }
+  if (lane == 31) scan[n] = inc;
+}
+
 // Initial full scan, one tile per block step: F_1 (cells pure before any
 // round) with their bitmap bits, the sum of each tile's counts, and the
 // decode's alive / nonempty counters.  Every bitmap word is written here.
@@ -426,10 +474,10 @@ __global__ void __launch_bounds__(kTClaimThreads, PP_TCLAIM_CTAS) k_tclaim(Cell 
   u32 *s_scan = s_hist + nb;                            // nb + 1
   u32 *s_base = s_scan + nb + 1;                        // nb
   u32 *s_bb = s_base + nb;                              // nb + 1
-  __shared__ u64 s_out[kTClaimChunk];
+  __shared__ u64 s_out[2][kTClaimChunk];  // a chunk's recovered keys, two chunks in turn
   __shared__ u64 s_fx[2][kTClaimChunk];   // frontier entries of this chunk and the next
   __shared__ u32 s_fc[2][kTClaimChunk];
-  __shared__ u32 s_nout, s_wt[kTClaimThreads / 32], s_segn;
+  __shared__ u32 s_nout, s_nout_cur, s_wt[kTClaimThreads / 32], s_segn;
   __shared__ u64 s_obase;
   const u32 tid = threadIdx.x;
   const u32 n = *(volatile u32 *)&ctl->n_front;
@@ -441,6 +489,8 @@ __global__ void __launch_bounds__(kTClaimThreads, PP_TCLAIM_CTAS) k_tclaim(Cell 
   const u64 keep = l2_evict_last_policy();
   const u32 bsh = kTRShift + tb.bin_tshift;  // cell -> coarse bin
   for (u32 b = tid; b <= nb; b += kTClaimThreads) s_bb[b] = tb.base64[min(b << tb.bin_tshift, tb.n_tiles)];
+  for (u32 b = tid; b < nb; b += kTClaimThreads) s_hist[b] = 0;  // then zeroed by warp 0 after each chunk
+  if (tid == 0) s_nout = 0;
   block_exclusive_scan<kTClaimThreads>(tb.fseg, s_pre, ns, s_wt);
   // segment of entry c: the last k with s_pre[k] <= c
   auto seg_of = [&](u64 c) -> u32 {
@@ -483,15 +533,14 @@ __global__ void __launch_bounds__(kTClaimThreads, PP_TCLAIM_CTAS) k_tclaim(Cell 
   u32 flags = 0;
   const u64 stride = (u64)gridDim.x * kTClaimChunk;
   int buf = 0;
-  if ((u64)blockIdx.x * kTClaimChunk < n) fetch((u64)blockIdx.x * kTClaimChunk, seg_of((u64)blockIdx.x * kTClaimChunk), 0);
-  for (u64 c0 = (u64)blockIdx.x * kTClaimChunk; c0 < n; c0 += stride, buf ^= 1) {
+  const u64 first = (u64)blockIdx.x * kTClaimChunk;
+  if (first < n) fetch(first, seg_of(first), 0);
+  // s_segn: segment of the chunk fetched next (warp 0 finds each chunk's
+  // successor's while the chunk is reserved)
+  if (tid == 0) s_segn = first + stride < n ? seg_of(first + stride) : 0u;
+  __syncthreads();
+  for (u64 c0 = first; c0 < n; c0 += stride, buf ^= 1) {
     const u64 c1 = c0 + stride;
-    for (u32 i = tid; i < nb; i += kTClaimThreads) s_hist[i] = 0;
-    if (tid == 0) {
-      s_nout = 0;
-      s_segn = c1 < n ? seg_of(c1) : 0u;
-    }
-    __syncthreads();
     // the next chunk's entries travel while this one is claimed
     if (c1 < n) fetch(c1, s_segn, buf ^ 1);
     else cp_async_commit();  // an empty group keeps the wait below uniform
@@ -538,7 +587,7 @@ __global__ void __launch_bounds__(kTClaimThreads, PP_TCLAIM_CTAS) k_tclaim(Cell 
     for (int it = 0; it < kTClaimItems; ++it) {
       if constexpr (!BATCH) {
         const u32 p = warp_reserve<u32>(win[it], &s_nout);
-        if (win[it]) s_out[p] = x[it];
+        if (win[it]) s_out[buf][p] = x[it];
       } else {
         // the warp's winners of one table take one run of its output range
         const TableArgs &T = bt.tabs[tbl[it]];
@@ -566,12 +615,33 @@ __global__ void __launch_bounds__(kTClaimThreads, PP_TCLAIM_CTAS) k_tclaim(Cell 
         rk[it][j] = ((need[it] >> j) & 1u) ? atomicAdd(s_hist + (cj[it][j] >> bsh), 1u) : 0u;
     }
     __syncthreads();
-    block_exclusive_scan<kTClaimThreads>(s_hist, s_scan, nb, s_wt);
-    for (u32 k = tid; k < nb; k += kTClaimThreads) {
-      const u32 h = s_hist[k];
-      s_base[k] = h ? atomicAdd(tb.cpos + (u64)k * kTRPosStride, h) : 0u;
+    // bin offsets and cursor reservations (by warp 0 alone for up to 128
+    // bins), the output reservation and the next fetch's segment; the
+    // histogram and s_nout start over
+    auto cursor = [&](u32 k) { return tb.cpos + (u64)k * kTRPosStride; };
+    if (nb > 128) {
+      block_exclusive_scan<kTClaimThreads>(s_hist, s_scan, nb, s_wt);
+      for (u32 k = tid; k < nb; k += kTClaimThreads) {
+        const u32 h = s_hist[k];
+        s_base[k] = h ? atomicAdd(cursor(k), h) : 0u;
+        s_hist[k] = 0;
+      }
     }
-    if (tid == 0 && s_nout) s_obase = atomicAdd(&ctl->n_out, (u64)s_nout);
+    if (tid < 32) {
+      u32 no = 0;
+      u64 ob = 0;
+      if (tid == 0) {
+        no = s_nout;
+        if (no) ob = atomicAdd(&ctl->n_out, (u64)no);
+      }
+      if (nb <= 128) warp_scan_reserve(s_hist, s_scan, s_base, nb, cursor);
+      if (tid == 0) {
+        s_nout_cur = no;
+        s_nout = 0;
+        s_obase = ob;
+        s_segn = c1 + stride < n ? seg_of(c1 + stride) : 0u;
+      }
+    }
     __syncthreads();
 #pragma unroll
     for (int it = 0; it < kTClaimItems; ++it) {
@@ -597,13 +667,15 @@ __global__ void __launch_bounds__(kTClaimThreads, PP_TCLAIM_CTAS) k_tclaim(Cell 
         flags |= FLAG_INTERNAL;  // more records than the bin's counts allow
       }
     }
-    const u32 no = s_nout;
+    const u32 no = s_nout_cur;
     const u64 ob = s_obase;
     for (u32 q = tid; q < no; q += kTClaimThreads) {
-      if (ob + q < out_cap) out[ob + q] = s_out[q];
+      if (ob + q < out_cap) out[ob + q] = s_out[buf][q];
       else flags |= FLAG_CAPACITY;
     }
-    __syncthreads();
+    // no barrier here: what the next chunk writes before its first barrier
+    // (s_out, the fetch buffers, the histogram) is not read from here on,
+    // and the rest is written only after that barrier
   }
   if (flags) atomicOr(&ctl->flags, flags);
 }
@@ -621,6 +693,8 @@ constexpr int kTSortThreads = PP_TSORT_THREADS;
 constexpr int kTSortPer = PP_TSORT_PER;
 constexpr u32 kTSortChunk = kTSortThreads * kTSortPer;  // coarse records per work item
 constexpr u32 kMaxBinTiles = 512;                         // tiles per coarse bin (at most)
+static_assert(kMaxBinTiles <= 512 && kTSortChunk <= 2048 && kTRShift == 12 && kTSortPer <= 32,
+              "k_tsort packs tile (9 bits), cell offset (12) and rank (11) into one word");
 
 // Dynamic shared memory of k_tsort: the chunk prefix over the bins (n_bins + 1
 // u32), per bin the round's first and end record and its region's start /
@@ -642,7 +716,7 @@ __global__ void __launch_bounds__(kTSortThreads, PP_TSORT_CTAS) k_tsort(TileRoun
   u64 *s_key = reinterpret_cast<u64 *>(smem + tsort_head_bytes(nb));  // kTSortChunk
   u16 *s_off = reinterpret_cast<u16 *>(s_key + kTSortChunk);          // kTSortChunk
   __shared__ u32 s_cnt[kMaxBinTiles], s_scan[kMaxBinTiles + 1], s_tb[kMaxBinTiles];
-  __shared__ u32 s_tbase[kMaxBinTiles + 1];  // the chunk's bin: region start of each tile / kTRAlign
+  __shared__ u32 s_tbase[2][kMaxBinTiles + 1];  // the chunk's bin: region start of each tile / kTRAlign
   __shared__ u32 s_wt[kTSortThreads / 32];
   const u32 tid = threadIdx.x;
   const u64 keep = l2_evict_last_policy();
@@ -656,6 +730,7 @@ __global__ void __launch_bounds__(kTSortThreads, PP_TSORT_CTAS) k_tsort(TileRoun
     const u32 p = tb.cpos[(u64)b * kTRPosStride];
     return (u64)p < re - rb ? p : (u32)(re - rb);
   };
+  for (u32 i = tid; i < ntile; i += kTSortThreads) s_cnt[i] = 0;  // then zeroed after each chunk's scan
   for (u32 b = tid; b < nb; b += kTSortThreads) {
     const u32 lo = tb.cdone[b], hi = bin_end(b);
     s_pre[b] = hi > lo ? (hi - lo + kTSortChunk - 1) / kTSortChunk : 0u;
@@ -667,7 +742,8 @@ __global__ void __launch_bounds__(kTSortThreads, PP_TSORT_CTAS) k_tsort(TileRoun
   block_exclusive_scan<kTSortThreads>(s_pre, s_pre, nb, s_wt);
   const u32 total = s_pre[nb];
   u32 flags = 0;
-  for (u32 ch = blockIdx.x; ch < total; ch += gridDim.x) {
+  u32 par = 0;  // s_tbase half of this chunk
+  for (u32 ch = blockIdx.x; ch < total; ch += gridDim.x, par ^= 1) {
     // bin of this chunk: the last b with s_pre[b] <= ch
     u32 a = 0, bb = nb;
     while (bb - a > 1) {
@@ -681,36 +757,50 @@ __global__ void __launch_bounds__(kTSortThreads, PP_TSORT_CTAS) k_tsort(TileRoun
     const u32 hi = min(lo + kTSortChunk, s_bhi[b]);
     const u32 t0 = b << tb.bin_tshift;
     u64 x[kTSortPer];
-    u32 lt[kTSortPer], rk[kTSortPer], cl[kTSortPer];
+    // a record's cell, then packed: tile in the bin (9 bits), cell in the
+    // tile (12 bits), rank among the chunk's records of its tile (11 bits)
+    u32 pk[kTSortPer];
+    u32 valid = 0;
 #pragma unroll
     for (int k = 0; k < kTSortPer; ++k) {
       const u32 i = lo + (u32)k * kTSortThreads + tid;
       const bool v = i < hi;
       x[k] = v ? __ldcs(tb.crec_key + rb + i) : 0ull;
-      cl[k] = v ? __ldcs(tb.crec_cell + rb + i) : 0xffffffffu;
+      pk[k] = v ? __ldcs(tb.crec_cell + rb + i) : 0u;
+      valid |= (u32)v << k;
     }
-    // the bin's tile bounds, loaded while the records are in flight
-    for (u32 i = tid; i <= ntile; i += kTSortThreads) s_tbase[i] = tb.base64[min(t0 + i, tb.n_tiles)];
-    for (u32 i = tid; i < ntile; i += kTSortThreads) s_cnt[i] = 0;
+    // the bin's tile bounds, loaded while the records are in flight, into
+    // the half that the chunk before the previous one read (every thread is
+    // past the previous chunk's first barrier, so those reads are done)
+    for (u32 i = tid; i <= ntile; i += kTSortThreads) s_tbase[par][i] = tb.base64[min(t0 + i, tb.n_tiles)];
+#pragma unroll
+    for (int k = 0; k < kTSortPer; ++k) {
+      if ((valid >> k) & 1u) {
+        const u32 lt = (pk[k] >> kTRShift) - t0;
+        const u32 rk = atomicAdd(s_cnt + lt, 1u);
+        pk[k] = lt | (pk[k] & (kTRCells - 1)) << 9 | rk << 21;
+      }
+    }
+    __syncthreads();
+    // tile offsets and cursor reservations: warp 0 alone for up to 128 tiles
+    auto cursor = [&](u32 i) { return tb.pos + (u64)(t0 + i) * kTRPosStride; };
+    if (ntile <= 128) {
+      if (tid < 32) warp_scan_reserve(s_cnt, s_scan, s_tb, ntile, cursor);
+    } else {
+      block_exclusive_scan<kTSortThreads>(s_cnt, s_scan, ntile, s_wt);
+      for (u32 i = tid; i < ntile; i += kTSortThreads) {
+        const u32 h = s_cnt[i];
+        s_tb[i] = h ? atomicAdd(cursor(i), h) : 0u;
+        s_cnt[i] = 0;
+      }
+    }
     __syncthreads();
 #pragma unroll
     for (int k = 0; k < kTSortPer; ++k) {
-      lt[k] = cl[k] != 0xffffffffu ? (cl[k] >> kTRShift) - t0 : 0u;
-      rk[k] = cl[k] != 0xffffffffu ? atomicAdd(s_cnt + lt[k], 1u) : 0u;
-    }
-    __syncthreads();
-    block_exclusive_scan<kTSortThreads>(s_cnt, s_scan, ntile, s_wt);
-    for (u32 i = tid; i < ntile; i += kTSortThreads) {
-      const u32 h = s_cnt[i];
-      s_tb[i] = h ? atomicAdd(tb.pos + (u64)(t0 + i) * kTRPosStride, h) : 0u;
-    }
-    __syncthreads();
-#pragma unroll
-    for (int k = 0; k < kTSortPer; ++k) {
-      if (cl[k] != 0xffffffffu) {
-        const u32 p = s_scan[lt[k]] + rk[k];
+      if ((valid >> k) & 1u) {
+        const u32 p = s_scan[pk[k] & 511u] + (pk[k] >> 21);
         s_key[p] = x[k];
-        s_off[p] = (u16)(cl[k] & (kTRCells - 1));
+        s_off[p] = (u16)((pk[k] >> 9) & (kTRCells - 1));
       }
     }
     __syncthreads();
@@ -723,15 +813,16 @@ __global__ void __launch_bounds__(kTSortThreads, PP_TSORT_CTAS) k_tsort(TileRoun
         if (s_scan[mid] <= p) l = mid;
         else h2 = mid;
       }
-      const u64 dst = (u64)s_tbase[l] * kTRAlign + s_tb[l] + (p - s_scan[l]);
-      if (dst < (u64)s_tbase[l + 1] * kTRAlign && dst < tb.rec_cap) {
+      const u64 dst = (u64)s_tbase[par][l] * kTRAlign + s_tb[l] + (p - s_scan[l]);
+      if (dst < (u64)s_tbase[par][l + 1] * kTRAlign && dst < tb.rec_cap) {
         st_l2_policy(tb.rec_key + dst, s_key[p], keep);
         tb.rec_off[dst] = s_off[p];
       } else {
         flags |= FLAG_INTERNAL;  // more records than the tile's counts allow
       }
     }
-    __syncthreads();
+    // no barrier here: the next chunk writes the other s_tbase half and the
+    // (already zeroed) histogram before its first barrier, the rest after it
   }
   if (flags) atomicOr(&ctl->flags, flags);
 }
@@ -802,8 +893,6 @@ __global__ void __launch_bounds__(kTRThreads, 2) k_tapply(Cell *__restrict__ cel
   u64 *s_dchk = s_dkey + kTRCells;
   u32 *s_dcnt = reinterpret_cast<u32 *>(s_dchk + kTRCells);
   u16 *s_touch = reinterpret_cast<u16 *>(s_dcnt + kTRCells);
-  u32 *s_dkey32 = reinterpret_cast<u32 *>(s_dkey);
-  u32 *s_dchk32 = reinterpret_cast<u32 *>(s_dchk);
   __shared__ u32 s_nt[2], s_seg;  // touched cells of the current tile: two counters, used in turn
   __shared__ u64 s_red[kTRThreads / 32];
   __shared__ u64 s_wseed[BATCH ? kTRCells / 32 : 1];
@@ -853,10 +942,8 @@ __global__ void __launch_bounds__(kTRThreads, 2) k_tapply(Cell *__restrict__ cel
         if (v) {
           const u64 cs = checksum(x[k], BATCH ? s_wseed[off >> 5] : seed0);
           first = atomicAdd(s_dcnt + off, 1u) == 0;
-          atomicXor(s_dkey32 + 2 * off, (u32)x[k]);
-          atomicXor(s_dkey32 + 2 * off + 1, (u32)(x[k] >> 32));
-          atomicXor(s_dchk32 + 2 * off, (u32)cs);
-          atomicXor(s_dchk32 + 2 * off + 1, (u32)(cs >> 32));
+          smem_xor64(s_dkey + off, x[k]);
+          smem_xor64(s_dchk + off, cs);
         }
         const u32 q = warp_reserve<u32>(first, &s_nt[par]);
         if (first) s_touch[q] = (u16)off;
@@ -1028,10 +1115,8 @@ __global__ void __launch_bounds__(kTSThreads, kTSCtas) k_tapply_sparse(Cell *__r
       if (o[k] != kTSEmpty) {
         const u64 cs = checksum(x[k], BATCH ? s_wseed[par][(o[k] & (kTRCells - 1)) >> 5] : seed0);
         atomicAdd(h_cnt + slot, 1u);
-        atomicXor(reinterpret_cast<u32 *>(h_key + slot), (u32)x[k]);
-        atomicXor(reinterpret_cast<u32 *>(h_key + slot) + 1, (u32)(x[k] >> 32));
-        atomicXor(reinterpret_cast<u32 *>(h_chk + slot), (u32)cs);
-        atomicXor(reinterpret_cast<u32 *>(h_chk + slot) + 1, (u32)(cs >> 32));
+        smem_xor64(h_key + slot, x[k]);
+        smem_xor64(h_chk + slot, cs);
       }
       const u32 q = warp_reserve<u32>(fresh, &s_ns[par]);
       if (fresh) s_slot[q] = (u16)slot;
