@@ -187,6 +187,9 @@ __device__ __forceinline__ void st_l2_policy(u64 *a, u64 v, u64 pol) {
 __device__ __forceinline__ void st_l2_policy(u32 *a, u32 v, u64 pol) {
   asm volatile("st.global.L2::cache_hint.b32 [%0], %1, %2;" ::"l"(a), "r"(v), "l"(pol) : "memory");
 }
+__device__ __forceinline__ void st_l2_policy(u16 *a, u16 v, u64 pol) {
+  asm volatile("st.global.L2::cache_hint.b16 [%0], %1, %2;" ::"l"(a), "h"(v), "l"(pol) : "memory");
+}
 
 // Invalidates the 128-byte L2 line at `a` (128-byte aligned) without writing
 // it back: for scratch data that no one reads again.

@@ -39,7 +39,7 @@ __device__ __forceinline__ void tile_bin(unsigned char *smem, const BinArgs &b, 
   const u64 keep = l2_evict_last_policy();
   const u32 set = slab & 1u;
   u64 *tkey = ta.key + set * ta.set_stride;
-  u32 *tcell = ta.cell + set * ta.set_stride;
+  u16 *toff = ta.off + set * ta.set_stride;
   u32 *ttab = BATCH ? ta.tab + set * ta.set_stride : nullptr;
   u32 *tcount = ta.count + set * kTilesPerSlab;
   const u64 oset = (u64)(slab % 3u) * ta.o_cap;
@@ -109,7 +109,7 @@ __device__ __forceinline__ void tile_bin(unsigned char *smem, const BinArgs &b, 
       if (slot < ta.cap) {
         const u64 dst = (u64)tile * ta.cap + slot;
         st_l2_policy(tkey + dst, s_key[p], keep);
-        st_l2_policy(tcell + dst, s_cell[p], keep);
+        st_l2_policy(toff + dst, (u16)(s_cell[p] & (kTileCells - 1)), keep);
         if (BATCH) st_l2_policy(ttab + dst, s_tab[p], keep);
       } else {
         const u32 q = atomicAdd(ta.o_count + slab, 1u);
@@ -239,7 +239,7 @@ __device__ __forceinline__ void tile_apply(unsigned char *smem, Cell *cells, con
       const u32 i = i0 + (u32)it * kTileThreads + threadIdx.x;
       const bool v = i < n;
       x[it] = v ? __ldcs(ta.key + src + i) : 0ull;
-      off[it] = v ? (u32)(__ldcs(ta.cell + src + i) - c0) : 0xffffffffu;
+      off[it] = v ? (u32)__ldcs(ta.off + src + i) : 0xffffffffu;
       seed[it] = (BATCH && v) ? chk_seed_of(tabs[__ldcs(ta.tab + src + i)]) : seed0;
     }
 #pragma unroll
@@ -256,9 +256,9 @@ __device__ __forceinline__ void tile_apply(unsigned char *smem, Cell *cells, con
   __syncthreads();
   if (threadIdx.x == 0) tcount[tile] = 0;  // ready for slab + 2
   // the tile's sorted records are dead now: drop their L2 lines unwritten (the
-  // tile's region starts on a 128-byte line, cap being a multiple of 32)
+  // tile's region starts on a 128-byte line, cap being a multiple of 64)
   for (u32 l = threadIdx.x; l < (n * 8 + 127) / 128; l += kTileThreads) l2_discard(ta.key + src + l * 16);
-  for (u32 l = threadIdx.x; l < (n * 4 + 127) / 128; l += kTileThreads) l2_discard(ta.cell + src + l * 32);
+  for (u32 l = threadIdx.x; l < (n * 2 + 127) / 128; l += kTileThreads) l2_discard(ta.off + src + l * 64);
   if (BATCH)
     for (u32 l = threadIdx.x; l < (n * 4 + 127) / 128; l += kTileThreads) l2_discard(ta.tab + src + l * 32);
   if constexpr (PRESCAN) {
@@ -301,7 +301,7 @@ __device__ __forceinline__ void tile_bin_keys(unsigned char *smem, const TableAr
   const u64 keep = l2_evict_last_policy();
   const u32 set = slab & 1u;
   u64 *tkey = ta.key + set * ta.set_stride;
-  u32 *tcell = ta.cell + set * ta.set_stride;
+  u16 *toff = ta.off + set * ta.set_stride;
   u32 *ttab = ta.tab + set * ta.set_stride;
   u32 *tcount = ta.count + set * kTilesPerSlab;
   const u64 oset = (u64)(slab % 3u) * ta.o_cap;
@@ -379,7 +379,7 @@ __device__ __forceinline__ void tile_bin_keys(unsigned char *smem, const TableAr
         if (slot < ta.cap) {
           const u64 dst = (u64)tile * ta.cap + slot;
           st_l2_policy(tkey + dst, s_key[p], keep);
-          st_l2_policy(tcell + dst, s_cell[p], keep);
+          st_l2_policy(toff + dst, (u16)(s_cell[p] & (kTileCells - 1)), keep);
           st_l2_policy(ttab + dst, k.table, keep);
         } else {
           const u32 q = atomicAdd(ta.o_count + slab, 1u);

@@ -94,7 +94,7 @@ constexpr int kTileBinChunk = kTileThreads * kTileBinItems;  // 4096 records per
 
 struct TileArgs {
   u64 *key;         // sorted records: two sets, set_stride records apart
-  u32 *cell;
+  u16 *off;         // each record's cell within its tile
   u32 *tab;         // batch: table of each record
   u32 *count;       // per tile, two sets of kTilesPerSlab (the apply role resets them)
   u64 set_stride;   // kTilesPerSlab * cap
@@ -161,7 +161,8 @@ constexpr int kClaimChunk = kBlock * kClaimItems;
 // Tile-pass buffers of one handle (host side; csrc/tiles.cu).
 struct TileBufs {
   u64 *key = nullptr, *o_key = nullptr;
-  u32 *cell = nullptr, *tab = nullptr, *count = nullptr;
+  u16 *off = nullptr;
+  u32 *tab = nullptr, *count = nullptr;
   u32 *o_cell = nullptr, *o_tab = nullptr, *o_count = nullptr;
   uint64_t cap = 0, o_cap = 0;  // per tile; per overflow set
   uint32_t o_slabs = 0;

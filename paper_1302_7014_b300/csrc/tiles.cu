@@ -9,7 +9,7 @@ static_assert(kTilesPerSlab == kTileThreads, "the bin role scans one histogram e
 
 void free_tiles(TileBufs &tb) {
   cudaFree(tb.key);
-  cudaFree(tb.cell);
+  cudaFree(tb.off);
   cudaFree(tb.tab);
   cudaFree(tb.count);
   cudaFree(tb.o_key);
@@ -44,17 +44,18 @@ static const void *tile_keys_fn(int rank) {
 }
 
 uint64_t tile_cap_for(uint64_t slab_cap) {
-  // a tile's expected share of its slab's list with slack, a multiple of 32
-  // records so that every tile's region starts on a 128-byte line (a fuller
-  // tile spills to the overflow list, which holds a whole slab)
+  // a tile's expected share of its slab's list with slack, a multiple of 64
+  // records so that every tile's region of 2-byte offsets starts on a
+  // 128-byte line (a fuller tile spills to the overflow list, which holds a
+  // whole slab)
   const uint64_t c = (uint64_t)((double)slab_cap / kTilesPerSlab * 1.15) + 256;
-  return (c + 31) / 32 * 32;
+  return (c + 63) / 64 * 64;
 }
 
 uint64_t tile_pass_bytes(uint64_t tile_cap, uint64_t o_cap, uint32_t n_slabs, bool batch) {
-  const uint64_t per = sizeof(u64) + sizeof(u32) + (batch ? sizeof(u32) : 0);
-  return 2 * tile_cap * kTilesPerSlab * per + 2 * kTilesPerSlab * sizeof(u32) + 3 * o_cap * per +
-         (uint64_t)n_slabs * sizeof(u32);
+  const uint64_t tab = batch ? sizeof(u32) : 0;
+  return 2 * tile_cap * kTilesPerSlab * (sizeof(u64) + sizeof(u16) + tab) + 2 * kTilesPerSlab * sizeof(u32) +
+         3 * o_cap * (sizeof(u64) + sizeof(u32) + tab) + (uint64_t)n_slabs * sizeof(u32);
 }
 
 pp_status ensure_tiles(TileBufs &tb, uint64_t tile_cap, uint64_t o_cap, uint32_t n_slabs, bool batch,
@@ -64,7 +65,7 @@ pp_status ensure_tiles(TileBufs &tb, uint64_t tile_cap, uint64_t o_cap, uint32_t
   if (tb.key && tile_cap <= tb.cap && o_cap <= tb.o_cap && n_slabs <= tb.o_slabs && batch == tb.batch)
     return PP_OK;
   PP_CUDA(cudaStreamSynchronize(s));
-  const uint64_t cap = tile_cap > tb.cap ? tile_cap : tb.cap;  // tile_cap_for: multiples of 32
+  const uint64_t cap = tile_cap > tb.cap ? tile_cap : tb.cap;  // tile_cap_for: multiples of 64
   const uint64_t ocap = o_cap > tb.o_cap ? o_cap : tb.o_cap;
   const uint32_t ns = n_slabs > tb.o_slabs ? n_slabs : tb.o_slabs;
   free_tiles(tb);
@@ -74,7 +75,7 @@ pp_status ensure_tiles(TileBufs &tb, uint64_t tile_cap, uint64_t o_cap, uint32_t
     if (e == cudaSuccess) e = cudaMalloc(p, bytes);
   };
   al((void **)&tb.key, rec * 8);
-  al((void **)&tb.cell, rec * 4);
+  al((void **)&tb.off, rec * 2);
   if (batch) al((void **)&tb.tab, rec * 4);
   al((void **)&tb.count, 2 * kTilesPerSlab * 4);
   al((void **)&tb.o_key, 3 * ocap * 8);
@@ -106,7 +107,7 @@ pp_status tile_apply_pass(Cell *cells, const TableArgs &tab0, const TableArgs *t
                           const PrescanArgs *pre) {
   if (pre && (tb.batch || !zero)) return fail(PP_ERR_INVALID_ARG, "tile pass: F_1 is found only by a plain build");
   PP_CUDA(cudaMemsetAsync(tb.o_count, 0, (size_t)ba.n_slabs * 4, s));
-  TileArgs ta{tb.key, tb.cell, tb.tab, tb.count, tb.cap * kTilesPerSlab, (u32)tb.cap, (u32)tb.o_cap,
+  TileArgs ta{tb.key, tb.off, tb.tab, tb.count, tb.cap * kTilesPerSlab, (u32)tb.cap, (u32)tb.o_cap,
               tb.o_key, tb.o_cell, tb.o_tab, tb.o_count};
   Cell *c = cells;
   TableArgs t0 = tab0;
@@ -135,7 +136,7 @@ pp_status tile_keys_pass(Cell *cells, const TableArgs *tabs, const u64 *keys, co
                          int sign, bool zero, cudaStream_t s) {
   if (!tb.batch) return fail(PP_ERR_INVALID_ARG, "tile pass: batch buffers expected");
   PP_CUDA(cudaMemsetAsync(tb.o_count, 0, (size_t)n_slabs * 4, s));
-  TileArgs ta{tb.key, tb.cell, tb.tab, tb.count, tb.cap * kTilesPerSlab, (u32)tb.cap, (u32)tb.o_cap,
+  TileArgs ta{tb.key, tb.off, tb.tab, tb.count, tb.cap * kTilesPerSlab, (u32)tb.cap, (u32)tb.o_cap,
               tb.o_key, tb.o_cell, tb.o_tab, tb.o_count};
   TileKeysArgs ka{keys, chunks, slab_chunk, n_slabs};
   Cell *c = cells;
