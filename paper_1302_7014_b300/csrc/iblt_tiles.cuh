@@ -125,9 +125,9 @@ __device__ __forceinline__ void tile_bin(unsigned char *smem, const BinArgs &b, 
 }
 
 // The write-out of a tile that also finds F_1 (PrescanArgs): a pure cell is
-// stored empty and pushed into the frontier segment of its tile (warp-wide
-// reservations on the segment's count), each warp writes the bitmap word of
-// its 32 cells, and the tile's count sum and the decode's counters are
+// stored empty and pushed into the frontier segment of its tile (one
+// reservation on the segment's count per warp), each warp writes the bitmap
+// words of its cells, and the tile's count sum and the decode's counters are
 // recorded.  The cells' values are the build's, so a cell is pure exactly when
 // a scan of the built table would find it pure.
 __device__ __forceinline__ void prescan_write(Cell *cells, u64 c0, u32 nc, const u64 *s_key, const u64 *s_chk,
@@ -140,10 +140,15 @@ __device__ __forceinline__ void prescan_write(Cell *cells, u64 c0, u32 nc, const
   u64 alive = 0, nonempty = 0, pushed = 0;
   long long sum = 0;
   u32 flags = 0;
-  for (u32 i = threadIdx.x; i < kTileCells; i += kTileThreads) {
-    const bool valid = i < nc;
+  // the write-out with every warp's ballots kept, then one reservation per
+  // warp in the tile's segment for all its pure cells
+  constexpr int K = kTileCells / kTileThreads;
+  u32 balls[K];
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    const u32 i = threadIdx.x + (u32)k * kTileThreads;
     bool pure = false;
-    if (valid) {
+    if (i < nc) {
       const u64 key = s_key[i], chk = s_chk[i];
       const int cnt = s_cnt[i];
       pure = cell_pure(cnt, key, chk, pre.seed_chk);
@@ -153,13 +158,20 @@ __device__ __forceinline__ void prescan_write(Cell *cells, u64 c0, u32 nc, const
       if (pure) st_cell_cs(cells + c0 + i, 0ull, 0ull, 0);
       else st_cell_cs(cells + c0 + i, key, chk, cnt);
     }
-    const u32 ball = __ballot_sync(kFull, pure);
-    if (lane == 0 && c0 + i < c0 + nc) pre.bitmap[(c0 + i) >> 5] = ball;  // i is the warp's first cell
-    u32 base = 0;
-    if (lane == 0 && ball) base = atomicAdd(pre.tb.fseg + seg, (u32)__popc(ball));
-    base = __shfl_sync(kFull, base, 0);
-    if (pure) {
-      const u32 p = base + __popc(ball & lanemask_lt());
+    balls[k] = __ballot_sync(kFull, pure);
+    if (lane == 0 && i < nc) pre.bitmap[(c0 + i) >> 5] = balls[k];  // i is the warp's first cell
+  }
+  u32 tot = 0;
+#pragma unroll
+  for (int k = 0; k < K; ++k) tot += __popc(balls[k]);
+  u32 base = 0;
+  if (lane == 0 && tot) base = atomicAdd(pre.tb.fseg + seg, tot);
+  base = __shfl_sync(kFull, base, 0);
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    if ((balls[k] >> lane) & 1u) {
+      const u32 i = threadIdx.x + (u32)k * kTileThreads;
+      const u32 p = base + __popc(balls[k] & lanemask_lt());
       if (p < pre.tb.cap_d) {
         pre.fkey[sbase + p] = s_key[i];
         pre.fcell[sbase + p] = (u32)(c0 + i);
@@ -168,6 +180,7 @@ __device__ __forceinline__ void prescan_write(Cell *cells, u64 c0, u32 nc, const
       }
       pushed += 1;
     }
+    base += __popc(balls[k]);
   }
   // the four figures in one reduction: shuffles within each warp, then thread
   // 0 over the warps (two's-complement sums, so the count sum may be signed)
