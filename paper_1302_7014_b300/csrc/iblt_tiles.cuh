@@ -48,7 +48,7 @@ __device__ __forceinline__ void tile_bin(unsigned char *smem, const BinArgs &b, 
   const u64 src = (u64)slab * b.cap;
   const u32 cbase = slab << kSlabShift;
   for (u32 c0 = bi * (u32)kTileBinChunk; c0 < n; c0 += nb * (u32)kTileBinChunk) {
-    s_hist[tid] = 0;
+    if (tid < kTilesPerSlab) s_hist[tid] = 0;
     __syncthreads();
     const u32 c1 = c0 + kTileBinChunk < n ? c0 + kTileBinChunk : n;
     // this thread's records: every load in flight at once, then their ranks
@@ -67,8 +67,8 @@ __device__ __forceinline__ void tile_bin(unsigned char *smem, const BinArgs &b, 
     for (int it = 0; it < kTileBinItems; ++it)
       rk[it] = c[it] != 0xffffffffu ? atomicAdd(s_hist + ((c[it] - cbase) >> kTileShift), 1u) : 0u;
     __syncthreads();
-    // exclusive scan of the 512-entry histogram: one entry per thread
-    const u32 own = s_hist[tid];
+    // exclusive scan of the slab's tile histogram: one entry per thread
+    const u32 own = tid < kTilesPerSlab ? s_hist[tid] : 0u;
     u32 inc = own;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
@@ -88,8 +88,10 @@ __device__ __forceinline__ void tile_bin(unsigned char *smem, const BinArgs &b, 
       if (tid < kTileThreads / 32) s_wt[tid] = wi - w;
     }
     __syncthreads();
-    s_scan[tid] = s_wt[tid >> 5] + inc - own;
-    s_base[tid] = own ? atomicAdd(tcount + tid, own) : 0u;
+    if (tid < kTilesPerSlab) {
+      s_scan[tid] = s_wt[tid >> 5] + inc - own;
+      s_base[tid] = own ? atomicAdd(tcount + tid, own) : 0u;
+    }
     __syncthreads();
     // order the chunk by tile in shared memory
 #pragma unroll
@@ -325,7 +327,7 @@ __device__ __forceinline__ void tile_bin_keys(unsigned char *smem, const TableAr
     const TableArgs &T = tabs[k.table];
     const int r = rank_of<R>(T);
     for (u32 k0 = k.begin; k0 < k.end; k0 += KEYS) {
-      s_hist[tid] = 0;
+      if (tid < kTilesPerSlab) s_hist[tid] = 0;
       __syncthreads();
       u64 x[KPT];
       u32 c[KPT][NR], rk[KPT][NR];
@@ -346,8 +348,8 @@ __device__ __forceinline__ void tile_bin_keys(unsigned char *smem, const TableAr
         }
       }
       __syncthreads();
-      // exclusive scan of the 512-entry histogram: one entry per thread
-      const u32 own = s_hist[tid];
+      // exclusive scan of the slab's tile histogram: one entry per thread
+      const u32 own = tid < kTilesPerSlab ? s_hist[tid] : 0u;
       u32 inc = own;
 #pragma unroll
       for (int o = 1; o < 32; o <<= 1) {
@@ -367,9 +369,12 @@ __device__ __forceinline__ void tile_bin_keys(unsigned char *smem, const TableAr
         if (tid < kTileThreads / 32) s_wt[tid] = wi - w;
       }
       __syncthreads();
-      s_scan[tid] = s_wt[tid >> 5] + inc - own;
-      s_base[tid] = own ? atomicAdd(tcount + tid, own) : 0u;
-      if (tid == kTileThreads - 1) s_total = s_scan[tid] + own;
+      const u32 excl = s_wt[tid >> 5] + inc - own;
+      if (tid < kTilesPerSlab) {
+        s_scan[tid] = excl;
+        s_base[tid] = own ? atomicAdd(tcount + tid, own) : 0u;
+      }
+      if (tid == kTileThreads - 1) s_total = excl + own;
       __syncthreads();
       // order the step's records by tile in shared memory
 #pragma unroll

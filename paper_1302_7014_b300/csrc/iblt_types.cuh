@@ -66,7 +66,10 @@ struct Chunk {
 };
 
 // Slab-binned build (iblt_binned.cuh).
-constexpr int kSlabShift = 21;               // 2^21 cells = 32 MB per slab
+#ifndef PP_SLAB_SHIFT
+#define PP_SLAB_SHIFT 21
+#endif
+constexpr int kSlabShift = PP_SLAB_SHIFT;    // 2^21 cells = 64 MB per slab
 constexpr u32 kSlabCells = 1u << kSlabShift;
 #ifndef PP_BIN_ITEMS
 #define PP_BIN_ITEMS 4

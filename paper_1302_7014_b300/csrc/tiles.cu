@@ -5,7 +5,7 @@
 
 namespace pp {
 
-static_assert(kTilesPerSlab == kTileThreads, "the bin role scans one histogram entry per thread");
+static_assert(kTilesPerSlab <= kTileThreads, "the bin role scans one histogram entry per thread");
 
 void free_tiles(TileBufs &tb) {
   cudaFree(tb.key);
