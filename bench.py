@@ -271,8 +271,9 @@ def bench_batched(pp, torch, args):
     b = pb.Batch([t.n_cells for t in tabs], [t.r for t in tabs], [t.table_seed for t in tabs])
 
     def bstep():
-        b.build(dkeys, koff, stream)   # clear + insert
-        return b.decode(out, koff, stream=stream)
+        # clear + insert + decode in one pp_batch_build_decode (the build's
+        # write-out finds F_1)
+        return b.build_decode(dkeys, koff, out, koff, stream=stream)
 
     steps = max(3, min(args.steps, 10))
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -335,18 +336,19 @@ def bench_batched(pp, torch, args):
     torch.cuda.empty_cache()
     n = len(tabs)
     # sector-floor bytes of one step, as for the headline table: the clear writes
-    # every 32 B cell, the build 8 + 64 r B per key, the decode the 4 B count of
-    # every cell plus 64 r + 16 B per key; the arena is far larger than L2
+    # every 32 B cell, the build 8 + 64 r B per key, the rounds 64 r + 16 B per
+    # key (no scan: the build's write-out finds F_1); the arena is far larger
+    # than L2
     cells = sum(t.n_cells for t in tabs)
     step_bytes = 32 * cells + sum(k.size * (8 + 64 * t.r) for k, t in zip(keys, tabs)) + \
-        4 * cells + sum(k.size * (64 * t.r + 16) for k, t in zip(keys, tabs))
+        sum(k.size * (64 * t.r + 16) for k, t in zip(keys, tabs))
     peak, peak_kind = hbm_peak()
     achieved = step_bytes / (b_ms * 1e-3) / 1e9
     return {"workload": "4096 IBLTs, cells log-uniform [2^8,2^20), r in {3,4}, load U[0.5, 0.9 c*]",
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "peak_source": f"{peak_kind} hbm_gbs",
-                         "model": "sector floor: 32 B/cell clear + (8+64r) B/key build + 4 B/cell scan "
-                                  "+ (64r+16) B/key decode"},
+                         "model": "sector floor: 32 B/cell clear + (8+64r) B/key build + (64r+16) B/key "
+                                  "rounds"},
             "tables": n, "cells": int(sum(t.n_cells for t in tabs)), "keys": total_keys,
             "batched_ms": b_ms, "plain_loop_ms": p_ms,
             "batched_tables_per_s": n / (b_ms * 1e-3), "plain_tables_per_s": n / (p_ms * 1e-3),
@@ -357,7 +359,7 @@ def bench_batched(pp, torch, args):
                           "key": tuned.key},
             "batched_keys_per_s": rec / steps / (b_ms * 1e-3), "speedup": p_ms / b_ms,
             "rounds_max": b_rounds, "identical_output": identical,
-            "step": "clear + insert + decode of every table"}
+            "step": "one pp_batch_build_decode: clear + insert + decode of every table"}
 
 
 def _serve_stream(ps, srv, reqs):
@@ -745,9 +747,8 @@ def profile_case(pp, torch, args, cfg):
         b = pb.Batch([t.n_cells for t in tabs], [t.r for t in tabs], [t.table_seed for t in tabs], opts)
 
         def call():
-            b.build(dk, koff, stream)
-            return b.decode(out, koff, stream=stream)
-        what = "pp_batch_build + pp_batch_decode, 4096 tables"
+            return b.build_decode(dk, koff, out, koff, stream=stream)
+        what = "pp_batch_build_decode, 4096 tables"
     else:
         n, r = cfg["n_cells"], cfg["r"]
         na, nb, nc = int(0.45 * n), int(0.30 * n), int(0.25 * n)

@@ -430,6 +430,18 @@ pp_status pp_batch_build(pp_batch *b, const uint64_t *d_keys, const uint64_t *h_
 pp_status pp_batch_decode(pp_batch *b, uint64_t *d_out_keys, const uint64_t *h_out_offsets,
                           pp_table_result *results, void *stream);
 
+/* pp_batch_build (keys as there) followed by pp_batch_decode (outputs as
+ * there; a table's range must hold the keys it gets, else CAPACITY and
+ * nothing is built).  Same tables, keys and results as the two calls.  When
+ * every table lies within two 2^21-cell slabs, the batch is large enough to
+ * be built slab by slab and the decode runs tile rounds, the build's write-
+ * out of each tile also finds the tile's pure cells (F_1, Sec. 1 round 1), so
+ * the decode starts at its first round without reading the arena once more.
+ * Synchronizes `stream`. */
+pp_status pp_batch_build_decode(pp_batch *b, const uint64_t *d_keys, const uint64_t *h_key_offsets,
+                                uint64_t *d_out_keys, const uint64_t *h_out_offsets, pp_table_result *results,
+                                void *stream);
+
 /* Copies table `table`'s cells to dst (host if to_host, else device). */
 pp_status pp_batch_copy_cells(pp_batch *b, uint32_t table, void *dst, int to_host, void *stream);
 
@@ -446,7 +458,7 @@ pp_status pp_batch_get_options(const pp_batch *b, pp_options *opt);
  * apply_ctas, binned (1 = address-ordered records, 2 = direct atomics),
  * insert_chunk and rounds (2 = tile rounds, 1 = binned or direct rounds) -- on
  * the caller's own batch and keys: each candidate runs
- * pp_batch_build + pp_batch_decode once untimed and `reps` times timed (CUDA
+ * pp_batch_build_decode once untimed and `reps` times timed (CUDA
  * events on `stream`, median).  Candidate 0 is the batch's options as they
  * were.  A candidate whose per-table rounds, recovered counts or residues
  * differ from candidate 0's is discarded and counted in report->mismatches.

@@ -58,6 +58,8 @@ _lib.declare("pp_batch_insert", ctypes.c_int, [vp, vp, ctypes.POINTER(u64), vp])
 _lib.declare("pp_batch_delete", ctypes.c_int, [vp, vp, ctypes.POINTER(u64), vp])
 _lib.declare("pp_batch_build", ctypes.c_int, [vp, vp, ctypes.POINTER(u64), vp])
 _lib.declare("pp_batch_decode", ctypes.c_int, [vp, vp, ctypes.POINTER(u64), ctypes.POINTER(TableResult), vp])
+_lib.declare("pp_batch_build_decode", ctypes.c_int,
+             [vp, vp, ctypes.POINTER(u64), vp, ctypes.POINTER(u64), ctypes.POINTER(TableResult), vp])
 _lib.declare("pp_batch_copy_cells", ctypes.c_int, [vp, u32, vp, ctypes.c_int, vp])
 _lib.declare("pp_batch_info", ctypes.c_int, [vp, ctypes.POINTER(u32), ctypes.POINTER(u64), ctypes.POINTER(u32)])
 _lib.declare("pp_batch_set_options", ctypes.c_int, [vp, ctypes.POINTER(Options)])
@@ -131,6 +133,22 @@ class Batch:
         _check(_lib.load().pp_batch_build(self._h, ptr, off_p, _stream_ptr(stream)), "pp_batch_build")
 
     def decode(self, out, out_offsets, round_cap: int = 256, stream=None) -> BatchOutcome:
+        return self._decode(lambda ptr, off_p, res: _lib.load().pp_batch_decode(
+            self._h, ptr, off_p, res, _stream_ptr(stream)), "pp_batch_decode", out, out_offsets, round_cap)
+
+    def build_decode(self, keys, key_offsets, out, out_offsets, round_cap: int = 256,
+                     stream=None) -> BatchOutcome:
+        """build() then decode() in one call; a large batch's build then also
+        finds the cells pure before round 1, and the decode does not scan the
+        arena again."""
+        koff, koff_p = _u64_array(key_offsets)
+        assert koff.size == self.n_tables + 1
+        kptr = _dev_ptr(keys, 8, "keys") if keys is not None and keys.numel() else None
+        return self._decode(lambda ptr, off_p, res: _lib.load().pp_batch_build_decode(
+            self._h, kptr, koff_p, ptr, off_p, res, _stream_ptr(stream)), "pp_batch_build_decode", out,
+            out_offsets, round_cap)
+
+    def _decode(self, call, name, out, out_offsets, round_cap) -> BatchOutcome:
         off, off_p = _u64_array(out_offsets)
         n = self.n_tables
         per_round = np.zeros((n, round_cap), dtype=np.uint64)
@@ -139,9 +157,7 @@ class Batch:
         results["recovered_per_round"] = (np.uint64(per_round.ctypes.data)
                                           + np.arange(n, dtype=np.uint64) * np.uint64(round_cap * 8))
         ptr = _dev_ptr(out, 8, "out") if out is not None and out.numel() else None
-        _check(_lib.load().pp_batch_decode(self._h, ptr, off_p,
-                                           ctypes.cast(results.ctypes.data, ctypes.POINTER(TableResult)),
-                                           _stream_ptr(stream)), "pp_batch_decode")
+        _check(call(ptr, off_p, ctypes.cast(results.ctypes.data, ctypes.POINTER(TableResult))), name)
         rounds = results["rounds"].astype(np.int64)
         return BatchOutcome(
             rounds=rounds,

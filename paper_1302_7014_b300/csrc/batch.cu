@@ -59,6 +59,9 @@ struct pp_batch {
   size_t smem_peel = 0;
   cudaGraphExec_t exec = nullptr;
   u64 *graph_out = nullptr;  // output buffer the instantiated graph writes to
+  cudaGraphExec_t exec_pre = nullptr;  // tile rounds after a build that found F_1
+  u64 *graph_out_pre = nullptr;
+  uint32_t graph_gen_pre = 0;
   // update records shared by the slab-binned build and the binned rounds
   u64 *rec_key = nullptr;
   u32 *rec_cell = nullptr, *rec_tab = nullptr, *bin_count = nullptr, *bin_overflow = nullptr;
@@ -91,6 +94,7 @@ namespace {
 void free_batch(pp_batch *b) {
   if (!b) return;
   if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->exec_pre) cudaGraphExecDestroy(b->exec_pre);
   cudaFree(b->tabs);
   cudaFree(b->cells);
   cudaFree(b->fkey);
@@ -175,6 +179,14 @@ bool use_binned(const pp_batch *b, uint64_t records) {
 // Bins of the binned rounds over the whole arena (2^19 cells each).  A bin's
 // list holds the updates of 0.35 keys per cell at the largest r in the batch;
 // fuller bins apply their excess directly.
+// Round kind: tile rounds for batches built from insertions only (forced on
+// or off by opt.rounds), for arenas of 2^21 cells or more by default.
+bool batch_wants_tiles(const pp_batch *b) {
+  const bool large = b->total_cells >= (1ull << 21);
+  return b->k.tscan && !b->had_deletes &&
+         (b->opt.rounds == 2 || (b->opt.rounds == 0 && large && b->opt.binned != 2));
+}
+
 pp_status ensure_round_bins(pp_batch *b, cudaStream_t s) {
   const u32 shift = round_bin_shift(b->total_cells);
   const uint32_t nb = (uint32_t)((b->total_cells + (1ull << shift) - 1) >> shift);
@@ -617,7 +629,7 @@ static pp_status batch_bin_pass(pp_batch *b, const uint64_t *d_keys, const uint6
 // sized for the expected records of the fullest slab, the overflow sets for
 // the most records a slab can receive (every key of every table it overlaps).
 static pp_status batch_keys_pass(pp_batch *b, const uint64_t *d_keys, const uint64_t *h_key_offsets, u32 nch,
-                                 int sign, bool zero_fill, cudaStream_t s) {
+                                 int sign, bool zero_fill, cudaStream_t s, const PrescanArgs *pre = nullptr) {
   const uint32_t ns = (uint32_t)((b->total_cells + kSlabCells - 1) / kSlabCells);
   std::vector<double> expect(ns, 0.0);
   std::vector<uint64_t> bound(ns, 0);
@@ -667,7 +679,7 @@ static pp_status batch_keys_pass(pp_batch *b, const uint64_t *d_keys, const uint
   pp_status st = ensure_tiles(b->tiles, tile_cap_for((uint64_t)mx + 1), ocap, ns, true, s);
   if (st != PP_OK) return st;
   return tile_keys_pass(b->cells, b->tabs, reinterpret_cast<const u64 *>(d_keys), b->ins_chunks, b->slab_chunk,
-                        ns, b->krank, b->tiles, b->total_cells, sign, zero_fill, s);
+                        ns, b->krank, b->tiles, b->total_cells, sign, zero_fill, s, pre);
 }
 
 // Pass 2: slab by slab (zero-filled first when building from scratch).
@@ -751,16 +763,17 @@ pp_status pp_batch_build(pp_batch *b, const uint64_t *d_keys, const uint64_t *h_
   return st;
 }
 
-pp_status pp_batch_decode(pp_batch *b, uint64_t *d_out_keys, const uint64_t *h_out_offsets,
-                          pp_table_result *results, void *stream) {
-  if (!b || !h_out_offsets || !results) return fail(PP_ERR_INVALID_ARG, "pp_batch_decode: NULL argument");
-  cudaStream_t s = as_stream(stream);
+// The decode's first part: the output ranges checked (CAPACITY before
+// anything runs), fresh per-table counters and control block, and the round
+// kind's buffers (the control block is on the device when this returns).
+static pp_status decode_prepare(pp_batch *b, uint64_t *d_out_keys, const uint64_t *h_out_offsets, cudaStream_t s,
+                                const char *fn) {
   bool moved = false;
   for (uint32_t i = 0; i < b->n_tables; ++i) {
     const uint64_t o0 = h_out_offsets[i], o1 = h_out_offsets[i + 1];
-    if (o1 < o0) return fail(PP_ERR_INVALID_ARG, "pp_batch_decode: output offsets decrease at table %u", i);
+    if (o1 < o0) return fail(PP_ERR_INVALID_ARG, "%s: output offsets decrease at table %u", fn, i);
     if (o1 - o0 < b->items[i])
-      return fail(PP_ERR_CAPACITY, "pp_batch_decode: table %u has %llu keys but %llu output slots", i,
+      return fail(PP_ERR_CAPACITY, "%s: table %u has %llu keys but %llu output slots", fn, i,
                   (unsigned long long)b->items[i], (unsigned long long)(o1 - o0));
     if (b->h_tabs[i].out_base != o0 || b->h_tabs[i].out_cap != o1 - o0) {
       b->h_tabs[i].out_base = o0;
@@ -768,7 +781,7 @@ pp_status pp_batch_decode(pp_batch *b, uint64_t *d_out_keys, const uint64_t *h_o
       moved = true;
     }
   }
-  if (h_out_offsets[b->n_tables] && !d_out_keys) return fail(PP_ERR_INVALID_ARG, "pp_batch_decode: NULL output");
+  if (h_out_offsets[b->n_tables] && !d_out_keys) return fail(PP_ERR_INVALID_ARG, "%s: NULL output", fn);
   if (moved)
     PP_CUDA(cudaMemcpyAsync(b->tabs, b->h_tabs.data(), b->n_tables * sizeof(TableArgs),
                             cudaMemcpyHostToDevice, s));
@@ -785,8 +798,7 @@ pp_status pp_batch_decode(pp_batch *b, uint64_t *d_out_keys, const uint64_t *h_o
   // round kind: tile rounds (batches built from insertions only), binned
   // atomic rounds (other large arenas), direct atomics (small arenas)
   const bool large = b->total_cells >= (1ull << 21);
-  const bool want_tiles = b->k.tscan && !b->had_deletes &&
-                          (b->opt.rounds == 2 || (b->opt.rounds == 0 && large && b->opt.binned != 2));
+  const bool want_tiles = batch_wants_tiles(b);
   const bool want_bins = !want_tiles && (b->opt.binned == 1 || (b->opt.binned == 0 && large));
   if (want_tiles) {
     pp_status st = ensure_batch_tiles(b, s);
@@ -805,12 +817,31 @@ pp_status pp_batch_decode(pp_batch *b, uint64_t *d_out_keys, const uint64_t *h_o
   b->binned_rounds = want_bins;
   b->tile_rounds = want_tiles;
   PP_CUDA(cudaMemcpyAsync(b->ctl, b->h_ctl, sizeof(DecodeCtl), cudaMemcpyHostToDevice, s));
-  u64 *out = reinterpret_cast<u64 *>(d_out_keys);
+  return PP_OK;
+}
+
+// The round loop of the kind decode_prepare chose (prescanned: tile rounds
+// after a build that found F_1).
+static pp_status decode_rounds(pp_batch *b, u64 *out, bool prescanned, cudaStream_t s) {
   if (b->tile_rounds && b->opt.host_loop) {
     TileRoundLaunch a;
     fill_tiles(b, a, out);
-    pp_status st = tre_host_loop(b->tre, b->k, a, &b->h_ctl->more, s);
+    pp_status st = tre_host_loop(b->tre, b->k, a, &b->h_ctl->more, s, prescanned);
     if (st != PP_OK) return st;
+  } else if (b->tile_rounds && prescanned) {
+    if (b->exec_pre && (b->graph_out_pre != out || b->graph_gen_pre != b->rec_gen)) {
+      cudaGraphExecDestroy(b->exec_pre);
+      b->exec_pre = nullptr;
+    }
+    if (!b->exec_pre) {
+      TileRoundLaunch a;
+      fill_tiles(b, a, out);
+      pp_status st = tre_build_graph(b->tre, b->k, a, &b->exec_pre, true);
+      if (st != PP_OK) return st;
+      b->graph_out_pre = out;
+      b->graph_gen_pre = b->rec_gen;
+    }
+    PP_CUDA(cudaGraphLaunch(b->exec_pre, s));
   } else if (b->tile_rounds) {
     if (!b->exec || b->graph_out != out) {
       if (b->exec) cudaGraphExecDestroy(b->exec);
@@ -851,6 +882,12 @@ pp_status pp_batch_decode(pp_batch *b, uint64_t *d_out_keys, const uint64_t *h_o
     }
     PP_CUDA(cudaGraphLaunch(b->exec, s));
   }
+  return PP_OK;
+}
+
+// The residue count and the per-table results; synchronizes s.
+static pp_status decode_finish(pp_batch *b, pp_table_result *results, cudaStream_t s, const char *fn) {
+  const uint32_t n = b->n_tables, sr = b->opt.stats_rounds;
   const bool scan_residue = b->binned_rounds || b->tile_rounds;
   if (scan_residue) {
     // the binned and tile rounds do not track emptied cells per table: count the residue
@@ -888,12 +925,73 @@ pp_status pp_batch_decode(pp_batch *b, uint64_t *d_out_keys, const uint64_t *h_o
     r.stats_complete = r.rounds <= sr;
     b->items[i] -= r.recovered <= b->items[i] ? r.recovered : b->items[i];
   }
-  if (b->h_ctl->flags & FLAG_CAPACITY) return fail(PP_ERR_CAPACITY, "pp_batch_decode: output overflow");
+  if (b->h_ctl->flags & FLAG_CAPACITY) return fail(PP_ERR_CAPACITY, "%s: output overflow", fn);
   if (b->h_ctl->flags & FLAG_INTERNAL)
-    return fail(PP_ERR_INVALID_ARG, "pp_batch_decode: a pure cell's key does not hash to it");
+    return fail(PP_ERR_INVALID_ARG, "%s: a pure cell's key does not hash to it", fn);
   if (b->h_ctl->flags & FLAG_ROUND_LIMIT)
-    return fail(PP_ERR_ROUND_LIMIT, "pp_batch_decode: stopped after max_rounds=%u rounds", b->opt.max_rounds);
+    return fail(PP_ERR_ROUND_LIMIT, "%s: stopped after max_rounds=%u rounds", fn, b->opt.max_rounds);
   return PP_OK;
+}
+
+
+pp_status pp_batch_decode(pp_batch *b, uint64_t *d_out_keys, const uint64_t *h_out_offsets,
+                          pp_table_result *results, void *stream) {
+  if (!b || !h_out_offsets || !results) return fail(PP_ERR_INVALID_ARG, "pp_batch_decode: NULL argument");
+  cudaStream_t s = as_stream(stream);
+  pp_status st = decode_prepare(b, d_out_keys, h_out_offsets, s, "pp_batch_decode");
+  if (st != PP_OK) return st;
+  st = decode_rounds(b, reinterpret_cast<u64 *>(d_out_keys), false, s);
+  if (st != PP_OK) return st;
+  return decode_finish(b, results, s, "pp_batch_decode");
+}
+
+pp_status pp_batch_build_decode(pp_batch *b, const uint64_t *d_keys, const uint64_t *h_key_offsets,
+                                uint64_t *d_out_keys, const uint64_t *h_out_offsets, pp_table_result *results,
+                                void *stream) {
+  if (!b || !h_key_offsets || !h_out_offsets || !results)
+    return fail(PP_ERR_INVALID_ARG, "pp_batch_build_decode: NULL argument");
+  cudaStream_t s = as_stream(stream);
+  uint64_t records = 0;
+  for (uint32_t i = 0; i < b->n_tables; ++i) {
+    if (h_key_offsets[i + 1] < h_key_offsets[i] || h_out_offsets[i + 1] < h_out_offsets[i])
+      return fail(PP_ERR_INVALID_ARG, "pp_batch_build_decode: offsets decrease at table %u", i);
+    const uint64_t m = h_key_offsets[i + 1] - h_key_offsets[i];
+    if (h_out_offsets[i + 1] - h_out_offsets[i] < m)
+      return fail(PP_ERR_CAPACITY, "pp_batch_build_decode: table %u gets %llu keys but %llu output slots", i,
+                  (unsigned long long)m, (unsigned long long)(h_out_offsets[i + 1] - h_out_offsets[i]));
+    records += m * b->h_tabs[i].r;
+  }
+  // the tile write-out finds F_1 when the build takes the keys' tile pass and
+  // the decode the tile rounds; otherwise the two calls
+  const bool had = b->had_deletes;
+  b->had_deletes = false;
+  const bool fused = records && b->keys_tiles && use_binned(b, records) && b->k.trescan && batch_wants_tiles(b);
+  b->had_deletes = had;
+  if (!fused) {
+    pp_status st = pp_batch_build(b, d_keys, h_key_offsets, stream);
+    if (st != PP_OK) return st;
+    return pp_batch_decode(b, d_out_keys, h_out_offsets, results, stream);
+  }
+  if (!d_keys) return fail(PP_ERR_INVALID_ARG, "pp_batch_build_decode: NULL keys");
+  for (auto &x : b->items) x = 0;
+  b->had_deletes = false;
+  u32 nch = 0;
+  uint64_t rec = 0;
+  pp_status st = upload_chunks(b, h_key_offsets, s, &nch, &rec);
+  if (st != PP_OK) return st;
+  add_items(b, h_key_offsets, +1);  // the record regions of the tile rounds are sized from them
+  st = decode_prepare(b, d_out_keys, h_out_offsets, s, "pp_batch_build_decode");
+  if (st != PP_OK) return st;
+  if (!b->tile_rounds) return fail(PP_ERR_INVALID_ARG, "pp_batch_build_decode: tile rounds expected");
+  const TileRoundBufs &tb = b->tre.trb;
+  PP_CUDA(cudaMemsetAsync(tb.fseg, 0, (size_t)tb.n_seg_d * sizeof(u32), s));
+  PP_CUDA(cudaMemsetAsync(tb.n_rescan, 0, sizeof(u32), s));
+  const PrescanArgs pre{tb, b->fkey, b->fcell, b->bitmap, b->ctl, 0ull, b->wseed};
+  st = batch_keys_pass(b, d_keys, h_key_offsets, nch, +1, true, s, &pre);
+  if (st != PP_OK) return st;
+  st = decode_rounds(b, reinterpret_cast<u64 *>(d_out_keys), true, s);
+  if (st != PP_OK) return st;
+  return decode_finish(b, results, s, "pp_batch_build_decode");
 }
 
 pp_status pp_batch_copy_cells(pp_batch *b, uint32_t table, void *dst, int to_host, void *stream) {

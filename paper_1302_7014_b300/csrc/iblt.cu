@@ -64,7 +64,7 @@ static IbltKernels iblt_kernels_t() {
     k.tapply = (const void *)k_tapply<R, B>;
     k.tapply_sparse = (const void *)k_tapply_sparse<R, B>;
     k.trestore = (const void *)k_trestore<R, B>;
-    if constexpr (!B) k.trescan = (const void *)k_trescan<R>;
+    k.trescan = (const void *)k_trescan<R, B>;
     static bool tattr = false;
     if (!tattr) {
       allow_max_dynamic_smem((const void *)k_tapply<R, B>);
@@ -1766,7 +1766,7 @@ pp_status build_decode_enqueue(pp_iblt *t, const uint64_t *d_keys, uint64_t m, u
   const TileRoundBufs &tb = t->tre.trb;
   PP_CUDA(cudaMemsetAsync(tb.fseg, 0, (size_t)tb.n_seg_d * sizeof(u32), s));
   PP_CUDA(cudaMemsetAsync(tb.n_rescan, 0, sizeof(u32), s));
-  const PrescanArgs pre{tb, t->fkey, t->fcell, t->bitmap, t->ctl, t->args.seed[t->r]};
+  const PrescanArgs pre{tb, t->fkey, t->fcell, t->bitmap, t->ctl, t->args.seed[t->r], nullptr};
   st = apply_pass(t, ba, +1, true, s, &pre);
   if (st != PP_OK) return st;
   if (built) PP_CUDA(cudaEventRecord(built, s));

@@ -132,6 +132,7 @@ __device__ __forceinline__ void tile_bin(unsigned char *smem, const BinArgs &b, 
 // words of its cells, and the tile's count sum and the decode's counters are
 // recorded.  The cells' values are the build's, so a cell is pure exactly when
 // a scan of the built table would find it pure.
+template <bool BATCH>
 __device__ __forceinline__ void prescan_write(Cell *cells, u64 c0, u32 nc, const u64 *s_key, const u64 *s_chk,
                                               const int *s_cnt, const PrescanArgs &pre) {
   __shared__ u64 s_red[4][kTileThreads / 32];
@@ -145,15 +146,24 @@ __device__ __forceinline__ void prescan_write(Cell *cells, u64 c0, u32 nc, const
   // the write-out with every warp's ballots kept, then one reservation per
   // warp in the tile's segment for all its pure cells
   constexpr int K = kTileCells / kTileThreads;
+  static_assert(K <= 32, "one lane per step holds the seed of the warp's word");
+  // BATCH: the warp's 32 cells of step k are one word of one table; lane k
+  // loads that word's seed for the whole warp, all steps' loads at once
+  u64 wsd = 0;
+  if (BATCH && lane < (u32)K) {
+    const u32 iw = lane * kTileThreads + (threadIdx.x & ~31u);
+    if (iw < nc) wsd = pre.wseed[(c0 + iw) >> 5];
+  }
   u32 balls[K];
 #pragma unroll
   for (int k = 0; k < K; ++k) {
     const u32 i = threadIdx.x + (u32)k * kTileThreads;
+    const u64 seed = BATCH ? __shfl_sync(kFull, wsd, k) : pre.seed_chk;
     bool pure = false;
     if (i < nc) {
       const u64 key = s_key[i], chk = s_chk[i];
       const int cnt = s_cnt[i];
-      pure = cell_pure(cnt, key, chk, pre.seed_chk);
+      pure = cell_pure(cnt, key, chk, seed);
       alive += cnt >= 2;
       nonempty += cnt != 0;
       sum += cnt;
@@ -278,7 +288,7 @@ __device__ __forceinline__ void tile_apply(unsigned char *smem, Cell *cells, con
     for (u32 l = threadIdx.x; l < (n * 4 + 127) / 128; l += kTileThreads) l2_discard(ta.tab + src + l * 32);
   if constexpr (PRESCAN) {
     if (cnt <= ta.cap) {
-      prescan_write(cells, c0, nc, s_key, s_chk, s_cnt, pre);
+      prescan_write<BATCH>(cells, c0, nc, s_key, s_chk, s_cnt, pre);
       return;
     }
     if (threadIdx.x == 0) pre.tb.rescan[atomicAdd(pre.tb.n_rescan, 1u)] = (u32)(c0 >> kTileShift);
@@ -457,11 +467,11 @@ __global__ void __launch_bounds__(kTileThreads, 2) k_tile_step(Cell *__restrict_
 
 // The batched tile step with the bin role taken from the keys (tile_bin_keys);
 // the apply role is k_tile_step's.
-template <int R>
+template <int R, bool PRESCAN = false>
 __global__ void __launch_bounds__(kTileThreads, 2) k_tile_step_keys(Cell *__restrict__ cells,
                                                            const TableArgs *__restrict__ tabs, TileKeysArgs ka,
                                                            TileArgs ta, u32 s, u32 n_apply, u32 n_bin,
-                                                           u64 n_cells, int sign, int zero) {
+                                                           u64 n_cells, int sign, int zero, PrescanArgs pre) {
   extern __shared__ __align__(16) unsigned char smem[];
   const u32 both = n_apply < n_bin ? n_apply : n_bin;
   const u32 blk = blockIdx.x;
@@ -489,8 +499,8 @@ __global__ void __launch_bounds__(kTileThreads, 2) k_tile_step_keys(Cell *__rest
     }
   }
   const TableArgs t0{};
-  const PrescanArgs none{};
-  if (s >= 1 && s - 1 < ka.n_slabs) tile_apply<true>(smem, cells, t0, tabs, ta, s - 1, idx, n_cells, sign, zero, none);
+  if (s >= 1 && s - 1 < ka.n_slabs)
+    tile_apply<true, PRESCAN>(smem, cells, t0, tabs, ta, s - 1, idx, n_cells, sign, zero, pre);
 }
 
 }  // namespace pp

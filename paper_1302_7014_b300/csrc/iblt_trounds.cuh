@@ -278,17 +278,17 @@ __global__ void __launch_bounds__(kTRThreads, 2) k_tscan(Cell *__restrict__ cell
 // tb.rescan, which the build's overflow pass changed after their write-out,
 // are scanned here, with what k_tscan does per tile; their pure cells join
 // the tile's frontier segment (tile % n_seg_d) behind the build's entries.
-// Usually the list is empty.
-template <int R>
+// Usually the list is empty.  BATCH: a cell's checksum seed is its word's.
+template <int R, bool BATCH>
 __global__ void __launch_bounds__(kTRThreads, 2) k_trescan(Cell *__restrict__ cells, const TableArgs tab0,
                                                         u64 *__restrict__ fkey, u32 *__restrict__ fcell,
                                                         u32 *__restrict__ bitmap, TileRoundBufs tb,
-                                                        DecodeCtl *__restrict__ ctl, TRBatch) {
+                                                        DecodeCtl *__restrict__ ctl, TRBatch bt) {
   __shared__ u64 s_red[kTRThreads / 32];
   const u32 nl = *(volatile u32 *)tb.n_rescan;
   if (blockIdx.x >= nl) return;  // uniform
   const u32 tid = threadIdx.x, lane = lane_id();
-  const u64 seed_chk = tab0.seed[rank_of<R>(tab0)];
+  const u64 seed0 = BATCH ? 0ull : tab0.seed[rank_of<R>(tab0)];
   const u32 n = tab0.n_cells;
   u64 alive = 0, nonempty = 0, pushed = 0;
   u32 flags = 0;
@@ -313,7 +313,7 @@ __global__ void __launch_bounds__(kTRThreads, 2) k_trescan(Cell *__restrict__ ce
       bool pure = false;
       if (c < n) {
         const int cnt = cnts[it];
-        pure = cell_pure(cnt, keys[it], chks[it], seed_chk);
+        pure = cell_pure(cnt, keys[it], chks[it], BATCH ? bt.wseed[c >> 5] : seed0);
         alive += cnt >= 2;
         nonempty += cnt != 0;
         sum += cnt;

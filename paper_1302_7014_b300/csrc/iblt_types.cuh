@@ -191,10 +191,11 @@ pp_status tile_apply_pass(Cell *cells, const TableArgs &tab0, const TableArgs *t
                           const PrescanArgs *pre = nullptr);
 // Batched tile pass with the bin role fed from the keys: slab_chunk (device,
 // 2 * n_slabs) holds each slab's range of `chunks`; rank as for iblt_kernels.
-// Every record of a slab must fit its overflow set (tb.o_cap).
+// Every record of a slab must fit its overflow set (tb.o_cap).  pre (a build
+// from empty cells only): the write-out also finds F_1 (PrescanArgs).
 pp_status tile_keys_pass(Cell *cells, const TableArgs *tabs, const u64 *keys, const Chunk *chunks,
                          const u32 *slab_chunk, uint32_t n_slabs, int rank, TileBufs &tb, uint64_t n_cells,
-                         int sign, bool zero, cudaStream_t s);
+                         int sign, bool zero, cudaStream_t s, const PrescanArgs *pre = nullptr);
 
 // A tile with records in the current round: records [lo, lo + n) (absolute slots).
 struct TileAct {
@@ -242,7 +243,8 @@ struct PrescanArgs {
   u64 *fkey;
   u32 *fcell, *bitmap;
   DecodeCtl *ctl;
-  u64 seed_chk;
+  u64 seed_chk;         // the checksum seed (single table)
+  const u64 *wseed;     // batch: the checksum seed of each 32-cell word
 };
 
 // 32-cell words per 4096-cell tile of the tile rounds (the batch's word maps
@@ -272,7 +274,7 @@ struct IbltKernels {
   const void *sg_claim = nullptr, *sg_apply = nullptr;                         // signed, binned rounds
   const void *tscan = nullptr, *tclaim = nullptr, *tapply = nullptr;           // tile rounds (plain only)
   const void *tapply_sparse = nullptr, *trestore = nullptr;
-  const void *trescan = nullptr;  // tile rounds after a build that found F_1 (plain only)
+  const void *trescan = nullptr;  // tile rounds after a build that found F_1
 };
 
 // The kernel set for a rank code: 3 or 4 = that r; -4 = any r <= 4 (batched

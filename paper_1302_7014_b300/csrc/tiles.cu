@@ -31,16 +31,19 @@ static const void *tile_step_fn(bool batch, bool prescan = false) {
   return batch ? (const void *)k_tile_step<true> : (const void *)k_tile_step<false>;
 }
 
-// rank as for iblt_kernels: 3, 4, -4 (any r <= 4) or 0 (any r)
-static const void *tile_keys_fn(int rank) {
+// rank as for iblt_kernels: 3, 4, -4 (any r <= 4) or 0 (any r); prescan: the
+// write-out also finds F_1
+static const void *tile_keys_fn(int rank, bool prescan) {
   static bool attr = false;
-  const void *f[4] = {(const void *)k_tile_step_keys<3>, (const void *)k_tile_step_keys<4>,
-                      (const void *)k_tile_step_keys<-4>, (const void *)k_tile_step_keys<0>};
+  const void *f[8] = {(const void *)k_tile_step_keys<3>,        (const void *)k_tile_step_keys<4>,
+                      (const void *)k_tile_step_keys<-4>,       (const void *)k_tile_step_keys<0>,
+                      (const void *)k_tile_step_keys<3, true>,  (const void *)k_tile_step_keys<4, true>,
+                      (const void *)k_tile_step_keys<-4, true>, (const void *)k_tile_step_keys<0, true>};
   if (!attr) {
     for (const void *p : f) cudaFuncSetAttribute(p, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tile_step_smem());
     attr = true;
   }
-  return rank == 3 ? f[0] : rank == 4 ? f[1] : rank == -4 ? f[2] : f[3];
+  return f[(prescan ? 4 : 0) + (rank == 3 ? 0 : rank == 4 ? 1 : rank == -4 ? 2 : 3)];
 }
 
 uint64_t tile_cap_for(uint64_t slab_cap) {
@@ -133,8 +136,9 @@ pp_status tile_apply_pass(Cell *cells, const TableArgs &tab0, const TableArgs *t
 
 pp_status tile_keys_pass(Cell *cells, const TableArgs *tabs, const u64 *keys, const Chunk *chunks,
                          const u32 *slab_chunk, uint32_t n_slabs, int rank, TileBufs &tb, uint64_t n_cells,
-                         int sign, bool zero, cudaStream_t s) {
+                         int sign, bool zero, cudaStream_t s, const PrescanArgs *pre) {
   if (!tb.batch) return fail(PP_ERR_INVALID_ARG, "tile pass: batch buffers expected");
+  if (pre && !zero) return fail(PP_ERR_INVALID_ARG, "tile pass: F_1 is found only by a build");
   PP_CUDA(cudaMemsetAsync(tb.o_count, 0, (size_t)n_slabs * 4, s));
   TileArgs ta{tb.key, tb.off, tb.tab, tb.count, tb.cap * kTilesPerSlab, (u32)tb.cap, (u32)tb.o_cap,
               tb.o_key, tb.o_cell, tb.o_tab, tb.o_count};
@@ -144,8 +148,9 @@ pp_status tile_keys_pass(Cell *cells, const TableArgs *tabs, const u64 *keys, co
   u32 step = 0, n_apply = 0, n_bin = 0;
   u64 n = n_cells;
   int sg = sign, z = zero ? 1 : 0;
-  void *args[] = {&c, &tp, &ka, &ta, &step, &n_apply, &n_bin, &n, &sg, &z};
-  const void *fn = tile_keys_fn(rank);
+  PrescanArgs pa = pre ? *pre : PrescanArgs{};
+  void *args[] = {&c, &tp, &ka, &ta, &step, &n_apply, &n_bin, &n, &sg, &z, &pa};
+  const void *fn = tile_keys_fn(rank, pre != nullptr);
   const u32 sms = (u32)sm_count();
   for (step = 0; step <= n_slabs + 1; ++step) {
     n_bin = step < n_slabs ? 3 * sms : 0u;

@@ -23,14 +23,12 @@ struct Candidate {
   uint32_t ctas_per_sm, apply_ctas, binned, insert_chunk, rounds;
 };
 
-// One build + decode of the batch; per-table results in res.
+// One build + decode of the batch (pp_batch_build_decode); per-table results in res.
 pp_status run_once(pp_batch *b, uint32_t n_tables, const uint64_t *d_keys, const uint64_t *h_key_offsets,
                    uint64_t *d_out, const uint64_t *h_out_offsets, std::vector<pp_table_result> &res,
                    cudaStream_t s) {
-  pp_status st = pp_batch_build(b, d_keys, h_key_offsets, s);
-  if (st != PP_OK) return st;
   res.assign(n_tables, pp_table_result{});
-  return pp_batch_decode(b, d_out, h_out_offsets, res.data(), s);
+  return pp_batch_build_decode(b, d_keys, h_key_offsets, d_out, h_out_offsets, res.data(), s);
 }
 
 bool same_results(const std::vector<pp_table_result> &a, const std::vector<pp_table_result> &b) {

@@ -377,3 +377,96 @@ def test_tile_rounds_decode_twice_and_reuse(ppb):
     out2 = torch.full((max(1, int(koff2[-1])),), -1, dtype=torch.int64, device="cuda")
     res3 = b.decode(out2, koff2)
     check_against_oracle(specs2, keys2, koff2, res3, out2.cpu().numpy().view(np.uint64), b, cells_every=2)
+
+
+# ---- build + decode in one call: the build's tile write-out finds F_1 --------
+def run_fused_batch(pp, bm, specs, opts, keys=None, max_rounds=None):
+    """Batch.build_decode against the oracle, table by table (keys, rounds,
+    survivors, residue cell for cell)."""
+    if keys is None:
+        keys = [ppgen.distinct_keys(ppgen.edges_from_c(s[2], s[0]), s[4]) for s in specs]
+    koff = np.concatenate([[0], np.cumsum([k.size for k in keys])]).astype(np.uint64)
+    b = bm.Batch([s[0] for s in specs], [s[1] for s in specs], [s[3] for s in specs], opts)
+    # junk first: the build must wipe it and the decode must not see it
+    b.insert(torch.from_numpy(ppgen.distinct_keys(int(koff[-1]), 5).view(np.int64)).cuda(), koff)
+    out = torch.full((max(1, int(koff[-1])),), -1, dtype=torch.int64, device="cuda")
+    dk = torch.from_numpy(np.concatenate(keys).view(np.int64)).cuda()
+    if max_rounds is None:
+        res = b.build_decode(dk, koff, out, koff)
+        check_against_oracle(specs, keys, koff, res, out.cpu().numpy().view(np.uint64), b)
+    else:
+        with pytest.raises(pp.PPError) as ei:
+            b.build_decode(dk, koff, out, koff)
+        assert ei.value.name == "PP_ERR_ROUND_LIMIT"
+        for i, s in enumerate(specs):
+            ot = oracle.IBLT(s[0], s[1], s[3])
+            ot.insert(keys[i])
+            ot.decode_rounds(max_rounds=max_rounds)
+            cells = b.cells(i)
+            assert (cells["count"].astype(np.int64) == ot.count).all(), i
+            assert (cells["key_xor"] == ot.keyx).all() and (cells["chk_xor"] == ot.chkx).all(), i
+    return b, keys, koff
+
+
+@pytest.mark.parametrize("rs,opts", [((3,), dict(binned=1, rounds=2)), ((3, 4), dict(binned=1, rounds=2)),
+                                     ((2, 3, 5, 6), dict(binned=1, rounds=2)),
+                                     ((3, 4), dict(binned=1, rounds=2, host_loop=1)),
+                                     ((3,), dict(binned=1, rounds=2, ctas_per_sm=1))],
+                         ids=["r3", "r3-4", "r2-6", "r3-4-hostloop", "r3-small-grid"])
+def test_batch_build_decode_parity(ppb, rs, opts):
+    """Tables over several 2^21-cell slabs, some straddling two: the keys'
+    tile pass finds F_1 as it writes each tile out and the tile rounds start
+    from it.  Every table against the oracle."""
+    pp, bm = ppb
+    specs = _specs(24, 301 + len(rs), rs=rs, lo=15, hi=20.6, c_lo=0.5, c_hi=0.95)
+    assert sum(s[0] for s in specs) > 2 * (1 << 21)
+    # loads near the threshold take hundreds of rounds: keep every round's count
+    run_fused_batch(pp, bm, specs, pp.options(stats_rounds=4096, **opts))
+
+
+def test_batch_build_decode_round_limit(ppb):
+    pp, bm = ppb
+    specs = _specs(16, 331, rs=(3, 4), lo=15, hi=19, c_lo=0.7, c_hi=0.8)
+    run_fused_batch(pp, bm, specs, pp.options(binned=1, rounds=2, max_rounds=3), max_rounds=3)
+
+
+def test_batch_build_decode_crowded_tile_is_rescanned(ppb):
+    """One table's keys crowd the first 4096-cell tile of the arena past its
+    list's share, so the build leaves that tile to the decode's rescan."""
+    pp, bm = ppb
+    specs = _specs(12, 341, rs=(3,), lo=16, hi=19, c_lo=0.6, c_hi=0.7)
+    n0 = 1 << 20
+    specs[0] = (n0, 3, 0.6, specs[0][3], specs[0][4])
+    keys = [ppgen.distinct_keys(ppgen.edges_from_c(s[2], s[0]), s[4]) for s in specs]
+    cand = np.setdiff1d(ppgen.distinct_keys(2_000_000, 342), keys[0])
+    first = oracle.key_cells(n0, 3, specs[0][3], cand)[:, 0].astype(np.int64)
+    keys[0] = np.concatenate([keys[0], cand[first < 4096][:3000]])
+    cells = oracle.key_cells(n0, 3, specs[0][3], keys[0]).astype(np.int64)
+    per_tile = np.bincount((cells >> 12).ravel())
+    assert per_tile[0] > 1.3 * per_tile[1:].mean() + 256
+    for hl in (0, 1):
+        run_fused_batch(pp, bm, specs, pp.options(binned=1, rounds=2, host_loop=hl, stats_rounds=4096), keys=keys)
+
+
+def test_batch_build_decode_unfused_cases(ppb):
+    """Where the build cannot find F_1 (a table larger than a slab, or a batch
+    built with direct atomics) the call builds and decodes one after the other,
+    with the same results; repeated calls and a plain decode after more
+    inserts stay right."""
+    pp, bm = ppb
+    specs = _specs(10, 351, rs=(3, 4), lo=12, hi=17, c_lo=0.5, c_hi=0.9)
+    specs[3] = ((1 << 21) + 4099, 3, 0.7, specs[3][3], specs[3][4])
+    run_fused_batch(pp, bm, specs, pp.options(binned=1, rounds=2, stats_rounds=4096))  # slab lists
+    small = _specs(30, 352, rs=(3, 4), lo=6, hi=12, c_lo=0.5, c_hi=0.9)
+    b, keys, koff = run_fused_batch(pp, bm, small, pp.options(stats_rounds=4096))  # small arena: direct atomics
+    for rep in range(2):                                                    # again, and on top of a decode
+        out = torch.full((int(koff[-1]),), -1, dtype=torch.int64, device="cuda")
+        res = b.build_decode(torch.from_numpy(np.concatenate(keys).view(np.int64)).cuda(), koff, out, koff)
+        check_against_oracle(small, keys, koff, res, out.cpu().numpy().view(np.uint64), b)
+    with pytest.raises(pp.PPError) as ei:
+        short = koff.copy()
+        short[1:] -= 1
+        short[0] = 0
+        b.build_decode(torch.from_numpy(np.concatenate(keys).view(np.int64)).cuda(), koff, out,
+                       np.maximum.accumulate(short))
+    assert ei.value.name == "PP_ERR_CAPACITY"
