@@ -234,16 +234,22 @@ def test_seeds_match_convention(pp):
     assert gt.seeds() == [int(s) for s in oracle.hash_seeds(0x1234, 4)]
 
 
-def test_headline_full_size(pp):
-    """2^26 cells, r = 3, load 0.75 against the oracle's stored trajectory."""
+@pytest.mark.parametrize("fused", [False, True], ids=["insert-decode", "build_decode"])
+def test_headline_full_size(pp, fused):
+    """2^26 cells, r = 3, load 0.75 against the oracle's stored trajectory:
+    insert then decode, and the benchmark's one-call build + decode (whose
+    build finds F_1)."""
     gold = json.load(open(os.path.join(GOLDEN, "full_size.json")))["iblt_headline"]
     n, r, m = gold["n_cells"], gold["r"], gold["m"]
     keys = ppgen.distinct_keys(m, gold["key_seed"])
     gt = pp.IBLT(n, r, gold["table_seed"])
     dkeys = _dev(keys)
-    gt.insert(dkeys)
     out = torch.zeros(m, dtype=torch.int64, device="cuda")
-    res = gt.decode(out)
+    if fused:
+        res = gt.build_decode(dkeys, out)
+    else:
+        gt.insert(dkeys)
+        res = gt.decode(out)
     assert res.rounds == gold["rounds"]
     assert res.recovered_per_round == gold["recovered_per_round"]
     assert res.alive_cells_per_round == gold["alive_cells_per_round"]
