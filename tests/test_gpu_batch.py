@@ -424,10 +424,13 @@ def test_batch_build_decode_parity(ppb, rs, opts):
     run_fused_batch(pp, bm, specs, pp.options(stats_rounds=4096, **opts))
 
 
-def test_batch_build_decode_round_limit(ppb):
+@pytest.mark.parametrize("host_loop", [0, 1], ids=["graph", "hostloop"])
+@pytest.mark.parametrize("max_rounds", [1, 3])
+def test_batch_build_decode_round_limit(ppb, host_loop, max_rounds):
     pp, bm = ppb
     specs = _specs(16, 331, rs=(3, 4), lo=15, hi=19, c_lo=0.7, c_hi=0.8)
-    run_fused_batch(pp, bm, specs, pp.options(binned=1, rounds=2, max_rounds=3), max_rounds=3)
+    run_fused_batch(pp, bm, specs, pp.options(binned=1, rounds=2, max_rounds=max_rounds, host_loop=host_loop),
+                    max_rounds=max_rounds)
 
 
 def test_batch_build_decode_crowded_tile_is_rescanned(ppb):

@@ -539,11 +539,16 @@ def test_build_decode_crowded_tile_is_rescanned(pp, host_loop):
     run_fused_case(pp, n, r, keys, seed, opts=pp.options(binned=1, rounds=2, host_loop=host_loop))
 
 
-def test_build_decode_round_limit(pp):
+@pytest.mark.parametrize("host_loop", [0, 1], ids=["graph", "hostloop"])
+@pytest.mark.parametrize("max_rounds", [1, 3])
+def test_build_decode_round_limit(pp, host_loop, max_rounds):
+    """Stopped by the round limit (after round 1: F_1's cells, emptied by the
+    build, are put back), the table is the oracle's after that round."""
     n, r, seed = (1 << 21) + 3, 3, 98
     keys = ppgen.distinct_keys(ppgen.edges_from_c(0.80, n), 9099)
+    opts = pp.options(binned=1, rounds=2, max_rounds=max_rounds, host_loop=host_loop)
     with pytest.raises(pp.PPError) as ei:
-        run_fused_case(pp, n, r, keys, seed, opts=pp.options(binned=1, rounds=2, max_rounds=3), max_rounds=3)
+        run_fused_case(pp, n, r, keys, seed, opts=opts, max_rounds=max_rounds)
     assert ei.value.name == "PP_ERR_ROUND_LIMIT"
 
 
