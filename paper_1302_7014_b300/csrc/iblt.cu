@@ -70,6 +70,7 @@ static IbltKernels iblt_kernels_t() {
       allow_max_dynamic_smem((const void *)k_tapply<R, B>);
       allow_max_dynamic_smem((const void *)k_tclaim<R, B>);
       allow_max_dynamic_smem((const void *)k_tsort);
+      allow_max_dynamic_smem((const void *)k_tapply_sparse<R, B>);
       tattr = true;
     }
   }
@@ -171,7 +172,7 @@ pp_status tre_setup(TileRoundEngine &e, const IbltKernels &k, uint64_t n_cells, 
   if (b.base) return PP_OK;
   const uint32_t nt = (uint32_t)((n_cells + kTRCells - 1) / kTRCells);
   e.grid_tapply = persistent_grid(k.tapply, kTRThreads, kTApplySmem, 2);
-  e.grid_tsparse = persistent_grid(k.tapply_sparse, kTSThreads, 0, kTSCtas);
+  e.grid_tsparse = persistent_grid(k.tapply_sparse, kTSThreads, kTSSmem, kTSCtas);
   e.grid_tscan = e.grid_tapply;
   const uint32_t nd = (uint32_t)e.grid_tapply, nsp = (uint32_t)e.grid_tsparse;
   const uint64_t cap_d = (uint64_t)kTRCells * ((nt + nd - 1) / nd);
@@ -346,7 +347,7 @@ pp_status tre_build_graph(const TileRoundEngine &e, const IbltKernels &k, TileRo
   // dense and sparse tiles in two kernels that may run side by side
   st = tre_node(&n_apply[0], body, &n_act, 1, k.tapply, e.grid_tapply, kTRThreads, kTApplySmem, a.apply);
   if (st != PP_OK) goto done;
-  st = tre_node(&n_apply[1], body, &n_act, 1, k.tapply_sparse, e.grid_tsparse, kTSThreads, 0, a.apply);
+  st = tre_node(&n_apply[1], body, &n_act, 1, k.tapply_sparse, e.grid_tsparse, kTSThreads, kTSSmem, a.apply);
   if (st != PP_OK) goto done;
   st = tre_node(&n_end, body, n_apply, 2, (const void *)k_round_end, 1, 32, 0, a.end);
   if (st != PP_OK) goto done;
@@ -370,7 +371,7 @@ pp_status tre_host_loop(const TileRoundEngine &e, const IbltKernels &k, TileRoun
                              e.smem_tsort, s));
     PP_CUDA(cudaLaunchKernel((const void *)k_tactive, dim3(e.grid_act), dim3(kBlock), a.active, 0, s));
     PP_CUDA(cudaLaunchKernel(k.tapply, dim3(e.grid_tapply), dim3(kTRThreads), a.apply, kTApplySmem, s));
-    PP_CUDA(cudaLaunchKernel(k.tapply_sparse, dim3(e.grid_tsparse), dim3(kTSThreads), a.apply, 0, s));
+    PP_CUDA(cudaLaunchKernel(k.tapply_sparse, dim3(e.grid_tsparse), dim3(kTSThreads), a.apply, kTSSmem, s));
     PP_CUDA(cudaLaunchKernel((const void *)k_round_end, dim3(1), dim3(32), a.end, 0, s));
     PP_CUDA(cudaMemcpyAsync(h_more, &a.ctl->more, sizeof(u32), cudaMemcpyDeviceToHost, s));
     PP_CUDA(cudaStreamSynchronize(s));

@@ -62,7 +62,7 @@ constexpr u32 kTSCap = 512;                  // records of a sparse tile (at mos
 constexpr u32 kTSSlots = 1024;               // hash slots of k_tapply_sparse
 constexpr u32 kTSEmpty = 0xffffffffu;
 #ifndef PP_TSPARSE_CTAS
-#define PP_TSPARSE_CTAS 6
+#define PP_TSPARSE_CTAS 4
 #endif
 constexpr int kTSCtas = PP_TSPARSE_CTAS;    // resident blocks per SM of k_tapply_sparse
 #ifndef PP_TCLAIM_ITEMS
@@ -1014,92 +1014,90 @@ __global__ void __launch_bounds__(kTRThreads, 2) k_tapply(Cell *__restrict__ cel
   if (flags) atomicOr(&ctl->flags, flags);
 }
 
+// Shared memory of k_tapply_sparse: two hash tables (slot -> cell offset,
+// folded key XOR, checksum XOR, record count) and their touched-slot lists.
+constexpr size_t kTSSmem = 2 * (size_t)kTSSlots * (4 + 8 + 8 + 4) + 2 * (size_t)kTSCap * 2;
+
 // The same for the sparse tiles, with a small hash table (open addressing on
 // the cell offset) in place of the per-cell arrays, so that many tiles are in
-// flight per SM.  Runs n_seg_s blocks; block b takes the sparse tiles b,
-// b + n_seg_s, ... (at most kTSCap records, hence pushes, each) and writes
-// frontier segment n_seg_d + b.  BATCH: the checksum seeds of a tile's 128
-// words travel with its records, into one of two shared buffers.
+// flight per SM; block b takes the sparse tiles b, b + n_seg_s, ... (at most
+// kTSCap records, hence pushes, each).  The block keeps two tables: while
+// the cells of tile k are loaded from memory, the records of tile k + 1 (in
+// registers since the previous step) are folded into the other table, and the
+// records of tile k + 2 are fetched; one barrier per tile.  Tile k uses table
+// k % 2, touched-slot counter k % 3 and (BATCH) seed buffer k % 3: a counter
+// or seed buffer is written again only after the barrier that follows its
+// last read.  Runs n_seg_s blocks; block b writes frontier segment n_seg_d + b.
 template <int R, bool BATCH>
 __global__ void __launch_bounds__(kTSThreads, kTSCtas) k_tapply_sparse(Cell *__restrict__ cells, const TableArgs tab0,
                                                                  TileRoundBufs tb, u64 *__restrict__ fkey,
                                                                  u32 *__restrict__ fcell, u32 *__restrict__ bitmap,
                                                                  DecodeCtl *__restrict__ ctl, TRBatch bt) {
   if (*(volatile u32 *)&ctl->round == 0) return;  // round 0: F_1 empty or an error, no work
-  __shared__ u32 h_off[kTSSlots];   // cell offset of the slot, kTSEmpty if free
-  __shared__ u64 h_key[kTSSlots], h_chk[kTSSlots];
-  __shared__ u32 h_cnt[kTSSlots];
-  __shared__ u16 s_slot[kTSCap];    // the slots in use
-  __shared__ u32 s_ns[2], s_seg;  // touched cells of the current tile: two counters, used in turn
+  extern __shared__ __align__(16) unsigned char smem[];
+  u64 *h_key = reinterpret_cast<u64 *>(smem);            // 2 x kTSSlots
+  u64 *h_chk = h_key + 2 * kTSSlots;                     // 2 x kTSSlots
+  u32 *h_off = reinterpret_cast<u32 *>(h_chk + 2 * kTSSlots);  // 2 x kTSSlots, kTSEmpty if free
+  u32 *h_cnt = h_off + 2 * kTSSlots;                     // 2 x kTSSlots
+  u16 *s_slot = reinterpret_cast<u16 *>(h_cnt + 2 * kTSSlots);  // 2 x kTSCap: the slots in use
+  __shared__ u32 s_ns[3], s_seg;
   __shared__ u64 s_red[kTSThreads / 32];
   constexpr u32 kW = kTRCells / 32;  // words of a tile
   static_assert(!BATCH || kTSThreads >= (int)kW, "one thread per word of a tile");
-  __shared__ u64 s_wseed[BATCH ? 2 : 1][BATCH ? kW : 1];
+  __shared__ u64 s_wseed[BATCH ? 3 : 1][BATCH ? kW : 1];
   const u32 tid = threadIdx.x;
   const u64 seed0 = BATCH ? 0ull : tab0.seed[rank_of<R>(tab0)];
   const u32 n_act = *(volatile u32 *)&ctl->n_act;
   const u64 seg0 = tb.fstart[tb.n_seg_d + blockIdx.x];
+  const u32 g = gridDim.x;
   u32 flags = 0;
-  for (u32 i = tid; i < kTSSlots; i += kTSThreads) {
+  for (u32 i = tid; i < 2 * kTSSlots; i += kTSThreads) {
     h_off[i] = kTSEmpty;
     h_key[i] = 0;
     h_chk[i] = 0;
     h_cnt[i] = 0;
   }
-  if (tid == 0) s_ns[0] = s_ns[1] = 0, s_seg = 0;
-  __syncthreads();
+  if (tid == 0) s_ns[0] = s_ns[1] = s_ns[2] = 0, s_seg = 0;
   u64 emptied = 0, dropped = 0;
   constexpr int PER = kTSCap / kTSThreads;
   static_assert(kTSCap % kTSThreads == 0, "a sparse tile's records split evenly over the threads");
-  // the records of the block's next tile are loaded while the current one's
-  // cells are updated, and the list entry of the tile after it one step
-  // earlier still, so that no load waits on another
-  TileAct nxt{}, nxt2{};
-  u64 nx[PER];
-  u32 no[PER];
-  u64 nws = 0;  // BATCH: the next tile's seed of word tid
-  auto load_tile = [&](u32 ai) {
-    nxt = nxt2;
-    nxt2.n = 0;
-    if (ai + gridDim.x < n_act) nxt2 = tb.act[ai + gridDim.x];
+  auto entry = [&](u32 ai) {
+    TileAct a{};
+    if (ai < n_act) a = tb.act[ai];
+    return a;
+  };
+  // a tile's records (and BATCH: its word seed for thread tid) into registers
+  u64 x[PER];
+  u32 o[PER];
+  u64 nws = 0;
+  auto fetch = [&](const TileAct &a) {
 #pragma unroll
     for (int k = 0; k < PER; ++k) {
       const u32 i = (u32)k * kTSThreads + tid;
-      no[k] = i < nxt.n ? (u32)__ldcs(tb.rec_off + nxt.lo + i) : kTSEmpty;
-      nx[k] = i < nxt.n ? __ldcs(tb.rec_key + nxt.lo + i) : 0ull;
+      o[k] = i < a.n ? (u32)__ldcs(tb.rec_off + a.lo + i) : kTSEmpty;
+      x[k] = i < a.n ? __ldcs(tb.rec_key + a.lo + i) : 0ull;
     }
-    if (BATCH && tid < kW && nxt.n) nws = bt.wseed[((u64)nxt.tile << (kTRShift - 5)) + tid];
+    if (BATCH && tid < kW && a.n) nws = bt.wseed[((u64)a.tile << (kTRShift - 5)) + tid];
   };
-  if (blockIdx.x < n_act) nxt2 = tb.act[blockIdx.x];
-  load_tile(blockIdx.x);
-  if constexpr (BATCH) {
-    if (tid < kW) s_wseed[0][tid] = nws;
-    __syncthreads();
-  }
-  u32 par = 0;
-  for (u32 ai = blockIdx.x; ai < n_act; ai += gridDim.x, par ^= 1) {
-    const TileAct cur = nxt;
-    const u64 b = cur.lo;
-    const u32 nrec = cur.n, t = cur.tile;
-    u64 x[PER];
-    u32 o[PER];
-#pragma unroll
-    for (int k = 0; k < PER; ++k) {
-      x[k] = nx[k];
-      o[k] = no[k];
-    }
+  // folds the records in registers into table hb (touched slots counted in
+  // s_ns[cb], listed in s_slot), checksums with seed buffer sb
+  auto fold = [&](u32 hb, u32 cb, u32 sb) {
+    u32 *ho = h_off + hb * kTSSlots, *hc = h_cnt + hb * kTSSlots;
+    u64 *hk = h_key + hb * kTSSlots, *hx = h_chk + hb * kTSSlots;
+    u16 *sl = s_slot + hb * kTSCap;
 #pragma unroll
     for (int k = 0; k < PER; ++k) {
       bool fresh = false;
       u32 slot = 0;
-      if (o[k] != kTSEmpty) {
-        const u32 off = o[k] & (kTRCells - 1);
+      u32 ok = o[k];
+      if (ok != kTSEmpty) {
+        const u32 off = ok & (kTRCells - 1);
         slot = off & (kTSSlots - 1);
         // at most kTSCap of the kTSSlots slots are taken, so a free or matching
         // slot is found within kTSCap + 1 probes
         bool found = false;
         for (u32 probe = 0; probe <= kTSCap; ++probe) {
-          const u32 prev = atomicCAS(h_off + slot, kTSEmpty, off);
+          const u32 prev = atomicCAS(ho + slot, kTSEmpty, off);
           if (prev == kTSEmpty || prev == off) {
             fresh = prev == kTSEmpty;
             found = true;
@@ -1109,64 +1107,88 @@ __global__ void __launch_bounds__(kTSThreads, kTSCtas) k_tapply_sparse(Cell *__r
         }
         if (!found) {
           flags |= FLAG_INTERNAL;
-          o[k] = kTSEmpty;
+          ok = kTSEmpty;
         }
       }
-      if (o[k] != kTSEmpty) {
-        const u64 cs = checksum(x[k], BATCH ? s_wseed[par][(o[k] & (kTRCells - 1)) >> 5] : seed0);
-        atomicAdd(h_cnt + slot, 1u);
-        smem_xor64(h_key + slot, x[k]);
-        smem_xor64(h_chk + slot, cs);
+      if (ok != kTSEmpty) {
+        const u64 cs = checksum(x[k], BATCH ? s_wseed[sb][(ok & (kTRCells - 1)) >> 5] : seed0);
+        atomicAdd(hc + slot, 1u);
+        smem_xor64(hk + slot, x[k]);
+        smem_xor64(hx + slot, cs);
       }
-      const u32 q = warp_reserve<u32>(fresh, &s_ns[par]);
-      if (fresh) s_slot[q] = (u16)slot;
+      const u32 q = warp_reserve<u32>(fresh, &s_ns[cb]);
+      if (fresh) sl[q] = (u16)slot;
     }
-    __syncthreads();
-    discard_records(tb, b, nrec, tid, kTSThreads);
-    load_tile(ai + gridDim.x);
-    const u32 ns = s_ns[par];
-    // the other counter was last read before the barrier above: ready it for the next tile
-    if (tid == 0) s_ns[par ^ 1] = 0;
-    const u32 c0 = t << kTRShift;
-    // both cells' loads before either store (the cell accesses are volatile
-    // asm, kept in program order)
+  };
+  // prologue: tile 0 folded into table 0, tile 1's records in registers
+  TileAct cur = entry(blockIdx.x), a1 = entry(blockIdx.x + g), a2 = entry(blockIdx.x + 2 * g);
+  fetch(cur);
+  if (BATCH && tid < kW) s_wseed[0][tid] = nws;
+  __syncthreads();  // tables, counters and seeds of tile 0 ready
+  if (cur.n) {
+    fold(0, 0, 0);
+    discard_records(tb, cur.lo, cur.n, tid, kTSThreads);
+  }
+  fetch(a1);
+  if (BATCH && tid < kW) s_wseed[1][tid] = nws;
+  __syncthreads();
+  u32 k = 0;
+  for (u32 ai = blockIdx.x; ai < n_act; ai += g, ++k) {
+    const u32 hb = k & 1u, cb = k % 3u;
+    const u32 ns = s_ns[cb];
+    const u32 c0 = cur.tile << kTRShift;
+    const u32 *ho = h_off + hb * kTSSlots, *hc = h_cnt + hb * kTSSlots;
+    const u64 *hk = h_key + hb * kTSSlots, *hx = h_chk + hb * kTSSlots;
+    const u16 *sl = s_slot + hb * kTSCap;
+    // the cells of tile k: every load in flight before any store (the cell
+    // accesses are volatile asm, kept in program order)
     u32 slots[PER], cs[PER];
     u64 keys[PER], chks[PER];
     int cnts[PER];
 #pragma unroll
-    for (int k = 0; k < PER; ++k) {
-      const u32 q = (u32)k * kTSThreads + tid;
-      slots[k] = cs[k] = 0;
-      keys[k] = chks[k] = 0;
-      cnts[k] = 0;
-      if (q < ns) {
-        slots[k] = s_slot[q];
-        cs[k] = c0 + h_off[slots[k]];
-        ld_cell_cg(cells + cs[k], keys[k], chks[k], cnts[k]);
+    for (int q = 0; q < PER; ++q) {
+      const u32 qq = (u32)q * kTSThreads + tid;
+      slots[q] = cs[q] = 0;
+      keys[q] = chks[q] = 0;
+      cnts[q] = 0;
+      if (qq < ns) {
+        slots[q] = sl[qq];
+        cs[q] = c0 + ho[slots[q]];
+        ld_cell_cg(cells + cs[q], keys[q], chks[q], cnts[q]);
       }
     }
+    // while they travel: tile k + 1 into the other table, tile k + 2 fetched
+    if (a1.n) {
+      fold(hb ^ 1u, (k + 1) % 3u, (k + 1) % 3u);
+      discard_records(tb, a1.lo, a1.n, tid, kTSThreads);
+    }
+    const TileAct a3 = entry(ai + 3 * g);
+    fetch(a2);
+    const u32 sb = k % 3u;
 #pragma unroll
-    for (int k = 0; k < PER; ++k) {
-      const u32 q = (u32)k * kTSThreads + tid;
-      const bool v = q < ns;
-      const u32 slot = slots[k], c = cs[k];
-      u64 key = keys[k], chk = chks[k];
-      const int cnt = cnts[k];
+    for (int q = 0; q < PER; ++q) {
+      const u32 qq = (u32)q * kTSThreads + tid;
+      const bool v = qq < ns;
+      const u32 slot = slots[q], c = cs[q];
+      u64 key = keys[q], chk = chks[q];
+      const int cnt = cnts[q];
       bool pure = false;
       if (v) {
-        const int nc = cnt - (int)h_cnt[slot];
-        key ^= h_key[slot];
-        chk ^= h_chk[slot];
-        pure = cell_pure(nc, key, chk, BATCH ? s_wseed[par][(c - c0) >> 5] : seed0);
+        const int nc = cnt - (int)hc[slot];
+        key ^= hk[slot];
+        chk ^= hx[slot];
+        pure = cell_pure(nc, key, chk, BATCH ? s_wseed[sb][(c - c0) >> 5] : seed0);
         // a pure cell is stored empty: its one key leaves it next round
         if (pure) st_cell_cs(cells + c, 0ull, 0ull, 0);
         else st_cell_cs(cells + c, key, chk, nc);
         emptied += (u64)(long long)((cnt != 0) - (!pure && nc != 0));
         dropped += cnt >= 2 && nc < 2;
-        h_off[slot] = kTSEmpty;
-        h_key[slot] = 0;
-        h_chk[slot] = 0;
-        h_cnt[slot] = 0;
+        u32 *hom = h_off + hb * kTSSlots, *hcm = h_cnt + hb * kTSSlots;
+        u64 *hkm = h_key + hb * kTSSlots, *hxm = h_chk + hb * kTSSlots;
+        hom[slot] = kTSEmpty;
+        hkm[slot] = 0;
+        hxm[slot] = 0;
+        hcm[slot] = 0;
       }
       const u32 p = warp_reserve<u32>(pure, &s_seg);
       if (pure && p < tb.cap_s) {
@@ -1177,9 +1199,13 @@ __global__ void __launch_bounds__(kTSThreads, kTSCtas) k_tapply_sparse(Cell *__r
         flags |= FLAG_INTERNAL;  // cannot happen: a segment holds every push of its block's tiles
       }
     }
-    // the next tile's seeds (loaded with its records) into the other buffer,
-    // whose last reads ended at the previous barrier
-    if (BATCH && tid < kW) s_wseed[par ^ 1][tid] = nws;
+    // tile k + 2's seeds and counter: their buffers were last read by tile
+    // k - 1, before the previous barrier
+    if (BATCH && tid < kW) s_wseed[(k + 2) % 3u][tid] = nws;
+    if (tid == 0) s_ns[(k + 2) % 3u] = 0;
+    cur = a1;
+    a1 = a2;
+    a2 = a3;
     __syncthreads();
   }
   const u64 e = block_sum<u64, kTSThreads>(emptied, s_red);
