@@ -85,7 +85,8 @@ typedef struct pp_options {
   uint32_t frontier_switch; /* pp_peel_kcore, kcore_mode 0: edge-centric rounds run while
                             |frontier| * frontier_switch >= edges left (default 2) */
   uint32_t insert_chunk; /* batches: keys per insert work item (default 4096) */
-  uint32_t l2_fetch;     /* pp_iblt_create: 1 (default) = set this process's L2 fetch
+  uint32_t l2_fetch;     /* pp_iblt_create, pp_batch_create, pp_server_start: 1
+                            (default) = set this process's L2 fetch
                             granularity limit (cudaLimitMaxL2FetchGranularity, a
                             per-context hint that ends with the process) to 32 bytes,
                             so that a scattered 32-byte cell read fetches one sector

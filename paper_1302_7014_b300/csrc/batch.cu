@@ -417,6 +417,8 @@ pp_status pp_batch_create(pp_batch **out, uint32_t n_tables, const uint64_t *n_c
   pp_batch *b = new pp_batch();
   b->n_tables = n_tables;
   b->opt = resolve_options(opt);
+  // scattered 32-byte cell reads: one sector fetched from DRAM, not two
+  if (b->opt.l2_fetch == 1) cudaDeviceSetLimit(cudaLimitMaxL2FetchGranularity, 32);
   b->h_tabs.resize(n_tables);
   b->items.assign(n_tables, 0);
   uint64_t base = 0;

@@ -505,6 +505,8 @@ pp_status pp_server_start(pp_server **out, const pp_server_config *cfg, const pp
     delete s;
     return cuda_fail(e, "cudaSetDevice", __FILE__, __LINE__);
   }
+  // scattered 32-byte cell reads: one sector fetched from DRAM, not two
+  if (o.l2_fetch == 1) cudaDeviceSetLimit(cudaLimitMaxL2FetchGranularity, 32);
   s->k = iblt_kernels((int)cfg->r, true);
   s->smem_peel = peel_smem_bytes(s->k.nr, true);
   pp_status st = alloc_server(s);
