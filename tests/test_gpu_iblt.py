@@ -588,3 +588,14 @@ def test_build_decode_repeated_with_growth_and_plain_calls(pp):
         small.build_decode(_dev(keys), out[:10])
     assert ei.value.name == "PP_ERR_CAPACITY"
     small.close()
+
+
+def test_build_decode_slab_overflow_falls_back(pp):
+    """Keys whose first cell falls in the first 2^21-cell slab overfill that
+    slab's list: build_decode notices before the tile pass and builds with
+    direct atomics, then decodes the plain way, with the oracle's results."""
+    n, r, seed = 1 << 23, 3, 7
+    cand = ppgen.distinct_keys(3_000_000, 8)
+    first = oracle.key_cells(n, r, seed, cand)[:, 0]
+    keys = cand[first < (1 << 21)]
+    run_fused_case(pp, n, r, keys, seed)
