@@ -362,37 +362,51 @@ __global__ void __launch_bounds__(kTRThreads, 2) k_trescan(Cell *__restrict__ ce
 __global__ void __launch_bounds__(1024) k_tprefix(TileRoundBufs tb, DecodeCtl *__restrict__ ctl) {
   __shared__ u64 s_w[33];
   const u32 tid = threadIdx.x;
-  const u32 per = (tb.n_tiles + 1023) / 1024;
-  const u32 lo = tid * per, hi = min(lo + per, tb.n_tiles);
-  u64 own = 0;
-  for (u32 t = lo; t < hi; ++t) own += (tb.sum[t] + kTRAlign - 1) / kTRAlign * kTRAlign;
-  u64 inc = own;
+  constexpr u32 kPer = 4;  // consecutive tiles per thread per pass: 4096 tiles a pass, loads coalesced
+  const u32 nt = tb.n_tiles;
+  u64 carry = 0;  // region bytes of the tiles before this pass (the same in every thread)
+  for (u32 p0 = 0; p0 < nt; p0 += 1024 * kPer) {
+    const u32 t0 = p0 + tid * kPer;
+    u64 v[kPer], own = 0;
 #pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const u64 y = __shfl_up_sync(kFull, inc, o);
-    if ((int)lane_id() >= o) inc += y;
-  }
-  if (lane_id() == 31) s_w[tid >> 5] = inc;
-  __syncthreads();
-  if (tid < 32) {
-    const u64 w = s_w[tid];
-    u64 wi = w;
+    for (u32 q = 0; q < kPer; ++q) {
+      v[q] = t0 + q < nt ? (u64)(tb.sum[t0 + q] + kTRAlign - 1) / kTRAlign * kTRAlign : 0ull;
+      own += v[q];
+    }
+    u64 inc = own;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
-      const u64 y = __shfl_up_sync(kFull, wi, o);
-      if ((int)tid >= o) wi += y;
+      const u64 y = __shfl_up_sync(kFull, inc, o);
+      if ((int)lane_id() >= o) inc += y;
     }
-    s_w[tid] = wi - w;
-    if (tid == 31) s_w[32] = wi;
-  }
-  __syncthreads();
-  u64 run = s_w[tid >> 5] + inc - own;
-  for (u32 t = lo; t < hi; ++t) {
-    tb.base[t] = run;
-    tb.base64[t] = (u32)(run / kTRAlign);
-    tb.pos[(u64)t * kTRPosStride] = 0;
-    tb.done[t] = 0;
-    run += (tb.sum[t] + kTRAlign - 1) / kTRAlign * kTRAlign;
+    if (lane_id() == 31) s_w[tid >> 5] = inc;
+    __syncthreads();
+    if (tid < 32) {
+      const u64 w = s_w[tid];
+      u64 wi = w;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const u64 y = __shfl_up_sync(kFull, wi, o);
+        if ((int)tid >= o) wi += y;
+      }
+      s_w[tid] = wi - w;
+      if (tid == 31) s_w[32] = wi;
+    }
+    __syncthreads();
+    u64 run = carry + s_w[tid >> 5] + inc - own;
+#pragma unroll
+    for (u32 q = 0; q < kPer; ++q) {
+      const u32 t = t0 + q;
+      if (t < nt) {
+        tb.base[t] = run;
+        tb.base64[t] = (u32)(run / kTRAlign);
+        tb.pos[(u64)t * kTRPosStride] = 0;
+        tb.done[t] = 0;
+      }
+      run += v[q];
+    }
+    carry += s_w[32];
+    __syncthreads();  // s_w is written again by the next pass
   }
   for (u32 k = tid; k < tb.n_seg_s; k += 1024) tb.fseg[tb.n_seg_d + k] = 0;
   for (u32 k = tid; k < tb.n_bins; k += 1024) {
@@ -400,10 +414,10 @@ __global__ void __launch_bounds__(1024) k_tprefix(TileRoundBufs tb, DecodeCtl *_
     tb.cdone[k] = 0;
   }
   if (tid == 0) {
-    tb.base[tb.n_tiles] = s_w[32];
-    tb.base64[tb.n_tiles] = (u32)(s_w[32] / kTRAlign);
+    tb.base[tb.n_tiles] = carry;
+    tb.base64[tb.n_tiles] = (u32)(carry / kTRAlign);
     u32 fl = *(volatile u32 *)&ctl->flags;
-    if (s_w[32] > tb.rec_cap) {
+    if (carry > tb.rec_cap) {
       atomicOr(&ctl->flags, (u32)FLAG_CAPACITY);
       fl |= FLAG_CAPACITY;
     }
